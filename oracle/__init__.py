@@ -1,0 +1,287 @@
+"""ctypes binding of the serial FP64 CPU oracle (``vcsgc_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain reference the CUDA path
+is checked against: only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  The product path never
+calls it, and it imports nothing from the CUDA package.
+
+``build()`` compiles the C source with gcc into ``oracle/liboracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "vcsgc_oracle.c")
+HDR = os.path.join(HERE, "vcsgc_oracle.h")
+LIB = os.path.join(HERE, "liboracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if the shared object is missing or stale."""
+    stale = (not os.path.exists(LIB) or
+             os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
+    if force or stale:
+        tmp = LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class EamIn(C.Structure):
+    _fields_ = [("nr", C.c_int32), ("dr", C.c_double), ("nrho", C.c_int32),
+                ("drho", C.c_double), ("rc", C.c_double),
+                ("pair", C.c_void_p * 3), ("dpair", C.c_void_p * 3),
+                ("dens", C.c_void_p * 2), ("ddens", C.c_void_p * 2),
+                ("embed", C.c_void_p * 2), ("dembed", C.c_void_p * 2)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("n_sites", C.c_int64), ("n_b", C.c_int64), ("energy", C.c_double),
+                ("steps", C.c_int64), ("trials", C.c_int64), ("local_accepts", C.c_int64),
+                ("global_trials", C.c_int64), ("global_accepts", C.c_int64),
+                ("flips", C.c_int64), ("near_ties", C.c_int64), ("sum_c", C.c_double),
+                ("sum_c2", C.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        P, D, I64, I32, U64 = C.c_void_p, C.c_double, C.c_int64, C.c_int, C.c_uint64
+        sig = {
+            "orc_create": (P, [I64, P, P, P, P, P, P, I32]),
+            "orc_free": (None, [P]),
+            "orc_set_params": (I32, [P, D, D, D, I32, D, U64]),
+            "orc_schedule_blocks": (I32, [P] + [I32] * 9),
+            "orc_schedule_sublattice": (I32, [P] + [I32] * 6),
+            "orc_schedule_spatial": (I32, [P] + [I32] * 6),
+            "orc_schedule_min_separation": (D, [P]),
+            "orc_schedule_info": (I64, [P, P, P]),
+            "orc_schedule_export": (None, [P, P, P, P]),
+            "orc_parallel_steps": (I32, [P, I64]),
+            "orc_serial_steps": (I32, [P, I64, I32]),
+            "orc_delta_e": (D, [P, I64]),
+            "orc_delta_e_full": (D, [P, I64]),
+            "orc_energy_full": (D, [P]),
+            "orc_flip": (None, [P, I64]),
+            "orc_get_types": (None, [P, P]),
+            "orc_set_types": (None, [P, P]),
+            "orc_get_rho": (None, [P, P]),
+            "orc_get_obs": (None, [P, P]),
+            "orc_reset_counters": (None, [P]),
+            "orc_neighbour_count": (I64, [P, I64]),
+            "orc_neighbour": (None, [P, I64, I64, P, P, P]),
+            "orc_philox": (None, [P, P, P]),
+            "orc_u01": (D, [C.c_uint32, C.c_uint32]),
+            "orc_below": (U64, [C.c_uint32, C.c_uint32, U64]),
+            "orc_spline": (I32, [P, I32, D, P, P]),
+            "orc_forces": (None, [P, P, P, P]),
+            "orc_set_md": (None, [P, P, P, P, D, D, D, D, D, U64]),
+            "orc_md_steps": (I32, [P, I64]),
+            "orc_get_md": (None, [P, P, P, P, P, P, P]),
+            "orc_kinetic_energy": (D, [P]),
+            "orc_hybrid_cycles": (I32, [P, I64, I64, I64]),
+            "orc_run_histogram": (I32, [P, I64, I32, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def philox(ctr, key):
+    """Philox4x32-10 block: four uint32 counter words, two key words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox(_p(c), _p(k), _p(out))
+    return out
+
+
+def u01(lo, hi):
+    return lib().orc_u01(int(lo), int(hi))
+
+
+def below(lo, hi, m):
+    return lib().orc_below(int(lo), int(hi), int(m))
+
+
+class System:
+    """One VC-SGC system held by the oracle."""
+
+    def __init__(self, lattice, types, tables, brute=False):
+        self._keep = []
+        x, y, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (lattice.x, lattice.y, lattice.z))
+        box = np.ascontiguousarray(lattice.box, dtype=np.float64)
+        t = np.ascontiguousarray(types, dtype=np.uint8)
+        e = EamIn()
+        e.nr, e.dr, e.nrho, e.drho, e.rc = tables.nr, tables.dr, tables.nrho, tables.drho, tables.rc
+
+        def ptr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return a.ctypes.data
+
+        for q in range(3):
+            e.pair[q] = ptr(tables.pair[q])
+            e.dpair[q] = ptr(tables.dpair[q])
+        for q in range(2):
+            e.dens[q] = ptr(tables.dens[q])
+            e.ddens[q] = ptr(tables.ddens[q])
+            e.embed[q] = ptr(tables.embed[q])
+            e.dembed[q] = ptr(tables.dembed[q])
+        self.n = int(x.shape[0])
+        self.h = lib().orc_create(self.n, _p(x), _p(y), _p(z), _p(box), _p(t), C.byref(e),
+                                  1 if brute else 0)
+        if not self.h:
+            raise ValueError("oracle: invalid system")
+        self._keep = []
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_free(self.h)
+            self.h = None
+
+    # ---- parameters and schedules
+    def set_params(self, phi, kappa, T, kappa_units=0, c0=-1.0, seed=0):
+        if lib().orc_set_params(self.h, phi, kappa, T, kappa_units, c0, seed):
+            raise ValueError("oracle: bad parameters")
+
+    def schedule_blocks(self, cells, block, colours=(2, 2, 2)):
+        if lib().orc_schedule_blocks(self.h, *cells, *block, *colours):
+            raise ValueError("oracle: block schedule does not divide the lattice")
+
+    def schedule_sublattice(self, cells, period=(4, 4, 4)):
+        if lib().orc_schedule_sublattice(self.h, *cells, *period):
+            raise ValueError("oracle: sublattice schedule does not divide the lattice")
+
+    def schedule_spatial(self, blocks, colours=(2, 2, 2)):
+        if lib().orc_schedule_spatial(self.h, *blocks, *colours):
+            raise ValueError("oracle: spatial schedule does not divide")
+
+    def schedule_min_separation(self):
+        return lib().orc_schedule_min_separation(self.h)
+
+    def schedule_tables(self):
+        nc = C.c_int64()
+        dpc = C.c_int64()
+        nd = lib().orc_schedule_info(self.h, C.byref(nc), C.byref(dpc))
+        col = np.zeros(nc.value + 1, dtype=np.int64)
+        dom = np.zeros(nd + 1, dtype=np.int64)
+        sites = np.zeros(self.n, dtype=np.int64)
+        lib().orc_schedule_export(self.h, _p(col), _p(dom), _p(sites))
+        return col, dom, sites
+
+    # ---- sampling
+    def parallel_steps(self, n):
+        if lib().orc_parallel_steps(self.h, int(n)):
+            raise RuntimeError("oracle: no schedule")
+
+    def serial_steps(self, n, mode=0):
+        lib().orc_serial_steps(self.h, int(n), int(mode))
+
+    def run_histogram(self, n_steps, mode=-1):
+        """Histogram of n_B after each of n_steps steps, and the mean energy."""
+        hist = np.zeros(self.n + 1, dtype=np.int64)
+        se = C.c_double(0.0)
+        if lib().orc_run_histogram(self.h, int(n_steps), int(mode), _p(hist), C.byref(se)):
+            raise RuntimeError("oracle: no schedule")
+        return hist, se.value / max(1, n_steps)
+
+    # ---- energies
+    def delta_e(self, i):
+        return lib().orc_delta_e(self.h, int(i))
+
+    def delta_e_full(self, i):
+        return lib().orc_delta_e_full(self.h, int(i))
+
+    def energy_full(self):
+        return lib().orc_energy_full(self.h)
+
+    def flip(self, i):
+        lib().orc_flip(self.h, int(i))
+
+    # ---- state
+    @property
+    def types(self):
+        out = np.zeros(self.n, dtype=np.uint8)
+        lib().orc_get_types(self.h, _p(out))
+        return out
+
+    def set_types(self, t):
+        t = np.ascontiguousarray(t, dtype=np.uint8)
+        lib().orc_set_types(self.h, _p(t))
+
+    @property
+    def rho(self):
+        out = np.zeros(self.n, dtype=np.float64)
+        lib().orc_get_rho(self.h, _p(out))
+        return out
+
+    def obs(self):
+        o = Obs()
+        lib().orc_get_obs(self.h, C.byref(o))
+        return {f: getattr(o, f) for f, _ in Obs._fields_}
+
+    def reset_counters(self):
+        lib().orc_reset_counters(self.h)
+
+    def neighbours(self, i):
+        k = lib().orc_neighbour_count(self.h, int(i))
+        out = []
+        j = C.c_int64()
+        r = C.c_double()
+        d = np.zeros(3)
+        for q in range(k):
+            lib().orc_neighbour(self.h, int(i), q, C.byref(j), C.byref(r), _p(d))
+            out.append((j.value, r.value, d.copy()))
+        return out
+
+    def spline(self, which, x):
+        v = C.c_double()
+        dv = C.c_double()
+        if lib().orc_spline(self.h, int(which), float(x), C.byref(v), C.byref(dv)):
+            raise ValueError("oracle: spline argument out of range")
+        return v.value, dv.value
+
+    # ---- MD
+    def forces(self):
+        f = [np.zeros(self.n) for _ in range(3)]
+        lib().orc_forces(self.h, *(_p(a) for a in f))
+        return f
+
+    def set_md(self, v, masses, dt, gamma, T, seed):
+        vv = [np.ascontiguousarray(a, dtype=np.float64) for a in v]
+        lib().orc_set_md(self.h, *(_p(a) for a in vv), masses[0], masses[1], dt, gamma, T, seed)
+
+    def md_steps(self, n):
+        if lib().orc_md_steps(self.h, int(n)):
+            raise RuntimeError("oracle: md not set up")
+
+    def md_state(self):
+        a = [np.zeros(self.n) for _ in range(6)]
+        lib().orc_get_md(self.h, *(_p(q) for q in a))
+        return a
+
+    def kinetic_energy(self):
+        return lib().orc_kinetic_energy(self.h)
+
+    def hybrid_cycles(self, n_cycles, n_md, n_mc):
+        if lib().orc_hybrid_cycles(self.h, int(n_cycles), int(n_md), int(n_mc)):
+            raise RuntimeError("oracle: hybrid cycle failed")

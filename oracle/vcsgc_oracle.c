@@ -1,0 +1,972 @@
+/*
+ * vcsgc_oracle.c -- serial FP64 CPU oracle for the parallel VC-SGC method.
+ *
+ * TEST INFRASTRUCTURE ONLY: the plain, slow reference the CUDA path is
+ * checked against.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code with the CUDA library.
+ *
+ * Written from the paper (Sadigh et al., "A scalable parallel Monte Carlo
+ * algorithm for atomistic simulations of precipitation in alloys"):
+ *   Sec. II C, Eq. pi_vcsgc ...... target distribution
+ *           pi_V ~ exp[-beta (U + phi n + kappa_p n^2)], n = N c
+ *   Sec. II C, Eq. trans_vcsgc ... serial acceptance rule
+ *   Sec. III B 2, Eq. mod ........ two-factor serial rule (factor 2 restored)
+ *   Sec. III B 2, Eq. trans_vcsgc_par1 .. local stage of the composite move
+ *   Sec. III B 2, Eq. trans_vcsgc_par2 .. global stage; the sign inside the
+ *           bracket is fixed by pi_V: exponent -beta kappa_p dn (dn + 2(n-n0))
+ *   Sec. III A ................... non-interacting domains, one colour per
+ *           step chosen with a synchronised random stream
+ *   Sec. IV A .................... hybrid MD + transmutation MC
+ *
+ * The only numerical shortcut is none: every energy difference is evaluated
+ * neighbour by neighbour from the spline tables, in slot order.
+ */
+#include "vcsgc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define KB_EV 8.617333262e-5       /* Boltzmann constant, eV/K */
+#define FTM 9.648533212331e-3      /* eV/(Angstrom amu) -> Angstrom/fs^2 */
+
+typedef struct {
+  int n;
+  double h;
+  double* y;
+  double* m; /* knot derivatives */
+} spline_t;
+
+typedef struct {
+  int64_t j;
+  double r;
+  double d[3];
+  int sx, sy, sz;
+} nbr_t;
+
+struct orc_sys {
+  int64_t n;
+  double box[3];
+  double *x, *y, *z;
+  uint8_t* t;
+  double* rho;
+  spline_t sp[7]; /* 0..2 pair AA AB BB, 3..4 dens A B, 5..6 embed A B */
+  double rc;
+  int brute;
+  /* neighbour list, CSR */
+  int64_t* nstart;
+  nbr_t* nb;
+  /* ensemble */
+  double phi, kappa, T, beta, kappa_p, c0, n0, dmu0;
+  uint32_t key[2];
+  uint64_t step;
+  int64_t nb_count;
+  double energy;
+  /* counters */
+  int64_t trials, local_acc, global_acc, global_trials, flips, near_ties;
+  double sum_c, sum_c2;
+  int64_t steps_done;
+  /* schedule */
+  int64_t n_colours, n_domains;
+  int64_t *col_start, *dom_start, *dom_sites;
+  int sched_kind; /* 0 none, 1 blocks, 2 sublattice, 3 spatial */
+  int sched_args[9];
+  /* md */
+  double *vx, *vy, *vz, *fx, *fy, *fz;
+  double mass[2], dt, gamma, T_md;
+  uint32_t md_key[2];
+  uint64_t md_step;
+};
+
+/* ---------------------------------------------------------------- Philox */
+/* Philox4x32-10 as published by Salmon et al. (SC'11): ten rounds of two
+ * 32x32->64 multiplies with the bijection (c0,c1,c2,c3) ->
+ * (hi1^c1^k0, lo1, hi0^c3^k1, lo0), key bumped by the Weyl constants. */
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform double in [0,1) from the top 53 bits of the 64-bit word hi:lo. */
+double orc_u01(uint32_t lo, uint32_t hi) {
+  uint64_t w = ((uint64_t)hi << 32) | lo;
+  return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* floor(w * m / 2^64): an index in [0, m) from the 64-bit word hi:lo. */
+uint64_t orc_below(uint32_t lo, uint32_t hi, uint64_t m) {
+  uint64_t w = ((uint64_t)hi << 32) | lo;
+  unsigned __int128 p = (unsigned __int128)w * (unsigned __int128)m;
+  return (uint64_t)(p >> 64);
+}
+
+static void draw(const orc_sys* s, uint64_t k, uint32_t d, uint32_t tag, uint32_t w[4]) {
+  uint32_t ctr[4] = {(uint32_t)k, (uint32_t)(k >> 32), d, tag};
+  orc_philox(ctr, s->key, w);
+}
+
+/* ---------------------------------------------------------------- spline */
+/* Cubic Hermite interpolation on a uniform grid with given (or central
+ * finite-difference) knot derivatives. */
+static int spline_init(spline_t* sp, int n, double h, const double* y, const double* m) {
+  sp->n = n;
+  sp->h = h;
+  sp->y = (double*)malloc(sizeof(double) * n);
+  sp->m = (double*)malloc(sizeof(double) * n);
+  if (!sp->y || !sp->m) return -1;
+  memcpy(sp->y, y, sizeof(double) * n);
+  if (m) {
+    memcpy(sp->m, m, sizeof(double) * n);
+  } else {
+    for (int j = 0; j < n; ++j) {
+      if (j == 0) sp->m[j] = (y[1] - y[0]) / h;
+      else if (j == n - 1) sp->m[j] = (y[n - 1] - y[n - 2]) / h;
+      else sp->m[j] = (y[j + 1] - y[j - 1]) / (2.0 * h);
+    }
+  }
+  return 0;
+}
+
+static int spline_eval(const spline_t* sp, double x, double* v, double* dv) {
+  double xmax = (sp->n - 1) * sp->h;
+  if (!(x >= 0.0) || x > xmax) return -1;
+  int j = (int)floor(x / sp->h);
+  if (j > sp->n - 2) j = sp->n - 2;
+  double h = sp->h;
+  double t = (x - j * h) / h;
+  double y0 = sp->y[j], y1 = sp->y[j + 1];
+  double m0 = sp->m[j] * h, m1 = sp->m[j + 1] * h;
+  double t2 = t * t, t3 = t2 * t;
+  double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + t;
+  double h01 = -2 * t3 + 3 * t2, h11 = t3 - t2;
+  if (v) *v = h00 * y0 + h10 * m0 + h01 * y1 + h11 * m1;
+  if (dv) {
+    double d00 = 6 * t2 - 6 * t, d10 = 3 * t2 - 4 * t + 1;
+    double d01 = -6 * t2 + 6 * t, d11 = 3 * t2 - 2 * t;
+    *dv = (d00 * y0 + d10 * m0 + d01 * y1 + d11 * m1) / h;
+  }
+  return 0;
+}
+
+int orc_spline(const orc_sys* s, int which, double x, double* v, double* dv) {
+  if (which < 0 || which > 6) return -1;
+  return spline_eval(&s->sp[which], x, v, dv);
+}
+
+/* table accessors: abort-free, out-of-range yields NaN so it shows up */
+static double phi_ab(const orc_sys* s, int a, int b, double r) {
+  double v;
+  if (spline_eval(&s->sp[a + b], r, &v, NULL)) return NAN;
+  return v;
+}
+static double dens_of(const orc_sys* s, int a, double r) {
+  double v;
+  if (spline_eval(&s->sp[3 + a], r, &v, NULL)) return NAN;
+  return v;
+}
+static double embed_of(const orc_sys* s, int a, double rho) {
+  double v;
+  if (spline_eval(&s->sp[5 + a], rho, &v, NULL)) return NAN;
+  return v;
+}
+
+/* --------------------------------------------------------- neighbour list */
+static int cmp_nbr(const void* pa, const void* pb) {
+  const nbr_t* a = (const nbr_t*)pa;
+  const nbr_t* b = (const nbr_t*)pb;
+  if (a->r != b->r) return a->r < b->r ? -1 : 1;
+  if (a->j != b->j) return a->j < b->j ? -1 : 1;
+  if (a->sx != b->sx) return a->sx < b->sx ? -1 : 1;
+  if (a->sy != b->sy) return a->sy < b->sy ? -1 : 1;
+  if (a->sz != b->sz) return a->sz < b->sz ? -1 : 1;
+  return 0;
+}
+
+typedef struct {
+  nbr_t* v;
+  int64_t n, cap;
+} nbr_vec;
+
+static int vec_push(nbr_vec* a, nbr_t e) {
+  if (a->n == a->cap) {
+    int64_t cap = a->cap ? 2 * a->cap : 1024;
+    nbr_t* p = (nbr_t*)realloc(a->v, sizeof(nbr_t) * cap);
+    if (!p) return -1;
+    a->v = p;
+    a->cap = cap;
+  }
+  a->v[a->n++] = e;
+  return 0;
+}
+
+/* Brute force: every j and every periodic image shift within reach. */
+static int build_brute(orc_sys* s, nbr_vec* all, int64_t* start) {
+  int m[3];
+  for (int a = 0; a < 3; ++a) m[a] = (int)ceil(s->rc / s->box[a]) + 1;
+  double rc2 = s->rc * s->rc;
+  for (int64_t i = 0; i < s->n; ++i) {
+    start[i] = all->n;
+    int64_t first = all->n;
+    for (int64_t j = 0; j < s->n; ++j)
+      for (int sx = -m[0]; sx <= m[0]; ++sx)
+        for (int sy = -m[1]; sy <= m[1]; ++sy)
+          for (int sz = -m[2]; sz <= m[2]; ++sz) {
+            if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
+            double dx = s->x[j] + sx * s->box[0] - s->x[i];
+            double dy = s->y[j] + sy * s->box[1] - s->y[i];
+            double dz = s->z[j] + sz * s->box[2] - s->z[i];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rc2) {
+              nbr_t e = {j, sqrt(r2), {dx, dy, dz}, sx, sy, sz};
+              if (vec_push(all, e)) return -1;
+            }
+          }
+    qsort(all->v + first, (size_t)(all->n - first), sizeof(nbr_t), cmp_nbr);
+  }
+  start[s->n] = all->n;
+  return 0;
+}
+
+/* Cell binning (at least 3 cells of side >= rc per axis, so the minimum
+ * image is the only image within rc). */
+static int build_cells(orc_sys* s, nbr_vec* all, int64_t* start) {
+  int nc[3];
+  for (int a = 0; a < 3; ++a) nc[a] = (int)floor(s->box[a] / s->rc);
+  int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+  int64_t* head = (int64_t*)malloc(sizeof(int64_t) * ncell);
+  int64_t* next = (int64_t*)malloc(sizeof(int64_t) * s->n);
+  int* cell = (int*)malloc(sizeof(int) * 3 * s->n);
+  if (!head || !next || !cell) { free(head); free(next); free(cell); return -1; }
+  for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+  const double* xs[3] = {s->x, s->y, s->z};
+  for (int64_t i = s->n - 1; i >= 0; --i) {
+    int c3[3];
+    for (int a = 0; a < 3; ++a) {
+      int c = (int)floor(xs[a][i] / s->box[a] * nc[a]);
+      if (c < 0) c = 0;
+      if (c >= nc[a]) c = nc[a] - 1;
+      c3[a] = c;
+      cell[3 * i + a] = c;
+    }
+    int64_t lin = ((int64_t)c3[2] * nc[1] + c3[1]) * nc[0] + c3[0];
+    next[i] = head[lin];
+    head[lin] = i;
+  }
+  double rc2 = s->rc * s->rc;
+  for (int64_t i = 0; i < s->n; ++i) {
+    start[i] = all->n;
+    int64_t first = all->n;
+    for (int ox = -1; ox <= 1; ++ox)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int oz = -1; oz <= 1; ++oz) {
+          int cx = (cell[3 * i] + ox + nc[0]) % nc[0];
+          int cy = (cell[3 * i + 1] + oy + nc[1]) % nc[1];
+          int cz = (cell[3 * i + 2] + oz + nc[2]) % nc[2];
+          int64_t lin = ((int64_t)cz * nc[1] + cy) * nc[0] + cx;
+          for (int64_t j = head[lin]; j >= 0; j = next[j]) {
+            if (j == i) continue;
+            double d[3];
+            int sh[3];
+            for (int a = 0; a < 3; ++a) {
+              double v = xs[a][j] - xs[a][i];
+              int k = (int)lround(v / s->box[a]);
+              d[a] = v - k * s->box[a];
+              sh[a] = -k;
+            }
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 < rc2) {
+              nbr_t e = {j, sqrt(r2), {d[0], d[1], d[2]}, sh[0], sh[1], sh[2]};
+              if (vec_push(all, e)) { free(head); free(next); free(cell); return -1; }
+            }
+          }
+        }
+    qsort(all->v + first, (size_t)(all->n - first), sizeof(nbr_t), cmp_nbr);
+  }
+  start[s->n] = all->n;
+  free(head);
+  free(next);
+  free(cell);
+  return 0;
+}
+
+static int build_neighbours(orc_sys* s) {
+  nbr_vec all = {NULL, 0, 0};
+  int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (s->n + 1));
+  if (!start) return -1;
+  int use_cells = !s->brute;
+  for (int a = 0; a < 3; ++a)
+    if (floor(s->box[a] / s->rc) < 3) use_cells = 0;
+  int rc = use_cells ? build_cells(s, &all, start) : build_brute(s, &all, start);
+  if (rc) { free(all.v); free(start); return -1; }
+  free(s->nstart);
+  free(s->nb);
+  s->nstart = start;
+  s->nb = all.v;
+  return 0;
+}
+
+static void compute_rho(orc_sys* s) {
+  for (int64_t i = 0; i < s->n; ++i) {
+    double r = 0.0;
+    for (int64_t k = s->nstart[i]; k < s->nstart[i + 1]; ++k)
+      r += dens_of(s, s->t[s->nb[k].j], s->nb[k].r);
+    s->rho[i] = r;
+  }
+}
+
+/* ---------------------------------------------------------------- energy */
+/* Neumaier-compensated running sum. */
+typedef struct { double s, c; } ksum;
+static void kadd(ksum* a, double v) {
+  double t = a->s + v;
+  if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+  else a->c += (v - t) + a->s;
+  a->s = t;
+}
+
+/* U = sum_i [ 1/2 sum_j phi_{t_i t_j}(r_ij) + F_{t_i}(rho_i) ]  (EAM). */
+double orc_energy_full(const orc_sys* s) {
+  ksum acc = {0, 0};
+  for (int64_t i = 0; i < s->n; ++i) {
+    int ti = s->t[i];
+    double rho = 0.0;
+    for (int64_t k = s->nstart[i]; k < s->nstart[i + 1]; ++k) {
+      const nbr_t* e = &s->nb[k];
+      kadd(&acc, 0.5 * phi_ab(s, ti, s->t[e->j], e->r));
+      rho += dens_of(s, s->t[e->j], e->r);
+    }
+    kadd(&acc, embed_of(s, ti, rho));
+  }
+  return acc.s + acc.c;
+}
+
+/* Energy change for flipping site i from t to t' = 1 - t:
+ *   pair:     sum_k [phi_{t' t_k}(r_ik) - phi_{t t_k}(r_ik)]
+ *   own:      F_{t'}(rho_i) - F_t(rho_i)   (rho_i does not depend on t_i)
+ *   re-embed: sum over distinct neighbours k of
+ *             F_{t_k}(rho_k + drho_k) - F_{t_k}(rho_k),
+ *             drho_k = sum over the slots of k of f_{t'}(r) - f_t(r). */
+double orc_delta_e(const orc_sys* s, int64_t i) {
+  int t = s->t[i], tp = 1 - t;
+  int64_t b = s->nstart[i], e = s->nstart[i + 1];
+  double pair = 0.0;
+  int any_drho = 0;
+  for (int64_t k = b; k < e; ++k) {
+    const nbr_t* nb = &s->nb[k];
+    int tk = s->t[nb->j];
+    pair += phi_ab(s, tp, tk, nb->r) - phi_ab(s, t, tk, nb->r);
+    if (dens_of(s, tp, nb->r) - dens_of(s, t, nb->r) != 0.0) any_drho = 1;
+  }
+  double own = embed_of(s, tp, s->rho[i]) - embed_of(s, t, s->rho[i]);
+  double reembed = 0.0;
+  if (any_drho) {
+    for (int64_t k = b; k < e; ++k) {
+      int64_t j = s->nb[k].j;
+      int seen = 0;
+      for (int64_t q = b; q < k; ++q)
+        if (s->nb[q].j == j) { seen = 1; break; }
+      if (seen) continue;
+      double drho = 0.0;
+      for (int64_t q = k; q < e; ++q)
+        if (s->nb[q].j == j) drho += dens_of(s, tp, s->nb[q].r) - dens_of(s, t, s->nb[q].r);
+      int tj = s->t[j];
+      reembed += embed_of(s, tj, s->rho[j] + drho) - embed_of(s, tj, s->rho[j]);
+    }
+  }
+  return pair + own + reembed;
+}
+
+void orc_flip(orc_sys* s, int64_t i) {
+  int t = s->t[i], tp = 1 - t;
+  for (int64_t k = s->nstart[i]; k < s->nstart[i + 1]; ++k) {
+    const nbr_t* nb = &s->nb[k];
+    s->rho[nb->j] += dens_of(s, tp, nb->r) - dens_of(s, t, nb->r);
+  }
+  s->t[i] = (uint8_t)tp;
+  s->nb_count += tp ? 1 : -1;
+}
+
+double orc_delta_e_full(orc_sys* s, int64_t i) {
+  double e0 = orc_energy_full(s);
+  uint8_t t = s->t[i];
+  s->t[i] = 1 - t;
+  double e1 = orc_energy_full(s);
+  s->t[i] = t;
+  return e1 - e0;
+}
+
+/* ---------------------------------------------------------------- create */
+orc_sys* orc_create(int64_t n, const double* x, const double* y, const double* z,
+                    const double box[3], const uint8_t* types, const orc_eam_in* eam,
+                    int brute) {
+  if (n <= 0 || !eam || eam->nr < 2 || eam->nrho < 2) return NULL;
+  for (int a = 0; a < 3; ++a)
+    if (!(box[a] > eam->rc)) return NULL; /* no self-images within rc */
+  orc_sys* s = (orc_sys*)calloc(1, sizeof(orc_sys));
+  if (!s) return NULL;
+  s->n = n;
+  memcpy(s->box, box, sizeof(double) * 3);
+  s->x = (double*)malloc(sizeof(double) * n);
+  s->y = (double*)malloc(sizeof(double) * n);
+  s->z = (double*)malloc(sizeof(double) * n);
+  s->t = (uint8_t*)malloc(n);
+  s->rho = (double*)malloc(sizeof(double) * n);
+  if (!s->x || !s->y || !s->z || !s->t || !s->rho) { orc_free(s); return NULL; }
+  memcpy(s->x, x, sizeof(double) * n);
+  memcpy(s->y, y, sizeof(double) * n);
+  memcpy(s->z, z, sizeof(double) * n);
+  memcpy(s->t, types, n);
+  s->rc = eam->rc;
+  s->brute = brute;
+  for (int p = 0; p < 3; ++p)
+    if (spline_init(&s->sp[p], eam->nr, eam->dr, eam->pair[p], eam->dpair[p])) { orc_free(s); return NULL; }
+  for (int a = 0; a < 2; ++a) {
+    if (spline_init(&s->sp[3 + a], eam->nr, eam->dr, eam->dens[a], eam->ddens[a])) { orc_free(s); return NULL; }
+    if (spline_init(&s->sp[5 + a], eam->nrho, eam->drho, eam->embed[a], eam->dembed[a])) { orc_free(s); return NULL; }
+  }
+  if (build_neighbours(s)) { orc_free(s); return NULL; }
+  compute_rho(s);
+  s->nb_count = 0;
+  for (int64_t i = 0; i < n; ++i) s->nb_count += s->t[i];
+  s->energy = orc_energy_full(s);
+  return s;
+}
+
+void orc_free(orc_sys* s) {
+  if (!s) return;
+  free(s->x); free(s->y); free(s->z); free(s->t); free(s->rho);
+  for (int p = 0; p < 7; ++p) { free(s->sp[p].y); free(s->sp[p].m); }
+  free(s->nstart); free(s->nb);
+  free(s->col_start); free(s->dom_start); free(s->dom_sites);
+  free(s->vx); free(s->vy); free(s->vz); free(s->fx); free(s->fy); free(s->fz);
+  free(s);
+}
+
+int orc_set_params(orc_sys* s, double phi, double kappa, double T, int kappa_units,
+                   double c0, uint64_t seed) {
+  if (!(T > 0) || !(kappa >= 0)) return -1;
+  s->phi = phi;
+  s->kappa = kappa;
+  s->T = T;
+  s->beta = 1.0 / (KB_EV * T);
+  s->kappa_p = kappa_units == 1 ? kappa : kappa * KB_EV * T / (double)s->n;
+  s->c0 = c0 < 0 ? (double)s->nb_count / (double)s->n : c0;
+  s->n0 = (double)s->n * s->c0;
+  /* Delta mu_0 = phi + 2 kappa N c0 (Eq. trans_vcsgc_par1) */
+  s->dmu0 = phi + 2.0 * s->kappa_p * s->n0;
+  s->key[0] = (uint32_t)seed;
+  s->key[1] = (uint32_t)(seed >> 32);
+  s->step = 0;
+  orc_reset_counters(s);
+  return 0;
+}
+
+void orc_reset_counters(orc_sys* s) {
+  s->trials = s->local_acc = s->global_acc = s->global_trials = 0;
+  s->flips = s->near_ties = 0;
+  s->sum_c = s->sum_c2 = 0.0;
+  s->steps_done = 0;
+}
+
+/* -------------------------------------------------------------- schedule */
+static int sched_alloc(orc_sys* s, int64_t n_colours, int64_t n_domains) {
+  free(s->col_start); free(s->dom_start); free(s->dom_sites);
+  s->col_start = (int64_t*)calloc(n_colours + 1, sizeof(int64_t));
+  s->dom_start = (int64_t*)calloc(n_domains + 1, sizeof(int64_t));
+  s->dom_sites = (int64_t*)calloc(s->n, sizeof(int64_t));
+  s->n_colours = n_colours;
+  s->n_domains = n_domains;
+  return (s->col_start && s->dom_start && s->dom_sites) ? 0 : -1;
+}
+
+int orc_schedule_blocks(orc_sys* s, int nx, int ny, int nz, int bx, int by, int bz,
+                        int px, int py, int pz) {
+  if ((int64_t)2 * nx * ny * nz != s->n) return -1;
+  if (bx < 1 || by < 1 || bz < 1 || px < 1 || py < 1 || pz < 1) return -1;
+  if (nx % bx || ny % by || nz % bz) return -1;
+  int nbx = nx / bx, nby = ny / by, nbz = nz / bz;
+  if (nbx % px || nby % py || nbz % pz) return -1;
+  int64_t ncol = (int64_t)px * py * pz, nblk = (int64_t)nbx * nby * nbz;
+  if (sched_alloc(s, ncol, nblk)) return -1;
+  int64_t dom = 0, site = 0;
+  for (int64_t c = 0; c < ncol; ++c) {
+    s->col_start[c] = dom;
+    for (int ibz = 0; ibz < nbz; ++ibz)
+      for (int iby = 0; iby < nby; ++iby)
+        for (int ibx = 0; ibx < nbx; ++ibx) {
+          int64_t col = ((int64_t)(ibz % pz) * py + (iby % py)) * px + (ibx % px);
+          if (col != c) continue;
+          s->dom_start[dom] = site;
+          for (int lz = 0; lz < bz; ++lz)
+            for (int ly = 0; ly < by; ++ly)
+              for (int lx = 0; lx < bx; ++lx)
+                for (int b = 0; b < 2; ++b) {
+                  int64_t cx = (int64_t)ibx * bx + lx, cy = (int64_t)iby * by + ly,
+                          cz = (int64_t)ibz * bz + lz;
+                  s->dom_sites[site++] = ((cz * ny + cy) * nx + cx) * 2 + b;
+                }
+          ++dom;
+        }
+  }
+  s->col_start[ncol] = dom;
+  s->dom_start[dom] = site;
+  s->sched_kind = 1;
+  return 0;
+}
+
+int orc_schedule_sublattice(orc_sys* s, int nx, int ny, int nz, int qx, int qy, int qz) {
+  if ((int64_t)2 * nx * ny * nz != s->n) return -1;
+  if (qx < 1 || qy < 1 || qz < 1 || nx % qx || ny % qy || nz % qz) return -1;
+  int64_t ncol = (int64_t)qx * qy * qz * 2;
+  if (sched_alloc(s, ncol, s->n)) return -1;
+  int64_t dom = 0;
+  for (int64_t c = 0; c < ncol; ++c) {
+    s->col_start[c] = dom;
+    for (int64_t i = 0; i < s->n; ++i) {
+      int64_t b = i % 2, cell = i / 2;
+      int64_t cx = cell % nx, cy = (cell / nx) % ny, cz = cell / ((int64_t)nx * ny);
+      int64_t col = (((cz % qz) * qy + (cy % qy)) * qx + (cx % qx)) * 2 + b;
+      if (col != c) continue;
+      s->dom_start[dom] = dom;
+      s->dom_sites[dom] = i;
+      ++dom;
+    }
+  }
+  s->col_start[ncol] = dom;
+  s->dom_start[dom] = dom;
+  s->sched_kind = 2;
+  return 0;
+}
+
+int orc_schedule_spatial(orc_sys* s, int nbx, int nby, int nbz, int px, int py, int pz) {
+  if (nbx < 1 || nby < 1 || nbz < 1 || px < 1 || py < 1 || pz < 1) return -1;
+  if (nbx % px || nby % py || nbz % pz) return -1;
+  int64_t ncol = (int64_t)px * py * pz, nblk = (int64_t)nbx * nby * nbz;
+  int64_t* blk = (int64_t*)malloc(sizeof(int64_t) * s->n);
+  if (!blk) return -1;
+  int nb3[3] = {nbx, nby, nbz};
+  const double* xs[3] = {s->x, s->y, s->z};
+  for (int64_t i = 0; i < s->n; ++i) {
+    int c3[3];
+    for (int a = 0; a < 3; ++a) {
+      int c = (int)floor(xs[a][i] / s->box[a] * nb3[a]);
+      if (c < 0) c = 0;
+      if (c >= nb3[a]) c = nb3[a] - 1;
+      c3[a] = c;
+    }
+    blk[i] = ((int64_t)c3[2] * nby + c3[1]) * nbx + c3[0];
+  }
+  if (sched_alloc(s, ncol, nblk)) { free(blk); return -1; }
+  int64_t dom = 0, site = 0;
+  for (int64_t c = 0; c < ncol; ++c) {
+    s->col_start[c] = dom;
+    for (int64_t b = 0; b < nblk; ++b) {
+      int64_t ibx = b % nbx, iby = (b / nbx) % nby, ibz = b / ((int64_t)nbx * nby);
+      int64_t col = ((ibz % pz) * py + (iby % py)) * px + (ibx % px);
+      if (col != c) continue;
+      s->dom_start[dom] = site;
+      for (int64_t i = 0; i < s->n; ++i)
+        if (blk[i] == b) s->dom_sites[site++] = i;
+      ++dom;
+    }
+  }
+  s->col_start[ncol] = dom;
+  s->dom_start[dom] = site;
+  free(blk);
+  s->sched_kind = 3;
+  s->sched_args[0] = nbx; s->sched_args[1] = nby; s->sched_args[2] = nbz;
+  s->sched_args[3] = px; s->sched_args[4] = py; s->sched_args[5] = pz;
+  return 0;
+}
+
+int64_t orc_schedule_info(const orc_sys* s, int64_t* n_colours, int64_t* domains_per_colour) {
+  if (n_colours) *n_colours = s->n_colours;
+  if (domains_per_colour) *domains_per_colour = s->n_colours ? s->col_start[1] - s->col_start[0] : 0;
+  return s->n_domains;
+}
+
+void orc_schedule_export(const orc_sys* s, int64_t* col_start, int64_t* dom_start,
+                         int64_t* dom_sites) {
+  if (col_start) memcpy(col_start, s->col_start, sizeof(int64_t) * (s->n_colours + 1));
+  if (dom_start) memcpy(dom_start, s->dom_start, sizeof(int64_t) * (s->n_domains + 1));
+  if (dom_sites) memcpy(dom_sites, s->dom_sites, sizeof(int64_t) * s->n);
+}
+
+static double min_image_dist(const orc_sys* s, int64_t i, int64_t j) {
+  double best = INFINITY;
+  for (int sx = -1; sx <= 1; ++sx)
+    for (int sy = -1; sy <= 1; ++sy)
+      for (int sz = -1; sz <= 1; ++sz) {
+        double dx = s->x[j] + sx * s->box[0] - s->x[i];
+        double dy = s->y[j] + sy * s->box[1] - s->y[i];
+        double dz = s->z[j] + sz * s->box[2] - s->z[i];
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        if (r < best) best = r;
+      }
+  return best;
+}
+
+double orc_schedule_min_separation(const orc_sys* s) {
+  double best = INFINITY;
+  for (int64_t c = 0; c < s->n_colours; ++c)
+    for (int64_t d1 = s->col_start[c]; d1 < s->col_start[c + 1]; ++d1)
+      for (int64_t d2 = d1 + 1; d2 < s->col_start[c + 1]; ++d2)
+        for (int64_t a = s->dom_start[d1]; a < s->dom_start[d1 + 1]; ++a)
+          for (int64_t b = s->dom_start[d2]; b < s->dom_start[d2 + 1]; ++b) {
+            double r = min_image_dist(s, s->dom_sites[a], s->dom_sites[b]);
+            if (r < best) best = r;
+          }
+  return best;
+}
+
+/* ------------------------------------------------------------- sampling */
+/* Metropolis decision u < min{1, exp(-X)}; counts decisions within 1e-9
+ * (relative) of the boundary, where CPU and GPU exp may round differently. */
+static int metropolis(orc_sys* s, double X, double u) {
+  if (X <= 0.0) {
+    if (X > -1e-9 && u >= 1.0 - 1e-9) s->near_ties++;
+    return 1;
+  }
+  double p = exp(-X);
+  if (fabs(u - p) <= 1e-9 * p) s->near_ties++;
+  return u < p;
+}
+
+static void sample_c(orc_sys* s) {
+  double c = (double)s->nb_count / (double)s->n;
+  s->sum_c += c;
+  s->sum_c2 += c * c;
+  s->steps_done++;
+}
+
+static void flip_commit(orc_sys* s, int64_t i) {
+  if (s->vx) {
+    /* keep the Maxwell distribution: v scaled by sqrt(m_old / m_new) */
+    double f = sqrt(s->mass[s->t[i]] / s->mass[1 - s->t[i]]);
+    s->vx[i] *= f; s->vy[i] *= f; s->vz[i] *= f;
+  }
+  orc_flip(s, i);
+}
+
+/* One composite step of the parallel algorithm (Sec. III B 2):
+ *  1. colour c drawn from the step's synchronised stream;
+ *  2. every domain d of colour c picks one of its sites uniformly and
+ *     proposes t -> 1 - t; the local stage accepts it with
+ *     min{1, exp[-beta (dE_i + s_i dmu0)]}, s_i = N dc_i = +-1;
+ *  3. dn = sum of s_i over the locally accepted moves;
+ *  4. the global stage accepts the whole composite move with
+ *     min{1, exp[-beta kappa_p dn (dn + 2 (n - n0))]};
+ *  5. if accepted every locally accepted site flips. */
+static void parallel_step(orc_sys* s, int64_t* acc_sites, double* acc_de) {
+  uint64_t k = s->step;
+  uint32_t w[4];
+  draw(s, k, 0xFFFFFFFFu, 1u, w);
+  int64_t c = (int64_t)orc_below(w[0], w[1], (uint64_t)s->n_colours);
+  double ug = orc_u01(w[2], w[3]);
+  int64_t d0 = s->col_start[c], d1 = s->col_start[c + 1];
+  int64_t nacc = 0, dn = 0;
+  for (int64_t g = d0; g < d1; ++g) {
+    int64_t size = s->dom_start[g + 1] - s->dom_start[g];
+    if (size == 0) continue;
+    draw(s, k, (uint32_t)(g - d0), 0u, w);
+    int64_t site = s->dom_sites[s->dom_start[g] + orc_below(w[0], w[1], (uint64_t)size)];
+    double u = orc_u01(w[2], w[3]);
+    int sg = s->t[site] == 0 ? 1 : -1;
+    double de = orc_delta_e(s, site);
+    double X = s->beta * (de + sg * s->dmu0);
+    s->trials++;
+    if (metropolis(s, X, u)) {
+      acc_sites[nacc] = site;
+      acc_de[nacc] = de;
+      nacc++;
+      dn += sg;
+    }
+  }
+  s->local_acc += nacc;
+  if (nacc > 0) {
+    s->global_trials++;
+    double Y = s->beta * s->kappa_p * (double)dn * ((double)dn + 2.0 * ((double)s->nb_count - s->n0));
+    if (metropolis(s, Y, ug)) {
+      s->global_acc++;
+      for (int64_t a = 0; a < nacc; ++a) {
+        flip_commit(s, acc_sites[a]);
+        s->energy += acc_de[a];
+      }
+      s->flips += nacc;
+    }
+  }
+  s->step++;
+  sample_c(s);
+}
+
+int orc_parallel_steps(orc_sys* s, int64_t n_steps) {
+  if (!s->n_colours) return -1;
+  int64_t maxd = 0;
+  for (int64_t c = 0; c < s->n_colours; ++c) {
+    int64_t d = s->col_start[c + 1] - s->col_start[c];
+    if (d > maxd) maxd = d;
+  }
+  int64_t* sites = (int64_t*)malloc(sizeof(int64_t) * (maxd + 1));
+  double* des = (double*)malloc(sizeof(double) * (maxd + 1));
+  if (!sites || !des) { free(sites); free(des); return -1; }
+  for (int64_t k = 0; k < n_steps; ++k) parallel_step(s, sites, des);
+  free(sites);
+  free(des);
+  return 0;
+}
+
+/* Serial single-site steps.
+ * mode 0, Eq. trans_vcsgc: X = beta (dE + N dc (phi + 2 kappa_p N c~)),
+ *         with N dc = s and 2 N c~ = n + n' = 2n + s.
+ * mode 1, Eq. mod: local factor with dmu0 times global factor with
+ *         exponent beta kappa_p s (s + 2 (n - n0)). */
+int orc_serial_steps(orc_sys* s, int64_t n_steps, int mode) {
+  for (int64_t q = 0; q < n_steps; ++q) {
+    uint64_t k = s->step;
+    uint32_t w[4], w2[4];
+    draw(s, k, 0u, 2u, w);
+    int64_t site = (int64_t)orc_below(w[0], w[1], (uint64_t)s->n);
+    double u = orc_u01(w[2], w[3]);
+    int sg = s->t[site] == 0 ? 1 : -1;
+    double de = orc_delta_e(s, site);
+    double n = (double)s->nb_count;
+    int acc;
+    s->trials++;
+    if (mode == 0) {
+      double X = s->beta * (de + sg * (s->phi + s->kappa_p * (2.0 * n + sg)));
+      acc = metropolis(s, X, u);
+      if (acc) s->local_acc++;
+    } else {
+      double X = s->beta * (de + sg * s->dmu0);
+      acc = metropolis(s, X, u);
+      if (acc) {
+        s->local_acc++;
+        s->global_trials++;
+        draw(s, k, 1u, 2u, w2);
+        double ug = orc_u01(w2[0], w2[1]);
+        double Y = s->beta * s->kappa_p * (double)sg * ((double)sg + 2.0 * (n - s->n0));
+        acc = metropolis(s, Y, ug);
+        if (acc) s->global_acc++;
+      }
+    }
+    if (acc) {
+      flip_commit(s, site);
+      s->energy += de;
+      s->flips++;
+    }
+    s->step++;
+    sample_c(s);
+  }
+  return 0;
+}
+
+int orc_run_histogram(orc_sys* s, int64_t n_steps, int mode, int64_t* hist, double* sum_e) {
+  for (int64_t q = 0; q < n_steps; ++q) {
+    int rc = mode < 0 ? orc_parallel_steps(s, 1) : orc_serial_steps(s, 1, mode);
+    if (rc) return rc;
+    hist[s->nb_count]++;
+    *sum_e += s->energy;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------- accessors */
+void orc_get_types(const orc_sys* s, uint8_t* out) { memcpy(out, s->t, s->n); }
+
+void orc_set_types(orc_sys* s, const uint8_t* in) {
+  memcpy(s->t, in, s->n);
+  s->nb_count = 0;
+  for (int64_t i = 0; i < s->n; ++i) s->nb_count += s->t[i];
+  compute_rho(s);
+  s->energy = orc_energy_full(s);
+}
+
+void orc_get_rho(const orc_sys* s, double* out) { memcpy(out, s->rho, sizeof(double) * s->n); }
+
+void orc_get_obs(const orc_sys* s, orc_obs* o) {
+  o->n_sites = s->n;
+  o->n_b = s->nb_count;
+  o->energy = s->energy;
+  o->steps = s->steps_done;
+  o->trials = s->trials;
+  o->local_accepts = s->local_acc;
+  o->global_trials = s->global_trials;
+  o->global_accepts = s->global_acc;
+  o->flips = s->flips;
+  o->near_ties = s->near_ties;
+  o->sum_c = s->sum_c;
+  o->sum_c2 = s->sum_c2;
+}
+
+int64_t orc_neighbour_count(const orc_sys* s, int64_t i) { return s->nstart[i + 1] - s->nstart[i]; }
+
+void orc_neighbour(const orc_sys* s, int64_t i, int64_t k, int64_t* j, double* r, double d[3]) {
+  const nbr_t* e = &s->nb[s->nstart[i] + k];
+  if (j) *j = e->j;
+  if (r) *r = e->r;
+  if (d) { d[0] = e->d[0]; d[1] = e->d[1]; d[2] = e->d[2]; }
+}
+
+/* -------------------------------------------------------------------- MD */
+/* F_i = sum_j [phi'_{t_i t_j}(r) + F'_{t_i}(rho_i) f'_{t_j}(r)
+ *              + F'_{t_j}(rho_j) f'_{t_i}(r)] (x_j - x_i) / r */
+void orc_forces(orc_sys* s, double* fx, double* fy, double* fz) {
+  double* dF = (double*)malloc(sizeof(double) * s->n);
+  for (int64_t i = 0; i < s->n; ++i) {
+    double v;
+    spline_eval(&s->sp[5 + s->t[i]], s->rho[i], NULL, &v);
+    dF[i] = v;
+  }
+  for (int64_t i = 0; i < s->n; ++i) {
+    int ti = s->t[i];
+    double f[3] = {0, 0, 0};
+    for (int64_t k = s->nstart[i]; k < s->nstart[i + 1]; ++k) {
+      const nbr_t* e = &s->nb[k];
+      int tj = s->t[e->j];
+      double dphi, dfj, dfi;
+      spline_eval(&s->sp[ti + tj], e->r, NULL, &dphi);
+      spline_eval(&s->sp[3 + tj], e->r, NULL, &dfj);
+      spline_eval(&s->sp[3 + ti], e->r, NULL, &dfi);
+      double g = dphi + dF[i] * dfj + dF[e->j] * dfi;
+      for (int a = 0; a < 3; ++a) f[a] += g * e->d[a] / e->r;
+    }
+    fx[i] = f[0]; fy[i] = f[1]; fz[i] = f[2];
+  }
+  free(dF);
+}
+
+void orc_set_md(orc_sys* s, const double* vx, const double* vy, const double* vz,
+                double mass_a, double mass_b, double dt, double gamma, double T_md,
+                uint64_t seed) {
+  if (!s->vx) {
+    s->vx = (double*)malloc(sizeof(double) * s->n);
+    s->vy = (double*)malloc(sizeof(double) * s->n);
+    s->vz = (double*)malloc(sizeof(double) * s->n);
+    s->fx = (double*)malloc(sizeof(double) * s->n);
+    s->fy = (double*)malloc(sizeof(double) * s->n);
+    s->fz = (double*)malloc(sizeof(double) * s->n);
+  }
+  memcpy(s->vx, vx, sizeof(double) * s->n);
+  memcpy(s->vy, vy, sizeof(double) * s->n);
+  memcpy(s->vz, vz, sizeof(double) * s->n);
+  s->mass[0] = mass_a;
+  s->mass[1] = mass_b;
+  s->dt = dt;
+  s->gamma = gamma;
+  s->T_md = T_md;
+  s->md_key[0] = (uint32_t)seed;
+  s->md_key[1] = (uint32_t)(seed >> 32);
+  s->md_step = 0;
+  orc_forces(s, s->fx, s->fy, s->fz);
+}
+
+static double wrap(double x, double L) {
+  double y = x - floor(x / L) * L;
+  if (y >= L) y -= L;
+  if (y < 0) y = 0;
+  return y;
+}
+
+/* Two standard normals by the Box-Muller transform of two uniforms. */
+static void box_muller(uint32_t w[4], double* z0, double* z1) {
+  double u1 = orc_u01(w[0], w[1]), u2 = orc_u01(w[2], w[3]);
+  double r = sqrt(-2.0 * log(1.0 - u1));
+  double th = 2.0 * M_PI * u2;
+  *z0 = r * cos(th);
+  *z1 = r * sin(th);
+}
+
+/* BAOAB Langevin velocity Verlet (gamma = 0 gives plain velocity Verlet). */
+int orc_md_steps(orc_sys* s, int64_t n_steps) {
+  if (!s->vx) return -1;
+  double dt = s->dt;
+  double c1 = exp(-s->gamma * dt), c2 = sqrt(1.0 - c1 * c1);
+  for (int64_t q = 0; q < n_steps; ++q) {
+    for (int64_t i = 0; i < s->n; ++i) {
+      double im = FTM / s->mass[s->t[i]];
+      s->vx[i] += 0.5 * dt * s->fx[i] * im;
+      s->vy[i] += 0.5 * dt * s->fy[i] * im;
+      s->vz[i] += 0.5 * dt * s->fz[i] * im;
+      s->x[i] += 0.5 * dt * s->vx[i];
+      s->y[i] += 0.5 * dt * s->vy[i];
+      s->z[i] += 0.5 * dt * s->vz[i];
+      if (s->gamma > 0) {
+        double sig = sqrt(KB_EV * s->T_md * FTM / s->mass[s->t[i]]);
+        uint32_t ctr[4] = {(uint32_t)s->md_step, (uint32_t)(s->md_step >> 32), (uint32_t)i, 3u};
+        uint32_t w[4];
+        double z0, z1, z2, z3;
+        orc_philox(ctr, s->md_key, w);
+        box_muller(w, &z0, &z1);
+        ctr[3] = 4u;
+        orc_philox(ctr, s->md_key, w);
+        box_muller(w, &z2, &z3);
+        s->vx[i] = c1 * s->vx[i] + c2 * sig * z0;
+        s->vy[i] = c1 * s->vy[i] + c2 * sig * z1;
+        s->vz[i] = c1 * s->vz[i] + c2 * sig * z2;
+      }
+      s->x[i] = wrap(s->x[i] + 0.5 * dt * s->vx[i], s->box[0]);
+      s->y[i] = wrap(s->y[i] + 0.5 * dt * s->vy[i], s->box[1]);
+      s->z[i] = wrap(s->z[i] + 0.5 * dt * s->vz[i], s->box[2]);
+    }
+    if (build_neighbours(s)) return -1;
+    compute_rho(s);
+    orc_forces(s, s->fx, s->fy, s->fz);
+    for (int64_t i = 0; i < s->n; ++i) {
+      double im = FTM / s->mass[s->t[i]];
+      s->vx[i] += 0.5 * dt * s->fx[i] * im;
+      s->vy[i] += 0.5 * dt * s->fy[i] * im;
+      s->vz[i] += 0.5 * dt * s->fz[i] * im;
+    }
+    s->md_step++;
+  }
+  s->energy = orc_energy_full(s);
+  return 0;
+}
+
+void orc_get_md(const orc_sys* s, double* x, double* y, double* z, double* vx, double* vy,
+                double* vz) {
+  if (x) memcpy(x, s->x, sizeof(double) * s->n);
+  if (y) memcpy(y, s->y, sizeof(double) * s->n);
+  if (z) memcpy(z, s->z, sizeof(double) * s->n);
+  if (vx && s->vx) memcpy(vx, s->vx, sizeof(double) * s->n);
+  if (vy && s->vy) memcpy(vy, s->vy, sizeof(double) * s->n);
+  if (vz && s->vz) memcpy(vz, s->vz, sizeof(double) * s->n);
+}
+
+double orc_kinetic_energy(const orc_sys* s) {
+  if (!s->vx) return 0.0;
+  double ke = 0.0;
+  for (int64_t i = 0; i < s->n; ++i)
+    ke += 0.5 * s->mass[s->t[i]] / FTM *
+          (s->vx[i] * s->vx[i] + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]);
+  return ke;
+}
+
+/* Hybrid MC/MD (Sec. IV A): n_md MD steps, then n_mc composite steps on the
+ * frozen positions.  Spatial schedules are rebuilt from the new positions. */
+int orc_hybrid_cycles(orc_sys* s, int64_t n_cycles, int64_t n_md, int64_t n_mc) {
+  for (int64_t c = 0; c < n_cycles; ++c) {
+    if (orc_md_steps(s, n_md)) return -1;
+    if (s->sched_kind == 3 &&
+        orc_schedule_spatial(s, s->sched_args[0], s->sched_args[1], s->sched_args[2],
+                             s->sched_args[3], s->sched_args[4], s->sched_args[5]))
+      return -1;
+    if (orc_parallel_steps(s, n_mc)) return -1;
+    /* forces follow the new types */
+    orc_forces(s, s->fx, s->fy, s->fz);
+  }
+  return 0;
+}
