@@ -1,0 +1,300 @@
+#!/usr/bin/env python3
+"""Throughput of the parallel VC-SGC transmutation sweep on one GB300.
+
+Workload: rigid BCC 80x80x80 cells (1,024,000 sites), EAM tabulated on
+5000-point grids, 2% B placed at random, T = 600 K, kappa = 1000 (units of
+kB T / N), phi scanned over 8 values across the two-phase region -- the 8
+phi values run as 8 replicas of one context.  Every colour of the period-4
+sublattice schedule trials all its 8,000 sites at once (128 colours).
+A step is one sweep of every replica: 8 x 1,024,000 trial moves.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Prints one JSON line.  Under torchrun each rank runs its own replicas (the
+method does not shard: replicas only) and rank 0 reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1012_5082_gb300 import inputs as I  # noqa: E402
+
+CELLS = 80
+T_K = 600.0
+KAPPA = 1000.0
+N_PHI = 8
+FRAC_B = 0.02
+# eV: SGC driving force of the 2% random start (dilute estimate -dE_dilute +
+# kT ln(c/(1-c)) with dE_dilute = 2.275 eV), so local A->B and B->A accepts
+# balance and composite moves stay small (parameter recipe of Sec. III C)
+DMU_S = -2.07
+BYTES_PER_TRIAL = 4 * 58 + 1 + 8  # neighbour row + own species + own F_B - F_A
+METRIC = "VC-SGC trial moves/s"
+
+
+def workload():
+    lat = I.bcc_lattice(CELLS, CELLS, CELLS)
+    types = I.random_types(lat.n, int(round(FRAC_B * lat.n)), seed=1001)
+    tab = I.eam_tables()
+    c0 = 0.02 + np.arange(N_PHI) * 0.48 / 7
+    # phi_j = dmu_S - 2 kappa kB T c0_j: dmu0 = dmu_S for every replica
+    phi = DMU_S - 2.0 * KAPPA * I.KB_EV * T_K * c0
+    return lat, types, tab, phi, c0
+
+
+def config_dict(extra=None):
+    d = {"workload": f"rigid BCC {CELLS}^3 cells (1,024,000 sites), EAM 5000-pt tables, "
+                     f"2% B, T=600 K, kappa=1000, {N_PHI} phi values as replicas, "
+                     "period-4 sublattice schedule (8,000 trials per colour step)",
+         "sites": 2 * CELLS ** 3, "replicas": N_PHI, "trials_per_step": N_PHI * 2 * CELLS ** 3,
+         "l2_policy": "inputs larger than L2 (int32 neighbour list 237 MB streamed each sweep)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(lat, types, tab, phi, c0, budget_s=12.0):
+    """The oracle, as it stands, on one host core: one replica of the same
+    workload, sweeps of the same schedule, about budget_s seconds."""
+    import oracle as O
+
+    s = O.System(lat, types, tab)
+    s.set_params(float(phi[0]), KAPPA, T_K, c0=float(c0[0]), seed=2001)
+    s.schedule_sublattice(lat.cells, (4, 4, 4))
+    t0 = time.perf_counter()
+    s.parallel_steps(4)
+    dt = time.perf_counter() - t0
+    n_steps = max(4, int(budget_s / max(dt / 4, 1e-6)))
+    t0 = time.perf_counter()
+    s.parallel_steps(n_steps)
+    dt = time.perf_counter() - t0
+    trials = s.obs()["trials"]
+    per_step = lat.n // 128
+    done = n_steps * per_step
+    return {"value": done / dt, "unit": "trial moves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_steps} colour steps ({done} trial moves, {done / lat.n:.2f} sweeps) of "
+                      f"replica 0 of the 80^3 workload, serial FP64 C oracle, {dt:.1f} s",
+            "trials_counted": int(trials)}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle times the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    lat, types, tab, phi, c0 = workload()
+    s = O.System(lat, types, tab)
+    s.set_params(float(phi[0]), KAPPA, T_K, c0=float(c0[0]), seed=2001)
+    s.schedule_sublattice(lat.cells, (4, 4, 4))
+    step_steps = 16  # colour steps per bench step: 128,000 trial moves
+    for _ in range(args.warmup):
+        s.parallel_steps(step_steps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.parallel_steps(step_steps)
+    dt = time.perf_counter() - t0
+    trials = args.steps * step_steps * (lat.n // 128)
+    v = trials / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "trial moves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict({"reference_sample": f"{step_steps} colour steps of replica 0 per step"}),
+            "cpu_baseline": {"value": v, "unit": "trial moves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{step_steps} colour steps ({step_steps * (lat.n // 128)} "
+                                       "trial moves) of replica 0 per step"},
+            "e2e": {"value": v, "unit": "trial moves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1012_5082_gb300 import vcsgc as V
+
+    lat, types, tab, phi, c0 = workload()
+    stream = torch.cuda.Stream()
+    seeds = np.arange(N_PHI, dtype=np.uint64) + np.uint64(2001 + 1000 * rank)
+    ctx = V.Context(lat, np.tile(types, N_PHI), tab, 0.0, KAPPA, T_K, schedule=V.SCHED_SUBLATTICE,
+                    sched=(4, 4, 4), n_replicas=N_PHI, phi_r=phi, c0_r=c0, seed_r=seeds,
+                    stream=stream, device=local)
+    spw = ctx.steps_per_sweep
+    trials_per_step = N_PHI * lat.n
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    # warm-up (also builds the CUDA graph)
+    ctx.sweep(args.warmup)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        ctx.sweep(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * trials_per_step * args.steps / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (propose: dE gather + local test)
+    n_prof = 2 * spw
+    ms_prop, ms_comm = ctx.profile_steps(n_prof)
+    avg_prop_ms = ms_prop / n_prof
+    bytes_per_launch = N_PHI * (lat.n // 128) * BYTES_PER_TRIAL
+    peak, peak_kind = measured_peak_hbm()
+    achieved = bytes_per_launch / (avg_prop_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_propose (colour step: site pick, dE gather, local Metropolis, dn reduction)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+            "traffic": None, "bytes_per_launch": bytes_per_launch,
+            "avg_launch_us": avg_prop_ms * 1e3, "avg_commit_us": ms_comm / n_prof * 1e3,
+            "share_of_step": ms_prop / (ms_prop + ms_comm)}
+
+    # end to end through the C ABI with host buffers: species up, one sweep,
+    # species and observables down, every step
+    pinned = torch.empty((N_PHI, lat.n), dtype=torch.uint8, pin_memory=True)
+    host = pinned.numpy()
+    for r in range(N_PHI):
+        host[r] = ctx.types(r)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for r in range(N_PHI):
+            ctx.set_types(host[r], r)
+        ctx.sweep(1)
+        obs = [ctx.observables(r) for r in range(N_PHI)]
+        for r in range(N_PHI):
+            host[r] = ctx.types(r)
+    barrier()
+    dt_e2e = time.perf_counter() - t0
+    e2e = {"value": world * trials_per_step * args.steps / dt_e2e, "unit": "trial moves/s",
+           "h2d_bytes_per_step": N_PHI * lat.n, "d2h_bytes_per_step": N_PHI * lat.n + N_PHI * 160}
+
+    o0 = ctx.observables(0)
+    ctx.close()
+    line = {"metric": METRIC, "value": value, "unit": "trial moves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict({"parallelism": f"replicas x{world}"}),
+            "e2e": e2e, "gpu_launches": 2 * spw * args.steps, "roofline": roof,
+            "clocks": clk.summary(),
+            "acceptance": {"local": o0["acc_local"], "global": o0["acc_global"], "c": o0["c"]}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(lat, types, tab, phi, c0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

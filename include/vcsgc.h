@@ -1,0 +1,247 @@
+/*
+ * vcsgc.h -- C ABI of the GB300 (sm_103a) implementation of the parallel
+ * variance-constrained semi-grandcanonical (VC-SGC) Monte Carlo method of
+ * Sadigh, Erhart, Stukowski, Caro, Martinez and Zepeda-Ruiz, "A scalable
+ * parallel Monte Carlo algorithm for atomistic simulations of precipitation
+ * in alloys", with the EAM molecular-dynamics step of its hybrid MC/MD scheme.
+ *
+ * Conventions
+ *   - Units: Angstrom, eV, K, fs, amu.  Species 0 = A, 1 = B; the
+ *     concentration c is the fraction of B sites (Sec. II: n = sum sigma_i).
+ *   - Every function returns an int status: VCSGC_OK (0) or a negative
+ *     VCSGC_ERR_* code; vcsgc_last_error() gives a text for the last failure.
+ *     No function traps, aborts or exits the process.
+ *   - Pointer arguments are HOST pointers unless stated otherwise.  Inputs are
+ *     copied during the call; the caller keeps ownership of its buffers.
+ *   - A context owns all device memory it allocates and releases it in
+ *     vcsgc_free().  Work is issued on the stream given in the options (the
+ *     legacy default stream when NULL); calls that return host data
+ *     synchronise that stream.
+ *   - A context may hold R >= 1 independent replicas (chains) of one lattice,
+ *     each with its own species array, phi, kappa, T and seed.  Replicas are
+ *     advanced together, one composite step each per colour step.
+ *   - Multi-GPU: none.  One context drives one GPU; replicas are the only
+ *     data-parallel axis.
+ */
+#ifndef VCSGC_H
+#define VCSGC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+#define VCSGC_OK 0
+#define VCSGC_ERR_INVALID_ARG (-1) /* argument out of its documented range  */
+#define VCSGC_ERR_CUDA (-2)        /* a CUDA runtime call failed            */
+#define VCSGC_ERR_TABLE_RANGE (-3) /* r or rho left an EAM table's grid     */
+#define VCSGC_ERR_NONFINITE (-4)   /* NaN or Inf met in an energy or force  */
+#define VCSGC_ERR_SCHEDULE (-5)    /* domains of one colour closer than the
+                                      independence radius 2 r_c, or sizes
+                                      that do not divide                    */
+#define VCSGC_ERR_TIMEOUT (-6)     /* a bounded device wait ran out         */
+#define VCSGC_ERR_NOMEM (-7)       /* device or host allocation failed      */
+#define VCSGC_ERR_STATE (-8)       /* call not valid in the context's state
+                                      (e.g. md_steps without velocities)    */
+#define VCSGC_ERR_OVERFLOW (-9)    /* neighbour list capacity exceeded      */
+
+/* ------------------------------------------------------------- lattices */
+/* The periodic cell the species live on (Sec. II: positions x^{3N}).
+ * kind 0: rigid BCC lattice of nx*ny*nz cubic cells of side a; site
+ *         i = ((cz*ny + cy)*nx + cx)*2 + b sits at a*(cx+b/2, cy+b/2, cz+b/2);
+ *         box = a*(nx, ny, nz); x, y, z, n, box are ignored.
+ * kind 1: n explicit positions (host SoA arrays x, y, z, each length n) in
+ *         the orthorhombic periodic box box[0..2]; each box length must
+ *         exceed 2 (r_c + skin). */
+typedef struct {
+  int32_t kind;
+  int32_t nx, ny, nz;
+  double a;
+  int64_t n;
+  const double* x;
+  const double* y;
+  const double* z;
+  double box[3];
+} vcsgc_lattice;
+
+/* EAM potential (Daw-Baskes form, the many-body short-range potential the
+ * paper's method targets, Sec. I and III A):
+ *   U = sum_i [ 1/2 sum_j phi_{t_i t_j}(r_ij) + F_{t_i}(rho_i) ],
+ *   rho_i = sum_j f_{t_j}(r_ij).
+ * Tables on uniform grids: r_j = j*dr (j < nr, covering [0, rc]) for
+ * pair[0..2] = phi_AA, phi_AB, phi_BB and dens[0..1] = f_A, f_B; rho_j =
+ * j*drho (j < nrho) for embed[0..1] = F_A, F_B.  d* arrays give the exact
+ * derivative at each knot; NULL selects central finite differences of the
+ * values (one-sided at the two ends).  Interpolation is cubic Hermite, so
+ * energies are C^1 and forces are the exact derivative of the interpolant. */
+typedef struct {
+  int32_t nr;
+  double dr;
+  int32_t nrho;
+  double drho;
+  double rc;
+  const double* pair[3];
+  const double* dpair[3];
+  const double* dens[2];
+  const double* ddens[2];
+  const double* embed[2];
+  const double* dembed[2];
+} vcsgc_eam_tables;
+
+/* ------------------------------------------------------------ schedules */
+/* Colour schedules: the domain decomposition of Sec. III A.  Each colour
+ * step draws one colour from the synchronised random stream; every domain of
+ * that colour proposes one flip at once.  Domains of one colour must be more
+ * than 2 r_c apart (many-body independence radius), which vcsgc_init checks.
+ *   BLOCKS:     (kind 0) domains = blocks of sched[0..2] = bx,by,bz cells,
+ *               colour = (block index mod p) per axis with sched[3..5] =
+ *               px,py,pz; one uniformly chosen site per domain per step.
+ *               The paper's octant scheme is p = (2,2,2).
+ *   SUBLATTICE: (kind 0) colour = (cx mod qx, cy mod qy, cz mod qz, basis)
+ *               with sched[0..2] = qx,qy,qz; every site of the colour is a
+ *               domain of its own, so all of them are trialled at once.
+ *   SPATIAL:    (kind 0 or 1) domains = sched[0..2] = nbx,nby,nbz boxes of
+ *               the periodic cell, colour as for BLOCKS with sched[3..5]. */
+#define VCSGC_SCHED_BLOCKS 0
+#define VCSGC_SCHED_SUBLATTICE 1
+#define VCSGC_SCHED_SPATIAL 2
+
+#define VCSGC_PREC_FP64 0
+#define VCSGC_PREC_MIXED 1
+
+typedef struct {
+  uint64_t seed;        /* Philox key of replica 0 (replica r: seed_r[r] or seed + r) */
+  double c0;            /* reference concentration of Eq. trans_vcsgc_par1; < 0: initial c */
+  int32_t kappa_units;  /* 0: kappa dimensionless, kappa_p = kappa kB T / N (eV)
+                           1: kappa_p = kappa in eV, Eq. pi_vcsgc as printed */
+  int32_t schedule;     /* VCSGC_SCHED_* */
+  int32_t sched[6];
+  int32_t precision;    /* VCSGC_PREC_FP64 */
+  int32_t n_replicas;   /* >= 1 */
+  const double* phi_r;  /* per-replica phi, kappa, T, seed, c0 (n_replicas each) or NULL */
+  const double* kappa_r;
+  const double* T_r;
+  const uint64_t* seed_r;
+  const double* c0_r;
+  /* molecular dynamics (hybrid scheme, Sec. IV A); used by md_steps */
+  double mass[2];       /* amu; default 55.845, 63.546 */
+  double dt;            /* fs; default 2 */
+  double gamma;         /* Langevin friction (1/fs); 0 = NVE; default 0.01 */
+  double T_md;          /* thermostat temperature (K); default = T */
+  double skin;          /* neighbour-list skin (Angstrom); default 0.3 */
+  uint64_t md_seed;     /* Philox key of the thermostat noise */
+  void* stream;         /* cudaStream_t; NULL: the context creates its own stream */
+  int32_t device;       /* CUDA device ordinal; < 0: the calling thread's current device */
+} vcsgc_options;
+
+/* Observables (Sec. II C): B count, concentration, energy, acceptance and
+ * the chemical-potential estimate dmu = phi + 2 kappa_p N <c> (Eq. gforce). */
+typedef struct {
+  int64_t n_sites;
+  int64_t n_b;
+  double c;
+  double energy;          /* incrementally tracked total energy (eV) */
+  double energy_per_atom;
+  int64_t steps;          /* colour (composite) steps */
+  int64_t trials;         /* local trial moves */
+  int64_t local_accepts;
+  int64_t global_trials;  /* steps with >= 1 local accept */
+  int64_t global_accepts;
+  int64_t flips;
+  int64_t near_ties;      /* decisions with |u - p| <= 1e-9 p */
+  double acc_local;       /* local_accepts / trials */
+  double acc_global;      /* global_accepts / global_trials */
+  double mean_c;          /* <c> over steps */
+  double var_c;
+  double dmu_est;         /* phi + 2 kappa_p N <c> */
+  double sweeps;          /* trials / N */
+  double kappa_p;         /* eV */
+  double dmu0;            /* phi + 2 kappa_p N c0 (eV) */
+} vcsgc_observables;
+
+/* Fill *opt with the defaults: seed 1, c0 = -1, kappa_units 0, SUBLATTICE
+ * (4,4,4), FP64, one replica, masses 55.845/63.546 amu, dt 2 fs, gamma
+ * 0.01/fs, skin 0.3 A, NULL stream. */
+int vcsgc_default_options(vcsgc_options* opt);
+
+/* Create a context: copy the lattice, species (n_replicas * N bytes,
+ * replica-major; 0 = A, 1 = B), EAM tables and ensemble parameters to the
+ * device, build the neighbour list (A1), rho and U (A2) and the colour
+ * schedule (A3).  phi (eV), kappa and T (K) follow Eq. pi_vcsgc:
+ * pi_V ~ exp[-beta (U + phi n + kappa_p n^2)].  opt may be NULL.
+ * Errors: INVALID_ARG (bad sizes, species other than 0/1, T <= 0),
+ * SCHEDULE, TABLE_RANGE, NOMEM, CUDA. */
+int vcsgc_init(void** ctx, const vcsgc_lattice* lattice, const uint8_t* types,
+               const vcsgc_eam_tables* eam, double phi, double kappa, double T,
+               const vcsgc_options* opt);
+
+/* Advance every replica by n_steps colour steps (composite moves of
+ * Sec. III B 2: site pick, dE gather, local Metropolis test with
+ * dmu0 = phi + 2 kappa_p N c0, reduction of dn, global test with exponent
+ * -beta kappa_p dn (dn + 2 (n - n0)), commit).  Asynchronous on the stream. */
+int vcsgc_steps(void* ctx, int64_t n_steps);
+
+/* n_sweeps sweeps: one sweep = N trial moves = N / (domains per colour)
+ * colour steps (the paper's MC cycle of N_at trials, Sec. IV B). */
+int vcsgc_sweep(void* ctx, int64_t n_sweeps);
+
+/* Colour steps per sweep for this context's schedule. */
+int vcsgc_steps_per_sweep(void* ctx, int64_t* out);
+
+/* n_steps MD steps (EAM forces, BAOAB Langevin velocity Verlet) on replica 0.
+ * Needs kind 1 (explicit positions), n_replicas = 1 and velocities set by
+ * vcsgc_set_velocities.  The neighbour list is rebuilt when an atom moved
+ * more than skin/2 since the last build. */
+int md_steps(void* ctx, int64_t n_steps);
+
+/* Hybrid MC/MD (Sec. IV A): n_cycles times (n_md MD steps, then n_mc colour
+ * steps on the frozen positions; a flipped atom's velocity is scaled by
+ * sqrt(m_old/m_new)).  SPATIAL schedules are rebuilt from the positions at
+ * the start of each MC phase. */
+int vcsgc_hybrid(void* ctx, int64_t n_cycles, int64_t n_md, int64_t n_mc);
+
+/* Observables of one replica (synchronises the stream). */
+int observables(void* ctx, int32_t replica, vcsgc_observables* out);
+
+/* Species of one replica: N bytes to/from host memory.  set_types
+ * recomputes rho and the energy and keeps the counters. */
+int vcsgc_get_types(void* ctx, int32_t replica, uint8_t* out);
+int vcsgc_set_types(void* ctx, int32_t replica, const uint8_t* in);
+/* Electron density rho_i of one replica, N doubles. */
+int vcsgc_get_rho(void* ctx, int32_t replica, double* out);
+/* Energy change of flipping each of sites[0..n) of one replica on its current
+ * state, evaluated by the sweep's own device code (A4); out: n doubles. */
+int vcsgc_delta_e(void* ctx, int32_t replica, const int64_t* sites, int64_t n, double* out);
+/* Total energy of one replica recomputed from scratch on the device. */
+int vcsgc_energy(void* ctx, int32_t replica, double* out);
+/* Forces of replica 0 (3 x N doubles, SoA fx, fy, fz). */
+int vcsgc_forces(void* ctx, double* fx, double* fy, double* fz);
+/* Positions and velocities of replica 0 (each N doubles; any may be NULL). */
+int vcsgc_get_md(void* ctx, double* x, double* y, double* z, double* vx, double* vy,
+                 double* vz);
+int vcsgc_set_velocities(void* ctx, const double* vx, const double* vy, const double* vz);
+/* Kinetic energy of replica 0 (eV). */
+int vcsgc_kinetic_energy(void* ctx, double* out);
+
+/* Run n colour steps with a CUDA event after each launch on the context's
+ * stream and return the summed device time (ms) of the propose kernels and
+ * of the commit kernels.  Same work as vcsgc_steps(n); for profiling. */
+int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_commit);
+
+/* Neighbour list of replica 0's lattice: capacity K per site and, for site
+ * i, the neighbour indices in out[0..count) (count <= K).  For tests. */
+int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* count);
+
+/* Text of the last error of ctx (or of the last failed vcsgc_init when ctx
+ * is NULL).  Valid until the next call on the same context. */
+const char* vcsgc_last_error(void* ctx);
+
+/* Release the context and all its device memory.  NULL is a no-op. */
+void vcsgc_free(void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

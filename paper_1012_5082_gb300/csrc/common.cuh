@@ -1,0 +1,209 @@
+// common.cuh -- device-side building blocks shared by the VC-SGC kernels:
+// the counter-based random stream, EAM table interpolation, the Metropolis
+// test, and the argument blocks passed to the kernels by value.
+//
+// Method: Sadigh et al., "A scalable parallel Monte Carlo algorithm for
+// atomistic simulations of precipitation in alloys" (Sec. III).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vcsgc {
+
+constexpr double KB_EV = 8.617333262e-5;      // Boltzmann constant, eV/K
+constexpr double FTM = 9.648533212331e-3;     // eV/(A amu) -> A/fs^2
+constexpr int MAX_SHELLS = 16;
+constexpr int MAX_OFFSETS = 256;
+
+// device error bits, OR-ed into a context-wide status word
+enum : unsigned {
+  ERRF_TABLE = 1u,      // r or rho outside a table grid
+  ERRF_NONFINITE = 2u,  // NaN/Inf energy difference or force
+  ERRF_OVERFLOW = 4u,   // neighbour row longer than its capacity
+  ERRF_TIMEOUT = 8u,    // bounded wait ran out
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Counter-based: each
+// (key, counter) pair gives four independent 32-bit words, so every trial of
+// every colour step draws its numbers without state or communication -- the
+// "synchronised seed" of Sec. III A taken to the limit.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// stream tags in the fourth counter word
+constexpr uint32_t TAG_TRIAL = 0u;   // (step, domain rank): site pick + local u
+constexpr uint32_t TAG_STEP = 1u;    // (step, 0xFFFFFFFF): colour + global u
+constexpr uint32_t TAG_NOISE0 = 3u;  // (md step, atom): thermostat normals
+constexpr uint32_t TAG_NOISE1 = 4u;
+
+__device__ __forceinline__ uint64_t word64(uint32_t lo, uint32_t hi) {
+  return ((uint64_t)hi << 32) | lo;
+}
+// index in [0, m): floor(w * m / 2^64)
+__device__ __forceinline__ uint64_t below64(uint32_t lo, uint32_t hi, uint64_t m) {
+  return __umul64hi(word64(lo, hi), m);
+}
+// top 53 bits of the word; u = u53 * 2^-53 in [0, 1)
+__device__ __forceinline__ uint64_t top53(uint32_t lo, uint32_t hi) {
+  return word64(lo, hi) >> 11;
+}
+
+// --------------------------------------------------------------- splines
+// Cubic on each grid interval in power form: v(t) = c0 + t(c1 + t(c2 + t c3)),
+// t = x/h - j in [0, 1]; the coefficients are derived on the device from the
+// caller's knot values and derivatives (Hermite data).
+struct __align__(32) Cubic {
+  double x, y, z, w;  // c0, c1, c2, c3
+};
+
+struct Spline {
+  const Cubic* c;
+  double inv_h;
+  double xmax;
+  int n_int;
+};
+
+struct Tables {
+  Spline sp[7];  // 0..2 pair AA AB BB, 3..4 density A B, 5..6 embedding A B
+};
+
+__device__ __forceinline__ int spline_locate(const Spline& s, double x, double& t, unsigned* err) {
+  if (!(x >= 0.0) || x > s.xmax) {
+    atomicOr(err, ERRF_TABLE);
+    t = 0.0;
+    return 0;
+  }
+  const double u = x * s.inv_h;
+  int j = (int)u;
+  if (j > s.n_int - 1) j = s.n_int - 1;
+  t = u - (double)j;
+  return j;
+}
+
+__device__ __forceinline__ double spline_val(const Spline& s, double x, unsigned* err) {
+  double t;
+  const int j = spline_locate(s, x, t, err);
+  const Cubic c = s.c[j];
+  return fma(t, fma(t, fma(t, c.w, c.z), c.y), c.x);
+}
+
+__device__ __forceinline__ double spline_val_at(const Spline& s, int j, double t) {
+  const Cubic c = s.c[j];
+  return fma(t, fma(t, fma(t, c.w, c.z), c.y), c.x);
+}
+
+// derivative d/dx at a located point
+__device__ __forceinline__ double spline_der_at(const Spline& s, int j, double t) {
+  const Cubic c = s.c[j];
+  return fma(t, fma(t, 3.0 * c.w, 2.0 * c.z), c.y) * s.inv_h;
+}
+
+// ------------------------------------------------------------ Metropolis
+// Decision u < min{1, exp(-X)} with u = u53 * 2^-53, exactly as an FP64
+// evaluation decides it.  GB300 runs FP32 ~60x faster than FP64, so the
+// exponential is first taken in FP32 with an error margin that covers the
+// rounding of X to float (|X| 2^-24 relative), expf's documented 2-ulp bound
+// and the float products; only decisions inside that margin (about one in
+// 10^5) fall through to the FP64 exp.  For X > 80 the FP64 p is below
+// 2^-53 <= u whenever u53 >= 1, so such moves are rejected without exp.
+// *tie is set when |u - p| <= 1e-9 p, where CPU and GPU exp may disagree.
+__device__ __forceinline__ bool metropolis(double X, uint64_t u53, int* tie) {
+  if (X <= 0.0) {
+    if (X > -1e-9 && (double)u53 * 0x1p-53 >= 1.0 - 1e-9) *tie = 1;
+    return true;
+  }
+  if (u53 != 0) {
+    if (X > 80.0) return false;
+    const float xf = (float)X;
+    const float pf = expf(-xf) * 9007199254740992.0f;  // p * 2^53
+    const float uf = (float)u53;
+    const float m = 9.5367431640625e-07f + xf * 2.384185791015625e-07f;  // 2^-20 + X 2^-22
+    if (uf * (1.0f + 1.1920929e-07f) < pf * (1.0f - m)) return true;
+    if (uf * (1.0f - 1.1920929e-07f) > pf * (1.0f + m)) return false;
+  }
+  const double p = exp(-X);
+  const double u = (double)u53 * 0x1p-53;
+  if (fabs(u - p) <= 1e-9 * p) *tie = 1;
+  return u < p;
+}
+
+// --------------------------------------------------------- state blocks
+// Per-replica ensemble parameters (Eq. pi_vcsgc, Eq. trans_vcsgc_par1).
+struct RepParams {
+  double beta;     // 1/(kB T)
+  double kappa_p;  // eV
+  double n0;       // N c0
+  double dmu0;     // phi + 2 kappa_p N c0
+  double phi;
+  uint2 key;       // Philox key
+};
+
+// Per-replica running state, advanced by the last block of each commit.
+struct RepState {
+  long long n;  // B count
+  long long step;
+  double energy;
+  long long trials, local_acc, global_trials, global_acc, flips, near_ties, steps;
+  double sum_c, sum_c2;
+};
+
+// Per-replica accumulator of one colour step (the paper's allgather of dc_i).
+struct StepAcc {
+  int dn;
+  int nacc;
+  double sum_de;
+  unsigned done;
+  int ties;
+};
+
+// Everything the colour-step kernels read, passed by value.
+struct McArgs {
+  long long N;
+  int R;
+  int K;                 // neighbour row stride
+  const int* nbr;        // [N][K], -1 padded
+  const int* nbr_cnt;    // [N] row lengths
+  uint8_t* types;        // [R][N]
+  double* rho;           // [R][N] when rho_per_rep, else [N]
+  int rho_per_rep;
+  const double* dF;      // [N] F_B(rho_i) - F_A(rho_i) (static-density forms)
+  double* vel[3];        // velocities of replica 0 or null (hybrid MC/MD)
+  double mass[2];
+  // shell form (rigid lattice): slots sorted by shell
+  int n_shells;
+  int shell_end[MAX_SHELLS];
+  const double* shell_tab;  // [0] = C_A, [1+s] = G_A[s], [1+S+s] = f_B - f_A at r_s,
+                            // [1+2S+s] = r_s
+  // general form (explicit positions)
+  const double* x;
+  const double* y;
+  const double* z;
+  double box[3];
+  double rc;
+  Tables tab;
+  // schedule
+  int n_colours;
+  const int* col_start;
+  const int* dom_start;
+  const int* dom_sites;
+  int dmax;
+  // replicas
+  const RepParams* rp;
+  RepState* rs;
+  StepAcc* acc;
+  int* acc_list;  // [R][dmax]
+  unsigned* err;
+};
+
+}  // namespace vcsgc

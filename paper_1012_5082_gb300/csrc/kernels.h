@@ -1,0 +1,85 @@
+// kernels.h -- launchers of the device kernels (host-callable, internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace vcsgc {
+
+constexpr int MC_BLOCK = 128;
+
+// ---- tables (kernels_nbr.cu)
+// Cubic coefficients of one table from knot values y[0..n) and optional knot
+// derivatives m (nullptr: central differences); out has n-1 intervals.
+void launch_spline_coeffs(const double* y, const double* m, int n, double h, Cubic* out,
+                          cudaStream_t st);
+// Per-shell pair and density differences of the rigid lattice:
+// tab[0] = C_A, tab[1+s] = G_A[s], tab[1+S+s] = f_B(r_s) - f_A(r_s), tab[1+2S+s] = r_s,
+// with r_s = (a/2) sqrt(h2[s]) and z[s] neighbours in shell s.
+void launch_shell_tables(Tables tab, const int* h2, const int* z, int S, double a, double* out,
+                         unsigned* err, cudaStream_t st);
+
+// ---- neighbour lists (kernels_nbr.cu)
+// Rigid BCC: row i lists the sites at the K half-lattice offsets hoff (x,y,z).
+void launch_lattice_neighbours(int nx, int ny, int nz, const int3* hoff, int K, int* nbr, int* cnt,
+                               cudaStream_t st);
+// Explicit positions: cell binning (side >= rl, >= 3 cells per axis) and a
+// full neighbour list within rl; rows longer than K set ERRF_OVERFLOW.
+struct CellList {
+  int nc[3];
+  int* cell_of;    // [N]
+  int* cell_count; // [ncell]
+  int* cell_start; // [ncell + 1]
+  int* cell_cursor;// [ncell]
+  int* sorted;     // [N]
+};
+void launch_cell_neighbours(long long N, const double* x, const double* y, const double* z,
+                            const double box[3], double rl, CellList cl, int K, int* nbr, int* cnt,
+                            unsigned* err, cudaStream_t st);
+
+// ---- density, energy (kernels_nbr.cu)
+// rho_i of replica r (shared array when !per_rep) and, if dF != nullptr,
+// dF_i = F_B(rho_i) - F_A(rho_i).
+void launch_rho(const McArgs& a, bool shell, int r, cudaStream_t st);
+// Block partial sums of the energy of replica r into part[0..nblocks).
+int energy_blocks(long long N);
+void launch_energy(const McArgs& a, bool shell, int r, double* part, cudaStream_t st);
+
+// ---- colour step (kernels_mc.cu)
+// phase 0: propose + commit; 1: propose only; 2: commit only
+void launch_colour_step(const McArgs& a, bool shell, bool reembed, cudaStream_t st, int phase = 0);
+void launch_delta_e_list(const McArgs& a, bool shell, bool reembed, int r, const int* sites, int n,
+                         double* out, cudaStream_t st);
+
+// ---- molecular dynamics (kernels_md.cu)
+struct MdArgs {
+  long long N;
+  int K;
+  const int* nbr;
+  const int* nbr_cnt;
+  const uint8_t* types;
+  double *x, *y, *z, *vx, *vy, *vz, *fx, *fy, *fz;
+  double* rho;
+  double* dFp;   // F'(rho_i)
+  double* dF;    // F_B(rho_i) - F_A(rho_i)
+  double *x0, *y0, *z0;  // positions at the last neighbour build
+  double box[3];
+  double rc;
+  double mass[2];
+  double dt, c1, c2, kT;
+  uint2 key;
+  Tables tab;
+  unsigned* err;
+  unsigned long long* max_disp2_bits;  // max squared displacement (as bits)
+};
+void launch_md_rho(const MdArgs& m, cudaStream_t st);
+void launch_md_force(const MdArgs& m, cudaStream_t st);
+void launch_md_first_half(const MdArgs& m, long long md_step, cudaStream_t st);
+void launch_md_second_half(const MdArgs& m, cudaStream_t st);
+void launch_md_snapshot(const MdArgs& m, cudaStream_t st);
+void launch_kinetic(const MdArgs& m, double* part, cudaStream_t st);
+int kinetic_blocks(long long N);
+
+}  // namespace vcsgc

@@ -1,0 +1,322 @@
+// kernels_mc.cu -- the colour step of the parallel VC-SGC method
+// (Sec. III B 2 of Sadigh et al.): site pick, energy difference, local
+// Metropolis stage, reduction of the concentration change, global stage and
+// commit.  One colour step is two launches:
+//   k_propose: every domain of the drawn colour picks a site, evaluates
+//              dE_i and the local test (Eq. trans_vcsgc_par1); accepted
+//              sites are compacted into a list and dn = sum s_i is reduced
+//              (warp shuffles, one atomic per block: the paper's allgather);
+//   k_commit:  every block derives the same global decision
+//              (Eq. trans_vcsgc_par2, exponent -beta kappa_p dn (dn + 2(n-n0)))
+//              and, if accepted, flips its share of the list and scatters the
+//              density change; the last block to finish advances the
+//              replica's counters.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vcsgc {
+
+__device__ __forceinline__ double min_image(double d, double L) {
+  return d - L * rint(d / L);
+}
+
+// Energy change of flipping site i of replica r, t -> t' = 1 - t:
+//   pair:     sum_k [phi_{t' t_k} - phi_{t t_k}](r_ik)
+//   own:      F_{t'}(rho_i) - F_t(rho_i)
+//   re-embed: sum_k F_{t_k}(rho_k + drho_k) - F_{t_k}(rho_k),
+//             drho_k = f_{t'}(r_ik) - f_t(r_ik)
+// SHELL: rigid lattice, slots grouped by shell so the pair sum is the
+// per-shell B count times a tabulated difference (exact in arithmetic, no
+// per-neighbour interpolation).  !SHELL: distances from positions.
+template <bool SHELL, bool REEMBED>
+__device__ double delta_e(const McArgs& a, int r, int i, unsigned* err) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const int t = ty[i];
+  const int* row = a.nbr + (long long)i * a.K;
+  double de;
+  if constexpr (SHELL) {
+    const int S = a.n_shells;
+    de = a.shell_tab[0];
+    int k = 0;
+    for (int s = 0; s < S; ++s) {
+      int cnt = 0;
+      const int end = a.shell_end[s];
+      for (; k < end; ++k) cnt += ty[row[k]];
+      de = fma((double)cnt, a.shell_tab[1 + s], de);
+    }
+    if (t) de = -de;
+    if constexpr (!REEMBED) {
+      const double dfi = a.dF[i];
+      de += t ? -dfi : dfi;
+    } else {
+      const double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
+      const double ri = rho[i];
+      de += spline_val(a.tab.sp[6 - t], ri, err) - spline_val(a.tab.sp[5 + t], ri, err);
+      k = 0;
+      for (int s = 0; s < S; ++s) {
+        const double dfs = a.shell_tab[1 + S + s];
+        const double drho = t ? -dfs : dfs;
+        const int end = a.shell_end[s];
+        for (; k < end; ++k) {
+          const int j = row[k];
+          const int tj = ty[j];
+          const double rj = rho[j];
+          de += spline_val(a.tab.sp[5 + tj], rj + drho, err) - spline_val(a.tab.sp[5 + tj], rj, err);
+        }
+      }
+    }
+  } else {
+    const int tp = 1 - t;
+    const int cnt = a.nbr_cnt[i];
+    const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
+    const double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
+    double pair = 0.0, re = 0.0;
+    for (int k = 0; k < cnt; ++k) {
+      const int j = row[k];
+      const double dx = min_image(a.x[j] - xi, a.box[0]);
+      const double dy = min_image(a.y[j] - yi, a.box[1]);
+      const double dz = min_image(a.z[j] - zi, a.box[2]);
+      const double rr = sqrt(dx * dx + dy * dy + dz * dz);
+      if (rr >= a.rc) continue;
+      const int tj = ty[j];
+      double tt;
+      const int jj = spline_locate(a.tab.sp[0], rr, tt, err);
+      pair += spline_val_at(a.tab.sp[tp + tj], jj, tt) - spline_val_at(a.tab.sp[t + tj], jj, tt);
+      if constexpr (REEMBED) {
+        const double drho = spline_val_at(a.tab.sp[3 + tp], jj, tt) - spline_val_at(a.tab.sp[3 + t], jj, tt);
+        const double rj = rho[j];
+        re += spline_val(a.tab.sp[5 + tj], rj + drho, err) - spline_val(a.tab.sp[5 + tj], rj, err);
+      }
+    }
+    double own;
+    if constexpr (REEMBED) {
+      const double ri = rho[i];
+      own = spline_val(a.tab.sp[5 + tp], ri, err) - spline_val(a.tab.sp[5 + t], ri, err);
+    } else {
+      own = t ? -a.dF[i] : a.dF[i];
+    }
+    de = pair + own + re;
+  }
+  return de;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void block_reduce3(int& a, int& b, double& c) {
+  __shared__ int sa[BLOCK / 32], sb[BLOCK / 32];
+  __shared__ double sc[BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sa[w] = a; sb[w] = b; sc[w] = c; }
+  __syncthreads();
+  if (w == 0) {
+    a = l < BLOCK / 32 ? sa[l] : 0;
+    b = l < BLOCK / 32 ? sb[l] : 0;
+    c = l < BLOCK / 32 ? sc[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+  }
+}
+
+__device__ __forceinline__ int draw_colour(const McArgs& a, uint2 key, long long step, uint64_t* ug53) {
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0xFFFFFFFFu, TAG_STEP), key);
+  if (ug53) *ug53 = top53(w.z, w.w);
+  return (int)below64(w.x, w.y, (uint64_t)a.n_colours);
+}
+
+template <bool SHELL, bool REEMBED>
+__global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
+  const int r = blockIdx.y;
+  const RepParams p = a.rp[r];
+  const long long step = a.rs[r].step;
+  const int c = draw_colour(a, p.key, step, nullptr);
+  const int d0 = a.col_start[c];
+  const int D = a.col_start[c + 1] - d0;
+  const int d = blockIdx.x * MC_BLOCK + threadIdx.x;
+  int dn = 0, acc = 0, tie = 0, site = -1;
+  double sde = 0.0;
+  if (d < D) {
+    const int g = d0 + d;
+    const int base = a.dom_start[g];
+    const int size = a.dom_start[g + 1] - base;
+    if (size > 0) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL), p.key);
+      site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
+      const uint64_t u53 = top53(w.z, w.w);
+      const int t = a.types[(long long)r * a.N + site];
+      const double sg = t ? -1.0 : 1.0;
+      const double de = delta_e<SHELL, REEMBED>(a, r, site, a.err);
+      if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
+      const double X = p.beta * fma(sg, p.dmu0, de);
+      if (metropolis(X, u53, &tie)) {
+        acc = 1;
+        dn = t ? -1 : 1;
+        sde = de;
+      }
+    }
+  }
+  // compact the accepted sites: warp ballot, one reservation per warp
+  const unsigned m = __ballot_sync(0xffffffffu, acc);
+  int slot_base = 0;
+  const int lane = threadIdx.x & 31;
+  if (m) {
+    if (lane == 0) slot_base = atomicAdd(&a.acc[r].nacc, __popc(m));
+    slot_base = __shfl_sync(0xffffffffu, slot_base, 0);
+    if (acc) a.acc_list[(long long)r * a.dmax + slot_base + __popc(m & ((1u << lane) - 1u))] = site;
+  }
+  if (tie) atomicAdd(&a.acc[r].ties, 1);
+  int dummy = 0;
+  block_reduce3<MC_BLOCK>(dn, dummy, sde);
+  if (threadIdx.x == 0 && (dn != 0 || sde != 0.0)) {
+    atomicAdd(&a.acc[r].dn, dn);
+    atomicAdd(&a.acc[r].sum_de, sde);
+  }
+}
+
+// flip site i of replica r and scatter its density change to its neighbours
+// (no two sites of one colour share a neighbour: they are > 2 r_c apart)
+template <bool SHELL, bool REEMBED>
+__device__ void commit_site(const McArgs& a, int r, int i, unsigned* err) {
+  uint8_t* ty = a.types + (long long)r * a.N;
+  const int t = ty[i];
+  ty[i] = (uint8_t)(1 - t);
+  if (a.vel[0] && r == 0) {
+    const double f = sqrt(a.mass[t] / a.mass[1 - t]);
+    a.vel[0][i] *= f;
+    a.vel[1][i] *= f;
+    a.vel[2][i] *= f;
+  }
+  if constexpr (REEMBED) {
+    const int* row = a.nbr + (long long)i * a.K;
+    double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
+    if constexpr (SHELL) {
+      const int S = a.n_shells;
+      int k = 0;
+      for (int s = 0; s < S; ++s) {
+        const double dfs = a.shell_tab[1 + S + s];
+        const double drho = t ? -dfs : dfs;
+        for (; k < a.shell_end[s]; ++k) rho[row[k]] += drho;
+      }
+    } else {
+      const int cnt = a.nbr_cnt[i];
+      const int tp = 1 - t;
+      for (int k = 0; k < cnt; ++k) {
+        const int j = row[k];
+        const double dx = min_image(a.x[j] - a.x[i], a.box[0]);
+        const double dy = min_image(a.y[j] - a.y[i], a.box[1]);
+        const double dz = min_image(a.z[j] - a.z[i], a.box[2]);
+        const double rr = sqrt(dx * dx + dy * dy + dz * dz);
+        if (rr >= a.rc) continue;
+        double tt;
+        const int jj = spline_locate(a.tab.sp[3], rr, tt, err);
+        rho[j] += spline_val_at(a.tab.sp[3 + tp], jj, tt) - spline_val_at(a.tab.sp[3 + t], jj, tt);
+      }
+    }
+  }
+}
+
+template <bool SHELL, bool REEMBED>
+__global__ void __launch_bounds__(MC_BLOCK) k_commit(McArgs a) {
+  const int r = blockIdx.y;
+  StepAcc* A = &a.acc[r];
+  RepState* S = &a.rs[r];
+  const RepParams p = a.rp[r];
+  const int nacc = *(volatile int*)&A->nacc;
+  const int dn = *(volatile int*)&A->dn;
+  const long long n = S->n;
+  const long long step = S->step;
+  uint64_t ug53;
+  const int c = draw_colour(a, p.key, step, &ug53);
+  bool G = false;
+  int tie = 0;
+  if (nacc > 0) {
+    const double Y = p.beta * p.kappa_p * (double)dn * ((double)dn + 2.0 * ((double)n - p.n0));
+    G = metropolis(Y, ug53, &tie);
+  }
+  if (G) {
+    for (int q = blockIdx.x * MC_BLOCK + threadIdx.x; q < nacc; q += gridDim.x * MC_BLOCK)
+      commit_site<SHELL, REEMBED>(a, r, a.acc_list[(long long)r * a.dmax + q], a.err);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned ticket = atomicAdd(&A->done, 1u);
+    if (ticket == gridDim.x - 1) {
+      __threadfence();
+      const int D = a.col_start[c + 1] - a.col_start[c];
+      S->trials += D;
+      S->local_acc += nacc;
+      S->near_ties += *(volatile int*)&A->ties + tie;
+      long long nn = n;
+      if (nacc > 0) {
+        S->global_trials += 1;
+        if (G) {
+          S->global_acc += 1;
+          S->flips += nacc;
+          nn = n + dn;
+          S->n = nn;
+          S->energy += *(volatile double*)&A->sum_de;
+        }
+      }
+      const double cc = (double)nn / (double)a.N;
+      S->sum_c += cc;
+      S->sum_c2 += cc * cc;
+      S->steps += 1;
+      S->step = step + 1;
+      A->dn = 0;
+      A->nacc = 0;
+      A->sum_de = 0.0;
+      A->ties = 0;
+      __threadfence();
+      A->done = 0u;
+    }
+  }
+}
+
+// dE of a list of sites with the sweep's own device function
+template <bool SHELL, bool REEMBED>
+__global__ void k_delta_e_list(McArgs a, int r, const int* sites, int n, double* out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = delta_e<SHELL, REEMBED>(a, r, sites[q], a.err);
+}
+
+// ----------------------------------------------------------------- launch
+template <bool SHELL, bool REEMBED>
+static void launch_step_t(const McArgs& a, cudaStream_t st, int phase) {
+  const int cb = (a.dmax + MC_BLOCK - 1) / MC_BLOCK;
+  if (phase != 2) k_propose<SHELL, REEMBED><<<dim3(cb, a.R), MC_BLOCK, 0, st>>>(a);
+  if (phase != 1) k_commit<SHELL, REEMBED><<<dim3(cb < 8 ? cb : 8, a.R), MC_BLOCK, 0, st>>>(a);
+}
+
+void launch_colour_step(const McArgs& a, bool shell, bool reembed, cudaStream_t st, int phase) {
+  if (shell) {
+    if (reembed) launch_step_t<true, true>(a, st, phase);
+    else launch_step_t<true, false>(a, st, phase);
+  } else {
+    if (reembed) launch_step_t<false, true>(a, st, phase);
+    else launch_step_t<false, false>(a, st, phase);
+  }
+}
+
+void launch_delta_e_list(const McArgs& a, bool shell, bool reembed, int r, const int* sites, int n,
+                         double* out, cudaStream_t st) {
+  const int b = 128, g = (n + b - 1) / b;
+  if (g == 0) return;
+  if (shell) {
+    if (reembed) k_delta_e_list<true, true><<<g, b, 0, st>>>(a, r, sites, n, out);
+    else k_delta_e_list<true, false><<<g, b, 0, st>>>(a, r, sites, n, out);
+  } else {
+    if (reembed) k_delta_e_list<false, true><<<g, b, 0, st>>>(a, r, sites, n, out);
+    else k_delta_e_list<false, false><<<g, b, 0, st>>>(a, r, sites, n, out);
+  }
+}
+
+}  // namespace vcsgc

@@ -1,0 +1,182 @@
+// kernels_md.cu -- EAM forces and BAOAB Langevin velocity Verlet, the MD half
+// of the hybrid MC/MD scheme (Sec. IV A of Sadigh et al.).
+//   rho pass:   rho_i = sum_j f_{t_j}(r_ij), F'(rho_i), F_B(rho_i) - F_A(rho_i)
+//   force pass: F_i = sum_j [phi'_{t_i t_j} + F'_i f'_{t_j} + F'_j f'_{t_i}](r_ij) (x_j - x_i)/r_ij
+//   B A O A B:  half kick, half drift, Ornstein-Uhlenbeck velocity update with
+//               Philox normals, half drift, (forces), half kick.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vcsgc {
+
+__device__ __forceinline__ double mimg(double d, double L) { return d - L * rint(d / L); }
+
+__global__ void k_md_rho(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int* row = m.nbr + i * m.K;
+  const int cnt = m.nbr_cnt[i];
+  const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  double rho = 0.0;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = row[k];
+    const double dx = mimg(m.x[j] - xi, m.box[0]);
+    const double dy = mimg(m.y[j] - yi, m.box[1]);
+    const double dz = mimg(m.z[j] - zi, m.box[2]);
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    if (r >= m.rc) continue;
+    rho += spline_val(m.tab.sp[3 + m.types[j]], r, m.err);
+  }
+  m.rho[i] = rho;
+  double t;
+  const int ti = m.types[i];
+  const int q = spline_locate(m.tab.sp[5 + ti], rho, t, m.err);
+  m.dFp[i] = spline_der_at(m.tab.sp[5 + ti], q, t);
+  m.dF[i] = spline_val_at(m.tab.sp[6], q, t) - spline_val_at(m.tab.sp[5], q, t);
+}
+
+__global__ void k_md_force(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int* row = m.nbr + i * m.K;
+  const int cnt = m.nbr_cnt[i];
+  const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  const int ti = m.types[i];
+  const double Fi = m.dFp[i];
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = row[k];
+    const double dx = mimg(m.x[j] - xi, m.box[0]);
+    const double dy = mimg(m.y[j] - yi, m.box[1]);
+    const double dz = mimg(m.z[j] - zi, m.box[2]);
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    if (r >= m.rc) continue;
+    const int tj = m.types[j];
+    double t;
+    const int q = spline_locate(m.tab.sp[0], r, t, m.err);
+    const double g = spline_der_at(m.tab.sp[ti + tj], q, t) + Fi * spline_der_at(m.tab.sp[3 + tj], q, t) +
+                     m.dFp[j] * spline_der_at(m.tab.sp[3 + ti], q, t);
+    const double gr = g / r;
+    fx = fma(gr, dx, fx);
+    fy = fma(gr, dy, fy);
+    fz = fma(gr, dz, fz);
+  }
+  if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(m.err, ERRF_NONFINITE);
+  m.fx[i] = fx;
+  m.fy[i] = fy;
+  m.fz[i] = fz;
+}
+
+__device__ __forceinline__ double wrap_box(double v, double L) {
+  double w = v - L * floor(v / L);
+  if (w >= L) w -= L;
+  if (w < 0.0) w = 0.0;
+  return w;
+}
+
+// Box-Muller: two standard normals from two uniforms
+__device__ __forceinline__ void normals(uint4 w, double& z0, double& z1) {
+  const double u1 = (double)top53(w.x, w.y) * 0x1p-53;
+  const double u2 = (double)top53(w.z, w.w) * 0x1p-53;
+  const double rr = sqrt(-2.0 * log(1.0 - u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  z0 = rr * c;
+  z1 = rr * s;
+}
+
+__global__ void k_md_first_half(MdArgs m, long long step) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int ti = m.types[i];
+  const double im = FTM / m.mass[ti];
+  const double h = 0.5 * m.dt;
+  double vx = m.vx[i] + h * m.fx[i] * im;
+  double vy = m.vy[i] + h * m.fy[i] * im;
+  double vz = m.vz[i] + h * m.fz[i] * im;
+  double x = m.x[i] + h * vx, y = m.y[i] + h * vy, z = m.z[i] + h * vz;
+  if (m.c2 > 0.0) {
+    const double sig = m.c2 * sqrt(m.kT * im);
+    const uint4 c0 = make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)i, TAG_NOISE0);
+    const uint4 c1 = make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)i, TAG_NOISE1);
+    double z0, z1, z2, z3;
+    normals(philox4x32_10(c0, m.key), z0, z1);
+    normals(philox4x32_10(c1, m.key), z2, z3);
+    vx = m.c1 * vx + sig * z0;
+    vy = m.c1 * vy + sig * z1;
+    vz = m.c1 * vz + sig * z2;
+  }
+  x = wrap_box(x + h * vx, m.box[0]);
+  y = wrap_box(y + h * vy, m.box[1]);
+  z = wrap_box(z + h * vz, m.box[2]);
+  m.vx[i] = vx;
+  m.vy[i] = vy;
+  m.vz[i] = vz;
+  m.x[i] = x;
+  m.y[i] = y;
+  m.z[i] = z;
+  const double dx = mimg(x - m.x0[i], m.box[0]);
+  const double dy = mimg(y - m.y0[i], m.box[1]);
+  const double dz = mimg(z - m.z0[i], m.box[2]);
+  const double d2 = dx * dx + dy * dy + dz * dz;
+  // non-negative doubles order like their bit patterns
+  atomicMax(m.max_disp2_bits, (unsigned long long)__double_as_longlong(d2));
+}
+
+__global__ void k_md_second_half(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const double im = FTM / m.mass[m.types[i]];
+  const double h = 0.5 * m.dt;
+  m.vx[i] += h * m.fx[i] * im;
+  m.vy[i] += h * m.fy[i] * im;
+  m.vz[i] += h * m.fz[i] * im;
+}
+
+__global__ void k_md_snapshot(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *m.max_disp2_bits = 0ull;
+  if (i >= m.N) return;
+  m.x0[i] = m.x[i];
+  m.y0[i] = m.y[i];
+  m.z0[i] = m.z[i];
+}
+
+constexpr int KE_BLOCK = 256;
+int kinetic_blocks(long long N) { return (int)((N + KE_BLOCK - 1) / KE_BLOCK); }
+
+__global__ void __launch_bounds__(KE_BLOCK) k_kinetic(MdArgs m, double* part) {
+  const long long i = (long long)blockIdx.x * KE_BLOCK + threadIdx.x;
+  double e = 0.0;
+  if (i < m.N) {
+    const double v2 = m.vx[i] * m.vx[i] + m.vy[i] * m.vy[i] + m.vz[i] * m.vz[i];
+    e = 0.5 * m.mass[m.types[i]] / FTM * v2;
+  }
+  __shared__ double sh[KE_BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < KE_BLOCK / 32; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+static unsigned grid_of(long long N) { return (unsigned)((N + 127) / 128); }
+
+void launch_md_rho(const MdArgs& m, cudaStream_t st) { k_md_rho<<<grid_of(m.N), 128, 0, st>>>(m); }
+void launch_md_force(const MdArgs& m, cudaStream_t st) { k_md_force<<<grid_of(m.N), 128, 0, st>>>(m); }
+void launch_md_first_half(const MdArgs& m, long long step, cudaStream_t st) {
+  k_md_first_half<<<grid_of(m.N), 128, 0, st>>>(m, step);
+}
+void launch_md_second_half(const MdArgs& m, cudaStream_t st) {
+  k_md_second_half<<<grid_of(m.N), 128, 0, st>>>(m);
+}
+void launch_md_snapshot(const MdArgs& m, cudaStream_t st) { k_md_snapshot<<<grid_of(m.N), 128, 0, st>>>(m); }
+void launch_kinetic(const MdArgs& m, double* part, cudaStream_t st) {
+  k_kinetic<<<kinetic_blocks(m.N), KE_BLOCK, 0, st>>>(m, part);
+}
+
+}  // namespace vcsgc

@@ -1,0 +1,298 @@
+// kernels_nbr.cu -- table set-up, neighbour lists, electron density and
+// total energy (EAM, Daw-Baskes form; the short-range many-body potential of
+// Sec. III A of Sadigh et al.).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vcsgc {
+
+// ------------------------------------------------------------ splines
+// Hermite data (y_j, m_j) on [x_j, x_j + h] -> power-form cubic in t:
+//   c0 = y0, c1 = h m0, c2 = 3 (y1 - y0) - h (2 m0 + m1), c3 = 2 (y0 - y1) + h (m0 + m1).
+// Missing derivatives: central differences, one-sided at the ends.
+__global__ void k_spline_coeffs(const double* y, const double* m, int n, double h, Cubic* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n - 1) return;
+  auto slope = [&](int q) -> double {
+    if (m) return m[q];
+    if (q == 0) return (y[1] - y[0]) / h;
+    if (q == n - 1) return (y[n - 1] - y[n - 2]) / h;
+    return (y[q + 1] - y[q - 1]) / (2.0 * h);
+  };
+  const double y0 = y[j], y1 = y[j + 1];
+  const double m0 = h * slope(j), m1 = h * slope(j + 1);
+  out[j] = Cubic{y0, m0, 3.0 * (y1 - y0) - 2.0 * m0 - m1, 2.0 * (y0 - y1) + m0 + m1};
+}
+
+void launch_spline_coeffs(const double* y, const double* m, int n, double h, Cubic* out,
+                          cudaStream_t st) {
+  k_spline_coeffs<<<(n + 255) / 256, 256, 0, st>>>(y, m, n, h, out);
+}
+
+// ------------------------------------------------------- shell tables
+// Rigid lattice: the pair part of dE(A->B) is
+//   sum_s [ (z_s - b_s) (phi_BA - phi_AA)(r_s) + b_s (phi_BB - phi_AB)(r_s) ]
+//   = C_A + sum_s b_s G_A[s],
+// C_A = sum_s z_s (phi_AB - phi_AA)(r_s), G_A[s] = (phi_BB - 2 phi_AB + phi_AA)(r_s).
+__global__ void k_shell_tables(Tables tab, const int* h2, const int* z, int S, double a,
+                               double* out, unsigned* err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double C = 0.0;
+  for (int s = 0; s < S; ++s) {
+    const double r = 0.5 * a * sqrt((double)h2[s]);
+    const double pAA = spline_val(tab.sp[0], r, err);
+    const double pAB = spline_val(tab.sp[1], r, err);
+    const double pBB = spline_val(tab.sp[2], r, err);
+    C += (double)z[s] * (pAB - pAA);
+    out[1 + s] = (pBB - pAB) - (pAB - pAA);
+    out[1 + S + s] = spline_val(tab.sp[4], r, err) - spline_val(tab.sp[3], r, err);
+    out[1 + 2 * S + s] = r;
+  }
+  out[0] = C;
+}
+
+void launch_shell_tables(Tables tab, const int* h2, const int* z, int S, double a, double* out,
+                         unsigned* err, cudaStream_t st) {
+  k_shell_tables<<<1, 32, 0, st>>>(tab, h2, z, S, a, out, err);
+}
+
+// --------------------------------------------------- lattice neighbours
+// Site (cx, cy, cz, b) has half-lattice coordinates H = 2 c + b; the
+// neighbour at offset h has coordinates H + h (periodic in 2 n), basis
+// (H + h) mod 2 and cell (H + h) / 2.
+__global__ void k_lattice_nbr(int nx, int ny, int nz, const int3* hoff, int K, int* nbr, int* cnt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long N = 2LL * nx * ny * nz;
+  if (i >= N) return;
+  const int b = (int)(i & 1);
+  const long long cell = i >> 1;
+  const int cx = (int)(cell % nx), cy = (int)((cell / nx) % ny), cz = (int)(cell / ((long long)nx * ny));
+  const int X = 2 * cx + b, Y = 2 * cy + b, Z = 2 * cz + b;
+  for (int k = 0; k < K; ++k) {
+    const int3 h = hoff[k];
+    int hx = (X + h.x) % (2 * nx); if (hx < 0) hx += 2 * nx;
+    int hy = (Y + h.y) % (2 * ny); if (hy < 0) hy += 2 * ny;
+    int hz = (Z + h.z) % (2 * nz); if (hz < 0) hz += 2 * nz;
+    const int bb = hx & 1;
+    const long long j = (((long long)(hz >> 1) * ny + (hy >> 1)) * nx + (hx >> 1)) * 2 + bb;
+    nbr[i * K + k] = (int)j;
+  }
+  cnt[i] = K;
+}
+
+void launch_lattice_neighbours(int nx, int ny, int nz, const int3* hoff, int K, int* nbr, int* cnt,
+                               cudaStream_t st) {
+  const long long N = 2LL * nx * ny * nz;
+  k_lattice_nbr<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(nx, ny, nz, hoff, K, nbr, cnt);
+}
+
+// ------------------------------------------------------ cell neighbours
+__device__ __forceinline__ int cell_index(double v, double L, int n) {
+  int c = (int)floor(v / L * n);
+  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+__global__ void k_cell_assign(long long N, const double* x, const double* y, const double* z,
+                              double bx, double by, double bz, int nx, int ny, int nz,
+                              int* cell_of, int* count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int c = (cell_index(z[i], bz, nz) * ny + cell_index(y[i], by, ny)) * nx + cell_index(x[i], bx, nx);
+  cell_of[i] = c;
+  atomicAdd(&count[c], 1);
+}
+
+// exclusive scan of count[0..n) into start[0..n], one block
+__global__ void k_scan(const int* count, int n, int* start) {
+  __shared__ int carry;
+  __shared__ int warp_sum[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < n ? count[i] : 0;
+    int s = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int q = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += q;
+    }
+    if (lane == 31) warp_sum[w] = s;
+    __syncthreads();
+    if (w == 0) {
+      int ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int q = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += q;
+      }
+      warp_sum[lane] = ws;
+    }
+    __syncthreads();
+    const int prefix = carry + (w ? warp_sum[w - 1] : 0) + s - v;
+    if (i < n) start[i] = prefix;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = prefix + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) start[n] = carry;
+}
+
+__global__ void k_cell_scatter(long long N, const int* cell_of, const int* start, int* cursor, int* sorted) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int c = cell_of[i];
+  sorted[start[c] + atomicAdd(&cursor[c], 1)] = (int)i;
+}
+
+// order each cell's members by index so the neighbour order is reproducible
+__global__ void k_cell_sort(int ncell, const int* start, int* sorted) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int b = start[c], e = start[c + 1];
+  for (int p = b + 1; p < e; ++p) {
+    const int v = sorted[p];
+    int q = p - 1;
+    while (q >= b && sorted[q] > v) {
+      sorted[q + 1] = sorted[q];
+      --q;
+    }
+    sorted[q + 1] = v;
+  }
+}
+
+__global__ void k_cell_nbr(long long N, const double* x, const double* y, const double* z, double bx,
+                           double by, double bz, int nx, int ny, int nz, const int* cell_of,
+                           const int* start, const int* sorted, double rl2, int K, int* nbr, int* cnt,
+                           unsigned* err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int c = cell_of[i];
+  const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+  const double xi = x[i], yi = y[i], zi = z[i];
+  int m = 0;
+  for (int oz = -1; oz <= 1; ++oz)
+    for (int oy = -1; oy <= 1; ++oy)
+      for (int ox = -1; ox <= 1; ++ox) {
+        const int qx = (cx + ox + nx) % nx, qy = (cy + oy + ny) % ny, qz = (cz + oz + nz) % nz;
+        const int q = (qz * ny + qy) * nx + qx;
+        for (int p = start[q]; p < start[q + 1]; ++p) {
+          const int j = sorted[p];
+          if (j == i) continue;
+          double dx = x[j] - xi, dy = y[j] - yi, dz = z[j] - zi;
+          dx -= bx * rint(dx / bx);
+          dy -= by * rint(dy / by);
+          dz -= bz * rint(dz / bz);
+          if (dx * dx + dy * dy + dz * dz < rl2) {
+            if (m < K) nbr[i * K + m] = j;
+            ++m;
+          }
+        }
+      }
+  if (m > K) atomicOr(err, ERRF_OVERFLOW);
+  const int mm = m < K ? m : K;
+  for (int k = mm; k < K; ++k) nbr[i * K + k] = -1;
+  cnt[i] = mm;
+}
+
+void launch_cell_neighbours(long long N, const double* x, const double* y, const double* z,
+                            const double box[3], double rl, CellList cl, int K, int* nbr, int* cnt,
+                            unsigned* err, cudaStream_t st) {
+  const int ncell = cl.nc[0] * cl.nc[1] * cl.nc[2];
+  const unsigned g = (unsigned)((N + 127) / 128);
+  cudaMemsetAsync(cl.cell_count, 0, sizeof(int) * ncell, st);
+  cudaMemsetAsync(cl.cell_cursor, 0, sizeof(int) * ncell, st);
+  k_cell_assign<<<g, 128, 0, st>>>(N, x, y, z, box[0], box[1], box[2], cl.nc[0], cl.nc[1], cl.nc[2],
+                                   cl.cell_of, cl.cell_count);
+  k_scan<<<1, 1024, 0, st>>>(cl.cell_count, ncell, cl.cell_start);
+  k_cell_scatter<<<g, 128, 0, st>>>(N, cl.cell_of, cl.cell_start, cl.cell_cursor, cl.sorted);
+  k_cell_sort<<<(ncell + 127) / 128, 128, 0, st>>>(ncell, cl.cell_start, cl.sorted);
+  k_cell_nbr<<<g, 128, 0, st>>>(N, x, y, z, box[0], box[1], box[2], cl.nc[0], cl.nc[1], cl.nc[2],
+                                cl.cell_of, cl.cell_start, cl.sorted, rl * rl, K, nbr, cnt, err);
+}
+
+// ------------------------------------------------------ density, energy
+__device__ __forceinline__ double pair_r(const McArgs& a, bool shell, int i, int k, int j, int s) {
+  if (shell) return a.shell_tab[1 + 2 * a.n_shells + s];
+  double dx = a.x[j] - a.x[i], dy = a.y[j] - a.y[i], dz = a.z[j] - a.z[i];
+  dx -= a.box[0] * rint(dx / a.box[0]);
+  dy -= a.box[1] * rint(dy / a.box[1]);
+  dz -= a.box[2] * rint(dz / a.box[2]);
+  return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+// rho_i = sum_k f_{t_k}(r_ik); dF_i = F_B(rho_i) - F_A(rho_i)
+template <bool SHELL>
+__global__ void k_rho(McArgs a, int r, double* dF) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const int* row = a.nbr + i * a.K;
+  const int cnt = a.nbr_cnt[i];
+  double rho = 0.0;
+  int s = 0;
+  for (int k = 0; k < cnt; ++k) {
+    if (SHELL) while (k >= a.shell_end[s]) ++s;
+    const int j = row[k];
+    const double rr = pair_r(a, SHELL, (int)i, k, j, s);
+    if (rr >= a.rc) continue;
+    rho += spline_val(a.tab.sp[3 + ty[j]], rr, a.err);
+  }
+  double* out = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
+  out[i] = rho;
+  if (dF) dF[i] = spline_val(a.tab.sp[6], rho, a.err) - spline_val(a.tab.sp[5], rho, a.err);
+}
+
+void launch_rho(const McArgs& a, bool shell, int r, cudaStream_t st) {
+  const unsigned g = (unsigned)((a.N + 127) / 128);
+  double* dF = const_cast<double*>(a.dF);
+  if (shell) k_rho<true><<<g, 128, 0, st>>>(a, r, dF);
+  else k_rho<false><<<g, 128, 0, st>>>(a, r, dF);
+}
+
+constexpr int E_BLOCK = 256;
+int energy_blocks(long long N) { return (int)((N + E_BLOCK - 1) / E_BLOCK); }
+
+// e_i = 1/2 sum_k phi_{t_i t_k}(r_ik) + F_{t_i}(rho_i), block partial sums
+template <bool SHELL>
+__global__ void __launch_bounds__(E_BLOCK) k_energy(McArgs a, int r, double* part) {
+  const long long i = (long long)blockIdx.x * E_BLOCK + threadIdx.x;
+  double e = 0.0;
+  if (i < a.N) {
+    const uint8_t* ty = a.types + (long long)r * a.N;
+    const int* row = a.nbr + i * a.K;
+    const int cnt = a.nbr_cnt[i];
+    const int ti = ty[i];
+    double rho = 0.0, ph = 0.0;
+    int s = 0;
+    for (int k = 0; k < cnt; ++k) {
+      if (SHELL) while (k >= a.shell_end[s]) ++s;
+      const int j = row[k];
+      const double rr = pair_r(a, SHELL, (int)i, k, j, s);
+      if (rr >= a.rc) continue;
+      const int tj = ty[j];
+      ph += spline_val(a.tab.sp[ti + tj], rr, a.err);
+      rho += spline_val(a.tab.sp[3 + tj], rr, a.err);
+    }
+    e = 0.5 * ph + spline_val(a.tab.sp[5 + ti], rho, a.err);
+  }
+  __shared__ double sh[E_BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < E_BLOCK / 32; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+void launch_energy(const McArgs& a, bool shell, int r, double* part, cudaStream_t st) {
+  const int g = energy_blocks(a.N);
+  if (shell) k_energy<true><<<g, E_BLOCK, 0, st>>>(a, r, part);
+  else k_energy<false><<<g, E_BLOCK, 0, st>>>(a, r, part);
+}
+
+}  // namespace vcsgc

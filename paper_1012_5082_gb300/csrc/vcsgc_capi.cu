@@ -1,0 +1,1063 @@
+// vcsgc_capi.cu -- host side of the C ABI declared in include/vcsgc.h:
+// argument checks, device allocation, table and schedule set-up, the
+// graph-captured colour-step loop, the MD driver and the observables.
+// Every numerical step of the method runs in the kernels of kernels_*.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/vcsgc.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace vcsgc;
+
+namespace {
+
+std::string g_init_error;
+
+struct Ctx {
+  std::string err;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int kind = 0;
+  int nx = 0, ny = 0, nz = 0;
+  double a = 0;
+  long long N = 0;
+  double box[3] = {0, 0, 0};
+  int R = 1;
+  double rc = 0, skin = 0, rl = 0;
+  bool shell = false, reembed = false;
+  int sched_kind = 0;
+  int sched[6] = {0, 0, 0, 0, 0, 0};
+  long long steps_per_sweep = 1;
+  // device memory
+  std::vector<void*> allocs;
+  uint8_t* types = nullptr;
+  double* rho = nullptr;
+  double* dF = nullptr;
+  double* dFp = nullptr;
+  double *x = nullptr, *y = nullptr, *z = nullptr;
+  double *vx = nullptr, *vy = nullptr, *vz = nullptr;
+  double *fx = nullptr, *fy = nullptr, *fz = nullptr;
+  double *x0 = nullptr, *y0 = nullptr, *z0 = nullptr;
+  unsigned long long* max_disp2 = nullptr;
+  int* nbr = nullptr;
+  int* nbr_cnt = nullptr;
+  int K = 0;
+  Cubic* coef[7] = {};
+  double* shell_tab = nullptr;
+  int* col_start = nullptr;
+  int* dom_start = nullptr;
+  int* dom_sites = nullptr;
+  int n_colours = 0, dmax = 0;
+  long long n_domains = 0;
+  RepParams* rp = nullptr;
+  RepState* rs = nullptr;
+  StepAcc* acc = nullptr;
+  int* acc_list = nullptr;
+  unsigned* derr = nullptr;
+  double* part = nullptr;
+  int part_n = 0;
+  int* sites_buf = nullptr;
+  double* de_buf = nullptr;
+  int sites_cap = 0;
+  CellList cl{};
+  std::vector<RepParams> h_rp;
+  // md
+  bool have_v = false;
+  long long md_step = 0;
+  double mass[2] = {55.845, 63.546};
+  double dt = 2.0, gamma = 0.01, T_md = 0.0;
+  uint64_t md_seed = 0;
+  bool forces_valid = false;
+  // graph
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  McArgs mc{};
+  MdArgs md{};
+};
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      return VCSGC_ERR_CUDA;                                                           \
+    }                                                                                  \
+  } while (0)
+
+int fail(Ctx* c, int code, const std::string& msg) {
+  c->err = msg;
+  return code;
+}
+
+template <typename T>
+int dalloc(Ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, VCSGC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return VCSGC_OK;
+}
+
+#define TRY(expr)             \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != VCSGC_OK) return rc_; \
+  } while (0)
+
+int check_device_error(Ctx* c) {
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (!e) return VCSGC_OK;
+  CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (e & ERRF_TIMEOUT) return fail(c, VCSGC_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (e & ERRF_OVERFLOW) return fail(c, VCSGC_ERR_OVERFLOW, "neighbour list capacity exceeded");
+  if (e & ERRF_TABLE) return fail(c, VCSGC_ERR_TABLE_RANGE, "r or rho outside the EAM table grid");
+  return fail(c, VCSGC_ERR_NONFINITE, "non-finite energy difference or force");
+}
+
+void fill_args(Ctx* c) {
+  McArgs& a = c->mc;
+  a.N = c->N;
+  a.R = c->R;
+  a.K = c->K;
+  a.nbr = c->nbr;
+  a.nbr_cnt = c->nbr_cnt;
+  a.types = c->types;
+  a.rho = c->rho;
+  a.rho_per_rep = c->reembed ? 1 : 0;
+  a.dF = c->dF;
+  a.vel[0] = c->have_v ? c->vx : nullptr;
+  a.vel[1] = c->have_v ? c->vy : nullptr;
+  a.vel[2] = c->have_v ? c->vz : nullptr;
+  a.mass[0] = c->mass[0];
+  a.mass[1] = c->mass[1];
+  a.shell_tab = c->shell_tab;
+  a.x = c->x;
+  a.y = c->y;
+  a.z = c->z;
+  for (int q = 0; q < 3; ++q) a.box[q] = c->box[q];
+  a.rc = c->rc;
+  a.n_colours = c->n_colours;
+  a.col_start = c->col_start;
+  a.dom_start = c->dom_start;
+  a.dom_sites = c->dom_sites;
+  a.dmax = c->dmax;
+  a.rp = c->rp;
+  a.rs = c->rs;
+  a.acc = c->acc;
+  a.acc_list = c->acc_list;
+  a.err = c->derr;
+
+  MdArgs& m = c->md;
+  m.N = c->N;
+  m.K = c->K;
+  m.nbr = c->nbr;
+  m.nbr_cnt = c->nbr_cnt;
+  m.types = c->types;
+  m.x = c->x; m.y = c->y; m.z = c->z;
+  m.vx = c->vx; m.vy = c->vy; m.vz = c->vz;
+  m.fx = c->fx; m.fy = c->fy; m.fz = c->fz;
+  m.rho = c->rho;
+  m.dFp = c->dFp;
+  m.dF = c->dF;
+  m.x0 = c->x0; m.y0 = c->y0; m.z0 = c->z0;
+  for (int q = 0; q < 3; ++q) m.box[q] = c->box[q];
+  m.rc = c->rc;
+  m.mass[0] = c->mass[0];
+  m.mass[1] = c->mass[1];
+  m.dt = c->dt;
+  m.c1 = std::exp(-c->gamma * c->dt);
+  m.c2 = std::sqrt(std::max(0.0, 1.0 - m.c1 * m.c1));
+  m.kT = KB_EV * c->T_md;
+  m.key = make_uint2((uint32_t)c->md_seed, (uint32_t)(c->md_seed >> 32));
+  m.tab = c->mc.tab;
+  m.err = c->derr;
+  m.max_disp2_bits = c->max_disp2;
+}
+
+void drop_graph(Ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_steps = 0;
+}
+
+// ----------------------------------------------------------- neighbours
+int build_cell_list(Ctx* c) {
+  for (int q = 0; q < 3; ++q) c->cl.nc[q] = (int)std::floor(c->box[q] / c->rl);
+  const int ncell = c->cl.nc[0] * c->cl.nc[1] * c->cl.nc[2];
+  if (!c->cl.cell_of) {
+    TRY(dalloc(c, &c->cl.cell_of, c->N));
+    TRY(dalloc(c, &c->cl.cell_count, ncell));
+    TRY(dalloc(c, &c->cl.cell_start, ncell + 1));
+    TRY(dalloc(c, &c->cl.cell_cursor, ncell));
+    TRY(dalloc(c, &c->cl.sorted, c->N));
+  }
+  for (int attempt = 0; attempt < 6; ++attempt) {
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    launch_cell_neighbours(c->N, c->x, c->y, c->z, c->box, c->rl, c->cl, c->K, c->nbr, c->nbr_cnt,
+                           c->derr, c->st);
+    CK(cudaGetLastError());
+    unsigned e = 0;
+    CK(cudaMemcpyAsync(&e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (!(e & ERRF_OVERFLOW)) return VCSGC_OK;
+    // grow the rows and rebuild
+    const int K2 = ((c->K * 3 / 2) + 7) / 8 * 8;
+    int* nb = nullptr;
+    TRY(dalloc(c, &nb, (size_t)c->N * K2));
+    c->nbr = nb;
+    c->K = K2;
+    fill_args(c);
+    drop_graph(c);
+  }
+  return fail(c, VCSGC_ERR_OVERFLOW, "neighbour rows kept overflowing");
+}
+
+// ------------------------------------------------------------- schedule
+// Host tables of the colour schedule: col_start[n_colours+1] indexes
+// domains, dom_start[n_domains+1] indexes dom_sites.
+struct Sched {
+  std::vector<int> col, dom, sites;
+};
+
+double cell_gap_distance(double a, int gap_cells) {
+  // closest BCC pair across gap_cells empty cells: a corner site and a
+  // body-centre site, a*sqrt((gap + 1/2)^2 + 1/2)
+  const double g = gap_cells + 0.5;
+  return a * std::sqrt(g * g + 0.5);
+}
+
+int build_schedule(Ctx* c, const std::vector<double>& hx, const std::vector<double>& hy,
+                   const std::vector<double>& hz, Sched& S) {
+  const double two_rc = 2.0 * c->rc;
+  const int* p = c->sched;
+  if (c->sched_kind == VCSGC_SCHED_BLOCKS || c->sched_kind == VCSGC_SCHED_SUBLATTICE) {
+    if (c->kind != 0) return fail(c, VCSGC_ERR_INVALID_ARG, "BLOCKS and SUBLATTICE schedules need a rigid lattice");
+  }
+  if (c->sched_kind == VCSGC_SCHED_BLOCKS) {
+    const int bx = p[0], by = p[1], bz = p[2], px = p[3], py = p[4], pz = p[5];
+    if (bx < 1 || by < 1 || bz < 1 || px < 1 || py < 1 || pz < 1 || c->nx % bx || c->ny % by || c->nz % bz)
+      return fail(c, VCSGC_ERR_SCHEDULE, "block size does not divide the lattice");
+    const int nbx = c->nx / bx, nby = c->ny / by, nbz = c->nz / bz;
+    if (nbx % px || nby % py || nbz % pz) return fail(c, VCSGC_ERR_SCHEDULE, "colour period does not divide the blocks");
+    const int nb[3] = {nbx, nby, nbz}, pp[3] = {px, py, pz}, bb[3] = {bx, by, bz};
+    for (int q = 0; q < 3; ++q)
+      if (nb[q] > pp[q] && cell_gap_distance(c->a, (pp[q] - 1) * bb[q]) <= two_rc)
+        return fail(c, VCSGC_ERR_SCHEDULE, "same-colour blocks closer than 2 r_c");
+    const int ncol = px * py * pz;
+    S.col.assign(ncol + 1, 0);
+    for (int col = 0; col < ncol; ++col) {
+      S.col[col] = (int)S.dom.size();
+      for (int ibz = 0; ibz < nbz; ++ibz)
+        for (int iby = 0; iby < nby; ++iby)
+          for (int ibx = 0; ibx < nbx; ++ibx) {
+            if (((ibz % pz) * py + (iby % py)) * px + (ibx % px) != col) continue;
+            S.dom.push_back((int)S.sites.size());
+            for (int lz = 0; lz < bz; ++lz)
+              for (int ly = 0; ly < by; ++ly)
+                for (int lx = 0; lx < bx; ++lx)
+                  for (int b = 0; b < 2; ++b) {
+                    const long long cx = ibx * bx + lx, cy = iby * by + ly, cz = ibz * bz + lz;
+                    S.sites.push_back((int)(((cz * c->ny + cy) * c->nx + cx) * 2 + b));
+                  }
+          }
+    }
+    S.col[ncol] = (int)S.dom.size();
+    S.dom.push_back((int)S.sites.size());
+  } else if (c->sched_kind == VCSGC_SCHED_SUBLATTICE) {
+    const int qx = p[0], qy = p[1], qz = p[2];
+    if (qx < 1 || qy < 1 || qz < 1 || c->nx % qx || c->ny % qy || c->nz % qz)
+      return fail(c, VCSGC_ERR_SCHEDULE, "sublattice period does not divide the lattice");
+    const int n3[3] = {c->nx, c->ny, c->nz}, q3[3] = {qx, qy, qz};
+    for (int q = 0; q < 3; ++q)
+      if (n3[q] > q3[q] && q3[q] * c->a <= two_rc)
+        return fail(c, VCSGC_ERR_SCHEDULE, "same-colour sublattice sites closer than 2 r_c");
+    const int ncol = qx * qy * qz * 2;
+    // bucket the sites by colour, ascending site index within a colour
+    std::vector<int> count(ncol + 1, 0);
+    auto colour_of = [&](long long i) {
+      const long long b = i & 1, cell = i >> 1;
+      const long long cx = cell % c->nx, cy = (cell / c->nx) % c->ny, cz = cell / ((long long)c->nx * c->ny);
+      return (int)((((cz % qz) * qy + (cy % qy)) * qx + (cx % qx)) * 2 + b);
+    };
+    for (long long i = 0; i < c->N; ++i) count[colour_of(i) + 1]++;
+    for (int q = 0; q < ncol; ++q) count[q + 1] += count[q];
+    S.col = count;
+    S.sites.assign(c->N, 0);
+    std::vector<int> cur(count.begin(), count.end() - 1);
+    for (long long i = 0; i < c->N; ++i) S.sites[cur[colour_of(i)]++] = (int)i;
+    S.dom.resize(c->N + 1);
+    for (long long i = 0; i <= c->N; ++i) S.dom[i] = (int)i;
+  } else if (c->sched_kind == VCSGC_SCHED_SPATIAL) {
+    const int nb[3] = {p[0], p[1], p[2]}, pp[3] = {p[3], p[4], p[5]};
+    for (int q = 0; q < 3; ++q) {
+      if (nb[q] < 1 || pp[q] < 1 || nb[q] % pp[q]) return fail(c, VCSGC_ERR_SCHEDULE, "spatial blocks do not divide");
+      if (nb[q] > pp[q] && (pp[q] - 1) * c->box[q] / nb[q] <= two_rc)
+        return fail(c, VCSGC_ERR_SCHEDULE, "same-colour spatial blocks closer than 2 r_c");
+    }
+    const int nblk = nb[0] * nb[1] * nb[2];
+    const int ncol = pp[0] * pp[1] * pp[2];
+    auto cidx = [](double v, double L, int n) {
+      int q = (int)std::floor(v / L * n);
+      return q < 0 ? 0 : (q >= n ? n - 1 : q);
+    };
+    std::vector<int> blk(c->N);
+    std::vector<int> bcount(nblk + 1, 0);
+    for (long long i = 0; i < c->N; ++i) {
+      blk[i] = (cidx(hz[i], c->box[2], nb[2]) * nb[1] + cidx(hy[i], c->box[1], nb[1])) * nb[0] +
+               cidx(hx[i], c->box[0], nb[0]);
+      bcount[blk[i] + 1]++;
+    }
+    // domains ordered by colour, then block index; sites ascending
+    std::vector<int> order;
+    S.col.assign(ncol + 1, 0);
+    for (int col = 0; col < ncol; ++col) {
+      S.col[col] = (int)order.size();
+      for (int b = 0; b < nblk; ++b) {
+        const int ibx = b % nb[0], iby = (b / nb[0]) % nb[1], ibz = b / (nb[0] * nb[1]);
+        if (((ibz % pp[2]) * pp[1] + (iby % pp[1])) * pp[0] + (ibx % pp[0]) == col) order.push_back(b);
+      }
+    }
+    S.col[ncol] = (int)order.size();
+    for (int b = 0; b < nblk; ++b) bcount[b + 1] += bcount[b];
+    std::vector<int> by_blk(c->N);
+    std::vector<int> cur(bcount.begin(), bcount.end() - 1);
+    for (long long i = 0; i < c->N; ++i) by_blk[cur[blk[i]]++] = (int)i;
+    S.dom.clear();
+    S.sites.clear();
+    S.sites.reserve(c->N);
+    for (int b : order) {
+      S.dom.push_back((int)S.sites.size());
+      for (int q = bcount[b]; q < bcount[b + 1]; ++q) S.sites.push_back(by_blk[q]);
+    }
+    S.dom.push_back((int)S.sites.size());
+  } else {
+    return fail(c, VCSGC_ERR_INVALID_ARG, "unknown schedule");
+  }
+  return VCSGC_OK;
+}
+
+int upload_schedule(Ctx* c, const Sched& S) {
+  const int ncol = (int)S.col.size() - 1;
+  int dmax = 0;
+  for (int q = 0; q < ncol; ++q) dmax = std::max(dmax, S.col[q + 1] - S.col[q]);
+  const bool realloc_needed = !c->col_start || ncol != c->n_colours ||
+                              (long long)S.dom.size() - 1 != c->n_domains || dmax > c->dmax;
+  if (realloc_needed) {
+    TRY(dalloc(c, &c->col_start, S.col.size()));
+    TRY(dalloc(c, &c->dom_start, S.dom.size()));
+    if (!c->dom_sites) TRY(dalloc(c, &c->dom_sites, c->N));
+    if (dmax > c->dmax) TRY(dalloc(c, &c->acc_list, (size_t)c->R * dmax));
+    drop_graph(c);
+  }
+  CK(cudaMemcpyAsync(c->col_start, S.col.data(), sizeof(int) * S.col.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->dom_start, S.dom.data(), sizeof(int) * S.dom.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->dom_sites, S.sites.data(), sizeof(int) * S.sites.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->n_colours = ncol;
+  c->n_domains = (long long)S.dom.size() - 1;
+  c->dmax = std::max(c->dmax, dmax);
+  const int dpc = S.col[1] - S.col[0];
+  c->steps_per_sweep = dpc > 0 ? std::max(1LL, (c->N + dpc / 2) / dpc) : 1;
+  fill_args(c);
+  return VCSGC_OK;
+}
+
+int positions_host(Ctx* c, std::vector<double>& hx, std::vector<double>& hy, std::vector<double>& hz) {
+  hx.resize(c->N);
+  hy.resize(c->N);
+  hz.resize(c->N);
+  CK(cudaMemcpyAsync(hx.data(), c->x, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(hy.data(), c->y, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(hz.data(), c->z, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return VCSGC_OK;
+}
+
+// --------------------------------------------------------------- energy
+int energy_of(Ctx* c, int r, double* out) {
+  launch_energy(c->mc, c->shell, r, c->part, c->st);
+  CK(cudaGetLastError());
+  std::vector<double> h(c->part_n);
+  CK(cudaMemcpyAsync(h.data(), c->part, sizeof(double) * c->part_n, cudaMemcpyDeviceToHost, c->st));
+  TRY(check_device_error(c));
+  // compensated sum of the block partials
+  double s = 0.0, comp = 0.0;
+  for (double v : h) {
+    const double t = s + v;
+    comp += std::fabs(s) >= std::fabs(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+  }
+  *out = s + comp;
+  return VCSGC_OK;
+}
+
+// recompute rho (and dF) of replica r, or of the shared array
+int refresh_rho(Ctx* c, int r) {
+  launch_rho(c->mc, c->shell, r, c->st);
+  CK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
+int sync_state_from_types(Ctx* c, int r, const uint8_t* host_types) {
+  long long nb = 0;
+  for (long long i = 0; i < c->N; ++i) nb += host_types[i];
+  if (c->reembed || r == 0) TRY(refresh_rho(c, r));
+  double e = 0.0;
+  TRY(energy_of(c, r, &e));
+  RepState s;
+  CK(cudaMemcpyAsync(&s, c->rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  s.n = nb;
+  s.energy = e;
+  CK(cudaMemcpyAsync(c->rs + r, &s, sizeof(RepState), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return VCSGC_OK;
+}
+
+int run_steps(Ctx* c, long long n) {
+  if (n <= 0) return VCSGC_OK;
+  const int G = 64;
+  if (n >= G) {
+    if (!c->graph) {
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+      for (int q = 0; q < G; ++q) launch_colour_step(c->mc, c->shell, c->reembed, c->st);
+      cudaError_t e1 = cudaGetLastError();
+      CK(cudaStreamEndCapture(c->st, &g));
+      if (e1 != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(c, VCSGC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e1));
+      }
+      cudaError_t e2 = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) return fail(c, VCSGC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(e2));
+      c->graph_steps = G;
+    }
+    while (n >= G) {
+      CK(cudaGraphLaunch(c->graph, c->st));
+      n -= G;
+    }
+  }
+  for (long long q = 0; q < n; ++q) launch_colour_step(c->mc, c->shell, c->reembed, c->st);
+  CK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
+// ------------------------------------------------------------------- MD
+int md_forces(Ctx* c) {
+  launch_md_rho(c->md, c->st);
+  launch_md_force(c->md, c->st);
+  CK(cudaGetLastError());
+  c->forces_valid = true;
+  return VCSGC_OK;
+}
+
+int md_rebuild(Ctx* c) {
+  TRY(build_cell_list(c));
+  launch_md_snapshot(c->md, c->st);
+  CK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
+int md_run(Ctx* c, long long n) {
+  if (!c->have_v) return fail(c, VCSGC_ERR_STATE, "md_steps needs velocities (vcsgc_set_velocities)");
+  if (c->kind != 1 || c->R != 1) return fail(c, VCSGC_ERR_STATE, "md_steps needs explicit positions and one replica");
+  if (!c->forces_valid) TRY(md_forces(c));
+  const double half_skin2 = 0.25 * c->skin * c->skin;
+  for (long long q = 0; q < n; ++q) {
+    launch_md_first_half(c->md, c->md_step, c->st);
+    CK(cudaGetLastError());
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->max_disp2, sizeof(bits), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double d2;
+    std::memcpy(&d2, &bits, sizeof(d2));
+    if (d2 > half_skin2) TRY(md_rebuild(c));
+    launch_md_rho(c->md, c->st);
+    launch_md_force(c->md, c->st);
+    launch_md_second_half(c->md, c->st);
+    CK(cudaGetLastError());
+    c->md_step++;
+  }
+  return VCSGC_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int vcsgc_default_options(vcsgc_options* o) {
+  if (!o) return VCSGC_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->seed = 1;
+  o->c0 = -1.0;
+  o->kappa_units = 0;
+  o->schedule = VCSGC_SCHED_SUBLATTICE;
+  o->sched[0] = o->sched[1] = o->sched[2] = 4;
+  o->precision = VCSGC_PREC_FP64;
+  o->n_replicas = 1;
+  o->mass[0] = 55.845;
+  o->mass[1] = 63.546;
+  o->dt = 2.0;
+  o->gamma = 0.01;
+  o->T_md = -1.0;
+  o->skin = 0.3;
+  o->md_seed = 12345;
+  o->device = -1;
+  return VCSGC_OK;
+}
+
+static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_eam_tables* E,
+                     double phi, double kappa, double T, const vcsgc_options* o) {
+  if (!L || !types || !E || !o) return fail(c, VCSGC_ERR_INVALID_ARG, "null argument");
+  if (o->precision != VCSGC_PREC_FP64) return fail(c, VCSGC_ERR_INVALID_ARG, "only FP64 precision is built");
+  if (o->n_replicas < 1) return fail(c, VCSGC_ERR_INVALID_ARG, "n_replicas < 1");
+  c->R = o->n_replicas;
+  c->kind = L->kind;
+  c->rc = E->rc;
+  c->skin = L->kind == 1 ? std::max(0.0, o->skin) : 0.0;
+  c->rl = c->rc + c->skin;
+  if (!(c->rc > 0)) return fail(c, VCSGC_ERR_INVALID_ARG, "rc <= 0");
+  if (L->kind == 0) {
+    if (L->nx < 1 || L->ny < 1 || L->nz < 1 || !(L->a > 0)) return fail(c, VCSGC_ERR_INVALID_ARG, "bad lattice size");
+    c->nx = L->nx; c->ny = L->ny; c->nz = L->nz; c->a = L->a;
+    c->N = 2LL * L->nx * L->ny * L->nz;
+    c->box[0] = L->a * L->nx; c->box[1] = L->a * L->ny; c->box[2] = L->a * L->nz;
+    for (int q = 0; q < 3; ++q)
+      if (!(c->box[q] > c->rc)) return fail(c, VCSGC_ERR_INVALID_ARG, "box shorter than r_c (self images)");
+  } else if (L->kind == 1) {
+    if (L->n < 1 || !L->x || !L->y || !L->z) return fail(c, VCSGC_ERR_INVALID_ARG, "bad explicit lattice");
+    c->N = L->n;
+    for (int q = 0; q < 3; ++q) {
+      c->box[q] = L->box[q];
+      if (!(c->box[q] > 2.0 * c->rl) || std::floor(c->box[q] / c->rl) < 3)
+        return fail(c, VCSGC_ERR_INVALID_ARG, "box must exceed 2 (r_c + skin) and hold 3 cells");
+    }
+  } else {
+    return fail(c, VCSGC_ERR_INVALID_ARG, "lattice kind must be 0 or 1");
+  }
+  if (c->N > 0x7fffffffLL) return fail(c, VCSGC_ERR_INVALID_ARG, "too many sites");
+  if (!(T > 0) || !(kappa >= 0)) return fail(c, VCSGC_ERR_INVALID_ARG, "T must be > 0 and kappa >= 0");
+  for (long long i = 0; i < (long long)c->R * c->N; ++i)
+    if (types[i] > 1) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
+  if (E->nr < 2 || E->nrho < 2 || !(E->dr > 0) || !(E->drho > 0))
+    return fail(c, VCSGC_ERR_INVALID_ARG, "bad table grid");
+  if ((E->nr - 1) * E->dr < c->rc * (1.0 - 1e-12)) return fail(c, VCSGC_ERR_INVALID_ARG, "r table shorter than rc");
+  for (int q = 0; q < 3; ++q)
+    if (!E->pair[q]) return fail(c, VCSGC_ERR_INVALID_ARG, "missing pair table");
+  for (int q = 0; q < 2; ++q)
+    if (!E->dens[q] || !E->embed[q]) return fail(c, VCSGC_ERR_INVALID_ARG, "missing table");
+
+  if (o->device >= 0) {
+    CK(cudaSetDevice(o->device));
+    c->device = o->device;
+  } else {
+    CK(cudaGetDevice(&c->device));
+  }
+  if (o->stream) {
+    c->st = (cudaStream_t)o->stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  c->mass[0] = o->mass[0] > 0 ? o->mass[0] : 55.845;
+  c->mass[1] = o->mass[1] > 0 ? o->mass[1] : 63.546;
+  c->dt = o->dt > 0 ? o->dt : 2.0;
+  c->gamma = o->gamma >= 0 ? o->gamma : 0.0;
+  c->T_md = o->T_md > 0 ? o->T_md : T;
+  c->md_seed = o->md_seed;
+
+  // same density function for both species: rho is species-independent and
+  // the re-embedding term vanishes identically
+  bool same = std::memcmp(E->dens[0], E->dens[1], sizeof(double) * E->nr) == 0;
+  if (same) {
+    if ((E->ddens[0] == nullptr) != (E->ddens[1] == nullptr)) same = false;
+    else if (E->ddens[0] && std::memcmp(E->ddens[0], E->ddens[1], sizeof(double) * E->nr) != 0) same = false;
+  }
+  c->reembed = !same;
+  c->shell = (c->kind == 0);
+  if (c->reembed && c->kind == 0)
+    for (int q = 0; q < 3; ++q)
+      if (!(c->box[q] > 2.0 * c->rc))
+        return fail(c, VCSGC_ERR_INVALID_ARG, "species-dependent density needs a box longer than 2 r_c");
+
+  TRY(dalloc(c, &c->derr, 1));
+  CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+
+  // ---- tables
+  for (int q = 0; q < 7; ++q) {
+    const bool rgrid = q < 5;
+    const int n = rgrid ? E->nr : E->nrho;
+    const double h = rgrid ? E->dr : E->drho;
+    const double* y = q < 3 ? E->pair[q] : (q < 5 ? E->dens[q - 3] : E->embed[q - 5]);
+    const double* m = q < 3 ? E->dpair[q] : (q < 5 ? E->ddens[q - 3] : E->dembed[q - 5]);
+    double *dy = nullptr, *dm = nullptr;
+    TRY(dalloc(c, &dy, n));
+    CK(cudaMemcpyAsync(dy, y, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+    if (m) {
+      TRY(dalloc(c, &dm, n));
+      CK(cudaMemcpyAsync(dm, m, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+    }
+    TRY(dalloc(c, &c->coef[q], n - 1));
+    launch_spline_coeffs(dy, dm, n, h, c->coef[q], c->st);
+    CK(cudaGetLastError());
+    Spline& s = c->mc.tab.sp[q];
+    s.c = c->coef[q];
+    s.inv_h = 1.0 / h;
+    s.xmax = (n - 1) * h;
+    s.n_int = n - 1;
+  }
+
+  // ---- positions (both kinds; kind 0 from the lattice)
+  TRY(dalloc(c, &c->x, c->N));
+  TRY(dalloc(c, &c->y, c->N));
+  TRY(dalloc(c, &c->z, c->N));
+  std::vector<double> hx(c->N), hy(c->N), hz(c->N);
+  if (c->kind == 0) {
+    for (long long i = 0; i < c->N; ++i) {
+      const long long b = i & 1, cell = i >> 1;
+      const long long cx = cell % c->nx, cy = (cell / c->nx) % c->ny, cz = cell / ((long long)c->nx * c->ny);
+      hx[i] = c->a * (cx + 0.5 * b);
+      hy[i] = c->a * (cy + 0.5 * b);
+      hz[i] = c->a * (cz + 0.5 * b);
+    }
+  } else {
+    for (long long i = 0; i < c->N; ++i) {
+      hx[i] = L->x[i] - c->box[0] * std::floor(L->x[i] / c->box[0]);
+      hy[i] = L->y[i] - c->box[1] * std::floor(L->y[i] / c->box[1]);
+      hz[i] = L->z[i] - c->box[2] * std::floor(L->z[i] / c->box[2]);
+      if (hx[i] >= c->box[0]) hx[i] = 0.0;
+      if (hy[i] >= c->box[1]) hy[i] = 0.0;
+      if (hz[i] >= c->box[2]) hz[i] = 0.0;
+    }
+  }
+  CK(cudaMemcpyAsync(c->x, hx.data(), sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->y, hy.data(), sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->z, hz.data(), sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
+
+  // ---- neighbour list (A1)
+  TRY(dalloc(c, &c->nbr_cnt, c->N));
+  if (c->kind == 0) {
+    // BCC half-lattice offsets within r_c, ordered by distance
+    struct Off { int h2, x, y, z; };
+    std::vector<Off> offs;
+    const double ha = 0.5 * c->a;
+    const int m = (int)std::ceil(c->rc / ha) + 1;
+    for (int x = -m; x <= m; ++x)
+      for (int y = -m; y <= m; ++y)
+        for (int z = -m; z <= m; ++z) {
+          if (((x ^ y) & 1) || ((x ^ z) & 1)) continue;
+          const int h2 = x * x + y * y + z * z;
+          if (h2 == 0 || ha * ha * h2 >= c->rc * c->rc) continue;
+          offs.push_back({h2, x, y, z});
+        }
+    std::sort(offs.begin(), offs.end(), [](const Off& p, const Off& q) {
+      if (p.h2 != q.h2) return p.h2 < q.h2;
+      if (p.x != q.x) return p.x < q.x;
+      if (p.y != q.y) return p.y < q.y;
+      return p.z < q.z;
+    });
+    if (offs.empty() || (int)offs.size() > MAX_OFFSETS) return fail(c, VCSGC_ERR_INVALID_ARG, "unsupported r_c / a");
+    c->K = (int)offs.size();
+    std::vector<int3> h3;
+    std::vector<int> sh2, sz;
+    int S = 0;
+    for (size_t k = 0; k < offs.size(); ++k) {
+      h3.push_back(make_int3(offs[k].x, offs[k].y, offs[k].z));
+      if (k == 0 || offs[k].h2 != offs[k - 1].h2) {
+        if (S == MAX_SHELLS) return fail(c, VCSGC_ERR_INVALID_ARG, "too many neighbour shells");
+        sh2.push_back(offs[k].h2);
+        sz.push_back(0);
+        ++S;
+      }
+      sz[S - 1]++;
+      c->mc.shell_end[S - 1] = (int)k + 1;
+    }
+    c->mc.n_shells = S;
+    int3* dh = nullptr;
+    int *dh2 = nullptr, *dz = nullptr;
+    TRY(dalloc(c, &dh, c->K));
+    TRY(dalloc(c, &dh2, S));
+    TRY(dalloc(c, &dz, S));
+    CK(cudaMemcpyAsync(dh, h3.data(), sizeof(int3) * c->K, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(dh2, sh2.data(), sizeof(int) * S, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(dz, sz.data(), sizeof(int) * S, cudaMemcpyHostToDevice, c->st));
+    TRY(dalloc(c, &c->nbr, (size_t)c->N * c->K));
+    launch_lattice_neighbours(c->nx, c->ny, c->nz, dh, c->K, c->nbr, c->nbr_cnt, c->st);
+    TRY(dalloc(c, &c->shell_tab, 1 + 3 * S));
+    launch_shell_tables(c->mc.tab, dh2, dz, S, c->a, c->shell_tab, c->derr, c->st);
+    CK(cudaGetLastError());
+  } else {
+    const double dens = c->N / (c->box[0] * c->box[1] * c->box[2]);
+    const double est = 4.0 / 3.0 * M_PI * c->rl * c->rl * c->rl * dens;
+    c->K = ((int)(est * 1.4) + 16 + 7) / 8 * 8;
+    TRY(dalloc(c, &c->nbr, (size_t)c->N * c->K));
+    c->mc.n_shells = 0;
+    TRY(dalloc(c, &c->shell_tab, 1));
+  }
+  // ---- buffers
+  TRY(dalloc(c, &c->types, (size_t)c->R * c->N));
+  CK(cudaMemcpyAsync(c->types, types, (size_t)c->R * c->N, cudaMemcpyHostToDevice, c->st));
+  TRY(dalloc(c, &c->rho, (size_t)(c->reembed ? c->R : 1) * c->N));
+  TRY(dalloc(c, &c->dF, c->N));
+  TRY(dalloc(c, &c->dFp, c->N));
+  TRY(dalloc(c, &c->fx, c->N));
+  TRY(dalloc(c, &c->fy, c->N));
+  TRY(dalloc(c, &c->fz, c->N));
+  TRY(dalloc(c, &c->x0, c->N));
+  TRY(dalloc(c, &c->y0, c->N));
+  TRY(dalloc(c, &c->z0, c->N));
+  TRY(dalloc(c, &c->max_disp2, 1));
+  TRY(dalloc(c, &c->rp, c->R));
+  TRY(dalloc(c, &c->rs, c->R));
+  TRY(dalloc(c, &c->acc, c->R));
+  CK(cudaMemsetAsync(c->rs, 0, sizeof(RepState) * c->R, c->st));
+  CK(cudaMemsetAsync(c->acc, 0, sizeof(StepAcc) * c->R, c->st));
+  c->part_n = std::max(energy_blocks(c->N), kinetic_blocks(c->N));
+  TRY(dalloc(c, &c->part, c->part_n));
+  fill_args(c);
+  if (c->kind == 1) TRY(md_rebuild(c));
+
+  // ---- schedule (A3)
+  c->sched_kind = o->schedule;
+  std::memcpy(c->sched, o->sched, sizeof(c->sched));
+  {
+    Sched S;
+    TRY(build_schedule(c, hx, hy, hz, S));
+    TRY(upload_schedule(c, S));
+  }
+
+  // ---- replica parameters (Eq. pi_vcsgc, Eq. trans_vcsgc_par1)
+  c->h_rp.resize(c->R);
+  std::vector<RepState> hs(c->R);
+  std::memset(hs.data(), 0, sizeof(RepState) * c->R);
+  for (int r = 0; r < c->R; ++r) {
+    const double ph = o->phi_r ? o->phi_r[r] : phi;
+    const double ka = o->kappa_r ? o->kappa_r[r] : kappa;
+    const double TT = o->T_r ? o->T_r[r] : T;
+    const uint64_t seed = o->seed_r ? o->seed_r[r] : o->seed + (uint64_t)r;
+    const double c0r = o->c0_r ? o->c0_r[r] : o->c0;
+    if (!(TT > 0) || !(ka >= 0)) return fail(c, VCSGC_ERR_INVALID_ARG, "replica T must be > 0, kappa >= 0");
+    long long nb = 0;
+    for (long long i = 0; i < c->N; ++i) nb += types[(long long)r * c->N + i];
+    RepParams& p = c->h_rp[r];
+    p.beta = 1.0 / (KB_EV * TT);
+    p.kappa_p = o->kappa_units == 1 ? ka : ka * KB_EV * TT / (double)c->N;
+    const double c0 = c0r < 0 ? (double)nb / (double)c->N : c0r;
+    p.n0 = (double)c->N * c0;
+    p.dmu0 = ph + 2.0 * p.kappa_p * p.n0;
+    p.phi = ph;
+    p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    hs[r].n = nb;
+  }
+  CK(cudaMemcpyAsync(c->rp, c->h_rp.data(), sizeof(RepParams) * c->R, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->rs, hs.data(), sizeof(RepState) * c->R, cudaMemcpyHostToDevice, c->st));
+
+  // ---- rho, dF and energies (A2)
+  if (c->reembed) {
+    for (int r = 0; r < c->R; ++r) TRY(refresh_rho(c, r));
+  } else {
+    TRY(refresh_rho(c, 0));
+  }
+  TRY(check_device_error(c));
+  for (int r = 0; r < c->R; ++r) {
+    double e;
+    TRY(energy_of(c, r, &e));
+    CK(cudaMemcpyAsync(&c->rs[r].energy, &e, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  if (c->kind == 1 && c->R == 1) TRY(md_forces(c));
+  TRY(check_device_error(c));
+  return VCSGC_OK;
+}
+
+static void destroy(Ctx* c) {
+  if (!c) return;
+  drop_graph(c);
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+int vcsgc_init(void** out, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_eam_tables* E,
+               double phi, double kappa, double T, const vcsgc_options* opt) {
+  if (!out) return VCSGC_ERR_INVALID_ARG;
+  *out = nullptr;
+  vcsgc_options def;
+  vcsgc_default_options(&def);
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) {
+    g_init_error = "host allocation failed";
+    return VCSGC_ERR_NOMEM;
+  }
+  const int rc = init_impl(c, L, types, E, phi, kappa, T, opt ? opt : &def);
+  if (rc != VCSGC_OK) {
+    g_init_error = c->err;
+    destroy(c);
+    return rc;
+  }
+  *out = c;
+  return VCSGC_OK;
+}
+
+void vcsgc_free(void* ctx) { destroy(static_cast<Ctx*>(ctx)); }
+
+const char* vcsgc_last_error(void* ctx) {
+  if (!ctx) return g_init_error.c_str();
+  return static_cast<Ctx*>(ctx)->err.c_str();
+}
+
+int vcsgc_steps(void* ctx, int64_t n) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || n < 0) return VCSGC_ERR_INVALID_ARG;
+  return run_steps(c, n);
+}
+
+int vcsgc_steps_per_sweep(void* ctx, int64_t* out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !out) return VCSGC_ERR_INVALID_ARG;
+  *out = c->steps_per_sweep;
+  return VCSGC_OK;
+}
+
+int vcsgc_sweep(void* ctx, int64_t n) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || n < 0) return VCSGC_ERR_INVALID_ARG;
+  return run_steps(c, n * c->steps_per_sweep);
+}
+
+int md_steps(void* ctx, int64_t n) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || n < 0) return VCSGC_ERR_INVALID_ARG;
+  TRY(md_run(c, n));
+  return check_device_error(c);
+}
+
+int vcsgc_hybrid(void* ctx, int64_t n_cycles, int64_t n_md, int64_t n_mc) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || n_cycles < 0 || n_md < 0 || n_mc < 0) return VCSGC_ERR_INVALID_ARG;
+  for (int64_t q = 0; q < n_cycles; ++q) {
+    TRY(md_run(c, n_md));
+    if (c->sched_kind == VCSGC_SCHED_SPATIAL) {
+      std::vector<double> hx, hy, hz;
+      TRY(positions_host(c, hx, hy, hz));
+      Sched S;
+      TRY(build_schedule(c, hx, hy, hz, S));
+      TRY(upload_schedule(c, S));
+    }
+    // positions moved: the tracked energy restarts from a full evaluation
+    double e;
+    TRY(energy_of(c, 0, &e));
+    CK(cudaMemcpyAsync(&c->rs[0].energy, &e, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    TRY(run_steps(c, n_mc));
+    c->forces_valid = false;
+    TRY(md_forces(c));
+  }
+  return check_device_error(c);
+}
+
+int observables(void* ctx, int32_t r, vcsgc_observables* o) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !o || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  TRY(check_device_error(c));
+  RepState s;
+  CK(cudaMemcpyAsync(&s, c->rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  const RepParams& p = c->h_rp[r];
+  std::memset(o, 0, sizeof(*o));
+  o->n_sites = c->N;
+  o->n_b = s.n;
+  o->c = (double)s.n / (double)c->N;
+  o->energy = s.energy;
+  o->energy_per_atom = s.energy / (double)c->N;
+  o->steps = s.steps;
+  o->trials = s.trials;
+  o->local_accepts = s.local_acc;
+  o->global_trials = s.global_trials;
+  o->global_accepts = s.global_acc;
+  o->flips = s.flips;
+  o->near_ties = s.near_ties;
+  o->acc_local = s.trials ? (double)s.local_acc / (double)s.trials : 0.0;
+  o->acc_global = s.global_trials ? (double)s.global_acc / (double)s.global_trials : 0.0;
+  o->mean_c = s.steps ? s.sum_c / (double)s.steps : o->c;
+  o->var_c = s.steps ? std::max(0.0, s.sum_c2 / (double)s.steps - o->mean_c * o->mean_c) : 0.0;
+  o->dmu_est = p.phi + 2.0 * p.kappa_p * (double)c->N * o->mean_c;
+  o->sweeps = (double)s.trials / (double)c->N;
+  o->kappa_p = p.kappa_p;
+  o->dmu0 = p.dmu0;
+  return VCSGC_OK;
+}
+
+int vcsgc_get_types(void* ctx, int32_t r, uint8_t* out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(out, c->types + (long long)r * c->N, c->N, cudaMemcpyDeviceToHost, c->st));
+  return check_device_error(c);
+}
+
+int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !in || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  for (long long i = 0; i < c->N; ++i)
+    if (in[i] > 1) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
+  CK(cudaMemcpyAsync(c->types + (long long)r * c->N, in, c->N, cudaMemcpyHostToDevice, c->st));
+  TRY(sync_state_from_types(c, r, in));
+  c->forces_valid = false;
+  return check_device_error(c);
+}
+
+int vcsgc_get_rho(void* ctx, int32_t r, double* out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  const double* src = c->rho + (c->reembed ? (long long)r * c->N : 0);
+  CK(cudaMemcpyAsync(out, src, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  return check_device_error(c);
+}
+
+int vcsgc_delta_e(void* ctx, int32_t r, const int64_t* sites, int64_t n, double* out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || (n > 0 && (!sites || !out)) || n < 0 || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  if (n == 0) return VCSGC_OK;
+  std::vector<int> s32(n);
+  for (int64_t q = 0; q < n; ++q) {
+    if (sites[q] < 0 || sites[q] >= c->N) return fail(c, VCSGC_ERR_INVALID_ARG, "site index out of range");
+    s32[q] = (int)sites[q];
+  }
+  if (n > c->sites_cap) {
+    TRY(dalloc(c, &c->sites_buf, n));
+    TRY(dalloc(c, &c->de_buf, n));
+    c->sites_cap = (int)n;
+  }
+  CK(cudaMemcpyAsync(c->sites_buf, s32.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
+  launch_delta_e_list(c->mc, c->shell, c->reembed, r, c->sites_buf, (int)n, c->de_buf, c->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, c->de_buf, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+  return check_device_error(c);
+}
+
+int vcsgc_energy(void* ctx, int32_t r, double* out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  return energy_of(c, r, out);
+}
+
+int vcsgc_forces(void* ctx, double* fx, double* fy, double* fz) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !fx || !fy || !fz) return VCSGC_ERR_INVALID_ARG;
+  if (!c->forces_valid) TRY(md_forces(c));
+  CK(cudaMemcpyAsync(fx, c->fx, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(fy, c->fy, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(fz, c->fz, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  return check_device_error(c);
+}
+
+int vcsgc_get_md(void* ctx, double* x, double* y, double* z, double* vx, double* vy, double* vz) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return VCSGC_ERR_INVALID_ARG;
+  double* dst[6] = {x, y, z, vx, vy, vz};
+  double* src[6] = {c->x, c->y, c->z, c->vx, c->vy, c->vz};
+  for (int q = 0; q < 6; ++q) {
+    if (!dst[q]) continue;
+    if (!src[q]) return fail(c, VCSGC_ERR_STATE, "velocities not set");
+    CK(cudaMemcpyAsync(dst[q], src[q], sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  }
+  return check_device_error(c);
+}
+
+int vcsgc_set_velocities(void* ctx, const double* vx, const double* vy, const double* vz) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !vx || !vy || !vz) return VCSGC_ERR_INVALID_ARG;
+  if (c->R != 1) return fail(c, VCSGC_ERR_STATE, "velocities need one replica");
+  if (!c->vx) {
+    TRY(dalloc(c, &c->vx, c->N));
+    TRY(dalloc(c, &c->vy, c->N));
+    TRY(dalloc(c, &c->vz, c->N));
+  }
+  CK(cudaMemcpyAsync(c->vx, vx, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->vy, vy, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->vz, vz, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
+  c->have_v = true;
+  fill_args(c);
+  drop_graph(c);
+  return check_device_error(c);
+}
+
+int vcsgc_kinetic_energy(void* ctx, double* out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !out) return VCSGC_ERR_INVALID_ARG;
+  if (!c->have_v) return fail(c, VCSGC_ERR_STATE, "velocities not set");
+  launch_kinetic(c->md, c->part, c->st);
+  CK(cudaGetLastError());
+  const int nb = kinetic_blocks(c->N);
+  std::vector<double> h(nb);
+  CK(cudaMemcpyAsync(h.data(), c->part, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
+  TRY(check_device_error(c));
+  double s = 0.0;
+  for (double v : h) s += v;
+  *out = s;
+  return VCSGC_OK;
+}
+
+int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_commit) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || n < 1 || !ms_propose || !ms_commit) return VCSGC_ERR_INVALID_ARG;
+  std::vector<cudaEvent_t> ev(2 * n + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(ev[0], c->st));
+  for (int64_t q = 0; q < n; ++q) {
+    launch_colour_step(c->mc, c->shell, c->reembed, c->st, 1);
+    CK(cudaEventRecord(ev[2 * q + 1], c->st));
+    launch_colour_step(c->mc, c->shell, c->reembed, c->st, 2);
+    CK(cudaEventRecord(ev[2 * q + 2], c->st));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  double tp = 0.0, tc = 0.0;
+  for (int64_t q = 0; q < n; ++q) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, ev[2 * q], ev[2 * q + 1]));
+    CK(cudaEventElapsedTime(&b, ev[2 * q + 1], ev[2 * q + 2]));
+    tp += a;
+    tc += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  *ms_propose = tp;
+  *ms_commit = tc;
+  return check_device_error(c);
+}
+
+int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* count) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !out || !count || i < 0 || i >= c->N || cap < 0) return VCSGC_ERR_INVALID_ARG;
+  int cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, c->nbr_cnt + i, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *count = cnt;
+  const int m = std::min(cnt, (int)cap);
+  if (m > 0) {
+    CK(cudaMemcpyAsync(out, c->nbr + i * c->K, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  return VCSGC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,321 @@
+"""Thin Python binding of the C ABI in ``include/vcsgc.h`` (ctypes).
+
+The module functions carry the C names and only marshal arguments: every
+step of the method runs in ``libvcsgc.so``'s CUDA kernels.  ``Context`` is a
+small convenience wrapper over the same calls.  There is no CPU fallback: if
+the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR = {-1: "INVALID_ARG", -2: "CUDA", -3: "TABLE_RANGE", -4: "NONFINITE", -5: "SCHEDULE",
+       -6: "TIMEOUT", -7: "NOMEM", -8: "STATE", -9: "OVERFLOW"}
+SCHED_BLOCKS, SCHED_SUBLATTICE, SCHED_SPATIAL = 0, 1, 2
+
+
+class VcsgcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"vcsgc error {code} ({ERR.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Lattice(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("a", C.c_double), ("n", C.c_int64), ("x", C.c_void_p), ("y", C.c_void_p),
+                ("z", C.c_void_p), ("box", C.c_double * 3)]
+
+
+class EamTables(C.Structure):
+    _fields_ = [("nr", C.c_int32), ("dr", C.c_double), ("nrho", C.c_int32), ("drho", C.c_double),
+                ("rc", C.c_double), ("pair", C.c_void_p * 3), ("dpair", C.c_void_p * 3),
+                ("dens", C.c_void_p * 2), ("ddens", C.c_void_p * 2), ("embed", C.c_void_p * 2),
+                ("dembed", C.c_void_p * 2)]
+
+
+class Options(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("c0", C.c_double), ("kappa_units", C.c_int32),
+                ("schedule", C.c_int32), ("sched", C.c_int32 * 6), ("precision", C.c_int32),
+                ("n_replicas", C.c_int32), ("phi_r", C.c_void_p), ("kappa_r", C.c_void_p),
+                ("T_r", C.c_void_p), ("seed_r", C.c_void_p), ("c0_r", C.c_void_p),
+                ("mass", C.c_double * 2), ("dt", C.c_double), ("gamma", C.c_double),
+                ("T_md", C.c_double), ("skin", C.c_double), ("md_seed", C.c_uint64),
+                ("stream", C.c_void_p), ("device", C.c_int32)]
+
+
+class Observables(C.Structure):
+    _fields_ = [("n_sites", C.c_int64), ("n_b", C.c_int64), ("c", C.c_double),
+                ("energy", C.c_double), ("energy_per_atom", C.c_double), ("steps", C.c_int64),
+                ("trials", C.c_int64), ("local_accepts", C.c_int64), ("global_trials", C.c_int64),
+                ("global_accepts", C.c_int64), ("flips", C.c_int64), ("near_ties", C.c_int64),
+                ("acc_local", C.c_double), ("acc_global", C.c_double), ("mean_c", C.c_double),
+                ("var_c", C.c_double), ("dmu_est", C.c_double), ("sweeps", C.c_double),
+                ("kappa_p", C.c_double), ("dmu0", C.c_double)]
+
+
+_lib = None
+EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", "vcsgc_steps_per_sweep",
+           "md_steps", "vcsgc_hybrid", "observables", "vcsgc_get_types", "vcsgc_set_types",
+           "vcsgc_get_rho", "vcsgc_delta_e", "vcsgc_energy", "vcsgc_forces", "vcsgc_get_md",
+           "vcsgc_set_velocities", "vcsgc_kinetic_energy", "vcsgc_neighbours", "vcsgc_last_error",
+           "vcsgc_free", "vcsgc_profile_steps"]
+
+
+def lib():
+    """Load libvcsgc.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libvcsgc.so is missing; the CUDA path cannot run")
+        L = C.CDLL(path)
+        P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "vcsgc_default_options": (I32, [P]),
+            "vcsgc_init": (I32, [C.POINTER(C.c_void_p), P, P, P, D, D, D, P]),
+            "vcsgc_steps": (I32, [P, I64]),
+            "vcsgc_sweep": (I32, [P, I64]),
+            "vcsgc_steps_per_sweep": (I32, [P, P]),
+            "md_steps": (I32, [P, I64]),
+            "vcsgc_hybrid": (I32, [P, I64, I64, I64]),
+            "observables": (I32, [P, I32, P]),
+            "vcsgc_get_types": (I32, [P, I32, P]),
+            "vcsgc_set_types": (I32, [P, I32, P]),
+            "vcsgc_get_rho": (I32, [P, I32, P]),
+            "vcsgc_delta_e": (I32, [P, I32, P, I64, P]),
+            "vcsgc_energy": (I32, [P, I32, P]),
+            "vcsgc_forces": (I32, [P, P, P, P]),
+            "vcsgc_get_md": (I32, [P, P, P, P, P, P, P]),
+            "vcsgc_set_velocities": (I32, [P, P, P, P]),
+            "vcsgc_kinetic_energy": (I32, [P, P]),
+            "vcsgc_neighbours": (I32, [P, I64, P, I32, P]),
+            "vcsgc_profile_steps": (I32, [P, I64, P, P]),
+            "vcsgc_last_error": (C.c_char_p, [P]),
+            "vcsgc_free": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(rc, ctx=None):
+    if rc != OK:
+        msg = lib().vcsgc_last_error(ctx)
+        raise VcsgcError(rc, msg.decode() if msg else "")
+
+
+# ------------------------------------------------- C-named entry points
+def vcsgc_default_options():
+    o = Options()
+    _check(lib().vcsgc_default_options(C.byref(o)))
+    return o
+
+
+def vcsgc_init(lattice, types, eam, phi, kappa, T, options=None):
+    """Returns the context handle; the caller frees it with vcsgc_free."""
+    h = C.c_void_p()
+    rc = lib().vcsgc_init(C.byref(h), C.byref(lattice), _ptr(types), C.byref(eam), phi, kappa, T,
+                          C.byref(options) if options is not None else None)
+    _check(rc, None)
+    return h
+
+
+def vcsgc_steps(ctx, n):
+    _check(lib().vcsgc_steps(ctx, int(n)), ctx)
+
+
+def vcsgc_sweep(ctx, n):
+    _check(lib().vcsgc_sweep(ctx, int(n)), ctx)
+
+
+def md_steps(ctx, n):
+    _check(lib().md_steps(ctx, int(n)), ctx)
+
+
+def observables(ctx, replica=0):
+    o = Observables()
+    _check(lib().observables(ctx, int(replica), C.byref(o)), ctx)
+    return {f: getattr(o, f) for f, _ in Observables._fields_}
+
+
+def vcsgc_free(ctx):
+    lib().vcsgc_free(ctx)
+
+
+# ----------------------------------------------------------- convenience
+class Context:
+    """Owns one C context; keeps the host arrays passed at init alive."""
+
+    def __init__(self, lattice, types, tables, phi, kappa, T, *, seed=1, c0=-1.0, kappa_units=0,
+                 schedule=SCHED_SUBLATTICE, sched=(4, 4, 4, 0, 0, 0), n_replicas=1, phi_r=None,
+                 kappa_r=None, T_r=None, seed_r=None, c0_r=None, masses=(55.845, 63.546), dt=2.0,
+                 gamma=0.01, T_md=-1.0, skin=0.3, md_seed=12345, stream=None, device=-1):
+        self._keep = []
+        L = Lattice()
+        if lattice.cells is not None and getattr(lattice, "rigid", True):
+            L.kind = 0
+            L.nx, L.ny, L.nz = lattice.cells
+            L.a = lattice.a
+        else:
+            L.kind = 1
+            xs = [np.ascontiguousarray(v, dtype=np.float64) for v in (lattice.x, lattice.y, lattice.z)]
+            self._keep += xs
+            L.n = xs[0].shape[0]
+            L.x, L.y, L.z = (v.ctypes.data for v in xs)
+            for q in range(3):
+                L.box[q] = float(lattice.box[q])
+        E = EamTables()
+        E.nr, E.dr, E.nrho, E.drho, E.rc = tables.nr, tables.dr, tables.nrho, tables.drho, tables.rc
+
+        def arr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return a.ctypes.data
+
+        for q in range(3):
+            E.pair[q] = arr(tables.pair[q])
+            E.dpair[q] = arr(tables.dpair[q])
+        for q in range(2):
+            E.dens[q] = arr(tables.dens[q])
+            E.ddens[q] = arr(tables.ddens[q])
+            E.embed[q] = arr(tables.embed[q])
+            E.dembed[q] = arr(tables.dembed[q])
+        o = vcsgc_default_options()
+        o.seed = seed
+        o.c0 = c0
+        o.kappa_units = kappa_units
+        o.schedule = schedule
+        for q in range(6):
+            o.sched[q] = sched[q] if q < len(sched) else 0
+        o.n_replicas = n_replicas
+        for name, val, dt_ in (("phi_r", phi_r, np.float64), ("kappa_r", kappa_r, np.float64),
+                               ("T_r", T_r, np.float64), ("seed_r", seed_r, np.uint64),
+                               ("c0_r", c0_r, np.float64)):
+            if val is not None:
+                a = np.ascontiguousarray(val, dtype=dt_)
+                self._keep.append(a)
+                setattr(o, name, a.ctypes.data)
+        o.mass[0], o.mass[1] = masses
+        o.dt, o.gamma, o.T_md, o.skin, o.md_seed = dt, gamma, T_md, skin, md_seed
+        if stream is not None:
+            o.stream = getattr(stream, "cuda_stream", stream)
+        o.device = device
+        t = np.ascontiguousarray(types, dtype=np.uint8)
+        self.n_replicas = n_replicas
+        self.h = vcsgc_init(L, t, E, phi, kappa, T, o)
+        self.n = int(t.shape[-1]) if t.ndim > 1 else int(t.shape[0]) // n_replicas
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            vcsgc_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def steps(self, n):
+        vcsgc_steps(self.h, n)
+
+    def sweep(self, n):
+        vcsgc_sweep(self.h, n)
+
+    @property
+    def steps_per_sweep(self):
+        v = C.c_int64()
+        _check(lib().vcsgc_steps_per_sweep(self.h, C.byref(v)), self.h)
+        return v.value
+
+    def md_steps(self, n):
+        md_steps(self.h, n)
+
+    def hybrid(self, n_cycles, n_md, n_mc):
+        _check(lib().vcsgc_hybrid(self.h, int(n_cycles), int(n_md), int(n_mc)), self.h)
+
+    def observables(self, replica=0):
+        return observables(self.h, replica)
+
+    def types(self, replica=0):
+        out = np.zeros(self.n, dtype=np.uint8)
+        _check(lib().vcsgc_get_types(self.h, int(replica), _ptr(out)), self.h)
+        return out
+
+    def set_types(self, t, replica=0):
+        t = np.ascontiguousarray(t, dtype=np.uint8)
+        _check(lib().vcsgc_set_types(self.h, int(replica), _ptr(t)), self.h)
+
+    def rho(self, replica=0):
+        out = np.zeros(self.n, dtype=np.float64)
+        _check(lib().vcsgc_get_rho(self.h, int(replica), _ptr(out)), self.h)
+        return out
+
+    def delta_e(self, sites, replica=0):
+        s = np.ascontiguousarray(sites, dtype=np.int64)
+        out = np.zeros(s.shape[0], dtype=np.float64)
+        _check(lib().vcsgc_delta_e(self.h, int(replica), _ptr(s), s.shape[0], _ptr(out)), self.h)
+        return out
+
+    def energy(self, replica=0):
+        v = C.c_double()
+        _check(lib().vcsgc_energy(self.h, int(replica), C.byref(v)), self.h)
+        return v.value
+
+    def forces(self):
+        f = [np.zeros(self.n) for _ in range(3)]
+        _check(lib().vcsgc_forces(self.h, *(_ptr(a) for a in f)), self.h)
+        return f
+
+    def md_state(self):
+        a = [np.zeros(self.n) for _ in range(6)]
+        _check(lib().vcsgc_get_md(self.h, *(_ptr(q) for q in a)), self.h)
+        return a
+
+    def positions(self):
+        a = [np.zeros(self.n) for _ in range(3)]
+        _check(lib().vcsgc_get_md(self.h, *(_ptr(q) for q in a), None, None, None), self.h)
+        return a
+
+    def set_velocities(self, v):
+        vv = [np.ascontiguousarray(q, dtype=np.float64) for q in v]
+        _check(lib().vcsgc_set_velocities(self.h, *(_ptr(q) for q in vv)), self.h)
+
+    def kinetic_energy(self):
+        v = C.c_double()
+        _check(lib().vcsgc_kinetic_energy(self.h, C.byref(v)), self.h)
+        return v.value
+
+    def profile_steps(self, n):
+        """Device time (ms) of the propose and commit kernels over n steps."""
+        a, b = C.c_double(), C.c_double()
+        _check(lib().vcsgc_profile_steps(self.h, int(n), C.byref(a), C.byref(b)), self.h)
+        return a.value, b.value
+
+    def neighbours(self, i, cap=256):
+        out = np.zeros(cap, dtype=np.int32)
+        cnt = C.c_int32()
+        _check(lib().vcsgc_neighbours(self.h, int(i), _ptr(out), cap, C.byref(cnt)), self.h)
+        return out[:min(cnt.value, cap)].copy()

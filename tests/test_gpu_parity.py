@@ -1,0 +1,205 @@
+"""CUDA path against the CPU oracle on the same seeded inputs (GPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1012_5082_gb300 import inputs as I
+from _pair import c0_config, compare_obs, make_pair
+
+pytestmark = pytest.mark.gpu
+
+DE_TOL = 1e-11  # eV: 1e-12 relative to the ~10 eV sum of |pair terms| of a site
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_1012_5082_gb300 import vcsgc
+    return vcsgc
+
+
+# ------------------------------------------------------------ A1, A2
+def test_lattice_neighbour_sets_match(V):
+    lat, types, tab = c0_config()
+    orc = O.System(lat, types, tab)
+    g = V.Context(lat, types, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2))
+    for i in list(range(0, lat.n, 97)) + [lat.n - 1]:
+        a = sorted(g.neighbours(i).tolist())
+        b = sorted(j for j, _, _ in orc.neighbours(i))
+        assert a == b
+    g.close()
+
+
+@pytest.mark.parametrize("dens_b", [1.0, 1.25])
+def test_rho_and_energy_match(V, dens_b):
+    lat, types, tab = c0_config(dens_b=dens_b)
+    orc = O.System(lat, types, tab)
+    g = V.Context(lat, types, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2))
+    assert np.allclose(g.rho(), orc.rho, rtol=1e-13, atol=0)
+    e_o = orc.energy_full()
+    assert abs(g.energy() - e_o) <= 1e-12 * abs(e_o)
+    assert abs(g.observables()["energy"] - e_o) <= 1e-12 * abs(e_o)
+    g.close()
+
+
+# ------------------------------------------------------------------ A4
+@pytest.mark.parametrize("dens_b", [1.0, 1.25])
+def test_delta_e_matches_on_rigid_lattice(V, dens_b):
+    lat, _, tab = c0_config(dens_b=dens_b)
+    types = I.random_types(lat.n, 600, seed=31)  # 30% B: every shell count occurs
+    orc = O.System(lat, types, tab)
+    g = V.Context(lat, types, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2))
+    sites = np.arange(lat.n)
+    de_g = g.delta_e(sites)
+    de_o = np.array([orc.delta_e(i) for i in sites])
+    assert np.max(np.abs(de_g - de_o)) < DE_TOL
+    g.close()
+
+
+@pytest.mark.parametrize("dens_b", [1.0, 1.25])
+def test_delta_e_matches_on_explicit_positions(V, dens_b):
+    lat, _, tab = c0_config(n_cells=7, dens_b=dens_b)
+    rng = np.random.default_rng(8)
+    pert = I.Lattice(x=lat.x + rng.normal(0, 0.08, lat.n), y=lat.y + rng.normal(0, 0.08, lat.n),
+                     z=lat.z + rng.normal(0, 0.08, lat.n), box=lat.box)
+    types = I.random_types(lat.n, 200, seed=32)
+    orc = O.System(pert, types, tab)
+    g = V.Context(pert, types, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_SPATIAL, sched=(2, 2, 2, 2, 2, 2))
+    sites = np.arange(lat.n)
+    de_g = g.delta_e(sites)
+    de_o = np.array([orc.delta_e(i) for i in sites])
+    assert np.max(np.abs(de_g - de_o)) < DE_TOL
+    assert np.allclose(g.rho(), orc.rho, rtol=1e-13, atol=0)
+    g.close()
+
+
+# ------------------------------------------------ trajectories (A3-A9)
+def _lockstep(orc, g, n_sweeps, steps_per_sweep):
+    """Advance both a sweep at a time; species must agree bit for bit unless
+    the oracle flagged a near-tie decision in that sweep (then re-sync)."""
+    resyncs = 0
+    for s in range(n_sweeps):
+        ties0 = orc.obs()["near_ties"]
+        g.sweep(1)
+        orc.parallel_steps(steps_per_sweep)
+        tg, to = g.types(), orc.types
+        if not np.array_equal(tg, to):
+            assert orc.obs()["near_ties"] > ties0, f"sweep {s}: species differ without a flagged tie"
+            g.set_types(to)
+            resyncs += 1
+    return resyncs
+
+
+CASES = {
+    # name: (phi, kappa, T, c0, dens_b, schedule, sched)
+    "c0-as-specified": (-2.0, 1000.0, 700.0, 0.05, 1.0, "blocks", (5, 5, 5, 2, 2, 2)),
+    "c0-active": (-8.3, 1000.0, 700.0, 0.05, 1.0, "blocks", (5, 5, 5, 2, 2, 2)),
+    "c0-reembed": (-7.4, 1000.0, 700.0, 0.05, 1.25, "blocks", (5, 5, 5, 2, 2, 2)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_trajectory_bit_exact_100_sweeps(V, name):
+    phi, kappa, T, c0, dens_b, sch, sched = CASES[name]
+    lat, types, tab = c0_config(dens_b=dens_b)
+    orc, g = make_pair(lat, types, tab, phi, kappa, T, c0=c0, seed=2000, schedule=sch, sched=sched)
+    assert g.steps_per_sweep == 2000
+    resyncs = _lockstep(orc, g, 100, 2000)
+    o_g, o_o = g.observables(), orc.obs()
+    if resyncs == 0:
+        compare_obs(o_o, o_g)
+    assert o_g["steps"] == 200000
+    if name != "c0-as-specified":
+        assert o_g["flips"] > 500
+    # incremental energy equals a fresh evaluation on both sides
+    assert abs(g.energy() - o_g["energy"]) <= 1e-9 * abs(o_g["energy"])
+    g.close()
+
+
+def test_sublattice_schedule_trajectory(V):
+    """Every site of one colour trialled at once (period-4 sublattice)."""
+    lat, types, tab = c0_config(n_cells=8)
+    orc, g = make_pair(lat, types, tab, -8.3, 1000.0, 700.0, c0=0.05, seed=2100,
+                       schedule="sublattice", sched=(4, 4, 4))
+    assert g.steps_per_sweep == 128
+    resyncs = _lockstep(orc, g, 60, 128)
+    if resyncs == 0:
+        compare_obs(orc.obs(), g.observables())
+    assert g.observables()["flips"] > 200
+    g.close()
+
+
+def test_replicas_match_independent_oracles(V):
+    """R replicas in one context equal R separate oracle chains."""
+    lat, types, tab = c0_config(n_cells=8)
+    phis = np.array([-8.3, -8.1, -8.5])
+    R = len(phis)
+    g = V.Context(lat, np.tile(types, R), tab, 0.0, 1000.0, 700.0, seed=500, c0=0.05,
+                  schedule=V.SCHED_SUBLATTICE, sched=(4, 4, 4), n_replicas=R, phi_r=phis,
+                  seed_r=np.array([500, 777, 9], dtype=np.uint64))
+    g.sweep(20)
+    for r, (phi, seed) in enumerate(zip(phis, (500, 777, 9))):
+        orc = O.System(lat, types, tab)
+        orc.set_params(phi, 1000.0, 700.0, c0=0.05, seed=seed)
+        orc.schedule_sublattice(lat.cells, (4, 4, 4))
+        orc.parallel_steps(20 * 128)
+        if orc.obs()["near_ties"] == 0:
+            assert np.array_equal(g.types(r), orc.types)
+            compare_obs(orc.obs(), g.observables(r))
+    g.close()
+
+
+def test_kappa_zero_global_stage_always_accepts(V):
+    lat, types, tab = c0_config()
+    g = V.Context(lat, types, tab, -2.28, 0.0, 700.0, seed=3, c0=0.05,
+                  schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2))
+    g.sweep(5)
+    o = g.observables()
+    assert o["global_trials"] > 0 and o["global_accepts"] == o["global_trials"]
+    g.close()
+
+
+# ------------------------------------------- full size, sampled outputs
+def test_full_size_80cubed_sampled(V):
+    """80^3 BCC (1,024,000 sites), period-4 sublattice, the launch the
+    benchmark times: after sweeps, dE at sampled sites equals the oracle's on
+    the same species, the B count equals the species array, and the tracked
+    energy equals a fresh evaluation."""
+    lat = I.bcc_lattice(80, 80, 80)
+    types = I.random_types(lat.n, int(0.02 * lat.n), seed=1001)
+    tab = I.eam_tables()
+    g = V.Context(lat, types, tab, -4.14, 1000.0, 600.0, seed=2001, c0=0.02,
+                  schedule=V.SCHED_SUBLATTICE, sched=(4, 4, 4))
+    g.sweep(3)
+    o = g.observables()
+    t = g.types()
+    assert int(t.sum()) == o["n_b"]
+    assert o["flips"] > 0
+    assert abs(g.energy() - o["energy"]) <= 1e-10 * abs(o["energy"])
+    orc = O.System(lat, t, tab)
+    rng = np.random.default_rng(5)
+    sites = rng.choice(lat.n, 3000, replace=False)
+    de_g = g.delta_e(sites)
+    de_o = np.array([orc.delta_e(int(i)) for i in sites])
+    assert np.max(np.abs(de_g - de_o)) < DE_TOL
+    g.close()
+
+
+# ------------------------------------------------------------- errors
+def test_invalid_arguments_are_reported(V):
+    lat, types, tab = c0_config()
+    bad = types.copy()
+    bad[3] = 2
+    with pytest.raises(V.VcsgcError) as e:
+        V.Context(lat, bad, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2))
+    assert e.value.code == -1
+    # blocks of 3 cells put same-colour sites closer than 2 r_c
+    lat12 = I.bcc_lattice(12, 12, 12)
+    with pytest.raises(V.VcsgcError) as e:
+        V.Context(lat12, np.zeros(lat12.n, np.uint8), tab, -2.0, 1000.0, 700.0,
+                  schedule=V.SCHED_BLOCKS, sched=(3, 3, 3, 2, 2, 2))
+    assert e.value.code == -5
+    with pytest.raises(V.VcsgcError) as e:
+        V.Context(lat, types, tab, -2.0, 1000.0, -5.0, schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2))
+    assert e.value.code == -1
