@@ -35,10 +35,11 @@ T_K = 600.0
 KAPPA = 1000.0
 N_PHI = 8
 FRAC_B = 0.02
-# eV: SGC driving force of the 2% random start (dilute estimate -dE_dilute +
-# kT ln(c/(1-c)) with dE_dilute = 2.275 eV), so local A->B and B->A accepts
-# balance and composite moves stay small (parameter recipe of Sec. III C)
-DMU_S = -2.07
+# eV: local driving force at which locally accepted A->B and B->A moves of
+# the random 2% start balance (expected dn = 0 per 8,000-trial colour step,
+# solved once from the distribution of dE on that start), so composite moves
+# stay small; phi_j = dmu0 - 2 kappa_p N c0_j (parameter recipe, Sec. III C)
+DMU_S = -2.02
 BYTES_PER_TRIAL = 4 * 58 + 1 + 8  # neighbour row + own species + own F_B - F_A
 METRIC = "VC-SGC trial moves/s"
 

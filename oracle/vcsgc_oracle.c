@@ -425,9 +425,15 @@ orc_sys* orc_create(int64_t n, const double* x, const double* y, const double* z
   s->t = (uint8_t*)malloc(n);
   s->rho = (double*)malloc(sizeof(double) * n);
   if (!s->x || !s->y || !s->z || !s->t || !s->rho) { orc_free(s); return NULL; }
-  memcpy(s->x, x, sizeof(double) * n);
-  memcpy(s->y, y, sizeof(double) * n);
-  memcpy(s->z, z, sizeof(double) * n);
+  /* positions are periodic: keep them in [0, L) */
+  for (int64_t i = 0; i < n; ++i) {
+    s->x[i] = x[i] - floor(x[i] / box[0]) * box[0];
+    s->y[i] = y[i] - floor(y[i] / box[1]) * box[1];
+    s->z[i] = z[i] - floor(z[i] / box[2]) * box[2];
+    if (s->x[i] >= box[0]) s->x[i] = 0.0;
+    if (s->y[i] >= box[1]) s->y[i] = 0.0;
+    if (s->z[i] >= box[2]) s->z[i] = 0.0;
+  }
   memcpy(s->t, types, n);
   s->rc = eam->rc;
   s->brute = brute;

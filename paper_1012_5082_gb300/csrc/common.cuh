@@ -153,6 +153,7 @@ struct RepParams {
 struct RepState {
   long long n;  // B count
   long long step;
+  long long fin_step;  // last finalised step (fused lattice form)
   double energy;
   long long trials, local_acc, global_trials, global_acc, flips, near_ties, steps;
   double sum_c, sum_c2;

@@ -47,6 +47,57 @@ void launch_rho(const McArgs& a, bool shell, int r, cudaStream_t st);
 int energy_blocks(long long N);
 void launch_energy(const McArgs& a, bool shell, int r, double* part, cudaStream_t st);
 
+// ---- fused colour step of the rigid lattice (kernels_lattice.cu)
+constexpr int LAT_BLOCK = 128;
+constexpr int LAT_MAX_SH = 8;     // shells
+constexpr int LAT_MAX_ROWS = 32;  // neighbour rows per basis
+constexpr int LAT_HALO = 4;       // halo bits at each end of a row (>= hmax)
+
+struct LatRow {
+  int dy, dz;                   // row offset (cells) from the site's row
+  uint32_t mask[LAT_MAX_SH];    // window bits of each shell
+};
+
+struct LatCtl {
+  long long base_step;          // step of the next launch with j = 0
+};
+
+struct LatArgs {
+  long long N;
+  int R;
+  int nx, ny, nz;
+  int W;                        // 64-bit words per row
+  long long rep_words;          // nz * ny * W
+  unsigned long long* bits;     // [R][nz][ny][W] (+1 pad word)
+  int hmax;                     // largest |half-lattice offset| along x
+  int n_rows[2];
+  LatRow rows[2][LAT_MAX_ROWS];
+  double C;                     // pair part of dE(A->B) with no B neighbour
+  double G[LAT_MAX_SH];         // change per B neighbour in each shell
+  const double* dF;             // [N] F_B(rho_i) - F_A(rho_i)
+  // schedule
+  int sublattice, qx, qy, qz;
+  int n_colours;
+  const int* col_start;
+  const int* dom_start;
+  const int* dom_sites;
+  int dmax;
+  // replicas
+  const RepParams* rp;
+  RepState* rs;
+  StepAcc* acc;                 // [R][3]
+  long long* n_start;           // [R][2]
+  int* pend;                    // [R][dmax]
+  LatCtl* ctl;
+  unsigned* err;
+};
+
+void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);
+void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st);
+void launch_lattice_pack(const LatArgs& a, const uint8_t* types, int r, cudaStream_t st);
+void launch_lattice_unpack(const LatArgs& a, uint8_t* types, int r, cudaStream_t st);
+void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st);
+
 // ---- colour step (kernels_mc.cu)
 // phase 0: propose + commit; 1: propose only; 2: commit only
 void launch_colour_step(const McArgs& a, bool shell, bool reembed, cudaStream_t st, int phase = 0);

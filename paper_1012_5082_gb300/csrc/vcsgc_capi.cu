@@ -81,6 +81,12 @@ struct Ctx {
   int graph_steps = 0;
   McArgs mc{};
   MdArgs md{};
+  // fused lattice form
+  bool fast = false;
+  LatArgs lat{};
+  long long h_base = 0;            // host mirror of lat.ctl->base_step
+  std::vector<int3> offsets;       // half-lattice neighbour offsets (kind 0)
+  std::vector<int> offset_shell;
 };
 
 #define CK(call)                                                                       \
@@ -91,6 +97,9 @@ struct Ctx {
       return VCSGC_ERR_CUDA;                                                           \
     }                                                                                  \
   } while (0)
+
+int flush(Ctx* c);
+int sync_bytes(Ctx* c, int r);
 
 int fail(Ctx* c, int code, const std::string& msg) {
   c->err = msg;
@@ -188,6 +197,23 @@ void fill_args(Ctx* c) {
   m.tab = c->mc.tab;
   m.err = c->derr;
   m.max_disp2_bits = c->max_disp2;
+
+  LatArgs& l = c->lat;
+  l.N = c->N;
+  l.R = c->R;
+  l.dF = c->dF;
+  l.sublattice = c->sched_kind == VCSGC_SCHED_SUBLATTICE ? 1 : 0;
+  l.qx = c->sched[0];
+  l.qy = c->sched[1];
+  l.qz = c->sched[2];
+  l.n_colours = c->n_colours;
+  l.col_start = c->col_start;
+  l.dom_start = c->dom_start;
+  l.dom_sites = c->dom_sites;
+  l.dmax = c->dmax;
+  l.rp = c->rp;
+  l.rs = c->rs;
+  l.err = c->derr;
 }
 
 void drop_graph(Ctx* c) {
@@ -391,6 +417,7 @@ int positions_host(Ctx* c, std::vector<double>& hx, std::vector<double>& hy, std
 
 // --------------------------------------------------------------- energy
 int energy_of(Ctx* c, int r, double* out) {
+  TRY(sync_bytes(c, r));
   launch_energy(c->mc, c->shell, r, c->part, c->st);
   CK(cudaGetLastError());
   std::vector<double> h(c->part_n);
@@ -430,8 +457,59 @@ int sync_state_from_types(Ctx* c, int r, const uint8_t* host_types) {
   return VCSGC_OK;
 }
 
+int run_steps_fast(Ctx* c, long long n) {
+  const int G = 64;
+  if (n >= G && !c->graph) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < G; ++q) launch_lattice_step(c->lat, q, true, c->st);
+    launch_lattice_advance(c->lat, G, c->st);
+    cudaError_t e1 = cudaGetLastError();
+    CK(cudaStreamEndCapture(c->st, &g));
+    if (e1 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(c, VCSGC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e1));
+    }
+    cudaError_t e2 = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return fail(c, VCSGC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(e2));
+    c->graph_steps = G;
+  }
+  while (n >= G) {
+    CK(cudaGraphLaunch(c->graph, c->st));
+    c->h_base += G;
+    n -= G;
+  }
+  if (n > 0) {
+    for (long long q = 0; q < n; ++q) launch_lattice_step(c->lat, (int)q, true, c->st);
+    launch_lattice_advance(c->lat, (int)n, c->st);
+    c->h_base += n;
+  }
+  CK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
+// apply the pending commit of the last proposed step (fused form)
+int flush(Ctx* c) {
+  if (!c->fast) return VCSGC_OK;
+  launch_lattice_step(c->lat, 0, false, c->st);
+  CK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
+// refresh the species bytes of replica r (or all when r < 0) from the bits
+int sync_bytes(Ctx* c, int r) {
+  if (!c->fast) return VCSGC_OK;
+  TRY(flush(c));
+  for (int q = 0; q < c->R; ++q)
+    if (r < 0 || q == r) launch_lattice_unpack(c->lat, c->types, q, c->st);
+  CK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
 int run_steps(Ctx* c, long long n) {
   if (n <= 0) return VCSGC_OK;
+  if (c->fast) return run_steps_fast(c, n);
   const int G = 64;
   if (n >= G) {
     if (!c->graph) {
@@ -523,6 +601,8 @@ int vcsgc_default_options(vcsgc_options* o) {
   o->device = -1;
   return VCSGC_OK;
 }
+
+static int setup_fast(Ctx* c, const std::vector<RepState>& hs);
 
 static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_eam_tables* E,
                      double phi, double kappa, double T, const vcsgc_options* o) {
@@ -676,7 +756,7 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
     });
     if (offs.empty() || (int)offs.size() > MAX_OFFSETS) return fail(c, VCSGC_ERR_INVALID_ARG, "unsupported r_c / a");
     c->K = (int)offs.size();
-    std::vector<int3> h3;
+    std::vector<int3>& h3 = c->offsets;
     std::vector<int> sh2, sz;
     int S = 0;
     for (size_t k = 0; k < offs.size(); ++k) {
@@ -688,6 +768,7 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
         ++S;
       }
       sz[S - 1]++;
+      c->offset_shell.push_back(S - 1);
       c->mc.shell_end[S - 1] = (int)k + 1;
     }
     c->mc.n_shells = S;
@@ -785,7 +866,77 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   }
   if (c->kind == 1 && c->R == 1) TRY(md_forces(c));
   TRY(check_device_error(c));
+  TRY(setup_fast(c, hs));
   return VCSGC_OK;
+}
+
+// The fused bit-packed form applies to a rigid lattice with one density
+// function and a BLOCKS or SUBLATTICE schedule.
+static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
+  if (c->kind != 0 || c->reembed || c->nx < 2) return VCSGC_OK;
+  if (c->sched_kind != VCSGC_SCHED_BLOCKS && c->sched_kind != VCSGC_SCHED_SUBLATTICE) return VCSGC_OK;
+  const int S = c->mc.n_shells;
+  if (S > LAT_MAX_SH) return VCSGC_OK;
+  LatArgs& l = c->lat;
+  int hmax = 0;
+  for (const int3& h : c->offsets) hmax = std::max(hmax, std::abs(h.x));
+  if (hmax > LAT_HALO) return VCSGC_OK;
+  for (int b = 0; b < 2; ++b) {
+    int nr = 0;
+    for (size_t k = 0; k < c->offsets.size(); ++k) {
+      const int3 h = c->offsets[k];
+      // neighbour row: floor((2Y + b + hy) / 2) - Y
+      const int dy = (int)std::floor((b + h.y) / 2.0), dz = (int)std::floor((b + h.z) / 2.0);
+      int q = 0;
+      while (q < nr && (l.rows[b][q].dy != dy || l.rows[b][q].dz != dz)) ++q;
+      if (q == nr) {
+        if (nr == LAT_MAX_ROWS) return VCSGC_OK;
+        l.rows[b][q].dy = dy;
+        l.rows[b][q].dz = dz;
+        for (int s = 0; s < LAT_MAX_SH; ++s) l.rows[b][q].mask[s] = 0u;
+        ++nr;
+      }
+      l.rows[b][q].mask[c->offset_shell[k]] |= 1u << (h.x + hmax);
+    }
+    l.n_rows[b] = nr;
+  }
+  std::vector<double> tab(1 + 3 * S);
+  CK(cudaMemcpyAsync(tab.data(), c->shell_tab, sizeof(double) * tab.size(), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  l.C = tab[0];
+  for (int s = 0; s < LAT_MAX_SH; ++s) l.G[s] = s < S ? tab[1 + s] : 0.0;
+  l.hmax = hmax;
+  l.nx = c->nx;
+  l.ny = c->ny;
+  l.nz = c->nz;
+  l.W = (2 * c->nx + 2 * LAT_HALO + 31) / 32;
+  l.rep_words = (long long)c->ny * c->nz * l.W;
+  TRY(dalloc(c, &l.bits, (size_t)(c->R * l.rep_words + 1)));
+  TRY(dalloc(c, &l.acc, (size_t)c->R * 3));
+  TRY(dalloc(c, &l.n_start, (size_t)c->R * 2));
+  TRY(dalloc(c, &l.pend, (size_t)c->R * c->dmax));
+  TRY(dalloc(c, &l.ctl, 1));
+  CK(cudaMemsetAsync(l.bits, 0, sizeof(unsigned long long) * (c->R * l.rep_words + 1), c->st));
+  CK(cudaMemsetAsync(l.acc, 0, sizeof(StepAcc) * c->R * 3, c->st));
+  CK(cudaMemsetAsync(l.pend, 0xFF, sizeof(int) * c->R * c->dmax, c->st));
+  CK(cudaMemsetAsync(l.ctl, 0, sizeof(LatCtl), c->st));
+  std::vector<long long> ns(2 * c->R, 0);
+  for (int r = 0; r < c->R; ++r) ns[2 * r] = hs[r].n;
+  CK(cudaMemcpyAsync(l.n_start, ns.data(), sizeof(long long) * ns.size(), cudaMemcpyHostToDevice, c->st));
+  // fin_step = -1: no step finalised yet
+  std::vector<RepState> rs(c->R);
+  CK(cudaMemcpyAsync(rs.data(), c->rs, sizeof(RepState) * c->R, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (auto& s : rs) s.fin_step = -1;
+  CK(cudaMemcpyAsync(c->rs, rs.data(), sizeof(RepState) * c->R, cudaMemcpyHostToDevice, c->st));
+  c->fast = true;
+  fill_args(c);
+  for (int r = 0; r < c->R; ++r) launch_lattice_pack(l, c->types, r, c->st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  c->h_base = 0;
+  drop_graph(c);
+  return check_device_error(c);
 }
 
 static void destroy(Ctx* c) {
@@ -878,6 +1029,7 @@ int vcsgc_hybrid(void* ctx, int64_t n_cycles, int64_t n_md, int64_t n_mc) {
 int observables(void* ctx, int32_t r, vcsgc_observables* o) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !o || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  TRY(flush(c));
   TRY(check_device_error(c));
   RepState s;
   CK(cudaMemcpyAsync(&s, c->rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, c->st));
@@ -910,6 +1062,7 @@ int observables(void* ctx, int32_t r, vcsgc_observables* o) {
 int vcsgc_get_types(void* ctx, int32_t r, uint8_t* out) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  TRY(sync_bytes(c, r));
   CK(cudaMemcpyAsync(out, c->types + (long long)r * c->N, c->N, cudaMemcpyDeviceToHost, c->st));
   return check_device_error(c);
 }
@@ -919,7 +1072,17 @@ int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
   if (!c || !in || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   for (long long i = 0; i < c->N; ++i)
     if (in[i] > 1) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
+  TRY(flush(c));
   CK(cudaMemcpyAsync(c->types + (long long)r * c->N, in, c->N, cudaMemcpyHostToDevice, c->st));
+  if (c->fast) {
+    long long nb = 0;
+    for (long long i = 0; i < c->N; ++i) nb += in[i];
+    launch_lattice_pack(c->lat, c->types, r, c->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->lat.n_start + 2 * r + (c->h_base & 1), &nb, sizeof(long long),
+                       cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
   TRY(sync_state_from_types(c, r, in));
   c->forces_valid = false;
   return check_device_error(c);
@@ -948,7 +1111,12 @@ int vcsgc_delta_e(void* ctx, int32_t r, const int64_t* sites, int64_t n, double*
     c->sites_cap = (int)n;
   }
   CK(cudaMemcpyAsync(c->sites_buf, s32.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->st));
-  launch_delta_e_list(c->mc, c->shell, c->reembed, r, c->sites_buf, (int)n, c->de_buf, c->st);
+  if (c->fast) {
+    TRY(flush(c));
+    launch_lattice_delta_e(c->lat, r, c->sites_buf, (int)n, c->de_buf, c->st);
+  } else {
+    launch_delta_e_list(c->mc, c->shell, c->reembed, r, c->sites_buf, (int)n, c->de_buf, c->st);
+  }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(out, c->de_buf, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
   return check_device_error(c);
@@ -1024,10 +1192,20 @@ int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_com
   for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(ev[0], c->st));
   for (int64_t q = 0; q < n; ++q) {
-    launch_colour_step(c->mc, c->shell, c->reembed, c->st, 1);
-    CK(cudaEventRecord(ev[2 * q + 1], c->st));
-    launch_colour_step(c->mc, c->shell, c->reembed, c->st, 2);
-    CK(cudaEventRecord(ev[2 * q + 2], c->st));
+    if (c->fast) {
+      launch_lattice_step(c->lat, (int)q, true, c->st);
+      CK(cudaEventRecord(ev[2 * q + 1], c->st));
+      CK(cudaEventRecord(ev[2 * q + 2], c->st));
+    } else {
+      launch_colour_step(c->mc, c->shell, c->reembed, c->st, 1);
+      CK(cudaEventRecord(ev[2 * q + 1], c->st));
+      launch_colour_step(c->mc, c->shell, c->reembed, c->st, 2);
+      CK(cudaEventRecord(ev[2 * q + 2], c->st));
+    }
+  }
+  if (c->fast) {
+    launch_lattice_advance(c->lat, (int)n, c->st);
+    c->h_base += n;
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));

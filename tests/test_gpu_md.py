@@ -1,0 +1,151 @@
+"""EAM forces, BAOAB MD and hybrid MC/MD of the CUDA path against the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1012_5082_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_1012_5082_gb300 import vcsgc
+    return vcsgc
+
+
+def perturbed(n_cells, sigma, seed):
+    lat = I.bcc_lattice(n_cells, n_cells, n_cells)
+    rng = np.random.default_rng(seed)
+    return I.Lattice(x=lat.x + rng.normal(0, sigma, lat.n), y=lat.y + rng.normal(0, sigma, lat.n),
+                     z=lat.z + rng.normal(0, sigma, lat.n), box=lat.box)
+
+
+@pytest.mark.parametrize("dens_b", [1.0, 1.25])
+def test_forces_match(V, dens_b):
+    tab = I.eam_tables(I.EAMParams(dens_scale=(1.0, dens_b)))
+    lat = perturbed(6, 0.1, 3)
+    t = I.random_types(lat.n, 80, seed=4)
+    orc = O.System(lat, t, tab)
+    g = V.Context(lat, t, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_SPATIAL, sched=(2, 2, 2, 2, 2, 2))
+    Fg, Fo = g.forces(), orc.forces()
+    for a in range(3):
+        assert np.max(np.abs(Fg[a] - Fo[a])) < 1e-10
+    assert abs(g.energy() - orc.energy_full()) < 1e-9
+    g.close()
+
+
+def _md_pair(V, lat, t, tab, gamma, T, dt, seed=7):
+    v = I.maxwell_velocities(t, T, seed=seed)
+    orc = O.System(lat, t, tab)
+    orc.set_md(v, (I.MASS_A, I.MASS_B), dt, gamma, T, 99)
+    g = V.Context(lat, t, tab, -2.0, 1000.0, T, schedule=V.SCHED_SPATIAL, sched=(2, 2, 2, 2, 2, 2),
+                  dt=dt, gamma=gamma, T_md=T, md_seed=99)
+    g.set_velocities(v)
+    return orc, g
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.02])
+def test_md_trajectory_matches(V, gamma):
+    """NVE (gamma = 0) and Langevin (same Philox noise) trajectories agree
+    with the oracle's to rounding over 40 steps, across neighbour rebuilds."""
+    tab = I.eam_tables()
+    lat = perturbed(6, 0.05, 5)
+    t = I.random_types(lat.n, 50, seed=6)
+    orc, g = _md_pair(V, lat, t, tab, gamma, 900.0, 2.0)
+    orc.md_steps(40)
+    g.md_steps(40)
+    xo = orc.md_state()
+    xg = g.md_state()
+    for a in range(3):
+        d = xg[a] - xo[a]
+        d -= lat.box[a] * np.round(d / lat.box[a])
+        assert np.max(np.abs(d)) < 1e-8
+        assert np.max(np.abs(xg[3 + a] - xo[3 + a])) < 1e-9
+    assert abs(g.kinetic_energy() - orc.kinetic_energy()) < 1e-8
+    g.close()
+
+
+def test_nve_energy_conserved_on_gpu(V):
+    tab = I.eam_tables()
+    lat = perturbed(8, 0.0, 1)
+    t = I.random_types(lat.n, 60, seed=2)
+    g = V.Context(lat, t, tab, -2.0, 1000.0, 300.0, schedule=V.SCHED_SPATIAL, sched=(2, 2, 2, 2, 2, 2),
+                  dt=1.0, gamma=0.0)
+    g.set_velocities(I.maxwell_velocities(t, 600.0, seed=3))
+    e0 = g.energy() + g.kinetic_energy()
+    es = []
+    for _ in range(10):
+        g.md_steps(50)
+        es.append(g.energy() + g.kinetic_energy())
+    es = np.array(es) - e0
+    assert np.max(np.abs(es)) / lat.n < 2e-5
+    assert abs(np.polyfit(np.arange(10) * 50.0, es / lat.n, 1)[0]) * 500 < 1e-5
+    g.close()
+
+
+def test_langevin_temperature(V):
+    tab = I.eam_tables()
+    lat = perturbed(8, 0.0, 1)
+    t = np.zeros(lat.n, np.uint8)
+    g = V.Context(lat, t, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_SPATIAL, sched=(2, 2, 2, 2, 2, 2),
+                  dt=2.0, gamma=0.02, T_md=700.0)
+    g.set_velocities(I.maxwell_velocities(t, 50.0, seed=1))
+    g.md_steps(400)
+    temps = []
+    for _ in range(30):
+        g.md_steps(10)
+        temps.append(2 * g.kinetic_energy() / (3 * lat.n * I.KB_EV))
+    assert abs(np.mean(temps) - 700.0) < 40.0
+    g.close()
+
+
+def test_hybrid_cycles_match(V):
+    """Hybrid MC/MD (Sec. IV A): MD steps, then colour steps on the frozen
+    positions with velocity rescaling of flipped atoms; species bit-exact."""
+    tab = I.eam_tables()
+    lat = perturbed(6, 0.05, 9)
+    t = I.random_types(lat.n, 20, seed=10)
+    T = 900.0
+    v = I.maxwell_velocities(t, T, seed=11)
+    orc = O.System(lat, t, tab)
+    orc.set_params(-3.0, 50.0, T, c0=0.05, seed=42)
+    orc.schedule_spatial((2, 2, 2), (2, 2, 2))
+    orc.set_md(v, (I.MASS_A, I.MASS_B), 2.0, 0.01, T, 99)
+    g = V.Context(lat, t, tab, -3.0, 50.0, T, seed=42, c0=0.05, schedule=V.SCHED_SPATIAL,
+                  sched=(2, 2, 2, 2, 2, 2), dt=2.0, gamma=0.01, T_md=T, md_seed=99)
+    g.set_velocities(v)
+    for _ in range(4):
+        g.hybrid(1, 5, 150)
+        orc.hybrid_cycles(1, 5, 150)
+        if orc.obs()["near_ties"]:
+            break
+        assert np.array_equal(g.types(), orc.types)
+    og, oo = g.observables(), orc.obs()
+    if oo["near_ties"] == 0:
+        assert og["flips"] == oo["flips"] and og["flips"] > 0
+        xo, xg = orc.md_state(), g.md_state()
+        assert np.max(np.abs(xg[3] - xo[3])) < 1e-8
+    g.close()
+
+
+def test_nanocrystal_mc_and_md(V):
+    """A small periodic Voronoi nanocrystal: explicit-position dE and forces
+    against the oracle, and a short hybrid run without errors."""
+    tab = I.eam_tables()
+    lat = I.nanocrystal(40.0, 4, seed=12)
+    t = I.random_types(lat.n, lat.n // 100, seed=13)
+    orc = O.System(lat, t, tab)
+    g = V.Context(lat, t, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_SPATIAL, sched=(2, 2, 2, 2, 2, 2))
+    sites = np.arange(0, lat.n, 7)
+    de_g = g.delta_e(sites)
+    de_o = np.array([orc.delta_e(int(i)) for i in sites])
+    assert np.max(np.abs(de_g - de_o)) < 1e-10
+    Fg, Fo = g.forces(), orc.forces()
+    for a in range(3):
+        assert np.max(np.abs(Fg[a] - Fo[a])) < 1e-9
+    g.set_velocities(I.maxwell_velocities(t, 700.0, seed=14))
+    g.hybrid(2, 10, 50)
+    o = g.observables()
+    assert o["steps"] == 100 and o["trials"] > 0
+    g.close()
