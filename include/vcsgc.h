@@ -234,6 +234,30 @@ int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_com
  * i, the neighbour indices in out[0..count) (count <= K).  For tests. */
 int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* count);
 
+/* Neighbour-list build that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc when they need a list, for example code that runs while another
+ * framework's caching allocator holds nearly all device memory, or code with
+ * a fixed memory budget.  It builds the same cell-binned full list as a
+ * context does for explicit positions.
+ *   In:  n positions as DEVICE arrays d_x, d_y, d_z (doubles, inside the
+ *        periodic box box[0..2], a HOST array), list radius rl (Angstrom).
+ *   Out: DEVICE arrays owned by the caller: d_nbr[n][K] (int32, row i lists
+ *        the atoms within rl of atom i under the minimum image, cell order,
+ *        -1 padded) and d_cnt[n] (row lengths).
+ * Work runs on `stream` (NULL: legacy default stream); the call waits for it.
+ * Its working space is one static device array of about 2.8 MB that every
+ * GPU loading this library holds until the process exits.  The first call on
+ * a device looks up that array's address (make it before any stream
+ * capture).  All calls share the array, so calls that overlap on the GPU
+ * race.  Limits: n <= 262144; each box length > 2 rl with at least 3 and, in
+ * total, at most 65536 binning cells of side >= rl.
+ * Errors: INVALID_ARG beyond those limits or for null pointers; OVERFLOW when
+ * a row had more than K neighbours (that row is truncated to K); CUDA. */
+int vcsgc_neighbour_list_noalloc(int64_t n, const double* d_x, const double* d_y,
+                                 const double* d_z, const double box[3], double rl, int32_t K,
+                                 int32_t* d_nbr, int32_t* d_cnt, void* stream);
+
 /* Text of the last error of ctx (or of the last failed vcsgc_init when ctx
  * is NULL).  Valid until the next call on the same context. */
 const char* vcsgc_last_error(void* ctx);

@@ -64,7 +64,7 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "md_steps", "vcsgc_hybrid", "observables", "vcsgc_get_types", "vcsgc_set_types",
            "vcsgc_get_rho", "vcsgc_delta_e", "vcsgc_energy", "vcsgc_forces", "vcsgc_get_md",
            "vcsgc_set_velocities", "vcsgc_kinetic_energy", "vcsgc_neighbours", "vcsgc_last_error",
-           "vcsgc_free", "vcsgc_profile_steps"]
+           "vcsgc_free", "vcsgc_profile_steps", "vcsgc_neighbour_list_noalloc"]
 
 
 def lib():
@@ -96,6 +96,7 @@ def lib():
             "vcsgc_kinetic_energy": (I32, [P, P]),
             "vcsgc_neighbours": (I32, [P, I64, P, I32, P]),
             "vcsgc_profile_steps": (I32, [P, I64, P, P]),
+            "vcsgc_neighbour_list_noalloc": (I32, [I64, P, P, P, P, D, I32, P, P, P]),
             "vcsgc_last_error": (C.c_char_p, [P]),
             "vcsgc_free": (None, [P]),
         }
@@ -153,6 +154,16 @@ def observables(ctx, replica=0):
 
 def vcsgc_free(ctx):
     lib().vcsgc_free(ctx)
+
+
+def vcsgc_neighbour_list_noalloc(n, d_x, d_y, d_z, box, rl, K, d_nbr, d_cnt, stream=None):
+    """Device pointers in and out (integers, e.g. torch tensor data_ptr());
+    returns the status code."""
+    b = (C.c_double * 3)(*[float(v) for v in box])
+    return lib().vcsgc_neighbour_list_noalloc(int(n), C.c_void_p(d_x), C.c_void_p(d_y),
+                                              C.c_void_p(d_z), b, float(rl), int(K),
+                                              C.c_void_p(d_nbr), C.c_void_p(d_cnt),
+                                              C.c_void_p(stream) if stream else None)
 
 
 # ----------------------------------------------------------- convenience
