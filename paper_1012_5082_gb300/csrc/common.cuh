@@ -166,6 +166,7 @@ struct StepAcc {
   double sum_de;
   unsigned done;
   int ties;
+  int sb[8];  // fused lattice form: sum over accepted moves of s_i b_s (per shell)
 };
 
 // Everything the colour-step kernels read, passed by value.

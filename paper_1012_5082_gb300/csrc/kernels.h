@@ -58,6 +58,14 @@ struct LatRow {
   uint32_t mask[LAT_MAX_SH];    // window bits of each shell
 };
 
+// per-replica constants of the FP32 screen of the local test
+struct LatRep {
+  float cpd32;   // C + dmu0 (eV)
+  float beta32;  // 1/(kB T)
+  float dx;      // absolute bound on |X32 - X| from the rounding of the inputs and sums
+  float pad;
+};
+
 struct LatCtl {
   long long base_step;          // step of the next launch with j = 0
 };
@@ -70,13 +78,22 @@ struct LatArgs {
   long long rep_words;          // nz * ny * W
   unsigned long long* bits;     // [R][nz][ny][W] (+1 pad word)
   int hmax;                     // largest |half-lattice offset| along x
+  int n_shells;                 // shells in use (<= LAT_MAX_SH)
+  int d_uniform;                // domains per colour (SUBLATTICE)
   int n_rows[2];
   LatRow rows[2][LAT_MAX_ROWS];
   double C;                     // pair part of dE(A->B) with no B neighbour
   double G[LAT_MAX_SH];         // change per B neighbour in each shell
+  float G32[LAT_MAX_SH];
   const double* dF;             // [N] F_B(rho_i) - F_A(rho_i)
+  const float* dF32;            // [N] the same in FP32
+  int df_uniform;               // every site has dF_i = dF0 (perfect lattice)
+  double dF0;
+  const LatRep* lrep;           // [R]
   // schedule
   int sublattice, qx, qy, qz;
+  int nxq, nyq;                 // nx / qx, ny / qy
+  float rcp_nx, rcp_ny, rcp_qx, rcp_qy, rcp_nxq, rcp_nyq;  // 1/d for fdiv
   int n_colours;
   const int* col_start;
   const int* dom_start;
@@ -94,6 +111,7 @@ struct LatArgs {
 
 void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st);
+void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 void launch_lattice_pack(const LatArgs& a, const uint8_t* types, int r, cudaStream_t st);
 void launch_lattice_unpack(const LatArgs& a, uint8_t* types, int r, cudaStream_t st);
 void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st);

@@ -30,13 +30,22 @@
 
 namespace vcsgc {
 
+// n / d for 0 <= n < 2^22 by a float reciprocal and one correction: the
+// float quotient is within 2^-23 relative of n/d < 2^22, so off by at most 1
+__device__ __forceinline__ int fdiv(int n, int d, float rcp) {
+  int q = __float2int_rz(__int2float_rn(n) * rcp);
+  const int r = n - q * d;
+  q += (r < 0) ? -1 : (r >= d ? 1 : 0);
+  return q;
+}
+
 __device__ __forceinline__ void decode_site(const LatArgs& a, int i, int& X, int& Y, int& Z, int& b) {
   b = i & 1;
   const int cell = i >> 1;
-  X = cell % a.nx;
-  const int q = cell / a.nx;
-  Y = q % a.ny;
-  Z = q / a.ny;
+  const int q = fdiv(cell, a.nx, a.rcp_nx);
+  X = cell - q * a.nx;
+  Z = fdiv(q, a.ny, a.rcp_ny);
+  Y = q - Z * a.ny;
 }
 
 __device__ __forceinline__ unsigned long long* row_ptr(const LatArgs& a, int r, int Y, int Z) {
@@ -80,31 +89,100 @@ __device__ __forceinline__ void xor_copies(const LatArgs& a, unsigned long long*
   }
 }
 
-// dE of flipping site i of replica r on the effective state
-__device__ __forceinline__ double lattice_delta_e(const LatArgs& a, int r, int i, uint32_t gm, int& t) {
-  int X, Y, Z, b;
-  decode_site(a, i, X, Y, Z, b);
+// Per-shell B counts of site i of replica r on the effective state, its
+// species t, and the half-coordinate bookkeeping (NS shells).
+// NR > 0: exactly NR rows per basis, unrolled so that every row load is in
+// flight at once; NR = 0: runtime row count.
+template <int NS, int NR>
+__device__ __forceinline__ void lattice_counts_at(const LatArgs& a, int r, int X, int Y, int Z, int b,
+                                                  uint32_t gm, int (&cnt)[NS], int& t) {
   const int H = 2 * X + b;
-  int cnt[LAT_MAX_SH];
 #pragma unroll
-  for (int s = 0; s < LAT_MAX_SH; ++s) cnt[s] = 0;
-  const int nr = a.n_rows[b];
-  for (int q = 0; q < nr; ++q) {
-    const LatRow& rw = a.rows[b][q];
+  for (int s = 0; s < NS; ++s) cnt[s] = 0;
+  const LatRow* rows = a.rows[b];
+  const int nr = NR > 0 ? NR : a.n_rows[b];
+#pragma unroll
+  for (int q = 0; q < (NR > 0 ? NR : LAT_MAX_ROWS); ++q) {
+    if (NR == 0 && q >= nr) break;
+    const LatRow& rw = rows[q];
     int yy = Y + rw.dy, zz = Z + rw.dz;
     yy = yy < 0 ? yy + a.ny : (yy >= a.ny ? yy - a.ny : yy);
     zz = zz < 0 ? zz + a.nz : (zz >= a.nz ? zz - a.nz : zz);
     const uint32_t win = window(row_ptr(a, r, yy, zz), H, a.hmax, gm);
 #pragma unroll
-    for (int s = 0; s < LAT_MAX_SH; ++s) cnt[s] += __popc(win & rw.mask[s]);
+    for (int s = 0; s < NS; ++s) cnt[s] += __popc(win & rw.mask[s]);
   }
   t = own_bit(row_ptr(a, r, Y, Z), H, gm);
+}
+
+template <int NS, int NR>
+__device__ __forceinline__ void lattice_counts(const LatArgs& a, int r, int i, uint32_t gm,
+                                               int (&cnt)[NS], int& t) {
+  int X, Y, Z, b;
+  decode_site(a, i, X, Y, Z, b);
+  lattice_counts_at<NS, NR>(a, r, X, Y, Z, b, gm, cnt, t);
+}
+
+// dE of flipping the site (FP64): the A->B value C + sum_s b_s G_s + dF_i,
+// negated for B->A
+template <int NS>
+__device__ __forceinline__ double lattice_de64(const LatArgs& a, const int (&cnt)[NS], int i, int t) {
   double de = a.C;
 #pragma unroll
-  for (int s = 0; s < LAT_MAX_SH; ++s) de = fma((double)cnt[s], a.G[s], de);
-  const double dfi = a.dF[i];
-  de += dfi;
+  for (int s = 0; s < NS; ++s) de = fma((double)cnt[s], a.G[s], de);
+  de += a.df_uniform ? a.dF0 : a.dF[i];
   return t ? -de : de;
+}
+
+template <int NS>
+__device__ __forceinline__ double lattice_delta_e(const LatArgs& a, int r, int i, uint32_t gm, int& t) {
+  int cnt[NS];
+  lattice_counts<NS, 0>(a, r, i, gm, cnt, t);
+  return lattice_de64<NS>(a, cnt, i, t);
+}
+
+// Local Metropolis decision of trial site i, identical to the FP64 decision
+// u < min{1, exp(-X)}, X = beta (dE + s dmu0).  X is first formed in FP32
+// from the integer counts: X32 = +-beta (C + dmu0 + sum_s b_s G_s + dF_i).
+// lr.dx bounds |X32 - X| (FP32 rounding of each input and partial sum,
+// derived on the host from the magnitudes of the terms); only when X32 and
+// that bound cannot settle the decision is X recomputed in FP64 (rare).
+template <int NS>
+__device__ __forceinline__ bool lattice_accept(const LatArgs& a, const LatRep& lr, const RepParams& p,
+                                               const int (&cnt)[NS], int i, int t, uint64_t u53,
+                                               int* tie) {
+  float s32 = lr.cpd32;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) s32 = fmaf((float)cnt[s], a.G32[s], s32);
+  s32 += a.df_uniform ? 0.0f : a.dF32[i];
+  const float x32 = (t ? -lr.beta32 : lr.beta32) * s32;
+  if (!isfinite(x32)) atomicOr(a.err, ERRF_NONFINITE);
+  const float dx = lr.dx + fabsf(x32) * 4.76837158203125e-07f;  // + |X| 2^-21
+  bool decided = false, acc = false;
+  if (x32 <= -2.0f * dx) {
+    decided = true;
+    acc = true;
+  } else if (u53 != 0) {
+    if (x32 >= 80.0f + dx) {
+      decided = true;
+    } else {
+      const float pf = expf(-x32) * 9007199254740992.0f;  // p * 2^53
+      const float uf = (float)u53;
+      const float m = dx + 9.5367431640625e-07f;          // + 2^-20 (expf, products)
+      if (uf * (1.0f + 1.1920929e-07f) < pf * (1.0f - m)) {
+        decided = true;
+        acc = true;
+      } else if (uf * (1.0f - 1.1920929e-07f) > pf * (1.0f + m)) {
+        decided = true;
+      }
+    }
+  }
+  if (!decided) {
+    const double de = lattice_de64<NS>(a, cnt, i, t);
+    const double sg = t ? -1.0 : 1.0;
+    acc = metropolis(p.beta * fma(sg, p.dmu0, de), u53, tie);
+  }
+  return acc;
 }
 
 __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long step, uint64_t* ug53) {
@@ -113,71 +191,118 @@ __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long
   return (int)below64(w.x, w.y, (uint64_t)a.n_colours);
 }
 
-template <bool PROPOSE>
+template <bool PROPOSE, int NS, int NR>
 __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
   const int r = blockIdx.y;
   const long long k = a.ctl->base_step + j;
   const long long kp = k - 1;
   const RepParams p = a.rp[r];
   const int d = blockIdx.x * LAT_BLOCK + threadIdx.x;
+  __shared__ int s_g[2];  // [0] = G_{k-1}, [1] = near-tie of that decision
 
-  // 1. global decision of step k-1
-  bool Gp = false;
-  int tie_p = 0, dnp = 0, naccp = 0, cp = 0;
-  long long np = 0;
-  if (kp >= 0) {
-    const StepAcc* Ap = a.acc + r * 3 + (int)(kp % 3);
-    naccp = *(volatile const int*)&Ap->nacc;
-    dnp = *(volatile const int*)&Ap->dn;
-    np = a.n_start[r * 2 + (int)(kp & 1)];
-    uint64_t ug53;
-    cp = lat_colour(a, p.key, kp, &ug53);
-    if (naccp > 0) {
-      const double Y = p.beta * p.kappa_p * (double)dnp * ((double)dnp + 2.0 * ((double)np - p.n0));
-      Gp = metropolis(Y, ug53, &tie_p);
+  // 1. global decision of step k-1: one thread per block, FP64
+  if (threadIdx.x == 0) {
+    int G = 0, tie = 0;
+    if (kp >= 0) {
+      const int naccp = *(volatile const int*)&a.acc[r * 3 + (int)(kp % 3)].nacc;
+      if (naccp > 0) {
+        const int dnp = *(volatile const int*)&a.acc[r * 3 + (int)(kp % 3)].dn;
+        const long long np = a.n_start[r * 2 + (int)(kp & 1)];
+        uint64_t ug53;
+        lat_colour(a, p.key, kp, &ug53);
+        const double Y = p.beta * p.kappa_p * (double)dnp * ((double)dnp + 2.0 * ((double)np - p.n0));
+        G = metropolis(Y, ug53, &tie) ? 1 : 0;
+      }
+    }
+    s_g[0] = G;
+    s_g[1] = tie;
+  }
+
+  // 2. propose inputs that do not depend on G: colour, site, random word
+  int site = -1, sX = 0, sY = 0, sZ = 0, sb_ = 0;
+  uint4 w = make_uint4(0, 0, 0, 0);
+  if (PROPOSE) {
+    const int c = lat_colour(a, p.key, k, nullptr);
+    const int D = a.sublattice ? a.d_uniform : a.col_start[c + 1] - a.col_start[c];
+    if (d < D) {
+      w = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)((uint64_t)k >> 32), (uint32_t)d, TAG_TRIAL), p.key);
+      if (a.sublattice) {
+        // colour c = (((pz qy + py) qx + px) 2 + b); trial d runs over the
+        // colour's sites in ascending index: d = (kz nyq + ky) nxq + kx
+        const int b = c & 1;
+        const int pc = c >> 1;
+        const int pq = fdiv(pc, a.qx, a.rcp_qx);
+        const int px = pc - pq * a.qx;
+        const int pz = fdiv(pq, a.qy, a.rcp_qy);
+        const int py = pq - pz * a.qy;
+        const int dq = fdiv(d, a.nxq, a.rcp_nxq);
+        const int kx = d - dq * a.nxq;
+        const int kz = fdiv(dq, a.nyq, a.rcp_nyq);
+        const int ky = dq - kz * a.nyq;
+        sX = px + a.qx * kx;
+        sY = py + a.qy * ky;
+        sZ = pz + a.qz * kz;
+        sb_ = b;
+        site = ((sZ * a.ny + sY) * a.nx + sX) * 2 + b;
+      } else {
+        const int g = a.col_start[c] + d;
+        const int base = a.dom_start[g];
+        const int size = a.dom_start[g + 1] - base;
+        site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
+        decode_site(a, site, sX, sY, sZ, sb_);
+      }
     }
   }
+  __syncthreads();
+  const bool Gp = s_g[0] != 0;
   const uint32_t gm = Gp ? 0xFFFFFFFFu : 0u;
 
-  // 2. commit this thread's pending flip of step k-1
+  // 3. commit this thread's pending flip of step k-1
   if (d < a.dmax) {
     int* slot = a.pend + (long long)r * a.dmax + d;
     const int ps = *slot;
     if (ps >= 0) {
-      int X, Y, Z, b;
-      decode_site(a, ps, X, Y, Z, b);
-      xor_copies(a, row_ptr(a, r, Y, Z), 2 * X + b, Gp, true);
+      // slot = row * 2048 + H (row = Z ny + Y, H = 2 X + b)
+      xor_copies(a, a.bits + (long long)r * a.rep_words + (long long)(ps >> 11) * a.W, ps & 2047, Gp, true);
       *slot = -1;
     }
   }
 
-  // 3. finalise step k-1 and clear the accumulator of step k+1
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    RepState* S = a.rs + r;
-    if (kp >= 0 && S->fin_step < kp) {
-      const StepAcc* Ap = a.acc + r * 3 + (int)(kp % 3);
-      const int D = a.col_start[cp + 1] - a.col_start[cp];
-      S->trials += D;
-      S->local_acc += naccp;
-      S->near_ties += *(volatile const int*)&Ap->ties + tie_p;
+  // 4. finalise step k-1 (second warp of block 0, off the first warp's
+  //    path) and clear the accumulator of step k+1; whole-struct accesses
+  if (blockIdx.x == 0 && threadIdx.x == 32) {
+    RepState S = a.rs[r];
+    if (kp >= 0 && S.fin_step < kp) {
+      const StepAcc A = a.acc[r * 3 + (int)(kp % 3)];
+      const long long np = a.n_start[r * 2 + (int)(kp & 1)];
+      const int cp = lat_colour(a, p.key, kp, nullptr);
+      const int D = a.sublattice ? a.d_uniform : a.col_start[cp + 1] - a.col_start[cp];
+      S.trials += D;
+      S.local_acc += A.nacc;
+      S.near_ties += A.ties + s_g[1];
       long long nn = np;
-      if (naccp > 0) {
-        S->global_trials += 1;
+      if (A.nacc > 0) {
+        S.global_trials += 1;
         if (Gp) {
-          S->global_acc += 1;
-          S->flips += naccp;
-          nn = np + dnp;
-          S->energy += *(volatile const double*)&Ap->sum_de;
+          S.global_acc += 1;
+          S.flips += A.nacc;
+          nn = np + A.dn;
+          // sum over the accepted moves of s_i (C + sum_s b_s G_s + dF_i)
+          double e = a.C * (double)A.dn;
+          for (int q = 0; q < NS; ++q) e = fma((double)A.sb[q], a.G[q], e);
+          e += a.df_uniform ? a.dF0 * (double)A.dn : A.sum_de;
+          S.energy += e;
         }
       }
-      S->n = nn;
+      S.n = nn;
       a.n_start[r * 2 + (int)(k & 1)] = nn;
       const double cc = (double)nn / (double)a.N;
-      S->sum_c += cc;
-      S->sum_c2 += cc * cc;
-      S->steps += 1;
-      S->step = k;
-      S->fin_step = kp;
+      S.sum_c += cc;
+      S.sum_c2 += cc * cc;
+      S.steps += 1;
+      S.step = k;
+      S.fin_step = kp;
+      a.rs[r] = S;
     }
     if (PROPOSE) {
       StepAcc* An = a.acc + r * 3 + (int)((k + 1) % 3);
@@ -185,79 +310,77 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
       An->nacc = 0;
       An->sum_de = 0.0;
       An->ties = 0;
+      for (int q = 0; q < NS; ++q) An->sb[q] = 0;
     }
   }
   if (!PROPOSE) return;
 
-  // 4. propose trial d of step k
-  const int c = lat_colour(a, p.key, k, nullptr);
-  const int g0 = a.col_start[c];
-  const int D = a.col_start[c + 1] - g0;
+  // 5. propose trial d of step k on the effective species
   int dn = 0, acc = 0, tie = 0;
-  double sde = 0.0;
-  if (d < D) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)((uint64_t)k >> 32), (uint32_t)d, TAG_TRIAL), p.key);
-    int site;
-    if (a.sublattice) {
-      // colour c = (((pz qy + py) qx + px) 2 + b); trial d runs over the
-      // colour's sites in ascending index: d = (kz nyq + ky) nxq + kx
-      const int b = c & 1;
-      const int pc = c >> 1;
-      const int px = pc % a.qx, py = (pc / a.qx) % a.qy, pz = pc / (a.qx * a.qy);
-      const int nxq = a.nx / a.qx, nyq = a.ny / a.qy;
-      const int kx = d % nxq, ky = (d / nxq) % nyq, kz = d / (nxq * nyq);
-      const int X = px + a.qx * kx, Y = py + a.qy * ky, Z = pz + a.qz * kz;
-      site = ((Z * a.ny + Y) * a.nx + X) * 2 + b;
-    } else {
-      const int g = g0 + d;
-      const int base = a.dom_start[g];
-      const int size = a.dom_start[g + 1] - base;
-      site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
-    }
-    int t;
-    const double de = lattice_delta_e(a, r, site, gm, t);
-    if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
-    const double sg = t ? -1.0 : 1.0;
-    const double X = p.beta * fma(sg, p.dmu0, de);
-    if (metropolis(X, top53(w.z, w.w), &tie)) {
-      int XX, YY, ZZ, bb;
-      decode_site(a, site, XX, YY, ZZ, bb);
-      xor_copies(a, row_ptr(a, r, YY, ZZ), 2 * XX + bb, false, true);  // set pending
-      a.pend[(long long)r * a.dmax + d] = site;
+  int sb[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) sb[q] = 0;
+  double sdf = 0.0;
+  if (site >= 0) {
+    int cnt[NS], t;
+    lattice_counts_at<NS, NR>(a, r, sX, sY, sZ, sb_, gm, cnt, t);
+    if (lattice_accept<NS>(a, a.lrep[r], p, cnt, site, t, top53(w.z, w.w), &tie)) {
+      const int H = 2 * sX + sb_;
+      xor_copies(a, row_ptr(a, r, sY, sZ), H, false, true);  // set pending
+      a.pend[(long long)r * a.dmax + d] = (sZ * a.ny + sY) * 2048 + H;
       acc = 1;
       dn = t ? -1 : 1;
-      sde = de;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) sb[q] = t ? -cnt[q] : cnt[q];
+      if (!a.df_uniform) sdf = t ? -a.dF[site] : a.dF[site];
     }
   }
-  // reduction of dn, accepts and sum dE (the paper's allgather of dc_i)
-  __shared__ int s_dn[LAT_BLOCK / 32], s_acc[LAT_BLOCK / 32], s_tie[LAT_BLOCK / 32];
-  __shared__ double s_de[LAT_BLOCK / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dn += __shfl_xor_sync(0xffffffffu, dn, o);
-    acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    tie += __shfl_xor_sync(0xffffffffu, tie, o);
-    sde += __shfl_xor_sync(0xffffffffu, sde, o);
-  }
+  // reduction of dn, accepts, per-shell sums and ties (the paper's
+  // allgather of dc_i); warps without an accept or a tie skip the shuffles
+  __shared__ int s_red[LAT_BLOCK / 32][NS + 3];
+  __shared__ double s_df[LAT_BLOCK / 32];
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { s_dn[wi] = dn; s_acc[wi] = acc; s_tie[wi] = tie; s_de[wi] = sde; }
+  const bool any = __ballot_sync(0xffffffffu, acc | tie) != 0u;
+  if (any) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dn += __shfl_xor_sync(0xffffffffu, dn, o);
+      acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      tie += __shfl_xor_sync(0xffffffffu, tie, o);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) sb[q] += __shfl_xor_sync(0xffffffffu, sb[q], o);
+      if (!a.df_uniform) sdf += __shfl_xor_sync(0xffffffffu, sdf, o);
+    }
+  }
+  if (l == 0) {
+    s_red[wi][0] = dn;
+    s_red[wi][1] = acc;
+    s_red[wi][2] = tie;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) s_red[wi][3 + q] = sb[q];
+    s_df[wi] = sdf;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int tdn = 0, tacc = 0, ttie = 0;
-    double tde = 0.0;
-    for (int q = 0; q < LAT_BLOCK / 32; ++q) {
-      tdn += s_dn[q];
-      tacc += s_acc[q];
-      ttie += s_tie[q];
-      tde += s_de[q];
+    int tot[NS + 3];
+#pragma unroll
+    for (int q = 0; q < NS + 3; ++q) tot[q] = 0;
+    double tdf = 0.0;
+    for (int w2 = 0; w2 < LAT_BLOCK / 32; ++w2) {
+#pragma unroll
+      for (int q = 0; q < NS + 3; ++q) tot[q] += s_red[w2][q];
+      if (!a.df_uniform) tdf += s_df[w2];
     }
-    if (tacc) {
-      StepAcc* A = a.acc + r * 3 + (int)(k % 3);
-      atomicAdd(&A->dn, tdn);
-      atomicAdd(&A->nacc, tacc);
-      atomicAdd(&A->sum_de, tde);
+    StepAcc* A = a.acc + r * 3 + (int)(k % 3);
+    if (tot[1]) {
+      atomicAdd(&A->dn, tot[0]);
+      atomicAdd(&A->nacc, tot[1]);
+#pragma unroll
+      for (int q = 0; q < NS; ++q)
+        if (tot[3 + q]) atomicAdd(&A->sb[q], tot[3 + q]);
+      if (!a.df_uniform) atomicAdd(&A->sum_de, tdf);
     }
-    if (ttie) atomicAdd(&a.acc[r * 3 + (int)(k % 3)].ties, ttie);
+    if (tot[2]) atomicAdd(&A->ties, tot[2]);
   }
 }
 
@@ -286,16 +409,37 @@ __global__ void k_lattice_unpack(LatArgs a, uint8_t* types, int r) {
   types[(long long)r * a.N + i] = (uint8_t)own_bit(row_ptr(a, r, Y, Z), 2 * X + b, 0u);
 }
 
+template <int NS>
 __global__ void k_lattice_delta_e(LatArgs a, int r, const int* sites, int n, double* out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   int t;
-  if (q < n) out[q] = lattice_delta_e(a, r, sites[q], 0u, t);
+  if (q < n) out[q] = lattice_delta_e<NS>(a, r, sites[q], 0u, t);
 }
 
-void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st) {
+template <int NS, int NR>
+static void step_ns(const LatArgs& a, int j, bool propose, cudaStream_t st) {
   const dim3 g((a.dmax + LAT_BLOCK - 1) / LAT_BLOCK, a.R);
-  if (propose) k_lattice_step<true><<<g, LAT_BLOCK, 0, st>>>(a, j);
-  else k_lattice_step<false><<<g, LAT_BLOCK, 0, st>>>(a, j);
+  if (propose) k_lattice_step<true, NS, NR><<<g, LAT_BLOCK, 0, st>>>(a, j);
+  else k_lattice_step<false, NS, NR><<<g, LAT_BLOCK, 0, st>>>(a, j);
+}
+
+__global__ void k_to_float(const double* in, float* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+void launch_to_float(const double* in, float* out, long long n, cudaStream_t st) {
+  k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+}
+
+// shells and neighbour rows as compile-time constants: the 5-shell, 13-row
+// BCC neighbourhood within r_c < sqrt(19) a/2 and the first-shell form are
+// unrolled; any other neighbourhood takes the runtime-count variant
+void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st) {
+  const int nr = a.n_rows[0] == a.n_rows[1] ? a.n_rows[0] : -1;
+  if (a.n_shells == 5 && nr == 13) step_ns<5, 13>(a, j, propose, st);
+  else if (a.n_shells == 1 && nr == 2) step_ns<1, 2>(a, j, propose, st);
+  else step_ns<LAT_MAX_SH, 0>(a, j, propose, st);
 }
 
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st) {
@@ -312,7 +456,7 @@ void launch_lattice_unpack(const LatArgs& a, uint8_t* types, int r, cudaStream_t
 }
 
 void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st) {
-  if (n > 0) k_lattice_delta_e<<<(n + 127) / 128, 128, 0, st>>>(a, r, sites, n, out);
+  if (n > 0) k_lattice_delta_e<LAT_MAX_SH><<<(n + 127) / 128, 128, 0, st>>>(a, r, sites, n, out);
 }
 
 }  // namespace vcsgc

@@ -57,6 +57,7 @@ struct Ctx {
   int* dom_sites = nullptr;
   int n_colours = 0, dmax = 0;
   long long n_domains = 0;
+  int sublattice_d = 0;            // domains per colour of a SUBLATTICE schedule
   RepParams* rp = nullptr;
   RepState* rs = nullptr;
   StepAcc* acc = nullptr;
@@ -400,6 +401,7 @@ int upload_schedule(Ctx* c, const Sched& S) {
   c->dmax = std::max(c->dmax, dmax);
   const int dpc = S.col[1] - S.col[0];
   c->steps_per_sweep = dpc > 0 ? std::max(1LL, (c->N + dpc / 2) / dpc) : 1;
+  c->sublattice_d = c->sched_kind == VCSGC_SCHED_SUBLATTICE ? dpc : 0;
   fill_args(c);
   return VCSGC_OK;
 }
@@ -874,6 +876,8 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
 // function and a BLOCKS or SUBLATTICE schedule.
 static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
   if (c->kind != 0 || c->reembed || c->nx < 2) return VCSGC_OK;
+  // index arithmetic of the fused form: sites < 2^22, rows < 2^20, 2 nx < 2048
+  if (c->N > (1LL << 22) || 2 * c->nx >= 2048 || (long long)c->ny * c->nz >= (1LL << 20)) return VCSGC_OK;
   if (c->sched_kind != VCSGC_SCHED_BLOCKS && c->sched_kind != VCSGC_SCHED_SUBLATTICE) return VCSGC_OK;
   const int S = c->mc.n_shells;
   if (S > LAT_MAX_SH) return VCSGC_OK;
@@ -904,8 +908,63 @@ static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
   CK(cudaMemcpyAsync(tab.data(), c->shell_tab, sizeof(double) * tab.size(), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
   l.C = tab[0];
-  for (int s = 0; s < LAT_MAX_SH; ++s) l.G[s] = s < S ? tab[1 + s] : 0.0;
+  for (int s = 0; s < LAT_MAX_SH; ++s) {
+    l.G[s] = s < S ? tab[1 + s] : 0.0;
+    l.G32[s] = (float)l.G[s];
+  }
+  // dF_i = F_B(rho_i) - F_A(rho_i): uniform on a perfect lattice
+  {
+    std::vector<double> dF(c->N);
+    CK(cudaMemcpyAsync(dF.data(), c->dF, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    bool uni = true;
+    double dmax = 0.0;
+    for (long long i = 0; i < c->N; ++i) {
+      if (dF[i] != dF[0]) uni = false;
+      dmax = std::max(dmax, std::fabs(dF[i]));
+    }
+    l.df_uniform = uni ? 1 : 0;
+    l.dF0 = dF[0];
+    float* df32 = nullptr;
+    TRY(dalloc(c, &df32, c->N));
+    launch_to_float(c->dF, df32, c->N, c->st);
+    CK(cudaGetLastError());
+    l.dF32 = df32;
+    // FP32 screen: per-replica constants and the bound on |X32 - X|
+    std::vector<int> zs(S, 0);
+    for (int sh : c->offset_shell) zs[sh]++;
+    double sumG = 0.0;
+    for (int s = 0; s < S; ++s) sumG += zs[s] * std::fabs(l.G[s]);
+    std::vector<LatRep> lr(c->R);
+    for (int r = 0; r < c->R; ++r) {
+      const RepParams& p = c->h_rp[r];
+      const double cpd = l.C + p.dmu0 + (uni ? l.dF0 : 0.0);
+      const double M = std::fabs(l.C) + std::fabs(p.dmu0) + sumG + dmax + std::fabs(cpd);
+      lr[r].cpd32 = (float)cpd;
+      lr[r].beta32 = (float)p.beta;
+      // (2 S + 3) roundings of at most 2^-24 M each, times beta, four-fold margin
+      lr[r].dx = (float)(4.0 * p.beta * (2 * S + 3) * std::ldexp(M, -24));
+      lr[r].pad = 0.0f;
+    }
+    LatRep* dlr = nullptr;
+    TRY(dalloc(c, &dlr, c->R));
+    CK(cudaMemcpyAsync(dlr, lr.data(), sizeof(LatRep) * c->R, cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    l.lrep = dlr;
+  }
   l.hmax = hmax;
+  l.n_shells = S;
+  l.rcp_nx = 1.0f / (float)c->nx;
+  l.rcp_ny = 1.0f / (float)c->ny;
+  if (c->sched_kind == VCSGC_SCHED_SUBLATTICE) {
+    l.nxq = c->nx / c->sched[0];
+    l.nyq = c->ny / c->sched[1];
+    l.rcp_qx = 1.0f / (float)c->sched[0];
+    l.rcp_qy = 1.0f / (float)c->sched[1];
+    l.rcp_nxq = 1.0f / (float)l.nxq;
+    l.rcp_nyq = 1.0f / (float)l.nyq;
+  }
+  l.d_uniform = c->sublattice_d;
   l.nx = c->nx;
   l.ny = c->ny;
   l.nz = c->nz;
