@@ -246,7 +246,7 @@ int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* c
  *        the atoms within rl of atom i under the minimum image, cell order,
  *        -1 padded) and d_cnt[n] (row lengths).
  * Work runs on `stream` (NULL: legacy default stream); the call waits for it.
- * Its working space is one static device array of about 2.8 MB that every
+ * Its working space is one static device array of about 6 MB that every
  * GPU loading this library holds until the process exits.  The first call on
  * a device looks up that array's address (make it before any stream
  * capture).  All calls share the array, so calls that overlap on the GPU

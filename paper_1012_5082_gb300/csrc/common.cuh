@@ -75,7 +75,8 @@ struct Spline {
 };
 
 struct Tables {
-  Spline sp[7];  // 0..2 pair AA AB BB, 3..4 density A B, 5..6 embedding A B
+  Spline sp[7];   // 0..2 pair AA AB BB, 3..4 density A B, 5..6 embedding A B
+  Spline dsp[7];  // derivatives d/dx of the same cubics, as quadratics (x, y, z)
 };
 
 __device__ __forceinline__ int spline_locate(const Spline& s, double x, double& t, unsigned* err) {
@@ -107,6 +108,23 @@ __device__ __forceinline__ double spline_val_at(const Spline& s, int j, double t
 __device__ __forceinline__ double spline_der_at(const Spline& s, int j, double t) {
   const Cubic c = s.c[j];
   return fma(t, fma(t, 3.0 * c.w, 2.0 * c.z), c.y) * s.inv_h;
+}
+
+// derivative from the derivative table: d0 + t (d1 + t d2)
+__device__ __forceinline__ double spline_dval_at(const Spline& ds, int j, double t) {
+  const Cubic c = ds.c[j];
+  return fma(t, fma(t, c.z, c.y), c.x);
+}
+
+// 1/sqrt(r2): FP32 estimate refined by two Newton-Raphson steps in FP64,
+// y <- y + y (1 - r2 y^2) / 2; each step squares the relative error, so the
+// 2^-22 estimate reaches full double precision.
+__device__ __forceinline__ double rsqrt_nr(double r2) {
+  double y = (double)rsqrtf((float)r2);
+  double e = fma(-r2 * y, y, 1.0);
+  y = fma(0.5 * y, e, y);
+  e = fma(-r2 * y, y, 1.0);
+  return fma(0.5 * y, e, y);
 }
 
 // ------------------------------------------------------------ Metropolis

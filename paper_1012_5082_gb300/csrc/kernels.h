@@ -15,6 +15,8 @@ constexpr int MC_BLOCK = 128;
 // derivatives m (nullptr: central differences); out has n-1 intervals.
 void launch_spline_coeffs(const double* y, const double* m, int n, double h, Cubic* out,
                           cudaStream_t st);
+// derivative quadratics (c1, 2 c2, 3 c3) / h of n_int cubic intervals
+void launch_spline_derivs(const Cubic* c, int n_int, double h, Cubic* out, cudaStream_t st);
 // Per-shell pair and density differences of the rigid lattice:
 // tab[0] = C_A, tab[1+s] = G_A[s], tab[1+S+s] = f_B(r_s) - f_A(r_s), tab[1+2S+s] = r_s,
 // with r_s = (a/2) sqrt(h2[s]) and z[s] neighbours in shell s.
@@ -29,6 +31,9 @@ void launch_lattice_neighbours(int nx, int ny, int nz, const int3* hoff, int K, 
 // full neighbour list within rl; rows longer than K set ERRF_OVERFLOW.
 struct CellList {
   int nc[3];
+  float* x32;      // [N] float copies of the positions (list criterion only)
+  float* y32;
+  float* z32;
   int* cell_of;    // [N]
   int* cell_count; // [ncell]
   int* cell_start; // [ncell + 1]

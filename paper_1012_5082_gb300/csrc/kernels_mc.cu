@@ -100,6 +100,49 @@ __device__ double delta_e(const McArgs& a, int r, int i, unsigned* err) {
   return de;
 }
 
+// The general (explicit-position) form of dE by one warp: lanes take
+// neighbours k = lane, lane + 32, ...; partial sums meet in a shuffle tree.
+// Every lane returns the total.
+template <bool REEMBED>
+__device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned* err) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const int t = ty[i];
+  const int tp = 1 - t;
+  const int* row = a.nbr + (long long)i * a.K;
+  const int cnt = a.nbr_cnt[i];
+  const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
+  const double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
+  const double rc2 = a.rc * a.rc;
+  double part = 0.0;
+  for (int k = lane; k < cnt; k += 32) {
+    const int j = row[k];
+    const double dx = min_image(a.x[j] - xi, a.box[0]);
+    const double dy = min_image(a.y[j] - yi, a.box[1]);
+    const double dz = min_image(a.z[j] - zi, a.box[2]);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rc2) continue;
+    const int tj = ty[j];
+    double tt;
+    const int jj = spline_locate(a.tab.sp[0], r2 * rsqrt_nr(r2), tt, err);
+    part += spline_val_at(a.tab.sp[tp + tj], jj, tt) - spline_val_at(a.tab.sp[t + tj], jj, tt);
+    if constexpr (REEMBED) {
+      const double drho = spline_val_at(a.tab.sp[3 + tp], jj, tt) - spline_val_at(a.tab.sp[3 + t], jj, tt);
+      const double rj = rho[j];
+      part += spline_val(a.tab.sp[5 + tj], rj + drho, err) - spline_val(a.tab.sp[5 + tj], rj, err);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  double own;
+  if constexpr (REEMBED) {
+    const double ri = rho[i];
+    own = spline_val(a.tab.sp[5 + tp], ri, err) - spline_val(a.tab.sp[5 + t], ri, err);
+  } else {
+    own = t ? -a.dF[i] : a.dF[i];
+  }
+  return part + own;
+}
+
 template <int BLOCK>
 __device__ __forceinline__ void block_reduce3(int& a, int& b, double& c) {
   __shared__ int sa[BLOCK / 32], sb[BLOCK / 32];
@@ -181,6 +224,41 @@ __global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
   }
 }
 
+// General form: one warp per trial.  Same draws and rule as k_propose.
+constexpr int MCW_BLOCK = 128;  // 4 trials per block
+
+template <bool REEMBED>
+__global__ void __launch_bounds__(MCW_BLOCK) k_propose_warp(McArgs a) {
+  const int r = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int d = blockIdx.x * (MCW_BLOCK / 32) + (threadIdx.x >> 5);
+  const RepParams p = a.rp[r];
+  const long long step = a.rs[r].step;
+  const int c = draw_colour(a, p.key, step, nullptr);
+  const int d0 = a.col_start[c];
+  const int D = a.col_start[c + 1] - d0;
+  if (d >= D) return;
+  const int g = d0 + d;
+  const int base = a.dom_start[g];
+  const int size = a.dom_start[g + 1] - base;
+  if (size == 0) return;
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL), p.key);
+  const int site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
+  const double de = delta_e_warp<REEMBED>(a, r, site, lane, a.err);
+  if (lane != 0) return;
+  const int t = a.types[(long long)r * a.N + site];
+  if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
+  int tie = 0;
+  const double X = p.beta * fma(t ? -1.0 : 1.0, p.dmu0, de);
+  if (metropolis(X, top53(w.z, w.w), &tie)) {
+    const int slot = atomicAdd(&a.acc[r].nacc, 1);
+    a.acc_list[(long long)r * a.dmax + slot] = site;
+    atomicAdd(&a.acc[r].dn, t ? -1 : 1);
+    atomicAdd(&a.acc[r].sum_de, de);
+  }
+  if (tie) atomicAdd(&a.acc[r].ties, 1);
+}
+
 // flip site i of replica r and scatter its density change to its neighbours
 // (no two sites of one colour share a neighbour: they are > 2 r_c apart)
 template <bool SHELL, bool REEMBED>
@@ -213,10 +291,10 @@ __device__ void commit_site(const McArgs& a, int r, int i, unsigned* err) {
         const double dx = min_image(a.x[j] - a.x[i], a.box[0]);
         const double dy = min_image(a.y[j] - a.y[i], a.box[1]);
         const double dz = min_image(a.z[j] - a.z[i], a.box[2]);
-        const double rr = sqrt(dx * dx + dy * dy + dz * dz);
-        if (rr >= a.rc) continue;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= a.rc * a.rc) continue;
         double tt;
-        const int jj = spline_locate(a.tab.sp[3], rr, tt, err);
+        const int jj = spline_locate(a.tab.sp[3], r2 * rsqrt_nr(r2), tt, err);
         rho[j] += spline_val_at(a.tab.sp[3 + tp], jj, tt) - spline_val_at(a.tab.sp[3 + t], jj, tt);
       }
     }
@@ -281,18 +359,33 @@ __global__ void __launch_bounds__(MC_BLOCK) k_commit(McArgs a) {
   }
 }
 
-// dE of a list of sites with the sweep's own device function
+// dE of a list of sites with the sweep's own device function (general
+// form: one warp per site, as in the sweep)
 template <bool SHELL, bool REEMBED>
 __global__ void k_delta_e_list(McArgs a, int r, const int* sites, int n, double* out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n) out[q] = delta_e<SHELL, REEMBED>(a, r, sites[q], a.err);
+  if (SHELL) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[q] = delta_e<SHELL, REEMBED>(a, r, sites[q], a.err);
+  } else {
+    const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= n) return;
+    const double de = delta_e_warp<REEMBED>(a, r, sites[q], threadIdx.x & 31, a.err);
+    if ((threadIdx.x & 31) == 0) out[q] = de;
+  }
 }
 
 // ----------------------------------------------------------------- launch
 template <bool SHELL, bool REEMBED>
 static void launch_step_t(const McArgs& a, cudaStream_t st, int phase) {
   const int cb = (a.dmax + MC_BLOCK - 1) / MC_BLOCK;
-  if (phase != 2) k_propose<SHELL, REEMBED><<<dim3(cb, a.R), MC_BLOCK, 0, st>>>(a);
+  if (phase != 2) {
+    if (SHELL) {
+      k_propose<SHELL, REEMBED><<<dim3(cb, a.R), MC_BLOCK, 0, st>>>(a);
+    } else {
+      const int wb = (a.dmax + MCW_BLOCK / 32 - 1) / (MCW_BLOCK / 32);
+      k_propose_warp<REEMBED><<<dim3(wb, a.R), MCW_BLOCK, 0, st>>>(a);
+    }
+  }
   if (phase != 1) k_commit<SHELL, REEMBED><<<dim3(cb < 8 ? cb : 8, a.R), MC_BLOCK, 0, st>>>(a);
 }
 
@@ -308,7 +401,7 @@ void launch_colour_step(const McArgs& a, bool shell, bool reembed, cudaStream_t 
 
 void launch_delta_e_list(const McArgs& a, bool shell, bool reembed, int r, const int* sites, int n,
                          double* out, cudaStream_t st) {
-  const int b = 128, g = (n + b - 1) / b;
+  const int b = 128, g = shell ? (n + b - 1) / b : (n + 3) / 4;
   if (g == 0) return;
   if (shell) {
     if (reembed) k_delta_e_list<true, true><<<g, b, 0, st>>>(a, r, sites, n, out);

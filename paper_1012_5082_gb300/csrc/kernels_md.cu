@@ -9,7 +9,7 @@
 
 namespace vcsgc {
 
-__device__ __forceinline__ double mimg(double d, double L) { return d - L * rint(d / L); }
+__device__ __forceinline__ double mimg(double d, double L, double iL) { return d - L * rint(d * iL); }
 
 __global__ void k_md_rho(MdArgs m) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -17,15 +17,17 @@ __global__ void k_md_rho(MdArgs m) {
   const int* row = m.nbr + i * m.K;
   const int cnt = m.nbr_cnt[i];
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
+  const double rc2 = m.rc * m.rc;
   double rho = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
-    const double dx = mimg(m.x[j] - xi, m.box[0]);
-    const double dy = mimg(m.y[j] - yi, m.box[1]);
-    const double dz = mimg(m.z[j] - zi, m.box[2]);
-    const double r = sqrt(dx * dx + dy * dy + dz * dz);
-    if (r >= m.rc) continue;
-    rho += spline_val(m.tab.sp[3 + m.types[j]], r, m.err);
+    const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+    const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+    const double dz = mimg(m.z[j] - zi, m.box[2], iz);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rc2) continue;
+    rho += spline_val(m.tab.sp[3 + m.types[j]], r2 * rsqrt_nr(r2), m.err);
   }
   m.rho[i] = rho;
   double t;
@@ -43,20 +45,24 @@ __global__ void k_md_force(MdArgs m) {
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
   const int ti = m.types[i];
   const double Fi = m.dFp[i];
+  const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
+  const double rc2 = m.rc * m.rc;
   double fx = 0.0, fy = 0.0, fz = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
-    const double dx = mimg(m.x[j] - xi, m.box[0]);
-    const double dy = mimg(m.y[j] - yi, m.box[1]);
-    const double dz = mimg(m.z[j] - zi, m.box[2]);
-    const double r = sqrt(dx * dx + dy * dy + dz * dz);
-    if (r >= m.rc) continue;
+    const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+    const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+    const double dz = mimg(m.z[j] - zi, m.box[2], iz);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rc2) continue;
+    const double ir = rsqrt_nr(r2);
     const int tj = m.types[j];
     double t;
-    const int q = spline_locate(m.tab.sp[0], r, t, m.err);
-    const double g = spline_der_at(m.tab.sp[ti + tj], q, t) + Fi * spline_der_at(m.tab.sp[3 + tj], q, t) +
-                     m.dFp[j] * spline_der_at(m.tab.sp[3 + ti], q, t);
-    const double gr = g / r;
+    const int q = spline_locate(m.tab.sp[0], r2 * ir, t, m.err);
+    const double g = fma(m.dFp[j], spline_dval_at(m.tab.dsp[3 + ti], q, t),
+                         fma(Fi, spline_dval_at(m.tab.dsp[3 + tj], q, t),
+                             spline_dval_at(m.tab.dsp[ti + tj], q, t)));
+    const double gr = g * ir;
     fx = fma(gr, dx, fx);
     fy = fma(gr, dy, fy);
     fz = fma(gr, dz, fz);
@@ -115,9 +121,9 @@ __global__ void k_md_first_half(MdArgs m, long long step) {
   m.x[i] = x;
   m.y[i] = y;
   m.z[i] = z;
-  const double dx = mimg(x - m.x0[i], m.box[0]);
-  const double dy = mimg(y - m.y0[i], m.box[1]);
-  const double dz = mimg(z - m.z0[i], m.box[2]);
+  const double dx = mimg(x - m.x0[i], m.box[0], 1.0 / m.box[0]);
+  const double dy = mimg(y - m.y0[i], m.box[1], 1.0 / m.box[1]);
+  const double dz = mimg(z - m.z0[i], m.box[2], 1.0 / m.box[2]);
   const double d2 = dx * dx + dy * dy + dz * dz;
   // non-negative doubles order like their bit patterns
   atomicMax(m.max_disp2_bits, (unsigned long long)__double_as_longlong(d2));

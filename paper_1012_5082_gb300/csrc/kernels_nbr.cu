@@ -29,6 +29,17 @@ void launch_spline_coeffs(const double* y, const double* m, int n, double h, Cub
   k_spline_coeffs<<<(n + 255) / 256, 256, 0, st>>>(y, m, n, h, out);
 }
 
+__global__ void k_spline_derivs(const Cubic* c, int n_int, double inv_h, Cubic* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_int) return;
+  const Cubic q = c[j];
+  out[j] = Cubic{q.y * inv_h, 2.0 * q.z * inv_h, 3.0 * q.w * inv_h, 0.0};
+}
+
+void launch_spline_derivs(const Cubic* c, int n_int, double h, Cubic* out, cudaStream_t st) {
+  k_spline_derivs<<<(n_int + 255) / 256, 256, 0, st>>>(c, n_int, 1.0 / h, out);
+}
+
 // ------------------------------------------------------- shell tables
 // Rigid lattice: the pair part of dE(A->B) is
 //   sum_s [ (z_s - b_s) (phi_BA - phi_AA)(r_s) + b_s (phi_BB - phi_AB)(r_s) ]
@@ -94,12 +105,15 @@ __device__ __forceinline__ int cell_index(double v, double L, int n) {
 
 __global__ void k_cell_assign(long long N, const double* x, const double* y, const double* z,
                               double bx, double by, double bz, int nx, int ny, int nz,
-                              int* cell_of, int* count) {
+                              int* cell_of, int* count, float* x32, float* y32, float* z32) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int c = (cell_index(z[i], bz, nz) * ny + cell_index(y[i], by, ny)) * nx + cell_index(x[i], bx, nx);
   cell_of[i] = c;
   atomicAdd(&count[c], 1);
+  x32[i] = (float)x[i];
+  y32[i] = (float)y[i];
+  z32[i] = (float)z[i];
 }
 
 // exclusive scan of count[0..n) into start[0..n], one block
@@ -162,15 +176,19 @@ __global__ void k_cell_sort(int ncell, const int* start, int* sorted) {
   }
 }
 
-__global__ void k_cell_nbr(long long N, const double* x, const double* y, const double* z, double bx,
-                           double by, double bz, int nx, int ny, int nz, const int* cell_of,
-                           const int* start, const int* sorted, double rl2, int K, int* nbr, int* cnt,
+// Candidates are tested in FP32 against (rl + 0.01 A)^2: positions below
+// 10^3 A carry < 1e-4 A of rounding, so every pair within rl is listed; the
+// few extra pairs beyond rl are skipped where the list is used (r >= r_c).
+__global__ void k_cell_nbr(long long N, const float* x, const float* y, const float* z, float bx,
+                           float by, float bz, int nx, int ny, int nz, const int* cell_of,
+                           const int* start, const int* sorted, float rl2, int K, int* nbr, int* cnt,
                            unsigned* err) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int c = cell_of[i];
   const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
-  const double xi = x[i], yi = y[i], zi = z[i];
+  const float xi = x[i], yi = y[i], zi = z[i];
+  const float ibx = 1.0f / bx, iby = 1.0f / by, ibz = 1.0f / bz;
   int m = 0;
   for (int oz = -1; oz <= 1; ++oz)
     for (int oy = -1; oy <= 1; ++oy)
@@ -180,10 +198,10 @@ __global__ void k_cell_nbr(long long N, const double* x, const double* y, const 
         for (int p = start[q]; p < start[q + 1]; ++p) {
           const int j = sorted[p];
           if (j == i) continue;
-          double dx = x[j] - xi, dy = y[j] - yi, dz = z[j] - zi;
-          dx -= bx * rint(dx / bx);
-          dy -= by * rint(dy / by);
-          dz -= bz * rint(dz / bz);
+          float dx = x[j] - xi, dy = y[j] - yi, dz = z[j] - zi;
+          dx -= bx * rintf(dx * ibx);
+          dy -= by * rintf(dy * iby);
+          dz -= bz * rintf(dz * ibz);
           if (dx * dx + dy * dy + dz * dz < rl2) {
             if (m < K) nbr[i * K + m] = j;
             ++m;
@@ -204,12 +222,14 @@ void launch_cell_neighbours(long long N, const double* x, const double* y, const
   cudaMemsetAsync(cl.cell_count, 0, sizeof(int) * ncell, st);
   cudaMemsetAsync(cl.cell_cursor, 0, sizeof(int) * ncell, st);
   k_cell_assign<<<g, 128, 0, st>>>(N, x, y, z, box[0], box[1], box[2], cl.nc[0], cl.nc[1], cl.nc[2],
-                                   cl.cell_of, cl.cell_count);
+                                   cl.cell_of, cl.cell_count, cl.x32, cl.y32, cl.z32);
   k_scan<<<1, 1024, 0, st>>>(cl.cell_count, ncell, cl.cell_start);
   k_cell_scatter<<<g, 128, 0, st>>>(N, cl.cell_of, cl.cell_start, cl.cell_cursor, cl.sorted);
   k_cell_sort<<<(ncell + 127) / 128, 128, 0, st>>>(ncell, cl.cell_start, cl.sorted);
-  k_cell_nbr<<<g, 128, 0, st>>>(N, x, y, z, box[0], box[1], box[2], cl.nc[0], cl.nc[1], cl.nc[2],
-                                cl.cell_of, cl.cell_start, cl.sorted, rl * rl, K, nbr, cnt, err);
+  const float rlm = (float)rl + 0.01f;
+  k_cell_nbr<<<g, 128, 0, st>>>(N, cl.x32, cl.y32, cl.z32, (float)box[0], (float)box[1], (float)box[2],
+                                cl.nc[0], cl.nc[1], cl.nc[2], cl.cell_of, cl.cell_start, cl.sorted,
+                                rlm * rlm, K, nbr, cnt, err);
 }
 
 // ------------------------------------------------------ density, energy
@@ -219,7 +239,8 @@ __device__ __forceinline__ double pair_r(const McArgs& a, bool shell, int i, int
   dx -= a.box[0] * rint(dx / a.box[0]);
   dy -= a.box[1] * rint(dy / a.box[1]);
   dz -= a.box[2] * rint(dz / a.box[2]);
-  return sqrt(dx * dx + dy * dy + dz * dz);
+  const double r2 = dx * dx + dy * dy + dz * dz;
+  return r2 * rsqrt_nr(r2);
 }
 
 // rho_i = sum_k f_{t_k}(r_ik); dF_i = F_B(rho_i) - F_A(rho_i)

@@ -51,6 +51,7 @@ struct Ctx {
   int* nbr_cnt = nullptr;
   int K = 0;
   Cubic* coef[7] = {};
+  Cubic* dcoef[7] = {};
   double* shell_tab = nullptr;
   int* col_start = nullptr;
   int* dom_start = nullptr;
@@ -228,6 +229,9 @@ int build_cell_list(Ctx* c) {
   for (int q = 0; q < 3; ++q) c->cl.nc[q] = (int)std::floor(c->box[q] / c->rl);
   const int ncell = c->cl.nc[0] * c->cl.nc[1] * c->cl.nc[2];
   if (!c->cl.cell_of) {
+    TRY(dalloc(c, &c->cl.x32, c->N));
+    TRY(dalloc(c, &c->cl.y32, c->N));
+    TRY(dalloc(c, &c->cl.z32, c->N));
     TRY(dalloc(c, &c->cl.cell_of, c->N));
     TRY(dalloc(c, &c->cl.cell_count, ncell));
     TRY(dalloc(c, &c->cl.cell_start, ncell + 1));
@@ -705,6 +709,12 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
     s.inv_h = 1.0 / h;
     s.xmax = (n - 1) * h;
     s.n_int = n - 1;
+    TRY(dalloc(c, &c->dcoef[q], n - 1));
+    launch_spline_derivs(c->coef[q], n - 1, h, c->dcoef[q], c->st);
+    CK(cudaGetLastError());
+    Spline& ds = c->mc.tab.dsp[q];
+    ds = s;
+    ds.c = c->dcoef[q];
   }
 
   // ---- positions (both kinds; kind 0 from the lattice)

@@ -28,9 +28,10 @@ using vcsgc::CellList;
 constexpr long long NL_MAX_ATOMS = 262144;  // 2^18 positions
 constexpr long long NL_MAX_CELLS = 65536;   // 2^16 binning cells
 
-// layout: cell_of[MAX_ATOMS] | sorted[MAX_ATOMS] | count[MAX_CELLS] |
+// layout (4-byte words): x32, y32, z32 [MAX_ATOMS each, float] |
+//         cell_of[MAX_ATOMS] | sorted[MAX_ATOMS] | count[MAX_CELLS] |
 //         start[MAX_CELLS + 1] | cursor[MAX_CELLS] | err (one word)
-constexpr long long NL_SCRATCH_INTS = 2 * NL_MAX_ATOMS + 3 * NL_MAX_CELLS + 1 + 1;
+constexpr long long NL_SCRATCH_INTS = 5 * NL_MAX_ATOMS + 3 * NL_MAX_CELLS + 1 + 1;
 
 static __device__ __align__(256) int g_nl_scratch[NL_SCRATCH_INTS];
 
@@ -81,9 +82,12 @@ extern "C" int vcsgc_neighbour_list_noalloc(int64_t n, const double* d_x, const 
   cl.nc[0] = nc[0];
   cl.nc[1] = nc[1];
   cl.nc[2] = nc[2];
-  cl.cell_of = base;
-  cl.sorted = base + NL_MAX_ATOMS;
-  cl.cell_count = base + 2 * NL_MAX_ATOMS;
+  cl.x32 = reinterpret_cast<float*>(base);
+  cl.y32 = reinterpret_cast<float*>(base + NL_MAX_ATOMS);
+  cl.z32 = reinterpret_cast<float*>(base + 2 * NL_MAX_ATOMS);
+  cl.cell_of = base + 3 * NL_MAX_ATOMS;
+  cl.sorted = base + 4 * NL_MAX_ATOMS;
+  cl.cell_count = base + 5 * NL_MAX_ATOMS;
   cl.cell_start = cl.cell_count + NL_MAX_CELLS;
   cl.cell_cursor = cl.cell_start + NL_MAX_CELLS + 1;
   unsigned* err = reinterpret_cast<unsigned*>(cl.cell_cursor + NL_MAX_CELLS);
