@@ -160,7 +160,7 @@ def cpu_baseline(lat, types, tab, phi, c0, budget_s=12.0):
             "trials_counted": int(trials)}
 
 
-def md_bench(V, torch, stream, local, steps=20, warmup=3, box=250.0):
+def md_bench(V, torch, stream, local, steps=20, warmup=3, box=250.0, precision=0):
     """MD atom-steps/s of the hybrid scheme's MD half on the nanocrystal
     workload: 25 nm periodic cube, 16 Voronoi grains of BCC (a = 2.855 A)
     with random centres and orientations, overlaps within 2.0 A removed,
@@ -175,7 +175,7 @@ def md_bench(V, torch, stream, local, steps=20, warmup=3, box=250.0):
     nb = 2 * int(box // 22.0)  # even box count, boxes wider than 2 r_c = 10.6 A
     ctx = V.Context(lat, types, tab, -1.0, KAPPA, 700.0, c0=0.01, schedule=V.SCHED_SPATIAL,
                     sched=(nb, nb, nb, 2, 2, 2), dt=2.0, gamma=0.01, T_md=700.0, stream=stream,
-                    device=local)
+                    device=local, precision=precision)
     ctx.set_velocities(v)
     ctx.md_steps(warmup)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -195,10 +195,63 @@ def md_bench(V, torch, stream, local, steps=20, warmup=3, box=250.0):
     o = ctx.observables()
     ctx.close()
     return {"metric": "MD atom-steps/s", "value": lat.n * steps / (ms * 1e-3), "unit": "atom-steps/s",
-            "atoms": lat.n, "steps": steps, "ms_per_step": ms / steps, "dtype": "f64",
+            "atoms": lat.n, "steps": steps, "ms_per_step": ms / steps,
+            "dtype": "f64" if precision == 0 else "f32 tables, f64 sums",
             "workload": "nanocrystal 25 nm, 16 grains, 1% B, Langevin 700 K, dt 2 fs",
             "hybrid_cycle_s": cyc, "hybrid_mc_trials": int(o["trials"]),
             "generate_s": gen_s}
+
+
+def mixed_bench(V, torch, stream, local, sweeps=40, warmup=3):
+    """The mixed-precision form on the 128^3 rigid lattice (4,194,304 sites) x
+    8 phi replicas, timed beside the FP64 form on the same workload, with the
+    error of the mixed form: per-trial dE (max, rms) over sampled sites on the
+    same species, energy per atom, and each chain's mean concentration."""
+    cells = 128
+    lat = I.bcc_lattice(cells, cells, cells)
+    types = I.random_types(lat.n, int(round(FRAC_B * lat.n)), seed=1003)
+    tab = I.eam_tables()
+    c0 = 0.02 + np.arange(N_PHI) * 0.48 / 7
+    phi = DMU_S - 2.0 * KAPPA * I.KB_EV * T_K * c0
+    seeds = np.arange(N_PHI, dtype=np.uint64) + np.uint64(4001)
+    out = {"workload": f"rigid BCC {cells}^3 cells ({lat.n} sites) x {N_PHI} phi replicas, "
+                       "period-4 sublattice, T=600 K, kappa=1000"}
+    ctxs = {}
+    for name, prec in (("fp64", V.PREC_FP64), ("mixed", V.PREC_MIXED)):
+        ctx = V.Context(lat, np.tile(types, N_PHI), tab, 0.0, KAPPA, T_K, schedule=V.SCHED_SUBLATTICE,
+                        sched=(4, 4, 4), n_replicas=N_PHI, phi_r=phi, c0_r=c0, seed_r=seeds,
+                        stream=stream, device=local, precision=prec)
+        ctx.sweep(warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.sweep(sweeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"value": N_PHI * lat.n * sweeps / (ms * 1e-3), "unit": "trial moves/s",
+                     "ms_per_sweep": ms / sweeps,
+                     "mean_c": [ctx.observables(r)["mean_c"] for r in range(N_PHI)]}
+        ctxs[name] = ctx
+    # errors on common species (those of the FP64 chain)
+    t = ctxs["fp64"].types(0)
+    ctxs["mixed"].set_types(t, 0)
+    rng = np.random.default_rng(7)
+    sites = rng.choice(lat.n, 200000, replace=False)
+    d64 = ctxs["fp64"].delta_e(sites, 0)
+    d32 = ctxs["mixed"].delta_e(sites, 0)
+    err = np.abs(d32 - d64)
+    e64 = ctxs["fp64"].energy(0) / lat.n
+    e32 = ctxs["mixed"].energy(0) / lat.n
+    dc = np.abs(np.array(out["mixed"]["mean_c"]) - np.array(out["fp64"]["mean_c"]))
+    out["error_vs_fp64"] = {"dE_max_eV": float(err.max()), "dE_rms_eV": float(np.sqrt(np.mean(err ** 2))),
+                            "energy_per_atom_eV": abs(e32 - e64), "mean_c_abs_max": float(dc.max()),
+                            "sampled_sites": int(len(sites))}
+    out["speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    for ctx in ctxs.values():
+        ctx.close()
+    return out
 
 
 def run_reference(args):
@@ -243,6 +296,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-md", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--md-only", action="store_true", help="only the MD measurement (profiling)")
     ap.add_argument("--md-box", type=float, default=250.0, help="nanocrystal box (A) for --md-only")
     args = ap.parse_args()
@@ -352,6 +406,9 @@ def main():
             "acceptance": {"local": o0["acc_local"], "global": o0["acc_global"], "c": o0["c"]}}
     if not args.no_md:
         line["md"] = md_bench(V, torch, stream, local)
+        line["md_mixed"] = md_bench(V, torch, stream, local, precision=V.PREC_MIXED)
+    if not args.no_mixed:
+        line["mixed_128cubed"] = mixed_bench(V, torch, stream, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lat, types, tab, phi, c0)
     if rank == 0:

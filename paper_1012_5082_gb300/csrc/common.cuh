@@ -127,6 +127,55 @@ __device__ __forceinline__ double rsqrt_nr(double r2) {
   return fma(0.5 * y, e, y);
 }
 
+// ------------------------------------------------- FP32 tables (mixed form)
+// The mixed-precision form evaluates pair, density and embedding-table
+// interpolants in FP32 from the same coefficients rounded to float; sums
+// (rho, dE, forces) and embedding differences stay FP64.
+struct __align__(16) Cubic32 {
+  float x, y, z, w;
+};
+
+struct Spline32 {
+  const Cubic32* c;
+  float inv_h;
+  float xmax;
+  int n_int;
+};
+
+struct Tables32 {
+  Spline32 sp[7];
+  Spline32 dsp[7];
+};
+
+__device__ __forceinline__ int spline32_locate(const Spline32& s, float x, float& t, unsigned* err) {
+  if (!(x >= 0.0f) || x > s.xmax) {
+    atomicOr(err, ERRF_TABLE);
+    t = 0.0f;
+    return 0;
+  }
+  const float u = x * s.inv_h;
+  int j = (int)u;
+  if (j > s.n_int - 1) j = s.n_int - 1;
+  t = u - (float)j;
+  return j;
+}
+
+__device__ __forceinline__ float spline32_val_at(const Spline32& s, int j, float t) {
+  const Cubic32 c = s.c[j];
+  return fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
+}
+
+__device__ __forceinline__ float spline32_dval_at(const Spline32& ds, int j, float t) {
+  const Cubic32 c = ds.c[j];
+  return fmaf(t, fmaf(t, c.z, c.y), c.x);
+}
+
+// minimum-image separation in FP32 of two FP64 coordinates (difference in FP64)
+__device__ __forceinline__ float mimg32(double xj, double xi, float L, float iL) {
+  float d = (float)(xj - xi);
+  return d - L * rintf(d * iL);
+}
+
 // ------------------------------------------------------------ Metropolis
 // Decision u < min{1, exp(-X)} with u = u53 * 2^-53, exactly as an FP64
 // evaluation decides it.  GB300 runs FP32 ~60x faster than FP64, so the
@@ -212,6 +261,8 @@ struct McArgs {
   double box[3];
   double rc;
   Tables tab;
+  Tables32 tab32;
+  int mixed;             // FP32 table evaluation (VCSGC_PREC_MIXED)
   // schedule
   int n_colours;
   const int* col_start;

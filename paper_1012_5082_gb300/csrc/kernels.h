@@ -17,11 +17,13 @@ void launch_spline_coeffs(const double* y, const double* m, int n, double h, Cub
                           cudaStream_t st);
 // derivative quadratics (c1, 2 c2, 3 c3) / h of n_int cubic intervals
 void launch_spline_derivs(const Cubic* c, int n_int, double h, Cubic* out, cudaStream_t st);
+// coefficients rounded to float (mixed form)
+void launch_to_cubic32(const Cubic* c, int n_int, Cubic32* out, cudaStream_t st);
 // Per-shell pair and density differences of the rigid lattice:
 // tab[0] = C_A, tab[1+s] = G_A[s], tab[1+S+s] = f_B(r_s) - f_A(r_s), tab[1+2S+s] = r_s,
 // with r_s = (a/2) sqrt(h2[s]) and z[s] neighbours in shell s.
 void launch_shell_tables(Tables tab, const int* h2, const int* z, int S, double a, double* out,
-                         unsigned* err, cudaStream_t st);
+                         unsigned* err, cudaStream_t st, const Tables32* tab32 = nullptr);
 
 // ---- neighbour lists (kernels_nbr.cu)
 // Rigid BCC: row i lists the sites at the K half-lattice offsets hoff (x,y,z).
@@ -137,6 +139,7 @@ struct MdArgs {
   double *x, *y, *z, *vx, *vy, *vz, *fx, *fy, *fz;
   double* rho;
   double* dFp;   // F'(rho_i)
+  float* dFp32;  // the same in FP32 (mixed form)
   double* dF;    // F_B(rho_i) - F_A(rho_i)
   double *x0, *y0, *z0;  // positions at the last neighbour build
   double box[3];
@@ -145,6 +148,8 @@ struct MdArgs {
   double dt, c1, c2, kT;
   uint2 key;
   Tables tab;
+  Tables32 tab32;
+  int mixed;
   unsigned* err;
   unsigned long long* max_disp2_bits;  // max squared displacement (as bits)
 };

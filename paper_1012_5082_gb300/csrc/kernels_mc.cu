@@ -103,7 +103,7 @@ __device__ double delta_e(const McArgs& a, int r, int i, unsigned* err) {
 // The general (explicit-position) form of dE by one warp: lanes take
 // neighbours k = lane, lane + 32, ...; partial sums meet in a shuffle tree.
 // Every lane returns the total.
-template <bool REEMBED>
+template <bool REEMBED, bool MIXED>
 __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned* err) {
   const uint8_t* ty = a.types + (long long)r * a.N;
   const int t = ty[i];
@@ -116,17 +116,41 @@ __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned
   double part = 0.0;
   for (int k = lane; k < cnt; k += 32) {
     const int j = row[k];
-    const double dx = min_image(a.x[j] - xi, a.box[0]);
-    const double dy = min_image(a.y[j] - yi, a.box[1]);
-    const double dz = min_image(a.z[j] - zi, a.box[2]);
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 >= rc2) continue;
     const int tj = ty[j];
-    double tt;
-    const int jj = spline_locate(a.tab.sp[0], r2 * rsqrt_nr(r2), tt, err);
-    part += spline_val_at(a.tab.sp[tp + tj], jj, tt) - spline_val_at(a.tab.sp[t + tj], jj, tt);
+    double vp, vm, fp = 0.0, fm = 0.0;
+    if constexpr (MIXED) {
+      // FP32 distance and table values, FP64 differences and sums
+      const float dx = mimg32(a.x[j], xi, (float)a.box[0], (float)(1.0 / a.box[0]));
+      const float dy = mimg32(a.y[j], yi, (float)a.box[1], (float)(1.0 / a.box[1]));
+      const float dz = mimg32(a.z[j], zi, (float)a.box[2], (float)(1.0 / a.box[2]));
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 >= (float)rc2) continue;
+      float tt;
+      const int jj = spline32_locate(a.tab32.sp[0], sqrtf(r2), tt, err);
+      vp = (double)spline32_val_at(a.tab32.sp[tp + tj], jj, tt);
+      vm = (double)spline32_val_at(a.tab32.sp[t + tj], jj, tt);
+      if (REEMBED) {
+        fp = (double)spline32_val_at(a.tab32.sp[3 + tp], jj, tt);
+        fm = (double)spline32_val_at(a.tab32.sp[3 + t], jj, tt);
+      }
+    } else {
+      const double dx = min_image(a.x[j] - xi, a.box[0]);
+      const double dy = min_image(a.y[j] - yi, a.box[1]);
+      const double dz = min_image(a.z[j] - zi, a.box[2]);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 >= rc2) continue;
+      double tt;
+      const int jj = spline_locate(a.tab.sp[0], r2 * rsqrt_nr(r2), tt, err);
+      vp = spline_val_at(a.tab.sp[tp + tj], jj, tt);
+      vm = spline_val_at(a.tab.sp[t + tj], jj, tt);
+      if (REEMBED) {
+        fp = spline_val_at(a.tab.sp[3 + tp], jj, tt);
+        fm = spline_val_at(a.tab.sp[3 + t], jj, tt);
+      }
+    }
+    part += vp - vm;
     if constexpr (REEMBED) {
-      const double drho = spline_val_at(a.tab.sp[3 + tp], jj, tt) - spline_val_at(a.tab.sp[3 + t], jj, tt);
+      const double drho = fp - fm;
       const double rj = rho[j];
       part += spline_val(a.tab.sp[5 + tj], rj + drho, err) - spline_val(a.tab.sp[5 + tj], rj, err);
     }
@@ -227,7 +251,7 @@ __global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
 // General form: one warp per trial.  Same draws and rule as k_propose.
 constexpr int MCW_BLOCK = 128;  // 4 trials per block
 
-template <bool REEMBED>
+template <bool REEMBED, bool MIXED>
 __global__ void __launch_bounds__(MCW_BLOCK) k_propose_warp(McArgs a) {
   const int r = blockIdx.y;
   const int lane = threadIdx.x & 31;
@@ -244,7 +268,7 @@ __global__ void __launch_bounds__(MCW_BLOCK) k_propose_warp(McArgs a) {
   if (size == 0) return;
   const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL), p.key);
   const int site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
-  const double de = delta_e_warp<REEMBED>(a, r, site, lane, a.err);
+  const double de = delta_e_warp<REEMBED, MIXED>(a, r, site, lane, a.err);
   if (lane != 0) return;
   const int t = a.types[(long long)r * a.N + site];
   if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
@@ -293,9 +317,16 @@ __device__ void commit_site(const McArgs& a, int r, int i, unsigned* err) {
         const double dz = min_image(a.z[j] - a.z[i], a.box[2]);
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= a.rc * a.rc) continue;
-        double tt;
-        const int jj = spline_locate(a.tab.sp[3], r2 * rsqrt_nr(r2), tt, err);
-        rho[j] += spline_val_at(a.tab.sp[3 + tp], jj, tt) - spline_val_at(a.tab.sp[3 + t], jj, tt);
+        if (a.mixed) {
+          float tt;
+          const int jj = spline32_locate(a.tab32.sp[3], sqrtf((float)r2), tt, err);
+          rho[j] += (double)spline32_val_at(a.tab32.sp[3 + tp], jj, tt) -
+                    (double)spline32_val_at(a.tab32.sp[3 + t], jj, tt);
+        } else {
+          double tt;
+          const int jj = spline_locate(a.tab.sp[3], r2 * rsqrt_nr(r2), tt, err);
+          rho[j] += spline_val_at(a.tab.sp[3 + tp], jj, tt) - spline_val_at(a.tab.sp[3 + t], jj, tt);
+        }
       }
     }
   }
@@ -369,7 +400,8 @@ __global__ void k_delta_e_list(McArgs a, int r, const int* sites, int n, double*
   } else {
     const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (q >= n) return;
-    const double de = delta_e_warp<REEMBED>(a, r, sites[q], threadIdx.x & 31, a.err);
+    const double de = a.mixed ? delta_e_warp<REEMBED, true>(a, r, sites[q], threadIdx.x & 31, a.err)
+                              : delta_e_warp<REEMBED, false>(a, r, sites[q], threadIdx.x & 31, a.err);
     if ((threadIdx.x & 31) == 0) out[q] = de;
   }
 }
@@ -383,7 +415,8 @@ static void launch_step_t(const McArgs& a, cudaStream_t st, int phase) {
       k_propose<SHELL, REEMBED><<<dim3(cb, a.R), MC_BLOCK, 0, st>>>(a);
     } else {
       const int wb = (a.dmax + MCW_BLOCK / 32 - 1) / (MCW_BLOCK / 32);
-      k_propose_warp<REEMBED><<<dim3(wb, a.R), MCW_BLOCK, 0, st>>>(a);
+      if (a.mixed) k_propose_warp<REEMBED, true><<<dim3(wb, a.R), MCW_BLOCK, 0, st>>>(a);
+      else k_propose_warp<REEMBED, false><<<dim3(wb, a.R), MCW_BLOCK, 0, st>>>(a);
     }
   }
   if (phase != 1) k_commit<SHELL, REEMBED><<<dim3(cb < 8 ? cb : 8, a.R), MC_BLOCK, 0, st>>>(a);

@@ -11,6 +11,7 @@ namespace vcsgc {
 
 __device__ __forceinline__ double mimg(double d, double L, double iL) { return d - L * rint(d * iL); }
 
+template <bool MIXED>
 __global__ void k_md_rho(MdArgs m) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.N) return;
@@ -22,21 +23,35 @@ __global__ void k_md_rho(MdArgs m) {
   double rho = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
-    const double dx = mimg(m.x[j] - xi, m.box[0], ix);
-    const double dy = mimg(m.y[j] - yi, m.box[1], iy);
-    const double dz = mimg(m.z[j] - zi, m.box[2], iz);
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    if (r2 >= rc2) continue;
-    rho += spline_val(m.tab.sp[3 + m.types[j]], r2 * rsqrt_nr(r2), m.err);
+    if constexpr (MIXED) {
+      const float dx = mimg32(m.x[j], xi, (float)m.box[0], (float)ix);
+      const float dy = mimg32(m.y[j], yi, (float)m.box[1], (float)iy);
+      const float dz = mimg32(m.z[j], zi, (float)m.box[2], (float)iz);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 >= (float)rc2) continue;
+      float t;
+      const Spline32& sp = m.tab32.sp[3 + m.types[j]];
+      const int q = spline32_locate(sp, sqrtf(r2), t, m.err);
+      rho += (double)spline32_val_at(sp, q, t);
+    } else {
+      const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+      const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+      const double dz = mimg(m.z[j] - zi, m.box[2], iz);
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 >= rc2) continue;
+      rho += spline_val(m.tab.sp[3 + m.types[j]], r2 * rsqrt_nr(r2), m.err);
+    }
   }
   m.rho[i] = rho;
   double t;
   const int ti = m.types[i];
   const int q = spline_locate(m.tab.sp[5 + ti], rho, t, m.err);
   m.dFp[i] = spline_der_at(m.tab.sp[5 + ti], q, t);
+  if (MIXED) m.dFp32[i] = (float)m.dFp[i];
   m.dF[i] = spline_val_at(m.tab.sp[6], q, t) - spline_val_at(m.tab.sp[5], q, t);
 }
 
+template <bool MIXED>
 __global__ void k_md_force(MdArgs m) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.N) return;
@@ -48,8 +63,29 @@ __global__ void k_md_force(MdArgs m) {
   const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
   const double rc2 = m.rc * m.rc;
   double fx = 0.0, fy = 0.0, fz = 0.0;
+  const float Fi32 = (float)Fi;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
+    if constexpr (MIXED) {
+      // FP32 geometry and table derivatives, FP64 force sums
+      const float dx = mimg32(m.x[j], xi, (float)m.box[0], (float)ix);
+      const float dy = mimg32(m.y[j], yi, (float)m.box[1], (float)iy);
+      const float dz = mimg32(m.z[j], zi, (float)m.box[2], (float)iz);
+      const float r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 >= (float)rc2) continue;
+      const float ir = rsqrtf(r2);
+      const int tj = m.types[j];
+      float t;
+      const int q = spline32_locate(m.tab32.sp[0], r2 * ir, t, m.err);
+      const float g = fmaf(m.dFp32[j], spline32_dval_at(m.tab32.dsp[3 + ti], q, t),
+                           fmaf(Fi32, spline32_dval_at(m.tab32.dsp[3 + tj], q, t),
+                                spline32_dval_at(m.tab32.dsp[ti + tj], q, t)));
+      const float gr = g * ir;
+      fx += (double)(gr * dx);
+      fy += (double)(gr * dy);
+      fz += (double)(gr * dz);
+      continue;
+    }
     const double dx = mimg(m.x[j] - xi, m.box[0], ix);
     const double dy = mimg(m.y[j] - yi, m.box[1], iy);
     const double dz = mimg(m.z[j] - zi, m.box[2], iz);
@@ -172,8 +208,14 @@ __global__ void __launch_bounds__(KE_BLOCK) k_kinetic(MdArgs m, double* part) {
 
 static unsigned grid_of(long long N) { return (unsigned)((N + 127) / 128); }
 
-void launch_md_rho(const MdArgs& m, cudaStream_t st) { k_md_rho<<<grid_of(m.N), 128, 0, st>>>(m); }
-void launch_md_force(const MdArgs& m, cudaStream_t st) { k_md_force<<<grid_of(m.N), 128, 0, st>>>(m); }
+void launch_md_rho(const MdArgs& m, cudaStream_t st) {
+  if (m.mixed) k_md_rho<true><<<grid_of(m.N), 128, 0, st>>>(m);
+  else k_md_rho<false><<<grid_of(m.N), 128, 0, st>>>(m);
+}
+void launch_md_force(const MdArgs& m, cudaStream_t st) {
+  if (m.mixed) k_md_force<true><<<grid_of(m.N), 128, 0, st>>>(m);
+  else k_md_force<false><<<grid_of(m.N), 128, 0, st>>>(m);
+}
 void launch_md_first_half(const MdArgs& m, long long step, cudaStream_t st) {
   k_md_first_half<<<grid_of(m.N), 128, 0, st>>>(m, step);
 }

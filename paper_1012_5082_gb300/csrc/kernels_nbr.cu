@@ -40,31 +40,56 @@ void launch_spline_derivs(const Cubic* c, int n_int, double h, Cubic* out, cudaS
   k_spline_derivs<<<(n_int + 255) / 256, 256, 0, st>>>(c, n_int, 1.0 / h, out);
 }
 
+__global__ void k_to_cubic32(const Cubic* c, int n_int, Cubic32* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_int) return;
+  const Cubic q = c[j];
+  out[j] = Cubic32{(float)q.x, (float)q.y, (float)q.z, (float)q.w};
+}
+
+void launch_to_cubic32(const Cubic* c, int n_int, Cubic32* out, cudaStream_t st) {
+  k_to_cubic32<<<(n_int + 255) / 256, 256, 0, st>>>(c, n_int, out);
+}
+
 // ------------------------------------------------------- shell tables
 // Rigid lattice: the pair part of dE(A->B) is
 //   sum_s [ (z_s - b_s) (phi_BA - phi_AA)(r_s) + b_s (phi_BB - phi_AB)(r_s) ]
 //   = C_A + sum_s b_s G_A[s],
 // C_A = sum_s z_s (phi_AB - phi_AA)(r_s), G_A[s] = (phi_BB - 2 phi_AB + phi_AA)(r_s).
-__global__ void k_shell_tables(Tables tab, const int* h2, const int* z, int S, double a,
-                               double* out, unsigned* err) {
+// value of table q at r: FP64, or FP32 interpolation widened (mixed form)
+__device__ __forceinline__ double tab_val(const Tables& tab, const Tables32* t32, int q, double r,
+                                          unsigned* err) {
+  if (t32) {
+    float t;
+    const int j = spline32_locate(t32->sp[q], (float)r, t, err);
+    return (double)spline32_val_at(t32->sp[q], j, t);
+  }
+  return spline_val(tab.sp[q], r, err);
+}
+
+__global__ void k_shell_tables(Tables tab, Tables32 tab32, int mixed, const int* h2, const int* z,
+                               int S, double a, double* out, unsigned* err) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const Tables32* t32 = mixed ? &tab32 : nullptr;
   double C = 0.0;
   for (int s = 0; s < S; ++s) {
     const double r = 0.5 * a * sqrt((double)h2[s]);
-    const double pAA = spline_val(tab.sp[0], r, err);
-    const double pAB = spline_val(tab.sp[1], r, err);
-    const double pBB = spline_val(tab.sp[2], r, err);
+    const double pAA = tab_val(tab, t32, 0, r, err);
+    const double pAB = tab_val(tab, t32, 1, r, err);
+    const double pBB = tab_val(tab, t32, 2, r, err);
     C += (double)z[s] * (pAB - pAA);
     out[1 + s] = (pBB - pAB) - (pAB - pAA);
-    out[1 + S + s] = spline_val(tab.sp[4], r, err) - spline_val(tab.sp[3], r, err);
+    out[1 + S + s] = tab_val(tab, t32, 4, r, err) - tab_val(tab, t32, 3, r, err);
     out[1 + 2 * S + s] = r;
   }
   out[0] = C;
 }
 
 void launch_shell_tables(Tables tab, const int* h2, const int* z, int S, double a, double* out,
-                         unsigned* err, cudaStream_t st) {
-  k_shell_tables<<<1, 32, 0, st>>>(tab, h2, z, S, a, out, err);
+                         unsigned* err, cudaStream_t st, const Tables32* tab32) {
+  Tables32 t{};
+  if (tab32) t = *tab32;
+  k_shell_tables<<<1, 32, 0, st>>>(tab, t, tab32 ? 1 : 0, h2, z, S, a, out, err);
 }
 
 // --------------------------------------------------- lattice neighbours
@@ -243,8 +268,29 @@ __device__ __forceinline__ double pair_r(const McArgs& a, bool shell, int i, int
   return r2 * rsqrt_nr(r2);
 }
 
-// rho_i = sum_k f_{t_k}(r_ik); dF_i = F_B(rho_i) - F_A(rho_i)
-template <bool SHELL>
+// FP32 distance of pair (i, j) for the mixed form (r_s on the rigid lattice)
+__device__ __forceinline__ float pair_r32(const McArgs& a, bool shell, int i, int j, int s) {
+  if (shell) return (float)a.shell_tab[1 + 2 * a.n_shells + s];
+  const float dx = mimg32(a.x[j], a.x[i], (float)a.box[0], (float)(1.0 / a.box[0]));
+  const float dy = mimg32(a.y[j], a.y[i], (float)a.box[1], (float)(1.0 / a.box[1]));
+  const float dz = mimg32(a.z[j], a.z[i], (float)a.box[2], (float)(1.0 / a.box[2]));
+  return sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+// table q at the pair distance: FP64, or FP32 widened to FP64 (mixed)
+template <bool MIXED>
+__device__ __forceinline__ double pair_tab(const McArgs& a, int q, double r64, float r32) {
+  if constexpr (MIXED) {
+    float t;
+    const int j = spline32_locate(a.tab32.sp[q], r32, t, a.err);
+    return (double)spline32_val_at(a.tab32.sp[q], j, t);
+  } else {
+    return spline_val(a.tab.sp[q], r64, a.err);
+  }
+}
+
+// rho_i = sum_k f_{t_k}(r_ik) (FP64 sum); dF_i = F_B(rho_i) - F_A(rho_i) (FP64)
+template <bool SHELL, bool MIXED>
 __global__ void k_rho(McArgs a, int r, double* dF) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
@@ -256,9 +302,16 @@ __global__ void k_rho(McArgs a, int r, double* dF) {
   for (int k = 0; k < cnt; ++k) {
     if (SHELL) while (k >= a.shell_end[s]) ++s;
     const int j = row[k];
-    const double rr = pair_r(a, SHELL, (int)i, k, j, s);
-    if (rr >= a.rc) continue;
-    rho += spline_val(a.tab.sp[3 + ty[j]], rr, a.err);
+    double rr = 0.0;
+    float rf = 0.0f;
+    if (MIXED) {
+      rf = pair_r32(a, SHELL, (int)i, j, s);
+      if (rf >= (float)a.rc) continue;
+    } else {
+      rr = pair_r(a, SHELL, (int)i, k, j, s);
+      if (rr >= a.rc) continue;
+    }
+    rho += pair_tab<MIXED>(a, 3 + ty[j], rr, rf);
   }
   double* out = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
   out[i] = rho;
@@ -268,15 +321,20 @@ __global__ void k_rho(McArgs a, int r, double* dF) {
 void launch_rho(const McArgs& a, bool shell, int r, cudaStream_t st) {
   const unsigned g = (unsigned)((a.N + 127) / 128);
   double* dF = const_cast<double*>(a.dF);
-  if (shell) k_rho<true><<<g, 128, 0, st>>>(a, r, dF);
-  else k_rho<false><<<g, 128, 0, st>>>(a, r, dF);
+  if (a.mixed) {
+    if (shell) k_rho<true, true><<<g, 128, 0, st>>>(a, r, dF);
+    else k_rho<false, true><<<g, 128, 0, st>>>(a, r, dF);
+  } else {
+    if (shell) k_rho<true, false><<<g, 128, 0, st>>>(a, r, dF);
+    else k_rho<false, false><<<g, 128, 0, st>>>(a, r, dF);
+  }
 }
 
 constexpr int E_BLOCK = 256;
 int energy_blocks(long long N) { return (int)((N + E_BLOCK - 1) / E_BLOCK); }
 
 // e_i = 1/2 sum_k phi_{t_i t_k}(r_ik) + F_{t_i}(rho_i), block partial sums
-template <bool SHELL>
+template <bool SHELL, bool MIXED>
 __global__ void __launch_bounds__(E_BLOCK) k_energy(McArgs a, int r, double* part) {
   const long long i = (long long)blockIdx.x * E_BLOCK + threadIdx.x;
   double e = 0.0;
@@ -290,11 +348,18 @@ __global__ void __launch_bounds__(E_BLOCK) k_energy(McArgs a, int r, double* par
     for (int k = 0; k < cnt; ++k) {
       if (SHELL) while (k >= a.shell_end[s]) ++s;
       const int j = row[k];
-      const double rr = pair_r(a, SHELL, (int)i, k, j, s);
-      if (rr >= a.rc) continue;
+      double rr = 0.0;
+      float rf = 0.0f;
+      if (MIXED) {
+        rf = pair_r32(a, SHELL, (int)i, j, s);
+        if (rf >= (float)a.rc) continue;
+      } else {
+        rr = pair_r(a, SHELL, (int)i, k, j, s);
+        if (rr >= a.rc) continue;
+      }
       const int tj = ty[j];
-      ph += spline_val(a.tab.sp[ti + tj], rr, a.err);
-      rho += spline_val(a.tab.sp[3 + tj], rr, a.err);
+      ph += pair_tab<MIXED>(a, ti + tj, rr, rf);
+      rho += pair_tab<MIXED>(a, 3 + tj, rr, rf);
     }
     e = 0.5 * ph + spline_val(a.tab.sp[5 + ti], rho, a.err);
   }
@@ -312,8 +377,13 @@ __global__ void __launch_bounds__(E_BLOCK) k_energy(McArgs a, int r, double* par
 
 void launch_energy(const McArgs& a, bool shell, int r, double* part, cudaStream_t st) {
   const int g = energy_blocks(a.N);
-  if (shell) k_energy<true><<<g, E_BLOCK, 0, st>>>(a, r, part);
-  else k_energy<false><<<g, E_BLOCK, 0, st>>>(a, r, part);
+  if (a.mixed) {
+    if (shell) k_energy<true, true><<<g, E_BLOCK, 0, st>>>(a, r, part);
+    else k_energy<false, true><<<g, E_BLOCK, 0, st>>>(a, r, part);
+  } else {
+    if (shell) k_energy<true, false><<<g, E_BLOCK, 0, st>>>(a, r, part);
+    else k_energy<false, false><<<g, E_BLOCK, 0, st>>>(a, r, part);
+  }
 }
 
 }  // namespace vcsgc

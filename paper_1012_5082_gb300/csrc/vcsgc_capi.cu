@@ -33,6 +33,7 @@ struct Ctx {
   int R = 1;
   double rc = 0, skin = 0, rl = 0;
   bool shell = false, reembed = false;
+  bool mixed = false;
   int sched_kind = 0;
   int sched[6] = {0, 0, 0, 0, 0, 0};
   long long steps_per_sweep = 1;
@@ -42,6 +43,7 @@ struct Ctx {
   double* rho = nullptr;
   double* dF = nullptr;
   double* dFp = nullptr;
+  float* dFp32 = nullptr;
   double *x = nullptr, *y = nullptr, *z = nullptr;
   double *vx = nullptr, *vy = nullptr, *vz = nullptr;
   double *fx = nullptr, *fy = nullptr, *fz = nullptr;
@@ -163,6 +165,7 @@ void fill_args(Ctx* c) {
   a.z = c->z;
   for (int q = 0; q < 3; ++q) a.box[q] = c->box[q];
   a.rc = c->rc;
+  a.mixed = c->mixed ? 1 : 0;
   a.n_colours = c->n_colours;
   a.col_start = c->col_start;
   a.dom_start = c->dom_start;
@@ -197,6 +200,9 @@ void fill_args(Ctx* c) {
   m.kT = KB_EV * c->T_md;
   m.key = make_uint2((uint32_t)c->md_seed, (uint32_t)(c->md_seed >> 32));
   m.tab = c->mc.tab;
+  m.tab32 = c->mc.tab32;
+  m.mixed = c->mixed ? 1 : 0;
+  m.dFp32 = c->dFp32;
   m.err = c->derr;
   m.max_disp2_bits = c->max_disp2;
 
@@ -613,7 +619,9 @@ static int setup_fast(Ctx* c, const std::vector<RepState>& hs);
 static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_eam_tables* E,
                      double phi, double kappa, double T, const vcsgc_options* o) {
   if (!L || !types || !E || !o) return fail(c, VCSGC_ERR_INVALID_ARG, "null argument");
-  if (o->precision != VCSGC_PREC_FP64) return fail(c, VCSGC_ERR_INVALID_ARG, "only FP64 precision is built");
+  if (o->precision != VCSGC_PREC_FP64 && o->precision != VCSGC_PREC_MIXED)
+    return fail(c, VCSGC_ERR_INVALID_ARG, "precision must be FP64 or MIXED");
+  c->mixed = o->precision == VCSGC_PREC_MIXED;
   if (o->n_replicas < 1) return fail(c, VCSGC_ERR_INVALID_ARG, "n_replicas < 1");
   c->R = o->n_replicas;
   c->kind = L->kind;
@@ -715,6 +723,22 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
     Spline& ds = c->mc.tab.dsp[q];
     ds = s;
     ds.c = c->dcoef[q];
+    if (c->mixed) {
+      Cubic32 *c32 = nullptr, *d32 = nullptr;
+      TRY(dalloc(c, &c32, n - 1));
+      TRY(dalloc(c, &d32, n - 1));
+      launch_to_cubic32(c->coef[q], n - 1, c32, c->st);
+      launch_to_cubic32(c->dcoef[q], n - 1, d32, c->st);
+      CK(cudaGetLastError());
+      Spline32& s32 = c->mc.tab32.sp[q];
+      s32.c = c32;
+      s32.inv_h = (float)(1.0 / h);
+      s32.xmax = (float)((n - 1) * h);
+      s32.n_int = n - 1;
+      Spline32& ds32 = c->mc.tab32.dsp[q];
+      ds32 = s32;
+      ds32.c = d32;
+    }
   }
 
   // ---- positions (both kinds; kind 0 from the lattice)
@@ -795,7 +819,8 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
     TRY(dalloc(c, &c->nbr, (size_t)c->N * c->K));
     launch_lattice_neighbours(c->nx, c->ny, c->nz, dh, c->K, c->nbr, c->nbr_cnt, c->st);
     TRY(dalloc(c, &c->shell_tab, 1 + 3 * S));
-    launch_shell_tables(c->mc.tab, dh2, dz, S, c->a, c->shell_tab, c->derr, c->st);
+    launch_shell_tables(c->mc.tab, dh2, dz, S, c->a, c->shell_tab, c->derr, c->st,
+                        c->mixed ? &c->mc.tab32 : nullptr);
     CK(cudaGetLastError());
   } else {
     const double dens = c->N / (c->box[0] * c->box[1] * c->box[2]);
@@ -811,6 +836,7 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   TRY(dalloc(c, &c->rho, (size_t)(c->reembed ? c->R : 1) * c->N));
   TRY(dalloc(c, &c->dF, c->N));
   TRY(dalloc(c, &c->dFp, c->N));
+  TRY(dalloc(c, &c->dFp32, c->N));
   TRY(dalloc(c, &c->fx, c->N));
   TRY(dalloc(c, &c->fy, c->N));
   TRY(dalloc(c, &c->fz, c->N));

@@ -18,6 +18,7 @@ OK = 0
 ERR = {-1: "INVALID_ARG", -2: "CUDA", -3: "TABLE_RANGE", -4: "NONFINITE", -5: "SCHEDULE",
        -6: "TIMEOUT", -7: "NOMEM", -8: "STATE", -9: "OVERFLOW"}
 SCHED_BLOCKS, SCHED_SUBLATTICE, SCHED_SPATIAL = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
 
 
 class VcsgcError(RuntimeError):
@@ -173,7 +174,8 @@ class Context:
     def __init__(self, lattice, types, tables, phi, kappa, T, *, seed=1, c0=-1.0, kappa_units=0,
                  schedule=SCHED_SUBLATTICE, sched=(4, 4, 4, 0, 0, 0), n_replicas=1, phi_r=None,
                  kappa_r=None, T_r=None, seed_r=None, c0_r=None, masses=(55.845, 63.546), dt=2.0,
-                 gamma=0.01, T_md=-1.0, skin=0.3, md_seed=12345, stream=None, device=-1):
+                 gamma=0.01, T_md=-1.0, skin=0.3, md_seed=12345, stream=None, device=-1,
+                 precision=0):
         self._keep = []
         L = Lattice()
         if lattice.cells is not None and getattr(lattice, "rigid", True):
@@ -214,6 +216,7 @@ class Context:
         for q in range(6):
             o.sched[q] = sched[q] if q < len(sched) else 0
         o.n_replicas = n_replicas
+        o.precision = precision
         for name, val, dt_ in (("phi_r", phi_r, np.float64), ("kappa_r", kappa_r, np.float64),
                                ("T_r", T_r, np.float64), ("seed_r", seed_r, np.uint64),
                                ("c0_r", c0_r, np.float64)):
