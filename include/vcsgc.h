@@ -180,6 +180,26 @@ int vcsgc_init(void** ctx, const vcsgc_lattice* lattice, const uint8_t* types,
                const vcsgc_eam_tables* eam, double phi, double kappa, double T,
                const vcsgc_options* opt);
 
+/* Batch of rigid BCC lattices of different sizes in one context: replica r
+ * has cells[3r..3r+2] = (nx, ny, nz) cells of side a, its species at
+ * types[sum_{q<r} N_q .. + N_r) (N_r = 2 nx ny nz, concatenated), and its own
+ * phi[r], kappa[r], T[r] (n_rep each; opt->seed_r / c0_r per replica as in
+ * vcsgc_init).  Every replica must use the SUBLATTICE schedule with the same
+ * period (each size divisible by it) and the same a and tables, with one
+ * density function.  All replicas advance together: one fused launch per
+ * colour step serves the whole batch.  Calls taking a replica index work on
+ * batches; md_steps, forces and neighbours do not (VCSGC_ERR_STATE).
+ * Errors: INVALID_ARG, SCHEDULE, NOMEM, CUDA. */
+int vcsgc_batch_init(void** ctx, int32_t n_rep, const int32_t* cells, double a, const uint8_t* types,
+                     const vcsgc_eam_tables* eam, const double* phi, const double* kappa,
+                     const double* T, const vcsgc_options* opt);
+
+/* Pick the thread-block size (64, 128 or 256) of the fused colour step by
+ * timing `steps` colour steps with each (these are real steps of the chain)
+ * and keep the fastest for later launches; *best_block receives it.  A
+ * context outside the fused form reports its fixed block size. */
+int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block);
+
 /* Advance every replica by n_steps colour steps (composite moves of
  * Sec. III B 2: site pick, dE gather, local Metropolis test with
  * dmu0 = phi + 2 kappa_p N c0, reduction of dn, global test with exponent

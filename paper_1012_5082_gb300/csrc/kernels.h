@@ -77,41 +77,49 @@ struct LatCtl {
   long long base_step;          // step of the next launch with j = 0
 };
 
+// geometry of one replica's rigid lattice in the bit-packed form
+struct LatGeom {
+  int nx, ny, nz, W;            // cells per axis, 64-bit words per row
+  long long bits_off;           // first word of the replica's rows
+  long long pend_off;           // first pending slot of the replica
+  long long n_sites;
+  int d;                        // domains per colour (SUBLATTICE)
+  int dmax;                     // pending slots of the replica
+  int nxq, nyq;                 // nx / qx, ny / qy
+  float rcp_nx, rcp_ny, rcp_nxq, rcp_nyq;  // 1/d for fdiv
+};
+
 struct LatArgs {
-  long long N;
   int R;
-  int nx, ny, nz;
-  int W;                        // 64-bit words per row
-  long long rep_words;          // nz * ny * W
-  unsigned long long* bits;     // [R][nz][ny][W] (+1 pad word)
+  int block;                    // threads per block (64, 128 or 256)
+  unsigned long long* bits;     // all replicas' rows (+1 pad word)
+  const LatGeom* geom;          // [R]
   int hmax;                     // largest |half-lattice offset| along x
   int n_shells;                 // shells in use (<= LAT_MAX_SH)
-  int d_uniform;                // domains per colour (SUBLATTICE)
   int n_rows[2];
   LatRow rows[2][LAT_MAX_ROWS];
   double C;                     // pair part of dE(A->B) with no B neighbour
   double G[LAT_MAX_SH];         // change per B neighbour in each shell
   float G32[LAT_MAX_SH];
-  const double* dF;             // [N] F_B(rho_i) - F_A(rho_i)
+  const double* dF;             // [N] F_B(rho_i) - F_A(rho_i) (single lattice)
   const float* dF32;            // [N] the same in FP32
   int df_uniform;               // every site has dF_i = dF0 (perfect lattice)
   double dF0;
   const LatRep* lrep;           // [R]
   // schedule
   int sublattice, qx, qy, qz;
-  int nxq, nyq;                 // nx / qx, ny / qy
-  float rcp_nx, rcp_ny, rcp_qx, rcp_qy, rcp_nxq, rcp_nyq;  // 1/d for fdiv
+  float rcp_qx, rcp_qy;
   int n_colours;
   const int* col_start;
   const int* dom_start;
   const int* dom_sites;
-  int dmax;
+  int dmax;                     // largest pending-slot count of a replica
   // replicas
   const RepParams* rp;
   RepState* rs;
   StepAcc* acc;                 // [R][3]
   long long* n_start;           // [R][2]
-  int* pend;                    // [R][dmax]
+  int* pend;                    // all replicas' pending slots
   LatCtl* ctl;
   unsigned* err;
 };
@@ -119,8 +127,8 @@ struct LatArgs {
 void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
-void launch_lattice_pack(const LatArgs& a, const uint8_t* types, int r, cudaStream_t st);
-void launch_lattice_unpack(const LatArgs& a, uint8_t* types, int r, cudaStream_t st);
+void launch_lattice_pack(const LatArgs& a, const LatGeom& g, const uint8_t* types_r, int r, cudaStream_t st);
+void launch_lattice_unpack(const LatArgs& a, const LatGeom& g, uint8_t* types_r, int r, cudaStream_t st);
 void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st);
 
 // ---- colour step (kernels_mc.cu)

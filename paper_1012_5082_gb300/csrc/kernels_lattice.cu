@@ -1,4 +1,4 @@
-// kernels_lattice.cu -- fused colour step for the rigid BCC lattice with one
+// kernels_lattice.cu -- fused colour step for rigid BCC lattices with one
 // density function (the production form of the parallel VC-SGC sweep,
 // Sec. III B 2 of Sadigh et al.).
 //
@@ -13,9 +13,10 @@
 // those counts).  Lanes of a warp are consecutive trial sites of one row of
 // the colour, so their windows come from the same words.
 //
-// One kernel per colour step k:
-//   1. every block derives the global decision G_{k-1} of the previous step
-//      (its dn was reduced by the previous launch);
+// One kernel per colour step k, for every replica at once (replicas may have
+// different lattice sizes; each has a geometry record):
+//   1. one thread per block derives the global decision G_{k-1} of the
+//      previous step (its dn was reduced by the previous launch);
 //   2. each thread commits its own pending flip of step k-1 with one atomic
 //      XOR that clears the pending bit and flips the species bit if G_{k-1};
 //   3. block (0, r) finalises step k-1 for replica r (n, energy, counters);
@@ -39,17 +40,17 @@ __device__ __forceinline__ int fdiv(int n, int d, float rcp) {
   return q;
 }
 
-__device__ __forceinline__ void decode_site(const LatArgs& a, int i, int& X, int& Y, int& Z, int& b) {
+__device__ __forceinline__ void decode_site(const LatGeom& g, int i, int& X, int& Y, int& Z, int& b) {
   b = i & 1;
   const int cell = i >> 1;
-  const int q = fdiv(cell, a.nx, a.rcp_nx);
-  X = cell - q * a.nx;
-  Z = fdiv(q, a.ny, a.rcp_ny);
-  Y = q - Z * a.ny;
+  const int q = fdiv(cell, g.nx, g.rcp_nx);
+  X = cell - q * g.nx;
+  Z = fdiv(q, g.ny, g.rcp_ny);
+  Y = q - Z * g.ny;
 }
 
-__device__ __forceinline__ unsigned long long* row_ptr(const LatArgs& a, int r, int Y, int Z) {
-  return a.bits + (long long)r * a.rep_words + ((long long)Z * a.ny + Y) * a.W;
+__device__ __forceinline__ unsigned long long* row_ptr(const LatArgs& a, const LatGeom& g, int Y, int Z) {
+  return a.bits + g.bits_off + ((long long)Z * g.ny + Y) * g.W;
 }
 
 // effective 32 species bits of a word under the pending decision mask gm
@@ -73,13 +74,13 @@ __device__ __forceinline__ int own_bit(const unsigned long long* row, int H, uin
 
 // the (up to two) bit copies of site H in its row: main p = 4 + H, halo
 // p - 2 nx (for H >= 2 nx - 4) and p + 2 nx (for H < 4)
-__device__ __forceinline__ void xor_copies(const LatArgs& a, unsigned long long* row, int H,
-                                           bool flip_species, bool flip_pending) {
+__device__ __forceinline__ void xor_copies(int nx, unsigned long long* row, int H, bool flip_species,
+                                           bool flip_pending) {
   int pos[3];
   int n = 0;
   pos[n++] = LAT_HALO + H;
-  if (H >= 2 * a.nx - LAT_HALO) pos[n++] = LAT_HALO + H - 2 * a.nx;
-  if (H < LAT_HALO) pos[n++] = LAT_HALO + H + 2 * a.nx;
+  if (H >= 2 * nx - LAT_HALO) pos[n++] = LAT_HALO + H - 2 * nx;
+  if (H < LAT_HALO) pos[n++] = LAT_HALO + H + 2 * nx;
   for (int q = 0; q < n; ++q) {
     const int p = pos[q];
     unsigned long long m = 0;
@@ -89,13 +90,12 @@ __device__ __forceinline__ void xor_copies(const LatArgs& a, unsigned long long*
   }
 }
 
-// Per-shell B counts of site i of replica r on the effective state, its
-// species t, and the half-coordinate bookkeeping (NS shells).
-// NR > 0: exactly NR rows per basis, unrolled so that every row load is in
-// flight at once; NR = 0: runtime row count.
+// Per-shell B counts of site (X, Y, Z, b) on the effective state and its
+// species t.  NR > 0: exactly NR rows per basis, unrolled so that every row
+// load is in flight at once; NR = 0: runtime row count.
 template <int NS, int NR>
-__device__ __forceinline__ void lattice_counts_at(const LatArgs& a, int r, int X, int Y, int Z, int b,
-                                                  uint32_t gm, int (&cnt)[NS], int& t) {
+__device__ __forceinline__ void lattice_counts_at(const LatArgs& a, const LatGeom& g, int X, int Y, int Z,
+                                                  int b, uint32_t gm, int (&cnt)[NS], int& t) {
   const int H = 2 * X + b;
 #pragma unroll
   for (int s = 0; s < NS; ++s) cnt[s] = 0;
@@ -106,25 +106,17 @@ __device__ __forceinline__ void lattice_counts_at(const LatArgs& a, int r, int X
     if (NR == 0 && q >= nr) break;
     const LatRow& rw = rows[q];
     int yy = Y + rw.dy, zz = Z + rw.dz;
-    yy = yy < 0 ? yy + a.ny : (yy >= a.ny ? yy - a.ny : yy);
-    zz = zz < 0 ? zz + a.nz : (zz >= a.nz ? zz - a.nz : zz);
-    const uint32_t win = window(row_ptr(a, r, yy, zz), H, a.hmax, gm);
+    yy = yy < 0 ? yy + g.ny : (yy >= g.ny ? yy - g.ny : yy);
+    zz = zz < 0 ? zz + g.nz : (zz >= g.nz ? zz - g.nz : zz);
+    const uint32_t win = window(row_ptr(a, g, yy, zz), H, a.hmax, gm);
 #pragma unroll
     for (int s = 0; s < NS; ++s) cnt[s] += __popc(win & rw.mask[s]);
   }
-  t = own_bit(row_ptr(a, r, Y, Z), H, gm);
-}
-
-template <int NS, int NR>
-__device__ __forceinline__ void lattice_counts(const LatArgs& a, int r, int i, uint32_t gm,
-                                               int (&cnt)[NS], int& t) {
-  int X, Y, Z, b;
-  decode_site(a, i, X, Y, Z, b);
-  lattice_counts_at<NS, NR>(a, r, X, Y, Z, b, gm, cnt, t);
+  t = own_bit(row_ptr(a, g, Y, Z), H, gm);
 }
 
 // dE of flipping the site (FP64): the A->B value C + sum_s b_s G_s + dF_i,
-// negated for B->A
+// negated for B->A (i is the site index within its replica)
 template <int NS>
 __device__ __forceinline__ double lattice_de64(const LatArgs& a, const int (&cnt)[NS], int i, int t) {
   double de = a.C;
@@ -132,13 +124,6 @@ __device__ __forceinline__ double lattice_de64(const LatArgs& a, const int (&cnt
   for (int s = 0; s < NS; ++s) de = fma((double)cnt[s], a.G[s], de);
   de += a.df_uniform ? a.dF0 : a.dF[i];
   return t ? -de : de;
-}
-
-template <int NS>
-__device__ __forceinline__ double lattice_delta_e(const LatArgs& a, int r, int i, uint32_t gm, int& t) {
-  int cnt[NS];
-  lattice_counts<NS, 0>(a, r, i, gm, cnt, t);
-  return lattice_de64<NS>(a, cnt, i, t);
 }
 
 // Local Metropolis decision of trial site i, identical to the FP64 decision
@@ -191,13 +176,14 @@ __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long
   return (int)below64(w.x, w.y, (uint64_t)a.n_colours);
 }
 
-template <bool PROPOSE, int NS, int NR>
-__global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
+template <bool PROPOSE, int NS, int NR, int BS>
+__global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   const int r = blockIdx.y;
+  const LatGeom g = a.geom[r];
   const long long k = a.ctl->base_step + j;
   const long long kp = k - 1;
   const RepParams p = a.rp[r];
-  const int d = blockIdx.x * LAT_BLOCK + threadIdx.x;
+  const int d = blockIdx.x * BS + threadIdx.x;
   __shared__ int s_g[2];  // [0] = G_{k-1}, [1] = near-tie of that decision
 
   // 1. global decision of step k-1: one thread per block, FP64
@@ -223,7 +209,7 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
   uint4 w = make_uint4(0, 0, 0, 0);
   if (PROPOSE) {
     const int c = lat_colour(a, p.key, k, nullptr);
-    const int D = a.sublattice ? a.d_uniform : a.col_start[c + 1] - a.col_start[c];
+    const int D = a.sublattice ? g.d : a.col_start[c + 1] - a.col_start[c];
     if (d < D) {
       w = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)((uint64_t)k >> 32), (uint32_t)d, TAG_TRIAL), p.key);
       if (a.sublattice) {
@@ -235,21 +221,21 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
         const int px = pc - pq * a.qx;
         const int pz = fdiv(pq, a.qy, a.rcp_qy);
         const int py = pq - pz * a.qy;
-        const int dq = fdiv(d, a.nxq, a.rcp_nxq);
-        const int kx = d - dq * a.nxq;
-        const int kz = fdiv(dq, a.nyq, a.rcp_nyq);
-        const int ky = dq - kz * a.nyq;
+        const int dq = fdiv(d, g.nxq, g.rcp_nxq);
+        const int kx = d - dq * g.nxq;
+        const int kz = fdiv(dq, g.nyq, g.rcp_nyq);
+        const int ky = dq - kz * g.nyq;
         sX = px + a.qx * kx;
         sY = py + a.qy * ky;
         sZ = pz + a.qz * kz;
         sb_ = b;
-        site = ((sZ * a.ny + sY) * a.nx + sX) * 2 + b;
+        site = ((sZ * g.ny + sY) * g.nx + sX) * 2 + b;
       } else {
-        const int g = a.col_start[c] + d;
-        const int base = a.dom_start[g];
-        const int size = a.dom_start[g + 1] - base;
+        const int gg = a.col_start[c] + d;
+        const int base = a.dom_start[gg];
+        const int size = a.dom_start[gg + 1] - base;
         site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
-        decode_site(a, site, sX, sY, sZ, sb_);
+        decode_site(g, site, sX, sY, sZ, sb_);
       }
     }
   }
@@ -258,12 +244,12 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
   const uint32_t gm = Gp ? 0xFFFFFFFFu : 0u;
 
   // 3. commit this thread's pending flip of step k-1
-  if (d < a.dmax) {
-    int* slot = a.pend + (long long)r * a.dmax + d;
+  if (d < g.dmax) {
+    int* slot = a.pend + g.pend_off + d;
     const int ps = *slot;
     if (ps >= 0) {
       // slot = row * 2048 + H (row = Z ny + Y, H = 2 X + b)
-      xor_copies(a, a.bits + (long long)r * a.rep_words + (long long)(ps >> 11) * a.W, ps & 2047, Gp, true);
+      xor_copies(g.nx, a.bits + g.bits_off + (long long)(ps >> 11) * g.W, ps & 2047, Gp, true);
       *slot = -1;
     }
   }
@@ -276,7 +262,7 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
       const StepAcc A = a.acc[r * 3 + (int)(kp % 3)];
       const long long np = a.n_start[r * 2 + (int)(kp & 1)];
       const int cp = lat_colour(a, p.key, kp, nullptr);
-      const int D = a.sublattice ? a.d_uniform : a.col_start[cp + 1] - a.col_start[cp];
+      const int D = a.sublattice ? g.d : a.col_start[cp + 1] - a.col_start[cp];
       S.trials += D;
       S.local_acc += A.nacc;
       S.near_ties += A.ties + s_g[1];
@@ -296,7 +282,7 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
       }
       S.n = nn;
       a.n_start[r * 2 + (int)(k & 1)] = nn;
-      const double cc = (double)nn / (double)a.N;
+      const double cc = (double)nn / (double)g.n_sites;
       S.sum_c += cc;
       S.sum_c2 += cc * cc;
       S.steps += 1;
@@ -323,11 +309,11 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
   double sdf = 0.0;
   if (site >= 0) {
     int cnt[NS], t;
-    lattice_counts_at<NS, NR>(a, r, sX, sY, sZ, sb_, gm, cnt, t);
+    lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
     if (lattice_accept<NS>(a, a.lrep[r], p, cnt, site, t, top53(w.z, w.w), &tie)) {
       const int H = 2 * sX + sb_;
-      xor_copies(a, row_ptr(a, r, sY, sZ), H, false, true);  // set pending
-      a.pend[(long long)r * a.dmax + d] = (sZ * a.ny + sY) * 2048 + H;
+      xor_copies(g.nx, row_ptr(a, g, sY, sZ), H, false, true);  // set pending
+      a.pend[g.pend_off + d] = (sZ * g.ny + sY) * 2048 + H;
       acc = 1;
       dn = t ? -1 : 1;
 #pragma unroll
@@ -337,8 +323,8 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
   }
   // reduction of dn, accepts, per-shell sums and ties (the paper's
   // allgather of dc_i); warps without an accept or a tie skip the shuffles
-  __shared__ int s_red[LAT_BLOCK / 32][NS + 3];
-  __shared__ double s_df[LAT_BLOCK / 32];
+  __shared__ int s_red[BS / 32][NS + 3];
+  __shared__ double s_df[BS / 32];
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
   const bool any = __ballot_sync(0xffffffffu, acc | tie) != 0u;
   if (any) {
@@ -366,7 +352,7 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
 #pragma unroll
     for (int q = 0; q < NS + 3; ++q) tot[q] = 0;
     double tdf = 0.0;
-    for (int w2 = 0; w2 < LAT_BLOCK / 32; ++w2) {
+    for (int w2 = 0; w2 < BS / 32; ++w2) {
 #pragma unroll
       for (int q = 0; q < NS + 3; ++q) tot[q] += s_red[w2][q];
       if (!a.df_uniform) tdf += s_df[w2];
@@ -386,14 +372,15 @@ __global__ void __launch_bounds__(LAT_BLOCK) k_lattice_step(LatArgs a, int j) {
 
 __global__ void k_lattice_advance(LatCtl* ctl, int n) { ctl->base_step += n; }
 
-// species bytes <-> bit rows (pending bits cleared)
-__global__ void k_lattice_pack(LatArgs a, const uint8_t* types, int r) {
+// species bytes of replica r <-> its bit rows (pending bits cleared)
+__global__ void k_lattice_pack(LatArgs a, const uint8_t* types_r, int r) {
+  const LatGeom g = a.geom[r];
   const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= (long long)a.ny * a.nz) return;
-  unsigned long long* w = a.bits + (long long)r * a.rep_words + row * a.W;
-  const uint8_t* t = types + (long long)r * a.N + row * 2 * a.nx;
-  for (int q = 0; q < a.W; ++q) w[q] = 0ull;
-  const int L = 2 * a.nx;
+  if (row >= (long long)g.ny * g.nz) return;
+  unsigned long long* w = a.bits + g.bits_off + row * g.W;
+  const uint8_t* t = types_r + row * 2 * g.nx;
+  for (int q = 0; q < g.W; ++q) w[q] = 0ull;
+  const int L = 2 * g.nx;
   for (int p = 0; p < L + 2 * LAT_HALO; ++p) {
     int H = p - LAT_HALO;
     H = H < 0 ? H + L : (H >= L ? H - L : H);
@@ -401,26 +388,25 @@ __global__ void k_lattice_pack(LatArgs a, const uint8_t* types, int r) {
   }
 }
 
-__global__ void k_lattice_unpack(LatArgs a, uint8_t* types, int r) {
+__global__ void k_lattice_unpack(LatArgs a, uint8_t* types_r, int r) {
+  const LatGeom g = a.geom[r];
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
+  if (i >= g.n_sites) return;
   int X, Y, Z, b;
-  decode_site(a, (int)i, X, Y, Z, b);
-  types[(long long)r * a.N + i] = (uint8_t)own_bit(row_ptr(a, r, Y, Z), 2 * X + b, 0u);
+  decode_site(g, (int)i, X, Y, Z, b);
+  types_r[i] = (uint8_t)own_bit(row_ptr(a, g, Y, Z), 2 * X + b, 0u);
 }
 
 template <int NS>
 __global__ void k_lattice_delta_e(LatArgs a, int r, const int* sites, int n, double* out) {
+  const LatGeom g = a.geom[r];
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  int t;
-  if (q < n) out[q] = lattice_delta_e<NS>(a, r, sites[q], 0u, t);
-}
-
-template <int NS, int NR>
-static void step_ns(const LatArgs& a, int j, bool propose, cudaStream_t st) {
-  const dim3 g((a.dmax + LAT_BLOCK - 1) / LAT_BLOCK, a.R);
-  if (propose) k_lattice_step<true, NS, NR><<<g, LAT_BLOCK, 0, st>>>(a, j);
-  else k_lattice_step<false, NS, NR><<<g, LAT_BLOCK, 0, st>>>(a, j);
+  if (q >= n) return;
+  int X, Y, Z, b, t;
+  decode_site(g, sites[q], X, Y, Z, b);
+  int cnt[NS];
+  lattice_counts_at<NS, 0>(a, g, X, Y, Z, b, 0u, cnt, t);
+  out[q] = lattice_de64<NS>(a, cnt, sites[q], t);
 }
 
 __global__ void k_to_float(const double* in, float* out, long long n) {
@@ -430,6 +416,22 @@ __global__ void k_to_float(const double* in, float* out, long long n) {
 
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st) {
   k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
+}
+
+template <int NS, int NR, int BS>
+static void step_bs(const LatArgs& a, int j, bool propose, cudaStream_t st) {
+  const dim3 g((a.dmax + BS - 1) / BS, a.R);
+  if (propose) k_lattice_step<true, NS, NR, BS><<<g, BS, 0, st>>>(a, j);
+  else k_lattice_step<false, NS, NR, BS><<<g, BS, 0, st>>>(a, j);
+}
+
+template <int NS, int NR>
+static void step_ns(const LatArgs& a, int j, bool propose, cudaStream_t st) {
+  switch (a.block) {
+    case 64: step_bs<NS, NR, 64>(a, j, propose, st); break;
+    case 256: step_bs<NS, NR, 256>(a, j, propose, st); break;
+    default: step_bs<NS, NR, 128>(a, j, propose, st); break;
+  }
 }
 
 // shells and neighbour rows as compile-time constants: the 5-shell, 13-row
@@ -446,13 +448,13 @@ void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st) {
   k_lattice_advance<<<1, 1, 0, st>>>(a.ctl, n);
 }
 
-void launch_lattice_pack(const LatArgs& a, const uint8_t* types, int r, cudaStream_t st) {
-  const long long rows = (long long)a.ny * a.nz;
-  k_lattice_pack<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(a, types, r);
+void launch_lattice_pack(const LatArgs& a, const LatGeom& g, const uint8_t* types_r, int r, cudaStream_t st) {
+  const long long rows = (long long)g.ny * g.nz;
+  k_lattice_pack<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(a, types_r, r);
 }
 
-void launch_lattice_unpack(const LatArgs& a, uint8_t* types, int r, cudaStream_t st) {
-  k_lattice_unpack<<<(unsigned)((a.N + 255) / 256), 256, 0, st>>>(a, types, r);
+void launch_lattice_unpack(const LatArgs& a, const LatGeom& g, uint8_t* types_r, int r, cudaStream_t st) {
+  k_lattice_unpack<<<(unsigned)((g.n_sites + 255) / 256), 256, 0, st>>>(a, types_r, r);
 }
 
 void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st) {

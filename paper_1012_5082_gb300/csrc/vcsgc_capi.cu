@@ -87,6 +87,14 @@ struct Ctx {
   MdArgs md{};
   // fused lattice form
   bool fast = false;
+  bool no_fast = false;            // set-up only (sub-context of a batch)
+  std::vector<LatGeom> h_geom;
+  double df_absmax = 0.0, sum_absG = 0.0;
+  // per-replica species arrays and sizes (single lattice: slices of types;
+  // batch: the sub-contexts' arrays)
+  std::vector<uint8_t*> rep_types;
+  std::vector<long long> rep_n;
+  std::vector<struct Ctx*> subs;   // batch of lattices of different sizes
   LatArgs lat{};
   long long h_base = 0;            // host mirror of lat.ctl->base_step
   std::vector<int3> offsets;       // half-lattice neighbour offsets (kind 0)
@@ -207,9 +215,7 @@ void fill_args(Ctx* c) {
   m.max_disp2_bits = c->max_disp2;
 
   LatArgs& l = c->lat;
-  l.N = c->N;
   l.R = c->R;
-  l.dF = c->dF;
   l.sublattice = c->sched_kind == VCSGC_SCHED_SUBLATTICE ? 1 : 0;
   l.qx = c->sched[0];
   l.qy = c->sched[1];
@@ -218,7 +224,6 @@ void fill_args(Ctx* c) {
   l.col_start = c->col_start;
   l.dom_start = c->dom_start;
   l.dom_sites = c->dom_sites;
-  l.dmax = c->dmax;
   l.rp = c->rp;
   l.rs = c->rs;
   l.err = c->derr;
@@ -430,6 +435,12 @@ int positions_host(Ctx* c, std::vector<double>& hx, std::vector<double>& hy, std
 // --------------------------------------------------------------- energy
 int energy_of(Ctx* c, int r, double* out) {
   TRY(sync_bytes(c, r));
+  if (!c->subs.empty()) {
+    CK(cudaStreamSynchronize(c->st));
+    const int rc = energy_of(c->subs[r], 0, out);
+    if (rc != VCSGC_OK) c->err = c->subs[r]->err;
+    return rc;
+  }
   launch_energy(c->mc, c->shell, r, c->part, c->st);
   CK(cudaGetLastError());
   std::vector<double> h(c->part_n);
@@ -514,7 +525,7 @@ int sync_bytes(Ctx* c, int r) {
   if (!c->fast) return VCSGC_OK;
   TRY(flush(c));
   for (int q = 0; q < c->R; ++q)
-    if (r < 0 || q == r) launch_lattice_unpack(c->lat, c->types, q, c->st);
+    if (r < 0 || q == r) launch_lattice_unpack(c->lat, c->h_geom[q], c->rep_types[q], q, c->st);
   CK(cudaGetLastError());
   return VCSGC_OK;
 }
@@ -833,6 +844,9 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   // ---- buffers
   TRY(dalloc(c, &c->types, (size_t)c->R * c->N));
   CK(cudaMemcpyAsync(c->types, types, (size_t)c->R * c->N, cudaMemcpyHostToDevice, c->st));
+  c->rep_types.resize(c->R);
+  c->rep_n.assign(c->R, c->N);
+  for (int r = 0; r < c->R; ++r) c->rep_types[r] = c->types + (long long)r * c->N;
   TRY(dalloc(c, &c->rho, (size_t)(c->reembed ? c->R : 1) * c->N));
   TRY(dalloc(c, &c->dF, c->N));
   TRY(dalloc(c, &c->dFp, c->N));
@@ -908,9 +922,11 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   return VCSGC_OK;
 }
 
-// The fused bit-packed form applies to a rigid lattice with one density
-// function and a BLOCKS or SUBLATTICE schedule.
-static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
+// Shared part of the fused bit-packed form (rows and shell masks of the
+// neighbourhood, shell constants, dF): 0 when set up, 1 when the lattice is
+// outside the form (the two-launch colour step is used instead).
+static int lattice_shared(Ctx* c, int& unsupported) {
+  unsupported = 1;
   if (c->kind != 0 || c->reembed || c->nx < 2) return VCSGC_OK;
   // index arithmetic of the fused form: sites < 2^22, rows < 2^20, 2 nx < 2048
   if (c->N > (1LL << 22) || 2 * c->nx >= 2048 || (long long)c->ny * c->nz >= (1LL << 20)) return VCSGC_OK;
@@ -949,84 +965,113 @@ static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
     l.G32[s] = (float)l.G[s];
   }
   // dF_i = F_B(rho_i) - F_A(rho_i): uniform on a perfect lattice
-  {
-    std::vector<double> dF(c->N);
-    CK(cudaMemcpyAsync(dF.data(), c->dF, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    bool uni = true;
-    double dmax = 0.0;
-    for (long long i = 0; i < c->N; ++i) {
-      if (dF[i] != dF[0]) uni = false;
-      dmax = std::max(dmax, std::fabs(dF[i]));
-    }
-    l.df_uniform = uni ? 1 : 0;
-    l.dF0 = dF[0];
-    float* df32 = nullptr;
-    TRY(dalloc(c, &df32, c->N));
-    launch_to_float(c->dF, df32, c->N, c->st);
-    CK(cudaGetLastError());
-    l.dF32 = df32;
-    // FP32 screen: per-replica constants and the bound on |X32 - X|
-    std::vector<int> zs(S, 0);
-    for (int sh : c->offset_shell) zs[sh]++;
-    double sumG = 0.0;
-    for (int s = 0; s < S; ++s) sumG += zs[s] * std::fabs(l.G[s]);
-    std::vector<LatRep> lr(c->R);
-    for (int r = 0; r < c->R; ++r) {
-      const RepParams& p = c->h_rp[r];
-      const double cpd = l.C + p.dmu0 + (uni ? l.dF0 : 0.0);
-      const double M = std::fabs(l.C) + std::fabs(p.dmu0) + sumG + dmax + std::fabs(cpd);
-      lr[r].cpd32 = (float)cpd;
-      lr[r].beta32 = (float)p.beta;
-      // (2 S + 3) roundings of at most 2^-24 M each, times beta, four-fold margin
-      lr[r].dx = (float)(4.0 * p.beta * (2 * S + 3) * std::ldexp(M, -24));
-      lr[r].pad = 0.0f;
-    }
-    LatRep* dlr = nullptr;
-    TRY(dalloc(c, &dlr, c->R));
-    CK(cudaMemcpyAsync(dlr, lr.data(), sizeof(LatRep) * c->R, cudaMemcpyHostToDevice, c->st));
-    CK(cudaStreamSynchronize(c->st));
-    l.lrep = dlr;
+  std::vector<double> dF(c->N);
+  CK(cudaMemcpyAsync(dF.data(), c->dF, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  bool uni = true;
+  c->df_absmax = 0.0;
+  for (long long i = 0; i < c->N; ++i) {
+    if (dF[i] != dF[0]) uni = false;
+    c->df_absmax = std::max(c->df_absmax, std::fabs(dF[i]));
   }
+  l.df_uniform = uni ? 1 : 0;
+  l.dF0 = dF[0];
+  float* df32 = nullptr;
+  TRY(dalloc(c, &df32, c->N));
+  launch_to_float(c->dF, df32, c->N, c->st);
+  CK(cudaGetLastError());
+  l.dF = c->dF;
+  l.dF32 = df32;
   l.hmax = hmax;
   l.n_shells = S;
-  l.rcp_nx = 1.0f / (float)c->nx;
-  l.rcp_ny = 1.0f / (float)c->ny;
-  if (c->sched_kind == VCSGC_SCHED_SUBLATTICE) {
-    l.nxq = c->nx / c->sched[0];
-    l.nyq = c->ny / c->sched[1];
-    l.rcp_qx = 1.0f / (float)c->sched[0];
-    l.rcp_qy = 1.0f / (float)c->sched[1];
-    l.rcp_nxq = 1.0f / (float)l.nxq;
-    l.rcp_nyq = 1.0f / (float)l.nyq;
+  std::vector<int> zs(S, 0);
+  for (int sh : c->offset_shell) zs[sh]++;
+  c->sum_absG = 0.0;
+  for (int s = 0; s < S; ++s) c->sum_absG += zs[s] * std::fabs(l.G[s]);
+  unsupported = 0;
+  return VCSGC_OK;
+}
+
+// FP32-screen constants of replica parameters p (bound on |X32 - X|)
+static LatRep lattice_rep(const Ctx* c, const RepParams& p) {
+  const LatArgs& l = c->lat;
+  const int S = l.n_shells;
+  LatRep lr;
+  const double cpd = l.C + p.dmu0 + (l.df_uniform ? l.dF0 : 0.0);
+  const double M = std::fabs(l.C) + std::fabs(p.dmu0) + c->sum_absG + c->df_absmax + std::fabs(cpd);
+  lr.cpd32 = (float)cpd;
+  lr.beta32 = (float)p.beta;
+  // (2 S + 3) roundings of at most 2^-24 M each, times beta, four-fold margin
+  lr.dx = (float)(4.0 * p.beta * (2 * S + 3) * std::ldexp(M, -24));
+  lr.pad = 0.0f;
+  return lr;
+}
+
+static LatGeom lattice_geom(int nx, int ny, int nz, const int q[3], int d, int dmax, long long bits_off,
+                            long long pend_off) {
+  LatGeom g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.W = (2 * nx + 2 * LAT_HALO + 31) / 32;
+  g.bits_off = bits_off;
+  g.pend_off = pend_off;
+  g.n_sites = 2LL * nx * ny * nz;
+  g.d = d;
+  g.dmax = dmax;
+  g.rcp_nx = 1.0f / (float)nx;
+  g.rcp_ny = 1.0f / (float)ny;
+  g.nxq = q ? nx / q[0] : 0;
+  g.nyq = q ? ny / q[1] : 0;
+  g.rcp_nxq = q ? 1.0f / (float)g.nxq : 0.0f;
+  g.rcp_nyq = q ? 1.0f / (float)g.nyq : 0.0f;
+  return g;
+}
+
+// Allocate and initialise the per-replica state of the fused form: rows of
+// all replicas in one array, accumulators, pending slots; pack the species.
+static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::vector<LatRep>& lr) {
+  LatArgs& l = c->lat;
+  const int R = c->R;
+  long long words = 0, slots = 0;
+  int dmax = 0;
+  for (const LatGeom& g : c->h_geom) {
+    words = std::max(words, g.bits_off + (long long)g.ny * g.nz * g.W);
+    slots = std::max(slots, g.pend_off + g.dmax);
+    dmax = std::max(dmax, g.dmax);
   }
-  l.d_uniform = c->sublattice_d;
-  l.nx = c->nx;
-  l.ny = c->ny;
-  l.nz = c->nz;
-  l.W = (2 * c->nx + 2 * LAT_HALO + 31) / 32;
-  l.rep_words = (long long)c->ny * c->nz * l.W;
-  TRY(dalloc(c, &l.bits, (size_t)(c->R * l.rep_words + 1)));
-  TRY(dalloc(c, &l.acc, (size_t)c->R * 3));
-  TRY(dalloc(c, &l.n_start, (size_t)c->R * 2));
-  TRY(dalloc(c, &l.pend, (size_t)c->R * c->dmax));
+  LatGeom* dg = nullptr;
+  LatRep* dlr = nullptr;
+  TRY(dalloc(c, &dg, R));
+  TRY(dalloc(c, &dlr, R));
+  TRY(dalloc(c, &l.bits, (size_t)(words + 1)));
+  TRY(dalloc(c, &l.acc, (size_t)R * 3));
+  TRY(dalloc(c, &l.n_start, (size_t)R * 2));
+  TRY(dalloc(c, &l.pend, (size_t)slots));
   TRY(dalloc(c, &l.ctl, 1));
-  CK(cudaMemsetAsync(l.bits, 0, sizeof(unsigned long long) * (c->R * l.rep_words + 1), c->st));
-  CK(cudaMemsetAsync(l.acc, 0, sizeof(StepAcc) * c->R * 3, c->st));
-  CK(cudaMemsetAsync(l.pend, 0xFF, sizeof(int) * c->R * c->dmax, c->st));
+  CK(cudaMemcpyAsync(dg, c->h_geom.data(), sizeof(LatGeom) * R, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(dlr, lr.data(), sizeof(LatRep) * R, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(l.bits, 0, sizeof(unsigned long long) * (words + 1), c->st));
+  CK(cudaMemsetAsync(l.acc, 0, sizeof(StepAcc) * R * 3, c->st));
+  CK(cudaMemsetAsync(l.pend, 0xFF, sizeof(int) * slots, c->st));
   CK(cudaMemsetAsync(l.ctl, 0, sizeof(LatCtl), c->st));
-  std::vector<long long> ns(2 * c->R, 0);
-  for (int r = 0; r < c->R; ++r) ns[2 * r] = hs[r].n;
+  std::vector<long long> ns(2 * R, 0);
+  for (int r = 0; r < R; ++r) ns[2 * r] = n0[r];
   CK(cudaMemcpyAsync(l.n_start, ns.data(), sizeof(long long) * ns.size(), cudaMemcpyHostToDevice, c->st));
   // fin_step = -1: no step finalised yet
-  std::vector<RepState> rs(c->R);
-  CK(cudaMemcpyAsync(rs.data(), c->rs, sizeof(RepState) * c->R, cudaMemcpyDeviceToHost, c->st));
+  std::vector<RepState> rs(R);
+  CK(cudaMemcpyAsync(rs.data(), c->rs, sizeof(RepState) * R, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  for (auto& s : rs) s.fin_step = -1;
-  CK(cudaMemcpyAsync(c->rs, rs.data(), sizeof(RepState) * c->R, cudaMemcpyHostToDevice, c->st));
+  for (auto& st : rs) st.fin_step = -1;
+  CK(cudaMemcpyAsync(c->rs, rs.data(), sizeof(RepState) * R, cudaMemcpyHostToDevice, c->st));
+  l.geom = dg;
+  l.lrep = dlr;
+  l.dmax = dmax;
+  l.R = R;
+  if (l.block == 0) l.block = 128;
   c->fast = true;
   fill_args(c);
-  for (int r = 0; r < c->R; ++r) launch_lattice_pack(l, c->types, r, c->st);
+  for (int r = 0; r < R; ++r) launch_lattice_pack(l, c->h_geom[r], c->rep_types[r], r, c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   c->h_base = 0;
@@ -1034,8 +1079,38 @@ static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
   return check_device_error(c);
 }
 
+// The fused bit-packed form applies to a rigid lattice with one density
+// function and a BLOCKS or SUBLATTICE schedule.
+static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
+  if (c->no_fast) return VCSGC_OK;
+  int unsupported = 1;
+  TRY(lattice_shared(c, unsupported));
+  if (unsupported) return VCSGC_OK;
+  LatArgs& l = c->lat;
+  const int q[3] = {c->sched[0], c->sched[1], c->sched[2]};
+  const bool sub = c->sched_kind == VCSGC_SCHED_SUBLATTICE;
+  if (sub) {
+    l.rcp_qx = 1.0f / (float)q[0];
+    l.rcp_qy = 1.0f / (float)q[1];
+  }
+  c->h_geom.clear();
+  const long long W = (2 * c->nx + 2 * LAT_HALO + 31) / 32;
+  for (int r = 0; r < c->R; ++r)
+    c->h_geom.push_back(lattice_geom(c->nx, c->ny, c->nz, sub ? q : nullptr, c->sublattice_d, c->dmax,
+                                     (long long)r * c->ny * c->nz * W, (long long)r * c->dmax));
+  std::vector<long long> n0(c->R);
+  std::vector<LatRep> lr(c->R);
+  for (int r = 0; r < c->R; ++r) {
+    n0[r] = hs[r].n;
+    lr[r] = lattice_rep(c, c->h_rp[r]);
+  }
+  return lattice_state(c, n0, lr);
+}
+
 static void destroy(Ctx* c) {
   if (!c) return;
+  for (Ctx* sc : c->subs) destroy(sc);
+  c->subs.clear();
   drop_graph(c);
   if (c->st) cudaStreamSynchronize(c->st);
   for (void* p : c->allocs) cudaFree(p);
@@ -1066,6 +1141,176 @@ int vcsgc_init(void** out, const vcsgc_lattice* L, const uint8_t* types, const v
 
 void vcsgc_free(void* ctx) { destroy(static_cast<Ctx*>(ctx)); }
 
+// Batch of rigid BCC lattices of different sizes: each replica is set up by a
+// context of its own (neighbour list, rho, energy, shell constants), then all
+// replicas' species are packed into one bit array and advanced by the same
+// fused colour-step launches.
+static int batch_impl(Ctx* c, int32_t n_rep, const int32_t* cells, double a, const uint8_t* types,
+                      const vcsgc_eam_tables* E, const double* phi, const double* kappa, const double* T,
+                      const vcsgc_options* o) {
+  if (n_rep < 1 || !cells || !types || !E || !phi || !kappa || !T || !o)
+    return fail(c, VCSGC_ERR_INVALID_ARG, "null argument or no replicas");
+  if (o->schedule != VCSGC_SCHED_SUBLATTICE) return fail(c, VCSGC_ERR_INVALID_ARG, "a batch needs the SUBLATTICE schedule");
+  if (o->device >= 0) {
+    CK(cudaSetDevice(o->device));
+    c->device = o->device;
+  } else {
+    CK(cudaGetDevice(&c->device));
+  }
+  if (o->stream) {
+    c->st = (cudaStream_t)o->stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  c->R = n_rep;
+  c->kind = 0;
+  c->sched_kind = o->schedule;
+  std::memcpy(c->sched, o->sched, sizeof(c->sched));
+  c->mixed = o->precision == VCSGC_PREC_MIXED;
+  long long off = 0;
+  for (int r = 0; r < n_rep; ++r) {
+    vcsgc_options so = *o;
+    so.n_replicas = 1;
+    so.phi_r = so.kappa_r = so.T_r = so.c0_r = nullptr;
+    so.seed_r = nullptr;
+    so.seed = o->seed_r ? o->seed_r[r] : o->seed + (uint64_t)r;
+    so.c0 = o->c0_r ? o->c0_r[r] : o->c0;
+    so.stream = c->st;
+    vcsgc_lattice L;
+    std::memset(&L, 0, sizeof(L));
+    L.kind = 0;
+    L.nx = cells[3 * r];
+    L.ny = cells[3 * r + 1];
+    L.nz = cells[3 * r + 2];
+    L.a = a;
+    Ctx* sc = new (std::nothrow) Ctx();
+    if (!sc) return fail(c, VCSGC_ERR_NOMEM, "host allocation failed");
+    sc->no_fast = true;
+    c->subs.push_back(sc);
+    const int rc = init_impl(sc, &L, types + off, E, phi[r], kappa[r], T[r], &so);
+    if (rc != VCSGC_OK) return fail(c, rc, "replica " + std::to_string(r) + ": " + sc->err);
+    off += sc->N;
+  }
+  Ctx* s0 = c->subs[0];
+  // shared parts from the first replica; every replica shares a, r_c and
+  // the tables, hence the neighbourhood and the shell constants
+  c->nx = s0->nx; c->ny = s0->ny; c->nz = s0->nz; c->a = a;
+  c->N = s0->N;
+  c->dF = s0->dF;
+  c->shell_tab = s0->shell_tab;
+  c->mc.n_shells = s0->mc.n_shells;
+  c->offsets = s0->offsets;
+  c->offset_shell = s0->offset_shell;
+  c->n_colours = s0->n_colours;
+  c->col_start = s0->col_start;
+  c->dom_start = s0->dom_start;
+  c->dom_sites = s0->dom_sites;
+  c->steps_per_sweep = s0->steps_per_sweep;
+  TRY(dalloc(c, &c->derr, 1));
+  CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+  int unsupported = 1;
+  TRY(lattice_shared(c, unsupported));
+  if (unsupported || !c->lat.df_uniform)
+    return fail(c, VCSGC_ERR_INVALID_ARG, "a batch needs perfect rigid lattices with one density function");
+  const int q[3] = {c->sched[0], c->sched[1], c->sched[2]};
+  c->lat.rcp_qx = 1.0f / (float)q[0];
+  c->lat.rcp_qy = 1.0f / (float)q[1];
+  c->h_geom.clear();
+  c->rep_types.clear();
+  c->rep_n.clear();
+  c->h_rp.clear();
+  std::vector<long long> n0;
+  std::vector<LatRep> lr;
+  std::vector<RepState> rs;
+  long long words = 0, slots = 0;
+  for (int r = 0; r < n_rep; ++r) {
+    Ctx* sc = c->subs[r];
+    if (sc->steps_per_sweep != c->steps_per_sweep || sc->mc.n_shells != c->mc.n_shells)
+      return fail(c, VCSGC_ERR_INVALID_ARG, "replicas must share the schedule period");
+    const LatGeom g = lattice_geom(sc->nx, sc->ny, sc->nz, q, sc->sublattice_d, sc->dmax, words, slots);
+    words += (long long)g.ny * g.nz * g.W;
+    slots += g.dmax;
+    c->h_geom.push_back(g);
+    c->rep_types.push_back(sc->types);
+    c->rep_n.push_back(sc->N);
+    c->h_rp.push_back(sc->h_rp[0]);
+    RepState st;
+    CK(cudaMemcpyAsync(&st, sc->rs, sizeof(RepState), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    n0.push_back(st.n);
+    rs.push_back(st);
+    lr.push_back(lattice_rep(c, sc->h_rp[0]));
+  }
+  c->dmax = 0;
+  for (const LatGeom& g : c->h_geom) c->dmax = std::max(c->dmax, g.dmax);
+  TRY(dalloc(c, &c->rp, n_rep));
+  TRY(dalloc(c, &c->rs, n_rep));
+  CK(cudaMemcpyAsync(c->rp, c->h_rp.data(), sizeof(RepParams) * n_rep, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->rs, rs.data(), sizeof(RepState) * n_rep, cudaMemcpyHostToDevice, c->st));
+  c->sublattice_d = s0->sublattice_d;
+  return lattice_state(c, n0, lr);
+}
+
+int vcsgc_batch_init(void** out, int32_t n_rep, const int32_t* cells, double a, const uint8_t* types,
+                     const vcsgc_eam_tables* E, const double* phi, const double* kappa, const double* T,
+                     const vcsgc_options* opt) {
+  if (!out) return VCSGC_ERR_INVALID_ARG;
+  *out = nullptr;
+  vcsgc_options def;
+  vcsgc_default_options(&def);
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) {
+    g_init_error = "host allocation failed";
+    return VCSGC_ERR_NOMEM;
+  }
+  const int rc = batch_impl(c, n_rep, cells, a, types, E, phi, kappa, T, opt ? opt : &def);
+  if (rc != VCSGC_OK) {
+    g_init_error = c->err;
+    destroy(c);
+    return rc;
+  }
+  *out = c;
+  return VCSGC_OK;
+}
+
+int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || steps < 1 || !best_block) return VCSGC_ERR_INVALID_ARG;
+  if (!c->fast) {
+    *best_block = MC_BLOCK;
+    return VCSGC_OK;
+  }
+  const int cand[3] = {64, 128, 256};
+  float best = 0.0f;
+  int bb = 128;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int b : cand) {
+    c->lat.block = b;
+    drop_graph(c);
+    // one untimed step with the candidate, then the timed ones
+    TRY(run_steps_fast(c, 1));
+    CK(cudaEventRecord(e0, c->st));
+    TRY(run_steps_fast(c, steps));
+    CK(cudaEventRecord(e1, c->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (best == 0.0f || ms < best) {
+      best = ms;
+      bb = b;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->lat.block = bb;
+  drop_graph(c);
+  *best_block = bb;
+  return check_device_error(c);
+}
+
 const char* vcsgc_last_error(void* ctx) {
   if (!ctx) return g_init_error.c_str();
   return static_cast<Ctx*>(ctx)->err.c_str();
@@ -1093,6 +1338,7 @@ int vcsgc_sweep(void* ctx, int64_t n) {
 int md_steps(void* ctx, int64_t n) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n < 0) return VCSGC_ERR_INVALID_ARG;
+  if (!c->subs.empty()) return fail(c, VCSGC_ERR_STATE, "no MD on a batch");
   TRY(md_run(c, n));
   return check_device_error(c);
 }
@@ -1131,11 +1377,12 @@ int observables(void* ctx, int32_t r, vcsgc_observables* o) {
   CK(cudaStreamSynchronize(c->st));
   const RepParams& p = c->h_rp[r];
   std::memset(o, 0, sizeof(*o));
-  o->n_sites = c->N;
+  const double Nr = (double)c->rep_n[r];
+  o->n_sites = c->rep_n[r];
   o->n_b = s.n;
-  o->c = (double)s.n / (double)c->N;
+  o->c = (double)s.n / Nr;
   o->energy = s.energy;
-  o->energy_per_atom = s.energy / (double)c->N;
+  o->energy_per_atom = s.energy / Nr;
   o->steps = s.steps;
   o->trials = s.trials;
   o->local_accepts = s.local_acc;
@@ -1147,8 +1394,8 @@ int observables(void* ctx, int32_t r, vcsgc_observables* o) {
   o->acc_global = s.global_trials ? (double)s.global_acc / (double)s.global_trials : 0.0;
   o->mean_c = s.steps ? s.sum_c / (double)s.steps : o->c;
   o->var_c = s.steps ? std::max(0.0, s.sum_c2 / (double)s.steps - o->mean_c * o->mean_c) : 0.0;
-  o->dmu_est = p.phi + 2.0 * p.kappa_p * (double)c->N * o->mean_c;
-  o->sweeps = (double)s.trials / (double)c->N;
+  o->dmu_est = p.phi + 2.0 * p.kappa_p * Nr * o->mean_c;
+  o->sweeps = (double)s.trials / Nr;
   o->kappa_p = p.kappa_p;
   o->dmu0 = p.dmu0;
   return VCSGC_OK;
@@ -1158,25 +1405,41 @@ int vcsgc_get_types(void* ctx, int32_t r, uint8_t* out) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   TRY(sync_bytes(c, r));
-  CK(cudaMemcpyAsync(out, c->types + (long long)r * c->N, c->N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(out, c->rep_types[r], c->rep_n[r], cudaMemcpyDeviceToHost, c->st));
   return check_device_error(c);
 }
 
 int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !in || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
-  for (long long i = 0; i < c->N; ++i)
+  const long long Nr = c->rep_n[r];
+  for (long long i = 0; i < Nr; ++i)
     if (in[i] > 1) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
   TRY(flush(c));
-  CK(cudaMemcpyAsync(c->types + (long long)r * c->N, in, c->N, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->rep_types[r], in, Nr, cudaMemcpyHostToDevice, c->st));
   if (c->fast) {
     long long nb = 0;
-    for (long long i = 0; i < c->N; ++i) nb += in[i];
-    launch_lattice_pack(c->lat, c->types, r, c->st);
+    for (long long i = 0; i < Nr; ++i) nb += in[i];
+    launch_lattice_pack(c->lat, c->h_geom[r], c->rep_types[r], r, c->st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->lat.n_start + 2 * r + (c->h_base & 1), &nb, sizeof(long long),
                        cudaMemcpyHostToDevice, c->st));
     CK(cudaStreamSynchronize(c->st));
+  }
+  if (!c->subs.empty()) {
+    // batch: n and the energy of replica r come from its set-up context
+    long long nb = 0;
+    for (long long i = 0; i < Nr; ++i) nb += in[i];
+    double e = 0.0;
+    TRY(energy_of(c, r, &e));
+    RepState st;
+    CK(cudaMemcpyAsync(&st, c->rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    st.n = nb;
+    st.energy = e;
+    CK(cudaMemcpyAsync(c->rs + r, &st, sizeof(RepState), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return check_device_error(c);
   }
   TRY(sync_state_from_types(c, r, in));
   c->forces_valid = false;
@@ -1186,6 +1449,7 @@ int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
 int vcsgc_get_rho(void* ctx, int32_t r, double* out) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  if (!c->subs.empty()) return vcsgc_get_rho(c->subs[r], 0, out);
   const double* src = c->rho + (c->reembed ? (long long)r * c->N : 0);
   CK(cudaMemcpyAsync(out, src, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
   return check_device_error(c);
@@ -1197,7 +1461,7 @@ int vcsgc_delta_e(void* ctx, int32_t r, const int64_t* sites, int64_t n, double*
   if (n == 0) return VCSGC_OK;
   std::vector<int> s32(n);
   for (int64_t q = 0; q < n; ++q) {
-    if (sites[q] < 0 || sites[q] >= c->N) return fail(c, VCSGC_ERR_INVALID_ARG, "site index out of range");
+    if (sites[q] < 0 || sites[q] >= c->rep_n[r]) return fail(c, VCSGC_ERR_INVALID_ARG, "site index out of range");
     s32[q] = (int)sites[q];
   }
   if (n > c->sites_cap) {
@@ -1226,6 +1490,7 @@ int vcsgc_energy(void* ctx, int32_t r, double* out) {
 int vcsgc_forces(void* ctx, double* fx, double* fy, double* fz) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !fx || !fy || !fz) return VCSGC_ERR_INVALID_ARG;
+  if (!c->subs.empty()) return fail(c, VCSGC_ERR_STATE, "forces are not defined for a batch");
   if (!c->forces_valid) TRY(md_forces(c));
   CK(cudaMemcpyAsync(fx, c->fx, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
   CK(cudaMemcpyAsync(fy, c->fy, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
@@ -1236,6 +1501,7 @@ int vcsgc_forces(void* ctx, double* fx, double* fy, double* fz) {
 int vcsgc_get_md(void* ctx, double* x, double* y, double* z, double* vx, double* vy, double* vz) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return VCSGC_ERR_INVALID_ARG;
+  if (!c->subs.empty()) return fail(c, VCSGC_ERR_STATE, "positions are per replica in a batch");
   double* dst[6] = {x, y, z, vx, vy, vz};
   double* src[6] = {c->x, c->y, c->z, c->vx, c->vy, c->vz};
   for (int q = 0; q < 6; ++q) {
@@ -1249,6 +1515,7 @@ int vcsgc_get_md(void* ctx, double* x, double* y, double* z, double* vx, double*
 int vcsgc_set_velocities(void* ctx, const double* vx, const double* vy, const double* vz) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !vx || !vy || !vz) return VCSGC_ERR_INVALID_ARG;
+  if (!c->subs.empty()) return fail(c, VCSGC_ERR_STATE, "no MD on a batch");
   if (c->R != 1) return fail(c, VCSGC_ERR_STATE, "velocities need one replica");
   if (!c->vx) {
     TRY(dalloc(c, &c->vx, c->N));
@@ -1321,6 +1588,7 @@ int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_com
 int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* count) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out || !count || i < 0 || i >= c->N || cap < 0) return VCSGC_ERR_INVALID_ARG;
+  if (!c->subs.empty()) return fail(c, VCSGC_ERR_STATE, "neighbour lists are per replica in a batch");
   int cnt = 0;
   CK(cudaMemcpyAsync(&cnt, c->nbr_cnt + i, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));

@@ -65,7 +65,8 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "md_steps", "vcsgc_hybrid", "observables", "vcsgc_get_types", "vcsgc_set_types",
            "vcsgc_get_rho", "vcsgc_delta_e", "vcsgc_energy", "vcsgc_forces", "vcsgc_get_md",
            "vcsgc_set_velocities", "vcsgc_kinetic_energy", "vcsgc_neighbours", "vcsgc_last_error",
-           "vcsgc_free", "vcsgc_profile_steps", "vcsgc_neighbour_list_noalloc"]
+           "vcsgc_free", "vcsgc_profile_steps", "vcsgc_neighbour_list_noalloc", "vcsgc_batch_init",
+           "vcsgc_autotune"]
 
 
 def lib():
@@ -98,6 +99,8 @@ def lib():
             "vcsgc_neighbours": (I32, [P, I64, P, I32, P]),
             "vcsgc_profile_steps": (I32, [P, I64, P, P]),
             "vcsgc_neighbour_list_noalloc": (I32, [I64, P, P, P, P, D, I32, P, P, P]),
+            "vcsgc_batch_init": (I32, [C.POINTER(C.c_void_p), I32, P, D, P, P, P, P, P, P]),
+            "vcsgc_autotune": (I32, [P, I64, P]),
             "vcsgc_last_error": (C.c_char_p, [P]),
             "vcsgc_free": (None, [P]),
         }
@@ -168,6 +171,28 @@ def vcsgc_neighbour_list_noalloc(n, d_x, d_y, d_z, box, rl, K, d_nbr, d_cnt, str
 
 
 # ----------------------------------------------------------- convenience
+def _eam_struct(tables, keep):
+    E = EamTables()
+    E.nr, E.dr, E.nrho, E.drho, E.rc = tables.nr, tables.dr, tables.nrho, tables.drho, tables.rc
+
+    def arr(a):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data
+
+    for q in range(3):
+        E.pair[q] = arr(tables.pair[q])
+        E.dpair[q] = arr(tables.dpair[q])
+    for q in range(2):
+        E.dens[q] = arr(tables.dens[q])
+        E.ddens[q] = arr(tables.ddens[q])
+        E.embed[q] = arr(tables.embed[q])
+        E.dembed[q] = arr(tables.dembed[q])
+    return E
+
+
 class Context:
     """Owns one C context; keeps the host arrays passed at init alive."""
 
@@ -328,8 +353,64 @@ class Context:
         _check(lib().vcsgc_profile_steps(self.h, int(n), C.byref(a), C.byref(b)), self.h)
         return a.value, b.value
 
+    def autotune(self, steps=64):
+        """Pick the fused colour step's block size by timing (real steps)."""
+        b = C.c_int32()
+        _check(lib().vcsgc_autotune(self.h, int(steps), C.byref(b)), self.h)
+        return b.value
+
     def neighbours(self, i, cap=256):
         out = np.zeros(cap, dtype=np.int32)
         cnt = C.c_int32()
         _check(lib().vcsgc_neighbours(self.h, int(i), _ptr(out), cap, C.byref(cnt)), self.h)
         return out[:min(cnt.value, cap)].copy()
+
+
+class Batch(Context):
+    """Rigid BCC lattices of different sizes advanced by one launch per colour
+    step (vcsgc_batch_init).  types: list of per-replica species arrays."""
+
+    def __init__(self, cells, types, tables, phi, kappa, T, *, a=2.855, seed=1, c0=-1.0,
+                 seed_r=None, c0_r=None, sched=(4, 4, 4), stream=None, device=-1, precision=0):
+        self._keep = []
+        cells = np.ascontiguousarray(cells, dtype=np.int32).reshape(-1, 3)
+        R = cells.shape[0]
+        t = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.uint8) for x in types]))
+        E = _eam_struct(tables, self._keep)
+        o = vcsgc_default_options()
+        o.seed = seed
+        o.c0 = c0
+        o.schedule = SCHED_SUBLATTICE
+        for q in range(3):
+            o.sched[q] = sched[q]
+        o.precision = precision
+        for name, val, dt_ in (("seed_r", seed_r, np.uint64), ("c0_r", c0_r, np.float64)):
+            if val is not None:
+                arr_ = np.ascontiguousarray(val, dtype=dt_)
+                self._keep.append(arr_)
+                setattr(o, name, arr_.ctypes.data)
+        if stream is not None:
+            o.stream = getattr(stream, "cuda_stream", stream)
+        o.device = device
+        ph = np.ascontiguousarray(np.broadcast_to(phi, (R,)), dtype=np.float64)
+        ka = np.ascontiguousarray(np.broadcast_to(kappa, (R,)), dtype=np.float64)
+        TT = np.ascontiguousarray(np.broadcast_to(T, (R,)), dtype=np.float64)
+        h = C.c_void_p()
+        rc = lib().vcsgc_batch_init(C.byref(h), R, _ptr(cells), float(a), _ptr(t), C.byref(E),
+                                    _ptr(ph), _ptr(ka), _ptr(TT), C.byref(o))
+        _check(rc, None)
+        self.h = h
+        self.n_replicas = R
+        self.sizes = [int(2 * c[0] * c[1] * c[2]) for c in cells]
+        self.n = self.sizes[0]
+        self._keep = []
+
+    def types(self, replica=0):
+        out = np.zeros(self.sizes[replica], dtype=np.uint8)
+        _check(lib().vcsgc_get_types(self.h, int(replica), _ptr(out)), self.h)
+        return out
+
+    def rho(self, replica=0):
+        out = np.zeros(self.sizes[replica], dtype=np.float64)
+        _check(lib().vcsgc_get_rho(self.h, int(replica), _ptr(out)), self.h)
+        return out

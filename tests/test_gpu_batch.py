@@ -1,0 +1,84 @@
+"""Batched replicas of different lattice sizes in one context (one launch
+per colour step) against independent oracle chains (GPU only)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1012_5082_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+CELLS = [(8, 8, 8), (12, 12, 12), (16, 8, 12)]
+PHI = [-2.45, -2.40, -2.50]
+T = [700.0, 650.0, 750.0]
+SEEDS = [11, 12, 13]
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_1012_5082_gb300 import vcsgc
+    return vcsgc
+
+
+def _start():
+    tab = I.eam_tables()
+    lats = [I.bcc_lattice(*c) for c in CELLS]
+    types = [I.random_types(l.n, l.n // 20, seed=100 + q) for q, l in enumerate(lats)]
+    return tab, lats, types
+
+
+def _oracles(tab, lats, types, steps):
+    out = []
+    for q, l in enumerate(lats):
+        o = O.System(l, types[q], tab)
+        o.set_params(PHI[q], 20.0, T[q], c0=0.05, seed=SEEDS[q])
+        o.schedule_sublattice(l.cells, (4, 4, 4))
+        o.parallel_steps(steps)
+        out.append(o)
+    return out
+
+
+def test_batch_of_uneven_lattices_matches_oracles(V):
+    tab, lats, types = _start()
+    b = V.Batch(CELLS, types, tab, PHI, 20.0, T, seed_r=np.array(SEEDS, np.uint64), c0=0.05)
+    b.sweep(15)
+    steps = 15 * 128
+    orcs = _oracles(tab, lats, types, steps)
+    for q, o in enumerate(orcs):
+        og = b.observables(q)
+        assert og["steps"] == steps
+        if o.obs()["near_ties"] == 0:
+            assert np.array_equal(b.types(q), o.types)
+            assert og["flips"] == o.obs()["flips"] and og["n_b"] == o.obs()["n_b"]
+            assert abs(og["energy"] - o.obs()["energy"]) <= 1e-9 * abs(o.obs()["energy"])
+        assert og["flips"] > 0
+    # the batch's own energy evaluation agrees with the tracked energy
+    assert abs(b.energy(1) - b.observables(1)["energy"]) <= 1e-9 * abs(b.energy(1))
+    b.close()
+
+
+def test_autotune_keeps_the_chain_exact(V):
+    tab, lats, types = _start()
+    b = V.Batch(CELLS, types, tab, PHI, 20.0, T, seed_r=np.array(SEEDS, np.uint64), c0=0.05)
+    best = b.autotune(steps=16)
+    assert best in (64, 128, 256)
+    b.sweep(2)
+    steps = 3 * (1 + 16) + 2 * 128
+    orcs = _oracles(tab, lats, types, steps)
+    for q, o in enumerate(orcs):
+        if o.obs()["near_ties"] == 0:
+            assert np.array_equal(b.types(q), o.types)
+    b.close()
+
+
+def test_batch_set_types_and_delta_e(V):
+    tab, lats, types = _start()
+    b = V.Batch(CELLS, types, tab, PHI, 20.0, T, seed_r=np.array(SEEDS, np.uint64), c0=0.05)
+    t2 = I.random_types(lats[2].n, lats[2].n // 3, seed=7)
+    b.set_types(t2, 2)
+    assert np.array_equal(b.types(2), t2)
+    o = O.System(lats[2], t2, tab)
+    sites = np.arange(0, lats[2].n, 5)
+    assert np.max(np.abs(b.delta_e(sites, 2) - np.array([o.delta_e(i) for i in sites]))) < 1e-11
+    assert abs(b.observables(2)["energy"] - o.energy_full()) < 1e-9 * abs(o.energy_full())
+    b.close()
