@@ -48,7 +48,11 @@ class Obs(C.Structure):
                 ("steps", C.c_int64), ("trials", C.c_int64), ("local_accepts", C.c_int64),
                 ("global_trials", C.c_int64), ("global_accepts", C.c_int64),
                 ("flips", C.c_int64), ("near_ties", C.c_int64), ("sum_c", C.c_double),
-                ("sum_c2", C.c_double)]
+                ("sum_c2", C.c_double), ("stage1_accepts", C.c_int64)]
+
+MLP_IN = 10
+MLP_H = 64
+MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
 
 
 def lib():
@@ -90,6 +94,11 @@ def lib():
             "orc_kinetic_energy": (D, [P]),
             "orc_hybrid_cycles": (I32, [P, I64, I64, I64]),
             "orc_run_histogram": (I32, [P, I64, I32, P, P]),
+            "orc_set_shells": (I32, [P, I32, P, D]),
+            "orc_descriptor": (I32, [P, I64, P]),
+            "orc_mlp_eval": (D, [P, P]),
+            "orc_set_surrogate": (I32, [P, I32, P]),
+            "orc_surrogate": (D, [P, I64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -118,6 +127,14 @@ def u01(lo, hi):
 
 def below(lo, hi, m):
     return lib().orc_below(int(lo), int(hi), int(m))
+
+
+def mlp_eval(params, x):
+    """The surrogate MLP (FP64) at one raw descriptor x (10 counts)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    assert p.shape == (MLP_NPARAM,) and xx.shape == (MLP_IN,)
+    return lib().orc_mlp_eval(_p(p), _p(xx))
 
 
 class System:
@@ -194,7 +211,8 @@ class System:
             raise RuntimeError("oracle: no schedule")
 
     def serial_steps(self, n, mode=0):
-        lib().orc_serial_steps(self.h, int(n), int(mode))
+        if lib().orc_serial_steps(self.h, int(n), int(mode)):
+            raise RuntimeError("oracle: serial mode 2 needs a surrogate")
 
     def run_histogram(self, n_steps, mode=-1):
         """Histogram of n_B after each of n_steps steps, and the mean energy."""
@@ -203,6 +221,32 @@ class System:
         if lib().orc_run_histogram(self.h, int(n_steps), int(mode), _p(hist), C.byref(se)):
             raise RuntimeError("oracle: no schedule")
         return hist, se.value / max(1, n_steps)
+
+    # ---- delayed acceptance
+    def set_shells(self, radii, tol=1e-6):
+        r = np.ascontiguousarray(radii, dtype=np.float64)
+        if lib().orc_set_shells(self.h, len(r), _p(r), float(tol)):
+            raise ValueError("oracle: bad shells")
+
+    def descriptor(self, i):
+        out = np.zeros(MLP_IN)
+        if lib().orc_descriptor(self.h, int(i), _p(out)):
+            raise ValueError("oracle: the descriptor needs 5 shells")
+        return out
+
+    def set_surrogate(self, kind, params=None):
+        """kind: 'off', 'mlp' (params: MLP_NPARAM values) or 'exact'."""
+        k = {"off": 0, "mlp": 1, "exact": 2}[kind]
+        p = None
+        if params is not None:
+            p = np.ascontiguousarray(params, dtype=np.float64)
+            assert p.shape == (MLP_NPARAM,)
+        if lib().orc_set_surrogate(self.h, k, None if p is None else _p(p)):
+            raise ValueError("oracle: bad surrogate (MLP needs 5 shells and parameters)")
+        self._params = p
+
+    def surrogate(self, i):
+        return lib().orc_surrogate(self.h, int(i))
 
     # ---- energies
     def delta_e(self, i):

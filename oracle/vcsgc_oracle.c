@@ -71,6 +71,13 @@ struct orc_sys {
   int64_t *col_start, *dom_start, *dom_sites;
   int sched_kind; /* 0 none, 1 blocks, 2 sublattice, 3 spatial */
   int sched_args[9];
+  /* delayed acceptance: stage-1 surrogate of the energy change */
+  int sur_kind;          /* 0 off, 1 MLP, 2 the exact energy change */
+  double* mlp;           /* ORC_MLP_NPARAM parameters */
+  int n_shells;
+  double shell_r[ORC_MAX_SHELLS];
+  double shell_tol;
+  int64_t s1_accepts;    /* trials that passed stage 1 */
   /* md */
   double *vx, *vy, *vz, *fx, *fy, *fz;
   double mass[2], dt, gamma, T_md;
@@ -458,6 +465,7 @@ void orc_free(orc_sys* s) {
   free(s->nstart); free(s->nb);
   free(s->col_start); free(s->dom_start); free(s->dom_sites);
   free(s->vx); free(s->vy); free(s->vz); free(s->fx); free(s->fy); free(s->fz);
+  free(s->mlp);
   free(s);
 }
 
@@ -483,6 +491,7 @@ int orc_set_params(orc_sys* s, double phi, double kappa, double T, int kappa_uni
 void orc_reset_counters(orc_sys* s) {
   s->trials = s->local_acc = s->global_acc = s->global_trials = 0;
   s->flips = s->near_ties = 0;
+  s->s1_accepts = 0;
   s->sum_c = s->sum_c2 = 0.0;
   s->steps_done = 0;
 }
@@ -638,6 +647,106 @@ double orc_schedule_min_separation(const orc_sys* s) {
   return best;
 }
 
+/* ------------------------------------------------- surrogate (stage 1) */
+/* The delayed-acceptance form replaces the local Metropolis factor by two
+ * stages (Christen and Fox, J. Comput. Graph. Stat. 14, 795 (2005)): a cheap
+ * prediction g_i of E(sigma with i = B) - E(sigma with i = A) is tested
+ * first, and only a move that passes is tested again with the exact energy
+ * change.  g_i is a function of the environment of i alone (every site but
+ * i), so the predicted change of the reverse move is exactly -s g_i and the
+ * product of the two stages keeps the ratio exp(-X) of the plain local rule.
+ *
+ * Environment descriptor of site i (ten counts, shells identified by their
+ * radii):
+ *   own[s] = number of B sites j != i in shell s of i;
+ *   nb[s]  = sum over the first-shell neighbours k of i of the number of B
+ *            sites j != i in shell s of k.
+ * MLP: x_c = count_c / max_c (max_c = the count when every site is B on the
+ * BCC lattice), z1 = W1 x + b1, h1 = SiLU(z1), z2 = W2 h1 + b2,
+ * h2 = SiLU(z2), g = w3 . h2 + b3, SiLU(z) = z / (1 + exp(-z)). */
+static const double k_desc_max[ORC_MLP_IN] = {8, 6, 12, 24, 8, 56, 48, 96, 192, 64};
+
+int orc_set_shells(orc_sys* s, int n_shells, const double* radii, double tol) {
+  if (n_shells < 1 || n_shells > ORC_MAX_SHELLS || !(tol > 0)) return -1;
+  s->n_shells = n_shells;
+  for (int q = 0; q < n_shells; ++q) s->shell_r[q] = radii[q];
+  s->shell_tol = tol;
+  return 0;
+}
+
+static int shell_of(const orc_sys* s, double r) {
+  for (int q = 0; q < s->n_shells; ++q)
+    if (fabs(r - s->shell_r[q]) <= s->shell_tol) return q;
+  return -1;
+}
+
+int orc_descriptor(const orc_sys* s, int64_t i, double out[ORC_MLP_IN]) {
+  if (s->n_shells != ORC_MLP_IN / 2) return -1;
+  for (int q = 0; q < ORC_MLP_IN; ++q) out[q] = 0.0;
+  for (int64_t a = s->nstart[i]; a < s->nstart[i + 1]; ++a) {
+    const int64_t j = s->nb[a].j;
+    const int q = shell_of(s, s->nb[a].r);
+    if (j == i || q < 0) continue;
+    out[q] += s->t[j];
+    if (q != 0) continue;
+    /* j is a first-shell neighbour k of i: add its shell counts */
+    for (int64_t b = s->nstart[j]; b < s->nstart[j + 1]; ++b) {
+      const int64_t j2 = s->nb[b].j;
+      const int q2 = shell_of(s, s->nb[b].r);
+      if (j2 == i || q2 < 0) continue;
+      out[ORC_MLP_IN / 2 + q2] += s->t[j2];
+    }
+  }
+  return 0;
+}
+
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+
+double orc_mlp_eval(const double* p, const double x[ORC_MLP_IN]) {
+  const double* W1 = p;
+  const double* b1 = W1 + ORC_MLP_H * ORC_MLP_IN;
+  const double* W2 = b1 + ORC_MLP_H;
+  const double* b2 = W2 + ORC_MLP_H * ORC_MLP_H;
+  const double* w3 = b2 + ORC_MLP_H;
+  const double b3 = w3[ORC_MLP_H];
+  double h1[ORC_MLP_H], h2[ORC_MLP_H];
+  for (int o = 0; o < ORC_MLP_H; ++o) {
+    double z = b1[o];
+    for (int c = 0; c < ORC_MLP_IN; ++c) z += W1[o * ORC_MLP_IN + c] * (x[c] / k_desc_max[c]);
+    h1[o] = silu(z);
+  }
+  for (int o = 0; o < ORC_MLP_H; ++o) {
+    double z = b2[o];
+    for (int c = 0; c < ORC_MLP_H; ++c) z += W2[o * ORC_MLP_H + c] * h1[c];
+    h2[o] = silu(z);
+  }
+  double y = b3;
+  for (int o = 0; o < ORC_MLP_H; ++o) y += w3[o] * h2[o];
+  return y;
+}
+
+int orc_set_surrogate(orc_sys* s, int kind, const double* params) {
+  if (kind < 0 || kind > 2) return -1;
+  if (kind == 1) {
+    if (!params || s->n_shells != ORC_MLP_IN / 2) return -1;
+    if (!s->mlp) s->mlp = (double*)malloc(sizeof(double) * ORC_MLP_NPARAM);
+    if (!s->mlp) return -1;
+    memcpy(s->mlp, params, sizeof(double) * ORC_MLP_NPARAM);
+  }
+  s->sur_kind = kind;
+  return 0;
+}
+
+double orc_surrogate(const orc_sys* s, int64_t i) {
+  if (s->sur_kind == 2) {
+    const double de = orc_delta_e(s, i);
+    return s->t[i] == 0 ? de : -de;
+  }
+  double x[ORC_MLP_IN];
+  orc_descriptor(s, i, x);
+  return orc_mlp_eval(s->mlp, x);
+}
+
 /* ------------------------------------------------------------- sampling */
 /* Metropolis decision u < min{1, exp(-X)}; counts decisions within 1e-9
  * (relative) of the boundary, where CPU and GPU exp may round differently. */
@@ -649,6 +758,24 @@ static int metropolis(orc_sys* s, double X, double u) {
   double p = exp(-X);
   if (fabs(u - p) <= 1e-9 * p) s->near_ties++;
   return u < p;
+}
+
+/* Local decision of trial site i with sign s_i = sg, drawn with u (stage 1
+ * or the plain rule) and, for delayed acceptance, u2 (stage 2).  Returns the
+ * decision; *de gets the exact energy change when it was evaluated.
+ *   plain:   u  < min{1, exp(-beta (dE + s dmu0))}                 (Eq. trans_vcsgc_par1)
+ *   stage 1: u  < min{1, exp(-beta (s g + s dmu0))}
+ *   stage 2: u2 < min{1, exp(-beta (dE - s g))}                    */
+static int local_decision(orc_sys* s, int64_t site, int sg, double u, double u2, double* de) {
+  if (!s->sur_kind) {
+    *de = orc_delta_e(s, site);
+    return metropolis(s, s->beta * (*de + sg * s->dmu0), u);
+  }
+  const double g = orc_surrogate(s, site);
+  if (!metropolis(s, s->beta * (sg * g + sg * s->dmu0), u)) return 0;
+  s->s1_accepts++;
+  *de = orc_delta_e(s, site);
+  return metropolis(s, s->beta * (*de - sg * g), u2);
 }
 
 static void sample_c(orc_sys* s) {
@@ -689,12 +816,16 @@ static void parallel_step(orc_sys* s, int64_t* acc_sites, double* acc_de) {
     if (size == 0) continue;
     draw(s, k, (uint32_t)(g - d0), 0u, w);
     int64_t site = s->dom_sites[s->dom_start[g] + orc_below(w[0], w[1], (uint64_t)size)];
-    double u = orc_u01(w[2], w[3]);
+    double u = orc_u01(w[2], w[3]), u2 = 0.0;
+    if (s->sur_kind) {
+      uint32_t w2[4];
+      draw(s, k, (uint32_t)(g - d0), 5u, w2);
+      u2 = orc_u01(w2[0], w2[1]);
+    }
     int sg = s->t[site] == 0 ? 1 : -1;
-    double de = orc_delta_e(s, site);
-    double X = s->beta * (de + sg * s->dmu0);
+    double de = 0.0;
     s->trials++;
-    if (metropolis(s, X, u)) {
+    if (local_decision(s, site, sg, u, u2, &de)) {
       acc_sites[nacc] = site;
       acc_de[nacc] = de;
       nacc++;
@@ -738,8 +869,11 @@ int orc_parallel_steps(orc_sys* s, int64_t n_steps) {
  * mode 0, Eq. trans_vcsgc: X = beta (dE + N dc (phi + 2 kappa_p N c~)),
  *         with N dc = s and 2 N c~ = n + n' = 2n + s.
  * mode 1, Eq. mod: local factor with dmu0 times global factor with
- *         exponent beta kappa_p s (s + 2 (n - n0)). */
+ *         exponent beta kappa_p s (s + 2 (n - n0)).
+ * mode 2: mode 1 with the local factor taken in the two delayed-acceptance
+ *         stages of the surrogate (orc_set_surrogate). */
 int orc_serial_steps(orc_sys* s, int64_t n_steps, int mode) {
+  if (mode == 2 && !s->sur_kind) return -1;
   for (int64_t q = 0; q < n_steps; ++q) {
     uint64_t k = s->step;
     uint32_t w[4], w2[4];
@@ -747,17 +881,25 @@ int orc_serial_steps(orc_sys* s, int64_t n_steps, int mode) {
     int64_t site = (int64_t)orc_below(w[0], w[1], (uint64_t)s->n);
     double u = orc_u01(w[2], w[3]);
     int sg = s->t[site] == 0 ? 1 : -1;
-    double de = orc_delta_e(s, site);
     double n = (double)s->nb_count;
+    double de = 0.0;
     int acc;
     s->trials++;
     if (mode == 0) {
+      de = orc_delta_e(s, site);
       double X = s->beta * (de + sg * (s->phi + s->kappa_p * (2.0 * n + sg)));
       acc = metropolis(s, X, u);
       if (acc) s->local_acc++;
     } else {
-      double X = s->beta * (de + sg * s->dmu0);
-      acc = metropolis(s, X, u);
+      double u2 = 0.0;
+      if (mode == 2) {
+        draw(s, k, 2u, 2u, w2);
+        u2 = orc_u01(w2[0], w2[1]);
+      }
+      const int kind = s->sur_kind;
+      if (mode == 1) s->sur_kind = 0;
+      acc = local_decision(s, site, sg, u, u2, &de);
+      s->sur_kind = kind;
       if (acc) {
         s->local_acc++;
         s->global_trials++;
@@ -815,6 +957,7 @@ void orc_get_obs(const orc_sys* s, orc_obs* o) {
   o->near_ties = s->near_ties;
   o->sum_c = s->sum_c;
   o->sum_c2 = s->sum_c2;
+  o->stage1_accepts = s->s1_accepts;
 }
 
 int64_t orc_neighbour_count(const orc_sys* s, int64_t i) { return s->nstart[i + 1] - s->nstart[i]; }

@@ -52,6 +52,11 @@ typedef struct {
 
 typedef struct orc_sys orc_sys;
 
+#define ORC_MAX_SHELLS 8
+#define ORC_MLP_IN 10
+#define ORC_MLP_H 64
+#define ORC_MLP_NPARAM (ORC_MLP_H * ORC_MLP_IN + ORC_MLP_H + ORC_MLP_H * ORC_MLP_H + ORC_MLP_H + ORC_MLP_H + 1)
+
 /* Observables of Sec. II C: B count n, energy, acceptance counters and
  * running moments of the concentration (sampled once per composite step). */
 typedef struct {
@@ -67,6 +72,7 @@ typedef struct {
   int64_t near_ties;     /* decisions with |u - p| <= 1e-9 p */
   double sum_c;          /* sum over steps of c after the step */
   double sum_c2;
+  int64_t stage1_accepts;/* delayed acceptance: trials that passed stage 1 */
 } orc_obs;
 
 /* Build a system from explicit positions (SoA) in an orthorhombic periodic
@@ -106,13 +112,40 @@ void orc_schedule_export(const orc_sys* s, int64_t* col_start, int64_t* dom_star
 
 /* Parallel composite steps (Sec. III B 2).  Returns 0. */
 int orc_parallel_steps(orc_sys* s, int64_t n_steps);
-/* Serial single-site steps: mode 0 = Eq. trans_vcsgc, mode 1 = Eq. mod. */
+/* Serial single-site steps: mode 0 = Eq. trans_vcsgc, mode 1 = Eq. mod,
+ * mode 2 = Eq. mod with a delayed-acceptance local factor (needs a
+ * surrogate; returns -1 otherwise). */
 int orc_serial_steps(orc_sys* s, int64_t n_steps, int mode);
 
 /* Run n_steps steps (mode -1: parallel composite; 0, 1: serial as above)
  * and add one count per step to hist[n_B] (hist has N+1 entries) and the
  * energy after each step to *sum_e.  Used for distribution tests. */
 int orc_run_histogram(orc_sys* s, int64_t n_steps, int mode, int64_t* hist, double* sum_e);
+
+/* Delayed acceptance (Christen and Fox 2005) of the local stage.  Stage 1
+ * accepts the move of site i (sign s = +1 for A->B, -1 for B->A) with
+ * min{1, exp[-beta (s g_i + s dmu0)]}, stage 2 with min{1, exp[-beta (dE_i -
+ * s g_i)]}; g_i predicts E(i = B) - E(i = A) from the environment of i only,
+ * so the two stages together keep the ratio of the plain local rule and the
+ * sampled distribution is unchanged.  Stage 2 draws its uniform from tag 5
+ * (parallel steps, counter (step, trial, 5)) or counter (step, 2, 2) (serial
+ * mode 2).
+ *
+ * Shells: n_shells radii (Angstrom); a neighbour at distance r is in shell q
+ * when |r - radii[q]| <= tol.
+ * Descriptor of site i (needs 5 shells): out[q] = B sites j != i in shell q
+ * of i; out[5 + q] = sum over the first-shell neighbours k of i of the B
+ * sites j != i in shell q of k (raw counts).
+ * MLP parameters (ORC_MLP_NPARAM doubles): W1[64][10], b1[64], W2[64][64],
+ * b2[64], w3[64], b3; inputs are count_c / max_c with max = (8, 6, 12, 24,
+ * 8, 56, 48, 96, 192, 64); SiLU activations; output g in eV.
+ * Surrogate kind: 0 off, 1 the MLP, 2 the exact energy change (a perfect
+ * surrogate, for tests). */
+int orc_set_shells(orc_sys* s, int n_shells, const double* radii, double tol);
+int orc_descriptor(const orc_sys* s, int64_t i, double out[ORC_MLP_IN]);
+double orc_mlp_eval(const double* params, const double x[ORC_MLP_IN]);
+int orc_set_surrogate(orc_sys* s, int kind, const double* params);
+double orc_surrogate(const orc_sys* s, int64_t i);
 
 /* Energy change for flipping site i (Sec. III A; EAM energy difference with
  * pair, own-embedding and neighbour re-embedding terms). */

@@ -293,7 +293,21 @@ CASES = [
     ("chain", 2000.0, -1.10, 0.5, 0.1, "parallel"),
     ("chain", 2000.0, -1.30, 2.0, 0.8, "parallel"),
     ("chain", 2000.0, -1.30, 2.0, 0.1, "serial2"),
+    # delayed acceptance with a random (deliberately poor) surrogate
+    ("cube", 1500.0, -1.60, 2.0, 0.1, "parallel-da"),
+    ("cube", 1500.0, -1.60, 2.0, 0.8, "serial2-da"),
+    ("chain", 2000.0, -1.30, 2.0, 0.8, "parallel-da"),
 ]
+
+
+def _random_surrogate(seed):
+    """MLP parameters that predict dE badly: random weights around a 1 eV
+    offset, so stage 2 has much to correct."""
+    rng = np.random.default_rng(seed)
+    H, IN = O.MLP_H, O.MLP_IN
+    parts = [rng.normal(0, 1.0, H * IN), rng.normal(0, 0.5, H), rng.normal(0, 0.125, H * H),
+             rng.normal(0, 0.3, H), rng.normal(0, 0.1, H), [1.0]]
+    return np.concatenate(parts)
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}-{c[5]}-k{c[3]}" for c in CASES])
@@ -316,7 +330,10 @@ def test_chain_matches_exact_enumeration(case, enum_cache):
     s.set_types(np.zeros(n, np.uint8))
     s.set_params(phi, kappa, T, kappa_units=0, c0=c0, seed=2024)
     s.schedule_blocks(sch["cells"], sch["block"], sch["colours"])
-    m = {"parallel": -1, "serial": 0, "serial2": 1}[mode]
+    if mode.endswith("-da"):
+        s.set_shells(SHELL_R)
+        s.set_surrogate("mlp", _random_surrogate(7))
+    m = {"parallel": -1, "serial": 0, "serial2": 1, "parallel-da": -1, "serial2-da": 2}[mode]
     s.run_histogram(5000, m)
     blocks = []
     hist_tot = np.zeros(n + 1)
@@ -336,6 +353,11 @@ def test_chain_matches_exact_enumeration(case, enum_cache):
     assert abs(np.mean(e_blocks) - Emean) < 5 * e_err + 1e-3
     # the distribution is non-degenerate
     assert P.max() < 0.6
+    if mode.endswith("-da"):
+        o = s.obs()
+        # stage 2 both rejects and accepts a real share of the stage-1 passes
+        assert 0.05 * o["trials"] < o["stage1_accepts"] < o["trials"]
+        assert o["local_accepts"] < 0.95 * o["stage1_accepts"]
 
 
 def test_kappa_zero_trajectory_independent_of_c0(tables):
