@@ -254,27 +254,32 @@ def mixed_bench(V, torch, stream, local, sweeps=40, warmup=3):
     return out
 
 
-def batch_bench(V, torch, stream, local, sweeps=30, warmup=3):
-    """64 replicas of rigid BCC of uneven sizes (L = 24 + 4 (r mod 7) cells,
-    27,648 to 221,184 sites) at 8 temperatures in 500-900 K x 8 phi values,
-    kappa = 1000, advanced together by one fused launch per colour step
-    (CUDA graphs of 64 steps); block size picked by the autotuner."""
-    tab = I.eam_tables()
-    cells, types, phi, T, c0 = [], [], [], [], []
+def c4_grid():
+    """(phi, T, c0) of the 64 replicas: 8 temperatures in 500-900 K x 8
+    concentrations c0 = 0.02 .. 0.5 with the same local driving force."""
+    phi, T, c0 = [], [], []
     for r in range(64):
-        L = 24 + 4 * (r % 7)
-        n = 2 * L ** 3
-        cells.append((L, L, L))
-        types.append(I.random_types(n, int(round(FRAC_B * n)), seed=3000 + r))
         Tr = 500.0 + 400.0 * (r // 8) / 7.0
         c0r = 0.02 + (r % 8) * 0.48 / 7
         T.append(Tr)
         c0.append(c0r)
         phi.append(DMU_S - 2.0 * KAPPA * I.KB_EV * Tr * c0r)
-    b = V.Batch(cells, types, tab, phi, KAPPA, T, c0_r=c0,
-                seed_r=np.arange(64, dtype=np.uint64) + np.uint64(3000), stream=stream, device=local)
-    best = b.autotune(steps=64)
-    b.sweep(warmup)
+    return phi, T, c0
+
+
+def c4_batch(V, stream, local, tab):
+    cells, types = [], []
+    for r in range(64):
+        L = 24 + 4 * (r % 7)
+        n = 2 * L ** 3
+        cells.append((L, L, L))
+        types.append(I.random_types(n, int(round(FRAC_B * n)), seed=3000 + r))
+    phi, T, c0 = c4_grid()
+    return V.Batch(cells, types, tab, phi, KAPPA, T, c0_r=c0,
+                   seed_r=np.arange(64, dtype=np.uint64) + np.uint64(3000), stream=stream, device=local)
+
+
+def timed_sweeps(torch, stream, b, sweeps):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -282,14 +287,92 @@ def batch_bench(V, torch, stream, local, sweeps=30, warmup=3):
     b.sweep(sweeps)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    return e0.elapsed_time(e1)
+
+
+def batch_bench(V, torch, stream, local, sweeps=30, warmup=3, surrogate=True):
+    """64 replicas of rigid BCC of uneven sizes (L = 24 + 4 (r mod 7) cells,
+    27,648 to 221,184 sites) at 8 temperatures in 500-900 K x 8 phi values,
+    kappa = 1000, advanced together by one fused launch per colour step
+    (CUDA graphs of 64 steps); block size picked by the autotuner.  With
+    surrogate: the same run with delayed acceptance by a network trained on
+    the sampler's own dE."""
+    tab = I.eam_tables()
+    b = c4_batch(V, stream, local, tab)
+    best = b.autotune(steps=64)
+    b.sweep(warmup)
+    ms = timed_sweeps(torch, stream, b, sweeps)
     total = sum(b.sizes)
-    acc = [b.observables(r)["acc_local"] for r in (0, 31, 63)]
+    obs = [b.observables(r) for r in range(64)]
     b.close()
-    return {"metric": "aggregate VC-SGC trial moves/s", "value": total * sweeps / (ms * 1e-3),
-            "unit": "trial moves/s", "replicas": 64, "sites_total": total, "sweeps": sweeps,
-            "ms_per_sweep": ms / sweeps, "block": best, "acc_local_sample": acc,
-            "workload": "64 replicas, L = 24..48 cells, T 500-900 K x 8 phi, kappa 1000, FP64"}
+    out = {"metric": "aggregate VC-SGC trial moves/s", "value": total * sweeps / (ms * 1e-3),
+           "unit": "trial moves/s", "replicas": 64, "sites_total": total, "sweeps": sweeps,
+           "ms_per_sweep": ms / sweeps, "block": best,
+           "acc_local_sample": [obs[r]["acc_local"] for r in (0, 31, 63)],
+           "workload": "64 replicas, L = 24..48 cells, T 500-900 K x 8 phi, kappa 1000, FP64"}
+    if surrogate:
+        out["delayed_acceptance"] = surrogate_bench(V, torch, stream, local, tab, sweeps, warmup, out["value"], obs)
+    return out
+
+
+def surrogate_bench(V, torch, stream, local, tab, sweeps, warmup, plain_value, plain_obs,
+                    n_samples=10_000_000, train_steps=5000, batch=4096, lr=2e-3):
+    """Form (4): (descriptor, dE) samples drawn by the sampler itself on 12^3
+    replicas of the 10^3 parity workload's EAM at the 64 (phi, T) points,
+    training by the GPU kernels, then the 64-replica batch with the network
+    as stage 1 of delayed acceptance."""
+    phi, T, c0 = c4_grid()
+    lat = I.bcc_lattice(12, 12, 12)
+    types = [I.random_types(lat.n, int(round(c * lat.n)), seed=5000 + r) for r, c in enumerate(c0)]
+    gen = V.Batch([(12, 12, 12)] * 64, types, tab, phi, KAPPA, T, c0_r=c0,
+                  seed_r=np.arange(64, dtype=np.uint64) + np.uint64(5000), stream=stream, device=local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xs, Ys, got = [], [], 0
+    gen.sweep(4)
+    while got < n_samples:
+        gen.sweep(2)
+        X, Y = gen.features()
+        Xs.append(X)
+        Ys.append(Y)
+        got += X.shape[0]
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    del Xs, Ys
+    gen.sweep(5)
+    Xh, Yh = gen.features()
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    gen.close()
+    s = V.Surrogate(I.mlp_init(7, out_bias=float(Y.mean())), stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = s.train(X, Y, batch=batch, steps=train_steps, lr=lr, seed=17)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    g = s.forward(Xh)
+    rmse = float(torch.sqrt(((g - Yh) ** 2).mean()))
+    b = c4_batch(V, stream, local, tab)
+    b.set_surrogate(s)
+    best = b.autotune(steps=64)
+    b.sweep(warmup)
+    ms = timed_sweeps(torch, stream, b, sweeps)
+    total = sum(b.sizes)
+    obs = [b.observables(r) for r in range(64)]
+    b.close()
+    s.close()
+    trials = sum(o["trials"] for o in obs)
+    s1 = sum(o["stage1_accepts"] for o in obs)
+    acc = sum(o["local_accepts"] for o in obs)
+    value = total * sweeps / (ms * 1e-3)
+    dc = [abs(obs[r]["mean_c"] - plain_obs[r]["mean_c"]) for r in range(64)]
+    return {"value": value, "unit": "trial moves/s", "speedup_vs_plain": value / plain_value,
+            "block": best, "stage1_rejection": 1.0 - s1 / trials, "stage2_acceptance": acc / max(1, s1),
+            "train_samples": int(X.shape[0]), "sample_gen_s": t_gen, "train_steps": train_steps,
+            "train_batch": batch, "train_s": t_train, "train_samples_per_s": train_steps * batch / t_train,
+            "loss_first": float(np.mean(hist[:10])), "loss_last": float(np.mean(hist[-100:])),
+            "holdout_rmse_eV": rmse, "holdout_std_eV": float(Yh.std()),
+            "mean_c_abs_diff_vs_plain": {"mean": float(np.mean(dc)), "max": float(np.max(dc))},
+            "network": "10-64-64-1 SiLU, BF16 mma.sync m16n8k16, FP32 accumulate; Adam"}
 
 
 def run_reference(args):
@@ -336,6 +419,7 @@ def main():
     ap.add_argument("--no-md", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--md-only", action="store_true", help="only the MD measurement (profiling)")
     ap.add_argument("--md-box", type=float, default=250.0, help="nanocrystal box (A) for --md-only")
     args = ap.parse_args()
@@ -449,7 +533,7 @@ def main():
     if not args.no_mixed:
         line["mixed_128cubed"] = mixed_bench(V, torch, stream, local)
     if not args.no_batch:
-        line["batch_64"] = batch_bench(V, torch, stream, local)
+        line["batch_64"] = batch_bench(V, torch, stream, local, surrogate=not args.no_surrogate)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lat, types, tab, phi, c0)
     if rank == 0:

@@ -162,6 +162,8 @@ typedef struct {
   double sweeps;          /* trials / N */
   double kappa_p;         /* eV */
   double dmu0;            /* phi + 2 kappa_p N c0 (eV) */
+  int64_t stage1_accepts; /* delayed acceptance: trials that passed stage 1
+                             (the exact dE was evaluated for these only) */
 } vcsgc_observables;
 
 /* Fill *opt with the defaults: seed 1, c0 = -1, kappa_units 0, SUBLATTICE
@@ -280,6 +282,74 @@ int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* c
 int vcsgc_neighbour_list_noalloc(int64_t n, const double* d_x, const double* d_y,
                                  const double* d_z, const double box[3], double rl, int32_t K,
                                  int32_t* d_nbr, int32_t* d_cnt, void* stream);
+
+/* ---- Delayed acceptance with a learned surrogate of dE.
+ * The local stage of the composite move (Sec. III B 2, Eq.
+ * trans_vcsgc_par1) split into two stages (Christen and Fox, J. Comput.
+ * Graph. Stat. 14 (2005) 795): a trial of site i (s = +1 for A->B, -1 for
+ * B->A) passes stage 1 when u < min{1, exp[-beta (s g_i + s dmu0)]} and is
+ * accepted when it also passes stage 2, u2 < min{1, exp[-beta (dE_i - s
+ * g_i)]}, where g_i is the surrogate's prediction of E(i = B) - E(i = A) and
+ * dE_i the exact energy change, evaluated only after stage 1.  g_i depends
+ * on the environment of i only (every site but i), so the product of the two
+ * stages has the ratio exp(-X) of the plain rule and the sampled
+ * distribution is unchanged, whatever the surrogate's error.  u is the
+ * plain rule's uniform; u2 comes from Philox counter (step, trial, 5).
+ *
+ * Environment descriptor of site i (ten counts): own[s] = B neighbours of i
+ * in shell s = 1..5; nb[s] = sum over the 8 first-shell neighbours k of i of
+ * the B sites other than i in shell s of k.  Only the rigid BCC lattice with
+ * r_c between sqrt(3) a and sqrt(19) a / 2 (five shells: 8, 6, 12, 24, 8
+ * sites) in the fused form has it.
+ *
+ * Surrogate network (VCSGC_MLP_NPARAM FP32 parameters, in this order):
+ * W1[64][10], b1[64], W2[64][64], b2[64], w3[64], b3.  x_c = count_c / max_c
+ * with max = (8, 6, 12, 24, 8, 56, 48, 96, 192, 64); z1 = W1 x + b1;
+ * h1 = SiLU(z1); z2 = W2 h1 + b2; h2 = SiLU(z2); g = w3 . h2 + b3 (eV).
+ * On the GPU x, W1, W2 and h1 enter the tensor cores as BF16 with FP32
+ * accumulation, and SiLU(z) = z (1 + tanh(z / 2)) / 2 uses the hardware
+ * tanh approximation. */
+#define VCSGC_MLP_IN 10
+#define VCSGC_MLP_NPARAM 4929
+
+/* Descriptors and exact targets of every site of every replica, on the
+ * current (committed) species.  DEVICE outputs owned by the caller:
+ * d_X[rows][10] (float, raw counts own[1..5], nb[1..5]) and d_Y[rows]
+ * (float, E(i = B) - E(i = A) in eV), rows = sum of the replica sizes,
+ * replica after replica in site order.  Errors: STATE when the context is
+ * not a fused rigid lattice with the five-shell neighbourhood; CUDA. */
+int vcsgc_features(void* ctx, float* d_X, float* d_Y);
+
+/* A surrogate network on the current device: FP32 master parameters (copied
+ * from the HOST array params[VCSGC_MLP_NPARAM]), Adam moments (zero) and
+ * packed BF16 fragments.  Work runs on `stream` (NULL: a stream of its own).
+ * Errors: INVALID_ARG, NONFINITE (a parameter is NaN or Inf), NOMEM, CUDA. */
+int vcsgc_mlp_create(void** mlp, const float* params, void* stream);
+/* Replace the parameters (HOST array); the Adam state restarts. */
+int vcsgc_mlp_set_params(void* mlp, const float* params);
+/* Copy the current FP32 parameters to the HOST array params. */
+int vcsgc_mlp_get_params(void* mlp, float* params);
+/* g for n raw descriptors: DEVICE d_X[n][10] in, DEVICE d_out[n] out (the
+ * same arithmetic as stage 1 of the colour step).  Waits for the result. */
+int vcsgc_mlp_forward(void* mlp, const float* d_X, int64_t n, float* d_out);
+/* Gradient of the mean squared error (1/n) sum (g - y)^2 over all n rows
+ * (DEVICE d_X[n][10], d_Y[n]): HOST grad[VCSGC_MLP_NPARAM] and *loss. */
+int vcsgc_mlp_grad(void* mlp, const float* d_X, const float* d_Y, int64_t n, float* grad, double* loss);
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr)
+ * on minibatches of `batch` rows drawn with replacement from the n rows
+ * (Philox keyed by seed, counter = Adam step).  loss_hist (HOST, `steps`
+ * entries, or NULL) receives each minibatch's mean squared error before its
+ * update.  Runs as a CUDA graph of 32 steps on the surrogate's stream. */
+int vcsgc_mlp_train(void* mlp, const float* d_X, const float* d_Y, int64_t n, int64_t batch, int64_t steps,
+                    double lr, uint64_t seed, double* loss_hist);
+const char* vcsgc_mlp_last_error(void* mlp);
+void vcsgc_mlp_free(void* mlp);
+
+/* Turn delayed acceptance on with a copy of the surrogate's current weights
+ * (later changes to mlp do not reach the context), or off when mlp is NULL.
+ * Applies to every replica from the next colour step.  Errors: STATE as for
+ * vcsgc_features; CUDA. */
+int vcsgc_set_surrogate(void* ctx, void* mlp);
 
 /* Text of the last error of ctx (or of the last failed vcsgc_init when ctx
  * is NULL).  Valid until the next call on the same context. */

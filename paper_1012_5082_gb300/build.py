@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvcsgc.so")
-SOURCES = ["kernels_mc.cu", "kernels_lattice.cu", "kernels_nbr.cu", "kernels_md.cu", "vcsgc_capi.cu",
-           "vcsgc_noalloc.cu"]
+SOURCES = ["kernels_mc.cu", "kernels_lattice.cu", "kernels_nbr.cu", "kernels_md.cu", "kernels_mlp.cu",
+           "vcsgc_capi.cu", "vcsgc_mlp.cu", "vcsgc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

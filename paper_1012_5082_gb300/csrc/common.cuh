@@ -46,6 +46,7 @@ constexpr uint32_t TAG_TRIAL = 0u;   // (step, domain rank): site pick + local u
 constexpr uint32_t TAG_STEP = 1u;    // (step, 0xFFFFFFFF): colour + global u
 constexpr uint32_t TAG_NOISE0 = 3u;  // (md step, atom): thermostat normals
 constexpr uint32_t TAG_NOISE1 = 4u;
+constexpr uint32_t TAG_STAGE2 = 5u;  // (step, domain rank): delayed-acceptance stage-2 u
 
 __device__ __forceinline__ uint64_t word64(uint32_t lo, uint32_t hi) {
   return ((uint64_t)hi << 32) | lo;
@@ -224,6 +225,7 @@ struct RepState {
   double energy;
   long long trials, local_acc, global_trials, global_acc, flips, near_ties, steps;
   double sum_c, sum_c2;
+  long long s1_acc;  // delayed acceptance: trials that passed stage 1
 };
 
 // Per-replica accumulator of one colour step (the paper's allgather of dc_i).
@@ -234,6 +236,7 @@ struct StepAcc {
   unsigned done;
   int ties;
   int sb[8];  // fused lattice form: sum over accepted moves of s_i b_s (per shell)
+  int s1;     // delayed acceptance: trials that passed stage 1
 };
 
 // Everything the colour-step kernels read, passed by value.

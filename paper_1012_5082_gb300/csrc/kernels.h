@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "mlp.cuh"
 
 namespace vcsgc {
 
@@ -87,6 +88,7 @@ struct LatGeom {
   int dmax;                     // pending slots of the replica
   int nxq, nyq;                 // nx / qx, ny / qy
   float rcp_nx, rcp_ny, rcp_nxq, rcp_nyq;  // 1/d for fdiv
+  long long site_off;           // first row of the replica in per-site outputs
 };
 
 struct LatArgs {
@@ -122,6 +124,10 @@ struct LatArgs {
   int* pend;                    // all replicas' pending slots
   LatCtl* ctl;
   unsigned* err;
+  // delayed acceptance (needs the 5-shell BCC neighbourhood): stage 1 tests
+  // the surrogate's prediction, stage 2 the exact dE
+  int da;
+  MlpW mlp;
 };
 
 void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);
@@ -130,6 +136,32 @@ void launch_to_float(const double* in, float* out, long long n, cudaStream_t st)
 void launch_lattice_pack(const LatArgs& a, const LatGeom& g, const uint8_t* types_r, int r, cudaStream_t st);
 void launch_lattice_unpack(const LatArgs& a, const LatGeom& g, uint8_t* types_r, int r, cudaStream_t st);
 void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st);
+// Environment counts X[row][10] and exact targets Y[row] = E(i = B) - E(i = A)
+// of every site of every replica (row = site_off + site); no pending flips.
+void launch_lattice_features(const LatArgs& a, long long max_sites, float* X, float* Y, cudaStream_t st);
+
+// ---- surrogate network (kernels_mlp.cu)
+struct MlpBuf {
+  uint2* w1f;   // [MLP_W1F]
+  uint2* w2f;   // [MLP_W2F]
+  uint2* w2tf;  // [MLP_W2F]
+  float* vec;   // [MLP_VEC]
+};
+MlpW mlp_view(const MlpBuf& b);
+void launch_mlp_pack(const float* p, const MlpBuf& b, cudaStream_t st);
+void launch_mlp_forward(const MlpBuf& b, const float* X, long long n, float* out, cudaStream_t st);
+// gradient of the mean squared error over a minibatch of B rows (sampled
+// from the n rows by Philox(key, step = *ctr, row) when sample) added to grad;
+// the batch loss is added to loss_hist[*ctr - *base] (loss_hist[0] when ctr
+// is null)
+void launch_mlp_backward(const MlpBuf& b, const float* X, const float* Y, long long n, long long B,
+                         bool sample, uint2 key, const long long* ctr, const long long* base, float* grad,
+                         double* loss_hist, cudaStream_t st);
+// buffers of a surrogate object made by vcsgc_mlp_create (false if null)
+bool mlp_object_buffers(void* mlp, MlpBuf* out);
+cudaStream_t mlp_object_stream(void* mlp);
+void launch_mlp_adam_pack(float* p, float* m, float* v, float* grad, float lr, long long* ctr, const MlpBuf& b,
+                          cudaStream_t st);
 
 // ---- colour step (kernels_mc.cu)
 // phase 0: propose + commit; 1: propose only; 2: commit only

@@ -115,6 +115,45 @@ __device__ __forceinline__ void lattice_counts_at(const LatArgs& a, const LatGeo
   t = own_bit(row_ptr(a, g, Y, Z), H, gm);
 }
 
+// Summed per-shell B counts of the 8 first-shell neighbours k of site
+// (X, Y, Z, b), each without the site itself (species ti, in shell 1 of k):
+// the second half of the surrogate's environment descriptor.  The
+// neighbours of a corner site (b = 0) are the body centres of the cells at
+// offsets {-1, 0}^3, those of a body centre the corners at {0, 1}^3.
+template <int NS, int NR>
+__device__ __forceinline__ void lattice_nb_counts(const LatArgs& a, const LatGeom& g, int X, int Y, int Z,
+                                                  int b, uint32_t gm, int ti, int (&nb)[NS]) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s) nb[s] = 0;
+  const int lo = b ? 0 : -1;
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    int xx = X + lo + (q & 1), yy = Y + lo + ((q >> 1) & 1), zz = Z + lo + (q >> 2);
+    xx = xx < 0 ? xx + g.nx : (xx >= g.nx ? xx - g.nx : xx);
+    yy = yy < 0 ? yy + g.ny : (yy >= g.ny ? yy - g.ny : yy);
+    zz = zz < 0 ? zz + g.nz : (zz >= g.nz ? zz - g.nz : zz);
+    int c[NS], tk;
+    lattice_counts_at<NS, NR>(a, g, xx, yy, zz, 1 - b, gm, c, tk);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) nb[s] += c[s];
+  }
+  nb[0] -= 8 * ti;
+}
+
+// The ten scaled descriptor inputs as BF16 pairs (p[4] = inputs 8, 9)
+template <int NS>
+__device__ __forceinline__ void descriptor_pairs(const int (&cnt)[NS], const int (&nb)[NS], uint32_t (&p)[5]) {
+  static_assert(NS == 5, "the descriptor has five shells");
+  float x[10];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    x[s] = (float)cnt[s] * mlp_in_scale(s);
+    x[5 + s] = (float)nb[s] * mlp_in_scale(5 + s);
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) p[c] = bf16x2(x[2 * c], x[2 * c + 1]);
+}
+
 // dE of flipping the site (FP64): the A->B value C + sum_s b_s G_s + dF_i,
 // negated for B->A (i is the site index within its replica)
 template <int NS>
@@ -176,7 +215,7 @@ __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long
   return (int)below64(w.x, w.y, (uint64_t)a.n_colours);
 }
 
-template <bool PROPOSE, int NS, int NR, int BS>
+template <bool PROPOSE, int NS, int NR, int BS, bool DA>
 __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   const int r = blockIdx.y;
   const LatGeom g = a.geom[r];
@@ -265,6 +304,7 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
       const int D = a.sublattice ? g.d : a.col_start[cp + 1] - a.col_start[cp];
       S.trials += D;
       S.local_acc += A.nacc;
+      S.s1_acc += A.s1;
       S.near_ties += A.ties + s_g[1];
       long long nn = np;
       if (A.nacc > 0) {
@@ -296,43 +336,70 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
       An->nacc = 0;
       An->sum_de = 0.0;
       An->ties = 0;
+      An->s1 = 0;
       for (int q = 0; q < NS; ++q) An->sb[q] = 0;
     }
   }
   if (!PROPOSE) return;
 
   // 5. propose trial d of step k on the effective species
-  int dn = 0, acc = 0, tie = 0;
+  int dn = 0, acc = 0, tie = 0, s1 = 0;
   int sb[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) sb[q] = 0;
   double sdf = 0.0;
-  if (site >= 0) {
-    int cnt[NS], t;
-    lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
-    if (lattice_accept<NS>(a, a.lrep[r], p, cnt, site, t, top53(w.z, w.w), &tie)) {
-      const int H = 2 * sX + sb_;
-      xor_copies(g.nx, row_ptr(a, g, sY, sZ), H, false, true);  // set pending
-      a.pend[g.pend_off + d] = (sZ * g.ny + sY) * 2048 + H;
-      acc = 1;
-      dn = t ? -1 : 1;
-#pragma unroll
-      for (int q = 0; q < NS; ++q) sb[q] = t ? -cnt[q] : cnt[q];
-      if (!a.df_uniform) sdf = t ? -a.dF[site] : a.dF[site];
+  int cnt[NS], t = 0;
+  bool accepted = false;
+  if constexpr (DA) {
+    // delayed acceptance: every lane of the warp takes part in the
+    // surrogate's evaluation (lanes without a trial feed zeros)
+    uint32_t P[5] = {0u, 0u, 0u, 0u, 0u};
+    if (site >= 0) {
+      lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
+      int nb[NS];
+      lattice_nb_counts<NS, NR>(a, g, sX, sY, sZ, sb_, gm, t, nb);
+      descriptor_pairs<NS>(cnt, nb, P);
     }
+    const float gnn = mlp_warp_eval(a.mlp, P);
+    if (site >= 0) {
+      // stage 1: u < min{1, exp[-beta (s g + s dmu0)]}
+      const double sg = t ? -1.0 : 1.0, gd = (double)gnn;
+      if (metropolis(p.beta * fma(sg, p.dmu0, sg * gd), top53(w.z, w.w), &tie)) {
+        // stage 2: u2 < min{1, exp[-beta (dE - s g)]}
+        s1 = 1;
+        const double de = lattice_de64<NS>(a, cnt, site, t);
+        const uint4 w2 =
+            philox4x32_10(make_uint4((uint32_t)k, (uint32_t)((uint64_t)k >> 32), (uint32_t)d, TAG_STAGE2), p.key);
+        accepted = metropolis(p.beta * fma(-sg, gd, de), top53(w2.x, w2.y), &tie);
+      }
+    }
+  } else if (site >= 0) {
+    lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
+    accepted = lattice_accept<NS>(a, a.lrep[r], p, cnt, site, t, top53(w.z, w.w), &tie);
+  }
+  if (accepted) {
+    const int H = 2 * sX + sb_;
+    xor_copies(g.nx, row_ptr(a, g, sY, sZ), H, false, true);  // set pending
+    a.pend[g.pend_off + d] = (sZ * g.ny + sY) * 2048 + H;
+    acc = 1;
+    dn = t ? -1 : 1;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) sb[q] = t ? -cnt[q] : cnt[q];
+    if (!a.df_uniform) sdf = t ? -a.dF[site] : a.dF[site];
   }
   // reduction of dn, accepts, per-shell sums and ties (the paper's
   // allgather of dc_i); warps without an accept or a tie skip the shuffles
-  __shared__ int s_red[BS / 32][NS + 3];
+  __shared__ int s_red[BS / 32][NS + 4];
   __shared__ double s_df[BS / 32];
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const bool any = __ballot_sync(0xffffffffu, acc | tie) != 0u;
+  const bool any = __ballot_sync(0xffffffffu, acc | tie | s1) != 0u;
   if (any) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       dn += __shfl_xor_sync(0xffffffffu, dn, o);
       acc += __shfl_xor_sync(0xffffffffu, acc, o);
       tie += __shfl_xor_sync(0xffffffffu, tie, o);
+      if constexpr (DA) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
 #pragma unroll
       for (int q = 0; q < NS; ++q) sb[q] += __shfl_xor_sync(0xffffffffu, sb[q], o);
       if (!a.df_uniform) sdf += __shfl_xor_sync(0xffffffffu, sdf, o);
@@ -344,17 +411,18 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
     s_red[wi][2] = tie;
 #pragma unroll
     for (int q = 0; q < NS; ++q) s_red[wi][3 + q] = sb[q];
+    s_red[wi][3 + NS] = s1;
     s_df[wi] = sdf;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int tot[NS + 3];
+    int tot[NS + 4];
 #pragma unroll
-    for (int q = 0; q < NS + 3; ++q) tot[q] = 0;
+    for (int q = 0; q < NS + 4; ++q) tot[q] = 0;
     double tdf = 0.0;
     for (int w2 = 0; w2 < BS / 32; ++w2) {
 #pragma unroll
-      for (int q = 0; q < NS + 3; ++q) tot[q] += s_red[w2][q];
+      for (int q = 0; q < NS + 4; ++q) tot[q] += s_red[w2][q];
       if (!a.df_uniform) tdf += s_df[w2];
     }
     StepAcc* A = a.acc + r * 3 + (int)(k % 3);
@@ -367,6 +435,7 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
       if (!a.df_uniform) atomicAdd(&A->sum_de, tdf);
     }
     if (tot[2]) atomicAdd(&A->ties, tot[2]);
+    if (DA && tot[3 + NS]) atomicAdd(&A->s1, tot[3 + NS]);
   }
 }
 
@@ -409,6 +478,32 @@ __global__ void k_lattice_delta_e(LatArgs a, int r, const int* sites, int n, dou
   out[q] = lattice_de64<NS>(a, cnt, sites[q], t);
 }
 
+// Descriptor counts and exact A->B energy change of every site (all
+// replicas; blockIdx.y = replica), species as stored (no pending flips)
+__global__ void k_lattice_features(LatArgs a, float* X, float* Y) {
+  const int r = blockIdx.y;
+  const LatGeom g = a.geom[r];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n_sites) return;
+  int sX, sY, sZ, b, t;
+  decode_site(g, (int)i, sX, sY, sZ, b);
+  int cnt[5], nb[5];
+  lattice_counts_at<5, 13>(a, g, sX, sY, sZ, b, 0u, cnt, t);
+  lattice_nb_counts<5, 13>(a, g, sX, sY, sZ, b, 0u, t, nb);
+  const long long row = g.site_off + i;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    X[row * MLP_IN + s] = (float)cnt[s];
+    X[row * MLP_IN + 5 + s] = (float)nb[s];
+  }
+  Y[row] = (float)lattice_de64<5>(a, cnt, (int)i, 0);
+}
+
+void launch_lattice_features(const LatArgs& a, long long max_sites, float* X, float* Y, cudaStream_t st) {
+  const dim3 grid((unsigned)((max_sites + 127) / 128), (unsigned)a.R);
+  k_lattice_features<<<grid, 128, 0, st>>>(a, X, Y);
+}
+
 __global__ void k_to_float(const double* in, float* out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -421,8 +516,9 @@ void launch_to_float(const double* in, float* out, long long n, cudaStream_t st)
 template <int NS, int NR, int BS>
 static void step_bs(const LatArgs& a, int j, bool propose, cudaStream_t st) {
   const dim3 g((a.dmax + BS - 1) / BS, a.R);
-  if (propose) k_lattice_step<true, NS, NR, BS><<<g, BS, 0, st>>>(a, j);
-  else k_lattice_step<false, NS, NR, BS><<<g, BS, 0, st>>>(a, j);
+  if (!propose) k_lattice_step<false, NS, NR, BS, false><<<g, BS, 0, st>>>(a, j);
+  else if (NS == 5 && NR == 13 && a.da) k_lattice_step<true, NS, NR, BS, NS == 5 && NR == 13><<<g, BS, 0, st>>>(a, j);
+  else k_lattice_step<true, NS, NR, BS, false><<<g, BS, 0, st>>>(a, j);
 }
 
 template <int NS, int NR>

@@ -99,6 +99,8 @@ struct Ctx {
   long long h_base = 0;            // host mirror of lat.ctl->base_step
   std::vector<int3> offsets;       // half-lattice neighbour offsets (kind 0)
   std::vector<int> offset_shell;
+  // delayed acceptance: the context's copy of the surrogate's fragments
+  MlpBuf sur{};
 };
 
 #define CK(call)                                                                       \
@@ -1095,9 +1097,11 @@ static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
   }
   c->h_geom.clear();
   const long long W = (2 * c->nx + 2 * LAT_HALO + 31) / 32;
-  for (int r = 0; r < c->R; ++r)
+  for (int r = 0; r < c->R; ++r) {
     c->h_geom.push_back(lattice_geom(c->nx, c->ny, c->nz, sub ? q : nullptr, c->sublattice_d, c->dmax,
                                      (long long)r * c->ny * c->nz * W, (long long)r * c->dmax));
+    c->h_geom.back().site_off = (long long)r * c->N;
+  }
   std::vector<long long> n0(c->R);
   std::vector<LatRep> lr(c->R);
   for (int r = 0; r < c->R; ++r) {
@@ -1223,12 +1227,14 @@ static int batch_impl(Ctx* c, int32_t n_rep, const int32_t* cells, double a, con
   std::vector<long long> n0;
   std::vector<LatRep> lr;
   std::vector<RepState> rs;
-  long long words = 0, slots = 0;
+  long long words = 0, slots = 0, sites = 0;
   for (int r = 0; r < n_rep; ++r) {
     Ctx* sc = c->subs[r];
     if (sc->steps_per_sweep != c->steps_per_sweep || sc->mc.n_shells != c->mc.n_shells)
       return fail(c, VCSGC_ERR_INVALID_ARG, "replicas must share the schedule period");
-    const LatGeom g = lattice_geom(sc->nx, sc->ny, sc->nz, q, sc->sublattice_d, sc->dmax, words, slots);
+    LatGeom g = lattice_geom(sc->nx, sc->ny, sc->nz, q, sc->sublattice_d, sc->dmax, words, slots);
+    g.site_off = sites;
+    sites += g.n_sites;
     words += (long long)g.ny * g.nz * g.W;
     slots += g.dmax;
     c->h_geom.push_back(g);
@@ -1398,6 +1404,7 @@ int observables(void* ctx, int32_t r, vcsgc_observables* o) {
   o->sweeps = (double)s.trials / Nr;
   o->kappa_p = p.kappa_p;
   o->dmu0 = p.dmu0;
+  o->stage1_accepts = s.s1_acc;
   return VCSGC_OK;
 }
 
@@ -1598,6 +1605,63 @@ int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* c
     CK(cudaMemcpyAsync(out, c->nbr + i * c->K, sizeof(int) * m, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
   }
+  return VCSGC_OK;
+}
+
+// ---- delayed acceptance (the learned first stage)
+static bool da_neighbourhood(const Ctx* c) {
+  // the descriptor's five BCC shells (8, 6, 12, 24, 8 sites) in 13 rows per basis
+  if (!c->fast || c->lat.n_shells != 5 || c->lat.n_rows[0] != 13 || c->lat.n_rows[1] != 13) return false;
+  int zs[5] = {0, 0, 0, 0, 0};
+  for (int sh : c->offset_shell) zs[sh]++;
+  return zs[0] == 8 && zs[1] == 6 && zs[2] == 12 && zs[3] == 24 && zs[4] == 8;
+}
+
+int vcsgc_features(void* ctx, float* d_X, float* d_Y) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !d_X || !d_Y) return VCSGC_ERR_INVALID_ARG;
+  if (!da_neighbourhood(c))
+    return fail(c, VCSGC_ERR_STATE, "features need the fused rigid-lattice form with the 5-shell BCC neighbourhood");
+  TRY(flush(c));
+  long long max_sites = 0;
+  for (const LatGeom& g : c->h_geom) max_sites = std::max(max_sites, g.n_sites);
+  launch_lattice_features(c->lat, max_sites, d_X, d_Y, c->st);
+  CK(cudaGetLastError());
+  return check_device_error(c);
+}
+
+int vcsgc_set_surrogate(void* ctx, void* mlp) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return VCSGC_ERR_INVALID_ARG;
+  if (!mlp) {
+    TRY(flush(c));
+    CK(cudaStreamSynchronize(c->st));
+    c->lat.da = 0;
+    drop_graph(c);
+    return VCSGC_OK;
+  }
+  if (!da_neighbourhood(c))
+    return fail(c, VCSGC_ERR_STATE,
+                "delayed acceptance needs the fused rigid-lattice form with the 5-shell BCC neighbourhood");
+  MlpBuf src{};
+  if (!mlp_object_buffers(mlp, &src)) return VCSGC_ERR_INVALID_ARG;
+  if (!c->sur.w1f) {
+    TRY(dalloc(c, &c->sur.w1f, MLP_W1F));
+    TRY(dalloc(c, &c->sur.w2f, MLP_W2F));
+    TRY(dalloc(c, &c->sur.w2tf, MLP_W2F));
+    TRY(dalloc(c, &c->sur.vec, MLP_VEC));
+  }
+  // the surrogate's own stream may still be writing its fragments
+  CK(cudaStreamSynchronize(mlp_object_stream(mlp)));
+  TRY(flush(c));
+  CK(cudaMemcpyAsync(c->sur.w1f, src.w1f, sizeof(uint2) * MLP_W1F, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(c->sur.w2f, src.w2f, sizeof(uint2) * MLP_W2F, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(c->sur.w2tf, src.w2tf, sizeof(uint2) * MLP_W2F, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(c->sur.vec, src.vec, sizeof(float) * MLP_VEC, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->lat.mlp = mlp_view(c->sur);
+  c->lat.da = 1;
+  drop_graph(c);  // the captured steps hold the arguments by value
   return VCSGC_OK;
 }
 

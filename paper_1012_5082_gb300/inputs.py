@@ -255,3 +255,22 @@ def maxwell_velocities(types: np.ndarray, T: float, seed: int,
     v -= p[None, :]
     return (np.ascontiguousarray(v[:, 0]), np.ascontiguousarray(v[:, 1]),
             np.ascontiguousarray(v[:, 2]))
+
+
+MLP_IN, MLP_H = 10, 64
+MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+
+
+def mlp_init(seed: int, out_bias: float = 0.0) -> np.ndarray:
+    """Initial parameters of the 10 -> 64 -> 64 -> 1 surrogate network in the
+    packed order W1[64][10], b1, W2[64][64], b2, w3[64], b3: Glorot-uniform
+    weights, zero biases, b3 = out_bias (float32)."""
+    rng = np.random.default_rng(seed)
+
+    def glorot(fan_out, fan_in):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        return rng.uniform(-lim, lim, size=fan_out * fan_in)
+
+    parts = [glorot(MLP_H, MLP_IN), np.zeros(MLP_H), glorot(MLP_H, MLP_H), np.zeros(MLP_H),
+             glorot(1, MLP_H), [out_bias]]
+    return np.concatenate(parts).astype(np.float32)

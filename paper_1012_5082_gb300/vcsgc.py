@@ -19,6 +19,8 @@ ERR = {-1: "INVALID_ARG", -2: "CUDA", -3: "TABLE_RANGE", -4: "NONFINITE", -5: "S
        -6: "TIMEOUT", -7: "NOMEM", -8: "STATE", -9: "OVERFLOW"}
 SCHED_BLOCKS, SCHED_SUBLATTICE, SCHED_SPATIAL = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
+MLP_IN = 10
+MLP_NPARAM = 4929
 
 
 class VcsgcError(RuntimeError):
@@ -57,7 +59,7 @@ class Observables(C.Structure):
                 ("global_accepts", C.c_int64), ("flips", C.c_int64), ("near_ties", C.c_int64),
                 ("acc_local", C.c_double), ("acc_global", C.c_double), ("mean_c", C.c_double),
                 ("var_c", C.c_double), ("dmu_est", C.c_double), ("sweeps", C.c_double),
-                ("kappa_p", C.c_double), ("dmu0", C.c_double)]
+                ("kappa_p", C.c_double), ("dmu0", C.c_double), ("stage1_accepts", C.c_int64)]
 
 
 _lib = None
@@ -66,7 +68,9 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_get_rho", "vcsgc_delta_e", "vcsgc_energy", "vcsgc_forces", "vcsgc_get_md",
            "vcsgc_set_velocities", "vcsgc_kinetic_energy", "vcsgc_neighbours", "vcsgc_last_error",
            "vcsgc_free", "vcsgc_profile_steps", "vcsgc_neighbour_list_noalloc", "vcsgc_batch_init",
-           "vcsgc_autotune"]
+           "vcsgc_autotune", "vcsgc_features", "vcsgc_mlp_create", "vcsgc_mlp_set_params",
+           "vcsgc_mlp_get_params", "vcsgc_mlp_forward", "vcsgc_mlp_grad", "vcsgc_mlp_train",
+           "vcsgc_mlp_last_error", "vcsgc_mlp_free", "vcsgc_set_surrogate"]
 
 
 def lib():
@@ -103,6 +107,16 @@ def lib():
             "vcsgc_autotune": (I32, [P, I64, P]),
             "vcsgc_last_error": (C.c_char_p, [P]),
             "vcsgc_free": (None, [P]),
+            "vcsgc_features": (I32, [P, P, P]),
+            "vcsgc_mlp_create": (I32, [C.POINTER(C.c_void_p), P, P]),
+            "vcsgc_mlp_set_params": (I32, [P, P]),
+            "vcsgc_mlp_get_params": (I32, [P, P]),
+            "vcsgc_mlp_forward": (I32, [P, P, I64, P]),
+            "vcsgc_mlp_grad": (I32, [P, P, P, I64, P, P]),
+            "vcsgc_mlp_train": (I32, [P, P, P, I64, I64, I64, D, C.c_uint64, P]),
+            "vcsgc_mlp_last_error": (C.c_char_p, [P]),
+            "vcsgc_mlp_free": (None, [P]),
+            "vcsgc_set_surrogate": (I32, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -168,6 +182,106 @@ def vcsgc_neighbour_list_noalloc(n, d_x, d_y, d_z, box, rl, K, d_nbr, d_cnt, str
                                               C.c_void_p(d_z), b, float(rl), int(K),
                                               C.c_void_p(d_nbr), C.c_void_p(d_cnt),
                                               C.c_void_p(stream) if stream else None)
+
+
+def vcsgc_features(ctx, d_X, d_Y):
+    """Device pointers (integers) of the caller's [rows][10] and [rows] float
+    buffers."""
+    _check(lib().vcsgc_features(ctx, C.c_void_p(d_X), C.c_void_p(d_Y)), ctx)
+
+
+def vcsgc_set_surrogate(ctx, mlp):
+    _check(lib().vcsgc_set_surrogate(ctx, mlp), ctx)
+
+
+def _check_mlp(rc, m):
+    if rc != OK:
+        msg = lib().vcsgc_mlp_last_error(m) if m else b""
+        raise VcsgcError(rc, msg.decode() if msg else "")
+
+
+def vcsgc_mlp_create(params, stream=None):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.shape == (MLP_NPARAM,)
+    h = C.c_void_p()
+    _check_mlp(lib().vcsgc_mlp_create(C.byref(h), _ptr(p), stream), None)
+    return h
+
+
+def vcsgc_mlp_forward(mlp, d_X, n, d_out):
+    _check_mlp(lib().vcsgc_mlp_forward(mlp, C.c_void_p(d_X), int(n), C.c_void_p(d_out)), mlp)
+
+
+def vcsgc_mlp_grad(mlp, d_X, d_Y, n):
+    g = np.zeros(MLP_NPARAM, dtype=np.float32)
+    loss = C.c_double()
+    _check_mlp(lib().vcsgc_mlp_grad(mlp, C.c_void_p(d_X), C.c_void_p(d_Y), int(n), _ptr(g), C.byref(loss)), mlp)
+    return g, loss.value
+
+
+def vcsgc_mlp_train(mlp, d_X, d_Y, n, batch, steps, lr, seed):
+    hist = np.zeros(max(1, int(steps)), dtype=np.float64)
+    _check_mlp(lib().vcsgc_mlp_train(mlp, C.c_void_p(d_X), C.c_void_p(d_Y), int(n), int(batch), int(steps),
+                                     float(lr), int(seed), _ptr(hist)), mlp)
+    return hist[:int(steps)]
+
+
+def vcsgc_mlp_get_params(mlp):
+    p = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _check_mlp(lib().vcsgc_mlp_get_params(mlp, _ptr(p)), mlp)
+    return p
+
+
+def vcsgc_mlp_set_params(mlp, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.shape == (MLP_NPARAM,)
+    _check_mlp(lib().vcsgc_mlp_set_params(mlp, _ptr(p)), mlp)
+
+
+def vcsgc_mlp_free(mlp):
+    lib().vcsgc_mlp_free(mlp)
+
+
+class Surrogate:
+    """The delayed-acceptance surrogate network (vcsgc_mlp_*); inputs and
+    outputs are CUDA float32 torch tensors."""
+
+    def __init__(self, params, stream=None):
+        self.h = vcsgc_mlp_create(params, None if stream is None else getattr(stream, "cuda_stream", stream))
+
+    def close(self):
+        if getattr(self, "h", None):
+            vcsgc_mlp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def params(self):
+        return vcsgc_mlp_get_params(self.h)
+
+    @params.setter
+    def params(self, p):
+        vcsgc_mlp_set_params(self.h, p)
+
+    def forward(self, X):
+        import torch
+        X = X.contiguous()
+        out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        vcsgc_mlp_forward(self.h, X.data_ptr(), X.shape[0], out.data_ptr())
+        return out
+
+    def grad(self, X, Y):
+        X, Y = X.contiguous(), Y.contiguous()
+        return vcsgc_mlp_grad(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0])
+
+    def train(self, X, Y, *, batch=4096, steps=1000, lr=1e-3, seed=1):
+        X, Y = X.contiguous(), Y.contiguous()
+        return vcsgc_mlp_train(self.h, X.data_ptr(), Y.data_ptr(), X.shape[0], batch, steps, lr, seed)
 
 
 # ----------------------------------------------------------- convenience
@@ -358,6 +472,21 @@ class Context:
         b = C.c_int32()
         _check(lib().vcsgc_autotune(self.h, int(steps), C.byref(b)), self.h)
         return b.value
+
+    def features(self):
+        """(X [rows, 10], Y [rows]) CUDA float32 tensors of every site of every
+        replica (vcsgc_features)."""
+        import torch
+        rows = int(sum(self.sizes)) if hasattr(self, "sizes") else self.n * self.n_replicas
+        X = torch.empty((rows, MLP_IN), dtype=torch.float32, device="cuda")
+        Y = torch.empty(rows, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        vcsgc_features(self.h, X.data_ptr(), Y.data_ptr())
+        return X, Y
+
+    def set_surrogate(self, surrogate):
+        """Delayed acceptance with a copy of surrogate's weights (None: off)."""
+        vcsgc_set_surrogate(self.h, None if surrogate is None else surrogate.h)
 
     def neighbours(self, i, cap=256):
         out = np.zeros(cap, dtype=np.int32)

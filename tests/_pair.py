@@ -39,3 +39,19 @@ def compare_obs(o_orc, o_gpu, exact=("n_b", "trials", "local_accepts", "global_t
     for k in exact:
         assert o_orc[k] == o_gpu[k], (k, o_orc[k], o_gpu[k])
     assert abs(o_orc["energy"] - o_gpu["energy"]) <= 1e-9 * max(1.0, abs(o_orc["energy"]))
+
+
+def lockstep(orc, g, n_sweeps, steps_per_sweep):
+    """Advance both a sweep at a time; species must agree bit for bit unless
+    the oracle flagged a near-tie decision in that sweep (then re-sync)."""
+    resyncs = 0
+    for s in range(n_sweeps):
+        ties0 = orc.obs()["near_ties"]
+        g.sweep(1)
+        orc.parallel_steps(steps_per_sweep)
+        tg, to = g.types(), orc.types
+        if not np.array_equal(tg, to):
+            assert orc.obs()["near_ties"] > ties0, f"sweep {s}: species differ without a flagged tie"
+            g.set_types(to)
+            resyncs += 1
+    return resyncs

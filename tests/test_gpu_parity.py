@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 from paper_1012_5082_gb300 import inputs as I
-from _pair import c0_config, compare_obs, make_pair
+from _pair import c0_config, compare_obs, lockstep as _lockstep, make_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -75,22 +75,6 @@ def test_delta_e_matches_on_explicit_positions(V, dens_b):
 
 
 # ------------------------------------------------ trajectories (A3-A9)
-def _lockstep(orc, g, n_sweeps, steps_per_sweep):
-    """Advance both a sweep at a time; species must agree bit for bit unless
-    the oracle flagged a near-tie decision in that sweep (then re-sync)."""
-    resyncs = 0
-    for s in range(n_sweeps):
-        ties0 = orc.obs()["near_ties"]
-        g.sweep(1)
-        orc.parallel_steps(steps_per_sweep)
-        tg, to = g.types(), orc.types
-        if not np.array_equal(tg, to):
-            assert orc.obs()["near_ties"] > ties0, f"sweep {s}: species differ without a flagged tie"
-            g.set_types(to)
-            resyncs += 1
-    return resyncs
-
-
 CASES = {
     # name: (phi, kappa, T, c0, dens_b, schedule, sched)
     "c0-as-specified": (-2.0, 1000.0, 700.0, 0.05, 1.0, "blocks", (5, 5, 5, 2, 2, 2)),
