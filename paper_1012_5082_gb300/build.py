@@ -69,5 +69,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_alu_peaks() -> str:
+    """Compile the standalone ALU throughput probe (csrc/alu_peaks.cu)."""
+    os.makedirs(BUILD, exist_ok=True)
+    exe = os.path.join(BUILD, "alu_peaks")
+    src = os.path.join(CSRC, "alu_peaks.cu")
+    if not os.path.exists(exe) or os.path.getmtime(exe) < os.path.getmtime(src):
+        r = subprocess.run([_nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", exe], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on alu_peaks.cu:\n{r.stderr}")
+    return exe
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))

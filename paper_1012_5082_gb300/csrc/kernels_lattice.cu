@@ -154,6 +154,50 @@ __device__ __forceinline__ void descriptor_pairs(const int (&cnt)[NS], const int
   for (int c = 0; c < 5; ++c) p[c] = bf16x2(x[2 * c], x[2 * c + 1]);
 }
 
+// The same counts in two phases: the raw words of the NR rows (and of the
+// site's own word) are loaded first -- they do not depend on the decision
+// mask -- so the loads overlap the derivation of G_{k-1}; the counts are
+// formed once gm is known.  A word read before another thread's commit of
+// step k-1 and one read after it give the same effective species.
+template <int NR>
+struct RowWords {
+  unsigned long long w0[NR], w1[NR], own;
+};
+
+template <int NR>
+__device__ __forceinline__ void lattice_rows_load(const LatArgs& a, const LatGeom& g, int X, int Y, int Z, int b,
+                                                  RowWords<NR>& rw) {
+  const int H = 2 * X + b;
+  const LatRow* rows = a.rows[b];
+  const int q0 = LAT_HALO + H - a.hmax;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    int yy = Y + rows[q].dy, zz = Z + rows[q].dz;
+    yy = yy < 0 ? yy + g.ny : (yy >= g.ny ? yy - g.ny : yy);
+    zz = zz < 0 ? zz + g.nz : (zz >= g.nz ? zz - g.nz : zz);
+    const unsigned long long* row = row_ptr(a, g, yy, zz);
+    rw.w0[q] = __ldcg(row + (q0 >> 5));
+    rw.w1[q] = __ldcg(row + (q0 >> 5) + 1);
+  }
+  rw.own = __ldcg(row_ptr(a, g, Y, Z) + ((LAT_HALO + H) >> 5));
+}
+
+template <int NS, int NR>
+__device__ __forceinline__ void lattice_counts_from(const LatArgs& a, int H, int b, const RowWords<NR>& rw,
+                                                    uint32_t gm, int (&cnt)[NS], int& t) {
+  const LatRow* rows = a.rows[b];
+  const int sh = (LAT_HALO + H - a.hmax) & 31;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) cnt[s] = 0;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const uint32_t win = __funnelshift_r(eff32(rw.w0[q], gm), eff32(rw.w1[q], gm), sh);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) cnt[s] += __popc(win & rows[q].mask[s]);
+  }
+  t = (eff32(rw.own, gm) >> ((LAT_HALO + H) & 31)) & 1;
+}
+
 // dE of flipping the site (FP64): the A->B value C + sum_s b_s G_s + dF_i,
 // negated for B->A (i is the site index within its replica)
 template <int NS>
@@ -215,35 +259,35 @@ __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long
   return (int)below64(w.x, w.y, (uint64_t)a.n_colours);
 }
 
+// Programmatic dependent launch: within a chain of colour steps every launch
+// after the first is made with programmatic stream serialization, so the
+// next step's blocks are scheduled, and draw their random numbers and pick
+// their sites, while this step drains.  What a step reads that the previous
+// step writes (accumulators, bits, pending slots, states) is read after
+// griddepcontrol.wait, which returns once the preceding grid has completed
+// and its memory is visible.  Before it a step reads only host-written
+// tables and the step base, which only k_lattice_advance writes: that
+// kernel and the first step after it are ordinary launches, so the base is
+// final before any step of the chain starts.  Without the attribute both
+// instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <bool PROPOSE, int NS, int NR, int BS, bool DA>
 __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
+  pdl_trigger();
   const int r = blockIdx.y;
   const LatGeom g = a.geom[r];
-  const long long k = a.ctl->base_step + j;
-  const long long kp = k - 1;
   const RepParams p = a.rp[r];
   const int d = blockIdx.x * BS + threadIdx.x;
+  const long long k = a.ctl->base_step + j;
+  const long long kp = k - 1;
   __shared__ int s_g[2];  // [0] = G_{k-1}, [1] = near-tie of that decision
 
-  // 1. global decision of step k-1: one thread per block, FP64
-  if (threadIdx.x == 0) {
-    int G = 0, tie = 0;
-    if (kp >= 0) {
-      const int naccp = *(volatile const int*)&a.acc[r * 3 + (int)(kp % 3)].nacc;
-      if (naccp > 0) {
-        const int dnp = *(volatile const int*)&a.acc[r * 3 + (int)(kp % 3)].dn;
-        const long long np = a.n_start[r * 2 + (int)(kp & 1)];
-        uint64_t ug53;
-        lat_colour(a, p.key, kp, &ug53);
-        const double Y = p.beta * p.kappa_p * (double)dnp * ((double)dnp + 2.0 * ((double)np - p.n0));
-        G = metropolis(Y, ug53, &tie) ? 1 : 0;
-      }
-    }
-    s_g[0] = G;
-    s_g[1] = tie;
-  }
-
-  // 2. propose inputs that do not depend on G: colour, site, random word
+  // inputs that depend on no earlier launch: the global uniform of step k-1
+  // (thread 0), the colour, site and random word of trial d of step k
+  uint64_t ug53 = 0;
+  if (threadIdx.x == 0 && kp >= 0) lat_colour(a, p.key, kp, &ug53);
   int site = -1, sX = 0, sY = 0, sZ = 0, sb_ = 0;
   uint4 w = make_uint4(0, 0, 0, 0);
   if (PROPOSE) {
@@ -277,6 +321,29 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
         decode_site(g, site, sX, sY, sZ, sb_);
       }
     }
+  }
+  pdl_wait();
+
+  // 1. global decision of step k-1: one thread per block, FP64
+  if (threadIdx.x == 0) {
+    int G = 0, tie = 0;
+    if (kp >= 0) {
+      const int naccp = *(volatile const int*)&a.acc[r * 3 + (int)(kp % 3)].nacc;
+      if (naccp > 0) {
+        const int dnp = *(volatile const int*)&a.acc[r * 3 + (int)(kp % 3)].dn;
+        const long long np = a.n_start[r * 2 + (int)(kp & 1)];
+        const double Y = p.beta * p.kappa_p * (double)dnp * ((double)dnp + 2.0 * ((double)np - p.n0));
+        G = metropolis(Y, ug53, &tie) ? 1 : 0;
+      }
+    }
+    s_g[0] = G;
+    s_g[1] = tie;
+  }
+
+  // rows of the trial site, loaded before the decision of step k-1 is known
+  RowWords<(NR > 0 ? NR : 1)> rw;
+  if constexpr (PROPOSE && !DA && NR > 0) {
+    if (site >= 0) lattice_rows_load<NR>(a, g, sX, sY, sZ, sb_, rw);
   }
   __syncthreads();
   const bool Gp = s_g[0] != 0;
@@ -374,7 +441,8 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
       }
     }
   } else if (site >= 0) {
-    lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
+    if constexpr (NR > 0) lattice_counts_from<NS, NR>(a, 2 * sX + sb_, sb_, rw, gm, cnt, t);
+    else lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
     accepted = lattice_accept<NS>(a, a.lrep[r], p, cnt, site, t, top53(w.z, w.w), &tie);
   }
   if (accepted) {
@@ -513,12 +581,30 @@ void launch_to_float(const double* in, float* out, long long n, cudaStream_t st)
   k_to_float<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, out, n);
 }
 
+// launch, with programmatic stream serialization when pdl (see pdl_wait)
+template <typename K>
+static void launch_step(K kern, dim3 grid, int block, cudaStream_t st, const LatArgs& a, int j, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, a, j);
+}
+
 template <int NS, int NR, int BS>
 static void step_bs(const LatArgs& a, int j, bool propose, cudaStream_t st) {
   const dim3 g((a.dmax + BS - 1) / BS, a.R);
-  if (!propose) k_lattice_step<false, NS, NR, BS, false><<<g, BS, 0, st>>>(a, j);
-  else if (NS == 5 && NR == 13 && a.da) k_lattice_step<true, NS, NR, BS, NS == 5 && NR == 13><<<g, BS, 0, st>>>(a, j);
-  else k_lattice_step<true, NS, NR, BS, false><<<g, BS, 0, st>>>(a, j);
+  const bool pdl = j > 0;  // the first step of a chain is an ordinary launch
+  if (!propose) launch_step(k_lattice_step<false, NS, NR, BS, false>, g, BS, st, a, j, pdl);
+  else if (NS == 5 && NR == 13 && a.da)
+    launch_step(k_lattice_step<true, NS, NR, BS, NS == 5 && NR == 13>, g, BS, st, a, j, pdl);
+  else launch_step(k_lattice_step<true, NS, NR, BS, false>, g, BS, st, a, j, pdl);
 }
 
 template <int NS, int NR>
