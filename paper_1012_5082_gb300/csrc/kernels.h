@@ -116,6 +116,8 @@ struct LatArgs {
   const int* dom_start;
   const int* dom_sites;
   int dmax;                     // largest pending-slot count of a replica
+  const int2* blk;              // [n_blk] (replica, first trial) of each block of `block` threads
+  int n_blk;
   // replicas
   const RepParams* rp;
   RepState* rs;
@@ -128,9 +130,12 @@ struct LatArgs {
   // the surrogate's prediction, stage 2 the exact dE
   int da;
   MlpW mlp;
+  int bcc5;                     // rows and masks equal the compile-time 5-shell BCC table
 };
 
 void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);
+// true when the rows and masks of a equal the compile-time five-shell table
+bool lattice_rows_bcc5(const LatArgs& a);
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 void launch_lattice_pack(const LatArgs& a, const LatGeom& g, const uint8_t* types_r, int r, cudaStream_t st);

@@ -115,6 +115,123 @@ __device__ __forceinline__ void lattice_counts_at(const LatArgs& a, const LatGeo
   t = own_bit(row_ptr(a, g, Y, Z), H, gm);
 }
 
+// raw words of a site's neighbour rows (w0, w1: the two words holding its
+// window in row q) and of its own word
+template <int NR>
+struct RowWords {
+  unsigned long long w0[NR], w1[NR], own;
+};
+
+// The five-shell BCC neighbourhood (r_c between sqrt(3) a and 2 a: half-
+// lattice offsets with |h|^2 in {3, 4, 8, 11, 12}, 58 sites) as compile-time
+// rows.  For basis b and row q: bits 7s..7s+6 hold the 7-bit window mask of
+// shell s (window bit h_x + 3), bits 40..43 hold dy + 2 and bits 44..47
+// dz + 2.  Rows and masks are the ones the host derives from the sorted
+// offset table; the host compares the two before it selects this form.  As
+// constants the masks let the compiler drop the (row, shell) pairs that
+// hold no site (33 of the 65 are non-empty) and turn one-bit masks into
+// bit tests.
+__host__ __device__ __forceinline__ constexpr unsigned long long bcc5_row(int b, int q) {
+  switch (16 * b + q) {
+    case 0: return 0x110228220014ull;
+    case 1: return 0x210008288414ull;
+    case 2: return 0x120008288414ull;
+    case 3: return 0x220008201114ull;
+    case 4: return 0x320002888400ull;
+    case 5: return 0x230002888400ull;
+    case 6: return 0x310222820000ull;
+    case 7: return 0x130222820000ull;
+    case 8: return 0x330220020000ull;
+    case 9: return 0x100002800000ull;
+    case 10: return 0x200002800000ull;
+    case 11: return 0x010002800000ull;
+    case 12: return 0x020002800000ull;
+    case 16: return 0x220008201114ull;
+    case 17: return 0x320008288414ull;
+    case 18: return 0x230008288414ull;
+    case 19: return 0x330228220014ull;
+    case 20: return 0x210002888400ull;
+    case 21: return 0x120002888400ull;
+    case 22: return 0x110220020000ull;
+    case 23: return 0x310222820000ull;
+    case 24: return 0x130222820000ull;
+    case 25: return 0x420002800000ull;
+    case 26: return 0x430002800000ull;
+    case 27: return 0x240002800000ull;
+    case 28: return 0x340002800000ull;
+    default: return 0ull;
+  }
+}
+
+__device__ __forceinline__ int wrap_add(int y, int dy, int n) {
+  y += dy;
+  return y < 0 ? y + n : (y >= n ? y - n : y);
+}
+
+template <int B>
+__device__ __forceinline__ void bcc5_rows_load(const LatArgs& a, const LatGeom& g, int X, int Y, int Z,
+                                               RowWords<13>& rw) {
+  const int q0 = LAT_HALO + 2 * X + B - 3;
+#pragma unroll
+  for (int q = 0; q < 13; ++q) {
+    const unsigned long long code = bcc5_row(B, q);
+    const int dy = (int)((code >> 40) & 15) - 2, dz = (int)((code >> 44) & 15) - 2;
+    const unsigned long long* row = row_ptr(a, g, wrap_add(Y, dy, g.ny), wrap_add(Z, dz, g.nz));
+    rw.w0[q] = __ldcg(row + (q0 >> 5));
+    rw.w1[q] = __ldcg(row + (q0 >> 5) + 1);
+  }
+  rw.own = __ldcg(row_ptr(a, g, Y, Z) + ((LAT_HALO + 2 * X + B) >> 5));
+}
+
+template <int B>
+__device__ __forceinline__ void bcc5_counts_from(int X, const RowWords<13>& rw, uint32_t gm, int (&cnt)[5],
+                                                 int& t) {
+  const int H = 2 * X + B;
+  const int sh = (LAT_HALO + H - 3) & 31;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) cnt[s] = 0;
+#pragma unroll
+  for (int q = 0; q < 13; ++q) {
+    const unsigned long long code = bcc5_row(B, q);
+    const uint32_t win = __funnelshift_r(eff32(rw.w0[q], gm), eff32(rw.w1[q], gm), sh);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      const uint32_t m = (uint32_t)(code >> (7 * s)) & 0x7Fu;
+      if (m) cnt[s] += __popc(win & m);
+    }
+  }
+  t = (eff32(rw.own, gm) >> ((LAT_HALO + H) & 31)) & 1;
+}
+
+template <int B>
+__device__ __forceinline__ void bcc5_counts_at(const LatArgs& a, const LatGeom& g, int X, int Y, int Z,
+                                               uint32_t gm, int (&cnt)[5], int& t) {
+  RowWords<13> rw;
+  bcc5_rows_load<B>(a, g, X, Y, Z, rw);
+  bcc5_counts_from<B>(X, rw, gm, cnt, t);
+}
+
+// first-shell neighbours' summed counts (as lattice_nb_counts) on the
+// compile-time rows; B is the basis of the site, the neighbours have 1 - B
+template <int B>
+__device__ __forceinline__ void bcc5_nb_counts(const LatArgs& a, const LatGeom& g, int X, int Y, int Z,
+                                               uint32_t gm, int ti, int (&nb)[5]) {
+#pragma unroll
+  for (int s = 0; s < 5; ++s) nb[s] = 0;
+  const int lo = B ? 0 : -1;
+#pragma unroll 1
+  for (int q = 0; q < 8; ++q) {
+    const int xx = wrap_add(X, lo + (q & 1), g.nx);
+    const int yy = wrap_add(Y, lo + ((q >> 1) & 1), g.ny);
+    const int zz = wrap_add(Z, lo + (q >> 2), g.nz);
+    int c[5], tk;
+    bcc5_counts_at<1 - B>(a, g, xx, yy, zz, gm, c, tk);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) nb[s] += c[s];
+  }
+  nb[0] -= 8 * ti;
+}
+
 // Summed per-shell B counts of the 8 first-shell neighbours k of site
 // (X, Y, Z, b), each without the site itself (species ti, in shell 1 of k):
 // the second half of the surrogate's environment descriptor.  The
@@ -159,10 +276,6 @@ __device__ __forceinline__ void descriptor_pairs(const int (&cnt)[NS], const int
 // mask -- so the loads overlap the derivation of G_{k-1}; the counts are
 // formed once gm is known.  A word read before another thread's commit of
 // step k-1 and one read after it give the same effective species.
-template <int NR>
-struct RowWords {
-  unsigned long long w0[NR], w1[NR], own;
-};
 
 template <int NR>
 __device__ __forceinline__ void lattice_rows_load(const LatArgs& a, const LatGeom& g, int X, int Y, int Z, int b,
@@ -273,13 +386,15 @@ __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <bool PROPOSE, int NS, int NR, int BS, bool DA>
+template <bool PROPOSE, int NS, int NR, int BS, bool DA, bool B5>
 __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   pdl_trigger();
-  const int r = blockIdx.y;
+  // block -> (replica, first trial): only the blocks a replica needs
+  const int2 bk = a.blk[blockIdx.x];
+  const int r = bk.x;
   const LatGeom g = a.geom[r];
   const RepParams p = a.rp[r];
-  const int d = blockIdx.x * BS + threadIdx.x;
+  const int d = bk.y + threadIdx.x;
   const long long k = a.ctl->base_step + j;
   const long long kp = k - 1;
   __shared__ int s_g[2];  // [0] = G_{k-1}, [1] = near-tie of that decision
@@ -343,7 +458,14 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   // rows of the trial site, loaded before the decision of step k-1 is known
   RowWords<(NR > 0 ? NR : 1)> rw;
   if constexpr (PROPOSE && !DA && NR > 0) {
-    if (site >= 0) lattice_rows_load<NR>(a, g, sX, sY, sZ, sb_, rw);
+    if (site >= 0) {
+      if constexpr (B5) {
+        if (sb_) bcc5_rows_load<1>(a, g, sX, sY, sZ, rw);
+        else bcc5_rows_load<0>(a, g, sX, sY, sZ, rw);
+      } else {
+        lattice_rows_load<NR>(a, g, sX, sY, sZ, sb_, rw);
+      }
+    }
   }
   __syncthreads();
   const bool Gp = s_g[0] != 0;
@@ -362,7 +484,7 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
 
   // 4. finalise step k-1 (second warp of block 0, off the first warp's
   //    path) and clear the accumulator of step k+1; whole-struct accesses
-  if (blockIdx.x == 0 && threadIdx.x == 32) {
+  if (bk.y == 0 && threadIdx.x == 32) {
     RepState S = a.rs[r];
     if (kp >= 0 && S.fin_step < kp) {
       const StepAcc A = a.acc[r * 3 + (int)(kp % 3)];
@@ -422,9 +544,19 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
     // surrogate's evaluation (lanes without a trial feed zeros)
     uint32_t P[5] = {0u, 0u, 0u, 0u, 0u};
     if (site >= 0) {
-      lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
       int nb[NS];
-      lattice_nb_counts<NS, NR>(a, g, sX, sY, sZ, sb_, gm, t, nb);
+      if constexpr (B5) {
+        if (sb_) {
+          bcc5_counts_at<1>(a, g, sX, sY, sZ, gm, cnt, t);
+          bcc5_nb_counts<1>(a, g, sX, sY, sZ, gm, t, nb);
+        } else {
+          bcc5_counts_at<0>(a, g, sX, sY, sZ, gm, cnt, t);
+          bcc5_nb_counts<0>(a, g, sX, sY, sZ, gm, t, nb);
+        }
+      } else {
+        lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
+        lattice_nb_counts<NS, NR>(a, g, sX, sY, sZ, sb_, gm, t, nb);
+      }
       descriptor_pairs<NS>(cnt, nb, P);
     }
     const float gnn = mlp_warp_eval(a.mlp, P);
@@ -441,8 +573,14 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
       }
     }
   } else if (site >= 0) {
-    if constexpr (NR > 0) lattice_counts_from<NS, NR>(a, 2 * sX + sb_, sb_, rw, gm, cnt, t);
-    else lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
+    if constexpr (B5) {
+      if (sb_) bcc5_counts_from<1>(sX, rw, gm, cnt, t);
+      else bcc5_counts_from<0>(sX, rw, gm, cnt, t);
+    } else if constexpr (NR > 0) {
+      lattice_counts_from<NS, NR>(a, 2 * sX + sb_, sb_, rw, gm, cnt, t);
+    } else {
+      lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
+    }
     accepted = lattice_accept<NS>(a, a.lrep[r], p, cnt, site, t, top53(w.z, w.w), &tie);
   }
   if (accepted) {
@@ -462,15 +600,16 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
   const bool any = __ballot_sync(0xffffffffu, acc | tie | s1) != 0u;
   if (any) {
+    // integer sums with one redux.sync each; the FP64 sum by shuffles
+    dn = __reduce_add_sync(0xffffffffu, dn);
+    acc = __reduce_add_sync(0xffffffffu, acc);
+    tie = __reduce_add_sync(0xffffffffu, tie);
+    if constexpr (DA) s1 = __reduce_add_sync(0xffffffffu, s1);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      dn += __shfl_xor_sync(0xffffffffu, dn, o);
-      acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      tie += __shfl_xor_sync(0xffffffffu, tie, o);
-      if constexpr (DA) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    for (int q = 0; q < NS; ++q) sb[q] = __reduce_add_sync(0xffffffffu, sb[q]);
+    if (!a.df_uniform) {
 #pragma unroll
-      for (int q = 0; q < NS; ++q) sb[q] += __shfl_xor_sync(0xffffffffu, sb[q], o);
-      if (!a.df_uniform) sdf += __shfl_xor_sync(0xffffffffu, sdf, o);
+      for (int o = 16; o > 0; o >>= 1) sdf += __shfl_xor_sync(0xffffffffu, sdf, o);
     }
   }
   if (l == 0) {
@@ -548,6 +687,7 @@ __global__ void k_lattice_delta_e(LatArgs a, int r, const int* sites, int n, dou
 
 // Descriptor counts and exact A->B energy change of every site (all
 // replicas; blockIdx.y = replica), species as stored (no pending flips)
+template <bool B5>
 __global__ void k_lattice_features(LatArgs a, float* X, float* Y) {
   const int r = blockIdx.y;
   const LatGeom g = a.geom[r];
@@ -556,8 +696,18 @@ __global__ void k_lattice_features(LatArgs a, float* X, float* Y) {
   int sX, sY, sZ, b, t;
   decode_site(g, (int)i, sX, sY, sZ, b);
   int cnt[5], nb[5];
-  lattice_counts_at<5, 13>(a, g, sX, sY, sZ, b, 0u, cnt, t);
-  lattice_nb_counts<5, 13>(a, g, sX, sY, sZ, b, 0u, t, nb);
+  if constexpr (B5) {
+    if (b) {
+      bcc5_counts_at<1>(a, g, sX, sY, sZ, 0u, cnt, t);
+      bcc5_nb_counts<1>(a, g, sX, sY, sZ, 0u, t, nb);
+    } else {
+      bcc5_counts_at<0>(a, g, sX, sY, sZ, 0u, cnt, t);
+      bcc5_nb_counts<0>(a, g, sX, sY, sZ, 0u, t, nb);
+    }
+  } else {
+    lattice_counts_at<5, 13>(a, g, sX, sY, sZ, b, 0u, cnt, t);
+    lattice_nb_counts<5, 13>(a, g, sX, sY, sZ, b, 0u, t, nb);
+  }
   const long long row = g.site_off + i;
 #pragma unroll
   for (int s = 0; s < 5; ++s) {
@@ -569,7 +719,8 @@ __global__ void k_lattice_features(LatArgs a, float* X, float* Y) {
 
 void launch_lattice_features(const LatArgs& a, long long max_sites, float* X, float* Y, cudaStream_t st) {
   const dim3 grid((unsigned)((max_sites + 127) / 128), (unsigned)a.R);
-  k_lattice_features<<<grid, 128, 0, st>>>(a, X, Y);
+  if (a.bcc5) k_lattice_features<true><<<grid, 128, 0, st>>>(a, X, Y);
+  else k_lattice_features<false><<<grid, 128, 0, st>>>(a, X, Y);
 }
 
 __global__ void k_to_float(const double* in, float* out, long long n) {
@@ -597,14 +748,25 @@ static void launch_step(K kern, dim3 grid, int block, cudaStream_t st, const Lat
   cudaLaunchKernelEx(&cfg, kern, a, j);
 }
 
+template <int NS, int NR, int BS, bool B5>
+static void step_b5(const LatArgs& a, int j, bool propose, cudaStream_t st) {
+  const dim3 g(a.n_blk);
+  const bool pdl = j > 0;  // the first step of a chain is an ordinary launch
+  constexpr bool DA_OK = NS == 5 && NR == 13;
+  if (!propose) launch_step(k_lattice_step<false, NS, NR, BS, false, B5>, g, BS, st, a, j, pdl);
+  else if (DA_OK && a.da) launch_step(k_lattice_step<true, NS, NR, BS, DA_OK, B5>, g, BS, st, a, j, pdl);
+  else launch_step(k_lattice_step<true, NS, NR, BS, false, B5>, g, BS, st, a, j, pdl);
+}
+
 template <int NS, int NR, int BS>
 static void step_bs(const LatArgs& a, int j, bool propose, cudaStream_t st) {
-  const dim3 g((a.dmax + BS - 1) / BS, a.R);
-  const bool pdl = j > 0;  // the first step of a chain is an ordinary launch
-  if (!propose) launch_step(k_lattice_step<false, NS, NR, BS, false>, g, BS, st, a, j, pdl);
-  else if (NS == 5 && NR == 13 && a.da)
-    launch_step(k_lattice_step<true, NS, NR, BS, NS == 5 && NR == 13>, g, BS, st, a, j, pdl);
-  else launch_step(k_lattice_step<true, NS, NR, BS, false>, g, BS, st, a, j, pdl);
+  if constexpr (NS == 5 && NR == 13) {
+    if (a.bcc5) {
+      step_b5<NS, NR, BS, true>(a, j, propose, st);
+      return;
+    }
+  }
+  step_b5<NS, NR, BS, false>(a, j, propose, st);
 }
 
 template <int NS, int NR>
@@ -624,6 +786,19 @@ void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st)
   if (a.n_shells == 5 && nr == 13) step_ns<5, 13>(a, j, propose, st);
   else if (a.n_shells == 1 && nr == 2) step_ns<1, 2>(a, j, propose, st);
   else step_ns<LAT_MAX_SH, 0>(a, j, propose, st);
+}
+
+bool lattice_rows_bcc5(const LatArgs& a) {
+  if (a.n_shells != 5 || a.hmax != 3 || a.n_rows[0] != 13 || a.n_rows[1] != 13) return false;
+  for (int b = 0; b < 2; ++b)
+    for (int q = 0; q < 13; ++q) {
+      const unsigned long long code = bcc5_row(b, q);
+      const LatRow& rw = a.rows[b][q];
+      if (rw.dy != (int)((code >> 40) & 15) - 2 || rw.dz != (int)((code >> 44) & 15) - 2) return false;
+      for (int s = 0; s < LAT_MAX_SH; ++s)
+        if (rw.mask[s] != (s < 5 ? (uint32_t)(code >> (7 * s)) & 0x7Fu : 0u)) return false;
+    }
+  return true;
 }
 
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st) {

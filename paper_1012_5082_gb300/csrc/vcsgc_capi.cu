@@ -101,7 +101,17 @@ struct Ctx {
   std::vector<int> offset_shell;
   // delayed acceptance: the context's copy of the surrogate's fragments
   MlpBuf sur{};
+  // fused form: block tables for blocks of 64, 128, 256 threads
+  int2* blk_tab[3] = {nullptr, nullptr, nullptr};
+  int n_blk_tab[3] = {0, 0, 0};
 };
+
+// point the fused step at the block table of its block size
+void select_blk(Ctx* c) {
+  const int q = c->lat.block == 64 ? 0 : (c->lat.block == 256 ? 2 : 1);
+  c->lat.blk = c->blk_tab[q];
+  c->lat.n_blk = c->n_blk_tab[q];
+}
 
 #define CK(call)                                                                       \
   do {                                                                                 \
@@ -986,6 +996,7 @@ static int lattice_shared(Ctx* c, int& unsupported) {
   l.dF32 = df32;
   l.hmax = hmax;
   l.n_shells = S;
+  l.bcc5 = lattice_rows_bcc5(l) ? 1 : 0;
   std::vector<int> zs(S, 0);
   for (int sh : c->offset_shell) zs[sh]++;
   c->sum_absG = 0.0;
@@ -1066,11 +1077,25 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   CK(cudaStreamSynchronize(c->st));
   for (auto& st : rs) st.fin_step = -1;
   CK(cudaMemcpyAsync(c->rs, rs.data(), sizeof(RepState) * R, cudaMemcpyHostToDevice, c->st));
+  // block tables: each replica gets ceil(dmax_r / BS) blocks (at least one,
+  // whose first thread-warp finalises the replica's steps)
+  const int bsz[3] = {64, 128, 256};
+  for (int q = 0; q < 3; ++q) {
+    std::vector<int2> tab;
+    for (int r = 0; r < R; ++r) {
+      const int nb = std::max(1, (c->h_geom[r].dmax + bsz[q] - 1) / bsz[q]);
+      for (int b = 0; b < nb; ++b) tab.push_back(make_int2(r, b * bsz[q]));
+    }
+    TRY(dalloc(c, &c->blk_tab[q], tab.size()));
+    CK(cudaMemcpyAsync(c->blk_tab[q], tab.data(), sizeof(int2) * tab.size(), cudaMemcpyHostToDevice, c->st));
+    c->n_blk_tab[q] = (int)tab.size();
+  }
   l.geom = dg;
   l.lrep = dlr;
   l.dmax = dmax;
   l.R = R;
   if (l.block == 0) l.block = 128;
+  select_blk(c);
   c->fast = true;
   fill_args(c);
   for (int r = 0; r < R; ++r) launch_lattice_pack(l, c->h_geom[r], c->rep_types[r], r, c->st);
@@ -1295,6 +1320,7 @@ int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
   CK(cudaEventCreate(&e1));
   for (int b : cand) {
     c->lat.block = b;
+    select_blk(c);
     drop_graph(c);
     // one untimed step with the candidate, then the timed ones
     TRY(run_steps_fast(c, 1));
@@ -1312,6 +1338,7 @@ int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->lat.block = bb;
+  select_blk(c);
   drop_graph(c);
   *best_block = bb;
   return check_device_error(c);
