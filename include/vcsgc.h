@@ -196,10 +196,13 @@ int vcsgc_batch_init(void** ctx, int32_t n_rep, const int32_t* cells, double a, 
                      const vcsgc_eam_tables* eam, const double* phi, const double* kappa,
                      const double* T, const vcsgc_options* opt);
 
-/* Pick the thread-block size (64, 128 or 256) of the fused colour step by
- * timing `steps` colour steps with each (these are real steps of the chain)
- * and keep the fastest for later launches; *best_block receives it.  A
- * context outside the fused form reports its fixed block size. */
+/* Pick the launch shape of the fused colour step by timing `steps` colour
+ * steps with each candidate (these are real steps of the chain): thread-
+ * block size 64, 128 or 256, each with and without loading the trial's
+ * neighbour rows ahead of the block barrier (shorter dependent chain, more
+ * registers).  The fastest is kept for later launches; *best_block receives
+ * its block size.  A context outside the fused form reports its fixed block
+ * size. */
 int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block);
 
 /* Advance every replica by n_steps colour steps (composite moves of

@@ -94,6 +94,7 @@ struct LatGeom {
 struct LatArgs {
   int R;
   int block;                    // threads per block (64, 128 or 256)
+  int prefetch;                 // load the trial's rows before the block barrier
   unsigned long long* bits;     // all replicas' rows (+1 pad word)
   const LatGeom* geom;          // [R]
   int hmax;                     // largest |half-lattice offset| along x

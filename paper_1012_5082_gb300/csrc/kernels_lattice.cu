@@ -386,7 +386,7 @@ __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <bool PROPOSE, int NS, int NR, int BS, bool DA, bool B5>
+template <bool PROPOSE, int NS, int NR, int BS, bool DA, bool B5, bool PF>
 __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   pdl_trigger();
   // block -> (replica, first trial): only the blocks a replica needs
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
 
   // rows of the trial site, loaded before the decision of step k-1 is known
   RowWords<(NR > 0 ? NR : 1)> rw;
-  if constexpr (PROPOSE && !DA && NR > 0) {
+  if constexpr (PF && PROPOSE && !DA && NR > 0) {
     if (site >= 0) {
       if constexpr (B5) {
         if (sb_) bcc5_rows_load<1>(a, g, sX, sY, sZ, rw);
@@ -573,10 +573,13 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
       }
     }
   } else if (site >= 0) {
-    if constexpr (B5) {
+    if constexpr (B5 && PF) {
       if (sb_) bcc5_counts_from<1>(sX, rw, gm, cnt, t);
       else bcc5_counts_from<0>(sX, rw, gm, cnt, t);
-    } else if constexpr (NR > 0) {
+    } else if constexpr (B5) {
+      if (sb_) bcc5_counts_at<1>(a, g, sX, sY, sZ, gm, cnt, t);
+      else bcc5_counts_at<0>(a, g, sX, sY, sZ, gm, cnt, t);
+    } else if constexpr (NR > 0 && PF) {
       lattice_counts_from<NS, NR>(a, 2 * sX + sb_, sb_, rw, gm, cnt, t);
     } else {
       lattice_counts_at<NS, NR>(a, g, sX, sY, sZ, sb_, gm, cnt, t);
@@ -748,14 +751,17 @@ static void launch_step(K kern, dim3 grid, int block, cudaStream_t st, const Lat
   cudaLaunchKernelEx(&cfg, kern, a, j);
 }
 
+// PF: the trial's row words are loaded before the block barrier (fewer
+// dependent steps, more registers); the autotuner picks it or not
 template <int NS, int NR, int BS, bool B5>
 static void step_b5(const LatArgs& a, int j, bool propose, cudaStream_t st) {
   const dim3 g(a.n_blk);
   const bool pdl = j > 0;  // the first step of a chain is an ordinary launch
   constexpr bool DA_OK = NS == 5 && NR == 13;
-  if (!propose) launch_step(k_lattice_step<false, NS, NR, BS, false, B5>, g, BS, st, a, j, pdl);
-  else if (DA_OK && a.da) launch_step(k_lattice_step<true, NS, NR, BS, DA_OK, B5>, g, BS, st, a, j, pdl);
-  else launch_step(k_lattice_step<true, NS, NR, BS, false, B5>, g, BS, st, a, j, pdl);
+  if (!propose) launch_step(k_lattice_step<false, NS, NR, BS, false, B5, false>, g, BS, st, a, j, pdl);
+  else if (DA_OK && a.da) launch_step(k_lattice_step<true, NS, NR, BS, DA_OK, B5, false>, g, BS, st, a, j, pdl);
+  else if (a.prefetch) launch_step(k_lattice_step<true, NS, NR, BS, false, B5, true>, g, BS, st, a, j, pdl);
+  else launch_step(k_lattice_step<true, NS, NR, BS, false, B5, false>, g, BS, st, a, j, pdl);
 }
 
 template <int NS, int NR, int BS>

@@ -1094,7 +1094,14 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   l.lrep = dlr;
   l.dmax = dmax;
   l.R = R;
-  if (l.block == 0) l.block = 128;
+  if (l.block == 0) {
+    l.block = 128;
+    // prefetching helps while one launch fits in one wave of resident blocks
+    // (4 per SM at its register count); past that, occupancy matters more
+    long long trials = 0;
+    for (const LatGeom& g : c->h_geom) trials += g.dmax;
+    l.prefetch = trials <= 152LL * 4 * 128 ? 1 : 0;
+  }
   select_blk(c);
   c->fast = true;
   fill_args(c);
@@ -1312,14 +1319,17 @@ int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
     *best_block = MC_BLOCK;
     return VCSGC_OK;
   }
-  const int cand[3] = {64, 128, 256};
+  // candidates: block size x row prefetch (prefetching shortens the
+  // dependent chain of a step but costs registers, i.e. resident blocks)
+  const int cand[6][2] = {{64, 1}, {128, 1}, {256, 1}, {64, 0}, {128, 0}, {256, 0}};
   float best = 0.0f;
-  int bb = 128;
+  int bb = 128, bp = 1;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (int b : cand) {
-    c->lat.block = b;
+  for (const auto& cb : cand) {
+    c->lat.block = cb[0];
+    c->lat.prefetch = cb[1];
     select_blk(c);
     drop_graph(c);
     // one untimed step with the candidate, then the timed ones
@@ -1332,11 +1342,13 @@ int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
     CK(cudaEventElapsedTime(&ms, e0, e1));
     if (best == 0.0f || ms < best) {
       best = ms;
-      bb = b;
+      bb = cb[0];
+      bp = cb[1];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  c->lat.prefetch = bp;
   c->lat.block = bb;
   select_blk(c);
   drop_graph(c);

@@ -63,7 +63,8 @@ def test_autotune_keeps_the_chain_exact(V):
     best = b.autotune(steps=16)
     assert best in (64, 128, 256)
     b.sweep(2)
-    steps = 3 * (1 + 16) + 2 * 128
+    # six candidates (3 block sizes x row prefetch on/off), 1 + 16 steps each
+    steps = 6 * (1 + 16) + 2 * 128
     orcs = _oracles(tab, lats, types, steps)
     for q, o in enumerate(orcs):
         if o.obs()["near_ties"] == 0:
