@@ -1,10 +1,19 @@
-// alu_peaks.cu -- standalone throughput probe of the arithmetic units the
-// colour step and the MD force kernel lean on (not part of libvcsgc.so).
+// alu_peaks.cu -- standalone probe of the arithmetic throughputs and the
+// step latencies the colour step and the MD force kernel lean on (not part
+// of libvcsgc.so).
 //
-// Each kernel runs 8 SMs' worth of blocks per SM (blocks = 8 x SMs, 256
-// threads) with independent dependency chains per thread, timed with CUDA
-// events after one warm-up launch; the figures are per GPU.  Printed as one
-// JSON object.  Build and run: python -m paper_1012_5082_gb300.alu_peaks
+// Throughputs: each kernel runs 8 blocks of 256 threads per SM with
+// independent dependency chains per thread, timed with CUDA events after one
+// warm-up launch; the figures are per GPU.
+// Latencies: (1) a CUDA graph of 64 launches of a 504 x 128 kernel (the
+// launch shape of one colour step of 80^3 x 8 replicas) that waits for its
+// predecessor, reads one word and adds one atomic, with and without
+// programmatic dependent launch: the floor of one step as its own kernel;
+// (2) a cooperative kernel of 1-3 blocks per SM crossing 2000 grid-wide
+// barriers (arrival counter plus a generation word, spin bounded by an
+// iteration limit that sets an error flag): the floor of one step inside a
+// persistent kernel.  Printed as one JSON object.
+// Build and run: python -m paper_1012_5082_gb300.alu_peaks
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -114,6 +123,50 @@ __global__ void k_mma(float* out, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+__global__ void k_step_floor(int* acc, const int* src, int j) {
+  pdl_trigger();
+  pdl_wait();
+  __shared__ int sv;
+  if (threadIdx.x == 0) sv = *(volatile const int*)(acc + ((j + 3) & 3));
+  int v = __ldcg(src + (blockIdx.x * blockDim.x + threadIdx.x) % 4096);
+  __syncthreads();
+  v += sv;
+  if (threadIdx.x == 0 && v == 123456789) acc[8] = v;
+  if (threadIdx.x == 0) atomicAdd(acc + (j & 3), 1);
+}
+
+// grid barrier: bar[0] arrivals, bar[1] generation; a spin longer than
+// max_spin iterations sets *err and every block returns at the next check
+__global__ void k_barriers(unsigned* bar, int* err, int steps, long long max_spin) {
+  volatile unsigned* gen = bar + 1;
+  for (int s = 0; s < steps; ++s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned g0 = *gen;
+      __threadfence();
+      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        bar[0] = 0;
+        __threadfence();
+        atomicAdd(const_cast<unsigned*>(gen), 1u);
+      } else {
+        long long n = 0;
+        while (*gen == g0) {
+          if (++n > max_spin) {
+            atomicExch(err, 1);
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (*(volatile int*)err) return;
+  }
+}
+
 }  // namespace
 
 #define CHECK(x)                                                                        \
@@ -161,15 +214,88 @@ int main() {
   CHECK(cudaGetLastError());
   CHECK(cudaDeviceSynchronize());
   const double warps = nthr / 32.0;
+
+  // (1) chain of step-shaped launches in a graph
+  cudaStream_t st;
+  CHECK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  int* acc = nullptr;
+  CHECK(cudaMalloc(&acc, 16 * sizeof(int)));
+  CHECK(cudaMemset(acc, 0, 16 * sizeof(int)));
+  CHECK(cudaMemset(buf, 0, 4096 * sizeof(int)));
+  const int G = 64, reps = 50;
+  double chain_us[2];
+  for (int pdl = 0; pdl < 2; ++pdl) {
+    cudaGraph_t g;
+    cudaGraphExec_t ge;
+    CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int jj = 0; jj < G; ++jj) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(504);
+      cfg.blockDim = dim3(128);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = (pdl && jj > 0) ? 1 : 0;
+      cudaLaunchKernelEx(&cfg, k_step_floor, acc, (const int*)u, jj);
+    }
+    CHECK(cudaStreamEndCapture(st, &g));
+    CHECK(cudaGraphInstantiate(&ge, g, 0));
+    CHECK(cudaGraphLaunch(ge, st));
+    CHECK(cudaStreamSynchronize(st));
+    CHECK(cudaEventRecord(e0, st));
+    for (int q = 0; q < reps; ++q) CHECK(cudaGraphLaunch(ge, st));
+    CHECK(cudaEventRecord(e1, st));
+    CHECK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    chain_us[pdl] = 1e3 * ms / (reps * G);
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+  }
+
+  // (2) grid-wide barriers of a cooperative kernel
+  unsigned* bar = nullptr;
+  int* err = nullptr;
+  CHECK(cudaMalloc(&bar, 2 * sizeof(unsigned)));
+  CHECK(cudaMalloc(&err, sizeof(int)));
+  int per_sm = 0;
+  CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barriers, 128, 0));
+  double bar_us[3] = {0.0, 0.0, 0.0};
+  int bar_err = 0;
+  for (int bps = 1; bps <= 3 && bps <= per_sm; ++bps) {
+    CHECK(cudaMemset(bar, 0, 2 * sizeof(unsigned)));
+    CHECK(cudaMemset(err, 0, sizeof(int)));
+    int blocks_c = p.multiProcessorCount * bps, steps = 2000;
+    long long max_spin = 2000000;
+    void* args[] = {&bar, &err, &steps, &max_spin};
+    CHECK(cudaEventRecord(e0, st));
+    CHECK(cudaLaunchCooperativeKernel((void*)k_barriers, dim3(blocks_c), dim3(128), args, 0, st));
+    CHECK(cudaEventRecord(e1, st));
+    CHECK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    int herr = 0;
+    CHECK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+    bar_err |= herr;
+    bar_us[bps - 1] = 1e3 * ms / steps;
+  }
   std::printf(
       "{\"gpu\": \"%s\", \"sms\": %d, \"fp64_fma_tflops\": %.3f, \"fp32_fma_tflops\": %.3f, "
       "\"fp64_exp_g_per_s\": %.2f, \"fp32_expf_g_per_s\": %.1f, \"tanh_approx_g_per_s\": %.1f, "
       "\"int32_xor_add_tops\": %.2f, \"popc_t_per_s\": %.2f, \"mulhi_lo_pairs_t_per_s\": %.2f, "
-      "\"mma_sync_bf16_tflops\": %.1f}\n",
+      "\"mma_sync_bf16_tflops\": %.1f, \"step_chain_us\": %.3f, \"step_chain_pdl_us\": %.3f, "
+      "\"grid_barrier_us\": [%.3f, %.3f, %.3f], \"grid_barrier_timeout\": %d}\n",
       p.name, p.multiProcessorCount, 2.0 * 8 * it64 * nthr / t_fma64 * 1e-12,
       2.0 * 8 * it32 * nthr / t_fma32 * 1e-12, itx * nthr / t_exp64 * 1e-9, itf * nthr / t_exp32 * 1e-9,
       4.0 * itt * nthr / t_tanh * 1e-9, 16.0 * iti * nthr / t_int * 1e-12, 4.0 * iti * nthr / t_popc * 1e-12,
-      4.0 * iti * nthr / t_mul * 1e-12, 2.0 * 16 * 8 * 16 * 4.0 * itm * warps / t_mma * 1e-12);
+      4.0 * iti * nthr / t_mul * 1e-12, 2.0 * 16 * 8 * 16 * 4.0 * itm * warps / t_mma * 1e-12, chain_us[0],
+      chain_us[1], bar_us[0], bar_us[1], bar_us[2], bar_err);
   cudaFree(buf);
+  cudaFree(acc);
+  cudaFree(bar);
+  cudaFree(err);
+  cudaStreamDestroy(st);
   return 0;
 }
