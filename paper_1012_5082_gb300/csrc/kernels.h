@@ -26,6 +26,16 @@ void launch_to_cubic32(const Cubic* c, int n_int, Cubic32* out, cudaStream_t st)
 void launch_shell_tables(Tables tab, const int* h2, const int* z, int S, double a, double* out,
                          unsigned* err, cudaStream_t st, const Tables32* tab32 = nullptr);
 
+// shell multiplicities passed by value
+struct LatZ {
+  int z[8];
+};
+// Energy table of the rigid lattice with uniform rho0 (kernels_nbr.cu):
+// phi_AA, phi_AB, phi_BB at each shell radius, F_A(rho0), F_B(rho0), z_s
+// (3 S + 2 + S doubles)
+void launch_lattice_energy_table(Tables tab, const Tables32* tab32, const double* shell_tab, int S, LatZ z,
+                                 const double* rho, double* etab, unsigned* err, cudaStream_t st);
+
 // ---- neighbour lists (kernels_nbr.cu)
 // Rigid BCC: row i lists the sites at the K half-lattice offsets hoff (x,y,z).
 void launch_lattice_neighbours(int nx, int ny, int nz, const int3* hoff, int K, int* nbr, int* cnt,
@@ -137,6 +147,13 @@ struct LatArgs {
 void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);
 // true when the rows and masks of a equal the compile-time five-shell table
 bool lattice_rows_bcc5(const LatArgs& a);
+// B count and energy of replica r from its packed species (perfect lattice,
+// one density function; etab from launch_lattice_energy_table), written to
+// its state (n, energy) and to n_start[2 r + parity]; part holds >= 2 *
+// lattice_energy_blocks(n_sites) doubles of scratch
+int lattice_energy_blocks(long long n_sites);
+void launch_lattice_energy(const LatArgs& a, const LatGeom& g, int r, const double* etab, double* part,
+                           int parity, cudaStream_t st);
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 void launch_lattice_pack(const LatArgs& a, const LatGeom& g, const uint8_t* types_r, int r, cudaStream_t st);

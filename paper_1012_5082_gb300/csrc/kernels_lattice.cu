@@ -726,6 +726,97 @@ void launch_lattice_features(const LatArgs& a, long long max_sites, float* X, fl
   else k_lattice_features<false><<<grid, 128, 0, st>>>(a, X, Y);
 }
 
+// Per-site energy and B count of replica r, block partial sums: part[2 b]
+// = energy, part[2 b + 1] = count (exact as a double)
+constexpr int LAT_E_BLOCK = 256;
+template <bool B5>
+__global__ void __launch_bounds__(LAT_E_BLOCK) k_lattice_energy(LatArgs a, int r, const double* etab, double* part) {
+  const LatGeom g = a.geom[r];
+  const int S = a.n_shells;
+  const long long i = (long long)blockIdx.x * LAT_E_BLOCK + threadIdx.x;
+  double e = 0.0;
+  int nb = 0;
+  if (i < g.n_sites) {
+    int X, Y, Z, b, t;
+    decode_site(g, (int)i, X, Y, Z, b);
+    if constexpr (B5) {
+      int cnt[5];
+      if (b) bcc5_counts_at<1>(a, g, X, Y, Z, 0u, cnt, t);
+      else bcc5_counts_at<0>(a, g, X, Y, Z, 0u, cnt, t);
+      const double* pa = etab + (t ? 5 : 0);   // phi_{t,A}
+      const double* pb = etab + (t ? 10 : 5);  // phi_{t,B}
+#pragma unroll
+      for (int s = 0; s < 5; ++s) e += (etab[17 + s] - cnt[s]) * pa[s] + cnt[s] * pb[s];
+      e = fma(0.5, e, etab[15 + t]);
+    } else {
+      int cnt[LAT_MAX_SH];
+      lattice_counts_at<LAT_MAX_SH, 0>(a, g, X, Y, Z, b, 0u, cnt, t);
+      const double* pa = etab + (t ? S : 0);
+      const double* pb = etab + (t ? 2 * S : S);
+      for (int s = 0; s < S; ++s) e += (etab[3 * S + 2 + s] - cnt[s]) * pa[s] + cnt[s] * pb[s];
+      e = fma(0.5, e, etab[3 * S + t]);
+    }
+    nb = t;
+  }
+  __shared__ double s_e[LAT_E_BLOCK / 32];
+  __shared__ int s_n[LAT_E_BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  nb = __reduce_add_sync(0xffffffffu, nb);
+  if ((threadIdx.x & 31) == 0) {
+    s_e[threadIdx.x >> 5] = e;
+    s_n[threadIdx.x >> 5] = nb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double te = 0.0;
+    int tn = 0;
+    for (int w = 0; w < LAT_E_BLOCK / 32; ++w) {
+      te += s_e[w];
+      tn += s_n[w];
+    }
+    part[2 * blockIdx.x] = te;
+    part[2 * blockIdx.x + 1] = (double)tn;
+  }
+}
+
+// Sum of the block partials in a fixed order (one block), written to the
+// replica's state and to the B count at the start of the next step
+__global__ void k_lattice_energy_final(LatArgs a, int r, const double* part, int nblk, int parity) {
+  __shared__ double s_e[256], s_n[256];
+  double e = 0.0, n = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+    e += part[2 * q];
+    n += part[2 * q + 1];
+  }
+  s_e[threadIdx.x] = e;
+  s_n[threadIdx.x] = n;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s_e[threadIdx.x] += s_e[threadIdx.x + w];
+      s_n[threadIdx.x] += s_n[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const long long nb = (long long)s_n[0];
+    a.rs[r].n = nb;
+    a.rs[r].energy = s_e[0];
+    a.n_start[2 * r + parity] = nb;
+  }
+}
+
+int lattice_energy_blocks(long long n_sites) { return (int)((n_sites + LAT_E_BLOCK - 1) / LAT_E_BLOCK); }
+
+void launch_lattice_energy(const LatArgs& a, const LatGeom& g, int r, const double* etab, double* part,
+                           int parity, cudaStream_t st) {
+  const int nblk = lattice_energy_blocks(g.n_sites);
+  if (a.bcc5) k_lattice_energy<true><<<nblk, LAT_E_BLOCK, 0, st>>>(a, r, etab, part);
+  else k_lattice_energy<false><<<nblk, LAT_E_BLOCK, 0, st>>>(a, r, etab, part);
+  k_lattice_energy_final<<<1, 256, 0, st>>>(a, r, part, nblk, parity);
+}
+
 __global__ void k_to_float(const double* in, float* out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];

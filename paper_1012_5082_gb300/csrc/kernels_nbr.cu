@@ -85,6 +85,33 @@ __global__ void k_shell_tables(Tables tab, Tables32 tab32, int mixed, const int*
   out[0] = C;
 }
 
+// Energy table of the rigid lattice with one density function (uniform
+// rho0): etab[s], etab[S + s], etab[2S + s] = phi_AA, phi_AB, phi_BB at r_s
+// (r_s = shell_tab[1 + 2S + s]), etab[3S] = F_A(rho0), etab[3S + 1] =
+// F_B(rho0), etab[3S + 2 + s] = z_s.  Site energy: F_t(rho0) + 1/2 sum_s
+// [(z_s - b_s) phi_{tA}(r_s) + b_s phi_{tB}(r_s)].
+__global__ void k_lattice_energy_table(Tables tab, Tables32 tab32, int mixed, const double* shell_tab, int S,
+                                       LatZ z, const double* rho, double* etab, unsigned* err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const Tables32* t32 = mixed ? &tab32 : nullptr;
+  for (int s = 0; s < S; ++s) {
+    const double r = shell_tab[1 + 2 * S + s];
+    etab[s] = tab_val(tab, t32, 0, r, err);
+    etab[S + s] = tab_val(tab, t32, 1, r, err);
+    etab[2 * S + s] = tab_val(tab, t32, 2, r, err);
+    etab[3 * S + 2 + s] = (double)z.z[s];
+  }
+  etab[3 * S] = tab_val(tab, t32, 5, rho[0], err);
+  etab[3 * S + 1] = tab_val(tab, t32, 6, rho[0], err);
+}
+
+void launch_lattice_energy_table(Tables tab, const Tables32* tab32, const double* shell_tab, int S, LatZ z,
+                                 const double* rho, double* etab, unsigned* err, cudaStream_t st) {
+  Tables32 t{};
+  if (tab32) t = *tab32;
+  k_lattice_energy_table<<<1, 32, 0, st>>>(tab, t, tab32 ? 1 : 0, shell_tab, S, z, rho, etab, err);
+}
+
 void launch_shell_tables(Tables tab, const int* h2, const int* z, int S, double a, double* out,
                          unsigned* err, cudaStream_t st, const Tables32* tab32) {
   Tables32 t{};

@@ -101,6 +101,10 @@ struct Ctx {
   std::vector<int> offset_shell;
   // delayed acceptance: the context's copy of the surrogate's fragments
   MlpBuf sur{};
+  // fused form, perfect lattice: energy table and partial sums of the
+  // lattice energy kernel (species set from the host)
+  double* etab = nullptr;
+  double* epart = nullptr;
   // fused form: block tables for blocks of 64, 128, 256 threads
   int2* blk_tab[3] = {nullptr, nullptr, nullptr};
   int n_blk_tab[3] = {0, 0, 0};
@@ -1001,6 +1005,16 @@ static int lattice_shared(Ctx* c, int& unsupported) {
   for (int sh : c->offset_shell) zs[sh]++;
   c->sum_absG = 0.0;
   for (int s = 0; s < S; ++s) c->sum_absG += zs[s] * std::fabs(l.G[s]);
+  if (uni) {
+    // energy of a species array set from the host: shell pair values and
+    // F_A, F_B at the uniform density
+    LatZ z{};
+    for (int s = 0; s < S; ++s) z.z[s] = zs[s];
+    TRY(dalloc(c, &c->etab, 4 * S + 2));
+    launch_lattice_energy_table(c->mc.tab, c->mixed ? &c->mc.tab32 : nullptr, c->shell_tab, S, z, c->rho,
+                                c->etab, c->derr, c->st);
+    CK(cudaGetLastError());
+  }
   unsupported = 0;
   return VCSGC_OK;
 }
@@ -1062,6 +1076,11 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   TRY(dalloc(c, &l.n_start, (size_t)R * 2));
   TRY(dalloc(c, &l.pend, (size_t)slots));
   TRY(dalloc(c, &l.ctl, 1));
+  {
+    long long nb = 1;
+    for (const LatGeom& g : c->h_geom) nb = std::max(nb, (long long)lattice_energy_blocks(g.n_sites));
+    TRY(dalloc(c, &c->epart, (size_t)(2 * nb)));
+  }
   CK(cudaMemcpyAsync(dg, c->h_geom.data(), sizeof(LatGeom) * R, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(dlr, lr.data(), sizeof(LatRep) * R, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(l.bits, 0, sizeof(unsigned long long) * (words + 1), c->st));
@@ -1234,6 +1253,9 @@ static int batch_impl(Ctx* c, int32_t n_rep, const int32_t* cells, double a, con
   c->nx = s0->nx; c->ny = s0->ny; c->nz = s0->nz; c->a = a;
   c->N = s0->N;
   c->dF = s0->dF;
+  c->rho = s0->rho;
+  c->mc.tab = s0->mc.tab;
+  c->mc.tab32 = s0->mc.tab32;
   c->shell_tab = s0->shell_tab;
   c->mc.n_shells = s0->mc.n_shells;
   c->offsets = s0->offsets;
@@ -1455,13 +1477,35 @@ int vcsgc_get_types(void* ctx, int32_t r, uint8_t* out) {
   return check_device_error(c);
 }
 
+// every byte 0 or 1 (eight at a time)
+static bool species_ok(const uint8_t* in, long long n) {
+  long long i = 0;
+  for (; i + 8 <= n; i += 8) {
+    uint64_t w;
+    std::memcpy(&w, in + i, 8);
+    if (w & 0xFEFEFEFEFEFEFEFEull) return false;
+  }
+  for (; i < n; ++i)
+    if (in[i] > 1) return false;
+  return true;
+}
+
 int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !in || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   const long long Nr = c->rep_n[r];
-  for (long long i = 0; i < Nr; ++i)
-    if (in[i] > 1) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
+  if (!species_ok(in, Nr)) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
   TRY(flush(c));
+  if (c->fast && c->etab) {
+    // perfect lattice with one density function: rho does not change; the
+    // B count and the energy come from the packed species on the device
+    CK(cudaMemcpyAsync(c->rep_types[r], in, Nr, cudaMemcpyHostToDevice, c->st));
+    launch_lattice_pack(c->lat, c->h_geom[r], c->rep_types[r], r, c->st);
+    launch_lattice_energy(c->lat, c->h_geom[r], r, c->etab, c->epart, (int)(c->h_base & 1), c->st);
+    CK(cudaGetLastError());
+    c->forces_valid = false;
+    return check_device_error(c);
+  }
   CK(cudaMemcpyAsync(c->rep_types[r], in, Nr, cudaMemcpyHostToDevice, c->st));
   if (c->fast) {
     long long nb = 0;

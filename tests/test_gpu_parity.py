@@ -189,3 +189,31 @@ def test_invalid_arguments_are_reported(V):
     with pytest.raises(V.VcsgcError) as e:
         V.Context(lat, types, tab, -2.0, 1000.0, -5.0, schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2))
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_types_energy_and_count(V, precision):
+    """Species set from the host: B count exact and energy equal to the
+    oracle's full recomputation (1e-12 relative).  The mixed form evaluates
+    its tables in FP32: F(rho0) ~ -3.5 eV and the pair terms carry relative
+    errors of a few 2^-24 from the cubic's roundings, a systematic ~1e-6
+    eV/atom (the 128^3 benchmark measures 9.8e-7); the bound is 3e-6 eV/atom."""
+    lat, types, tab = c0_config()
+    g = V.Context(lat, types, tab, -2.0, 1000.0, 700.0, schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2),
+                  precision=precision)
+    g.sweep(2)
+    for seed, nb in ((71, 600), (72, 17), (73, 1999)):
+        t = I.random_types(lat.n, nb, seed=seed)
+        g.set_types(t)
+        o = O.System(lat, t, tab)
+        og = g.observables()
+        assert og["n_b"] == nb
+        e = o.energy_full()
+        tol = 1e-12 * abs(e) if precision == 0 else 3e-6 * lat.n
+        assert abs(og["energy"] - e) <= tol, (og["energy"], e)
+        assert np.array_equal(g.types(), t)
+    with pytest.raises(V.VcsgcError):
+        bad = t.copy()
+        bad[5] = 2
+        g.set_types(bad)
+    g.close()
