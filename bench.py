@@ -15,6 +15,7 @@ method does not shard: replicas only) and rank 0 reports the aggregate.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -498,25 +499,23 @@ def main():
             "trials_per_launch": trials_per_launch, "avg_launch_us": avg_ms * 1e3,
             "isolated_launch_us": (ms_prop + ms_comm) / n_prof * 1e3}
 
-    # end to end through the C ABI with host buffers: species up, one sweep,
-    # species and observables down, every step
-    pinned = torch.empty((N_PHI, lat.n), dtype=torch.uint8, pin_memory=True)
+    # end to end through the C ABI with host buffers: every replica's species
+    # up from pinned memory, one sweep, observables and species down, every step
+    pinned = torch.empty(N_PHI * lat.n, dtype=torch.uint8, pin_memory=True)
     host = pinned.numpy()
-    for r in range(N_PHI):
-        host[r] = ctx.types(r)
+    ctx.types_all(host)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for r in range(N_PHI):
-            ctx.set_types(host[r], r)
+        ctx.set_types_all(host)
         ctx.sweep(1)
-        obs = [ctx.observables(r) for r in range(N_PHI)]
-        for r in range(N_PHI):
-            host[r] = ctx.types(r)
+        obs = ctx.observables_all()
+        ctx.types_all(host)
     barrier()
     dt_e2e = time.perf_counter() - t0
     e2e = {"value": world * trials_per_step * args.steps / dt_e2e, "unit": "trial moves/s",
-           "h2d_bytes_per_step": N_PHI * lat.n, "d2h_bytes_per_step": N_PHI * lat.n + N_PHI * 160}
+           "h2d_bytes_per_step": N_PHI * lat.n,
+           "d2h_bytes_per_step": N_PHI * lat.n + N_PHI * ctypes.sizeof(V.Observables)}
 
     o0 = ctx.observables(0)
     ctx.close()

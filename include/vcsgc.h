@@ -232,11 +232,19 @@ int vcsgc_hybrid(void* ctx, int64_t n_cycles, int64_t n_md, int64_t n_mc);
 
 /* Observables of one replica (synchronises the stream). */
 int observables(void* ctx, int32_t replica, vcsgc_observables* out);
+/* Observables of every replica: out[R] (one synchronisation). */
+int vcsgc_observables_all(void* ctx, vcsgc_observables* out);
 
 /* Species of one replica: N bytes to/from host memory.  set_types
- * recomputes rho and the energy and keeps the counters. */
+ * recomputes rho and the energy and keeps the counters.  Errors:
+ * INVALID_ARG when a byte is neither 0 nor 1 (nothing is changed). */
 int vcsgc_get_types(void* ctx, int32_t replica, uint8_t* out);
 int vcsgc_set_types(void* ctx, int32_t replica, const uint8_t* in);
+/* Species of every replica at once: the replicas' arrays back to back
+ * (replica 0 first; sum of the replica sizes bytes), one transfer per
+ * replica and one synchronisation in all.  Same errors as above. */
+int vcsgc_get_types_all(void* ctx, uint8_t* out);
+int vcsgc_set_types_all(void* ctx, const uint8_t* in);
 /* Electron density rho_i of one replica, N doubles. */
 int vcsgc_get_rho(void* ctx, int32_t replica, double* out);
 /* Energy change of flipping each of sites[0..n) of one replica on its current

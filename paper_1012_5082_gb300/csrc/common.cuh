@@ -22,6 +22,7 @@ enum : unsigned {
   ERRF_NONFINITE = 2u,  // NaN/Inf energy difference or force
   ERRF_OVERFLOW = 4u,   // neighbour row longer than its capacity
   ERRF_TIMEOUT = 8u,    // bounded wait ran out
+  ERRF_SPECIES = 16u,   // a species byte set from the host is neither 0 nor 1
 };
 
 // ---------------------------------------------------------------- Philox

@@ -147,17 +147,27 @@ struct LatArgs {
 void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);
 // true when the rows and masks of a equal the compile-time five-shell table
 bool lattice_rows_bcc5(const LatArgs& a);
-// B count and energy of replica r from its packed species (perfect lattice,
-// one density function; etab from launch_lattice_energy_table), written to
-// its state (n, energy) and to n_start[2 r + parity]; part holds >= 2 *
-// lattice_energy_blocks(n_sites) doubles of scratch
-int lattice_energy_blocks(long long n_sites);
-void launch_lattice_energy(const LatArgs& a, const LatGeom& g, int r, const double* etab, double* part,
-                           int parity, cudaStream_t st);
+// B count and energy of replicas r0 .. r0 + nrep - 1 from their packed
+// species (perfect lattice, one density function; etab from
+// launch_lattice_energy_table), written to their states (n, energy) and to
+// n_start[2 r + parity]; part holds nrep * pstride * lattice_energy_width()
+// doubles of scratch, pstride >= lattice_energy_blocks(max_words), max_words
+// the largest replica's word count ny nz W
+int lattice_energy_blocks(long long max_words);
+int lattice_energy_width();
+void launch_lattice_energy(const LatArgs& a, int r0, int nrep, long long max_words, const double* etab,
+                           double* part, int pstride, int parity, cudaStream_t st);
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
-void launch_lattice_pack(const LatArgs& a, const LatGeom& g, const uint8_t* types_r, int r, cudaStream_t st);
-void launch_lattice_unpack(const LatArgs& a, const LatGeom& g, uint8_t* types_r, int r, cudaStream_t st);
+// species bytes (tptr[r], a device array of R pointers) <-> bit rows of
+// replicas r0 .. r0 + nrep - 1
+void launch_lattice_pack(const LatArgs& a, uint8_t* const* tptr, int r0, int nrep, long long max_words,
+                         cudaStream_t st);
+// sets ERRF_SPECIES in *err when a byte of t[0..n) is neither 0 nor 1; the
+// pack and lattice-energy kernels then write nothing
+void launch_species_check(const uint8_t* t, long long n, unsigned* err, cudaStream_t st);
+void launch_lattice_unpack(const LatArgs& a, uint8_t* const* tptr, int r0, int nrep, long long max_sites,
+                           cudaStream_t st);
 void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st);
 // Environment counts X[row][10] and exact targets Y[row] = E(i = B) - E(i = A)
 // of every site of every replica (row = site_off + site); no pending flips.

@@ -652,22 +652,54 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
 __global__ void k_lattice_advance(LatCtl* ctl, int n) { ctl->base_step += n; }
 
 // species bytes of replica r <-> its bit rows (pending bits cleared)
-__global__ void k_lattice_pack(LatArgs a, const uint8_t* types_r, int r) {
-  const LatGeom g = a.geom[r];
-  const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= (long long)g.ny * g.nz) return;
-  unsigned long long* w = a.bits + g.bits_off + row * g.W;
-  const uint8_t* t = types_r + row * 2 * g.nx;
-  for (int q = 0; q < g.W; ++q) w[q] = 0ull;
-  const int L = 2 * g.nx;
-  for (int p = 0; p < L + 2 * LAT_HALO; ++p) {
-    int H = p - LAT_HALO;
-    H = H < 0 ? H + L : (H >= L ? H - L : H);
-    if (t[H]) w[p >> 5] |= 1ull << (p & 31);
+// species bytes set from the host: any byte other than 0 or 1 sets
+// ERRF_SPECIES (16 bytes per thread)
+__global__ void k_species_check(const uint8_t* t, long long n, unsigned* err) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long i = 16 * q;
+  if (i >= n) return;
+  unsigned bad = 0u;
+  if (i + 16 <= n && ((uintptr_t)(t + i) & 15) == 0) {
+    const uint4 w = *reinterpret_cast<const uint4*>(t + i);
+    bad = (w.x | w.y | w.z | w.w) & 0xFEFEFEFEu;
+  } else {
+    for (long long k = i; k < n && k < i + 16; ++k) bad |= t[k] & 0xFEu;
   }
+  if (bad) atomicOr(err, ERRF_SPECIES);
 }
 
-__global__ void k_lattice_unpack(LatArgs a, uint8_t* types_r, int r) {
+void launch_species_check(const uint8_t* t, long long n, unsigned* err, cudaStream_t st) {
+  const long long threads = (n + 15) / 16;
+  if (threads > 0) k_species_check<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(t, n, err);
+}
+
+// one thread per 64-bit word of the rows: 32 species bits (halo included),
+// pending half zero; nothing is written after a failed species check.
+// Replica r0 + blockIdx.y, species bytes at tptr[r].
+__global__ void k_lattice_pack(LatArgs a, uint8_t* const* tptr, int r0) {
+  if (*(volatile unsigned*)a.err & ERRF_SPECIES) return;
+  const int r = r0 + blockIdx.y;
+  const LatGeom g = a.geom[r];
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)g.ny * g.nz * g.W) return;
+  const long long row = idx / g.W;
+  const int q = (int)(idx - row * g.W);
+  const uint8_t* t = tptr[r] + row * 2 * g.nx;
+  const int L = 2 * g.nx;
+  uint32_t bits = 0u;
+  for (int k = 0; k < 32; ++k) {
+    const int p = 32 * q + k;
+    if (p >= L + 2 * LAT_HALO) break;
+    int H = p - LAT_HALO;
+    H = H < 0 ? H + L : (H >= L ? H - L : H);
+    bits |= (uint32_t)(t[H] & 1u) << k;
+  }
+  a.bits[g.bits_off + idx] = (unsigned long long)bits;
+}
+
+__global__ void k_lattice_unpack(LatArgs a, uint8_t* const* tptr, int r0) {
+  const int r = r0 + blockIdx.y;
+  uint8_t* types_r = tptr[r];
   const LatGeom g = a.geom[r];
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.n_sites) return;
@@ -726,95 +758,117 @@ void launch_lattice_features(const LatArgs& a, long long max_sites, float* X, fl
   else k_lattice_features<false><<<grid, 128, 0, st>>>(a, X, Y);
 }
 
-// Per-site energy and B count of replica r, block partial sums: part[2 b]
-// = energy, part[2 b + 1] = count (exact as a double)
+// Energy and B count of replica r = r0 + blockIdx.y from its packed species.
+// With phi_ab(r_s) the pair values at the shell radii, G_s = phi_BB - 2
+// phi_AB + phi_AA and one uniform density rho0,
+//   E = N F_A + n_B (F_B - F_A) + 1/2 sum_s z_s [N phi_AA + 2 n_B (phi_AB - phi_AA)]
+//       + 1/2 sum_s G_s P_s,   P_s = sum over B sites i of b_s(i),
+// (expand phi_{t_i t_j} in t_i, t_j and sum over ordered neighbour pairs), so
+// only B sites are visited: one thread per 32-bit species word of the rows,
+// a loop over its set bits (halo bits excluded).  Block partial sums of
+// (P_1 .. P_S, n_B): part[r - r0][b][LAT_E_W], stride pstride blocks.
 constexpr int LAT_E_BLOCK = 256;
+constexpr int LAT_E_W = LAT_MAX_SH + 1;
 template <bool B5>
-__global__ void __launch_bounds__(LAT_E_BLOCK) k_lattice_energy(LatArgs a, int r, const double* etab, double* part) {
+__global__ void __launch_bounds__(LAT_E_BLOCK)
+    k_lattice_energy(LatArgs a, int r0, double* part, int pstride) {
+  if (*(volatile unsigned*)a.err & ERRF_SPECIES) return;
+  const int r = r0 + blockIdx.y;
+  part += (long long)LAT_E_W * pstride * blockIdx.y;
   const LatGeom g = a.geom[r];
-  const int S = a.n_shells;
-  const long long i = (long long)blockIdx.x * LAT_E_BLOCK + threadIdx.x;
-  double e = 0.0;
-  int nb = 0;
-  if (i < g.n_sites) {
-    int X, Y, Z, b, t;
-    decode_site(g, (int)i, X, Y, Z, b);
-    if constexpr (B5) {
-      int cnt[5];
-      if (b) bcc5_counts_at<1>(a, g, X, Y, Z, 0u, cnt, t);
-      else bcc5_counts_at<0>(a, g, X, Y, Z, 0u, cnt, t);
-      const double* pa = etab + (t ? 5 : 0);   // phi_{t,A}
-      const double* pb = etab + (t ? 10 : 5);  // phi_{t,B}
+  const long long nw = (long long)g.ny * g.nz * g.W;
+  if ((long long)blockIdx.x * LAT_E_BLOCK >= nw) return;
+  const long long idx = (long long)blockIdx.x * LAT_E_BLOCK + threadIdx.x;
+  int acc[LAT_E_W];
 #pragma unroll
-      for (int s = 0; s < 5; ++s) e += (etab[17 + s] - cnt[s]) * pa[s] + cnt[s] * pb[s];
-      e = fma(0.5, e, etab[15 + t]);
-    } else {
-      int cnt[LAT_MAX_SH];
-      lattice_counts_at<LAT_MAX_SH, 0>(a, g, X, Y, Z, b, 0u, cnt, t);
-      const double* pa = etab + (t ? S : 0);
-      const double* pb = etab + (t ? 2 * S : S);
-      for (int s = 0; s < S; ++s) e += (etab[3 * S + 2 + s] - cnt[s]) * pa[s] + cnt[s] * pb[s];
-      e = fma(0.5, e, etab[3 * S + t]);
+  for (int s = 0; s < LAT_E_W; ++s) acc[s] = 0;
+  if (idx < nw) {
+    const long long row = idx / g.W;
+    const int q = (int)(idx - row * g.W);
+    const int Y = (int)(row % g.ny), Z = (int)(row / g.ny);
+    uint32_t w = (uint32_t)a.bits[g.bits_off + idx];
+    // keep bits p = 32 q + k with LAT_HALO <= p < LAT_HALO + 2 nx
+    const int lo = LAT_HALO - 32 * q, hi = LAT_HALO + 2 * g.nx - 32 * q;
+    if (lo > 0) w &= lo >= 32 ? 0u : ~((1u << lo) - 1u);
+    if (hi < 32) w &= hi <= 0 ? 0u : ((1u << hi) - 1u);
+    while (w) {
+      const int k = __ffs(w) - 1;
+      w &= w - 1u;
+      const int H = 32 * q + k - LAT_HALO;
+      const int X = H >> 1, b = H & 1;
+      int t;
+      if constexpr (B5) {
+        int cnt[5];
+        if (b) bcc5_counts_at<1>(a, g, X, Y, Z, 0u, cnt, t);
+        else bcc5_counts_at<0>(a, g, X, Y, Z, 0u, cnt, t);
+#pragma unroll
+        for (int s = 0; s < 5; ++s) acc[s] += cnt[s];
+      } else {
+        int cnt[LAT_MAX_SH];
+        lattice_counts_at<LAT_MAX_SH, 0>(a, g, X, Y, Z, b, 0u, cnt, t);
+#pragma unroll
+        for (int s = 0; s < LAT_MAX_SH; ++s) acc[s] += cnt[s];
+      }
+      acc[LAT_MAX_SH] += 1;
     }
-    nb = t;
   }
-  __shared__ double s_e[LAT_E_BLOCK / 32];
-  __shared__ int s_n[LAT_E_BLOCK / 32];
+  __shared__ int s_acc[LAT_E_BLOCK / 32][LAT_E_W];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-  nb = __reduce_add_sync(0xffffffffu, nb);
+  for (int s = 0; s < LAT_E_W; ++s) acc[s] = __reduce_add_sync(0xffffffffu, acc[s]);
   if ((threadIdx.x & 31) == 0) {
-    s_e[threadIdx.x >> 5] = e;
-    s_n[threadIdx.x >> 5] = nb;
+#pragma unroll
+    for (int s = 0; s < LAT_E_W; ++s) s_acc[threadIdx.x >> 5][s] = acc[s];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double te = 0.0;
-    int tn = 0;
-    for (int w = 0; w < LAT_E_BLOCK / 32; ++w) {
-      te += s_e[w];
-      tn += s_n[w];
-    }
-    part[2 * blockIdx.x] = te;
-    part[2 * blockIdx.x + 1] = (double)tn;
+  if (threadIdx.x < LAT_E_W) {
+    long long tot = 0;
+    for (int w2 = 0; w2 < LAT_E_BLOCK / 32; ++w2) tot += s_acc[w2][threadIdx.x];
+    part[(long long)LAT_E_W * blockIdx.x + threadIdx.x] = (double)tot;
   }
 }
 
-// Sum of the block partials in a fixed order (one block), written to the
-// replica's state and to the B count at the start of the next step
-__global__ void k_lattice_energy_final(LatArgs a, int r, const double* part, int nblk, int parity) {
-  __shared__ double s_e[256], s_n[256];
-  double e = 0.0, n = 0.0;
-  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
-    e += part[2 * q];
-    n += part[2 * q + 1];
+// Sums of the block partials (one block per replica r0 + blockIdx.x), the
+// energy, written to the replica's state and to the B count at the start of
+// the next step.  etab: phi_AA, phi_AB, phi_BB per shell, F_A, F_B, z_s.
+__global__ void k_lattice_energy_final(LatArgs a, int r0, const double* etab, const double* part, int pstride,
+                                       int parity) {
+  if (*(volatile unsigned*)a.err & ERRF_SPECIES) return;
+  const int r = r0 + blockIdx.x;
+  part += (long long)LAT_E_W * pstride * blockIdx.x;
+  const LatGeom g = a.geom[r];
+  const int nblk = (int)((((long long)g.ny * g.nz * g.W) + LAT_E_BLOCK - 1) / LAT_E_BLOCK);
+  __shared__ double s_tot[LAT_E_W];
+  if (threadIdx.x < LAT_E_W) {
+    double t = 0.0;  // integer-valued: exact
+    for (int q = 0; q < nblk; ++q) t += part[(long long)LAT_E_W * q + threadIdx.x];
+    s_tot[threadIdx.x] = t;
   }
-  s_e[threadIdx.x] = e;
-  s_n[threadIdx.x] = n;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      s_e[threadIdx.x] += s_e[threadIdx.x + w];
-      s_n[threadIdx.x] += s_n[threadIdx.x + w];
-    }
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
-    const long long nb = (long long)s_n[0];
+    const int S = a.n_shells;
+    const double N = (double)g.n_sites, nB = s_tot[LAT_MAX_SH];
+    double pair = 0.0;
+    for (int s = 0; s < S; ++s) {
+      const double pAA = etab[s], pAB = etab[S + s], pBB = etab[2 * S + s], z = etab[3 * S + 2 + s];
+      pair += z * (N * pAA + 2.0 * nB * (pAB - pAA)) + (pBB - 2.0 * pAB + pAA) * s_tot[s];
+    }
+    const double e = N * etab[3 * S] + nB * (etab[3 * S + 1] - etab[3 * S]) + 0.5 * pair;
+    const long long nb = (long long)nB;
     a.rs[r].n = nb;
-    a.rs[r].energy = s_e[0];
+    a.rs[r].energy = e;
     a.n_start[2 * r + parity] = nb;
   }
 }
 
-int lattice_energy_blocks(long long n_sites) { return (int)((n_sites + LAT_E_BLOCK - 1) / LAT_E_BLOCK); }
+int lattice_energy_blocks(long long max_words) { return (int)((max_words + LAT_E_BLOCK - 1) / LAT_E_BLOCK); }
+int lattice_energy_width() { return LAT_E_W; }
 
-void launch_lattice_energy(const LatArgs& a, const LatGeom& g, int r, const double* etab, double* part,
-                           int parity, cudaStream_t st) {
-  const int nblk = lattice_energy_blocks(g.n_sites);
-  if (a.bcc5) k_lattice_energy<true><<<nblk, LAT_E_BLOCK, 0, st>>>(a, r, etab, part);
-  else k_lattice_energy<false><<<nblk, LAT_E_BLOCK, 0, st>>>(a, r, etab, part);
-  k_lattice_energy_final<<<1, 256, 0, st>>>(a, r, part, nblk, parity);
+void launch_lattice_energy(const LatArgs& a, int r0, int nrep, long long max_words, const double* etab,
+                           double* part, int pstride, int parity, cudaStream_t st) {
+  const dim3 grid(lattice_energy_blocks(max_words), nrep);
+  if (a.bcc5) k_lattice_energy<true><<<grid, LAT_E_BLOCK, 0, st>>>(a, r0, part, pstride);
+  else k_lattice_energy<false><<<grid, LAT_E_BLOCK, 0, st>>>(a, r0, part, pstride);
+  k_lattice_energy_final<<<nrep, 32, 0, st>>>(a, r0, etab, part, pstride, parity);
 }
 
 __global__ void k_to_float(const double* in, float* out, long long n) {
@@ -902,13 +956,14 @@ void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st) {
   k_lattice_advance<<<1, 1, 0, st>>>(a.ctl, n);
 }
 
-void launch_lattice_pack(const LatArgs& a, const LatGeom& g, const uint8_t* types_r, int r, cudaStream_t st) {
-  const long long rows = (long long)g.ny * g.nz;
-  k_lattice_pack<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(a, types_r, r);
+void launch_lattice_pack(const LatArgs& a, uint8_t* const* tptr, int r0, int nrep, long long max_words,
+                         cudaStream_t st) {
+  k_lattice_pack<<<dim3((unsigned)((max_words + 255) / 256), nrep), 256, 0, st>>>(a, tptr, r0);
 }
 
-void launch_lattice_unpack(const LatArgs& a, const LatGeom& g, uint8_t* types_r, int r, cudaStream_t st) {
-  k_lattice_unpack<<<(unsigned)((g.n_sites + 255) / 256), 256, 0, st>>>(a, types_r, r);
+void launch_lattice_unpack(const LatArgs& a, uint8_t* const* tptr, int r0, int nrep, long long max_sites,
+                           cudaStream_t st) {
+  k_lattice_unpack<<<dim3((unsigned)((max_sites + 255) / 256), nrep), 256, 0, st>>>(a, tptr, r0);
 }
 
 void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st) {

@@ -105,6 +105,9 @@ struct Ctx {
   // lattice energy kernel (species set from the host)
   double* etab = nullptr;
   double* epart = nullptr;
+  int epstride = 0;                // lattice-energy partials per replica
+  uint8_t** d_tptr = nullptr;      // device array of the replicas' species arrays
+  long long max_words = 0, max_sites = 0;
   // fused form: block tables for blocks of 64, 128, 256 threads
   int2* blk_tab[3] = {nullptr, nullptr, nullptr};
   int n_blk_tab[3] = {0, 0, 0};
@@ -161,6 +164,7 @@ int check_device_error(Ctx* c) {
   if (!e) return VCSGC_OK;
   CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
   CK(cudaStreamSynchronize(c->st));
+  if (e & ERRF_SPECIES) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
   if (e & ERRF_TIMEOUT) return fail(c, VCSGC_ERR_TIMEOUT, "a bounded device wait ran out");
   if (e & ERRF_OVERFLOW) return fail(c, VCSGC_ERR_OVERFLOW, "neighbour list capacity exceeded");
   if (e & ERRF_TABLE) return fail(c, VCSGC_ERR_TABLE_RANGE, "r or rho outside the EAM table grid");
@@ -540,8 +544,8 @@ int flush(Ctx* c) {
 int sync_bytes(Ctx* c, int r) {
   if (!c->fast) return VCSGC_OK;
   TRY(flush(c));
-  for (int q = 0; q < c->R; ++q)
-    if (r < 0 || q == r) launch_lattice_unpack(c->lat, c->h_geom[q], c->rep_types[q], q, c->st);
+  if (r < 0) launch_lattice_unpack(c->lat, c->d_tptr, 0, c->R, c->max_sites, c->st);
+  else launch_lattice_unpack(c->lat, c->d_tptr, r, 1, c->h_geom[r].n_sites, c->st);
   CK(cudaGetLastError());
   return VCSGC_OK;
 }
@@ -1076,11 +1080,15 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   TRY(dalloc(c, &l.n_start, (size_t)R * 2));
   TRY(dalloc(c, &l.pend, (size_t)slots));
   TRY(dalloc(c, &l.ctl, 1));
-  {
-    long long nb = 1;
-    for (const LatGeom& g : c->h_geom) nb = std::max(nb, (long long)lattice_energy_blocks(g.n_sites));
-    TRY(dalloc(c, &c->epart, (size_t)(2 * nb)));
+  c->max_words = c->max_sites = 0;
+  for (const LatGeom& g : c->h_geom) {
+    c->max_words = std::max(c->max_words, (long long)g.ny * g.nz * g.W);
+    c->max_sites = std::max(c->max_sites, g.n_sites);
   }
+  c->epstride = lattice_energy_blocks(c->max_words);
+  TRY(dalloc(c, &c->epart, (size_t)((long long)lattice_energy_width() * R * c->epstride)));
+  TRY(dalloc(c, &c->d_tptr, (size_t)R));
+  CK(cudaMemcpyAsync(c->d_tptr, c->rep_types.data(), sizeof(uint8_t*) * R, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(dg, c->h_geom.data(), sizeof(LatGeom) * R, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(dlr, lr.data(), sizeof(LatRep) * R, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(l.bits, 0, sizeof(unsigned long long) * (words + 1), c->st));
@@ -1124,7 +1132,7 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   select_blk(c);
   c->fast = true;
   fill_args(c);
-  for (int r = 0; r < R; ++r) launch_lattice_pack(l, c->h_geom[r], c->rep_types[r], r, c->st);
+  launch_lattice_pack(l, c->d_tptr, 0, R, c->max_words, c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   c->h_base = 0;
@@ -1434,14 +1442,7 @@ int vcsgc_hybrid(void* ctx, int64_t n_cycles, int64_t n_md, int64_t n_mc) {
   return check_device_error(c);
 }
 
-int observables(void* ctx, int32_t r, vcsgc_observables* o) {
-  Ctx* c = static_cast<Ctx*>(ctx);
-  if (!c || !o || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
-  TRY(flush(c));
-  TRY(check_device_error(c));
-  RepState s;
-  CK(cudaMemcpyAsync(&s, c->rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
+static void fill_observables(const Ctx* c, int r, const RepState& s, vcsgc_observables* o) {
   const RepParams& p = c->h_rp[r];
   std::memset(o, 0, sizeof(*o));
   const double Nr = (double)c->rep_n[r];
@@ -1466,6 +1467,28 @@ int observables(void* ctx, int32_t r, vcsgc_observables* o) {
   o->kappa_p = p.kappa_p;
   o->dmu0 = p.dmu0;
   o->stage1_accepts = s.s1_acc;
+}
+
+int observables(void* ctx, int32_t r, vcsgc_observables* o) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !o || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  TRY(flush(c));
+  TRY(check_device_error(c));
+  RepState s;
+  CK(cudaMemcpyAsync(&s, c->rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  fill_observables(c, r, s, o);
+  return VCSGC_OK;
+}
+
+int vcsgc_observables_all(void* ctx, vcsgc_observables* o) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !o) return VCSGC_ERR_INVALID_ARG;
+  TRY(flush(c));
+  std::vector<RepState> s(c->R);
+  CK(cudaMemcpyAsync(s.data(), c->rs, sizeof(RepState) * c->R, cudaMemcpyDeviceToHost, c->st));
+  TRY(check_device_error(c));
+  for (int r = 0; r < c->R; ++r) fill_observables(c, r, s[r], o + r);
   return VCSGC_OK;
 }
 
@@ -1477,40 +1500,64 @@ int vcsgc_get_types(void* ctx, int32_t r, uint8_t* out) {
   return check_device_error(c);
 }
 
-// every byte 0 or 1 (eight at a time)
+// every byte 0 or 1: an OR over 32-byte chunks, tested once at the end
 static bool species_ok(const uint8_t* in, long long n) {
+  uint64_t acc = 0;
   long long i = 0;
+  for (; i + 32 <= n; i += 32) {
+    uint64_t w[4];
+    std::memcpy(w, in + i, 32);
+    acc |= (w[0] | w[1]) | (w[2] | w[3]);
+  }
   for (; i + 8 <= n; i += 8) {
     uint64_t w;
     std::memcpy(&w, in + i, 8);
-    if (w & 0xFEFEFEFEFEFEFEFEull) return false;
+    acc |= w;
   }
-  for (; i < n; ++i)
-    if (in[i] > 1) return false;
-  return true;
+  uint8_t tail = 0;
+  for (; i < n; ++i) tail |= in[i];
+  return !(acc & 0xFEFEFEFEFEFEFEFEull) && !(tail & 0xFEu);
+}
+
+// after a device species check: on a bad byte the bits (and so the state)
+// were left unchanged; the species bytes are restored from them
+static int checked_species(Ctx* c) {
+  const int rc = check_device_error(c);
+  if (rc == VCSGC_ERR_INVALID_ARG) {
+    const std::string msg = c->err;
+    TRY(sync_bytes(c, -1));
+    TRY(check_device_error(c));
+    c->err = msg;
+  }
+  return rc;
 }
 
 int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !in || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   const long long Nr = c->rep_n[r];
-  if (!species_ok(in, Nr)) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
-  TRY(flush(c));
   if (c->fast && c->etab) {
     // perfect lattice with one density function: rho does not change; the
-    // B count and the energy come from the packed species on the device
+    // species are checked, packed, counted and summed on the device
+    TRY(flush(c));
+    const LatGeom& g = c->h_geom[r];
     CK(cudaMemcpyAsync(c->rep_types[r], in, Nr, cudaMemcpyHostToDevice, c->st));
-    launch_lattice_pack(c->lat, c->h_geom[r], c->rep_types[r], r, c->st);
-    launch_lattice_energy(c->lat, c->h_geom[r], r, c->etab, c->epart, (int)(c->h_base & 1), c->st);
+    launch_species_check(c->rep_types[r], Nr, c->derr, c->st);
+    launch_lattice_pack(c->lat, c->d_tptr, r, 1, (long long)g.ny * g.nz * g.W, c->st);
+    launch_lattice_energy(c->lat, r, 1, (long long)g.ny * g.nz * g.W, c->etab, c->epart, c->epstride,
+                          (int)(c->h_base & 1), c->st);
     CK(cudaGetLastError());
     c->forces_valid = false;
-    return check_device_error(c);
+    return checked_species(c);
   }
+  if (!species_ok(in, Nr)) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
+  TRY(flush(c));
   CK(cudaMemcpyAsync(c->rep_types[r], in, Nr, cudaMemcpyHostToDevice, c->st));
   if (c->fast) {
     long long nb = 0;
     for (long long i = 0; i < Nr; ++i) nb += in[i];
-    launch_lattice_pack(c->lat, c->h_geom[r], c->rep_types[r], r, c->st);
+    launch_lattice_pack(c->lat, c->d_tptr, r, 1, (long long)c->h_geom[r].ny * c->h_geom[r].nz * c->h_geom[r].W,
+                        c->st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(c->lat.n_start + 2 * r + (c->h_base & 1), &nb, sizeof(long long),
                        cudaMemcpyHostToDevice, c->st));
@@ -1534,6 +1581,69 @@ int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
   TRY(sync_state_from_types(c, r, in));
   c->forces_valid = false;
   return check_device_error(c);
+}
+
+int vcsgc_get_types_all(void* ctx, uint8_t* out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !out) return VCSGC_ERR_INVALID_ARG;
+  TRY(sync_bytes(c, -1));
+  long long off = 0;
+  bool contiguous = true;
+  for (int r = 0; r < c->R; ++r) {
+    if (c->rep_types[r] != c->rep_types[0] + off) contiguous = false;
+    off += c->rep_n[r];
+  }
+  if (contiguous) {
+    CK(cudaMemcpyAsync(out, c->rep_types[0], off, cudaMemcpyDeviceToHost, c->st));
+  } else {
+    off = 0;
+    for (int r = 0; r < c->R; ++r) {
+      CK(cudaMemcpyAsync(out + off, c->rep_types[r], c->rep_n[r], cudaMemcpyDeviceToHost, c->st));
+      off += c->rep_n[r];
+    }
+  }
+  return check_device_error(c);
+}
+
+int vcsgc_set_types_all(void* ctx, const uint8_t* in) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !in) return VCSGC_ERR_INVALID_ARG;
+  if (!(c->fast && c->etab)) {
+    long long total = 0;
+    for (int r = 0; r < c->R; ++r) total += c->rep_n[r];
+    if (!species_ok(in, total)) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
+    long long off = 0;
+    for (int r = 0; r < c->R; ++r) {
+      TRY(vcsgc_set_types(ctx, r, in + off));
+      off += c->rep_n[r];
+    }
+    return VCSGC_OK;
+  }
+  TRY(flush(c));
+  // one transfer and one check when the replicas' arrays are back to back
+  bool contiguous = true;
+  long long off = 0;
+  for (int r = 0; r < c->R; ++r) {
+    if (c->rep_types[r] != c->rep_types[0] + off) contiguous = false;
+    off += c->rep_n[r];
+  }
+  if (contiguous) {
+    CK(cudaMemcpyAsync(c->rep_types[0], in, off, cudaMemcpyHostToDevice, c->st));
+    launch_species_check(c->rep_types[0], off, c->derr, c->st);
+  } else {
+    off = 0;
+    for (int r = 0; r < c->R; ++r) {
+      CK(cudaMemcpyAsync(c->rep_types[r], in + off, c->rep_n[r], cudaMemcpyHostToDevice, c->st));
+      launch_species_check(c->rep_types[r], c->rep_n[r], c->derr, c->st);
+      off += c->rep_n[r];
+    }
+  }
+  launch_lattice_pack(c->lat, c->d_tptr, 0, c->R, c->max_words, c->st);
+  launch_lattice_energy(c->lat, 0, c->R, c->max_words, c->etab, c->epart, c->epstride, (int)(c->h_base & 1),
+                        c->st);
+  CK(cudaGetLastError());
+  c->forces_valid = false;
+  return checked_species(c);
 }
 
 int vcsgc_get_rho(void* ctx, int32_t r, double* out) {

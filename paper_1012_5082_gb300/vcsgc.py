@@ -70,7 +70,8 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_free", "vcsgc_profile_steps", "vcsgc_neighbour_list_noalloc", "vcsgc_batch_init",
            "vcsgc_autotune", "vcsgc_features", "vcsgc_mlp_create", "vcsgc_mlp_set_params",
            "vcsgc_mlp_get_params", "vcsgc_mlp_forward", "vcsgc_mlp_grad", "vcsgc_mlp_train",
-           "vcsgc_mlp_last_error", "vcsgc_mlp_free", "vcsgc_set_surrogate"]
+           "vcsgc_mlp_last_error", "vcsgc_mlp_free", "vcsgc_set_surrogate", "vcsgc_observables_all",
+           "vcsgc_get_types_all", "vcsgc_set_types_all"]
 
 
 def lib():
@@ -117,6 +118,9 @@ def lib():
             "vcsgc_mlp_last_error": (C.c_char_p, [P]),
             "vcsgc_mlp_free": (None, [P]),
             "vcsgc_set_surrogate": (I32, [P, P]),
+            "vcsgc_observables_all": (I32, [P, P]),
+            "vcsgc_get_types_all": (I32, [P, P]),
+            "vcsgc_set_types_all": (I32, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -420,6 +424,29 @@ class Context:
     def set_types(self, t, replica=0):
         t = np.ascontiguousarray(t, dtype=np.uint8)
         _check(lib().vcsgc_set_types(self.h, int(replica), _ptr(t)), self.h)
+
+    def _total_sites(self):
+        return int(sum(self.sizes)) if hasattr(self, "sizes") else self.n * self.n_replicas
+
+    def types_all(self, out=None):
+        """Every replica's species back to back (vcsgc_get_types_all); out: a
+        contiguous uint8 array of the total size (e.g. pinned), or None."""
+        if out is None:
+            out = np.zeros(self._total_sites(), dtype=np.uint8)
+        assert out.dtype == np.uint8 and out.flags.c_contiguous and out.size == self._total_sites()
+        _check(lib().vcsgc_get_types_all(self.h, _ptr(out)), self.h)
+        return out
+
+    def set_types_all(self, t):
+        t = np.ascontiguousarray(t, dtype=np.uint8)
+        assert t.size == self._total_sites()
+        _check(lib().vcsgc_set_types_all(self.h, _ptr(t)), self.h)
+
+    def observables_all(self):
+        R = self.n_replicas
+        arr = (Observables * R)()
+        _check(lib().vcsgc_observables_all(self.h, arr), self.h)
+        return [{f: getattr(o, f) for f, _ in Observables._fields_} for o in arr]
 
     def rho(self, replica=0):
         out = np.zeros(self.n, dtype=np.float64)

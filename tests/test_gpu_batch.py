@@ -83,3 +83,31 @@ def test_batch_set_types_and_delta_e(V):
     assert np.max(np.abs(b.delta_e(sites, 2) - np.array([o.delta_e(i) for i in sites]))) < 1e-11
     assert abs(b.observables(2)["energy"] - o.energy_full()) < 1e-9 * abs(o.energy_full())
     b.close()
+
+
+def test_all_replica_species_and_observables(V):
+    """The all-replica calls equal the per-replica ones: species back to back,
+    energies and counts against the oracle after set_types_all."""
+    tab, lats, types = _start()
+    b = V.Batch(CELLS, types, tab, PHI, 20.0, T, seed_r=np.array(SEEDS, np.uint64), c0=0.05)
+    b.sweep(2)
+    allt = b.types_all()
+    off = 0
+    for q, l in enumerate(lats):
+        assert np.array_equal(allt[off:off + l.n], b.types(q))
+        off += l.n
+    new = [I.random_types(l.n, l.n // 3 + q, seed=90 + q) for q, l in enumerate(lats)]
+    b.set_types_all(np.concatenate(new))
+    obs = b.observables_all()
+    for q, l in enumerate(lats):
+        o = O.System(l, new[q], tab)
+        assert obs[q] == b.observables(q)
+        assert obs[q]["n_b"] == int(new[q].sum())
+        assert abs(obs[q]["energy"] - o.energy_full()) <= 1e-12 * abs(o.energy_full())
+        assert np.array_equal(b.types(q), new[q])
+    bad = np.concatenate(new)
+    bad[3] = 7
+    with pytest.raises(V.VcsgcError):
+        b.set_types_all(bad)
+    assert np.array_equal(b.types_all(), np.concatenate(new))
+    b.close()
