@@ -88,6 +88,10 @@ struct LatCtl {
   long long base_step;          // step of the next launch with j = 0
 };
 
+// colours and global uniforms of a chain's steps (entry j + 1: step
+// base + j, j = -1 .. LAT_CTAB - 2), per replica
+constexpr int LAT_CTAB = 65;
+
 // geometry of one replica's rigid lattice in the bit-packed form
 struct LatGeom {
   int nx, ny, nz, W;            // cells per axis, 64-bit words per row
@@ -136,6 +140,8 @@ struct LatArgs {
   long long* n_start;           // [R][2]
   int* pend;                    // all replicas' pending slots
   LatCtl* ctl;
+  int* ctab;                    // [R][LAT_CTAB]
+  unsigned long long* ugtab;    // [R][LAT_CTAB] top 53 bits of the global uniform
   unsigned* err;
   // delayed acceptance (needs the 5-shell BCC neighbourhood): stage 1 tests
   // the surrogate's prediction, stage 2 the exact dE
@@ -157,7 +163,9 @@ int lattice_energy_blocks(long long max_words);
 int lattice_energy_width();
 void launch_lattice_energy(const LatArgs& a, int r0, int nrep, long long max_words, const double* etab,
                            double* part, int pstride, int parity, cudaStream_t st);
+// step base += n, then the colour table of the new base
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st);
+void launch_colour_table(const LatArgs& a, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 // species bytes (tptr[r], a device array of R pointers) <-> bit rows of
 // replicas r0 .. r0 + nrep - 1

@@ -172,15 +172,24 @@ template <int B>
 __device__ __forceinline__ void bcc5_rows_load(const LatArgs& a, const LatGeom& g, int X, int Y, int Z,
                                                RowWords<13>& rw) {
   const int q0 = LAT_HALO + 2 * X + B - 3;
+  // word offsets of the wrapped rows Y + dy and planes Z + dz (dy, dz in
+  // -2..2; the unrolled loop below uses only those its rows need)
+  int yo[5], zo[5];
+#pragma unroll
+  for (int d = -2; d <= 2; ++d) {
+    yo[d + 2] = wrap_add(Y, d, g.ny) * g.W;
+    zo[d + 2] = wrap_add(Z, d, g.nz) * g.ny * g.W;
+  }
+  const unsigned long long* base = a.bits + g.bits_off + (q0 >> 5);
 #pragma unroll
   for (int q = 0; q < 13; ++q) {
     const unsigned long long code = bcc5_row(B, q);
     const int dy = (int)((code >> 40) & 15) - 2, dz = (int)((code >> 44) & 15) - 2;
-    const unsigned long long* row = row_ptr(a, g, wrap_add(Y, dy, g.ny), wrap_add(Z, dz, g.nz));
-    rw.w0[q] = __ldcg(row + (q0 >> 5));
-    rw.w1[q] = __ldcg(row + (q0 >> 5) + 1);
+    const unsigned long long* row = base + zo[dz + 2] + yo[dy + 2];
+    rw.w0[q] = __ldcg(row);
+    rw.w1[q] = __ldcg(row + 1);
   }
-  rw.own = __ldcg(row_ptr(a, g, Y, Z) + ((LAT_HALO + 2 * X + B) >> 5));
+  rw.own = __ldcg(a.bits + g.bits_off + zo[2] + yo[2] + ((LAT_HALO + 2 * X + B) >> 5));
 }
 
 template <int B>
@@ -400,13 +409,20 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   __shared__ int s_g[2];  // [0] = G_{k-1}, [1] = near-tie of that decision
 
   // inputs that depend on no earlier launch: the global uniform of step k-1
-  // (thread 0), the colour, site and random word of trial d of step k
+  // (thread 0), the colour, site and random word of trial d of step k.
+  // Colours and global uniforms of the chain's steps come from the table
+  // the advance kernel filled (entry j + 1 for step base + j).
+  const bool tab = j < LAT_CTAB - 1;
+  const int* ctab = a.ctab + r * LAT_CTAB;
   uint64_t ug53 = 0;
-  if (threadIdx.x == 0 && kp >= 0) lat_colour(a, p.key, kp, &ug53);
+  if (threadIdx.x == 0 && kp >= 0) {
+    if (tab) ug53 = a.ugtab[r * LAT_CTAB + j];
+    else lat_colour(a, p.key, kp, &ug53);
+  }
   int site = -1, sX = 0, sY = 0, sZ = 0, sb_ = 0;
   uint4 w = make_uint4(0, 0, 0, 0);
   if (PROPOSE) {
-    const int c = lat_colour(a, p.key, k, nullptr);
+    const int c = tab ? ctab[j + 1] : lat_colour(a, p.key, k, nullptr);
     const int D = a.sublattice ? g.d : a.col_start[c + 1] - a.col_start[c];
     if (d < D) {
       w = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)((uint64_t)k >> 32), (uint32_t)d, TAG_TRIAL), p.key);
@@ -439,14 +455,39 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   }
   pdl_wait();
 
+  // loads of what step k-1 wrote, all issued before the block barrier: the
+  // pending slot this thread commits, and (second warp of the replica's
+  // first block) the replica state and step k-1's accumulator, staged in
+  // shared memory for the finalisation
+  int* const slot = a.pend + g.pend_off + d;
+  const int ps = d < g.dmax ? __ldcg(slot) : -1;
+  __shared__ RepState s_rs;
+  __shared__ StepAcc s_acc;
+  __shared__ long long s_np;
+  const bool fin_warp = bk.y == 0 && (threadIdx.x >> 5) == 1;
+  if (fin_warp) {
+    const int l = threadIdx.x & 31;
+    static_assert(sizeof(RepState) <= 128 && sizeof(StepAcc) <= 128, "one word per lane");
+    if (l < (int)(sizeof(RepState) / 4))
+      reinterpret_cast<uint32_t*>(&s_rs)[l] = __ldcg(reinterpret_cast<const uint32_t*>(a.rs + r) + l);
+    if (kp >= 0) {
+      if (l < (int)(sizeof(StepAcc) / 4))
+        reinterpret_cast<uint32_t*>(&s_acc)[l] =
+            __ldcg(reinterpret_cast<const uint32_t*>(a.acc + r * 3 + (int)(kp % 3)) + l);
+      if (l == 0) s_np = __ldcg(a.n_start + r * 2 + (int)(kp & 1));
+    }
+  }
+
   // 1. global decision of step k-1: one thread per block, FP64
   if (threadIdx.x == 0) {
     int G = 0, tie = 0;
     if (kp >= 0) {
-      const int naccp = *(volatile const int*)&a.acc[r * 3 + (int)(kp % 3)].nacc;
+      // dn and nacc of step k-1 in one 8-byte load, n at its start beside it
+      const unsigned long long dn_nacc =
+          __ldcg(reinterpret_cast<const unsigned long long*>(&a.acc[r * 3 + (int)(kp % 3)].dn));
+      const long long np = __ldcg(a.n_start + r * 2 + (int)(kp & 1));
+      const int dnp = (int)(uint32_t)dn_nacc, naccp = (int)(uint32_t)(dn_nacc >> 32);
       if (naccp > 0) {
-        const int dnp = *(volatile const int*)&a.acc[r * 3 + (int)(kp % 3)].dn;
-        const long long np = a.n_start[r * 2 + (int)(kp & 1)];
         const double Y = p.beta * p.kappa_p * (double)dnp * ((double)dnp + 2.0 * ((double)np - p.n0));
         G = metropolis(Y, ug53, &tie) ? 1 : 0;
       }
@@ -471,25 +512,19 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   const bool Gp = s_g[0] != 0;
   const uint32_t gm = Gp ? 0xFFFFFFFFu : 0u;
 
-  // 3. commit this thread's pending flip of step k-1
-  if (d < g.dmax) {
-    int* slot = a.pend + g.pend_off + d;
-    const int ps = *slot;
-    if (ps >= 0) {
-      // slot = row * 2048 + H (row = Z ny + Y, H = 2 X + b)
-      xor_copies(g.nx, a.bits + g.bits_off + (long long)(ps >> 11) * g.W, ps & 2047, Gp, true);
-      *slot = -1;
-    }
-  }
+  // 3. commit this thread's pending flip of step k-1 (slot = row * 2048 +
+  //    H, row = Z ny + Y, H = 2 X + b).  The slot itself is rewritten at the
+  //    end with this step's pending flip, if any.
+  if (ps >= 0) xor_copies(g.nx, a.bits + g.bits_off + (long long)(ps >> 11) * g.W, ps & 2047, Gp, true);
 
-  // 4. finalise step k-1 (second warp of block 0, off the first warp's
-  //    path) and clear the accumulator of step k+1; whole-struct accesses
-  if (bk.y == 0 && threadIdx.x == 32) {
-    RepState S = a.rs[r];
+  // 4. finalise step k-1 (second warp of the replica's first block, off the
+  //    first warp's path) and clear the accumulator of step k+1
+  if (fin_warp && threadIdx.x == 32) {
+    RepState S = s_rs;
     if (kp >= 0 && S.fin_step < kp) {
-      const StepAcc A = a.acc[r * 3 + (int)(kp % 3)];
-      const long long np = a.n_start[r * 2 + (int)(kp & 1)];
-      const int cp = lat_colour(a, p.key, kp, nullptr);
+      const StepAcc A = s_acc;
+      const long long np = s_np;
+      const int cp = tab ? ctab[j] : lat_colour(a, p.key, kp, nullptr);
       const int D = a.sublattice ? g.d : a.col_start[cp + 1] - a.col_start[cp];
       S.trials += D;
       S.local_acc += A.nacc;
@@ -529,7 +564,10 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
       for (int q = 0; q < NS; ++q) An->sb[q] = 0;
     }
   }
-  if (!PROPOSE) return;
+  if (!PROPOSE) {
+    if (ps >= 0) *slot = -1;
+    return;
+  }
 
   // 5. propose trial d of step k on the effective species
   int dn = 0, acc = 0, tie = 0, s1 = 0;
@@ -589,12 +627,14 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
   if (accepted) {
     const int H = 2 * sX + sb_;
     xor_copies(g.nx, row_ptr(a, g, sY, sZ), H, false, true);  // set pending
-    a.pend[g.pend_off + d] = (sZ * g.ny + sY) * 2048 + H;
+    *slot = (sZ * g.ny + sY) * 2048 + H;
     acc = 1;
     dn = t ? -1 : 1;
 #pragma unroll
     for (int q = 0; q < NS; ++q) sb[q] = t ? -cnt[q] : cnt[q];
     if (!a.df_uniform) sdf = t ? -a.dF[site] : a.dF[site];
+  } else if (ps >= 0) {
+    *slot = -1;
   }
   // reduction of dn, accepts, per-shell sums and ties (the paper's
   // allgather of dc_i); warps without an accept or a tie skip the shuffles
@@ -650,6 +690,23 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
 }
 
 __global__ void k_lattice_advance(LatCtl* ctl, int n) { ctl->base_step += n; }
+
+// colours and global uniforms of steps base - 1 .. base + LAT_CTAB - 2 of
+// every replica (one block per replica); entries for steps < 0 are zero
+__global__ void k_colour_table(LatArgs a) {
+  const int r = blockIdx.x, t = threadIdx.x;
+  if (t >= LAT_CTAB) return;
+  const long long k = a.ctl->base_step + t - 1;
+  int c = 0;
+  uint64_t ug = 0;
+  if (k >= 0) c = lat_colour(a, a.rp[r].key, k, &ug);
+  a.ctab[r * LAT_CTAB + t] = c;
+  a.ugtab[r * LAT_CTAB + t] = ug;
+}
+
+void launch_colour_table(const LatArgs& a, cudaStream_t st) {
+  k_colour_table<<<a.R, 96, 0, st>>>(a);
+}
 
 // species bytes of replica r <-> its bit rows (pending bits cleared)
 // species bytes set from the host: any byte other than 0 or 1 sets
@@ -954,6 +1011,7 @@ bool lattice_rows_bcc5(const LatArgs& a) {
 
 void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st) {
   k_lattice_advance<<<1, 1, 0, st>>>(a.ctl, n);
+  launch_colour_table(a, st);
 }
 
 void launch_lattice_pack(const LatArgs& a, uint8_t* const* tptr, int r0, int nrep, long long max_words,

@@ -1080,6 +1080,8 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   TRY(dalloc(c, &l.n_start, (size_t)R * 2));
   TRY(dalloc(c, &l.pend, (size_t)slots));
   TRY(dalloc(c, &l.ctl, 1));
+  TRY(dalloc(c, &l.ctab, (size_t)R * LAT_CTAB));
+  TRY(dalloc(c, &l.ugtab, (size_t)R * LAT_CTAB));
   c->max_words = c->max_sites = 0;
   for (const LatGeom& g : c->h_geom) {
     c->max_words = std::max(c->max_words, (long long)g.ny * g.nz * g.W);
@@ -1133,6 +1135,7 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   c->fast = true;
   fill_args(c);
   launch_lattice_pack(l, c->d_tptr, 0, R, c->max_words, c->st);
+  launch_colour_table(l, c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   c->h_base = 0;
