@@ -56,6 +56,9 @@ struct CellList {
 void launch_cell_neighbours(long long N, const double* x, const double* y, const double* z,
                             const double box[3], double rl, CellList cl, int K, int* nbr, int* cnt,
                             unsigned* err, cudaStream_t st);
+// half list: the entries j > i of each full row (same stride K)
+void launch_half_list(long long N, int K, const int* nbr, const int* cnt, int* nbr_h, int* cnt_h,
+                      cudaStream_t st);
 
 // ---- density, energy (kernels_nbr.cu)
 // rho_i of replica r (shared array when !per_rep) and, if dF != nullptr,
@@ -216,6 +219,9 @@ struct MdArgs {
   int K;
   const int* nbr;
   const int* nbr_cnt;
+  const int* nbr_h;      // half list (j > i, stride K) of the FP64 form, or null
+  const int* cnt_h;
+  int same_dens;         // f_A = f_B: one density table value serves both ends
   const uint8_t* types;
   double *x, *y, *z, *vx, *vy, *vz, *fx, *fy, *fz;
   double* rho;

@@ -51,6 +51,98 @@ __global__ void k_md_rho(MdArgs m) {
   m.dF[i] = spline_val_at(m.tab.sp[6], q, t) - spline_val_at(m.tab.sp[5], q, t);
 }
 
+// FP64 form on the half list (each pair once, j > i): rho_i and rho_j both
+// receive the pair's density (atomic adds into rho, zeroed before); with one
+// density function (same_dens) one table value serves both ends.
+__global__ void k_md_rho_half(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int* row = m.nbr_h + i * m.K;
+  const int cnt = m.cnt_h[i];
+  const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
+  const double rc2 = m.rc * m.rc;
+  const int ti = m.types[i];
+  double rho = 0.0;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = row[k];
+    const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+    const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+    const double dz = mimg(m.z[j] - zi, m.box[2], iz);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rc2) continue;
+    const double r = r2 * rsqrt_nr(r2);
+    const int tj = m.types[j];
+    double t;
+    const int q = spline_locate(m.tab.sp[3], r, t, m.err);
+    const double fj = spline_val_at(m.tab.sp[3 + tj], q, t);  // density of j at i
+    const double fi = m.same_dens ? fj : spline_val_at(m.tab.sp[3 + ti], q, t);
+    rho += fj;
+    atomicAdd(m.rho + j, fi);
+  }
+  atomicAdd(m.rho + i, rho);
+}
+
+// F'(rho_i) and F_B(rho_i) - F_A(rho_i) once rho is complete
+__global__ void k_md_embed(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const double rho = m.rho[i];
+  double t;
+  const int ti = m.types[i];
+  const int q = spline_locate(m.tab.sp[5 + ti], rho, t, m.err);
+  m.dFp[i] = spline_der_at(m.tab.sp[5 + ti], q, t);
+  m.dF[i] = spline_val_at(m.tab.sp[6], q, t) - spline_val_at(m.tab.sp[5], q, t);
+}
+
+// FP64 forces on the half list: F_i += g (x_j - x_i) / r, F_j -= the same,
+// g = phi'_{ti tj} + F'_i f'_{tj} + F'_j f'_{ti} (one density derivative
+// when same_dens); force arrays zeroed before
+__global__ void k_md_force_half(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int* row = m.nbr_h + i * m.K;
+  const int cnt = m.cnt_h[i];
+  const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  const int ti = m.types[i];
+  const double Fi = m.dFp[i];
+  const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
+  const double rc2 = m.rc * m.rc;
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = row[k];
+    const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+    const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+    const double dz = mimg(m.z[j] - zi, m.box[2], iz);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rc2) continue;
+    const double ir = rsqrt_nr(r2);
+    const int tj = m.types[j];
+    double t;
+    const int q = spline_locate(m.tab.sp[0], r2 * ir, t, m.err);
+    const double Fj = m.dFp[j];
+    double g;
+    if (m.same_dens) {
+      g = fma(Fi + Fj, spline_dval_at(m.tab.dsp[3], q, t), spline_dval_at(m.tab.dsp[ti + tj], q, t));
+    } else {
+      g = fma(Fj, spline_dval_at(m.tab.dsp[3 + ti], q, t),
+              fma(Fi, spline_dval_at(m.tab.dsp[3 + tj], q, t), spline_dval_at(m.tab.dsp[ti + tj], q, t)));
+    }
+    const double gr = g * ir;
+    const double gx = gr * dx, gy = gr * dy, gz = gr * dz;
+    fx += gx;
+    fy += gy;
+    fz += gz;
+    atomicAdd(m.fx + j, -gx);
+    atomicAdd(m.fy + j, -gy);
+    atomicAdd(m.fz + j, -gz);
+  }
+  if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(m.err, ERRF_NONFINITE);
+  atomicAdd(m.fx + i, fx);
+  atomicAdd(m.fy + i, fy);
+  atomicAdd(m.fz + i, fz);
+}
+
 template <bool MIXED>
 __global__ void k_md_force(MdArgs m) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -209,12 +301,27 @@ __global__ void __launch_bounds__(KE_BLOCK) k_kinetic(MdArgs m, double* part) {
 static unsigned grid_of(long long N) { return (unsigned)((N + 127) / 128); }
 
 void launch_md_rho(const MdArgs& m, cudaStream_t st) {
-  if (m.mixed) k_md_rho<true><<<grid_of(m.N), 128, 0, st>>>(m);
-  else k_md_rho<false><<<grid_of(m.N), 128, 0, st>>>(m);
+  if (m.mixed) {
+    k_md_rho<true><<<grid_of(m.N), 128, 0, st>>>(m);
+  } else if (m.nbr_h) {
+    cudaMemsetAsync(m.rho, 0, sizeof(double) * m.N, st);
+    k_md_rho_half<<<grid_of(m.N), 128, 0, st>>>(m);
+    k_md_embed<<<grid_of(m.N), 128, 0, st>>>(m);
+  } else {
+    k_md_rho<false><<<grid_of(m.N), 128, 0, st>>>(m);
+  }
 }
 void launch_md_force(const MdArgs& m, cudaStream_t st) {
-  if (m.mixed) k_md_force<true><<<grid_of(m.N), 128, 0, st>>>(m);
-  else k_md_force<false><<<grid_of(m.N), 128, 0, st>>>(m);
+  if (m.mixed) {
+    k_md_force<true><<<grid_of(m.N), 128, 0, st>>>(m);
+  } else if (m.nbr_h) {
+    cudaMemsetAsync(m.fx, 0, sizeof(double) * m.N, st);
+    cudaMemsetAsync(m.fy, 0, sizeof(double) * m.N, st);
+    cudaMemsetAsync(m.fz, 0, sizeof(double) * m.N, st);
+    k_md_force_half<<<grid_of(m.N), 128, 0, st>>>(m);
+  } else {
+    k_md_force<false><<<grid_of(m.N), 128, 0, st>>>(m);
+  }
 }
 void launch_md_first_half(const MdArgs& m, long long step, cudaStream_t st) {
   k_md_first_half<<<grid_of(m.N), 128, 0, st>>>(m, step);

@@ -284,6 +284,24 @@ void launch_cell_neighbours(long long N, const double* x, const double* y, const
                                 rlm * rlm, K, nbr, cnt, err);
 }
 
+__global__ void k_half_list(long long N, int K, const int* nbr, const int* cnt, int* nbr_h, int* cnt_h) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int* row = nbr + i * K;
+  int* out = nbr_h + i * K;
+  int m = 0;
+  for (int k = 0; k < cnt[i]; ++k) {
+    const int j = row[k];
+    if (j > i) out[m++] = j;
+  }
+  cnt_h[i] = m;
+}
+
+void launch_half_list(long long N, int K, const int* nbr, const int* cnt, int* nbr_h, int* cnt_h,
+                      cudaStream_t st) {
+  k_half_list<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(N, K, nbr, cnt, nbr_h, cnt_h);
+}
+
 // ------------------------------------------------------ density, energy
 __device__ __forceinline__ double pair_r(const McArgs& a, bool shell, int i, int k, int j, int s) {
   if (shell) return a.shell_tab[1 + 2 * a.n_shells + s];

@@ -52,6 +52,9 @@ struct Ctx {
   int* nbr = nullptr;
   int* nbr_cnt = nullptr;
   int K = 0;
+  int* nbr_h = nullptr;            // half list of the FP64 MD form
+  int* cnt_h = nullptr;
+  int K_h = 0;                     // row stride nbr_h was allocated for
   Cubic* coef[7] = {};
   Cubic* dcoef[7] = {};
   double* shell_tab = nullptr;
@@ -210,6 +213,9 @@ void fill_args(Ctx* c) {
   m.K = c->K;
   m.nbr = c->nbr;
   m.nbr_cnt = c->nbr_cnt;
+  m.nbr_h = c->K_h == c->K ? c->nbr_h : nullptr;
+  m.cnt_h = c->cnt_h;
+  m.same_dens = c->reembed ? 0 : 1;
   m.types = c->types;
   m.x = c->x; m.y = c->y; m.z = c->z;
   m.vx = c->vx; m.vy = c->vy; m.vz = c->vz;
@@ -277,7 +283,20 @@ int build_cell_list(Ctx* c) {
     unsigned e = 0;
     CK(cudaMemcpyAsync(&e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    if (!(e & ERRF_OVERFLOW)) return VCSGC_OK;
+    if (!(e & ERRF_OVERFLOW)) {
+      if (!c->mixed && c->R == 1) {
+        // half list for the FP64 MD passes (each pair once)
+        if (c->K_h != c->K) {
+          TRY(dalloc(c, &c->nbr_h, (size_t)c->N * c->K));
+          if (!c->cnt_h) TRY(dalloc(c, &c->cnt_h, c->N));
+          c->K_h = c->K;
+          fill_args(c);
+        }
+        launch_half_list(c->N, c->K, c->nbr, c->nbr_cnt, c->nbr_h, c->cnt_h, c->st);
+        CK(cudaGetLastError());
+      }
+      return VCSGC_OK;
+    }
     // grow the rows and rebuild
     const int K2 = ((c->K * 3 / 2) + 7) / 8 * 8;
     int* nb = nullptr;
