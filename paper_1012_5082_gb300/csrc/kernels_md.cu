@@ -51,6 +51,16 @@ __global__ void k_md_rho(MdArgs m) {
   m.dF[i] = spline_val_at(m.tab.sp[6], q, t) - spline_val_at(m.tab.sp[5], q, t);
 }
 
+// interval and offset of r on a table grid when 0 <= r < r_c <= the grid's
+// end is already known (no range test)
+__device__ __forceinline__ int locate_in(const Spline& s, double r, double& t) {
+  const double u = r * s.inv_h;
+  int j = (int)u;
+  j = j < s.n_int - 1 ? j : s.n_int - 1;
+  t = u - (double)j;
+  return j;
+}
+
 // FP64 form on the half list (each pair once, j > i): rho_i and rho_j both
 // receive the pair's density (atomic adds into rho, zeroed before); with one
 // density function (same_dens) one table value serves both ends.
@@ -74,7 +84,7 @@ __global__ void k_md_rho_half(MdArgs m) {
     const double r = r2 * rsqrt_nr(r2);
     const int tj = m.types[j];
     double t;
-    const int q = spline_locate(m.tab.sp[3], r, t, m.err);
+    const int q = locate_in(m.tab.sp[3], r, t);
     const double fj = spline_val_at(m.tab.sp[3 + tj], q, t);  // density of j at i
     const double fi = m.same_dens ? fj : spline_val_at(m.tab.sp[3 + ti], q, t);
     rho += fj;
@@ -119,7 +129,7 @@ __global__ void k_md_force_half(MdArgs m) {
     const double ir = rsqrt_nr(r2);
     const int tj = m.types[j];
     double t;
-    const int q = spline_locate(m.tab.sp[0], r2 * ir, t, m.err);
+    const int q = locate_in(m.tab.sp[0], r2 * ir, t);
     const double Fj = m.dFp[j];
     double g;
     if (m.same_dens) {
