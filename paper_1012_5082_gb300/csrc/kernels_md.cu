@@ -93,6 +93,82 @@ __global__ void k_md_rho_half(MdArgs m) {
   atomicAdd(m.rho + i, rho);
 }
 
+// mixed form on the half list: FP32 geometry and tables, FP64 sums
+__global__ void k_md_rho_half32(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int* row = m.nbr_h + i * m.K;
+  const int cnt = m.cnt_h[i];
+  const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  const float bx = (float)m.box[0], by = (float)m.box[1], bz = (float)m.box[2];
+  const float ix = (float)(1.0 / m.box[0]), iy = (float)(1.0 / m.box[1]), iz = (float)(1.0 / m.box[2]);
+  const float rc2 = (float)(m.rc * m.rc);
+  const int ti = m.types[i];
+  double rho = 0.0;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = row[k];
+    const float dx = mimg32(m.x[j], xi, bx, ix);
+    const float dy = mimg32(m.y[j], yi, by, iy);
+    const float dz = mimg32(m.z[j], zi, bz, iz);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rc2) continue;
+    const int tj = m.types[j];
+    float t;
+    const int q = spline32_locate(m.tab32.sp[3], sqrtf(r2), t, m.err);
+    const float fj = spline32_val_at(m.tab32.sp[3 + tj], q, t);
+    const float fi = m.same_dens ? fj : spline32_val_at(m.tab32.sp[3 + ti], q, t);
+    rho += (double)fj;
+    atomicAdd(m.rho + j, (double)fi);
+  }
+  atomicAdd(m.rho + i, rho);
+}
+
+__global__ void k_md_force_half32(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const int* row = m.nbr_h + i * m.K;
+  const int cnt = m.cnt_h[i];
+  const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  const int ti = m.types[i];
+  const float Fi = m.dFp32[i];
+  const float bx = (float)m.box[0], by = (float)m.box[1], bz = (float)m.box[2];
+  const float ix = (float)(1.0 / m.box[0]), iy = (float)(1.0 / m.box[1]), iz = (float)(1.0 / m.box[2]);
+  const float rc2 = (float)(m.rc * m.rc);
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = row[k];
+    const float dx = mimg32(m.x[j], xi, bx, ix);
+    const float dy = mimg32(m.y[j], yi, by, iy);
+    const float dz = mimg32(m.z[j], zi, bz, iz);
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= rc2) continue;
+    const float ir = rsqrtf(r2);
+    const int tj = m.types[j];
+    float t;
+    const int q = spline32_locate(m.tab32.sp[0], r2 * ir, t, m.err);
+    const float Fj = m.dFp32[j];
+    float g;
+    if (m.same_dens) {
+      g = fmaf(Fi + Fj, spline32_dval_at(m.tab32.dsp[3], q, t), spline32_dval_at(m.tab32.dsp[ti + tj], q, t));
+    } else {
+      g = fmaf(Fj, spline32_dval_at(m.tab32.dsp[3 + ti], q, t),
+               fmaf(Fi, spline32_dval_at(m.tab32.dsp[3 + tj], q, t), spline32_dval_at(m.tab32.dsp[ti + tj], q, t)));
+    }
+    const float gr = g * ir;
+    const double gx = (double)(gr * dx), gy = (double)(gr * dy), gz = (double)(gr * dz);
+    fx += gx;
+    fy += gy;
+    fz += gz;
+    atomicAdd(m.fx + j, -gx);
+    atomicAdd(m.fy + j, -gy);
+    atomicAdd(m.fz + j, -gz);
+  }
+  if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(m.err, ERRF_NONFINITE);
+  atomicAdd(m.fx + i, fx);
+  atomicAdd(m.fy + i, fy);
+  atomicAdd(m.fz + i, fz);
+}
+
 // F'(rho_i) and F_B(rho_i) - F_A(rho_i) once rho is complete
 __global__ void k_md_embed(MdArgs m) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -103,6 +179,7 @@ __global__ void k_md_embed(MdArgs m) {
   const int q = spline_locate(m.tab.sp[5 + ti], rho, t, m.err);
   m.dFp[i] = spline_der_at(m.tab.sp[5 + ti], q, t);
   m.dF[i] = spline_val_at(m.tab.sp[6], q, t) - spline_val_at(m.tab.sp[5], q, t);
+  if (m.mixed) m.dFp32[i] = (float)m.dFp[i];
 }
 
 // FP64 forces on the half list: F_i += g (x_j - x_i) / r, F_j -= the same,
@@ -311,24 +388,26 @@ __global__ void __launch_bounds__(KE_BLOCK) k_kinetic(MdArgs m, double* part) {
 static unsigned grid_of(long long N) { return (unsigned)((N + 127) / 128); }
 
 void launch_md_rho(const MdArgs& m, cudaStream_t st) {
-  if (m.mixed) {
-    k_md_rho<true><<<grid_of(m.N), 128, 0, st>>>(m);
-  } else if (m.nbr_h) {
+  if (m.nbr_h) {
     cudaMemsetAsync(m.rho, 0, sizeof(double) * m.N, st);
-    k_md_rho_half<<<grid_of(m.N), 128, 0, st>>>(m);
+    if (m.mixed) k_md_rho_half32<<<grid_of(m.N), 128, 0, st>>>(m);
+    else k_md_rho_half<<<grid_of(m.N), 128, 0, st>>>(m);
     k_md_embed<<<grid_of(m.N), 128, 0, st>>>(m);
+  } else if (m.mixed) {
+    k_md_rho<true><<<grid_of(m.N), 128, 0, st>>>(m);
   } else {
     k_md_rho<false><<<grid_of(m.N), 128, 0, st>>>(m);
   }
 }
 void launch_md_force(const MdArgs& m, cudaStream_t st) {
-  if (m.mixed) {
-    k_md_force<true><<<grid_of(m.N), 128, 0, st>>>(m);
-  } else if (m.nbr_h) {
+  if (m.nbr_h) {
     cudaMemsetAsync(m.fx, 0, sizeof(double) * m.N, st);
     cudaMemsetAsync(m.fy, 0, sizeof(double) * m.N, st);
     cudaMemsetAsync(m.fz, 0, sizeof(double) * m.N, st);
-    k_md_force_half<<<grid_of(m.N), 128, 0, st>>>(m);
+    if (m.mixed) k_md_force_half32<<<grid_of(m.N), 128, 0, st>>>(m);
+    else k_md_force_half<<<grid_of(m.N), 128, 0, st>>>(m);
+  } else if (m.mixed) {
+    k_md_force<true><<<grid_of(m.N), 128, 0, st>>>(m);
   } else {
     k_md_force<false><<<grid_of(m.N), 128, 0, st>>>(m);
   }

@@ -284,8 +284,8 @@ int build_cell_list(Ctx* c) {
     CK(cudaMemcpyAsync(&e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     if (!(e & ERRF_OVERFLOW)) {
-      if (!c->mixed && c->R == 1) {
-        // half list for the FP64 MD passes (each pair once)
+      if (c->R == 1) {
+        // half list for the MD passes (each pair once)
         if (c->K_h != c->K) {
           TRY(dalloc(c, &c->nbr_h, (size_t)c->N * c->K));
           if (!c->cnt_h) TRY(dalloc(c, &c->cnt_h, c->N));
