@@ -187,19 +187,43 @@ __device__ __forceinline__ float mimg32(double xj, double xi, float L, float iL)
 // 10^5) fall through to the FP64 exp.  For X > 80 the FP64 p is below
 // 2^-53 <= u whenever u53 >= 1, so such moves are rejected without exp.
 // *tie is set when |u - p| <= 1e-9 p, where CPU and GPU exp may disagree.
+// u53 as a float from two 32-bit conversions and one FMA (a 64-bit integer
+// conversion would occupy the slow FP64 pipe): within 2^-23 relative
+__device__ __forceinline__ float u53_float(uint64_t u53) {
+  return fmaf(__uint2float_rn((uint32_t)(u53 >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)u53));
+}
+
+// u >= 1 - 1e-9 (the near-tie test at X = 0) on the integer u53: the FP64
+// value nearest 1 - 1e-9 times 2^53 is an integer, computed at compile time
+constexpr uint64_t U53_NEAR_ONE = (uint64_t)((1.0 - 1e-9) * 9007199254740992.0);
+
+// FP32 screen of u < min{1, exp(-X)} given x32 with |x32 - X| <= dx:
+// 1 accept, 0 reject, -1 undecided (decide in FP64)
+__device__ __forceinline__ int screen32(float x32, float dx, uint64_t u53) {
+  if (x32 <= -2.0f * dx) return 1;
+  if (u53 == 0) return -1;
+  if (x32 >= 80.0f + dx) return 0;
+  const float pf = expf(-x32) * 9007199254740992.0f;  // p * 2^53
+  const float uf = u53_float(u53);
+  const float m = dx + 9.5367431640625e-07f;          // + 2^-20 (expf, products)
+  if (uf * (1.0f + 2.384185791015625e-07f) < pf * (1.0f - m)) return 1;
+  if (uf * (1.0f - 2.384185791015625e-07f) > pf * (1.0f + m)) return 0;
+  return -1;
+}
+
 __device__ __forceinline__ bool metropolis(double X, uint64_t u53, int* tie) {
   if (X <= 0.0) {
-    if (X > -1e-9 && (double)u53 * 0x1p-53 >= 1.0 - 1e-9) *tie = 1;
+    if (X > -1e-9 && u53 >= U53_NEAR_ONE) *tie = 1;
     return true;
   }
   if (u53 != 0) {
     if (X > 80.0) return false;
     const float xf = (float)X;
     const float pf = expf(-xf) * 9007199254740992.0f;  // p * 2^53
-    const float uf = (float)u53;
+    const float uf = u53_float(u53);
     const float m = 9.5367431640625e-07f + xf * 2.384185791015625e-07f;  // 2^-20 + X 2^-22
-    if (uf * (1.0f + 1.1920929e-07f) < pf * (1.0f - m)) return true;
-    if (uf * (1.0f - 1.1920929e-07f) > pf * (1.0f + m)) return false;
+    if (uf * (1.0f + 2.384185791015625e-07f) < pf * (1.0f - m)) return true;
+    if (uf * (1.0f - 2.384185791015625e-07f) > pf * (1.0f + m)) return false;
   }
   const double p = exp(-X);
   const double u = (double)u53 * 0x1p-53;

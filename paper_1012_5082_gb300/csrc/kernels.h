@@ -84,7 +84,9 @@ struct LatRep {
   float cpd32;   // C + dmu0 (eV)
   float beta32;  // 1/(kB T)
   float dx;      // absolute bound on |X32 - X| from the rounding of the inputs and sums
-  float pad;
+  float bk32;    // beta kappa_p (global stage)
+  float n0_32;   // N c0
+  float pad[3];
 };
 
 struct LatCtl {

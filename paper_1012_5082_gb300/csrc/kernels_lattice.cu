@@ -348,31 +348,34 @@ __device__ __forceinline__ bool lattice_accept(const LatArgs& a, const LatRep& l
   const float x32 = (t ? -lr.beta32 : lr.beta32) * s32;
   if (!isfinite(x32)) atomicOr(a.err, ERRF_NONFINITE);
   const float dx = lr.dx + fabsf(x32) * 4.76837158203125e-07f;  // + |X| 2^-21
-  bool decided = false, acc = false;
-  if (x32 <= -2.0f * dx) {
-    decided = true;
-    acc = true;
-  } else if (u53 != 0) {
-    if (x32 >= 80.0f + dx) {
-      decided = true;
-    } else {
-      const float pf = expf(-x32) * 9007199254740992.0f;  // p * 2^53
-      const float uf = (float)u53;
-      const float m = dx + 9.5367431640625e-07f;          // + 2^-20 (expf, products)
-      if (uf * (1.0f + 1.1920929e-07f) < pf * (1.0f - m)) {
-        decided = true;
-        acc = true;
-      } else if (uf * (1.0f - 1.1920929e-07f) > pf * (1.0f + m)) {
-        decided = true;
-      }
-    }
+  const int dec = screen32(x32, dx, u53);
+  if (dec >= 0) return dec != 0;
+  const double de = lattice_de64<NS>(a, cnt, i, t);
+  const double sg = t ? -1.0 : 1.0;
+  return metropolis(p.beta * fma(sg, p.dmu0, de), u53, tie);
+}
+
+// Global decision of a step with dn != 0 accepted locally out of n at its
+// start: u_g < min{1, exp(-Y)}, Y = beta kappa_p dn (dn + 2 (n - n0))
+// (Eq. trans_vcsgc_par2), identical to the FP64 decision: Y is formed in FP32
+// with a bound on its rounding (beta kappa_p and n0 rounded to float, n <
+// 2^24 exact, two products and two sums), FP64 only when the screen cannot
+// settle it or |Y| is tiny.
+__device__ __forceinline__ bool global_accept(const LatRep& lr, const RepParams& p, int dn, long long n,
+                                              uint64_t ug53, int* tie) {
+  if (dn == 0) {
+    if (ug53 >= U53_NEAR_ONE) *tie = 1;
+    return true;
   }
-  if (!decided) {
-    const double de = lattice_de64<NS>(a, cnt, i, t);
-    const double sg = t ? -1.0 : 1.0;
-    acc = metropolis(p.beta * fma(sg, p.dmu0, de), u53, tie);
+  const float fdn = (float)dn, diff = (float)n - lr.n0_32;
+  const float y32 = lr.bk32 * fdn * fmaf(2.0f, diff, fdn);
+  const float dy = fabsf(lr.bk32 * fdn) * (fabsf(fdn) + 2.0f * ((float)n + lr.n0_32)) * 4.76837158203125e-07f;
+  if (fabsf(y32) > 1e-6f) {
+    const int dec = screen32(y32, dy, ug53);
+    if (dec >= 0) return dec != 0;
   }
-  return acc;
+  const double Y = p.beta * p.kappa_p * (double)dn * ((double)dn + 2.0 * ((double)n - p.n0));
+  return metropolis(Y, ug53, tie);
 }
 
 __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long step, uint64_t* ug53) {
@@ -487,10 +490,7 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
           __ldcg(reinterpret_cast<const unsigned long long*>(&a.acc[r * 3 + (int)(kp % 3)].dn));
       const long long np = __ldcg(a.n_start + r * 2 + (int)(kp & 1));
       const int dnp = (int)(uint32_t)dn_nacc, naccp = (int)(uint32_t)(dn_nacc >> 32);
-      if (naccp > 0) {
-        const double Y = p.beta * p.kappa_p * (double)dnp * ((double)dnp + 2.0 * ((double)np - p.n0));
-        G = metropolis(Y, ug53, &tie) ? 1 : 0;
-      }
+      if (naccp > 0) G = global_accept(a.lrep[r], p, dnp, np, ug53, &tie) ? 1 : 0;
     }
     s_g[0] = G;
     s_g[1] = tie;

@@ -1053,7 +1053,9 @@ static LatRep lattice_rep(const Ctx* c, const RepParams& p) {
   lr.beta32 = (float)p.beta;
   // (2 S + 3) roundings of at most 2^-24 M each, times beta, four-fold margin
   lr.dx = (float)(4.0 * p.beta * (2 * S + 3) * std::ldexp(M, -24));
-  lr.pad = 0.0f;
+  lr.bk32 = (float)(p.beta * p.kappa_p);
+  lr.n0_32 = (float)p.n0;
+  lr.pad[0] = lr.pad[1] = lr.pad[2] = 0.0f;
   return lr;
 }
 
