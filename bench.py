@@ -489,7 +489,8 @@ def main():
     # roofline of the dominant kernel: the fused colour step (one launch per
     # colour step; state resident in L2, so ALU work and latency bound it).
     # Its average duration is the timed region over its launches there (the
-    # graph's other node, one step-counter update per 64 launches, is ~0.1%).
+    # graph's other nodes, the step-base advance and the colour table of the
+    # next 64 steps, add ~3 us per 64 launches, ~1%).
     avg_ms = ms_max / (args.steps * spw)
     n_prof = 2 * spw
     ms_prop, ms_comm = ctx.profile_steps(n_prof)
@@ -533,7 +534,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict({"parallelism": f"replicas x{world}"}),
-            "e2e": e2e, "gpu_launches": spw * args.steps + (spw * args.steps) // 64, "roofline": roof,
+            "e2e": e2e, "gpu_launches": spw * args.steps + 2 * ((spw * args.steps) // 64), "roofline": roof,
             "clocks": clk.summary(),
             "acceptance": {"local": o0["acc_local"], "global": o0["acc_global"], "c": o0["c"]}}
     if not args.no_md:
