@@ -346,8 +346,9 @@ int vcsgc_mlp_forward(void* mlp, const float* d_X, int64_t n, float* d_out);
 /* Gradient of the mean squared error (1/n) sum (g - y)^2 over all n rows
  * (DEVICE d_X[n][10], d_Y[n]): HOST grad[VCSGC_MLP_NPARAM] and *loss. */
 int vcsgc_mlp_grad(void* mlp, const float* d_X, const float* d_Y, int64_t n, float* grad, double* loss);
-/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr)
- * on minibatches of `batch` rows drawn with replacement from the n rows
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8; learning rate lr
+ * decaying by a half cosine to lr / 100 over the call's steps) on
+ * minibatches of `batch` rows drawn with replacement from the n rows
  * (Philox keyed by seed, counter = Adam step).  loss_hist (HOST, `steps`
  * entries, or NULL) receives each minibatch's mean squared error before its
  * update.  Runs as a CUDA graph of 32 steps on the surrogate's stream. */

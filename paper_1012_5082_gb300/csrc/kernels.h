@@ -206,8 +206,10 @@ void launch_mlp_backward(const MlpBuf& b, const float* X, const float* Y, long l
 // buffers of a surrogate object made by vcsgc_mlp_create (false if null)
 bool mlp_object_buffers(void* mlp, MlpBuf* out);
 cudaStream_t mlp_object_stream(void* mlp);
-void launch_mlp_adam_pack(float* p, float* m, float* v, float* grad, float lr, long long* ctr, const MlpBuf& b,
-                          cudaStream_t st);
+// one Adam step (learning rate lr decayed by a half cosine to lr / 100 over
+// `total` steps counted from ctr[1]; no decay when total <= 1)
+void launch_mlp_adam_pack(float* p, float* m, float* v, float* grad, float lr, long long total, long long* ctr,
+                          const MlpBuf& b, cudaStream_t st);
 
 // ---- colour step (kernels_mc.cu)
 // phase 0: propose + commit; 1: propose only; 2: commit only

@@ -296,14 +296,20 @@ __global__ void k_mlp_pack(const float* p, uint2* w1f, uint2* w2f, uint2* w2tf, 
   pack_block(p, w1f, w2f, w2tf, vec);
 }
 
-// Adam (Kingma and Ba) on the FP32 parameters with step t = *ctr + 1; the
-// gradient is cleared for the next step, the fragments re-packed and the
-// counter advanced.
+// Adam (Kingma and Ba) on the FP32 parameters with step t = ctr[0] + 1 and
+// a learning rate decaying from lr to lr / 100 by a half cosine over the
+// `total` steps of the run that started at step ctr[1]; the gradient is
+// cleared for the next step, the fragments re-packed and the counter
+// advanced.
 __global__ void __launch_bounds__(1024) k_mlp_adam_pack(float* p, float* m, float* v, float* grad, float lr,
-                                                        long long* ctr, uint2* w1f, uint2* w2f, uint2* w2tf,
-                                                        float* vec) {
+                                                        long long total, long long* ctr, uint2* w1f, uint2* w2f,
+                                                        uint2* w2tf, float* vec) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float t = (float)(*ctr + 1);
+  const float t = (float)(ctr[0] + 1);
+  if (total > 1) {
+    const float f = (float)(ctr[0] - ctr[1]) / (float)(total - 1);
+    lr *= 0.01f + 0.495f * (1.0f + cospif(fminf(f, 1.0f)));
+  }
   const float c1 = 1.0f / (1.0f - powf(b1, t)), c2 = 1.0f / (1.0f - powf(b2, t));
   for (int q = threadIdx.x; q < MLP_NPARAM; q += blockDim.x) {
     const float gq = grad[q];
@@ -349,9 +355,9 @@ void launch_mlp_backward(const MlpBuf& b, const float* X, const float* Y, long l
                                                                  ctr, base, grad, loss_hist);
 }
 
-void launch_mlp_adam_pack(float* p, float* m, float* v, float* grad, float lr, long long* ctr, const MlpBuf& b,
-                          cudaStream_t st) {
-  k_mlp_adam_pack<<<1, 1024, 0, st>>>(p, m, v, grad, lr, ctr, b.w1f, b.w2f, b.w2tf, b.vec);
+void launch_mlp_adam_pack(float* p, float* m, float* v, float* grad, float lr, long long total, long long* ctr,
+                          const MlpBuf& b, cudaStream_t st) {
+  k_mlp_adam_pack<<<1, 1024, 0, st>>>(p, m, v, grad, lr, total, ctr, b.w1f, b.w2f, b.w2tf, b.vec);
 }
 
 }  // namespace vcsgc

@@ -190,7 +190,7 @@ int vcsgc_mlp_train(void* mlp, const float* d_X, const float* d_Y, int64_t n, in
   const float flr = (float)lr;
   auto one_step = [&]() {
     launch_mlp_backward(m->buf, d_X, d_Y, n, batch, true, key, m->ctr, m->ctr + 1, m->grad, m->loss, m->st);
-    launch_mlp_adam_pack(m->p, m->m, m->v, m->grad, flr, m->ctr, m->buf, m->st);
+    launch_mlp_adam_pack(m->p, m->m, m->v, m->grad, flr, (long long)steps, m->ctr, m->buf, m->st);
   };
   const int G = 32;
   long long left = steps;
