@@ -388,6 +388,45 @@ def surrogate_bench(V, torch, stream, local, tab, sweeps, warmup, plain_value, p
             "network": "10-64-64-1 SiLU, BF16 mma.sync m16n8k16, FP32 accumulate; Adam"}
 
 
+def ising_bench(V, torch, stream, local, sweeps=30, warmup=3):
+    """The Ising-type lattice gas of Sec. II B (BCC, pair interactions to the
+    second shell, eps_AA(1) = eps_BB(1) = -10 U, eps_AB(1) = -9.7 U, eps(2) =
+    -2 U, U = 0.1 eV, k_B T = 0.8617 U) through the same kernels: throughput on
+    80^3 x 8 replicas at c0 = 1/2, and the parallel method's acceptance in the
+    paper's set-up (40^3 cells, 64 domains of 10^3 cells in octants, one trial
+    per domain per step) against kappa at c0 = 1/2, dmu0 = 0."""
+    tab = I.ising_tables()
+    T = 1000.0
+    kT = I.KB_EV * T
+    out = {"workload": "Ising-type lattice gas, BCC, eps(1) -10/-9.7/-10 U, eps(2) -2 U, U = 0.1 eV, T = 1000 K"}
+    lat = I.bcc_lattice(CELLS, CELLS, CELLS)
+    types = I.random_types(lat.n, lat.n // 2, seed=6001)
+    kappa = 100.0
+    ctx = V.Context(lat, np.tile(types, N_PHI), tab, -kappa * kT, kappa, T, schedule=V.SCHED_SUBLATTICE,
+                    sched=(4, 4, 4), n_replicas=N_PHI, c0=0.5,
+                    seed_r=np.arange(N_PHI, dtype=np.uint64) + np.uint64(6001), stream=stream, device=local)
+    ctx.sweep(warmup)
+    ms = timed_sweeps(torch, stream, ctx, sweeps)
+    out["throughput"] = {"value": N_PHI * lat.n * sweeps / (ms * 1e-3), "unit": "trial moves/s",
+                         "config": f"{CELLS}^3 x {N_PHI} replicas, period-4 sublattice, c0 = 0.5, kappa = 100"}
+    ctx.close()
+    lat = I.bcc_lattice(40, 40, 40)
+    acc = {}
+    for kappa in (10.0, 100.0, 1000.0):
+        ctx = V.Context(lat, I.random_types(lat.n, lat.n // 2, seed=6101), tab, -kappa * kT, kappa, T,
+                        schedule=V.SCHED_BLOCKS, sched=(5, 5, 5, 2, 2, 2), c0=0.5, seed=6102,
+                        stream=stream, device=local)
+        ctx.sweep(20)
+        o0 = ctx.observables()
+        ctx.sweep(30)
+        o1 = ctx.observables()
+        acc[str(kappa)] = (o1["flips"] - o0["flips"]) / (o1["trials"] - o0["trials"])
+        ctx.close()
+    out["acceptance_parallel_64_domains"] = acc
+    out["paper_max_acceptance"] = {"parallel": 0.34, "serial": 0.47, "c": 0.5}
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle times the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -433,6 +472,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-ising", action="store_true")
     ap.add_argument("--md-only", action="store_true", help="only the MD measurement (profiling)")
     ap.add_argument("--md-box", type=float, default=250.0, help="nanocrystal box (A) for --md-only")
     args = ap.parse_args()
@@ -544,6 +584,8 @@ def main():
         line["mixed_128cubed"] = mixed_bench(V, torch, stream, local)
     if not args.no_batch:
         line["batch_64"] = batch_bench(V, torch, stream, local, surrogate=not args.no_surrogate)
+    if not args.no_ising:
+        line["ising"] = ising_bench(V, torch, stream, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lat, types, tab, phi, c0)
     if rank == 0:

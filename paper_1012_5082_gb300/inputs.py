@@ -170,6 +170,57 @@ def eam_tables(p: EAMParams | None = None) -> EAMTables:
                      dens=dens, ddens=ddens, embed=emb, dembed=demb)
 
 
+# ------------------------------------------------- Ising lattice gas
+@dataclasses.dataclass
+class IsingParams:
+    """Pair-only lattice gas on BCC up to the second neighbour shell (the
+    paper's Ising-type model, Sec. II B): eps_ab(1), eps_ab(2) in units of U
+    for ab = AA, AB, BB; no density, no embedding.  The pair tables are flat
+    at eps(1) around the first shell (a sqrt(3)/2) and at eps(2) around the
+    second (a), joined by quintic smoothsteps, and fall to zero before r_c,
+    so the splines return the exact shell values."""
+
+    U: float = 0.1                          # eV (k_B T = 0.8617 U at T = 1000 K)
+    eps1: tuple = (-10.0, -9.7, -10.0)
+    eps2: tuple = (-2.0, -2.0, -2.0)
+    a: float = 2.855
+    rc: float = 3.5
+    nr: int = 2000
+    steps: tuple = (2.60, 2.75, 3.05, 3.35)  # eps1 -> eps2 on [s0, s1], eps2 -> 0 on [s2, s3]
+
+    def pair(self, p, r):
+        r = np.asarray(r, dtype=np.float64)
+
+        def step(lo, hi):
+            x = np.clip((r - lo) / (hi - lo), 0.0, 1.0)
+            return 10 * x**3 - 15 * x**4 + 6 * x**5, (30 * x**2 - 60 * x**3 + 30 * x**4) / (hi - lo)
+
+        s0, s1, s2, s3 = self.steps
+        e1, e2 = self.eps1[p] * self.U, self.eps2[p] * self.U
+        a1, da1 = step(s0, s1)
+        a2, da2 = step(s2, s3)
+        v = (e1 + (e2 - e1) * a1) * (1.0 - a2)
+        dv = (e2 - e1) * da1 * (1.0 - a2) - (e1 + (e2 - e1) * a1) * da2
+        return v, dv
+
+
+def ising_tables(p: IsingParams | None = None) -> EAMTables:
+    """EAMTables of the lattice gas (zero density and embedding)."""
+    p = p or IsingParams()
+    dr = p.rc / (p.nr - 1)
+    r = np.arange(p.nr, dtype=np.float64) * dr
+    pair, dpair = [], []
+    for q in range(3):
+        v, dv = p.pair(q, r)
+        pair.append(np.ascontiguousarray(v))
+        dpair.append(np.ascontiguousarray(dv))
+    nrho, rho_max = 64, 1.0
+    zr, zrho = np.zeros(p.nr), np.zeros(nrho)
+    return EAMTables(rc=p.rc, nr=p.nr, dr=dr, nrho=nrho, drho=rho_max / (nrho - 1), pair=pair, dpair=dpair,
+                     dens=[zr.copy(), zr.copy()], ddens=[zr.copy(), zr.copy()],
+                     embed=[zrho.copy(), zrho.copy()], dembed=[zrho.copy(), zrho.copy()])
+
+
 # ------------------------------------------------------------ nanocrystal
 def _haar_rotations(rng, k):
     """k rotation matrices uniformly distributed on SO(3) (unit quaternions
