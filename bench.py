@@ -423,6 +423,24 @@ def ising_bench(V, torch, stream, local, sweeps=30, warmup=3):
         acc[str(kappa)] = (o1["flips"] - o0["flips"]) / (o1["trials"] - o0["trials"])
         ctx.close()
     out["acceptance_parallel_64_domains"] = acc
+    # dmu(c) = phi + 2 kappa_p N <c> at dmu0 = 0 across the gap: the finite
+    # system's van der Waals loop (16^3 cells, kappa = 1000, 4 replicas per c0)
+    kappa, L, S = 1000.0, 16, 4
+    c0s = np.round(np.arange(1, 13) * 0.04 + 0.02, 2)
+    c0r = np.repeat(c0s, S)
+    lat = I.bcc_lattice(L, L, L)
+    types = [I.random_types(lat.n, int(round(c * lat.n)), seed=6200 + q) for q, c in enumerate(c0r)]
+    b = V.Batch([(L, L, L)] * len(c0r), types, tab, -2.0 * kappa * kT * c0r, kappa, T,
+                seed_r=np.arange(len(c0r), dtype=np.uint64) + 6300, c0_r=c0r, stream=stream, device=local)
+    b.sweep(500)
+    s0 = b.observables_all()
+    b.sweep(1000)
+    s1 = b.observables_all()
+    b.close()
+    c = np.array([(s1[q]["mean_c"] * s1[q]["steps"] - s0[q]["mean_c"] * s0[q]["steps"])
+                  / (s1[q]["steps"] - s0[q]["steps"]) for q in range(len(c0r))]).reshape(-1, S)
+    dmu = 2.0 * kappa * kT * (c - c0s[:, None])
+    out["dmu_of_c_meV"] = {f"{x:.2f}": round(float(v) * 1e3, 3) for x, v in zip(c0s, dmu.mean(axis=1))}
     out["paper_max_acceptance"] = {"parallel": 0.34, "serial": 0.47, "c": 0.5}
     return out
 

@@ -105,3 +105,35 @@ def test_ising_c_equals_c0_at_dmu(V, tab):
     mp, ep = _window_c(V, tab, c0, dmu + 0.02, kappa, seed=2900)
     shift = -0.02 / (2.0 * kappa * kT)
     assert abs((mp - m1) - shift) < 0.2 * abs(shift) + 5 * math.hypot(ep, e1), (m1, mp, shift)
+
+
+def test_ising_van_der_waals_loop(V, tab):
+    """Inside the miscibility gap the constraint holds the system at any mean
+    concentration, so dmu(c) = phi + 2 kappa_p N <c> (Eq. gforce) traces the
+    finite system's van der Waals loop instead of jumping across the gap
+    (Sec. III C): falling from the dilute side, it overshoots below the
+    coexistence value 0 near c = 0.2 and turns back up to 0 at c = 1/2 (A <-> B
+    symmetry).  16^3 cells, kappa = 1000, 8 replicas per c0 in one batch."""
+    kappa, L, S = 1000.0, 16, 8
+    kT = I.KB_EV * T_ISING
+    c0s = np.array([0.10, 0.20, 0.40, 0.50])
+    c0r = np.repeat(c0s, S)
+    R = len(c0r)
+    lat = I.bcc_lattice(L, L, L)
+    types = [I.random_types(lat.n, int(round(c * lat.n)), seed=3000 + q) for q, c in enumerate(c0r)]
+    b = V.Batch([(L, L, L)] * R, types, tab, -2.0 * kappa * kT * c0r, kappa, T_ISING,
+                seed_r=np.arange(R, dtype=np.uint64) + 3100, c0_r=c0r)
+    b.sweep(500)
+    s0 = b.observables_all()
+    b.sweep(1000)
+    s1 = b.observables_all()
+    b.close()
+    c = np.array([(s1[q]["mean_c"] * s1[q]["steps"] - s0[q]["mean_c"] * s0[q]["steps"])
+                  / (s1[q]["steps"] - s0[q]["steps"]) for q in range(R)]).reshape(-1, S)
+    dmu = 2.0 * kappa * kT * (c - c0s[:, None])
+    m = dmu.mean(axis=1)
+    e = dmu.std(axis=1, ddof=1) / math.sqrt(S)
+    assert m[0] > m[1] + 5 * math.hypot(e[0], e[1]), (m, e)   # falling from the dilute side
+    assert m[1] < -5 * e[1], (m, e)                            # below coexistence
+    assert m[2] > m[1] + 5 * math.hypot(e[1], e[2]), (m, e)   # and back up: the loop
+    assert abs(m[3]) < 5 * e[3] + 2e-4, (m, e)                 # 0 at c = 1/2
