@@ -67,6 +67,10 @@ def lib():
             "orc_schedule_blocks": (I32, [P] + [I32] * 9),
             "orc_schedule_sublattice": (I32, [P] + [I32] * 6),
             "orc_schedule_spatial": (I32, [P] + [I32] * 6),
+            "orc_schedule_overlap": (I32, [P] + [I32] * 9),
+            "orc_schedule_weights": (I32, [P, P]),
+            "orc_track_trials": (I32, [P, I32]),
+            "orc_trial_counts": (None, [P, P]),
             "orc_schedule_min_separation": (D, [P]),
             "orc_schedule_info": (I64, [P, P, P]),
             "orc_schedule_export": (None, [P, P, P, P]),
@@ -192,6 +196,27 @@ class System:
         if lib().orc_schedule_spatial(self.h, *blocks, *colours):
             raise ValueError("oracle: spatial schedule does not divide")
 
+    def schedule_overlap(self, cells, cell, gap):
+        """Overlapping, position-weighted domains: cells of `cell` lattice
+        cells, same-colour domains `gap` lattice cells apart (Sec. III A)."""
+        if lib().orc_schedule_overlap(self.h, *cells, *cell, *gap):
+            raise ValueError("oracle: overlapping schedule does not divide the lattice")
+
+    def schedule_weights(self):
+        """Pick weights parallel to schedule_tables()'s sites, or None."""
+        col, dom, sites = self.schedule_tables()
+        wt = np.zeros(len(sites), dtype=np.int64)
+        return wt if lib().orc_schedule_weights(self.h, _p(wt)) else None
+
+    def track_trials(self, on=True):
+        if lib().orc_track_trials(self.h, int(bool(on))):
+            raise MemoryError("oracle: trial counters")
+
+    def trial_counts(self):
+        out = np.zeros(self.n, dtype=np.int64)
+        lib().orc_trial_counts(self.h, _p(out))
+        return out
+
     def schedule_min_separation(self):
         return lib().orc_schedule_min_separation(self.h)
 
@@ -201,7 +226,8 @@ class System:
         nd = lib().orc_schedule_info(self.h, C.byref(nc), C.byref(dpc))
         col = np.zeros(nc.value + 1, dtype=np.int64)
         dom = np.zeros(nd + 1, dtype=np.int64)
-        sites = np.zeros(self.n, dtype=np.int64)
+        lib().orc_schedule_export(self.h, _p(col), _p(dom), None)
+        sites = np.zeros(int(dom[-1]), dtype=np.int64)
         lib().orc_schedule_export(self.h, _p(col), _p(dom), _p(sites))
         return col, dom, sites
 

@@ -69,7 +69,9 @@ struct orc_sys {
   /* schedule */
   int64_t n_colours, n_domains;
   int64_t *col_start, *dom_start, *dom_sites;
-  int sched_kind; /* 0 none, 1 blocks, 2 sublattice, 3 spatial */
+  int64_t* dom_wt;       /* pick weight of each dom_sites entry, or NULL (uniform) */
+  int64_t* site_trials;  /* trials per site, or NULL (not counted) */
+  int sched_kind; /* 0 none, 1 blocks, 2 sublattice, 3 spatial, 4 overlapping */
   int sched_args[9];
   /* delayed acceptance: stage-1 surrogate of the energy change */
   int sur_kind;          /* 0 off, 1 MLP, 2 the exact energy change */
@@ -463,7 +465,8 @@ void orc_free(orc_sys* s) {
   free(s->x); free(s->y); free(s->z); free(s->t); free(s->rho);
   for (int p = 0; p < 7; ++p) { free(s->sp[p].y); free(s->sp[p].m); }
   free(s->nstart); free(s->nb);
-  free(s->col_start); free(s->dom_start); free(s->dom_sites);
+  free(s->col_start); free(s->dom_start); free(s->dom_sites); free(s->dom_wt);
+  free(s->site_trials);
   free(s->vx); free(s->vy); free(s->vz); free(s->fx); free(s->fy); free(s->fz);
   free(s->mlp);
   free(s);
@@ -498,7 +501,8 @@ void orc_reset_counters(orc_sys* s) {
 
 /* -------------------------------------------------------------- schedule */
 static int sched_alloc(orc_sys* s, int64_t n_colours, int64_t n_domains) {
-  free(s->col_start); free(s->dom_start); free(s->dom_sites);
+  free(s->col_start); free(s->dom_start); free(s->dom_sites); free(s->dom_wt);
+  s->dom_wt = NULL;
   s->col_start = (int64_t*)calloc(n_colours + 1, sizeof(int64_t));
   s->dom_start = (int64_t*)calloc(n_domains + 1, sizeof(int64_t));
   s->dom_sites = (int64_t*)calloc(s->n, sizeof(int64_t));
@@ -607,6 +611,97 @@ int orc_schedule_spatial(orc_sys* s, int nbx, int nby, int nbz, int px, int py, 
   return 0;
 }
 
+/* Overlapping, position-weighted domains (Sec. III A, the optimal
+ * decomposition): the lattice is cut into cells of lx*ly*lz lattice cells;
+ * along each axis a domain covers either the first l - g or the last l - g
+ * lattice cells of its cell, so the eight domains of a cell (colour bits
+ * bx, by, bz) overlap in the middle and domains of one colour in
+ * neighbouring cells are g lattice cells apart.  A site covered by m_x m_y
+ * m_z domains (m = 1 or 2 per axis) has the pick weight 8 / (m_x m_y m_z):
+ * with the domain's site drawn in proportion to weight, every site is picked
+ * with probability 1 / (2 lx ly lz) per step.  Within a domain the sites are
+ * listed by decreasing weight, ascending index within one weight. */
+int orc_schedule_overlap(orc_sys* s, int nx, int ny, int nz, int lx, int ly, int lz,
+                         int gx, int gy, int gz) {
+  if ((int64_t)2 * nx * ny * nz != s->n) return -1;
+  int n3[3] = {nx, ny, nz}, l3[3] = {lx, ly, lz}, g3[3] = {gx, gy, gz}, nc[3], ld[3];
+  for (int q = 0; q < 3; ++q) {
+    if (l3[q] < 1 || g3[q] < 0 || n3[q] % l3[q] || 2 * g3[q] > l3[q]) return -1;
+    nc[q] = n3[q] / l3[q];
+    ld[q] = l3[q] - g3[q];
+  }
+  int64_t ncells = (int64_t)nc[0] * nc[1] * nc[2];
+  int64_t per_dom = (int64_t)2 * ld[0] * ld[1] * ld[2];
+  if (sched_alloc(s, 8, 8 * ncells)) return -1;
+  free(s->dom_sites);
+  s->dom_sites = (int64_t*)calloc(8 * ncells * per_dom, sizeof(int64_t));
+  s->dom_wt = (int64_t*)calloc(8 * ncells * per_dom, sizeof(int64_t));
+  int64_t* tmp = (int64_t*)malloc(sizeof(int64_t) * per_dom);
+  int64_t* tw = (int64_t*)malloc(sizeof(int64_t) * per_dom);
+  if (!s->dom_sites || !s->dom_wt || !tmp || !tw) { free(tmp); free(tw); return -1; }
+  int64_t dom = 0, pos = 0;
+  for (int c = 0; c < 8; ++c) {
+    int bit[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+    s->col_start[c] = dom;
+    for (int icz = 0; icz < nc[2]; ++icz)
+      for (int icy = 0; icy < nc[1]; ++icy)
+        for (int icx = 0; icx < nc[0]; ++icx) {
+          int ic[3] = {icx, icy, icz};
+          int64_t k = 0;
+          for (int tz = 0; tz < ld[2]; ++tz)
+            for (int ty = 0; ty < ld[1]; ++ty)
+              for (int tx = 0; tx < ld[0]; ++tx) {
+                int t3[3] = {tx, ty, tz}, X[3];
+                int cover = 1;
+                for (int q = 0; q < 3; ++q) {
+                  int local = bit[q] * g3[q] + t3[q]; /* position inside the cell */
+                  int m = 0;
+                  for (int b = 0; b < 2; ++b)
+                    if (local >= b * g3[q] && local < b * g3[q] + ld[q]) ++m;
+                  cover *= m;
+                  X[q] = ic[q] * l3[q] + local;
+                }
+                for (int b = 0; b < 2; ++b) {
+                  tmp[k] = (((int64_t)X[2] * ny + X[1]) * nx + X[0]) * 2 + b;
+                  tw[k] = 8 / cover;
+                  ++k;
+                }
+              }
+          s->dom_start[dom] = pos;
+          for (int64_t w = 8; w >= 1; w /= 2)
+            for (int64_t q = 0; q < per_dom; ++q)
+              if (tw[q] == w) {
+                s->dom_sites[pos] = tmp[q];
+                s->dom_wt[pos] = w;
+                ++pos;
+              }
+          ++dom;
+        }
+  }
+  s->col_start[8] = dom;
+  s->dom_start[dom] = pos;
+  free(tmp);
+  free(tw);
+  s->sched_kind = 4;
+  return 0;
+}
+
+int orc_schedule_weights(const orc_sys* s, int64_t* wt) {
+  if (!s->dom_wt) return 0;
+  if (wt) memcpy(wt, s->dom_wt, sizeof(int64_t) * s->dom_start[s->n_domains]);
+  return 1;
+}
+
+int orc_track_trials(orc_sys* s, int on) {
+  free(s->site_trials);
+  s->site_trials = on ? (int64_t*)calloc(s->n, sizeof(int64_t)) : NULL;
+  return on && !s->site_trials ? -1 : 0;
+}
+
+void orc_trial_counts(const orc_sys* s, int64_t* out) {
+  for (int64_t i = 0; i < s->n; ++i) out[i] = s->site_trials ? s->site_trials[i] : 0;
+}
+
 int64_t orc_schedule_info(const orc_sys* s, int64_t* n_colours, int64_t* domains_per_colour) {
   if (n_colours) *n_colours = s->n_colours;
   if (domains_per_colour) *domains_per_colour = s->n_colours ? s->col_start[1] - s->col_start[0] : 0;
@@ -617,7 +712,7 @@ void orc_schedule_export(const orc_sys* s, int64_t* col_start, int64_t* dom_star
                          int64_t* dom_sites) {
   if (col_start) memcpy(col_start, s->col_start, sizeof(int64_t) * (s->n_colours + 1));
   if (dom_start) memcpy(dom_start, s->dom_start, sizeof(int64_t) * (s->n_domains + 1));
-  if (dom_sites) memcpy(dom_sites, s->dom_sites, sizeof(int64_t) * s->n);
+  if (dom_sites) memcpy(dom_sites, s->dom_sites, sizeof(int64_t) * s->dom_start[s->n_domains]);
 }
 
 static double min_image_dist(const orc_sys* s, int64_t i, int64_t j) {
@@ -815,7 +910,22 @@ static void parallel_step(orc_sys* s, int64_t* acc_sites, double* acc_de) {
     int64_t size = s->dom_start[g + 1] - s->dom_start[g];
     if (size == 0) continue;
     draw(s, k, (uint32_t)(g - d0), 0u, w);
-    int64_t site = s->dom_sites[s->dom_start[g] + orc_below(w[0], w[1], (uint64_t)size)];
+    int64_t site;
+    if (s->dom_wt) {
+      /* weighted pick: r uniform on [0, total weight), the first site whose
+       * running weight exceeds r */
+      int64_t total = 0;
+      for (int64_t q = s->dom_start[g]; q < s->dom_start[g + 1]; ++q) total += s->dom_wt[q];
+      int64_t r = (int64_t)orc_below(w[0], w[1], (uint64_t)total), run = 0, q = s->dom_start[g];
+      for (;; ++q) {
+        run += s->dom_wt[q];
+        if (r < run) break;
+      }
+      site = s->dom_sites[q];
+    } else {
+      site = s->dom_sites[s->dom_start[g] + orc_below(w[0], w[1], (uint64_t)size)];
+    }
+    if (s->site_trials) s->site_trials[site]++;
     double u = orc_u01(w[2], w[3]), u2 = 0.0;
     if (s->sur_kind) {
       uint32_t w2[4];

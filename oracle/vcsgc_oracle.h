@@ -102,11 +102,28 @@ int orc_schedule_blocks(orc_sys* s, int nx, int ny, int nz, int bx, int by, int 
                         int px, int py, int pz);
 int orc_schedule_sublattice(orc_sys* s, int nx, int ny, int nz, int qx, int qy, int qz);
 int orc_schedule_spatial(orc_sys* s, int nbx, int nby, int nbz, int px, int py, int pz);
+/* Overlapping, position-weighted domains (Sec. III A): cells of lx*ly*lz
+ * lattice cells, eight colours (one bit per axis); along each axis the
+ * domain of bit b covers lattice cells [b g, b g + l - g) of its cell, so
+ * same-colour domains of neighbouring cells are g lattice cells apart and
+ * the eight domains of a cell overlap where 2 g < l.  Each listed site has
+ * the pick weight 8 / (number of the cell's domains that contain it); a
+ * domain lists its sites by decreasing weight, ascending index within one
+ * weight.  Needs l | n and 0 <= 2 g <= l per axis; returns 0 or -1. */
+int orc_schedule_overlap(orc_sys* s, int nx, int ny, int nz, int lx, int ly, int lz,
+                         int gx, int gy, int gz);
+/* Pick weights of the dom_sites entries (dom_start[n_domains] values) when
+ * the schedule is weighted: returns 1 and fills wt (may be NULL), else 0. */
+int orc_schedule_weights(const orc_sys* s, int64_t* wt);
+/* Count the trials of each site in parallel steps (on != 0), or stop. */
+int orc_track_trials(orc_sys* s, int on);
+void orc_trial_counts(const orc_sys* s, int64_t* out);
 /* Smallest distance between two sites of distinct domains of one colour. */
 double orc_schedule_min_separation(const orc_sys* s);
 int64_t orc_schedule_info(const orc_sys* s, int64_t* n_colours, int64_t* domains_per_colour);
 /* Export domain tables: col_start[n_colours+1], dom_start[n_domains+1],
- * dom_sites[N] (each may be NULL). */
+ * dom_sites[dom_start[n_domains]] (N, or more for overlapping domains; each
+ * may be NULL). */
 void orc_schedule_export(const orc_sys* s, int64_t* col_start, int64_t* dom_start,
                          int64_t* dom_sites);
 
