@@ -103,10 +103,21 @@ typedef struct {
  *               with sched[0..2] = qx,qy,qz; every site of the colour is a
  *               domain of its own, so all of them are trialled at once.
  *   SPATIAL:    (kind 0 or 1) domains = sched[0..2] = nbx,nby,nbz boxes of
- *               the periodic cell, colour as for BLOCKS with sched[3..5]. */
+ *               the periodic cell, colour as for BLOCKS with sched[3..5].
+ *   OVERLAP:    (kind 0) overlapping, position-weighted domains (Sec. III A):
+ *               cells of sched[0..2] = lx,ly,lz lattice cells, eight colours
+ *               (one bit per axis); along each axis the domain of bit b
+ *               covers cell-local lattice cells [b g, b g + l - g), g =
+ *               sched[3..5], so same-colour domains are g cells apart and the
+ *               eight domains of a cell overlap where 2 g < l.  A site in m of
+ *               its cell's domains is picked with weight 8 / m, which makes
+ *               every site's pick probability 1 / (2 lx ly lz) per step; a
+ *               domain lists its sites by decreasing weight, ascending index
+ *               within one weight.  Needs l | n and 2 g <= l per axis. */
 #define VCSGC_SCHED_BLOCKS 0
 #define VCSGC_SCHED_SUBLATTICE 1
 #define VCSGC_SCHED_SPATIAL 2
+#define VCSGC_SCHED_OVERLAP 3
 
 #define VCSGC_PREC_FP64 0
 #define VCSGC_PREC_MIXED 1

@@ -56,6 +56,25 @@ __device__ __forceinline__ uint64_t word64(uint32_t lo, uint32_t hi) {
 __device__ __forceinline__ uint64_t below64(uint32_t lo, uint32_t hi, uint64_t m) {
   return __umul64hi(word64(lo, hi), m);
 }
+// Site pick inside a domain (Sec. III A).  Uniform domains (n == 0): the
+// index below(size).  Position-weighted domains list their sites in n <= 4
+// classes of equal weight 2^sh[k], class k starting at index beg[k], with
+// cum[k] the weight of classes 0..k; a draw r = below(cum[n-1]) falls in the
+// class with cum[k-1] <= r < cum[k] and picks index beg[k] + (r - cum[k-1])
+// / 2^sh[k], the first site whose running weight exceeds r.
+struct PickTab {
+  int n;
+  int cum[4], beg[4], sh[4];
+};
+__device__ __forceinline__ int pick_index(const PickTab& t, uint32_t lo, uint32_t hi, int size) {
+  if (t.n == 0) return (int)below64(lo, hi, (uint64_t)size);
+  const int r = (int)below64(lo, hi, (uint64_t)t.cum[t.n - 1]);
+  int k = 0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) k += (q + 1 < t.n && r >= t.cum[q]) ? 1 : 0;
+  const int prev = k ? t.cum[k - 1] : 0;
+  return t.beg[k] + ((r - prev) >> t.sh[k]);
+}
 // top 53 bits of the word; u = u53 * 2^-53 in [0, 1)
 __device__ __forceinline__ uint64_t top53(uint32_t lo, uint32_t hi) {
   return word64(lo, hi) >> 11;
@@ -296,6 +315,7 @@ struct McArgs {
   const int* col_start;
   const int* dom_start;
   const int* dom_sites;
+  PickTab pick;          // site weights of overlapping domains (n = 0: uniform)
   int dmax;
   // replicas
   const RepParams* rp;

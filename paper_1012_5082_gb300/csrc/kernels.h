@@ -135,6 +135,7 @@ struct LatArgs {
   const int* col_start;
   const int* dom_start;
   const int* dom_sites;
+  PickTab pick;                 // site weights of overlapping domains (n = 0: uniform)
   int dmax;                     // largest pending-slot count of a replica
   const int2* blk;              // [n_blk] (replica, first trial) of each block of `block` threads
   int n_blk;

@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {
         const int gg = a.col_start[c] + d;
         const int base = a.dom_start[gg];
         const int size = a.dom_start[gg + 1] - base;
-        site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
+        site = a.dom_sites[base + pick_index(a.pick, w.x, w.y, size)];
         decode_site(g, site, sX, sY, sZ, sb_);
       }
     }

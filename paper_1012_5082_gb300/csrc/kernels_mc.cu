@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
     const int size = a.dom_start[g + 1] - base;
     if (size > 0) {
       const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL), p.key);
-      site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
+      site = a.dom_sites[base + pick_index(a.pick, w.x, w.y, size)];
       const uint64_t u53 = top53(w.z, w.w);
       const int t = a.types[(long long)r * a.N + site];
       const double sg = t ? -1.0 : 1.0;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(MCW_BLOCK) k_propose_warp(McArgs a) {
   const int size = a.dom_start[g + 1] - base;
   if (size == 0) return;
   const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL), p.key);
-  const int site = a.dom_sites[base + (int)below64(w.x, w.y, (uint64_t)size)];
+  const int site = a.dom_sites[base + pick_index(a.pick, w.x, w.y, size)];
   const double de = delta_e_warp<REEMBED, MIXED>(a, r, site, lane, a.err);
   if (lane != 0) return;
   const int t = a.types[(long long)r * a.N + site];

@@ -61,6 +61,8 @@ struct Ctx {
   int* col_start = nullptr;
   int* dom_start = nullptr;
   int* dom_sites = nullptr;
+  long long dom_sites_cap = 0;     // entries dom_sites was allocated for
+  PickTab pick{};                  // site weights of an OVERLAP schedule
   int n_colours = 0, dmax = 0;
   long long n_domains = 0;
   int sublattice_d = 0;            // domains per colour of a SUBLATTICE schedule
@@ -201,6 +203,7 @@ void fill_args(Ctx* c) {
   a.col_start = c->col_start;
   a.dom_start = c->dom_start;
   a.dom_sites = c->dom_sites;
+  a.pick = c->pick;
   a.dmax = c->dmax;
   a.rp = c->rp;
   a.rs = c->rs;
@@ -250,6 +253,7 @@ void fill_args(Ctx* c) {
   l.col_start = c->col_start;
   l.dom_start = c->dom_start;
   l.dom_sites = c->dom_sites;
+  l.pick = c->pick;
   l.rp = c->rp;
   l.rs = c->rs;
   l.err = c->derr;
@@ -311,9 +315,10 @@ int build_cell_list(Ctx* c) {
 
 // ------------------------------------------------------------- schedule
 // Host tables of the colour schedule: col_start[n_colours+1] indexes
-// domains, dom_start[n_domains+1] indexes dom_sites.
+// domains, dom_start[n_domains+1] indexes dom_sites; wt (OVERLAP only) holds
+// each entry's pick weight.
 struct Sched {
-  std::vector<int> col, dom, sites;
+  std::vector<int> col, dom, sites, wt;
 };
 
 double cell_gap_distance(double a, int gap_cells) {
@@ -327,8 +332,9 @@ int build_schedule(Ctx* c, const std::vector<double>& hx, const std::vector<doub
                    const std::vector<double>& hz, Sched& S) {
   const double two_rc = 2.0 * c->rc;
   const int* p = c->sched;
-  if (c->sched_kind == VCSGC_SCHED_BLOCKS || c->sched_kind == VCSGC_SCHED_SUBLATTICE) {
-    if (c->kind != 0) return fail(c, VCSGC_ERR_INVALID_ARG, "BLOCKS and SUBLATTICE schedules need a rigid lattice");
+  if (c->sched_kind == VCSGC_SCHED_BLOCKS || c->sched_kind == VCSGC_SCHED_SUBLATTICE ||
+      c->sched_kind == VCSGC_SCHED_OVERLAP) {
+    if (c->kind != 0) return fail(c, VCSGC_ERR_INVALID_ARG, "lattice schedules need a rigid lattice");
   }
   if (c->sched_kind == VCSGC_SCHED_BLOCKS) {
     const int bx = p[0], by = p[1], bz = p[2], px = p[3], py = p[4], pz = p[5];
@@ -384,6 +390,58 @@ int build_schedule(Ctx* c, const std::vector<double>& hx, const std::vector<doub
     for (long long i = 0; i < c->N; ++i) S.sites[cur[colour_of(i)]++] = (int)i;
     S.dom.resize(c->N + 1);
     for (long long i = 0; i <= c->N; ++i) S.dom[i] = (int)i;
+  } else if (c->sched_kind == VCSGC_SCHED_OVERLAP) {
+    // cells of l lattice cells per axis; the domain of colour bit b covers
+    // cell-local coordinates [b g, b g + l - g); weight 8 / coverage
+    const int n3[3] = {c->nx, c->ny, c->nz};
+    int l3[3], g3[3], nc[3], ld[3];
+    for (int q = 0; q < 3; ++q) {
+      l3[q] = p[q];
+      g3[q] = p[3 + q];
+      if (l3[q] < 1 || g3[q] < 0 || 2 * g3[q] > l3[q] || n3[q] % l3[q])
+        return fail(c, VCSGC_ERR_SCHEDULE, "overlap cells do not divide the lattice, or 2 g > l");
+      nc[q] = n3[q] / l3[q];
+      ld[q] = l3[q] - g3[q];
+      if (nc[q] > 1 && cell_gap_distance(c->a, g3[q]) <= two_rc)
+        return fail(c, VCSGC_ERR_SCHEDULE, "same-colour overlapping domains closer than 2 r_c");
+    }
+    // coverage of a cell-local coordinate along one axis: 1 or 2
+    auto cover = [&](int q, int x) { return (x < ld[q] ? 1 : 0) + (x >= g3[q] ? 1 : 0); };
+    const long long per_dom = 2LL * ld[0] * ld[1] * ld[2];
+    const long long ncell = (long long)nc[0] * nc[1] * nc[2];
+    if (8 * ncell * per_dom >= (1LL << 31)) return fail(c, VCSGC_ERR_SCHEDULE, "overlap tables too large");
+    S.col.assign(9, 0);
+    std::vector<int> tmp, tw;
+    for (int col = 0; col < 8; ++col) {
+      const int o[3] = {(col & 1) * g3[0], ((col >> 1) & 1) * g3[1], ((col >> 2) & 1) * g3[2]};
+      S.col[col] = (int)S.dom.size();
+      for (int icz = 0; icz < nc[2]; ++icz)
+        for (int icy = 0; icy < nc[1]; ++icy)
+          for (int icx = 0; icx < nc[0]; ++icx) {
+            tmp.clear();
+            tw.clear();
+            for (int tz = o[2]; tz < o[2] + ld[2]; ++tz)
+              for (int ty = o[1]; ty < o[1] + ld[1]; ++ty)
+                for (int tx = o[0]; tx < o[0] + ld[0]; ++tx) {
+                  const long long cx = (long long)icx * l3[0] + tx, cy = (long long)icy * l3[1] + ty,
+                                  cz = (long long)icz * l3[2] + tz;
+                  const int w = 8 / (cover(0, tx) * cover(1, ty) * cover(2, tz));
+                  for (int b = 0; b < 2; ++b) {
+                    tmp.push_back((int)(((cz * c->ny + cy) * c->nx + cx) * 2 + b));
+                    tw.push_back(w);
+                  }
+                }
+            S.dom.push_back((int)S.sites.size());
+            for (int w = 8; w >= 1; w >>= 1)
+              for (size_t q = 0; q < tmp.size(); ++q)
+                if (tw[q] == w) {
+                  S.sites.push_back(tmp[q]);
+                  S.wt.push_back(w);
+                }
+          }
+    }
+    S.col[8] = (int)S.dom.size();
+    S.dom.push_back((int)S.sites.size());
   } else if (c->sched_kind == VCSGC_SCHED_SPATIAL) {
     const int nb[3] = {p[0], p[1], p[2]}, pp[3] = {p[3], p[4], p[5]};
     for (int q = 0; q < 3; ++q) {
@@ -433,17 +491,47 @@ int build_schedule(Ctx* c, const std::vector<double>& hx, const std::vector<doub
   return VCSGC_OK;
 }
 
+// Class table of the weighted pick: every domain must list the same
+// sequence of weights (true of the OVERLAP geometry), each a power of two.
+static int pick_table(Ctx* c, const Sched& S, PickTab& t) {
+  t = PickTab{};
+  if (S.wt.empty()) return VCSGC_OK;
+  const int n0 = S.dom[1] - S.dom[0];
+  for (int k = 0; k < n0;) {
+    const int w = S.wt[k];
+    int e = k;
+    while (e < n0 && S.wt[e] == w) ++e;
+    if (t.n == 4 || w < 1 || (w & (w - 1))) return fail(c, VCSGC_ERR_SCHEDULE, "pick weights not in four power-of-two classes");
+    t.beg[t.n] = k;
+    t.sh[t.n] = __builtin_ctz((unsigned)w);
+    t.cum[t.n] = (t.n ? t.cum[t.n - 1] : 0) + (e - k) * w;
+    ++t.n;
+    k = e;
+  }
+  for (size_t d = 0; d + 1 < S.dom.size(); ++d) {
+    if (S.dom[d + 1] - S.dom[d] != n0) return fail(c, VCSGC_ERR_SCHEDULE, "weighted domains differ in size");
+    for (int k = 0; k < n0; ++k)
+      if (S.wt[S.dom[d] + k] != S.wt[k]) return fail(c, VCSGC_ERR_SCHEDULE, "weighted domains differ in weights");
+  }
+  return VCSGC_OK;
+}
+
 int upload_schedule(Ctx* c, const Sched& S) {
   const int ncol = (int)S.col.size() - 1;
   int dmax = 0;
   for (int q = 0; q < ncol; ++q) dmax = std::max(dmax, S.col[q + 1] - S.col[q]);
+  TRY(pick_table(c, S, c->pick));
   const bool realloc_needed = !c->col_start || ncol != c->n_colours ||
                               (long long)S.dom.size() - 1 != c->n_domains || dmax > c->dmax;
   if (realloc_needed) {
     TRY(dalloc(c, &c->col_start, S.col.size()));
     TRY(dalloc(c, &c->dom_start, S.dom.size()));
-    if (!c->dom_sites) TRY(dalloc(c, &c->dom_sites, c->N));
     if (dmax > c->dmax) TRY(dalloc(c, &c->acc_list, (size_t)c->R * dmax));
+    drop_graph(c);
+  }
+  if ((long long)S.sites.size() > c->dom_sites_cap) {
+    TRY(dalloc(c, &c->dom_sites, S.sites.size()));
+    c->dom_sites_cap = (long long)S.sites.size();
     drop_graph(c);
   }
   CK(cudaMemcpyAsync(c->col_start, S.col.data(), sizeof(int) * S.col.size(), cudaMemcpyHostToDevice, c->st));
@@ -969,7 +1057,9 @@ static int lattice_shared(Ctx* c, int& unsupported) {
   if (c->kind != 0 || c->reembed || c->nx < 2) return VCSGC_OK;
   // index arithmetic of the fused form: sites < 2^22, rows < 2^20, 2 nx < 2048
   if (c->N > (1LL << 22) || 2 * c->nx >= 2048 || (long long)c->ny * c->nz >= (1LL << 20)) return VCSGC_OK;
-  if (c->sched_kind != VCSGC_SCHED_BLOCKS && c->sched_kind != VCSGC_SCHED_SUBLATTICE) return VCSGC_OK;
+  if (c->sched_kind != VCSGC_SCHED_BLOCKS && c->sched_kind != VCSGC_SCHED_SUBLATTICE &&
+      c->sched_kind != VCSGC_SCHED_OVERLAP)
+    return VCSGC_OK;
   const int S = c->mc.n_shells;
   if (S > LAT_MAX_SH) return VCSGC_OK;
   LatArgs& l = c->lat;

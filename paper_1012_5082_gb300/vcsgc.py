@@ -17,7 +17,7 @@ from . import build as _build
 OK = 0
 ERR = {-1: "INVALID_ARG", -2: "CUDA", -3: "TABLE_RANGE", -4: "NONFINITE", -5: "SCHEDULE",
        -6: "TIMEOUT", -7: "NOMEM", -8: "STATE", -9: "OVERFLOW"}
-SCHED_BLOCKS, SCHED_SUBLATTICE, SCHED_SPATIAL = 0, 1, 2
+SCHED_BLOCKS, SCHED_SUBLATTICE, SCHED_SPATIAL, SCHED_OVERLAP = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED = 0, 1
 MLP_IN = 10
 MLP_NPARAM = 4929

@@ -15,7 +15,8 @@ def c0_config(n_cells=10, frac_b=0.05, seed_types=1000, dens_b=1.0):
 
 
 def make_pair(lat, types, tab, phi, kappa, T, *, c0, seed, schedule, sched, kappa_units=0):
-    """schedule: ('blocks', cells, block, colours) or ('sublattice', cells, period)."""
+    """schedule: 'blocks' (block, colours), 'sublattice' (period), 'overlap'
+    (cell, gap) or 'spatial' (boxes, colours)."""
     from paper_1012_5082_gb300 import vcsgc as V
 
     orc = O.System(lat, types, tab)
@@ -26,6 +27,9 @@ def make_pair(lat, types, tab, phi, kappa, T, *, c0, seed, schedule, sched, kapp
     elif schedule == "sublattice":
         orc.schedule_sublattice(lat.cells, sched[:3])
         kind = V.SCHED_SUBLATTICE
+    elif schedule == "overlap":
+        orc.schedule_overlap(lat.cells, sched[:3], sched[3:])
+        kind = V.SCHED_OVERLAP
     else:
         orc.schedule_spatial(sched[:3], sched[3:])
         kind = V.SCHED_SPATIAL
