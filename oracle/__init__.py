@@ -1,11 +1,12 @@
-"""ctypes binding of the serial FP64 CPU oracle (``vcsgc_oracle.c``).
+"""ctypes binding of the serial FP64 CPU oracle (``vcsgc_oracle.c``, and
+``vcsgc_multi.c`` for the multicomponent generalisation).
 
 TEST INFRASTRUCTURE ONLY.  The oracle is the plain reference the CUDA path
 is checked against: only the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import this package.  The product path never
 calls it, and it imports nothing from the CUDA package.
 
-``build()`` compiles the C source with gcc into ``oracle/liboracle.so``.
+``build()`` compiles the C sources with gcc into ``oracle/liboracle.so``.
 """
 from __future__ import annotations
 
@@ -18,6 +19,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "vcsgc_oracle.c")
 HDR = os.path.join(HERE, "vcsgc_oracle.h")
+SRCS = [SRC, os.path.join(HERE, "vcsgc_multi.c")]
+HDRS = [HDR, os.path.join(HERE, "vcsgc_multi.h"), os.path.join(HERE, "orc_internal.h")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 _lib = None
@@ -26,11 +29,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle if the shared object is missing or stale."""
     stale = (not os.path.exists(LIB) or
-             os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
+             os.path.getmtime(LIB) < max(os.path.getmtime(f) for f in SRCS + HDRS))
     if force or stale:
         tmp = LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC",
-                               "-shared", "-o", tmp, SRC, "-lm"])
+                               "-shared", "-o", tmp, *SRCS, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -103,6 +106,21 @@ def lib():
             "orc_mlp_eval": (D, [P, P]),
             "orc_set_surrogate": (I32, [P, I32, P]),
             "orc_surrogate": (D, [P, I64]),
+            "orcm_tri": (I32, [I32, I32, I32]),
+            "orcm_create": (P, [I64, P, P, P, P, P, P]),
+            "orcm_free": (None, [P]),
+            "orcm_set_params": (I32, [P, P, P, D, P, U64]),
+            "orcm_schedule_sublattice": (I32, [P] + [I32] * 6),
+            "orcm_schedule_blocks": (I32, [P] + [I32] * 9),
+            "orcm_parallel_steps": (I32, [P, I64]),
+            "orcm_run_histogram": (I32, [P, I64, P, P]),
+            "orcm_energy_full": (D, [P]),
+            "orcm_delta_e": (D, [P, I64, I32]),
+            "orcm_delta_e_full": (D, [P, I64, I32]),
+            "orcm_get_types": (None, [P, P]),
+            "orcm_set_types": (None, [P, P]),
+            "orcm_get_rho": (None, [P, P]),
+            "orcm_get_obs": (None, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -355,3 +373,131 @@ class System:
     def hybrid_cycles(self, n_cycles, n_md, n_mc):
         if lib().orc_hybrid_cycles(self.h, int(n_cycles), int(n_md), int(n_mc)):
             raise RuntimeError("oracle: hybrid cycle failed")
+
+
+# ------------------------------------------------------------ multicomponent
+MULTI_MAX_K = 4
+
+
+class MultiEamIn(C.Structure):
+    _fields_ = [("K", C.c_int32), ("nr", C.c_int32), ("dr", C.c_double), ("nrho", C.c_int32),
+                ("drho", C.c_double), ("rc", C.c_double),
+                ("pair", C.c_void_p * 10), ("dpair", C.c_void_p * 10),
+                ("dens", C.c_void_p * 4), ("ddens", C.c_void_p * 4),
+                ("embed", C.c_void_p * 4), ("dembed", C.c_void_p * 4)]
+
+
+class MultiObs(C.Structure):
+    _fields_ = [("n_sites", C.c_int64), ("K", C.c_int32), ("pad", C.c_int32), ("n", C.c_int64 * 4),
+                ("energy", C.c_double), ("steps", C.c_int64), ("trials", C.c_int64),
+                ("local_accepts", C.c_int64), ("global_trials", C.c_int64), ("global_accepts", C.c_int64),
+                ("flips", C.c_int64), ("near_ties", C.c_int64), ("sum_c", C.c_double * 4),
+                ("sum_c2", C.c_double * 4)]
+
+
+class MultiSystem:
+    """K-species VC-SGC system held by the multicomponent oracle.  tables:
+    an EAMTables with K = len(tables.dens) species and K (K + 1) / 2 pair
+    tables in the order (0,0), (0,1), ..., (K-1,K-1)."""
+
+    def __init__(self, lattice, types, tables):
+        keep = []
+        x, y, z = (np.ascontiguousarray(v, dtype=np.float64) for v in (lattice.x, lattice.y, lattice.z))
+        box = np.ascontiguousarray(lattice.box, dtype=np.float64)
+        t = np.ascontiguousarray(types, dtype=np.uint8)
+        K = len(tables.dens)
+        assert len(tables.pair) == K * (K + 1) // 2
+        e = MultiEamIn()
+        e.K, e.nr, e.dr, e.nrho, e.drho, e.rc = K, tables.nr, tables.dr, tables.nrho, tables.drho, tables.rc
+
+        def ptr(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data
+
+        for q in range(len(tables.pair)):
+            e.pair[q] = ptr(tables.pair[q])
+            e.dpair[q] = ptr(tables.dpair[q])
+        for q in range(K):
+            e.dens[q] = ptr(tables.dens[q])
+            e.ddens[q] = ptr(tables.ddens[q])
+            e.embed[q] = ptr(tables.embed[q])
+            e.dembed[q] = ptr(tables.dembed[q])
+        self.n = int(x.shape[0])
+        self.K = K
+        self.h = lib().orcm_create(self.n, _p(x), _p(y), _p(z), _p(box), _p(t), C.byref(e))
+        if not self.h:
+            raise ValueError("oracle: invalid multicomponent system")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orcm_free(self.h)
+            self.h = None
+
+    def set_params(self, phi, kappa, T, c0=None, seed=1):
+        """phi, kappa, c0: one value per solute species 1..K-1 (c0 < 0 or
+        None: the current concentration)."""
+        m = self.K - 1
+        ph = np.ascontiguousarray(np.broadcast_to(phi, (m,)), dtype=np.float64)
+        ka = np.ascontiguousarray(np.broadcast_to(kappa, (m,)), dtype=np.float64)
+        cc = np.ascontiguousarray(np.broadcast_to(-1.0 if c0 is None else c0, (m,)), dtype=np.float64)
+        if lib().orcm_set_params(self.h, _p(ph), _p(ka), float(T), _p(cc), int(seed) & (2**64 - 1)):
+            raise ValueError("oracle: bad parameters")
+
+    def schedule_sublattice(self, cells, period=(4, 4, 4)):
+        if lib().orcm_schedule_sublattice(self.h, *cells, *period):
+            raise ValueError("oracle: sublattice schedule does not divide the lattice")
+
+    def schedule_blocks(self, cells, block, colours=(2, 2, 2)):
+        if lib().orcm_schedule_blocks(self.h, *cells, *block, *colours):
+            raise ValueError("oracle: block schedule does not divide the lattice")
+
+    def parallel_steps(self, n):
+        if lib().orcm_parallel_steps(self.h, int(n)):
+            raise RuntimeError("oracle: no schedule")
+
+    def run_histogram(self, n_steps):
+        """Joint histogram of the solute counts (shape (N+1,)*(K-1), axis q
+        = species q+1) after each of n_steps steps, and the mean energy."""
+        nb = (self.n + 1) ** (self.K - 1)
+        hist = np.zeros(nb, dtype=np.int64)
+        se = C.c_double(0.0)
+        if lib().orcm_run_histogram(self.h, int(n_steps), _p(hist), C.byref(se)):
+            raise RuntimeError("oracle: no schedule")
+        # bin = n_1 + (N+1) (n_2 + (N+1) n_3): C order puts n_1 last
+        return hist.reshape((self.n + 1,) * (self.K - 1)).transpose(), se.value / max(1, n_steps)
+
+    def energy_full(self):
+        return lib().orcm_energy_full(self.h)
+
+    def delta_e(self, i, b):
+        return lib().orcm_delta_e(self.h, int(i), int(b))
+
+    def delta_e_full(self, i, b):
+        return lib().orcm_delta_e_full(self.h, int(i), int(b))
+
+    @property
+    def types(self):
+        out = np.zeros(self.n, dtype=np.uint8)
+        lib().orcm_get_types(self.h, _p(out))
+        return out
+
+    def set_types(self, t):
+        tt = np.ascontiguousarray(t, dtype=np.uint8)
+        assert tt.shape == (self.n,) and tt.max(initial=0) < self.K
+        lib().orcm_set_types(self.h, _p(tt))
+
+    def rho(self):
+        out = np.zeros(self.n)
+        lib().orcm_get_rho(self.h, _p(out))
+        return out
+
+    def obs(self):
+        o = MultiObs()
+        lib().orcm_get_obs(self.h, C.byref(o))
+        K = o.K
+        return {"n_sites": o.n_sites, "K": K, "n": [o.n[a] for a in range(K)], "energy": o.energy,
+                "steps": o.steps, "trials": o.trials, "local_accepts": o.local_accepts,
+                "global_trials": o.global_trials, "global_accepts": o.global_accepts, "flips": o.flips,
+                "near_ties": o.near_ties, "sum_c": [o.sum_c[a] for a in range(K)],
+                "sum_c2": [o.sum_c2[a] for a in range(K)]}

@@ -22,6 +22,7 @@
  * neighbour by neighbour from the spline tables, in slot order.
  */
 #include "vcsgc_oracle.h"
+#include "orc_internal.h"
 
 #include <math.h>
 #include <stdlib.h>
@@ -30,12 +31,6 @@
 #define KB_EV 8.617333262e-5       /* Boltzmann constant, eV/K */
 #define FTM 9.648533212331e-3      /* eV/(Angstrom amu) -> Angstrom/fs^2 */
 
-typedef struct {
-  int n;
-  double h;
-  double* y;
-  double* m; /* knot derivatives */
-} spline_t;
 
 typedef struct {
   int64_t j;
@@ -130,7 +125,7 @@ static void draw(const orc_sys* s, uint64_t k, uint32_t d, uint32_t tag, uint32_
 /* ---------------------------------------------------------------- spline */
 /* Cubic Hermite interpolation on a uniform grid with given (or central
  * finite-difference) knot derivatives. */
-static int spline_init(spline_t* sp, int n, double h, const double* y, const double* m) {
+int orc_hermite_init(spline_t* sp, int n, double h, const double* y, const double* m) {
   sp->n = n;
   sp->h = h;
   sp->y = (double*)malloc(sizeof(double) * n);
@@ -149,7 +144,7 @@ static int spline_init(spline_t* sp, int n, double h, const double* y, const dou
   return 0;
 }
 
-static int spline_eval(const spline_t* sp, double x, double* v, double* dv) {
+int orc_hermite_eval(const spline_t* sp, double x, double* v, double* dv) {
   double xmax = (sp->n - 1) * sp->h;
   if (!(x >= 0.0) || x > xmax) return -1;
   int j = (int)floor(x / sp->h);
@@ -172,23 +167,23 @@ static int spline_eval(const spline_t* sp, double x, double* v, double* dv) {
 
 int orc_spline(const orc_sys* s, int which, double x, double* v, double* dv) {
   if (which < 0 || which > 6) return -1;
-  return spline_eval(&s->sp[which], x, v, dv);
+  return orc_hermite_eval(&s->sp[which], x, v, dv);
 }
 
 /* table accessors: abort-free, out-of-range yields NaN so it shows up */
 static double phi_ab(const orc_sys* s, int a, int b, double r) {
   double v;
-  if (spline_eval(&s->sp[a + b], r, &v, NULL)) return NAN;
+  if (orc_hermite_eval(&s->sp[a + b], r, &v, NULL)) return NAN;
   return v;
 }
 static double dens_of(const orc_sys* s, int a, double r) {
   double v;
-  if (spline_eval(&s->sp[3 + a], r, &v, NULL)) return NAN;
+  if (orc_hermite_eval(&s->sp[3 + a], r, &v, NULL)) return NAN;
   return v;
 }
 static double embed_of(const orc_sys* s, int a, double rho) {
   double v;
-  if (spline_eval(&s->sp[5 + a], rho, &v, NULL)) return NAN;
+  if (orc_hermite_eval(&s->sp[5 + a], rho, &v, NULL)) return NAN;
   return v;
 }
 
@@ -447,10 +442,10 @@ orc_sys* orc_create(int64_t n, const double* x, const double* y, const double* z
   s->rc = eam->rc;
   s->brute = brute;
   for (int p = 0; p < 3; ++p)
-    if (spline_init(&s->sp[p], eam->nr, eam->dr, eam->pair[p], eam->dpair[p])) { orc_free(s); return NULL; }
+    if (orc_hermite_init(&s->sp[p], eam->nr, eam->dr, eam->pair[p], eam->dpair[p])) { orc_free(s); return NULL; }
   for (int a = 0; a < 2; ++a) {
-    if (spline_init(&s->sp[3 + a], eam->nr, eam->dr, eam->dens[a], eam->ddens[a])) { orc_free(s); return NULL; }
-    if (spline_init(&s->sp[5 + a], eam->nrho, eam->drho, eam->embed[a], eam->dembed[a])) { orc_free(s); return NULL; }
+    if (orc_hermite_init(&s->sp[3 + a], eam->nr, eam->dr, eam->dens[a], eam->ddens[a])) { orc_free(s); return NULL; }
+    if (orc_hermite_init(&s->sp[5 + a], eam->nrho, eam->drho, eam->embed[a], eam->dembed[a])) { orc_free(s); return NULL; }
   }
   if (build_neighbours(s)) { orc_free(s); return NULL; }
   compute_rho(s);
@@ -1086,7 +1081,7 @@ void orc_forces(orc_sys* s, double* fx, double* fy, double* fz) {
   double* dF = (double*)malloc(sizeof(double) * s->n);
   for (int64_t i = 0; i < s->n; ++i) {
     double v;
-    spline_eval(&s->sp[5 + s->t[i]], s->rho[i], NULL, &v);
+    orc_hermite_eval(&s->sp[5 + s->t[i]], s->rho[i], NULL, &v);
     dF[i] = v;
   }
   for (int64_t i = 0; i < s->n; ++i) {
@@ -1096,9 +1091,9 @@ void orc_forces(orc_sys* s, double* fx, double* fy, double* fz) {
       const nbr_t* e = &s->nb[k];
       int tj = s->t[e->j];
       double dphi, dfj, dfi;
-      spline_eval(&s->sp[ti + tj], e->r, NULL, &dphi);
-      spline_eval(&s->sp[3 + tj], e->r, NULL, &dfj);
-      spline_eval(&s->sp[3 + ti], e->r, NULL, &dfi);
+      orc_hermite_eval(&s->sp[ti + tj], e->r, NULL, &dphi);
+      orc_hermite_eval(&s->sp[3 + tj], e->r, NULL, &dfj);
+      orc_hermite_eval(&s->sp[3 + ti], e->r, NULL, &dfi);
       double g = dphi + dF[i] * dfj + dF[e->j] * dfi;
       for (int a = 0; a < 3; ++a) f[a] += g * e->d[a] / e->r;
     }

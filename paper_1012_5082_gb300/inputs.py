@@ -153,11 +153,13 @@ def eam_tables(p: EAMParams | None = None) -> EAMTables:
     drho = p.rho_max / (p.nrho - 1)
     rho = np.arange(p.nrho, dtype=np.float64) * drho
     pair, dpair, dens, ddens, emb, demb = [], [], [], [], [], []
-    for q in range(3):
+    K = len(p.A_embed)
+    assert len(p.pair_scale) == K * (K + 1) // 2 and len(p.dens_scale) == K
+    for q in range(len(p.pair_scale)):
         v, dv = p.pair(q, r)
         pair.append(np.ascontiguousarray(v))
         dpair.append(np.ascontiguousarray(dv))
-    for t in range(2):
+    for t in range(K):
         v, dv = p.dens(t, r)
         dens.append(np.ascontiguousarray(v))
         ddens.append(np.ascontiguousarray(dv))
@@ -168,6 +170,31 @@ def eam_tables(p: EAMParams | None = None) -> EAMTables:
         demb.append(np.ascontiguousarray(dv))
     return EAMTables(rc=p.rc, nr=p.nr, dr=dr, nrho=p.nrho, drho=drho, pair=pair, dpair=dpair,
                      dens=dens, ddens=ddens, embed=emb, dembed=demb)
+
+
+def multi_eam_params(K: int, dens_scale=None, **kw) -> EAMParams:
+    """K-species form of the synthetic EAM (K = 2..4): the binary's A and B
+    plus C and D.  Pair scales in the order (0,0), (0,1), ..., (K-1,K-1);
+    for K = 2 the binary parameters exactly."""
+    scale = {(0, 0): 1.0, (0, 1): 0.85, (1, 1): 0.9, (0, 2): 0.8, (1, 2): 0.75, (2, 2): 0.95,
+             (0, 3): 0.9, (1, 3): 0.8, (2, 3): 0.85, (3, 3): 1.05}
+    A = (1.8, 1.5, 1.65, 1.95)
+    pairs = tuple(scale[(a, b)] for a in range(K) for b in range(a, K))
+    ds = tuple(dens_scale) if dens_scale is not None else (1.0,) * K
+    return EAMParams(pair_scale=pairs, A_embed=A[:K], dens_scale=ds, **kw)
+
+
+def multi_random_types(n: int, counts, seed: int) -> np.ndarray:
+    """Species 0 everywhere except counts[q] sites of species q + 1, placed
+    uniformly at random (a seeded permutation)."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n)
+    t = np.zeros(n, dtype=np.uint8)
+    k = 0
+    for q, c in enumerate(counts):
+        t[perm[k:k + c]] = q + 1
+        k += c
+    return t
 
 
 # ------------------------------------------------- Ising lattice gas
