@@ -381,6 +381,97 @@ const char* vcsgc_last_error(void* ctx);
 /* Release the context and all its device memory.  NULL is a no-op. */
 void vcsgc_free(void* ctx);
 
+/* ------------------------------------------------------ multicomponent
+ * K-species form (2 <= K <= 4) of the parallel transmutation step on a
+ * rigid BCC lattice.  The paper derives the method for binary alloys and
+ * notes that more species follow directly (Sec. II); this form keeps one
+ * variance constraint per solute species alpha = 1..K-1 (species 0 is the
+ * solvent):
+ *   pi_V ~ exp{-beta [U + sum_alpha (phi_alpha n_alpha + kappa_p,alpha n_alpha^2)]},
+ *   kappa_p,alpha = kappa_alpha kB T / N (kappa dimensionless).
+ * A trial at site i of species a proposes b uniformly among the other K-1
+ * species (Philox (step, domain rank, 6)); the local stage (Eq.
+ * trans_vcsgc_par1 per solute) accepts with
+ *   min{1, exp[-beta (dE_i + dmu0_b - dmu0_a)]},
+ *   dmu0_alpha = phi_alpha + 2 kappa_p,alpha N c0_alpha, dmu0_0 = 0,
+ * and the global stage (Eq. trans_vcsgc_par2 per solute) with
+ *   min{1, exp[-beta sum_alpha kappa_p,alpha dn_alpha (dn_alpha + 2 (n_alpha - N c0_alpha))]}.
+ * Schedule: the period-q sublattice (colour (cx mod qx, cy mod qy, cz mod
+ * qz, basis), every site of the colour trialled at once); q a > 2 r_c is
+ * required.  For K = 2 the chain is the binary one of vcsgc_init with the
+ * SUBLATTICE schedule. */
+#define VCSGC_MULTI_MAX_K 4
+
+/* EAM tables of K species, grids as for vcsgc_eam_tables: pair[p] for the
+ * unordered pair p = tri(a, b), a <= b, in the order (0,0), (0,1), ...,
+ * (0,K-1), (1,1), ..., (K-1,K-1); dens[a]; embed[a].  Derivative arrays may
+ * be NULL (central differences). */
+typedef struct {
+  int32_t K;
+  int32_t nr;
+  double dr;
+  int32_t nrho;
+  double drho;
+  double rc;
+  const double* pair[10];
+  const double* dpair[10];
+  const double* dens[4];
+  const double* ddens[4];
+  const double* embed[4];
+  const double* dembed[4];
+} vcsgc_multi_tables;
+
+typedef struct {
+  int64_t n_sites;
+  int32_t K;
+  int32_t pad;
+  int64_t n[4];           /* sites of each species */
+  double c[4];
+  double energy;          /* incrementally tracked total energy (eV) */
+  double energy_per_atom;
+  int64_t steps, trials, local_accepts, global_trials, global_accepts, flips, near_ties;
+  double acc_local, acc_global;
+  double mean_c[4];       /* <c_alpha> over steps */
+  double var_c[4];
+  double dmu_est[4];      /* phi_alpha + 2 kappa_p,alpha N <c_alpha> (Eq. gforce per solute) */
+  double kappa_p[4];      /* eV */
+  double dmu0[4];         /* eV */
+  double sweeps;          /* trials / N */
+} vcsgc_multi_obs;
+
+/* Create a K-species context of n_replicas copies of one rigid lattice
+ * (lattice->kind 0; each edge at least 2 r_c long).  HOST inputs, copied:
+ * types[n_replicas][N] (values < K), phi, kappa, c0 [n_replicas][K-1]
+ * (replica-major; c0 < 0: the replica's initial concentration of that
+ * species), T[n_replicas], seed_r[n_replicas] (Philox keys; NULL: r + 1).
+ * period[3] = (qx, qy, qz) divides the cell counts.  stream: a cudaStream_t
+ * or NULL (the context makes its own); device < 0: the current device.
+ * Errors: INVALID_ARG (sizes, species, K, period), SCHEDULE (q a <= 2 r_c),
+ * NOMEM, CUDA, TABLE_RANGE (a shell outside the grids). */
+int vcsgc_multi_init(void** out, const vcsgc_lattice* lattice, const uint8_t* types, const vcsgc_multi_tables* tables,
+                     int32_t n_replicas, const double* phi, const double* kappa, const double* T, const double* c0,
+                     const uint64_t* seed_r, const int32_t period[3], void* stream, int32_t device);
+/* n sweeps (N / (sites per colour) colour steps each) or n colour steps on
+ * every replica; asynchronous on the context's stream.  Errors: CUDA. */
+int vcsgc_multi_sweep(void* m, int64_t n);
+int vcsgc_multi_steps(void* m, int64_t n);
+int vcsgc_multi_steps_per_sweep(void* m, int64_t* out);
+/* Synchronises; fills *out for replica r.  Errors: INVALID_ARG, CUDA, and
+ * the device error bits (TABLE_RANGE, NONFINITE). */
+int vcsgc_multi_observables(void* m, int32_t r, vcsgc_multi_obs* out);
+/* Species of replica r, HOST buffers of N bytes.  set_types recomputes the
+ * densities, counts and energy and keeps the counters.  Errors: INVALID_ARG
+ * (r, a value >= K), CUDA. */
+int vcsgc_multi_get_types(void* m, int32_t r, uint8_t* out);
+int vcsgc_multi_set_types(void* m, int32_t r, const uint8_t* in);
+/* dE of site sites[q] becoming species to[q] in replica r (HOST arrays of
+ * n; out HOST).  Errors: INVALID_ARG, CUDA, device error bits. */
+int vcsgc_multi_delta_e(void* m, int32_t r, const int64_t* sites, const uint8_t* to, int64_t n, double* out);
+/* Full energy of replica r from its species and densities (eV). */
+int vcsgc_multi_energy(void* m, int32_t r, double* out);
+const char* vcsgc_multi_last_error(void* m);
+void vcsgc_multi_free(void* m);
+
 #ifdef __cplusplus
 }
 #endif

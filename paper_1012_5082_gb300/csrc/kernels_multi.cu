@@ -1,0 +1,317 @@
+// Multicomponent colour step (K <= 4 species, rigid BCC lattice, period-q
+// sublattice schedule).  The paper works the method out for a binary alloy
+// and notes that the generalisation to more species is straightforward
+// (Sec. II); the form built here keeps one variance constraint per solute
+// species alpha = 1..K-1:
+//   pi_V ~ exp{-beta [U + sum_alpha (phi_alpha n_alpha + kappa_p,alpha n_alpha^2)]}.
+// A trial at site i of species a proposes species b, uniform among the K-1
+// others.  Local stage (Eq. trans_vcsgc_par1 per solute):
+//   min{1, exp[-beta (dE_i + dmu0_b - dmu0_a)]},  dmu0_0 = 0;
+// global stage (Eq. trans_vcsgc_par2 per solute):
+//   min{1, exp[-beta sum_alpha kappa_p,alpha dn_alpha (dn_alpha + 2 (n_alpha - n0_alpha))]}.
+//
+// One thread per trial.  dE on the rigid lattice: the pair part from the
+// per-shell neighbour counts by species (four byte counters in one word per
+// shell) against the shell table phi_ab(r_s) staged in shared memory; the
+// own embedding change F_b(rho_i) - F_a(rho_i); and, where the densities
+// differ between species, the re-embedding of every neighbour j,
+// F_{t_j}(rho_j + f_b(r_s) - f_a(r_s)) - F_{t_j}(rho_j).  Two launches per
+// colour step: propose (local stage, compaction of the accepts, per-solute
+// dn by warp reductions; the last block of each replica takes the global
+// decision) and commit (species and density scatter of an accepted step).
+#include "multi.cuh"
+
+namespace vcsgc {
+
+__host__ __device__ __forceinline__ int multi_tri(int K, int a, int b) {
+  if (a > b) {
+    const int q = a;
+    a = b;
+    b = q;
+  }
+  return a * K - a * (a - 1) / 2 + (b - a);
+}
+
+__global__ void k_multi_shell_tables(const Spline* pair, const Spline* dens, int K, const double* r_s, int n_sh,
+                                     double* V, double* Fd, unsigned* err) {
+  const int nv = n_sh * K * K;
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+    const int s = q / (K * K), a = (q / K) % K, b = q % K;
+    V[q] = spline_val(pair[multi_tri(K, a, b)], r_s[s], err);
+  }
+  for (int q = threadIdx.x; q < n_sh * K; q += blockDim.x) Fd[q] = spline_val(dens[q % K], r_s[q / K], err);
+}
+
+void launch_multi_shell_tables(const Spline* pair, const Spline* dens, int K, const double* r_s, int n_sh,
+                               double* V, double* Fd, unsigned* err, cudaStream_t st) {
+  k_multi_shell_tables<<<1, 128, 0, st>>>(pair, dens, K, r_s, n_sh, V, Fd, err);
+}
+
+// rho_i = sum_j f_{t_j}(r_ij)
+__global__ void k_multi_rho(MultiArgs a, int r0) {
+  const int r = r0 + blockIdx.y;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  double rho = 0.0;
+  for (int k = 0; k < a.n_off; ++k) {
+    const int4 h = a.off[k];
+    rho += a.Fd[h.w * a.K + ty[multi_nbr(a, (int)i, h)]];
+  }
+  a.rho[(long long)r * a.N + i] = rho;
+}
+
+void launch_multi_rho(const MultiArgs& a, int r0, int nrep, cudaStream_t st) {
+  const dim3 grid((unsigned)((a.N + 255) / 256), (unsigned)nrep);
+  k_multi_rho<<<grid, 256, 0, st>>>(a, r0);
+}
+
+// E = sum_i [1/2 sum_j phi_{t_i t_j}(r_ij) + F_{t_i}(rho_i)], block partials
+constexpr int MK_EBLOCK = 256;
+
+int multi_energy_blocks(long long N) { return (int)((N + MK_EBLOCK - 1) / MK_EBLOCK); }
+
+__global__ void __launch_bounds__(MK_EBLOCK) k_multi_energy(MultiArgs a, int r0, double* part) {
+  const int r = r0 + blockIdx.y;
+  const long long i = (long long)blockIdx.x * MK_EBLOCK + threadIdx.x;
+  double e = 0.0;
+  if (i < a.N) {
+    const uint8_t* ty = a.types + (long long)r * a.N;
+    const int ti = ty[i];
+    double pair = 0.0;
+    for (int k = 0; k < a.n_off; ++k) {
+      const int4 h = a.off[k];
+      pair += a.V[(h.w * a.K + ti) * a.K + ty[multi_nbr(a, (int)i, h)]];
+    }
+    e = 0.5 * pair + spline_val(a.embed[ti], a.rho[(long long)r * a.N + i], a.err);
+  }
+  __shared__ double sh[MK_EBLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < MK_EBLOCK / 32; ++w) t += sh[w];
+    part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+void launch_multi_energy(const MultiArgs& a, int r0, int nrep, double* part, cudaStream_t st) {
+  const dim3 grid((unsigned)multi_energy_blocks(a.N), (unsigned)nrep);
+  k_multi_energy<<<grid, MK_EBLOCK, 0, st>>>(a, r0, part);
+}
+
+// dE of site i (replica r) going from species ta to tb; sV, sFd: the shell
+// tables (shared or global)
+template <bool REEMBED>
+__device__ double multi_de(const MultiArgs& a, const double* sV, const double* sFd, int r, int i, int ta, int tb) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const double* rho = a.rho + (long long)r * a.N;
+  const int K = a.K;
+  double pair = 0.0, re = 0.0;
+  int k = 0;
+  for (int s = 0; s < a.n_sh; ++s) {
+    unsigned cnt = 0u;  // byte beta: neighbours of species beta in shell s
+    const double dfs = sFd[s * K + tb] - sFd[s * K + ta];
+    for (; k < a.n_off && a.off[k].w == s; ++k) {
+      const int j = multi_nbr(a, i, a.off[k]);
+      const int tj = ty[j];
+      cnt += 1u << (8 * tj);
+      if constexpr (REEMBED) {
+        const double rj = rho[j];
+        re += spline_val(a.embed[tj], rj + dfs, a.err) - spline_val(a.embed[tj], rj, a.err);
+      }
+    }
+    const double* Vb = sV + (s * K + tb) * K;
+    const double* Va = sV + (s * K + ta) * K;
+    for (int be = 0; be < K; ++be) pair += (double)((cnt >> (8 * be)) & 255u) * (Vb[be] - Va[be]);
+  }
+  const double ri = rho[i];
+  const double own = spline_val(a.embed[tb], ri, a.err) - spline_val(a.embed[ta], ri, a.err);
+  return pair + own + re;
+}
+
+__device__ __forceinline__ int multi_target(const MultiArgs& a, const MRepParams& p, long long step, int d, int ta) {
+  if (a.K == 2) return 1 - ta;
+  const uint4 w6 = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_SPECIES),
+                                 p.key);
+  return (ta + 1 + (int)below64(w6.x, w6.y, (uint64_t)(a.K - 1))) % a.K;
+}
+
+template <bool REEMBED>
+__global__ void __launch_bounds__(MK_BLOCK) k_multi_propose(MultiArgs a) {
+  __shared__ double sV[MK_MAX_SH * MK_MAX * MK_MAX];
+  __shared__ double sFd[MK_MAX_SH * MK_MAX];
+  __shared__ int s_red[MK_BLOCK / 32][MK_MAX + 1];
+  __shared__ double s_de[MK_BLOCK / 32];
+  __shared__ bool s_last;
+  const int K = a.K;
+  for (int q = threadIdx.x; q < a.n_sh * K * K; q += MK_BLOCK) sV[q] = a.V[q];
+  for (int q = threadIdx.x; q < a.n_sh * K; q += MK_BLOCK) sFd[q] = a.Fd[q];
+  __syncthreads();
+
+  const int r = blockIdx.y;
+  const MRepParams& p = a.rp[r];
+  const long long step = a.rs[r].step;
+  const uint4 wc = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0xFFFFFFFFu, TAG_STEP),
+                                 p.key);
+  const int c = (int)below64(wc.x, wc.y, (uint64_t)a.n_colours);
+  const int d = blockIdx.x * MK_BLOCK + threadIdx.x;
+  int acc = 0, tie = 0, ta = 0, tb = 0, site = -1;
+  double de = 0.0;
+  if (d < a.D) {
+    site = multi_site(a, c, d);
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL),
+                                  p.key);
+    ta = a.types[(long long)r * a.N + site];
+    tb = multi_target(a, p, step, d, ta);
+    de = multi_de<REEMBED>(a, sV, sFd, r, site, ta, tb);
+    if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
+    acc = metropolis(p.beta * (de + (p.dmu0[tb] - p.dmu0[ta])), top53(w.z, w.w), &tie) ? 1 : 0;
+  }
+  MStepAcc* A = a.acc + 2 * r + (int)(step & 1);
+  // compaction of the local accepts: one reservation per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, acc);
+  if (m) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&A->nacc, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (acc) a.pend[(long long)r * a.D + base + __popc(m & ((1u << lane) - 1u))] = make_int2(site, tb);
+  }
+  // per-solute dn, ties and the dE sum: warp, then block, then one atomic each
+#pragma unroll
+  for (int al = 1; al < MK_MAX; ++al) {
+    const int v = acc ? (int)(tb == al) - (int)(ta == al) : 0;
+    const int sv = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) s_red[warp][al] = sv;
+  }
+  const int st = __reduce_add_sync(0xffffffffu, tie);
+  double sd = acc ? de : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  if (lane == 0) {
+    s_red[warp][0] = st;
+    s_de[warp] = sd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tsum = 0;
+    double dsum = 0.0;
+    for (int w = 0; w < MK_BLOCK / 32; ++w) {
+      tsum += s_red[w][0];
+      dsum += s_de[w];
+    }
+    for (int al = 1; al < K; ++al) {
+      int v = 0;
+      for (int w = 0; w < MK_BLOCK / 32; ++w) v += s_red[w][al];
+      if (v) atomicAdd(&A->dn[al], v);
+    }
+    if (tsum) atomicAdd(&A->ties, tsum);
+    if (dsum != 0.0) atomicAdd(&A->sum_de, dsum);
+    __threadfence();
+    s_last = atomicAdd(&A->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  // global stage (last block of the replica): every block's sums are visible
+  __threadfence();
+  const int nacc = __ldcg(&A->nacc);
+  MRepState s = a.rs[r];
+  s.trials += a.D;
+  s.local_acc += nacc;
+  s.near_ties += __ldcg(&A->ties);
+  int accept = 0;
+  if (nacc > 0) {
+    s.global_trials++;
+    int dn[MK_MAX];
+    double Y = 0.0;
+    for (int al = 1; al < K; ++al) {
+      dn[al] = __ldcg(&A->dn[al]);
+      Y += p.beta * p.kappa_p[al] * (double)dn[al] * ((double)dn[al] + 2.0 * ((double)s.cnt[al] - p.n0[al]));
+    }
+    int gtie = 0;
+    accept = metropolis(Y, top53(wc.z, wc.w), &gtie) ? 1 : 0;
+    s.near_ties += gtie;
+    if (accept) {
+      s.global_acc++;
+      s.flips += nacc;
+      long long d0 = 0;
+      for (int al = 1; al < K; ++al) {
+        s.cnt[al] += dn[al];
+        d0 += dn[al];
+      }
+      s.cnt[0] -= d0;
+      s.energy += __ldcg(&A->sum_de);
+    }
+  }
+  A->accept = accept;
+  A->done = 0u;
+  s.steps++;
+  for (int al = 0; al < K; ++al) {
+    const double cc = (double)s.cnt[al] / (double)a.N;
+    s.sum_c[al] += cc;
+    s.sum_c2[al] += cc * cc;
+  }
+  s.step++;
+  a.rs[r] = s;
+}
+
+// apply an accepted step: species, and the density change of the neighbours
+template <bool REEMBED>
+__global__ void __launch_bounds__(MK_BLOCK) k_multi_commit(MultiArgs a) {
+  const int r = blockIdx.y;
+  const long long step = a.rs[r].step - 1;  // the step the propose launch decided
+  const MStepAcc* A = a.acc + 2 * r + (int)(step & 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // the other buffer takes the next step's sums
+    MStepAcc* B = a.acc + 2 * r + (int)((step + 1) & 1);
+    for (int al = 0; al < MK_MAX; ++al) B->dn[al] = 0;
+    B->nacc = 0;
+    B->ties = 0;
+    B->accept = 0;
+    B->sum_de = 0.0;
+  }
+  const int q = blockIdx.x * MK_BLOCK + threadIdx.x;
+  if (!A->accept || q >= A->nacc) return;
+  const int2 e = a.pend[(long long)r * a.D + q];
+  uint8_t* ty = a.types + (long long)r * a.N;
+  const int ta = ty[e.x], tb = e.y;
+  ty[e.x] = (uint8_t)tb;
+  if constexpr (REEMBED) {
+    double* rho = a.rho + (long long)r * a.N;
+    for (int k = 0; k < a.n_off; ++k) {
+      const int4 h = a.off[k];
+      rho[multi_nbr(a, e.x, h)] += a.Fd[h.w * a.K + tb] - a.Fd[h.w * a.K + ta];
+    }
+  }
+}
+
+void launch_multi_step(const MultiArgs& a, cudaStream_t st) {
+  const dim3 grid((unsigned)((a.D + MK_BLOCK - 1) / MK_BLOCK), (unsigned)a.R);
+  if (a.reembed) {
+    k_multi_propose<true><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_commit<true><<<grid, MK_BLOCK, 0, st>>>(a);
+  } else {
+    k_multi_propose<false><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_commit<false><<<grid, MK_BLOCK, 0, st>>>(a);
+  }
+}
+
+__global__ void k_multi_delta_e(MultiArgs a, int r, const long long* sites, const uint8_t* to, int n, double* out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int i = (int)sites[q];
+  const int ta = a.types[(long long)r * a.N + i], tb = to[q];
+  out[q] = ta == tb ? 0.0
+                    : (a.reembed ? multi_de<true>(a, a.V, a.Fd, r, i, ta, tb) : multi_de<false>(a, a.V, a.Fd, r, i, ta, tb));
+}
+
+void launch_multi_delta_e(const MultiArgs& a, int r, const long long* sites, const uint8_t* to, int n, double* out,
+                          cudaStream_t st) {
+  if (n <= 0) return;
+  k_multi_delta_e<<<(n + 127) / 128, 128, 0, st>>>(a, r, sites, to, n, out);
+}
+
+}  // namespace vcsgc

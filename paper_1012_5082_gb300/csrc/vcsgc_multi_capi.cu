@@ -1,0 +1,469 @@
+// C ABI of the multicomponent colour step (declarations and the method's
+// statement in include/vcsgc.h).  One context holds R replicas of one rigid
+// BCC lattice with K <= 4 species; every colour step is a propose and a
+// commit launch, captured as CUDA graphs of 64 steps.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "multi.cuh"
+#include "vcsgc.h"
+
+namespace vcsgc {
+namespace {
+
+struct Multi {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int R = 1, K = 2;
+  int nx = 0, ny = 0, nz = 0;
+  double a = 0, rc = 0;
+  long long N = 0;
+  long long steps_per_sweep = 1;
+  MultiArgs args{};
+  std::vector<void*> allocs;
+  std::vector<MRepParams> h_rp;
+  double* part = nullptr;
+  int n_part = 0;
+  long long* d_sites = nullptr;
+  uint8_t* d_to = nullptr;
+  double* d_out = nullptr;
+  long long buf_n = 0;
+  cudaGraphExec_t graph = nullptr;
+};
+
+#define MCK(call)                                                                      \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      m->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      return VCSGC_ERR_CUDA;                                                           \
+    }                                                                                  \
+  } while (0)
+#define MTRY(expr)                     \
+  do {                                 \
+    int rc_ = (expr);                  \
+    if (rc_ != VCSGC_OK) return rc_;   \
+  } while (0)
+
+int mfail(Multi* m, int code, const std::string& msg) {
+  m->err = msg;
+  return code;
+}
+
+template <typename T>
+int malloc_dev(Multi* m, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(T) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return mfail(m, VCSGC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  m->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return VCSGC_OK;
+}
+
+int device_error(Multi* m) {
+  unsigned e = 0;
+  MCK(cudaMemcpyAsync(&e, m->args.err, sizeof(unsigned), cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  if (!e) return VCSGC_OK;
+  MCK(cudaMemsetAsync(m->args.err, 0, sizeof(unsigned), m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  if (e & ERRF_TABLE) return mfail(m, VCSGC_ERR_TABLE_RANGE, "r or rho outside the EAM table grid");
+  return mfail(m, VCSGC_ERR_NONFINITE, "non-finite energy difference");
+}
+
+// Spline of n samples on the grid j h, coefficients built on the device
+int make_spline(Multi* m, const double* y, const double* dy, int n, double h, Spline& s) {
+  double *yd = nullptr, *md = nullptr;
+  Cubic* c = nullptr;
+  MTRY(malloc_dev(m, &yd, n));
+  MCK(cudaMemcpyAsync(yd, y, sizeof(double) * n, cudaMemcpyHostToDevice, m->st));
+  if (dy) {
+    MTRY(malloc_dev(m, &md, n));
+    MCK(cudaMemcpyAsync(md, dy, sizeof(double) * n, cudaMemcpyHostToDevice, m->st));
+  }
+  MTRY(malloc_dev(m, &c, n - 1));
+  launch_spline_coeffs(yd, md, n, h, c, m->st);
+  MCK(cudaGetLastError());
+  s.c = c;
+  s.inv_h = 1.0 / h;
+  s.xmax = (n - 1) * h;
+  s.n_int = n - 1;
+  return VCSGC_OK;
+}
+
+// energy of replica r from its species and densities (compensated sum of
+// the block partials)
+int energy_of(Multi* m, int r, double* out) {
+  launch_multi_energy(m->args, r, 1, m->part, m->st);
+  MCK(cudaGetLastError());
+  std::vector<double> h(m->n_part);
+  MCK(cudaMemcpyAsync(h.data(), m->part, sizeof(double) * m->n_part, cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  MTRY(device_error(m));
+  double s = 0.0, c = 0.0;
+  for (double v : h) {
+    const double t = s + v;
+    c += std::fabs(s) >= std::fabs(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+  }
+  *out = s + c;
+  return VCSGC_OK;
+}
+
+// densities, counts and energy of replica r from host species t
+int load_replica(Multi* m, int r, const uint8_t* t, bool reset_counters) {
+  for (long long i = 0; i < m->N; ++i)
+    if (t[i] >= m->K) return mfail(m, VCSGC_ERR_INVALID_ARG, "species value >= K");
+  MCK(cudaMemcpyAsync(m->args.types + (long long)r * m->N, t, m->N, cudaMemcpyHostToDevice, m->st));
+  launch_multi_rho(m->args, r, 1, m->st);
+  MCK(cudaGetLastError());
+  double e = 0.0;
+  MTRY(energy_of(m, r, &e));
+  MRepState s{};
+  if (!reset_counters) {
+    MCK(cudaMemcpyAsync(&s, m->args.rs + r, sizeof(MRepState), cudaMemcpyDeviceToHost, m->st));
+    MCK(cudaStreamSynchronize(m->st));
+  }
+  for (int al = 0; al < MK_MAX; ++al) s.cnt[al] = 0;
+  for (long long i = 0; i < m->N; ++i) s.cnt[t[i]]++;
+  s.energy = e;
+  MCK(cudaMemcpyAsync(m->args.rs + r, &s, sizeof(MRepState), cudaMemcpyHostToDevice, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  return VCSGC_OK;
+}
+
+int run_steps(Multi* m, long long n) {
+  const int G = 64;
+  if (n >= G && !m->graph) {
+    cudaGraph_t g;
+    MCK(cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < G; ++q) launch_multi_step(m->args, m->st);
+    cudaError_t e1 = cudaGetLastError();
+    MCK(cudaStreamEndCapture(m->st, &g));
+    if (e1 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return mfail(m, VCSGC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e1));
+    }
+    cudaError_t e2 = cudaGraphInstantiate(&m->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return mfail(m, VCSGC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(e2));
+  }
+  for (; n >= G; n -= G) MCK(cudaGraphLaunch(m->graph, m->st));
+  for (; n > 0; --n) launch_multi_step(m->args, m->st);
+  MCK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
+void destroy(Multi* m) {
+  if (!m) return;
+  if (m->st) cudaStreamSynchronize(m->st);
+  if (m->graph) cudaGraphExecDestroy(m->graph);
+  for (void* p : m->allocs) cudaFree(p);
+  if (m->own_stream && m->st) cudaStreamDestroy(m->st);
+  delete m;
+}
+
+thread_local std::string g_init_err;
+
+int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_multi_tables* T, int R,
+         const double* phi, const double* kappa, const double* Tk, const double* c0, const uint64_t* seed_r,
+         const int32_t period[3], void* stream, int device) {
+  if (!L || !types || !T || !phi || !kappa || !Tk || !c0 || !period || R < 1)
+    return mfail(m, VCSGC_ERR_INVALID_ARG, "null argument or n_replicas < 1");
+  if (L->kind != 0) return mfail(m, VCSGC_ERR_INVALID_ARG, "the multicomponent form needs a rigid lattice (kind 0)");
+  if (T->K < 2 || T->K > MK_MAX) return mfail(m, VCSGC_ERR_INVALID_ARG, "K must be 2..4");
+  if (T->nr < 2 || T->nrho < 2 || !(T->dr > 0) || !(T->drho > 0) || !(T->rc > 0))
+    return mfail(m, VCSGC_ERR_INVALID_ARG, "bad table grid");
+  m->K = T->K;
+  m->R = R;
+  m->nx = L->nx;
+  m->ny = L->ny;
+  m->nz = L->nz;
+  m->a = L->a;
+  m->rc = T->rc;
+  if (m->nx < 1 || m->ny < 1 || m->nz < 1 || !(m->a > 0)) return mfail(m, VCSGC_ERR_INVALID_ARG, "bad lattice");
+  m->N = 2LL * m->nx * m->ny * m->nz;
+  if (m->N >= (1LL << 30)) return mfail(m, VCSGC_ERR_INVALID_ARG, "lattice too large");
+  const int n3[3] = {m->nx, m->ny, m->nz};
+  for (int q = 0; q < 3; ++q) {
+    if (period[q] < 1 || n3[q] % period[q]) return mfail(m, VCSGC_ERR_INVALID_ARG, "period does not divide the lattice");
+    if (n3[q] * m->a <= 2.0 * m->rc) return mfail(m, VCSGC_ERR_INVALID_ARG, "lattice edge not longer than 2 r_c");
+    if (n3[q] > period[q] && period[q] * m->a <= 2.0 * m->rc)
+      return mfail(m, VCSGC_ERR_SCHEDULE, "same-colour sublattice sites closer than 2 r_c");
+  }
+  if (device >= 0) MCK(cudaSetDevice(device));
+  MCK(cudaGetDevice(&m->device));
+  if (stream) {
+    m->st = static_cast<cudaStream_t>(stream);
+  } else {
+    MCK(cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking));
+    m->own_stream = true;
+  }
+  MultiArgs& a = m->args;
+  a.R = R;
+  a.K = m->K;
+  a.nx = m->nx;
+  a.ny = m->ny;
+  a.nz = m->nz;
+  a.N = m->N;
+  a.qx = period[0];
+  a.qy = period[1];
+  a.qz = period[2];
+  a.nxq = m->nx / a.qx;
+  a.nyq = m->ny / a.qy;
+  a.nzq = m->nz / a.qz;
+  a.n_colours = 2 * a.qx * a.qy * a.qz;
+  a.D = a.nxq * a.nyq * a.nzq;
+  m->steps_per_sweep = a.n_colours;
+  // neighbour offsets h (half-lattice units, all even or all odd) with
+  // (a/2)|h| < r_c, by |h|^2 then h; one shell per distinct |h|^2
+  struct Off {
+    int x, y, z, h2;
+  };
+  std::vector<Off> offs;
+  const int H = (int)std::floor(2.0 * m->rc / m->a) + 1;
+  for (int hx = -H; hx <= H; ++hx)
+    for (int hy = -H; hy <= H; ++hy)
+      for (int hz = -H; hz <= H; ++hz) {
+        if ((hx & 1) != (hy & 1) || (hy & 1) != (hz & 1)) continue;
+        const int h2 = hx * hx + hy * hy + hz * hz;
+        if (h2 == 0 || 0.5 * m->a * std::sqrt((double)h2) >= m->rc) continue;
+        offs.push_back({hx, hy, hz, h2});
+      }
+  std::sort(offs.begin(), offs.end(), [](const Off& p, const Off& q) {
+    if (p.h2 != q.h2) return p.h2 < q.h2;
+    if (p.x != q.x) return p.x < q.x;
+    if (p.y != q.y) return p.y < q.y;
+    return p.z < q.z;
+  });
+  if ((int)offs.size() > MK_MAX_OFF) return mfail(m, VCSGC_ERR_INVALID_ARG, "too many neighbours within r_c");
+  std::vector<double> r_s;
+  for (size_t k = 0; k < offs.size(); ++k) {
+    if (k == 0 || offs[k].h2 != offs[k - 1].h2) r_s.push_back(0.5 * m->a * std::sqrt((double)offs[k].h2));
+    a.off[k] = make_int4(offs[k].x, offs[k].y, offs[k].z, (int)r_s.size() - 1);
+  }
+  if ((int)r_s.size() > MK_MAX_SH) return mfail(m, VCSGC_ERR_INVALID_ARG, "too many neighbour shells within r_c");
+  a.n_off = (int)offs.size();
+  a.n_sh = (int)r_s.size();
+  // tables: splines, then the shell values phi_ab(r_s), f_a(r_s)
+  const int P = m->K * (m->K + 1) / 2;
+  std::vector<Spline> sp_pair(P), sp_dens(m->K);
+  for (int p = 0; p < P; ++p) {
+    if (!T->pair[p]) return mfail(m, VCSGC_ERR_INVALID_ARG, "missing pair table");
+    MTRY(make_spline(m, T->pair[p], T->dpair[p], T->nr, T->dr, sp_pair[p]));
+  }
+  for (int al = 0; al < m->K; ++al) {
+    if (!T->dens[al] || !T->embed[al]) return mfail(m, VCSGC_ERR_INVALID_ARG, "missing density or embedding table");
+    MTRY(make_spline(m, T->dens[al], T->ddens[al], T->nr, T->dr, sp_dens[al]));
+    MTRY(make_spline(m, T->embed[al], T->dembed[al], T->nrho, T->drho, a.embed[al]));
+  }
+  Spline *d_pair = nullptr, *d_dens = nullptr;
+  double *d_rs = nullptr, *V = nullptr, *Fd = nullptr;
+  MTRY(malloc_dev(m, &d_pair, P));
+  MTRY(malloc_dev(m, &d_dens, m->K));
+  MTRY(malloc_dev(m, &d_rs, r_s.size()));
+  MTRY(malloc_dev(m, &V, r_s.size() * m->K * m->K));
+  MTRY(malloc_dev(m, &Fd, r_s.size() * m->K));
+  MTRY(malloc_dev(m, &a.err, 1));
+  MCK(cudaMemsetAsync(a.err, 0, sizeof(unsigned), m->st));
+  MCK(cudaMemcpyAsync(d_pair, sp_pair.data(), sizeof(Spline) * P, cudaMemcpyHostToDevice, m->st));
+  MCK(cudaMemcpyAsync(d_dens, sp_dens.data(), sizeof(Spline) * m->K, cudaMemcpyHostToDevice, m->st));
+  MCK(cudaMemcpyAsync(d_rs, r_s.data(), sizeof(double) * r_s.size(), cudaMemcpyHostToDevice, m->st));
+  launch_multi_shell_tables(d_pair, d_dens, m->K, d_rs, a.n_sh, V, Fd, a.err, m->st);
+  MCK(cudaGetLastError());
+  a.V = V;
+  a.Fd = Fd;
+  std::vector<double> hFd(r_s.size() * m->K);
+  MCK(cudaMemcpyAsync(hFd.data(), Fd, sizeof(double) * hFd.size(), cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  MTRY(device_error(m));
+  a.reembed = 0;
+  for (int s = 0; s < a.n_sh; ++s)
+    for (int al = 1; al < m->K; ++al)
+      if (hFd[s * m->K + al] != hFd[s * m->K]) a.reembed = 1;
+  // state
+  MTRY(malloc_dev(m, &a.types, (size_t)R * m->N));
+  MTRY(malloc_dev(m, &a.rho, (size_t)R * m->N));
+  MRepParams* rp = nullptr;
+  MTRY(malloc_dev(m, &rp, R));
+  a.rp = rp;
+  MTRY(malloc_dev(m, &a.rs, R));
+  MTRY(malloc_dev(m, &a.acc, 2 * R));
+  MTRY(malloc_dev(m, &a.pend, (size_t)R * a.D));
+  m->n_part = multi_energy_blocks(m->N);
+  MTRY(malloc_dev(m, &m->part, m->n_part));
+  MCK(cudaMemsetAsync(a.acc, 0, sizeof(MStepAcc) * 2 * R, m->st));
+  MCK(cudaMemsetAsync(a.rs, 0, sizeof(MRepState) * R, m->st));
+  m->h_rp.resize(R);
+  const int S = m->K - 1;
+  for (int r = 0; r < R; ++r) {
+    const uint8_t* t = types + (long long)r * m->N;
+    MTRY(load_replica(m, r, t, true));
+    long long cnt[MK_MAX] = {0, 0, 0, 0};
+    for (long long i = 0; i < m->N; ++i) cnt[t[i]]++;
+    MRepParams& p = m->h_rp[r];
+    p = MRepParams{};
+    if (!(Tk[r] > 0)) return mfail(m, VCSGC_ERR_INVALID_ARG, "T must be > 0");
+    p.beta = 1.0 / (KB_EV * Tk[r]);
+    for (int al = 1; al < m->K; ++al) {
+      const double ph = phi[(long long)r * S + al - 1], ka = kappa[(long long)r * S + al - 1];
+      const double cc = c0[(long long)r * S + al - 1];
+      p.phi[al] = ph;
+      p.kappa_p[al] = ka * KB_EV * Tk[r] / (double)m->N;
+      p.n0[al] = (double)m->N * (cc < 0.0 ? (double)cnt[al] / (double)m->N : cc);
+      p.dmu0[al] = ph + 2.0 * p.kappa_p[al] * p.n0[al];
+    }
+    const uint64_t seed = seed_r ? seed_r[r] : (uint64_t)r + 1;
+    p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  }
+  MCK(cudaMemcpyAsync(rp, m->h_rp.data(), sizeof(MRepParams) * R, cudaMemcpyHostToDevice, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  return VCSGC_OK;
+}
+
+Multi* as_multi(void* h) { return static_cast<Multi*>(h); }
+
+}  // namespace
+}  // namespace vcsgc
+
+using namespace vcsgc;
+
+extern "C" {
+
+int vcsgc_multi_init(void** out, const vcsgc_lattice* lattice, const uint8_t* types, const vcsgc_multi_tables* tables,
+                     int32_t n_replicas, const double* phi, const double* kappa, const double* T, const double* c0,
+                     const uint64_t* seed_r, const int32_t period[3], void* stream, int32_t device) {
+  if (!out) return VCSGC_ERR_INVALID_ARG;
+  *out = nullptr;
+  Multi* m = new (std::nothrow) Multi();
+  if (!m) return VCSGC_ERR_NOMEM;
+  const int rc = init(m, lattice, types, tables, n_replicas, phi, kappa, T, c0, seed_r, period, stream, device);
+  if (rc != VCSGC_OK) {
+    g_init_err = m->err;
+    destroy(m);
+    return rc;
+  }
+  *out = m;
+  return VCSGC_OK;
+}
+
+int vcsgc_multi_steps(void* h, int64_t n) {
+  Multi* m = as_multi(h);
+  if (!m || n < 0) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  return run_steps(m, n);
+}
+
+int vcsgc_multi_sweep(void* h, int64_t n) {
+  Multi* m = as_multi(h);
+  if (!m || n < 0) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  return run_steps(m, n * m->steps_per_sweep);
+}
+
+int vcsgc_multi_steps_per_sweep(void* h, int64_t* out) {
+  Multi* m = as_multi(h);
+  if (!m || !out) return VCSGC_ERR_INVALID_ARG;
+  *out = m->steps_per_sweep;
+  return VCSGC_OK;
+}
+
+int vcsgc_multi_observables(void* h, int32_t r, vcsgc_multi_obs* o) {
+  Multi* m = as_multi(h);
+  if (!m || !o || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  MRepState s;
+  MCK(cudaMemcpyAsync(&s, m->args.rs + r, sizeof(MRepState), cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  MTRY(device_error(m));
+  const MRepParams& p = m->h_rp[r];
+  std::memset(o, 0, sizeof(*o));
+  o->n_sites = m->N;
+  o->K = m->K;
+  o->energy = s.energy;
+  o->energy_per_atom = s.energy / (double)m->N;
+  o->steps = s.steps;
+  o->trials = s.trials;
+  o->local_accepts = s.local_acc;
+  o->global_trials = s.global_trials;
+  o->global_accepts = s.global_acc;
+  o->flips = s.flips;
+  o->near_ties = s.near_ties;
+  o->acc_local = s.trials ? (double)s.local_acc / (double)s.trials : 0.0;
+  o->acc_global = s.global_trials ? (double)s.global_acc / (double)s.global_trials : 0.0;
+  o->sweeps = (double)s.trials / (double)m->N;
+  for (int al = 0; al < m->K; ++al) {
+    o->n[al] = s.cnt[al];
+    o->c[al] = (double)s.cnt[al] / (double)m->N;
+    o->mean_c[al] = s.steps ? s.sum_c[al] / (double)s.steps : o->c[al];
+    o->var_c[al] = s.steps ? std::max(0.0, s.sum_c2[al] / (double)s.steps - o->mean_c[al] * o->mean_c[al]) : 0.0;
+    o->kappa_p[al] = p.kappa_p[al];
+    o->dmu0[al] = p.dmu0[al];
+    o->dmu_est[al] = al ? p.phi[al] + 2.0 * p.kappa_p[al] * (double)m->N * o->mean_c[al] : 0.0;
+  }
+  return VCSGC_OK;
+}
+
+int vcsgc_multi_get_types(void* h, int32_t r, uint8_t* out) {
+  Multi* m = as_multi(h);
+  if (!m || !out || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  MCK(cudaMemcpyAsync(out, m->args.types + (long long)r * m->N, m->N, cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  return VCSGC_OK;
+}
+
+int vcsgc_multi_set_types(void* h, int32_t r, const uint8_t* in) {
+  Multi* m = as_multi(h);
+  if (!m || !in || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  return load_replica(m, r, in, false);
+}
+
+int vcsgc_multi_delta_e(void* h, int32_t r, const int64_t* sites, const uint8_t* to, int64_t n, double* out) {
+  Multi* m = as_multi(h);
+  if (!m || r < 0 || r >= m->R || n < 0 || (n > 0 && (!sites || !to || !out)) || n > (1LL << 30))
+    return VCSGC_ERR_INVALID_ARG;
+  for (int64_t q = 0; q < n; ++q)
+    if (sites[q] < 0 || sites[q] >= m->N || to[q] >= m->K) return mfail(m, VCSGC_ERR_INVALID_ARG, "site or species out of range");
+  if (n == 0) return VCSGC_OK;
+  MCK(cudaSetDevice(m->device));
+  if (n > m->buf_n) {
+    MTRY(malloc_dev(m, &m->d_sites, n));
+    MTRY(malloc_dev(m, &m->d_to, n));
+    MTRY(malloc_dev(m, &m->d_out, n));
+    m->buf_n = n;
+  }
+  MCK(cudaMemcpyAsync(m->d_sites, sites, sizeof(long long) * n, cudaMemcpyHostToDevice, m->st));
+  MCK(cudaMemcpyAsync(m->d_to, to, n, cudaMemcpyHostToDevice, m->st));
+  launch_multi_delta_e(m->args, r, m->d_sites, m->d_to, (int)n, m->d_out, m->st);
+  MCK(cudaGetLastError());
+  MCK(cudaMemcpyAsync(out, m->d_out, sizeof(double) * n, cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  return device_error(m);
+}
+
+int vcsgc_multi_energy(void* h, int32_t r, double* out) {
+  Multi* m = as_multi(h);
+  if (!m || !out || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  return energy_of(m, r, out);
+}
+
+const char* vcsgc_multi_last_error(void* h) {
+  Multi* m = as_multi(h);
+  return m ? m->err.c_str() : g_init_err.c_str();
+}
+
+void vcsgc_multi_free(void* h) { destroy(as_multi(h)); }
+
+}  // extern "C"

@@ -71,7 +71,10 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_autotune", "vcsgc_features", "vcsgc_mlp_create", "vcsgc_mlp_set_params",
            "vcsgc_mlp_get_params", "vcsgc_mlp_forward", "vcsgc_mlp_grad", "vcsgc_mlp_train",
            "vcsgc_mlp_last_error", "vcsgc_mlp_free", "vcsgc_set_surrogate", "vcsgc_observables_all",
-           "vcsgc_get_types_all", "vcsgc_set_types_all"]
+           "vcsgc_get_types_all", "vcsgc_set_types_all", "vcsgc_multi_init", "vcsgc_multi_sweep",
+           "vcsgc_multi_steps", "vcsgc_multi_steps_per_sweep", "vcsgc_multi_observables",
+           "vcsgc_multi_get_types", "vcsgc_multi_set_types", "vcsgc_multi_delta_e", "vcsgc_multi_energy",
+           "vcsgc_multi_last_error", "vcsgc_multi_free"]
 
 
 def lib():
@@ -121,6 +124,17 @@ def lib():
             "vcsgc_observables_all": (I32, [P, P]),
             "vcsgc_get_types_all": (I32, [P, P]),
             "vcsgc_set_types_all": (I32, [P, P]),
+            "vcsgc_multi_init": (I32, [C.POINTER(C.c_void_p), P, P, P, I32, P, P, P, P, P, P, P, I32]),
+            "vcsgc_multi_sweep": (I32, [P, I64]),
+            "vcsgc_multi_steps": (I32, [P, I64]),
+            "vcsgc_multi_steps_per_sweep": (I32, [P, P]),
+            "vcsgc_multi_observables": (I32, [P, I32, P]),
+            "vcsgc_multi_get_types": (I32, [P, I32, P]),
+            "vcsgc_multi_set_types": (I32, [P, I32, P]),
+            "vcsgc_multi_delta_e": (I32, [P, I32, P, P, I64, P]),
+            "vcsgc_multi_energy": (I32, [P, I32, P]),
+            "vcsgc_multi_last_error": (C.c_char_p, [P]),
+            "vcsgc_multi_free": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -570,3 +584,133 @@ class Batch(Context):
         out = np.zeros(self.sizes[replica], dtype=np.float64)
         _check(lib().vcsgc_get_rho(self.h, int(replica), _ptr(out)), self.h)
         return out
+
+
+# ------------------------------------------------------------ multicomponent
+class MultiTables(C.Structure):
+    _fields_ = [("K", C.c_int32), ("nr", C.c_int32), ("dr", C.c_double), ("nrho", C.c_int32),
+                ("drho", C.c_double), ("rc", C.c_double),
+                ("pair", C.c_void_p * 10), ("dpair", C.c_void_p * 10),
+                ("dens", C.c_void_p * 4), ("ddens", C.c_void_p * 4),
+                ("embed", C.c_void_p * 4), ("dembed", C.c_void_p * 4)]
+
+
+class MultiObs(C.Structure):
+    _fields_ = [("n_sites", C.c_int64), ("K", C.c_int32), ("pad", C.c_int32), ("n", C.c_int64 * 4),
+                ("c", C.c_double * 4), ("energy", C.c_double), ("energy_per_atom", C.c_double),
+                ("steps", C.c_int64), ("trials", C.c_int64), ("local_accepts", C.c_int64),
+                ("global_trials", C.c_int64), ("global_accepts", C.c_int64), ("flips", C.c_int64),
+                ("near_ties", C.c_int64), ("acc_local", C.c_double), ("acc_global", C.c_double),
+                ("mean_c", C.c_double * 4), ("var_c", C.c_double * 4), ("dmu_est", C.c_double * 4),
+                ("kappa_p", C.c_double * 4), ("dmu0", C.c_double * 4), ("sweeps", C.c_double)]
+
+
+class Multi:
+    """K-species (K <= 4) colour step on R replicas of one rigid BCC lattice
+    (vcsgc_multi_init).  tables: EAMTables with K = len(tables.dens) species
+    and K (K + 1) / 2 pair tables in the order (0,0), (0,1), ..., (K-1,K-1).
+    types: (R, N) or (N,) species; phi, kappa, c0: (R, K-1) or broadcastable;
+    T: (R,) or scalar."""
+
+    def __init__(self, lattice, types, tables, phi, kappa, T, *, c0=-1.0, seed_r=None, period=(4, 4, 4),
+                 n_replicas=None, stream=None, device=-1):
+        keep = []
+        K = len(tables.dens)
+        t = np.asarray(types, dtype=np.uint8)
+        R = n_replicas or (t.shape[0] if t.ndim == 2 else 1)
+        N = lattice.n
+        t = np.ascontiguousarray(np.broadcast_to(t.reshape(-1, N), (R, N)), dtype=np.uint8)
+        E = MultiTables()
+        E.K, E.nr, E.dr, E.nrho, E.drho, E.rc = K, tables.nr, tables.dr, tables.nrho, tables.drho, tables.rc
+
+        def ptr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data
+
+        for q in range(len(tables.pair)):
+            E.pair[q] = ptr(tables.pair[q])
+            E.dpair[q] = ptr(tables.dpair[q])
+        for q in range(K):
+            E.dens[q] = ptr(tables.dens[q])
+            E.ddens[q] = ptr(tables.ddens[q])
+            E.embed[q] = ptr(tables.embed[q])
+            E.dembed[q] = ptr(tables.dembed[q])
+        if lattice.cells is None:
+            raise ValueError("the multicomponent form needs a rigid lattice")
+        L = Lattice()
+        L.kind = 0
+        L.nx, L.ny, L.nz = lattice.cells
+        L.a = lattice.a
+        L.n = N
+        ph = np.ascontiguousarray(np.broadcast_to(phi, (R, K - 1)), dtype=np.float64)
+        ka = np.ascontiguousarray(np.broadcast_to(kappa, (R, K - 1)), dtype=np.float64)
+        cc = np.ascontiguousarray(np.broadcast_to(c0, (R, K - 1)), dtype=np.float64)
+        TT = np.ascontiguousarray(np.broadcast_to(T, (R,)), dtype=np.float64)
+        sr = None if seed_r is None else np.ascontiguousarray(seed_r, dtype=np.uint64)
+        per = np.ascontiguousarray(period, dtype=np.int32)
+        st = None if stream is None else getattr(stream, "cuda_stream", stream)
+        h = C.c_void_p()
+        rc = lib().vcsgc_multi_init(C.byref(h), C.byref(L), _ptr(t), C.byref(E), R, _ptr(ph), _ptr(ka), _ptr(TT),
+                                    _ptr(cc), _ptr(sr), _ptr(per), st, int(device))
+        if rc != OK:
+            msg = lib().vcsgc_multi_last_error(None)
+            raise VcsgcError(rc, msg.decode() if msg else "")
+        self.h = h
+        self.K, self.R, self.n = K, R, N
+        spw = C.c_int64()
+        self._chk(lib().vcsgc_multi_steps_per_sweep(self.h, C.byref(spw)))
+        self.steps_per_sweep = spw.value
+
+    def _chk(self, rc):
+        if rc != OK:
+            msg = lib().vcsgc_multi_last_error(self.h)
+            raise VcsgcError(rc, msg.decode() if msg else "")
+
+    def sweep(self, n=1):
+        self._chk(lib().vcsgc_multi_sweep(self.h, int(n)))
+
+    def steps(self, n):
+        self._chk(lib().vcsgc_multi_steps(self.h, int(n)))
+
+    def observables(self, r=0):
+        o = MultiObs()
+        self._chk(lib().vcsgc_multi_observables(self.h, int(r), C.byref(o)))
+        K = o.K
+        out = {}
+        for f, _ in MultiObs._fields_:
+            v = getattr(o, f)
+            out[f] = [v[a] for a in range(K)] if isinstance(v, C.Array) else v
+        return out
+
+    def types(self, r=0):
+        out = np.zeros(self.n, dtype=np.uint8)
+        self._chk(lib().vcsgc_multi_get_types(self.h, int(r), _ptr(out)))
+        return out
+
+    def set_types(self, t, r=0):
+        tt = np.ascontiguousarray(t, dtype=np.uint8)
+        assert tt.shape == (self.n,)
+        self._chk(lib().vcsgc_multi_set_types(self.h, int(r), _ptr(tt)))
+
+    def delta_e(self, sites, to, r=0):
+        s = np.ascontiguousarray(sites, dtype=np.int64)
+        tt = np.ascontiguousarray(np.broadcast_to(to, s.shape), dtype=np.uint8)
+        out = np.zeros(s.shape[0])
+        self._chk(lib().vcsgc_multi_delta_e(self.h, int(r), _ptr(s), _ptr(tt), s.shape[0], _ptr(out)))
+        return out
+
+    def energy(self, r=0):
+        e = C.c_double()
+        self._chk(lib().vcsgc_multi_energy(self.h, int(r), C.byref(e)))
+        return e.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vcsgc_multi_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

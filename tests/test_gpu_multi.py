@@ -1,0 +1,103 @@
+"""Multicomponent colour step on the GPU against the multicomponent oracle:
+energy changes to every target species and total energies (FP64), and
+trajectories site for site over whole sweeps for K = 3 (one density
+function) and K = 4 (species-dependent densities: re-embedding), with the
+oracle's near-tie flags as the only allowed divergence."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1012_5082_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # K, density scales, phi (eV), kappa, T (K), c0 (per solute)
+    3: (None, [-2.3, -2.1], 10.0, 1200.0, 0.05),
+    4: ((1.0, 1.25, 0.85, 1.1), [-1.45, -2.45, 0.2], 10.0, 1200.0, 0.05),
+}
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_1012_5082_gb300 import vcsgc
+    return vcsgc
+
+
+def _pair(V, K, cells=(8, 8, 8), seed=3, R=1):
+    ds, phi, kappa, T, c0 = CASES[K]
+    tab = I.eam_tables(I.multi_eam_params(K, dens_scale=ds))
+    lat = I.bcc_lattice(*cells)
+    t = I.multi_random_types(lat.n, [int(c0 * lat.n)] * (K - 1), seed=seed)
+    orc = O.MultiSystem(lat, t, tab)
+    orc.set_params(phi, [kappa] * (K - 1), T, c0=[c0] * (K - 1), seed=seed + 100)
+    orc.schedule_sublattice(lat.cells, (4, 4, 4))
+    g = V.Multi(lat, t, tab, phi, kappa, T, c0=c0, seed_r=np.array([seed + 100] * R, dtype=np.uint64),
+                n_replicas=R)
+    return lat, tab, orc, g
+
+
+@pytest.mark.parametrize("K", [3, 4])
+def test_multi_delta_e_and_energy(V, K):
+    """dE of 300 random (site, target species) pairs within 1e-11 eV of the
+    oracle's neighbour-by-neighbour sum, and the energy within 1e-12
+    relative."""
+    lat, tab, orc, g = _pair(V, K)
+    rng = np.random.default_rng(K)
+    sites = rng.integers(0, lat.n, 300)
+    to = rng.integers(0, K, 300).astype(np.uint8)
+    d_gpu = g.delta_e(sites, to)
+    d_orc = np.array([orc.delta_e(i, b) for i, b in zip(sites, to)])
+    assert np.abs(d_gpu - d_orc).max() < 1e-11, np.abs(d_gpu - d_orc).max()
+    assert np.count_nonzero(d_orc) > 200
+    e = orc.energy_full()
+    assert abs(g.energy() - e) <= 1e-12 * abs(e)
+    assert abs(g.observables()["energy"] - e) <= 1e-12 * abs(e)
+    g.close()
+
+
+@pytest.mark.parametrize("K,sweeps", [(3, 60), (4, 30)])
+def test_multi_trajectory_bit_exact(V, K, sweeps):
+    """8^3 cells, period-4 sublattice (8 trials per colour step): species
+    agree after every sweep; counters and counts agree exactly, the tracked
+    energy to 1e-9 relative, and it equals the full energy."""
+    lat, tab, orc, g = _pair(V, K)
+    spw = g.steps_per_sweep
+    assert spw == 128
+    resyncs = 0
+    for s in range(sweeps):
+        ties0 = orc.obs()["near_ties"]
+        g.sweep(1)
+        orc.parallel_steps(spw)
+        tg, to = g.types(), orc.types
+        if not np.array_equal(tg, to):
+            assert orc.obs()["near_ties"] > ties0, f"sweep {s}: species differ without a flagged tie"
+            g.set_types(to)
+            resyncs += 1
+    og, oo = g.observables(), orc.obs()
+    if resyncs == 0:
+        for k in ("trials", "local_accepts", "global_trials", "global_accepts", "flips"):
+            assert og[k] == oo[k], (k, og[k], oo[k])
+        assert og["n"] == oo["n"]
+        assert abs(og["energy"] - oo["energy"]) <= 1e-9 * abs(oo["energy"])
+        for a in range(K):
+            assert abs(og["mean_c"][a] * og["steps"] - oo["sum_c"][a]) < 1e-9 * oo["steps"]
+    assert og["flips"] > 500
+    assert abs(g.energy() - og["energy"]) <= 1e-9 * abs(og["energy"])
+    g.close()
+
+
+def test_multi_replicas_independent(V):
+    """Two replicas with the same seed and start evolve identically; a third
+    with another seed does not."""
+    ds, phi, kappa, T, c0 = CASES[3]
+    tab = I.eam_tables(I.multi_eam_params(3, dens_scale=ds))
+    lat = I.bcc_lattice(8, 8, 8)
+    t = I.multi_random_types(lat.n, [int(c0 * lat.n)] * 2, seed=9)
+    g = V.Multi(lat, np.stack([t, t, t]), tab, phi, kappa, T, c0=c0,
+                seed_r=np.array([5, 5, 6], dtype=np.uint64))
+    g.sweep(20)
+    assert np.array_equal(g.types(0), g.types(1))
+    assert not np.array_equal(g.types(0), g.types(2))
+    assert g.observables(0)["flips"] == g.observables(1)["flips"] > 0
+    g.close()
