@@ -445,6 +445,68 @@ def ising_bench(V, torch, stream, local, sweeps=30, warmup=3):
     return out
 
 
+def overlap_bench(V, torch, stream, local, sweeps=4, warmup=1):
+    """Overlapping, position-weighted domains (Sec. III A) against the plain
+    octants on the same cells of the headline lattice (80^3 x 8 replicas,
+    the same phi and c0, 2% B start): cells of 10^3 lattice cells, octants =
+    blocks of 5^3 in 2x2x2 colours, overlapping = domains of 6^3 with gap 4
+    (13.0 A > 2 r_c); one trial per cell per colour step (512 per replica).
+    Reports throughput and replica 0's energy per atom after 2, 5, 10 and 20
+    sweeps from the supersaturated start (the relaxation the larger trial
+    volume is meant to speed up), with the period-4 sublattice beside them."""
+    lat, types, tab, phi, c0 = workload()
+    seeds = np.arange(N_PHI, dtype=np.uint64) + np.uint64(7001)
+    out = {"workload": "80^3 x 8 replicas, headline phi/c0, cells of 10^3 lattice cells"}
+    for name, kind, sched in (("octants", V.SCHED_BLOCKS, (5, 5, 5, 2, 2, 2)),
+                              ("overlapping", V.SCHED_OVERLAP, (10, 10, 10, 4, 4, 4)),
+                              ("sublattice", V.SCHED_SUBLATTICE, (4, 4, 4))):
+        ctx = V.Context(lat, np.tile(types, N_PHI), tab, 0.0, KAPPA, T_K, schedule=kind, sched=sched,
+                        n_replicas=N_PHI, phi_r=phi, c0_r=c0, seed_r=seeds, stream=stream, device=local)
+        # replica 0 (c0 = the starting 2 %): energy per atom as the
+        # supersaturated start relaxes
+        e = {"0": ctx.observables(0)["energy_per_atom"]}
+        done = 0
+        for k in (2, 5, 10, 20):
+            ctx.sweep(k - done)
+            done = k
+            e[str(k)] = ctx.observables(0)["energy_per_atom"]
+        ctx.sweep(warmup)
+        ms = timed_sweeps(torch, stream, ctx, sweeps)
+        out[name] = {"trial_moves_per_s": N_PHI * lat.n * sweeps / (ms * 1e-3),
+                     "trials_per_step": N_PHI * (lat.n // ctx.steps_per_sweep),
+                     "us_per_step": ms * 1e3 / (sweeps * ctx.steps_per_sweep),
+                     "energy_per_atom_after_sweeps": e}
+        ctx.close()
+    return out
+
+
+def multi_bench(V, torch, stream, local, sweeps=10, warmup=2):
+    """Multicomponent colour step: 80^3 x 8 replicas, period-4 sublattice,
+    K = 3 (one density function) and K = 4 (species-dependent densities,
+    re-embedding), 5% of each solute at random, T = 1200 K, kappa = 10."""
+    lat = I.bcc_lattice(CELLS, CELLS, CELLS)
+    out = {}
+    # phi per solute: the local driving forces at which the expected dn of
+    # every solute vanishes on the random start (solved once from the dE of
+    # every site to every target species), minus 2 kappa kB T c0
+    for K, ds, ph in ((3, None, [-1.928, -1.628]), (4, (1.0, 1.25, 0.85, 1.1), [-1.173, -2.037, 0.567])):
+        tab = I.eam_tables(I.multi_eam_params(K, dens_scale=ds))
+        t = np.stack([I.multi_random_types(lat.n, [int(0.05 * lat.n)] * (K - 1), seed=8000 + r)
+                      for r in range(N_PHI)])
+        g = V.Multi(lat, t, tab, ph, 10.0, 1200.0, c0=0.05,
+                    seed_r=np.arange(N_PHI, dtype=np.uint64) + np.uint64(8100), stream=stream, device=local)
+        g.sweep(warmup)
+        ms = timed_sweeps(torch, stream, g, sweeps)
+        o = g.observables(0)
+        out[f"K{K}"] = {"trial_moves_per_s": N_PHI * lat.n * sweeps / (ms * 1e-3),
+                        "us_per_step": ms * 1e3 / (sweeps * g.steps_per_sweep),
+                        "reembed": ds is not None, "acc_local": o["acc_local"], "acc_global": o["acc_global"],
+                        "launches_per_step": 2}
+        g.close()
+    out["workload"] = "80^3 x 8 replicas, period-4 sublattice (64,000 trials per colour step)"
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle times the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -491,8 +553,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-ising", action="store_true")
+    ap.add_argument("--no-overlap", action="store_true")
+    ap.add_argument("--no-multi", action="store_true")
     ap.add_argument("--md-only", action="store_true", help="only the MD measurement (profiling)")
     ap.add_argument("--md-box", type=float, default=250.0, help="nanocrystal box (A) for --md-only")
+    ap.add_argument("--multi-only", action="store_true", help="only the multicomponent measurement (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -515,6 +580,10 @@ def main():
     if args.md_only:
         print(json.dumps(md_bench(V, torch, torch.cuda.Stream(), local, steps=args.steps,
                                   warmup=args.warmup, box=args.md_box)), flush=True)
+        return 0
+    if args.multi_only:
+        print(json.dumps(multi_bench(V, torch, torch.cuda.Stream(), local, sweeps=args.steps,
+                                     warmup=args.warmup)), flush=True)
         return 0
     lat, types, tab, phi, c0 = workload()
     stream = torch.cuda.Stream()
@@ -604,6 +673,10 @@ def main():
         line["batch_64"] = batch_bench(V, torch, stream, local, surrogate=not args.no_surrogate)
     if not args.no_ising:
         line["ising"] = ising_bench(V, torch, stream, local)
+    if not args.no_overlap:
+        line["overlap"] = overlap_bench(V, torch, stream, local)
+    if not args.no_multi:
+        line["multicomponent"] = multi_bench(V, torch, stream, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lat, types, tab, phi, c0)
     if rank == 0:

@@ -11,8 +11,8 @@
 //   min{1, exp[-beta sum_alpha kappa_p,alpha dn_alpha (dn_alpha + 2 (n_alpha - n0_alpha))]}.
 //
 // One thread per trial.  dE on the rigid lattice: the pair part from the
-// per-shell neighbour counts by species (four byte counters in one word per
-// shell) against the shell table phi_ab(r_s) staged in shared memory; the
+// per-shell neighbour counts by species (one 64-bit word per species, 8 bits
+// per shell) against the shell table phi_ab(r_s) staged in shared memory; the
 // own embedding change F_b(rho_i) - F_a(rho_i); and, where the densities
 // differ between species, the re-embedding of every neighbour j,
 // F_{t_j}(rho_j + f_b(r_s) - f_a(r_s)) - F_{t_j}(rho_j).  Two launches per
@@ -45,6 +45,19 @@ __global__ void k_multi_shell_tables(const Spline* pair, const Spline* dens, int
 void launch_multi_shell_tables(const Spline* pair, const Spline* dens, int K, const double* r_s, int n_sh,
                                double* V, double* Fd, unsigned* err, cudaStream_t st) {
   k_multi_shell_tables<<<1, 128, 0, st>>>(pair, dens, K, r_s, n_sh, V, Fd, err);
+}
+
+__global__ void k_multi_fixed(const double* V, int n_sh, int K, int qbits, long long* Dq) {
+  const int n = n_sh * K * K * K;
+  const double sc = ldexp(1.0, qbits);
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const int be = q % K, b = (q / K) % K, a = (q / (K * K)) % K, s = q / (K * K * K);
+    Dq[q] = llrint((V[(s * K + b) * K + be] - V[(s * K + a) * K + be]) * sc);
+  }
+}
+
+void launch_multi_fixed(const double* V, int n_sh, int K, int qbits, long long* Dq, cudaStream_t st) {
+  k_multi_fixed<<<1, 256, 0, st>>>(V, n_sh, K, qbits, Dq);
 }
 
 // rho_i = sum_j f_{t_j}(r_ij)
@@ -103,34 +116,155 @@ void launch_multi_energy(const MultiArgs& a, int r0, int nrep, double* part, cud
 }
 
 // dE of site i (replica r) going from species ta to tb; sV, sFd: the shell
-// tables (shared or global)
+// tables (shared or global).  The neighbours are visited in chunks of 8:
+// the chunk's index arithmetic and loads are issued before any of its sums,
+// so up to 8 L2 reads per thread are in flight at once.  Per-shell counts by
+// species sit in one 64-bit word per species (8 bits per shell).
+constexpr int MK_CHUNK = 8;
+
 template <bool REEMBED>
 __device__ double multi_de(const MultiArgs& a, const double* sV, const double* sFd, int r, int i, int ta, int tb) {
   const uint8_t* ty = a.types + (long long)r * a.N;
   const double* rho = a.rho + (long long)r * a.N;
   const int K = a.K;
-  double pair = 0.0, re = 0.0;
-  int k = 0;
-  for (int s = 0; s < a.n_sh; ++s) {
-    unsigned cnt = 0u;  // byte beta: neighbours of species beta in shell s
-    const double dfs = sFd[s * K + tb] - sFd[s * K + ta];
-    for (; k < a.n_off && a.off[k].w == s; ++k) {
-      const int j = multi_nbr(a, i, a.off[k]);
-      const int tj = ty[j];
-      cnt += 1u << (8 * tj);
-      if constexpr (REEMBED) {
-        const double rj = rho[j];
-        re += spline_val(a.embed[tj], rj + dfs, a.err) - spline_val(a.embed[tj], rj, a.err);
+  const int3 p = multi_half(a, i);
+  unsigned long long c0 = 0ull, c1 = 0ull, c2 = 0ull, c3 = 0ull;
+  double re = 0.0;
+  for (int k0 = 0; k0 < a.n_off; k0 += MK_CHUNK) {
+    int tj[MK_CHUNK];
+    double rj[MK_CHUNK];
+#pragma unroll
+    for (int u = 0; u < MK_CHUNK; ++u) {
+      const int k = k0 + u;
+      tj[u] = 0;
+      rj[u] = 0.0;
+      if (k < a.n_off) {
+        const int j = multi_nbr_at(a, p, a.off[k]);
+        tj[u] = ty[j];
+        if constexpr (REEMBED) rj[u] = rho[j];
       }
     }
+#pragma unroll
+    for (int u = 0; u < MK_CHUNK; ++u) {
+      const int k = k0 + u;
+      if (k < a.n_off) {
+        const int s = a.off[k].w;
+        const unsigned long long inc = 1ull << (8 * s);
+        c0 += tj[u] == 0 ? inc : 0ull;
+        c1 += tj[u] == 1 ? inc : 0ull;
+        c2 += tj[u] == 2 ? inc : 0ull;
+        c3 += tj[u] == 3 ? inc : 0ull;
+        if constexpr (REEMBED) {
+          const double dfs = sFd[s * K + tb] - sFd[s * K + ta];
+          re += spline_val(a.embed[tj[u]], rj[u] + dfs, a.err) - spline_val(a.embed[tj[u]], rj[u], a.err);
+        }
+      }
+    }
+  }
+  double pair = 0.0;
+  for (int s = 0; s < a.n_sh; ++s) {
     const double* Vb = sV + (s * K + tb) * K;
     const double* Va = sV + (s * K + ta) * K;
-    for (int be = 0; be < K; ++be) pair += (double)((cnt >> (8 * be)) & 255u) * (Vb[be] - Va[be]);
+    const int sh = 8 * s;
+    pair += (double)((c0 >> sh) & 255ull) * (Vb[0] - Va[0]);
+    pair += (double)((c1 >> sh) & 255ull) * (Vb[1] - Va[1]);
+    if (K > 2) pair += (double)((c2 >> sh) & 255ull) * (Vb[2] - Va[2]);
+    if (K > 3) pair += (double)((c3 >> sh) & 255ull) * (Vb[3] - Va[3]);
   }
   const double ri = rho[i];
   const double own = spline_val(a.embed[tb], ri, a.err) - spline_val(a.embed[ta], ri, a.err);
   return pair + own + re;
 }
+
+// The same dE with the compile-time five-shell table, basis B of the trial
+// site in cell (cx, cy, cz): the wrapped x, y, z offsets of the cells -2..2
+// are computed once, every neighbour index is then three adds, and the
+// per-shell counts sit in one 32-bit word per shell (8 bits per species).
+// Without re-embedding the density is the same at every site and the own
+// embedding change comes from the table sDF[a K + b].
+__device__ __forceinline__ int mk_wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// n / d for 0 <= n < 2^22 from the float reciprocal, corrected to the exact
+// quotient
+__device__ __forceinline__ int mk_div(int n, int d, float rcp) {
+  int q = __float2int_rz(__int2float_rn(n) * rcp);
+  const int rr = n - q * d;
+  q += rr < 0 ? -1 : (rr >= d ? 1 : 0);
+  return q;
+}
+
+template <int B, bool REEMBED>
+__device__ double multi_de_bcc5(const MultiArgs& a, const long long* sDq, const double* sFd, const double* sDF, int r,
+                                int i, int cx, int cy, int cz, int ta, int tb) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const double* rho = a.rho + (long long)r * a.N;
+  const int K = a.K;
+  int xo[5], yo[5], zo[5];
+#pragma unroll
+  for (int d = -2; d <= 2; ++d) {
+    xo[d + 2] = 2 * mk_wrap(cx + d, a.nx);
+    yo[d + 2] = 2 * a.nx * mk_wrap(cy + d, a.ny);
+    zo[d + 2] = 2 * a.nx * a.ny * mk_wrap(cz + d, a.nz);
+  }
+  unsigned cnt[5] = {0u, 0u, 0u, 0u, 0u};
+  double re = 0.0;
+  // without re-embedding all 58 species loads are issued at once; with it,
+  // chunks of 8 (each also loads a density)
+  constexpr int CH = REEMBED ? MK_CHUNK : MK_BCC5_N;
+#pragma unroll
+  for (int k0 = 0; k0 < MK_BCC5_N; k0 += CH) {
+    int tj[CH];
+    double rj[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (k0 + u < MK_BCC5_N) {
+        const int code = mk_bcc5_code(k0 + u);
+        const int hx = (code & 15) - 4, hy = ((code >> 4) & 15) - 4, hz = ((code >> 8) & 15) - 4;
+        const int bb = B ^ (hx & 1);
+        const int j = zo[((B + hz - bb) >> 1) + 2] + yo[((B + hy - bb) >> 1) + 2] + xo[((B + hx - bb) >> 1) + 2] + bb;
+        tj[u] = ty[j];
+        if constexpr (REEMBED) rj[u] = rho[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (k0 + u < MK_BCC5_N) {
+        const int s = mk_bcc5_code(k0 + u) >> 12;
+        cnt[s] += 1u << (8 * tj[u]);
+        if constexpr (REEMBED) {
+          const double dfs = sFd[s * K + tb] - sFd[s * K + ta];
+          re += spline_val(a.embed[tj[u]], rj[u] + dfs, a.err) - spline_val(a.embed[tj[u]], rj[u], a.err);
+        }
+      }
+    }
+  }
+  // pair part: integer counts times the fixed-point differences, exact in
+  // 64 bits; one conversion to FP64 at the end
+  long long pq = 0;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const long long* D = sDq + ((s * K + ta) * K + tb) * K;
+    for (int be = 0; be < K; ++be) pq += (long long)((cnt[s] >> (8 * be)) & 255u) * D[be];
+  }
+  const double pair = ldexp((double)pq, -a.qbits);
+  double own;
+  if constexpr (REEMBED) {
+    const double ri = rho[i];
+    own = spline_val(a.embed[tb], ri, a.err) - spline_val(a.embed[ta], ri, a.err);
+  } else {
+    own = sDF[ta * K + tb];
+  }
+  return pair + own + re;
+}
+
+__global__ void k_multi_df(MultiArgs a, double* dF) {
+  const int q = threadIdx.x;
+  if (q >= a.K * a.K) return;
+  const double r0 = a.rho[0];
+  dF[q] = spline_val(a.embed[q % a.K], r0, a.err) - spline_val(a.embed[q / a.K], r0, a.err);
+}
+
+void launch_multi_df(const MultiArgs& a, double* dF, cudaStream_t st) { k_multi_df<<<1, 32, 0, st>>>(a, dF); }
 
 __device__ __forceinline__ int multi_target(const MultiArgs& a, const MRepParams& p, long long step, int d, int ta) {
   if (a.K == 2) return 1 - ta;
@@ -143,30 +277,58 @@ template <bool REEMBED>
 __global__ void __launch_bounds__(MK_BLOCK) k_multi_propose(MultiArgs a) {
   __shared__ double sV[MK_MAX_SH * MK_MAX * MK_MAX];
   __shared__ double sFd[MK_MAX_SH * MK_MAX];
+  __shared__ double sDF[MK_MAX * MK_MAX];
+  __shared__ long long sDq[5 * MK_MAX * MK_MAX * MK_MAX];
+  __shared__ uint4 s_wc;
+  __shared__ int s_col[4];
   __shared__ int s_red[MK_BLOCK / 32][MK_MAX + 1];
   __shared__ double s_de[MK_BLOCK / 32];
   __shared__ bool s_last;
   const int K = a.K;
   for (int q = threadIdx.x; q < a.n_sh * K * K; q += MK_BLOCK) sV[q] = a.V[q];
   for (int q = threadIdx.x; q < a.n_sh * K; q += MK_BLOCK) sFd[q] = a.Fd[q];
-  __syncthreads();
-
+  if (!REEMBED && threadIdx.x < K * K) sDF[threadIdx.x] = a.dF[threadIdx.x];
+  if (a.bcc5)
+    for (int q = threadIdx.x; q < 5 * K * K * K; q += MK_BLOCK) sDq[q] = a.Dq[q];
   const int r = blockIdx.y;
   const MRepParams& p = a.rp[r];
   const long long step = a.rs[r].step;
-  const uint4 wc = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0xFFFFFFFFu, TAG_STEP),
-                                 p.key);
-  const int c = (int)below64(wc.x, wc.y, (uint64_t)a.n_colours);
+  if (threadIdx.x == 0) {
+    // the step's colour (and global uniform), once per block
+    const uint4 wc = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0xFFFFFFFFu, TAG_STEP),
+                                   p.key);
+    const int c = (int)below64(wc.x, wc.y, (uint64_t)a.n_colours);
+    const int pc = c >> 1;
+    s_wc = wc;
+    s_col[0] = c;
+    s_col[1] = pc % a.qx;
+    s_col[2] = (pc / a.qx) % a.qy;
+    s_col[3] = pc / (a.qx * a.qy);
+  }
+  __syncthreads();
+  const uint4 wc = s_wc;
+  const int c = s_col[0];
   const int d = blockIdx.x * MK_BLOCK + threadIdx.x;
   int acc = 0, tie = 0, ta = 0, tb = 0, site = -1;
   double de = 0.0;
   if (d < a.D) {
-    site = multi_site(a, c, d);
+    // site of trial d: ascending index within the colour
+    const int b = c & 1;
+    const int dq = mk_div(d, a.nxq, a.rcp_nxq);
+    const int kx = d - dq * a.nxq;
+    const int kz = mk_div(dq, a.nyq, a.rcp_nyq);
+    const int ky = dq - kz * a.nyq;
+    const int cx = s_col[1] + a.qx * kx, cy = s_col[2] + a.qy * ky, cz = s_col[3] + a.qz * kz;
+    site = ((cz * a.ny + cy) * a.nx + cx) * 2 + b;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL),
                                   p.key);
     ta = a.types[(long long)r * a.N + site];
     tb = multi_target(a, p, step, d, ta);
-    de = multi_de<REEMBED>(a, sV, sFd, r, site, ta, tb);
+    if (a.bcc5)
+      de = b ? multi_de_bcc5<1, REEMBED>(a, sDq, sFd, sDF, r, site, cx, cy, cz, ta, tb)
+             : multi_de_bcc5<0, REEMBED>(a, sDq, sFd, sDF, r, site, cx, cy, cz, ta, tb);
+    else
+      de = multi_de<REEMBED>(a, sV, sFd, r, site, ta, tb);
     if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
     acc = metropolis(p.beta * (de + (p.dmu0[tb] - p.dmu0[ta])), top53(w.z, w.w), &tie) ? 1 : 0;
   }
@@ -273,29 +435,36 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit(MultiArgs a) {
     B->accept = 0;
     B->sum_de = 0.0;
   }
-  const int q = blockIdx.x * MK_BLOCK + threadIdx.x;
-  if (!A->accept || q >= A->nacc) return;
-  const int2 e = a.pend[(long long)r * a.D + q];
-  uint8_t* ty = a.types + (long long)r * a.N;
-  const int ta = ty[e.x], tb = e.y;
-  ty[e.x] = (uint8_t)tb;
-  if constexpr (REEMBED) {
-    double* rho = a.rho + (long long)r * a.N;
-    for (int k = 0; k < a.n_off; ++k) {
-      const int4 h = a.off[k];
-      rho[multi_nbr(a, e.x, h)] += a.Fd[h.w * a.K + tb] - a.Fd[h.w * a.K + ta];
+  if (!A->accept) return;
+  const int nacc = A->nacc;
+  for (int q = blockIdx.x * MK_BLOCK + threadIdx.x; q < nacc; q += gridDim.x * MK_BLOCK) {
+    const int2 e = a.pend[(long long)r * a.D + q];
+    uint8_t* ty = a.types + (long long)r * a.N;
+    const int ta = ty[e.x], tb = e.y;
+    ty[e.x] = (uint8_t)tb;
+    if constexpr (REEMBED) {
+      double* rho = a.rho + (long long)r * a.N;
+      const int3 p = multi_half(a, e.x);
+      for (int k = 0; k < a.n_off; ++k) {
+        const int4 h = a.off[k];
+        rho[multi_nbr_at(a, p, h)] += a.Fd[h.w * a.K + tb] - a.Fd[h.w * a.K + ta];
+      }
     }
   }
 }
 
 void launch_multi_step(const MultiArgs& a, cudaStream_t st) {
-  const dim3 grid((unsigned)((a.D + MK_BLOCK - 1) / MK_BLOCK), (unsigned)a.R);
+  const int nb = (a.D + MK_BLOCK - 1) / MK_BLOCK;
+  const dim3 grid((unsigned)nb, (unsigned)a.R);
+  // the accepts of a step are a small share of its trials: a few blocks per
+  // replica stride over them
+  const dim3 cgrid((unsigned)(nb < 4 ? nb : 4), (unsigned)a.R);
   if (a.reembed) {
     k_multi_propose<true><<<grid, MK_BLOCK, 0, st>>>(a);
-    k_multi_commit<true><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_commit<true><<<cgrid, MK_BLOCK, 0, st>>>(a);
   } else {
     k_multi_propose<false><<<grid, MK_BLOCK, 0, st>>>(a);
-    k_multi_commit<false><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_commit<false><<<cgrid, MK_BLOCK, 0, st>>>(a);
   }
 }
 

@@ -60,6 +60,13 @@ struct MultiArgs {
   const double* V;
   const double* Fd;
   int reembed;          // f_a(r_s) differs between species at some shell
+  int bcc5;             // the offsets are the compile-time five-shell table
+  const double* dF;     // [K][K] F_b(rho0) - F_a(rho0) (no re-embedding: rho uniform)
+  // pair part in fixed point: Dq[((s K + a) K + b) K + beta] = round((phi_b,beta(r_s)
+  // - phi_a,beta(r_s)) 2^qbits); sums of 58 such terms stay below 2^62
+  const long long* Dq;
+  int qbits;
+  float rcp_nxq, rcp_nyq;  // 1 / nxq, 1 / nyq for the trial decode
   Spline embed[MK_MAX];
   uint8_t* types;       // [R][N]
   double* rho;          // [R][N]
@@ -80,12 +87,17 @@ __device__ __forceinline__ int multi_site(const MultiArgs& a, int c, int d) {
   return ((cz * a.ny + cy) * a.nx + cx) * 2 + b;
 }
 
-// neighbour of site i along half-lattice offset h (periodic)
-__device__ __forceinline__ int multi_nbr(const MultiArgs& a, int i, int4 h) {
+// lattice coordinates of site i: p = (2 cx + b, 2 cy + b, 2 cz + b)
+__device__ __forceinline__ int3 multi_half(const MultiArgs& a, int i) {
   const int b = i & 1;
   const int cell = i >> 1;
   const int cx = cell % a.nx, cy = (cell / a.nx) % a.ny, cz = cell / (a.nx * a.ny);
-  const int qx = 2 * cx + b + h.x, qy = 2 * cy + b + h.y, qz = 2 * cz + b + h.z;
+  return make_int3(2 * cx + b, 2 * cy + b, 2 * cz + b);
+}
+
+// neighbour at half-lattice position p + h (periodic; |h| < 2 n per axis)
+__device__ __forceinline__ int multi_nbr_at(const MultiArgs& a, int3 p, int4 h) {
+  const int qx = p.x + h.x, qy = p.y + h.y, qz = p.z + h.z;
   const int bb = qx & 1;
   int X = (qx - bb) >> 1, Y = (qy - bb) >> 1, Z = (qz - bb) >> 1;
   X += X < 0 ? a.nx : (X >= a.nx ? -a.nx : 0);
@@ -94,8 +106,43 @@ __device__ __forceinline__ int multi_nbr(const MultiArgs& a, int i, int4 h) {
   return ((Z * a.ny + Y) * a.nx + X) * 2 + bb;
 }
 
+__device__ __forceinline__ int multi_nbr(const MultiArgs& a, int i, int4 h) {
+  return multi_nbr_at(a, multi_half(a, i), h);
+}
+
+// The 58 neighbours of a BCC site out to the fifth shell (r_c between
+// a sqrt(3) and a sqrt(19)/2), as half-lattice offsets h (all even or all
+// odd), ordered by |h|^2 then (hx, hy, hz): shells |h|^2 = 3, 4, 8, 11, 12
+// with 8, 6, 12, 24, 8 sites.  Packed (hx + 4) | (hy + 4) << 4 |
+// (hz + 4) << 8 | shell << 12; a compile-time switch so that unrolled
+// loops fold the offsets into constants.
+constexpr int MK_BCC5_N = 58;
+__host__ __device__ __forceinline__ constexpr int mk_bcc5_code(int k) {
+  switch (k) {
+    case 0: return 0x0333; case 1: return 0x0533; case 2: return 0x0353; case 3: return 0x0553;
+    case 4: return 0x0335; case 5: return 0x0535; case 6: return 0x0355; case 7: return 0x0555;
+    case 8: return 0x1442; case 9: return 0x1424; case 10: return 0x1244; case 11: return 0x1644;
+    case 12: return 0x1464; case 13: return 0x1446; case 14: return 0x2422; case 15: return 0x2242;
+    case 16: return 0x2642; case 17: return 0x2462; case 18: return 0x2224; case 19: return 0x2624;
+    case 20: return 0x2264; case 21: return 0x2664; case 22: return 0x2426; case 23: return 0x2246;
+    case 24: return 0x2646; case 25: return 0x2466; case 26: return 0x3331; case 27: return 0x3531;
+    case 28: return 0x3351; case 29: return 0x3551; case 30: return 0x3313; case 31: return 0x3513;
+    case 32: return 0x3133; case 33: return 0x3733; case 34: return 0x3153; case 35: return 0x3753;
+    case 36: return 0x3373; case 37: return 0x3573; case 38: return 0x3315; case 39: return 0x3515;
+    case 40: return 0x3135; case 41: return 0x3735; case 42: return 0x3155; case 43: return 0x3755;
+    case 44: return 0x3375; case 45: return 0x3575; case 46: return 0x3337; case 47: return 0x3537;
+    case 48: return 0x3357; case 49: return 0x3557; case 50: return 0x4222; case 51: return 0x4622;
+    case 52: return 0x4262; case 53: return 0x4662; case 54: return 0x4226; case 55: return 0x4626;
+    case 56: return 0x4266; case 57: return 0x4666;
+    default: return 0;
+  }
+}
+
 void launch_multi_shell_tables(const Spline* pair, const Spline* dens, int K, const double* r_s, int n_sh,
                                double* V, double* Fd, unsigned* err, cudaStream_t st);
+// dF[a K + b] = F_b(rho_0) - F_a(rho_0) at the uniform density rho_0 of site 0
+void launch_multi_df(const MultiArgs& a, double* dF, cudaStream_t st);
+void launch_multi_fixed(const double* V, int n_sh, int K, int qbits, long long* Dq, cudaStream_t st);
 void launch_multi_rho(const MultiArgs& a, int r0, int nrep, cudaStream_t st);
 // per-site energies summed into block partials part[r][blocks]
 int multi_energy_blocks(long long N);

@@ -282,6 +282,11 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
   MCK(cudaGetLastError());
   a.V = V;
   a.Fd = Fd;
+  a.rcp_nxq = 1.0f / (float)a.nxq;
+  a.rcp_nyq = 1.0f / (float)a.nyq;
+  // fixed-point pair differences: the scale keeps 58 x 24 x max|dphi| < 2^62
+  std::vector<double> hV(r_s.size() * m->K * m->K);
+  MCK(cudaMemcpyAsync(hV.data(), V, sizeof(double) * hV.size(), cudaMemcpyDeviceToHost, m->st));
   std::vector<double> hFd(r_s.size() * m->K);
   MCK(cudaMemcpyAsync(hFd.data(), Fd, sizeof(double) * hFd.size(), cudaMemcpyDeviceToHost, m->st));
   MCK(cudaStreamSynchronize(m->st));
@@ -290,6 +295,24 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
   for (int s = 0; s < a.n_sh; ++s)
     for (int al = 1; al < m->K; ++al)
       if (hFd[s * m->K + al] != hFd[s * m->K]) a.reembed = 1;
+  double vmax = 0.0;
+  for (double v : hV) vmax = std::max(vmax, std::fabs(v));
+  if (!std::isfinite(vmax)) return mfail(m, VCSGC_ERR_NONFINITE, "non-finite pair table at a shell");
+  // |phi_b - phi_a| <= 2 vmax; 58 x 24 x 2 vmax x 2^qbits < 2^62
+  a.qbits = 52;
+  while (a.qbits > 0 && 2.0 * vmax * 58.0 * 24.0 * std::ldexp(1.0, a.qbits) >= std::ldexp(1.0, 62)) --a.qbits;
+  long long* Dq = nullptr;
+  MTRY(malloc_dev(m, &Dq, (size_t)a.n_sh * m->K * m->K * m->K));
+  launch_multi_fixed(V, a.n_sh, m->K, a.qbits, Dq, m->st);
+  MCK(cudaGetLastError());
+  a.Dq = Dq;
+  a.bcc5 = a.n_off == MK_BCC5_N ? 1 : 0;
+  for (int k = 0; k < a.n_off && a.bcc5; ++k) {
+    const int code = mk_bcc5_code(k);
+    if (a.off[k].x != (code & 15) - 4 || a.off[k].y != ((code >> 4) & 15) - 4 ||
+        a.off[k].z != ((code >> 8) & 15) - 4 || a.off[k].w != code >> 12)
+      a.bcc5 = 0;
+  }
   // state
   MTRY(malloc_dev(m, &a.types, (size_t)R * m->N));
   MTRY(malloc_dev(m, &a.rho, (size_t)R * m->N));
@@ -325,6 +348,13 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
     const uint64_t seed = seed_r ? seed_r[r] : (uint64_t)r + 1;
     p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   }
+  // without re-embedding every site has the density of site 0: the own
+  // embedding change is a K x K table
+  double* dF = nullptr;
+  MTRY(malloc_dev(m, &dF, MK_MAX * MK_MAX));
+  launch_multi_df(a, dF, m->st);
+  MCK(cudaGetLastError());
+  a.dF = dF;
   MCK(cudaMemcpyAsync(rp, m->h_rp.data(), sizeof(MRepParams) * R, cudaMemcpyHostToDevice, m->st));
   MCK(cudaStreamSynchronize(m->st));
   return VCSGC_OK;
