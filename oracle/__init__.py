@@ -106,6 +106,10 @@ def lib():
             "orc_mlp_eval": (D, [P, P]),
             "orc_set_surrogate": (I32, [P, I32, P]),
             "orc_surrogate": (D, [P, I64]),
+            "orc_set_ensemble": (I32, [P, I32, D, D, D, I32]),
+            "orc_virial": (D, [P]),
+            "orc_md_state": (None, [P, P]),
+            "orc_minimize": (I32, [P, D, I64, P, P]),
             "orcm_tri": (I32, [I32, I32, I32]),
             "orcm_create": (P, [I64, P, P, P, P, P, P]),
             "orcm_free": (None, [P]),
@@ -321,6 +325,29 @@ class System:
         out = np.zeros(self.n, dtype=np.float64)
         lib().orc_get_rho(self.h, _p(out))
         return out
+
+    def set_ensemble(self, kind, t_damp=100.0, p_damp=1000.0, p_ext_bar=0.0, chain=3):
+        """kind: 'langevin', 'nvt' or 'npt' (Nose-Hoover chains, MTK barostat)."""
+        k = {"langevin": 0, "nvt": 1, "npt": 2}[kind]
+        if lib().orc_set_ensemble(self.h, k, float(t_damp), float(p_damp), float(p_ext_bar), int(chain)):
+            raise ValueError("oracle: bad ensemble parameters")
+
+    def virial(self):
+        return lib().orc_virial(self.h)
+
+    def ensemble_state(self):
+        out = np.zeros(9)
+        lib().orc_md_state(self.h, _p(out))
+        keys = ("kinetic", "potential", "temperature", "pressure_bar", "volume", "conserved", "lx", "ly", "lz")
+        return dict(zip(keys, out.tolist()))
+
+    def minimize(self, ftol=1e-4, max_iter=1000):
+        it = C.c_int64()
+        fm = C.c_double()
+        rc = lib().orc_minimize(self.h, float(ftol), int(max_iter), C.byref(it), C.byref(fm))
+        if rc < 0:
+            raise MemoryError("oracle: minimize")
+        return {"converged": rc == 0, "iterations": it.value, "fmax": fm.value}
 
     def obs(self):
         o = Obs()

@@ -80,6 +80,14 @@ struct orc_sys {
   double mass[2], dt, gamma, T_md;
   uint32_t md_key[2];
   uint64_t md_step;
+  /* Nose-Hoover ensembles: 0 Langevin (BAOAB), 1 NVT, 2 NPT (isotropic) */
+  int ens;
+  int chain;                               /* thermostat chain length M */
+  double t_damp, p_damp, p_ext;            /* fs, fs, eV/A^3 */
+  double xi[ORC_MAX_CHAIN], eta[ORC_MAX_CHAIN], Q[ORC_MAX_CHAIN];
+  double xib[ORC_MAX_CHAIN], etab[ORC_MAX_CHAIN], Qb[ORC_MAX_CHAIN];
+  double veps, W;                          /* barostat velocity (1/fs) and mass */
+  double virial;                           /* sum over pairs r_ij . F_ij (eV) */
 };
 
 /* ---------------------------------------------------------------- Philox */
@@ -1084,6 +1092,9 @@ void orc_forces(orc_sys* s, double* fx, double* fy, double* fz) {
     orc_hermite_eval(&s->sp[5 + s->t[i]], s->rho[i], NULL, &v);
     dF[i] = v;
   }
+  /* the pair (i, j) pulls i along d_ij = r_j - r_i with g = dU/dr_ij; its
+   * virial term r_ij . F_ij = -g r, each pair seen from both ends */
+  double vir = 0.0;
   for (int64_t i = 0; i < s->n; ++i) {
     int ti = s->t[i];
     double f[3] = {0, 0, 0};
@@ -1096,9 +1107,11 @@ void orc_forces(orc_sys* s, double* fx, double* fy, double* fz) {
       orc_hermite_eval(&s->sp[3 + ti], e->r, NULL, &dfi);
       double g = dphi + dF[i] * dfj + dF[e->j] * dfi;
       for (int a = 0; a < 3; ++a) f[a] += g * e->d[a] / e->r;
+      vir -= 0.5 * g * e->r;
     }
     fx[i] = f[0]; fy[i] = f[1]; fz[i] = f[2];
   }
+  s->virial = vir;
   free(dF);
 }
 
@@ -1143,9 +1156,12 @@ static void box_muller(uint32_t w[4], double* z0, double* z1) {
   *z1 = r * sin(th);
 }
 
+static int nh_steps(orc_sys* s, int64_t n_steps);
+
 /* BAOAB Langevin velocity Verlet (gamma = 0 gives plain velocity Verlet). */
 int orc_md_steps(orc_sys* s, int64_t n_steps) {
   if (!s->vx) return -1;
+  if (s->ens) return nh_steps(s, n_steps);
   double dt = s->dt;
   double c1 = exp(-s->gamma * dt), c2 = sqrt(1.0 - c1 * c1);
   for (int64_t q = 0; q < n_steps; ++q) {
@@ -1188,6 +1204,273 @@ int orc_md_steps(orc_sys* s, int64_t n_steps) {
   }
   s->energy = orc_energy_full(s);
   return 0;
+}
+
+/* ------------------------------------------------ Nose-Hoover ensembles */
+#define BAR_EV_A3 6.241509074460763e-07 /* 1 bar in eV / A^3 */
+
+int orc_set_ensemble(orc_sys* s, int kind, double t_damp, double p_damp, double p_ext_bar, int chain) {
+  if (kind < 0 || kind > 2 || chain < 1 || chain > ORC_MAX_CHAIN) return -1;
+  if (kind && !(t_damp > 0.0)) return -1;
+  if (kind == 2 && !(p_damp > 0.0)) return -1;
+  s->ens = kind;
+  s->chain = chain;
+  s->t_damp = t_damp;
+  s->p_damp = p_damp;
+  s->p_ext = p_ext_bar * BAR_EV_A3;
+  double kT = KB_EV * s->T_md, nf = 3.0 * (double)s->n;
+  for (int k = 0; k < ORC_MAX_CHAIN; ++k) {
+    s->xi[k] = s->eta[k] = s->xib[k] = s->etab[k] = 0.0;
+    s->Q[k] = (k == 0 ? nf : 1.0) * kT * t_damp * t_damp;
+    s->Qb[k] = kT * p_damp * p_damp;
+  }
+  s->veps = 0.0;
+  s->W = (nf + 3.0) * kT * p_damp * p_damp;
+  return 0;
+}
+
+double orc_virial(orc_sys* s) {
+  double* f = (double*)malloc(sizeof(double) * 3 * s->n);
+  orc_forces(s, f, f + s->n, f + 2 * s->n);
+  free(f);
+  return s->virial;
+}
+
+/* sum_i m_i v_i^2 (eV), twice the kinetic energy */
+static double twice_ke(const orc_sys* s) {
+  double k2 = 0.0;
+  for (int64_t i = 0; i < s->n; ++i)
+    k2 += s->mass[s->t[i]] / FTM * (s->vx[i] * s->vx[i] + s->vy[i] * s->vy[i] + s->vz[i] * s->vz[i]);
+  return k2;
+}
+
+/* Propagate a Nose-Hoover chain (M links, masses Q, velocities xi,
+ * positions eta) for a time h, driven by K2 = sum m v^2 of the g degrees
+ * of freedom it couples to (target g kT).  Symmetric splitting: the last
+ * link a half step, the links down to the first with the next link's
+ * friction applied as exp factors around each half kick, the coupled
+ * velocities scaled by exp(-h xi_1), the positions eta advanced, and the
+ * mirror sequence back up.  Returns the velocity scale factor. */
+static double nhc_propagate(int M, const double* Q, double* xi, double* eta, double K2, double gkT, double kT,
+                            double h) {
+  double scale = 1.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    /* pass 0: links M..1; pass 1 (after the scaling): links 1..M */
+    for (int q = 0; q < M; ++q) {
+      int k = pass == 0 ? M - 1 - q : q;
+      double G = k == 0 ? (K2 * scale * scale - gkT) / Q[0] : (Q[k - 1] * xi[k - 1] * xi[k - 1] - kT) / Q[k];
+      double e = k + 1 < M ? exp(-0.25 * h * xi[k + 1]) : 1.0;
+      xi[k] = (xi[k] * e + 0.5 * h * G) * e;
+    }
+    if (pass == 0) {
+      scale = exp(-h * xi[0]);
+      for (int k = 0; k < M; ++k) eta[k] += h * xi[k];
+    }
+  }
+  return scale;
+}
+
+static double sinhc(double x) {
+  /* sinh(x) / x; the Taylor series where x is small */
+  if (fabs(x) < 1e-4) return 1.0 + x * x / 6.0 + x * x * x * x / 120.0;
+  return sinh(x) / x;
+}
+
+/* One half kick of the particle velocities with the barostat coupling
+ * alpha v_eps: v <- v e^{-a h} + h (F/m) e^{-a h/2} sinhc(a h/2). */
+static void kick(orc_sys* s, double h, double a) {
+  double e1 = exp(-a * h), e2 = exp(-0.5 * a * h) * sinhc(0.5 * a * h);
+  for (int64_t i = 0; i < s->n; ++i) {
+    double im = FTM / s->mass[s->t[i]];
+    s->vx[i] = s->vx[i] * e1 + h * s->fx[i] * im * e2;
+    s->vy[i] = s->vy[i] * e1 + h * s->fy[i] * im * e2;
+    s->vz[i] = s->vz[i] * e1 + h * s->fz[i] * im * e2;
+  }
+}
+
+static void scale_v(orc_sys* s, double f) {
+  for (int64_t i = 0; i < s->n; ++i) {
+    s->vx[i] *= f;
+    s->vy[i] *= f;
+    s->vz[i] *= f;
+  }
+}
+
+/* barostat force: [alpha K2 + W_vir - 3 V P_ext] / W, alpha = 1 + 3 / N_f */
+static double baro_force(const orc_sys* s, double K2) {
+  double nf = 3.0 * (double)s->n, V = s->box[0] * s->box[1] * s->box[2];
+  return ((1.0 + 3.0 / nf) * K2 + s->virial - 3.0 * V * s->p_ext) / s->W;
+}
+
+/* Trotter-split MTK step: thermostats, barostat velocity, particle
+ * velocities, positions and box, forces, and the mirror sequence. */
+static int nh_steps(orc_sys* s, int64_t n_steps) {
+  double dt = s->dt, h = 0.5 * dt, kT = KB_EV * s->T_md, nf = 3.0 * (double)s->n;
+  int npt = s->ens == 2;
+  for (int64_t q = 0; q < n_steps; ++q) {
+    for (int half = 0; half < 2; ++half) {
+      if (half == 1) {
+        /* positions and box: r e^{v dt} + dt v e^{v dt/2} sinhc(v dt/2) */
+        double ve = npt ? s->veps : 0.0;
+        double e1 = exp(ve * dt), e2 = dt * exp(0.5 * ve * dt) * sinhc(0.5 * ve * dt);
+        for (int a = 0; a < 3; ++a) s->box[a] *= e1;
+        for (int64_t i = 0; i < s->n; ++i) {
+          s->x[i] = wrap(s->x[i] * e1 + s->vx[i] * e2, s->box[0]);
+          s->y[i] = wrap(s->y[i] * e1 + s->vy[i] * e2, s->box[1]);
+          s->z[i] = wrap(s->z[i] * e1 + s->vz[i] * e2, s->box[2]);
+        }
+        if (build_neighbours(s)) return -1;
+        compute_rho(s);
+        orc_forces(s, s->fx, s->fy, s->fz);
+        kick(s, h, npt ? (1.0 + 3.0 / nf) * s->veps : 0.0);
+        if (npt) {
+          s->veps += h * baro_force(s, twice_ke(s));
+          s->veps *= nhc_propagate(s->chain, s->Qb, s->xib, s->etab, s->W * s->veps * s->veps, kT, kT, h);
+        }
+        scale_v(s, nhc_propagate(s->chain, s->Q, s->xi, s->eta, twice_ke(s), nf * kT, kT, h));
+      } else {
+        scale_v(s, nhc_propagate(s->chain, s->Q, s->xi, s->eta, twice_ke(s), nf * kT, kT, h));
+        if (npt) {
+          s->veps *= nhc_propagate(s->chain, s->Qb, s->xib, s->etab, s->W * s->veps * s->veps, kT, kT, h);
+          s->veps += h * baro_force(s, twice_ke(s));
+        }
+        kick(s, h, npt ? (1.0 + 3.0 / nf) * s->veps : 0.0);
+      }
+    }
+    s->md_step++;
+  }
+  s->energy = orc_energy_full(s);
+  return 0;
+}
+
+void orc_md_state(orc_sys* s, double out[9]) {
+  double K2 = s->vx ? twice_ke(s) : 0.0, nf = 3.0 * (double)s->n, kT = KB_EV * s->T_md;
+  double V = s->box[0] * s->box[1] * s->box[2];
+  double pe = orc_energy_full(s);
+  double vir = orc_virial(s);
+  double H = 0.5 * K2 + pe;
+  if (s->ens) {
+    for (int k = 0; k < s->chain; ++k) H += 0.5 * s->Q[k] * s->xi[k] * s->xi[k] + (k == 0 ? nf : 1.0) * kT * s->eta[k];
+    if (s->ens == 2) {
+      H += s->p_ext * V + 0.5 * s->W * s->veps * s->veps;
+      for (int k = 0; k < s->chain; ++k) H += 0.5 * s->Qb[k] * s->xib[k] * s->xib[k] + kT * s->etab[k];
+    }
+  }
+  out[0] = 0.5 * K2;
+  out[1] = pe;
+  out[2] = K2 / (nf * KB_EV);
+  out[3] = (K2 + vir) / (3.0 * V) / BAR_EV_A3;
+  out[4] = V;
+  out[5] = H;
+  out[6] = s->box[0];
+  out[7] = s->box[1];
+  out[8] = s->box[2];
+}
+
+/* ------------------------------------------------- conjugate gradients */
+static double dot3(const orc_sys* s, const double* a, const double* b) {
+  double t = 0.0;
+  for (int64_t i = 0; i < 3 * s->n; ++i) t += a[i] * b[i];
+  (void)s;
+  return t;
+}
+
+/* energy and forces at x0 + alpha d (positions wrapped), into f */
+static double eval_at(orc_sys* s, const double* x0, const double* d, double alpha, double* f) {
+  for (int64_t i = 0; i < s->n; ++i) {
+    s->x[i] = wrap(x0[i] + alpha * d[i], s->box[0]);
+    s->y[i] = wrap(x0[s->n + i] + alpha * d[s->n + i], s->box[1]);
+    s->z[i] = wrap(x0[2 * s->n + i] + alpha * d[2 * s->n + i], s->box[2]);
+  }
+  build_neighbours(s);
+  compute_rho(s);
+  orc_forces(s, f, f + s->n, f + 2 * s->n);
+  return orc_energy_full(s);
+}
+
+int orc_minimize(orc_sys* s, double ftol, int64_t max_iter, int64_t* iters, double* fmax_out) {
+  int64_t n3 = 3 * s->n;
+  double* x0 = (double*)malloc(sizeof(double) * n3);
+  double* f = (double*)malloc(sizeof(double) * n3);
+  double* g = (double*)malloc(sizeof(double) * n3);
+  double* d = (double*)malloc(sizeof(double) * n3);
+  if (!x0 || !f || !g || !d) { free(x0); free(f); free(g); free(d); return -1; }
+  memcpy(x0, s->x, sizeof(double) * s->n);
+  memcpy(x0 + s->n, s->y, sizeof(double) * s->n);
+  memcpy(x0 + 2 * s->n, s->z, sizeof(double) * s->n);
+  eval_at(s, x0, x0, 0.0, f);
+  memcpy(d, f, sizeof(double) * n3);
+  double ff = dot3(s, f, f), step = 0.0;
+  int64_t it = 0;
+  int rc = 1;
+  double fmax = 0.0;
+  for (; it < max_iter; ++it) {
+    fmax = 0.0;
+    for (int64_t i = 0; i < s->n; ++i) {
+      double a = sqrt(f[i] * f[i] + f[s->n + i] * f[s->n + i] + f[2 * s->n + i] * f[2 * s->n + i]);
+      if (a > fmax) fmax = a;
+    }
+    if (fmax < ftol) { rc = 0; break; }
+    /* line search: a zero of phi'(alpha) = -F(x0 + alpha d) . d by secant
+     * steps from 0 and a first step that moves no atom more than 0.05 A */
+    double dmax = 0.0;
+    for (int64_t i = 0; i < s->n; ++i) {
+      double a = sqrt(d[i] * d[i] + d[s->n + i] * d[s->n + i] + d[2 * s->n + i] * d[2 * s->n + i]);
+      if (a > dmax) dmax = a;
+    }
+    double a0 = 0.0, p0 = -dot3(s, f, d), pstart = fabs(p0);
+    double a1 = step > 0.0 ? step : 0.05 / dmax;
+    if (a1 * dmax > 0.2) a1 = 0.2 / dmax;
+    eval_at(s, x0, d, a1, g);
+    double p1 = -dot3(s, g, d);
+    /* extend until the derivative changes sign */
+    for (int ls = 0; ls < 30 && p1 < 0.0 && fabs(p1) > 1e-3 * pstart; ++ls) {
+      a0 = a1;
+      p0 = p1;
+      a1 *= 2.0;
+      eval_at(s, x0, d, a1, g);
+      p1 = -dot3(s, g, d);
+    }
+    /* regula falsi inside [a0, a1] (p0 < 0 < p1) */
+    for (int ls = 0; ls < 40 && fabs(p1) > 1e-3 * pstart && p1 > 0.0; ++ls) {
+      double a2 = a0 - p0 * (a1 - a0) / (p1 - p0);
+      eval_at(s, x0, d, a2, g);
+      double p2 = -dot3(s, g, d);
+      if (p2 < 0.0) {
+        a0 = a2;
+        p0 = p2;
+        if (fabs(p2) <= 1e-3 * pstart) {
+          a1 = a2;
+          p1 = p2;
+        }
+      } else {
+        a1 = a2;
+        p1 = p2;
+      }
+    }
+    if (p1 > 0.0 && fabs(p1) > 1e-3 * pstart) eval_at(s, x0, d, a1, g); /* positions at a1 */
+    step = a1;
+    for (int64_t i = 0; i < s->n; ++i) {
+      x0[i] = s->x[i];
+      x0[s->n + i] = s->y[i];
+      x0[2 * s->n + i] = s->z[i];
+    }
+    /* Polak-Ribiere with restart */
+    double gg = dot3(s, g, g), gf = dot3(s, g, f);
+    double beta = (gg - gf) / ff;
+    if (beta < 0.0) beta = 0.0;
+    for (int64_t k = 0; k < n3; ++k) d[k] = g[k] + beta * d[k];
+    if (dot3(s, g, d) <= 0.0) memcpy(d, g, sizeof(double) * n3);
+    memcpy(f, g, sizeof(double) * n3);
+    ff = gg;
+  }
+  if (s->fx) memcpy(s->fx, f, sizeof(double) * s->n), memcpy(s->fy, f + s->n, sizeof(double) * s->n),
+      memcpy(s->fz, f + 2 * s->n, sizeof(double) * s->n);
+  s->energy = orc_energy_full(s);
+  if (iters) *iters = it;
+  if (fmax_out) *fmax_out = fmax;
+  free(x0); free(f); free(g); free(d);
+  return rc;
 }
 
 void orc_get_md(const orc_sys* s, double* x, double* y, double* z, double* vx, double* vy,

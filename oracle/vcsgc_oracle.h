@@ -206,6 +206,29 @@ double orc_kinetic_energy(const orc_sys* s);
  * sqrt(m_old/m_new). */
 int orc_hybrid_cycles(orc_sys* s, int64_t n_cycles, int64_t n_md, int64_t n_mc);
 
+/* The paper's MD ensemble (Sec. IV B: Nose-Hoover thermostat and barostat)
+ * in the isotropic form of Martyna, Tobias, Klein (J. Chem. Phys. 101, 4177
+ * (1994)) with Nose-Hoover chains (Martyna, Klein, Tuckerman, J. Chem.
+ * Phys. 97, 2635 (1992)), integrated by a Trotter splitting (Martyna,
+ * Tuckerman, Tobias, Klein, Mol. Phys. 87, 1117 (1996)).
+ *   kind 0: Langevin (orc_set_md's gamma), 1: NVT, 2: NPT.
+ *   t_damp, p_damp: relaxation times (fs); p_ext in bar; chain: M <= 4.
+ * Masses: Q_1 = N_f kT t_damp^2, Q_k = kT t_damp^2 (k > 1); barostat
+ * W = (N_f + 3) kT p_damp^2 and its chain kT p_damp^2; N_f = 3 N.
+ * Returns 0 or -1. */
+#define ORC_MAX_CHAIN 4
+int orc_set_ensemble(orc_sys* s, int kind, double t_damp, double p_damp, double p_ext_bar, int chain);
+/* Virial sum over pairs r_ij . F_ij (eV) at the current positions. */
+double orc_virial(orc_sys* s);
+/* out[0..8]: kinetic energy, potential energy, temperature (K), pressure
+ * (bar), volume (A^3), conserved extended energy (eV), box x, y, z. */
+void orc_md_state(orc_sys* s, double out[9]);
+/* Polak-Ribiere conjugate-gradient minimisation of the potential energy in
+ * the positions (box and species fixed) until max |F_i| < ftol (eV/A) or
+ * max_iter iterations; the line search finds a zero of the directional
+ * derivative by secant steps.  Returns 0 (converged), 1 (max_iter) or -1. */
+int orc_minimize(orc_sys* s, double ftol, int64_t max_iter, int64_t* iters, double* fmax);
+
 #ifdef __cplusplus
 }
 #endif

@@ -172,6 +172,15 @@ def eam_tables(p: EAMParams | None = None) -> EAMTables:
                      dens=dens, ddens=ddens, embed=emb, dembed=demb)
 
 
+def npt_eam_params(**kw) -> EAMParams:
+    """The synthetic EAM with the embedding's rho^2 coefficient raised from
+    1e-3 to 0.0119446 so that the perfect BCC crystal at a = 2.855 A is at
+    zero pressure and mechanically stable (the workloads' coefficient leaves
+    it at about -880 kbar, with the energy falling under compression): for
+    constant-pressure MD."""
+    return EAMParams(c2=0.0119446, **kw)
+
+
 def multi_eam_params(K: int, dens_scale=None, **kw) -> EAMParams:
     """K-species form of the synthetic EAM (K = 2..4): the binary's A and B
     plus C and D.  Pair scales in the order (0,0), (0,1), ..., (K-1,K-1);
