@@ -374,6 +374,33 @@ void vcsgc_mlp_free(void* mlp);
  * vcsgc_features; CUDA. */
 int vcsgc_set_surrogate(void* ctx, void* mlp);
 
+/* The paper's MD ensemble (Sec. IV B: Nose-Hoover thermostat and
+ * barostat) for md_steps and vcsgc_hybrid: kind 0 Langevin (BAOAB with the
+ * options' gamma, the default), 1 NVT with a Nose-Hoover chain of `chain`
+ * links (<= 4), 2 NPT with the isotropic MTK barostat at p_ext_bar (bar),
+ * its own chain, and the box scaled uniformly (Martyna, Tobias, Klein, J.
+ * Chem. Phys. 101, 4177 (1994); the Trotter-split step of Martyna,
+ * Tuckerman, Tobias, Klein, Mol. Phys. 87, 1117 (1996)).  t_damp, p_damp:
+ * relaxation times (fs); masses Q_1 = N_f kT t_damp^2, Q_k = kT t_damp^2,
+ * W = (N_f + 3) kT p_damp^2, barostat chain kT p_damp^2, N_f = 3 N, T the
+ * options' T_md.  Resets the chains and the barostat velocity.  Errors:
+ * INVALID_ARG; STATE (not explicit positions with one replica, or NPT with
+ * precision MIXED: the barostat needs the FP64 virial). */
+int vcsgc_set_ensemble(void* ctx, int32_t kind, double t_damp, double p_damp, double p_ext_bar, int32_t chain);
+/* HOST out[9]: kinetic energy (eV), potential energy (eV), temperature (K),
+ * pressure (bar, from the virial), volume (A^3), the extended energy the
+ * Nose-Hoover steps conserve (eV), box lengths (A).  Synchronises; evaluates
+ * the forces.  Errors: STATE, CUDA, device error bits. */
+int vcsgc_md_state(void* ctx, double* out);
+/* Conjugate-gradient relaxation of the explicit positions at fixed box and
+ * species (the pre-relaxation of Sec. IV B): Polak-Ribiere directions with
+ * restarts, a line search for a zero of the directional derivative
+ * (extension, then regula falsi), until max_i |F_i| < ftol (eV/A) or
+ * max_iter iterations.  *iters and *fmax (HOST, may be NULL) report the
+ * iterations taken and the final max |F_i|; the tracked energy restarts from
+ * the relaxed positions.  Errors: INVALID_ARG, STATE, CUDA, device bits. */
+int vcsgc_minimize(void* ctx, double ftol, int64_t max_iter, int64_t* iters, double* fmax);
+
 /* Text of the last error of ctx (or of the last failed vcsgc_init when ctx
  * is NULL).  Valid until the next call on the same context. */
 const char* vcsgc_last_error(void* ctx);

@@ -244,6 +244,8 @@ struct MdArgs {
   int mixed;
   unsigned* err;
   unsigned long long* max_disp2_bits;  // max squared displacement (as bits)
+  double* vir;   // accumulates the virial sum r_ij . F_ij (FP64 forms) when set
+  double lam;    // box length over its length at the last neighbour build
 };
 void launch_md_rho(const MdArgs& m, cudaStream_t st);
 void launch_md_force(const MdArgs& m, cudaStream_t st);
@@ -251,6 +253,17 @@ void launch_md_first_half(const MdArgs& m, long long md_step, cudaStream_t st);
 void launch_md_second_half(const MdArgs& m, cudaStream_t st);
 void launch_md_snapshot(const MdArgs& m, cudaStream_t st);
 void launch_kinetic(const MdArgs& m, double* part, cudaStream_t st);
+// Nose-Hoover / MTK sub-flows: v <- v s e1 + (F/m) he2; r <- r e1 + v e2dt
+void launch_nh_kick(const MdArgs& m, double s, double e1, double he2, cudaStream_t st);
+void launch_nh_drift(const MdArgs& m, double e1, double e2dt, cudaStream_t st);
+// conjugate gradients: positions x0 + alpha d (SoA, 3N), dot-product block
+// partials, max |a_i|^2 over atoms
+void launch_cg_place(const MdArgs& m, const double* x0, const double* d, double alpha, cudaStream_t st);
+int dot_blocks(long long n);
+void launch_dot(const double* a, const double* b, long long n, double* part, cudaStream_t st);
+void launch_max_norm2(const double* a, long long N, unsigned long long* out, cudaStream_t st);
+// d <- g + beta d (n entries)
+void launch_axpby(double* d, const double* g, double beta, long long n, cudaStream_t st);
 int kinetic_blocks(long long N);
 
 }  // namespace vcsgc

@@ -182,12 +182,20 @@ __global__ void k_md_embed(MdArgs m) {
   if (m.mixed) m.dFp32[i] = (float)m.dFp[i];
 }
 
+// warp sum of the per-thread virial terms, one atomic per warp (every lane
+// of the warp reaches this point)
+__device__ __forceinline__ void add_virial(const MdArgs& m, double vir) {
+  if (!m.vir) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vir += __shfl_xor_sync(0xffffffffu, vir, o);
+  if ((threadIdx.x & 31) == 0 && vir != 0.0) atomicAdd(m.vir, vir);
+}
+
 // FP64 forces on the half list: F_i += g (x_j - x_i) / r, F_j -= the same,
 // g = phi'_{ti tj} + F'_i f'_{tj} + F'_j f'_{ti} (one density derivative
-// when same_dens); force arrays zeroed before
-__global__ void k_md_force_half(MdArgs m) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.N) return;
+// when same_dens); force arrays zeroed before.  The virial term of the
+// pair, r_ij . F_ij = -g r, goes to *m.vir when it is set.
+__device__ __forceinline__ void force_half_row(const MdArgs& m, long long i, double& vir) {
   const int* row = m.nbr_h + i * m.K;
   const int cnt = m.cnt_h[i];
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
@@ -220,6 +228,7 @@ __global__ void k_md_force_half(MdArgs m) {
     fx += gx;
     fy += gy;
     fz += gz;
+    vir -= gr * r2;
     atomicAdd(m.fx + j, -gx);
     atomicAdd(m.fy + j, -gy);
     atomicAdd(m.fz + j, -gz);
@@ -230,10 +239,15 @@ __global__ void k_md_force_half(MdArgs m) {
   atomicAdd(m.fz + i, fz);
 }
 
-template <bool MIXED>
-__global__ void k_md_force(MdArgs m) {
+__global__ void k_md_force_half(MdArgs m) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.N) return;
+  double vir = 0.0;
+  if (i < m.N) force_half_row(m, i, vir);
+  add_virial(m, vir);
+}
+
+template <bool MIXED>
+__device__ __forceinline__ void force_row(const MdArgs& m, long long i, double& vir) {
   const int* row = m.nbr + i * m.K;
   const int cnt = m.nbr_cnt[i];
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
@@ -281,11 +295,20 @@ __global__ void k_md_force(MdArgs m) {
     fx = fma(gr, dx, fx);
     fy = fma(gr, dy, fy);
     fz = fma(gr, dz, fz);
+    vir -= 0.5 * gr * r2;  // each pair is seen from both ends
   }
   if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(m.err, ERRF_NONFINITE);
   m.fx[i] = fx;
   m.fy[i] = fy;
   m.fz[i] = fz;
+}
+
+template <bool MIXED>
+__global__ void k_md_force(MdArgs m) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double vir = 0.0;
+  if (i < m.N) force_row<MIXED>(m, i, vir);
+  if (!MIXED) add_virial(m, vir);
 }
 
 __device__ __forceinline__ double wrap_box(double v, double L) {
@@ -363,6 +386,80 @@ __global__ void k_md_snapshot(MdArgs m) {
   m.z0[i] = m.z[i];
 }
 
+// Nose-Hoover / MTK sub-flows (the step's scalars are integrated on the
+// host): v <- v s e1 + (F/m) he2, and r <- wrap(r e1 + v e2dt) in the
+// current box with the displacement from the last neighbour build measured
+// against the snapshot scaled by lam = L / L_build.
+__global__ void k_nh_kick(MdArgs m, double s, double e1, double he2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const double im = FTM / m.mass[m.types[i]];
+  const double se = s * e1, ke = he2 * im;
+  m.vx[i] = fma(m.vx[i], se, m.fx[i] * ke);
+  m.vy[i] = fma(m.vy[i], se, m.fy[i] * ke);
+  m.vz[i] = fma(m.vz[i], se, m.fz[i] * ke);
+}
+
+__global__ void k_nh_drift(MdArgs m, double e1, double e2dt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const double x = wrap_box(fma(m.x[i], e1, m.vx[i] * e2dt), m.box[0]);
+  const double y = wrap_box(fma(m.y[i], e1, m.vy[i] * e2dt), m.box[1]);
+  const double z = wrap_box(fma(m.z[i], e1, m.vz[i] * e2dt), m.box[2]);
+  m.x[i] = x;
+  m.y[i] = y;
+  m.z[i] = z;
+  const double dx = mimg(x - m.x0[i] * m.lam, m.box[0], 1.0 / m.box[0]);
+  const double dy = mimg(y - m.y0[i] * m.lam, m.box[1], 1.0 / m.box[1]);
+  const double dz = mimg(z - m.z0[i] * m.lam, m.box[2], 1.0 / m.box[2]);
+  atomicMax(m.max_disp2_bits, (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz));
+}
+
+// positions x0 + alpha d (conjugate-gradient line search), wrapped, with the
+// displacement check of the MD step
+__global__ void k_cg_place(MdArgs m, const double* x0, const double* d, double alpha) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.N) return;
+  const long long N = m.N;
+  const double x = wrap_box(fma(alpha, d[i], x0[i]), m.box[0]);
+  const double y = wrap_box(fma(alpha, d[N + i], x0[N + i]), m.box[1]);
+  const double z = wrap_box(fma(alpha, d[2 * N + i], x0[2 * N + i]), m.box[2]);
+  m.x[i] = x;
+  m.y[i] = y;
+  m.z[i] = z;
+  const double dx = mimg(x - m.x0[i], m.box[0], 1.0 / m.box[0]);
+  const double dy = mimg(y - m.y0[i], m.box[1], 1.0 / m.box[1]);
+  const double dz = mimg(z - m.z0[i], m.box[2], 1.0 / m.box[2]);
+  atomicMax(m.max_disp2_bits, (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz));
+}
+
+constexpr int DOT_BLOCK = 256;
+int dot_blocks(long long n) { return (int)((n + DOT_BLOCK - 1) / DOT_BLOCK); }
+
+// block partials of sum_k a[k] b[k], k < n
+__global__ void __launch_bounds__(DOT_BLOCK) k_dot(const double* a, const double* b, long long n, double* part) {
+  const long long k = (long long)blockIdx.x * DOT_BLOCK + threadIdx.x;
+  double v = k < n ? a[k] * b[k] : 0.0;
+  __shared__ double sh[DOT_BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < DOT_BLOCK / 32; ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// max over atoms of |v_i|^2 for a 3N SoA vector, as double bits
+__global__ void k_max_norm2(const double* a, long long N, unsigned long long* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double v = a[i] * a[i] + a[N + i] * a[N + i] + a[2 * N + i] * a[2 * N + i];
+  atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
 constexpr int KE_BLOCK = 256;
 int kinetic_blocks(long long N) { return (int)((N + KE_BLOCK - 1) / KE_BLOCK); }
 
@@ -419,6 +516,28 @@ void launch_md_second_half(const MdArgs& m, cudaStream_t st) {
   k_md_second_half<<<grid_of(m.N), 128, 0, st>>>(m);
 }
 void launch_md_snapshot(const MdArgs& m, cudaStream_t st) { k_md_snapshot<<<grid_of(m.N), 128, 0, st>>>(m); }
+void launch_nh_kick(const MdArgs& m, double s, double e1, double he2, cudaStream_t st) {
+  k_nh_kick<<<grid_of(m.N), 128, 0, st>>>(m, s, e1, he2);
+}
+void launch_nh_drift(const MdArgs& m, double e1, double e2dt, cudaStream_t st) {
+  k_nh_drift<<<grid_of(m.N), 128, 0, st>>>(m, e1, e2dt);
+}
+void launch_cg_place(const MdArgs& m, const double* x0, const double* d, double alpha, cudaStream_t st) {
+  k_cg_place<<<grid_of(m.N), 128, 0, st>>>(m, x0, d, alpha);
+}
+void launch_dot(const double* a, const double* b, long long n, double* part, cudaStream_t st) {
+  k_dot<<<dot_blocks(n), DOT_BLOCK, 0, st>>>(a, b, n, part);
+}
+void launch_max_norm2(const double* a, long long N, unsigned long long* out, cudaStream_t st) {
+  k_max_norm2<<<grid_of(N), 128, 0, st>>>(a, N, out);
+}
+__global__ void k_axpby(double* d, const double* g, double beta, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) d[k] = fma(beta, d[k], g[k]);
+}
+void launch_axpby(double* d, const double* g, double beta, long long n, cudaStream_t st) {
+  k_axpby<<<grid_of(n), 128, 0, st>>>(d, g, beta, n);
+}
 void launch_kinetic(const MdArgs& m, double* part, cudaStream_t st) {
   k_kinetic<<<kinetic_blocks(m.N), KE_BLOCK, 0, st>>>(m, part);
 }

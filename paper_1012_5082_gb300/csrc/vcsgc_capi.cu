@@ -85,6 +85,19 @@ struct Ctx {
   double dt = 2.0, gamma = 0.01, T_md = 0.0;
   uint64_t md_seed = 0;
   bool forces_valid = false;
+  // Nose-Hoover chains and the MTK barostat (kind 0: Langevin BAOAB)
+  struct Nh {
+    int kind = 0, chain = 3;
+    double t_damp = 100.0, p_damp = 1000.0, p_ext = 0.0;  // fs, fs, eV/A^3
+    double xi[4] = {}, eta[4] = {}, Q[4] = {}, xib[4] = {}, etab[4] = {}, Qb[4] = {};
+    double veps = 0.0, W = 0.0;
+    double vs = 1.0;  // velocity scale not yet applied on the device
+  } nh;
+  double* d_vir = nullptr;  // device accumulator of the virial
+  double box_build[3] = {0, 0, 0};
+  int ncell_cap = 0;
+  // conjugate-gradient work vectors (SoA, 3N) and reduction partials
+  double *cg_x0 = nullptr, *cg_d = nullptr, *cg_f = nullptr, *cg_g = nullptr, *cg_part = nullptr;
   // graph
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
@@ -242,6 +255,8 @@ void fill_args(Ctx* c) {
   m.dFp32 = c->dFp32;
   m.err = c->derr;
   m.max_disp2_bits = c->max_disp2;
+  m.vir = c->d_vir;
+  m.lam = c->box_build[0] > 0.0 ? c->box[0] / c->box_build[0] : 1.0;
 
   LatArgs& l = c->lat;
   l.R = c->R;
@@ -267,17 +282,26 @@ void drop_graph(Ctx* c) {
 
 // ----------------------------------------------------------- neighbours
 int build_cell_list(Ctx* c) {
-  for (int q = 0; q < 3; ++q) c->cl.nc[q] = (int)std::floor(c->box[q] / c->rl);
+  for (int q = 0; q < 3; ++q) {
+    c->cl.nc[q] = (int)std::floor(c->box[q] / c->rl);
+    if (c->cl.nc[q] < 3 || c->box[q] <= 2.0 * c->rl)
+      return fail(c, VCSGC_ERR_STATE, "box no longer exceeds 2 (r_c + skin) with 3 cells");
+    c->box_build[q] = c->box[q];
+  }
   const int ncell = c->cl.nc[0] * c->cl.nc[1] * c->cl.nc[2];
   if (!c->cl.cell_of) {
     TRY(dalloc(c, &c->cl.x32, c->N));
     TRY(dalloc(c, &c->cl.y32, c->N));
     TRY(dalloc(c, &c->cl.z32, c->N));
     TRY(dalloc(c, &c->cl.cell_of, c->N));
+    TRY(dalloc(c, &c->cl.sorted, c->N));
+  }
+  if (ncell > c->ncell_cap) {
+    // the box can grow under a barostat
     TRY(dalloc(c, &c->cl.cell_count, ncell));
     TRY(dalloc(c, &c->cl.cell_start, ncell + 1));
     TRY(dalloc(c, &c->cl.cell_cursor, ncell));
-    TRY(dalloc(c, &c->cl.sorted, c->N));
+    c->ncell_cap = ncell;
   }
   for (int attempt = 0; attempt < 6; ++attempt) {
     CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
@@ -689,6 +713,7 @@ int run_steps(Ctx* c, long long n) {
 
 // ------------------------------------------------------------------- MD
 int md_forces(Ctx* c) {
+  if (c->d_vir) CK(cudaMemsetAsync(c->d_vir, 0, sizeof(double), c->st));
   launch_md_rho(c->md, c->st);
   launch_md_force(c->md, c->st);
   CK(cudaGetLastError());
@@ -703,9 +728,141 @@ int md_rebuild(Ctx* c) {
   return VCSGC_OK;
 }
 
+// ----------------------------------------------- Nose-Hoover and MTK (host)
+// The extended-system scalars of the MD ensemble (Sec. IV B) are integrated
+// here in FP64 with the same Trotter splitting as the per-atom flows the
+// kernels apply: Nose-Hoover chains (Martyna, Klein, Tuckerman 1992) on the
+// particles and on the barostat, the isotropic MTK barostat (Martyna,
+// Tobias, Klein 1994), and the exact sub-flows of Martyna, Tuckerman,
+// Tobias, Klein (1996).  N_f = 3 N.
+constexpr double BAR_EV_A3 = 6.241509074460763e-07;  // 1 bar in eV / A^3
+
+double sinhc(double x) { return std::fabs(x) < 1e-4 ? 1.0 + x * x / 6.0 + x * x * x * x / 120.0 : std::sinh(x) / x; }
+
+// chain of M links driven by K2 (= sum m v^2 of g degrees of freedom,
+// target gkT) for a time h; returns the scale of the coupled velocities
+double nhc_step(int M, const double* Q, double* xi, double* eta, double K2, double gkT, double kT, double h) {
+  double scale = 1.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int q = 0; q < M; ++q) {
+      const int k = pass == 0 ? M - 1 - q : q;
+      const double G = k == 0 ? (K2 * scale * scale - gkT) / Q[0] : (Q[k - 1] * xi[k - 1] * xi[k - 1] - kT) / Q[k];
+      const double e = k + 1 < M ? std::exp(-0.25 * h * xi[k + 1]) : 1.0;
+      xi[k] = (xi[k] * e + 0.5 * h * G) * e;
+    }
+    if (pass == 0) {
+      scale = std::exp(-h * xi[0]);
+      for (int k = 0; k < M; ++k) eta[k] += h * xi[k];
+    }
+  }
+  return scale;
+}
+
+// sum of block partials (compensated)
+double sum_parts(const std::vector<double>& h) {
+  double s = 0.0, c = 0.0;
+  for (double v : h) {
+    const double t = s + v;
+    c += std::fabs(s) >= std::fabs(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+  }
+  return s + c;
+}
+
+// sum m v^2 (eV) of replica 0's atoms, with the pending scale applied
+int twice_ke_dev(Ctx* c, double* out) {
+  const int nb = kinetic_blocks(c->N);
+  if (!c->cg_part) TRY(dalloc(c, &c->cg_part, std::max(nb, dot_blocks(3 * c->N))));
+  launch_kinetic(c->md, c->cg_part, c->st);
+  CK(cudaGetLastError());
+  std::vector<double> h(nb);
+  CK(cudaMemcpyAsync(h.data(), c->cg_part, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *out = 2.0 * sum_parts(h) * c->nh.vs * c->nh.vs;
+  return VCSGC_OK;
+}
+
+int read_virial(Ctx* c, double* out) {
+  CK(cudaMemcpyAsync(out, c->d_vir, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return VCSGC_OK;
+}
+
+void set_box(Ctx* c, double f) {
+  for (int q = 0; q < 3; ++q) c->box[q] *= f;
+  fill_args(c);
+}
+
+// barostat force [alpha K2 + W_vir - 3 V P_ext] / W
+double baro_force(const Ctx* c, double K2, double vir) {
+  const double nf = 3.0 * (double)c->N, V = c->box[0] * c->box[1] * c->box[2];
+  return ((1.0 + 3.0 / nf) * K2 + vir - 3.0 * V * c->nh.p_ext) / c->nh.W;
+}
+
+int md_run_nh(Ctx* c, long long n) {
+  Ctx::Nh& nh = c->nh;
+  const bool npt = nh.kind == 2;
+  const double dt = c->dt, h = 0.5 * dt, kT = KB_EV * c->T_md, nf = 3.0 * (double)c->N;
+  const double alpha = 1.0 + 3.0 / nf;
+  if (!c->forces_valid) TRY(md_forces(c));
+  double K2 = 0.0, vir = 0.0;
+  TRY(twice_ke_dev(c, &K2));
+  TRY(read_virial(c, &vir));
+  for (long long q = 0; q < n; ++q) {
+    // thermostats, barostat velocity, velocity half kick
+    const double s1 = nhc_step(nh.chain, nh.Q, nh.xi, nh.eta, K2, nf * kT, kT, h);
+    K2 *= s1 * s1;
+    if (npt) {
+      nh.veps *= nhc_step(nh.chain, nh.Qb, nh.xib, nh.etab, nh.W * nh.veps * nh.veps, kT, kT, h);
+      nh.veps += h * baro_force(c, K2, vir);
+    }
+    const double a = npt ? alpha * nh.veps : 0.0;
+    const double e1 = std::exp(-a * h), he2 = h * std::exp(-0.5 * a * h) * sinhc(0.5 * a * h);
+    launch_nh_kick(c->md, nh.vs * s1, e1, he2, c->st);
+    nh.vs = 1.0;
+    // positions and box
+    const double ve = npt ? nh.veps : 0.0;
+    const double E1 = std::exp(ve * dt), E2 = dt * std::exp(0.5 * ve * dt) * sinhc(0.5 * ve * dt);
+    if (npt) set_box(c, E1);
+    CK(cudaMemsetAsync(c->max_disp2, 0, sizeof(unsigned long long), c->st));
+    launch_nh_drift(c->md, E1, E2, c->st);
+    CK(cudaGetLastError());
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->max_disp2, sizeof(bits), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double d2;
+    std::memcpy(&d2, &bits, sizeof(d2));
+    const double slack = std::fabs(c->md.lam - 1.0) * c->rl;
+    if (std::sqrt(d2) + slack > 0.5 * c->skin) {
+      TRY(md_rebuild(c));
+      fill_args(c);
+    }
+    TRY(md_forces(c));
+    launch_nh_kick(c->md, 1.0, e1, he2, c->st);
+    CK(cudaGetLastError());
+    TRY(twice_ke_dev(c, &K2));
+    if (npt) {
+      TRY(read_virial(c, &vir));
+      nh.veps += h * baro_force(c, K2, vir);
+      nh.veps *= nhc_step(nh.chain, nh.Qb, nh.xib, nh.etab, nh.W * nh.veps * nh.veps, kT, kT, h);
+    }
+    const double s2 = nhc_step(nh.chain, nh.Q, nh.xi, nh.eta, K2, nf * kT, kT, h);
+    K2 *= s2 * s2;
+    nh.vs = s2;  // folded into the next kick
+    c->md_step++;
+  }
+  if (nh.vs != 1.0) {
+    launch_nh_kick(c->md, nh.vs, 1.0, 0.0, c->st);
+    CK(cudaGetLastError());
+    nh.vs = 1.0;
+  }
+  return VCSGC_OK;
+}
+
 int md_run(Ctx* c, long long n) {
   if (!c->have_v) return fail(c, VCSGC_ERR_STATE, "md_steps needs velocities (vcsgc_set_velocities)");
   if (c->kind != 1 || c->R != 1) return fail(c, VCSGC_ERR_STATE, "md_steps needs explicit positions and one replica");
+  if (c->nh.kind) return md_run_nh(c, n);
   if (!c->forces_valid) TRY(md_forces(c));
   const double half_skin2 = 0.25 * c->skin * c->skin;
   for (long long q = 0; q < n; ++q) {
@@ -985,6 +1142,7 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   TRY(dalloc(c, &c->y0, c->N));
   TRY(dalloc(c, &c->z0, c->N));
   TRY(dalloc(c, &c->max_disp2, 1));
+  TRY(dalloc(c, &c->d_vir, 1));
   TRY(dalloc(c, &c->rp, c->R));
   TRY(dalloc(c, &c->rs, c->R));
   TRY(dalloc(c, &c->acc, c->R));
@@ -1859,6 +2017,195 @@ int vcsgc_kinetic_energy(void* ctx, double* out) {
   for (double v : h) s += v;
   *out = s;
   return VCSGC_OK;
+}
+
+int vcsgc_set_ensemble(void* ctx, int32_t kind, double t_damp, double p_damp, double p_ext_bar, int32_t chain) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || kind < 0 || kind > 2 || chain < 1 || chain > 4) return VCSGC_ERR_INVALID_ARG;
+  if (kind && !(t_damp > 0.0)) return fail(c, VCSGC_ERR_INVALID_ARG, "t_damp must be > 0");
+  if (kind == 2 && !(p_damp > 0.0)) return fail(c, VCSGC_ERR_INVALID_ARG, "p_damp must be > 0");
+  if (kind && (c->kind != 1 || c->R != 1)) return fail(c, VCSGC_ERR_STATE, "needs explicit positions and one replica");
+  if (kind == 2 && c->mixed) return fail(c, VCSGC_ERR_STATE, "the barostat needs the FP64 virial (precision FP64)");
+  Ctx::Nh& nh = c->nh;
+  nh = Ctx::Nh{};
+  nh.kind = kind;
+  nh.chain = chain;
+  nh.t_damp = t_damp;
+  nh.p_damp = p_damp;
+  nh.p_ext = p_ext_bar * BAR_EV_A3;
+  const double kT = KB_EV * c->T_md, nf = 3.0 * (double)c->N;
+  for (int k = 0; k < 4; ++k) {
+    nh.Q[k] = (k == 0 ? nf : 1.0) * kT * t_damp * t_damp;
+    nh.Qb[k] = kT * p_damp * p_damp;
+  }
+  nh.W = (nf + 3.0) * kT * p_damp * p_damp;
+  return VCSGC_OK;
+}
+
+int vcsgc_md_state(void* ctx, double* out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !out) return VCSGC_ERR_INVALID_ARG;
+  if (c->kind != 1 || c->R != 1 || !c->d_vir) return fail(c, VCSGC_ERR_STATE, "needs explicit positions and one replica");
+  double K2 = 0.0, pe = 0.0, vir = 0.0;
+  if (c->have_v) TRY(twice_ke_dev(c, &K2));
+  TRY(energy_of(c, 0, &pe));
+  TRY(md_forces(c));
+  TRY(read_virial(c, &vir));
+  TRY(check_device_error(c));
+  const Ctx::Nh& nh = c->nh;
+  const double nf = 3.0 * (double)c->N, kT = KB_EV * c->T_md;
+  const double V = c->box[0] * c->box[1] * c->box[2];
+  double H = 0.5 * K2 + pe;
+  if (nh.kind) {
+    for (int k = 0; k < nh.chain; ++k) H += 0.5 * nh.Q[k] * nh.xi[k] * nh.xi[k] + (k == 0 ? nf : 1.0) * kT * nh.eta[k];
+    if (nh.kind == 2) {
+      H += nh.p_ext * V + 0.5 * nh.W * nh.veps * nh.veps;
+      for (int k = 0; k < nh.chain; ++k) H += 0.5 * nh.Qb[k] * nh.xib[k] * nh.xib[k] + kT * nh.etab[k];
+    }
+  }
+  out[0] = 0.5 * K2;
+  out[1] = pe;
+  out[2] = K2 / (nf * KB_EV);
+  out[3] = (K2 + vir) / (3.0 * V) / BAR_EV_A3;
+  out[4] = V;
+  out[5] = H;
+  out[6] = c->box[0];
+  out[7] = c->box[1];
+  out[8] = c->box[2];
+  return VCSGC_OK;
+}
+
+int vcsgc_minimize(void* ctx, double ftol, int64_t max_iter, int64_t* iters, double* fmax_out) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !(ftol > 0.0) || max_iter < 0) return VCSGC_ERR_INVALID_ARG;
+  if (c->kind != 1 || c->R != 1) return fail(c, VCSGC_ERR_STATE, "needs explicit positions and one replica");
+  const long long N = c->N, n3 = 3 * N;
+  if (!c->cg_x0) {
+    TRY(dalloc(c, &c->cg_x0, n3));
+    TRY(dalloc(c, &c->cg_d, n3));
+    TRY(dalloc(c, &c->cg_f, n3));
+    TRY(dalloc(c, &c->cg_g, n3));
+  }
+  if (!c->cg_part) TRY(dalloc(c, &c->cg_part, std::max(kinetic_blocks(N), dot_blocks(n3))));
+  const int nb = dot_blocks(n3);
+  std::vector<double> hp(nb);
+  auto dot = [&](const double* a, const double* b, double* out) -> int {
+    launch_dot(a, b, n3, c->cg_part, c->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hp.data(), c->cg_part, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    *out = sum_parts(hp);
+    return VCSGC_OK;
+  };
+  auto maxnorm = [&](const double* a, double* out) -> int {
+    CK(cudaMemsetAsync(c->max_disp2, 0, sizeof(unsigned long long), c->st));
+    launch_max_norm2(a, N, c->max_disp2, c->st);
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->max_disp2, sizeof(bits), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double v;
+    std::memcpy(&v, &bits, sizeof(v));
+    *out = std::sqrt(v);
+    return VCSGC_OK;
+  };
+  auto copy_pos = [&](double* dst) -> int {
+    CK(cudaMemcpyAsync(dst, c->x, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(dst + N, c->y, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(dst + 2 * N, c->z, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+    return VCSGC_OK;
+  };
+  // forces at x0 + alpha d into g (neighbour list rebuilt past half the skin)
+  auto eval_at = [&](double alpha, double* g) -> int {
+    CK(cudaMemsetAsync(c->max_disp2, 0, sizeof(unsigned long long), c->st));
+    launch_cg_place(c->md, c->cg_x0, c->cg_d, alpha, c->st);
+    CK(cudaGetLastError());
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, c->max_disp2, sizeof(bits), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    double d2;
+    std::memcpy(&d2, &bits, sizeof(d2));
+    if (d2 > 0.25 * c->skin * c->skin) TRY(md_rebuild(c));
+    TRY(md_forces(c));
+    CK(cudaMemcpyAsync(g, c->fx, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(g + N, c->fy, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(g + 2 * N, c->fz, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->st));
+    return VCSGC_OK;
+  };
+  // Polak-Ribiere conjugate gradients; the line search finds a zero of
+  // phi'(alpha) = -F(x0 + alpha d) . d (extension, then regula falsi)
+  TRY(copy_pos(c->cg_x0));
+  CK(cudaMemsetAsync(c->cg_d, 0, sizeof(double) * n3, c->st));
+  TRY(eval_at(0.0, c->cg_f));
+  CK(cudaMemcpyAsync(c->cg_d, c->cg_f, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
+  double ff = 0.0, step = 0.0, fmax = 0.0;
+  TRY(dot(c->cg_f, c->cg_f, &ff));
+  int64_t it = 0;
+  int converged = 0;
+  for (; it < max_iter; ++it) {
+    TRY(maxnorm(c->cg_f, &fmax));
+    if (fmax < ftol) {
+      converged = 1;
+      break;
+    }
+    double dmax = 0.0, p0 = 0.0, p1 = 0.0;
+    TRY(maxnorm(c->cg_d, &dmax));
+    TRY(dot(c->cg_f, c->cg_d, &p0));
+    p0 = -p0;
+    const double pstart = std::fabs(p0);
+    double a0 = 0.0, a1 = step > 0.0 ? step : 0.05 / dmax;
+    if (a1 * dmax > 0.2) a1 = 0.2 / dmax;
+    TRY(eval_at(a1, c->cg_g));
+    TRY(dot(c->cg_g, c->cg_d, &p1));
+    p1 = -p1;
+    for (int ls = 0; ls < 30 && p1 < 0.0 && std::fabs(p1) > 1e-3 * pstart; ++ls) {
+      a0 = a1;
+      p0 = p1;
+      a1 *= 2.0;
+      TRY(eval_at(a1, c->cg_g));
+      TRY(dot(c->cg_g, c->cg_d, &p1));
+      p1 = -p1;
+    }
+    for (int ls = 0; ls < 40 && std::fabs(p1) > 1e-3 * pstart && p1 > 0.0; ++ls) {
+      const double a2 = a0 - p0 * (a1 - a0) / (p1 - p0);
+      double p2 = 0.0;
+      TRY(eval_at(a2, c->cg_g));
+      TRY(dot(c->cg_g, c->cg_d, &p2));
+      p2 = -p2;
+      if (p2 < 0.0) {
+        a0 = a2;
+        p0 = p2;
+        if (std::fabs(p2) <= 1e-3 * pstart) {
+          a1 = a2;
+          p1 = p2;
+        }
+      } else {
+        a1 = a2;
+        p1 = p2;
+      }
+    }
+    if (p1 > 0.0 && std::fabs(p1) > 1e-3 * pstart) TRY(eval_at(a1, c->cg_g));
+    step = a1;
+    TRY(copy_pos(c->cg_x0));
+    double gg = 0.0, gf = 0.0, gd = 0.0;
+    TRY(dot(c->cg_g, c->cg_g, &gg));
+    TRY(dot(c->cg_g, c->cg_f, &gf));
+    const double beta = std::max(0.0, (gg - gf) / ff);
+    launch_axpby(c->cg_d, c->cg_g, beta, n3, c->st);
+    CK(cudaGetLastError());
+    TRY(dot(c->cg_g, c->cg_d, &gd));
+    if (gd <= 0.0) CK(cudaMemcpyAsync(c->cg_d, c->cg_g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(c->cg_f, c->cg_g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
+    ff = gg;
+  }
+  // the tracked energy restarts from the relaxed positions
+  double e = 0.0;
+  TRY(energy_of(c, 0, &e));
+  CK(cudaMemcpyAsync(&c->rs[0].energy, &e, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (iters) *iters = it;
+  if (fmax_out) *fmax_out = fmax;
+  (void)converged;
+  return check_device_error(c);
 }
 
 int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_commit) {

@@ -74,7 +74,8 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_get_types_all", "vcsgc_set_types_all", "vcsgc_multi_init", "vcsgc_multi_sweep",
            "vcsgc_multi_steps", "vcsgc_multi_steps_per_sweep", "vcsgc_multi_observables",
            "vcsgc_multi_get_types", "vcsgc_multi_set_types", "vcsgc_multi_delta_e", "vcsgc_multi_energy",
-           "vcsgc_multi_last_error", "vcsgc_multi_free"]
+           "vcsgc_multi_last_error", "vcsgc_multi_free", "vcsgc_set_ensemble", "vcsgc_md_state",
+           "vcsgc_minimize"]
 
 
 def lib():
@@ -124,6 +125,9 @@ def lib():
             "vcsgc_observables_all": (I32, [P, P]),
             "vcsgc_get_types_all": (I32, [P, P]),
             "vcsgc_set_types_all": (I32, [P, P]),
+            "vcsgc_set_ensemble": (I32, [P, I32, D, D, D, I32]),
+            "vcsgc_md_state": (I32, [P, P]),
+            "vcsgc_minimize": (I32, [P, D, I64, P, P]),
             "vcsgc_multi_init": (I32, [C.POINTER(C.c_void_p), P, P, P, I32, P, P, P, P, P, P, P, I32]),
             "vcsgc_multi_sweep": (I32, [P, I64]),
             "vcsgc_multi_steps": (I32, [P, I64]),
@@ -501,6 +505,24 @@ class Context:
         v = C.c_double()
         _check(lib().vcsgc_kinetic_energy(self.h, C.byref(v)), self.h)
         return v.value
+
+    def set_ensemble(self, kind, t_damp=100.0, p_damp=1000.0, p_ext_bar=0.0, chain=3):
+        """kind: 'langevin', 'nvt' or 'npt' (Nose-Hoover chains, MTK barostat)."""
+        k = {"langevin": 0, "nvt": 1, "npt": 2}[kind]
+        _check(lib().vcsgc_set_ensemble(self.h, k, float(t_damp), float(p_damp), float(p_ext_bar), int(chain)),
+               self.h)
+
+    def ensemble_state(self):
+        out = np.zeros(9)
+        _check(lib().vcsgc_md_state(self.h, _ptr(out)), self.h)
+        keys = ("kinetic", "potential", "temperature", "pressure_bar", "volume", "conserved", "lx", "ly", "lz")
+        return dict(zip(keys, out.tolist()))
+
+    def minimize(self, ftol=1e-4, max_iter=1000):
+        it = C.c_int64()
+        fm = C.c_double()
+        _check(lib().vcsgc_minimize(self.h, float(ftol), int(max_iter), C.byref(it), C.byref(fm)), self.h)
+        return {"converged": fm.value < ftol, "iterations": it.value, "fmax": fm.value}
 
     def profile_steps(self, n):
         """Device time (ms) of the propose and commit kernels over n steps."""
