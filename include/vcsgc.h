@@ -401,6 +401,19 @@ int vcsgc_md_state(void* ctx, double* out);
  * the relaxed positions.  Errors: INVALID_ARG, STATE, CUDA, device bits. */
 int vcsgc_minimize(void* ctx, double ftol, int64_t max_iter, int64_t* iters, double* fmax);
 
+/* Checkpoint and resume.  vcsgc_save applies the pending commit and writes
+ * to `path` every replica's species, its running state (step counters, B
+ * count, tracked energy, acceptance counters, concentration sums), the
+ * fused form's step base, and for explicit positions the positions, box,
+ * velocities, MD step and Nose-Hoover state.  vcsgc_load restores them into
+ * a context created from the same lattice, tables and options (checked:
+ * sizes, replica count, schedule, form); the Philox streams are counters, so
+ * n sweeps, save, load into a new context and m sweeps give the species of
+ * n + m sweeps bit for bit.  The surrogate (vcsgc_set_surrogate) is not
+ * saved.  Errors: INVALID_ARG (path, mismatch), CUDA. */
+int vcsgc_save(void* ctx, const char* path);
+int vcsgc_load(void* ctx, const char* path);
+
 /* Text of the last error of ctx (or of the last failed vcsgc_init when ctx
  * is NULL).  Valid until the next call on the same context. */
 const char* vcsgc_last_error(void* ctx);

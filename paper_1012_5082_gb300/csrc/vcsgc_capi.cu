@@ -2208,6 +2208,118 @@ int vcsgc_minimize(void* ctx, double ftol, int64_t max_iter, int64_t* iters, dou
   return check_device_error(c);
 }
 
+// ------------------------------------------------------ checkpoint / resume
+// File: "VCSGCCK1", a header of int64 (N, R, kind, schedule, fast,
+// sizeof(RepState), sizeof(Nh), have_v), rep_n[R], the species of every
+// replica, the RepState array, the fused step base, the MD step, the box,
+// then (explicit positions) x, y, z, (velocities) vx, vy, vz, and the
+// Nose-Hoover state.  Host byte order.
+static const char kCkMagic[8] = {'V', 'C', 'S', 'G', 'C', 'C', 'K', '1'};
+
+int vcsgc_save(void* ctx, const char* path) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !path) return VCSGC_ERR_INVALID_ARG;
+  TRY(sync_bytes(c, -1));
+  long long tot = 0;
+  for (int r = 0; r < c->R; ++r) tot += c->rep_n[r];
+  std::vector<uint8_t> types(tot);
+  long long off = 0;
+  for (int r = 0; r < c->R; ++r) {
+    CK(cudaMemcpyAsync(types.data() + off, c->rep_types[r], c->rep_n[r], cudaMemcpyDeviceToHost, c->st));
+    off += c->rep_n[r];
+  }
+  std::vector<RepState> rs(c->R);
+  CK(cudaMemcpyAsync(rs.data(), c->rs, sizeof(RepState) * c->R, cudaMemcpyDeviceToHost, c->st));
+  std::vector<double> md;
+  const bool pos = c->kind == 1;
+  if (pos) {
+    md.resize((c->have_v ? 6 : 3) * (size_t)c->N);
+    double* dst[6] = {c->x, c->y, c->z, c->vx, c->vy, c->vz};
+    for (int q = 0; q < (c->have_v ? 6 : 3); ++q)
+      CK(cudaMemcpyAsync(md.data() + q * c->N, dst[q], sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  TRY(check_device_error(c));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(c, VCSGC_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  const long long hdr[8] = {c->N, c->R, c->kind, c->sched_kind, c->fast ? 1 : 0, (long long)sizeof(RepState),
+                            (long long)sizeof(Ctx::Nh), c->have_v ? 1 : 0};
+  bool ok = std::fwrite(kCkMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            std::fwrite(c->rep_n.data(), sizeof(long long), c->R, f) == (size_t)c->R &&
+            std::fwrite(types.data(), 1, tot, f) == (size_t)tot &&
+            std::fwrite(rs.data(), sizeof(RepState), c->R, f) == (size_t)c->R &&
+            std::fwrite(&c->h_base, sizeof(long long), 1, f) == 1 && std::fwrite(&c->md_step, sizeof(long long), 1, f) == 1 &&
+            std::fwrite(c->box, sizeof(double), 3, f) == 3 &&
+            (md.empty() || std::fwrite(md.data(), sizeof(double), md.size(), f) == md.size()) &&
+            std::fwrite(&c->nh, sizeof(Ctx::Nh), 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? VCSGC_OK : fail(c, VCSGC_ERR_INVALID_ARG, std::string("write failed: ") + path);
+}
+
+int vcsgc_load(void* ctx, const char* path) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !path) return VCSGC_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(c, VCSGC_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  char magic[8];
+  long long hdr[8];
+  std::vector<long long> rep_n(c->R);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkMagic, 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, f) == 1;
+  ok = ok && hdr[0] == c->N && hdr[1] == c->R && hdr[2] == c->kind && hdr[3] == c->sched_kind &&
+       hdr[4] == (c->fast ? 1 : 0) && hdr[5] == (long long)sizeof(RepState) && hdr[6] == (long long)sizeof(Ctx::Nh);
+  ok = ok && std::fread(rep_n.data(), sizeof(long long), c->R, f) == (size_t)c->R && rep_n == c->rep_n;
+  long long tot = 0;
+  for (long long v : rep_n) tot += v;
+  std::vector<uint8_t> types(ok ? tot : 0);
+  std::vector<RepState> rs(c->R);
+  long long h_base = 0, md_step = 0;
+  double box[3] = {0, 0, 0};
+  const bool pos = c->kind == 1, vel = ok && hdr[7] == 1;
+  std::vector<double> md(pos ? (vel ? 6 : 3) * (size_t)c->N : 0);
+  Ctx::Nh nh;
+  ok = ok && std::fread(types.data(), 1, tot, f) == (size_t)tot &&
+       std::fread(rs.data(), sizeof(RepState), c->R, f) == (size_t)c->R &&
+       std::fread(&h_base, sizeof(long long), 1, f) == 1 && std::fread(&md_step, sizeof(long long), 1, f) == 1 &&
+       std::fread(box, sizeof(double), 3, f) == 3 &&
+       (md.empty() || std::fread(md.data(), sizeof(double), md.size(), f) == md.size()) &&
+       std::fread(&nh, sizeof(Ctx::Nh), 1, f) == 1;
+  std::fclose(f);
+  if (!ok) return fail(c, VCSGC_ERR_INVALID_ARG, "checkpoint does not match this context (sizes, schedule or form)");
+  TRY(flush(c));
+  CK(cudaStreamSynchronize(c->st));
+  // step base (fused form) first: the species upload writes n at its parity
+  c->h_base = h_base;
+  if (c->fast) {
+    LatCtl ctl{h_base};
+    CK(cudaMemcpyAsync(c->lat.ctl, &ctl, sizeof(LatCtl), cudaMemcpyHostToDevice, c->st));
+    launch_colour_table(c->lat, c->st);
+    CK(cudaGetLastError());
+  }
+  if (pos) {
+    for (int q = 0; q < 3; ++q) c->box[q] = box[q];
+    double* dst[3] = {c->x, c->y, c->z};
+    for (int q = 0; q < 3; ++q)
+      CK(cudaMemcpyAsync(dst[q], md.data() + q * c->N, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
+    fill_args(c);
+    TRY(md_rebuild(c));
+    if (vel) TRY(vcsgc_set_velocities(c, md.data() + 3 * c->N, md.data() + 4 * c->N, md.data() + 5 * c->N));
+    c->md_step = md_step;
+    c->nh = nh;
+  }
+  long long off = 0;
+  for (int r = 0; r < c->R; ++r) {
+    TRY(vcsgc_set_types(c, r, types.data() + off));
+    off += rep_n[r];
+  }
+  // counters, step and the tracked energy exactly as saved
+  CK(cudaMemcpyAsync(c->rs, rs.data(), sizeof(RepState) * c->R, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->forces_valid = false;
+  fill_args(c);
+  return check_device_error(c);
+}
+
 int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_commit) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n < 1 || !ms_propose || !ms_commit) return VCSGC_ERR_INVALID_ARG;

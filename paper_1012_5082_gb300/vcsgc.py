@@ -75,7 +75,7 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_multi_steps", "vcsgc_multi_steps_per_sweep", "vcsgc_multi_observables",
            "vcsgc_multi_get_types", "vcsgc_multi_set_types", "vcsgc_multi_delta_e", "vcsgc_multi_energy",
            "vcsgc_multi_last_error", "vcsgc_multi_free", "vcsgc_set_ensemble", "vcsgc_md_state",
-           "vcsgc_minimize"]
+           "vcsgc_minimize", "vcsgc_save", "vcsgc_load"]
 
 
 def lib():
@@ -126,6 +126,8 @@ def lib():
             "vcsgc_get_types_all": (I32, [P, P]),
             "vcsgc_set_types_all": (I32, [P, P]),
             "vcsgc_set_ensemble": (I32, [P, I32, D, D, D, I32]),
+            "vcsgc_save": (I32, [P, C.c_char_p]),
+            "vcsgc_load": (I32, [P, C.c_char_p]),
             "vcsgc_md_state": (I32, [P, P]),
             "vcsgc_minimize": (I32, [P, D, I64, P, P]),
             "vcsgc_multi_init": (I32, [C.POINTER(C.c_void_p), P, P, P, I32, P, P, P, P, P, P, P, I32]),
@@ -505,6 +507,12 @@ class Context:
         v = C.c_double()
         _check(lib().vcsgc_kinetic_energy(self.h, C.byref(v)), self.h)
         return v.value
+
+    def save(self, path):
+        _check(lib().vcsgc_save(self.h, os.fsencode(path)), self.h)
+
+    def load(self, path):
+        _check(lib().vcsgc_load(self.h, os.fsencode(path)), self.h)
 
     def set_ensemble(self, kind, t_damp=100.0, p_damp=1000.0, p_ext_bar=0.0, chain=3):
         """kind: 'langevin', 'nvt' or 'npt' (Nose-Hoover chains, MTK barostat)."""
