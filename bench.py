@@ -547,7 +547,7 @@ def multi_bench(V, torch, stream, local, sweeps=10, warmup=2):
         out[f"K{K}"] = {"trial_moves_per_s": N_PHI * lat.n * sweeps / (ms * 1e-3),
                         "us_per_step": ms * 1e3 / (sweeps * g.steps_per_sweep),
                         "reembed": ds is not None, "acc_local": o["acc_local"], "acc_global": o["acc_global"],
-                        "launches_per_step": 2}
+                        "launches_per_step": 2 if ds is not None else 1}
         g.close()
     out["workload"] = "80^3 x 8 replicas, period-4 sublattice (64,000 trials per colour step)"
     return out

@@ -75,6 +75,12 @@ __device__ __forceinline__ int pick_index(const PickTab& t, uint32_t lo, uint32_
   const int prev = k ? t.cum[k - 1] : 0;
   return t.beg[k] + ((r - prev) >> t.sh[k]);
 }
+// programmatic dependent launch: wait for the preceding grid (and its
+// memory), and let the next grid be scheduled; no-ops without the launch
+// attribute
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // top 53 bits of the word; u = u53 * 2^-53 in [0, 1)
 __device__ __forceinline__ uint64_t top53(uint32_t lo, uint32_t hi) {
   return word64(lo, hi) >> 11;

@@ -395,8 +395,7 @@ __device__ __forceinline__ int lat_colour(const LatArgs& a, uint2 key, long long
 // kernel and the first step after it are ordinary launches, so the base is
 // final before any step of the chain starts.  Without the attribute both
 // instructions are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// (pdl_wait and pdl_trigger are in common.cuh)
 
 template <bool PROPOSE, int NS, int NR, int BS, bool DA, bool B5, bool PF>
 __global__ void __launch_bounds__(BS) k_lattice_step(LatArgs a, int j) {

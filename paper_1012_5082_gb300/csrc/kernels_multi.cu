@@ -246,7 +246,7 @@ __device__ double multi_de_bcc5(const MultiArgs& a, const long long* sDq, const 
     const long long* D = sDq + ((s * K + ta) * K + tb) * K;
     for (int be = 0; be < K; ++be) pq += (long long)((cnt[s] >> (8 * be)) & 255u) * D[be];
   }
-  const double pair = ldexp((double)pq, -a.qbits);
+  const double pair = (double)pq * a.qscale;
   double own;
   if constexpr (REEMBED) {
     const double ri = rho[i];
@@ -467,6 +467,302 @@ void launch_multi_step(const MultiArgs& a, cudaStream_t st) {
     k_multi_commit<false><<<cgrid, MK_BLOCK, 0, st>>>(a);
   }
 }
+
+// ------------------------------------------------------------ fused form
+// One launch per colour step k (no re-embedding, five-shell table):
+//  1. every block takes the global decision of step k - 1 from that step's
+//     sums (the same FP64 arithmetic in every block, so the same result);
+//  2. each thread commits its pending flip of step k - 1 (slot d): the new
+//     species if the step was accepted, else the old one;
+//  3. block 0 of the replica folds step k - 1 into the running state;
+//  4. each thread proposes trial d of step k on the effective species: a
+//     neighbour whose byte still carries a pending flip of step k - 1 counts
+//     with its new species when that step was accepted, so the commits of
+//     other blocks need not have landed;
+//  5. an accepted trial marks its site pending (high nibble) and its slot.
+// Concurrent readers see either the byte before its commit (species and
+// pending) or after (the committed species): both give the same effective
+// species.  Same-colour sites are more than 2 r_c apart, so no trial reads
+// another trial of its own step.
+// neighbour bytes of the site in cell (cx, cy, cz), basis B: all 58 loads
+// issued at once
+template <int B>
+__device__ __forceinline__ void multi_bytes(const MultiArgs& a, const uint8_t* ty, int cx, int cy, int cz,
+                                            unsigned* by) {
+  int xo[5], yo[5], zo[5];
+#pragma unroll
+  for (int dd = -2; dd <= 2; ++dd) {
+    xo[dd + 2] = 2 * mk_wrap(cx + dd, a.nx);
+    yo[dd + 2] = 2 * a.nx * mk_wrap(cy + dd, a.ny);
+    zo[dd + 2] = 2 * a.nx * a.ny * mk_wrap(cz + dd, a.nz);
+  }
+#pragma unroll
+  for (int k = 0; k < MK_BCC5_N; ++k) {
+    const int code = mk_bcc5_code(k);
+    const int hx = (code & 15) - 4, hy = ((code >> 4) & 15) - 4, hz = ((code >> 8) & 15) - 4;
+    const int bb = B ^ (hx & 1);
+    by[k] = __ldcg(ty + zo[((B + hz - bb) >> 1) + 2] + yo[((B + hy - bb) >> 1) + 2] + xo[((B + hx - bb) >> 1) + 2] + bb);
+  }
+}
+
+// pair part of dE in fixed point from the neighbour bytes and the effective
+// species (gmask = 0xF0 when the previous step was accepted: a pending
+// nibble then counts)
+__device__ __forceinline__ long long multi_pq_bytes(const MultiArgs& a, const long long* sDq, const unsigned* by,
+                                                    unsigned gmask, int ta, int tb) {
+  const int K = a.K;
+  unsigned cnt[5] = {0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int k = 0; k < MK_BCC5_N; ++k) {
+    const unsigned v = by[k];
+    const unsigned te = (v & gmask) ? (v >> 4) - 1u : (v & 15u);
+    cnt[mk_bcc5_code(k) >> 12] += 1u << (8 * te);
+  }
+  long long pq = 0;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const long long* D = sDq + ((s * K + ta) * K + tb) * K;
+    for (int be = 0; be < K; ++be) pq += (long long)((cnt[s] >> (8 * be)) & 255u) * D[be];
+  }
+  return pq;
+}
+
+// Launches of a chain after the first use programmatic dependent launch:
+// before griddepcontrol.wait a step reads only what no step writes (the
+// tables, the parameters, the step base, which only the advance kernel
+// changes and the first launch after it is ordinary) and draws its random
+// numbers; what the previous step wrote is read after the wait.
+template <bool PROPOSE>
+__global__ void __launch_bounds__(MK_BLOCK) k_multi_fused(MultiArgs a, int j) {
+  pdl_trigger();
+  __shared__ long long sDq[5 * MK_MAX * MK_MAX * MK_MAX];
+  __shared__ double sDF[MK_MAX * MK_MAX];
+  __shared__ int s_G, s_tie;
+  __shared__ int s_red[MK_BLOCK / 32][MK_MAX + 1];
+  __shared__ double s_de[MK_BLOCK / 32];
+  __shared__ int s_acc[MK_BLOCK / 32];
+  const int K = a.K;
+  const int r = blockIdx.y;
+  const MRepParams& p = a.rp[r];
+  const long long k = *a.base + j, kp = k - 1;
+  const int d = blockIdx.x * MK_BLOCK + threadIdx.x;
+  if (PROPOSE) {
+    for (int q = threadIdx.x; q < 5 * K * K * K; q += MK_BLOCK) sDq[q] = a.Dq[q];
+    if (threadIdx.x < K * K) sDF[threadIdx.x] = a.dF[threadIdx.x];
+  }
+  // draws and the site of trial d of step k; the global uniform of step k-1
+  uint64_t ug = 0;
+  if (threadIdx.x == 0 && kp >= 0) {
+    const uint4 wp = philox4x32_10(make_uint4((uint32_t)kp, (uint32_t)((uint64_t)kp >> 32), 0xFFFFFFFFu, TAG_STEP),
+                                   p.key);
+    ug = top53(wp.z, wp.w);
+  }
+  int site = -1, b = 0, cx = 0, cy = 0, cz = 0, toff = 0;
+  uint64_t u53 = 0;
+  if (PROPOSE && d < a.D) {
+    const uint4 wc = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)((uint64_t)k >> 32), 0xFFFFFFFFu, TAG_STEP),
+                                   p.key);
+    const int c = (int)below64(wc.x, wc.y, (uint64_t)a.n_colours);
+    const int pc = c >> 1;
+    b = c & 1;
+    const int dq = mk_div(d, a.nxq, a.rcp_nxq);
+    const int kx = d - dq * a.nxq;
+    const int kz = mk_div(dq, a.nyq, a.rcp_nyq);
+    const int ky = dq - kz * a.nyq;
+    cx = pc % a.qx + a.qx * kx;
+    cy = (pc / a.qx) % a.qy + a.qy * ky;
+    cz = pc / (a.qx * a.qy) + a.qz * kz;
+    site = ((cz * a.ny + cy) * a.nx + cx) * 2 + b;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)((uint64_t)k >> 32), (uint32_t)d, TAG_TRIAL),
+                                  p.key);
+    u53 = top53(w.z, w.w);
+    if (K > 2) {
+      const uint4 w6 = philox4x32_10(
+          make_uint4((uint32_t)k, (uint32_t)((uint64_t)k >> 32), (uint32_t)d, TAG_SPECIES), p.key);
+      toff = (int)below64(w6.x, w6.y, (uint64_t)(K - 1));
+    }
+  }
+  pdl_wait();
+
+  // loads of what the previous steps wrote, all before the block barrier
+  uint8_t* ty = a.types + (long long)r * a.N;
+  int* slot = a.slot + (long long)r * a.D + d;
+  int ps = -1;
+  unsigned vps = 0u, vown = 0u;
+  unsigned by[MK_BCC5_N];
+  if (d < a.D) {
+    ps = __ldcg(slot);
+    if (ps >= 0) vps = __ldcg(ty + ps);
+  }
+  if (site >= 0) {
+    vown = __ldcg(ty + site);
+    if (b) multi_bytes<1>(a, ty, cx, cy, cz, by);
+    else multi_bytes<0>(a, ty, cx, cy, cz, by);
+  }
+  if (threadIdx.x == 0) {
+    // global decision of step k-1 (every block, the same FP64 arithmetic)
+    int G = 0, tie = 0;
+    if (kp >= 0) {
+      const MStepAcc* A = a.acc + 3 * r + (int)(kp % 3);
+      if (__ldcg(&A->nacc) > 0) {
+        const long long* n0 = a.nstart + (2 * r + (int)(kp & 1)) * MK_MAX;
+        double Y = 0.0;
+        for (int al = 1; al < K; ++al) {
+          const double dn = (double)__ldcg(&A->dn[al]);
+          Y += p.beta * p.kappa_p[al] * dn * (dn + 2.0 * ((double)__ldcg(n0 + al) - p.n0[al]));
+        }
+        G = metropolis(Y, ug, &tie) ? 1 : 0;
+      }
+    }
+    s_G = G;
+    s_tie = tie;
+  }
+  __syncthreads();
+  const int G = s_G;
+  const unsigned gmask = G ? 0xF0u : 0u;
+  // commit this thread's pending flip of step k-1
+  if (ps >= 0) ty[ps] = (uint8_t)((vps & gmask) ? (vps >> 4) - 1u : (vps & 15u));
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    MRepState S = a.rs[r];
+    if (kp >= 0 && S.fin_step < kp) {
+      const MStepAcc* A = a.acc + 3 * r + (int)(kp % 3);
+      const int nacc = __ldcg(&A->nacc);
+      const long long* n0 = a.nstart + (2 * r + (int)(kp & 1)) * MK_MAX;
+      long long cnt[MK_MAX];
+      for (int al = 0; al < MK_MAX; ++al) cnt[al] = __ldcg(n0 + al);
+      S.trials += a.D;
+      S.local_acc += nacc;
+      S.near_ties += __ldcg(&A->ties) + s_tie;
+      if (nacc > 0) {
+        S.global_trials++;
+        if (G) {
+          S.global_acc++;
+          S.flips += nacc;
+          long long d0 = 0;
+          for (int al = 1; al < K; ++al) {
+            const int dn = __ldcg(&A->dn[al]);
+            cnt[al] += dn;
+            d0 += dn;
+          }
+          cnt[0] -= d0;
+          S.energy += __ldcg(&A->sum_de);
+        }
+      }
+      long long* n1 = a.nstart + (2 * r + (int)(k & 1)) * MK_MAX;
+      for (int al = 0; al < K; ++al) {
+        S.cnt[al] = cnt[al];
+        n1[al] = cnt[al];
+        const double cc = (double)cnt[al] / (double)a.N;
+        S.sum_c[al] += cc;
+        S.sum_c2[al] += cc * cc;
+      }
+      S.steps++;
+      S.step = k;
+      S.fin_step = kp;
+      a.rs[r] = S;
+    }
+    if (PROPOSE) {
+      MStepAcc* Bn = a.acc + 3 * r + (int)((k + 1) % 3);
+      for (int al = 0; al < MK_MAX; ++al) Bn->dn[al] = 0;
+      Bn->nacc = 0;
+      Bn->ties = 0;
+      Bn->sum_de = 0.0;
+    }
+  }
+  if (!PROPOSE) {
+    if (ps >= 0) *slot = -1;
+    return;
+  }
+  int acc = 0, tie = 0, ta = 0, tb = 0;
+  double de = 0.0;
+  if (site >= 0) {
+    // the site's own byte may carry this thread's pending flip of step k-1
+    ta = (int)((vown & gmask) ? (vown >> 4) - 1u : (vown & 15u));
+    tb = K == 2 ? 1 - ta : (ta + 1 + toff) % K;
+    const long long pq = multi_pq_bytes(a, sDq, by, gmask, ta, tb);
+    // FP32 screen of u < min{1, exp(-X)}, X = beta (dE + dmu0_b - dmu0_a):
+    // the pair part and the constant rounded to float, |x32 - X| bounded by
+    // their size times 2^-21; FP64 only when the screen cannot decide
+    const float e32 = (float)pq * (float)a.qscale, c32 = p.c32[ta * K + tb];
+    const float x32 = p.beta32 * (e32 + c32);
+    const float dx = (p.beta32 * (fabsf(e32) + fabsf(c32)) + fabsf(x32)) * 4.76837158203125e-07f;
+    const int dec = screen32(x32, dx, u53);
+    if (dec >= 0) {
+      acc = dec;
+    } else {
+      const double d64 = (double)pq * a.qscale + sDF[ta * K + tb];
+      acc = metropolis(p.beta * (d64 + (p.dmu0[tb] - p.dmu0[ta])), u53, &tie) ? 1 : 0;
+    }
+    if (acc) {
+      de = (double)pq * a.qscale + sDF[ta * K + tb];
+      if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
+    }
+    if (acc) {
+      ty[site] = (uint8_t)(ta | ((tb + 1) << 4));
+      *slot = site;
+    } else if (ps >= 0) {
+      *slot = -1;
+    }
+  } else if (ps >= 0) {
+    *slot = -1;
+  }
+  // per-solute dn, accepts, ties and the dE sum: warp, block, one atomic each
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int al = 1; al < MK_MAX; ++al) {
+    const int sv = __reduce_add_sync(0xffffffffu, acc ? (int)(tb == al) - (int)(ta == al) : 0);
+    if (lane == 0) s_red[warp][al] = sv;
+  }
+  const int sa = __reduce_add_sync(0xffffffffu, acc);
+  const int st = __reduce_add_sync(0xffffffffu, tie);
+  double sd = acc ? de : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  if (lane == 0) {
+    s_red[warp][0] = st;
+    s_acc[warp] = sa;
+    s_de[warp] = sd;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int na = 0, nt = 0;
+    double dsum = 0.0;
+    for (int w2 = 0; w2 < MK_BLOCK / 32; ++w2) {
+      na += s_acc[w2];
+      nt += s_red[w2][0];
+      dsum += s_de[w2];
+    }
+    MStepAcc* A = a.acc + 3 * r + (int)(k % 3);
+    if (na) {
+      atomicAdd(&A->nacc, na);
+      for (int al = 1; al < K; ++al) {
+        int v = 0;
+        for (int w2 = 0; w2 < MK_BLOCK / 32; ++w2) v += s_red[w2][al];
+        if (v) atomicAdd(&A->dn[al], v);
+      }
+      atomicAdd(&A->sum_de, dsum);
+    }
+    if (nt) atomicAdd(&A->ties, nt);
+  }
+}
+
+__global__ void k_multi_advance(long long* base, int n) { *base += n; }
+
+void launch_multi_fused(const MultiArgs& a, int j, bool propose, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((a.D + MK_BLOCK - 1) / MK_BLOCK), (unsigned)a.R);
+  cfg.blockDim = dim3(MK_BLOCK);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (propose && j > 0) ? 1 : 0;  // the first launch of a chain is ordinary
+  if (propose) cudaLaunchKernelEx(&cfg, k_multi_fused<true>, a, j);
+  else cudaLaunchKernelEx(&cfg, k_multi_fused<false>, a, j);
+}
+
+void launch_multi_advance(long long* base, int n, cudaStream_t st) { k_multi_advance<<<1, 1, 0, st>>>(base, n); }
 
 __global__ void k_multi_delta_e(MultiArgs a, int r, const long long* sites, const uint8_t* to, int n, double* out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;

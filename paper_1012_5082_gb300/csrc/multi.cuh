@@ -24,11 +24,16 @@ struct MRepParams {
   double dmu0[MK_MAX];  // phi_alpha + 2 kappa_p,alpha n0_alpha
   double phi[MK_MAX];
   uint2 key;
+  // FP32 screen of the local decision (no re-embedding): beta, and
+  // dF_ab + dmu0_b - dmu0_a rounded to float, [a K + b]
+  float beta32;
+  float c32[MK_MAX * MK_MAX];
 };
 
 struct MRepState {
   long long cnt[MK_MAX];
   long long step;
+  long long fin_step;  // fused form: last step whose decision is folded in
   double energy;
   long long trials, local_acc, global_trials, global_acc, flips, near_ties, steps;
   double sum_c[MK_MAX], sum_c2[MK_MAX];
@@ -66,15 +71,24 @@ struct MultiArgs {
   // - phi_a,beta(r_s)) 2^qbits); sums of 58 such terms stay below 2^62
   const long long* Dq;
   int qbits;
+  double qscale;        // 2^-qbits
   float rcp_nxq, rcp_nyq;  // 1 / nxq, 1 / nyq for the trial decode
   Spline embed[MK_MAX];
   uint8_t* types;       // [R][N]
   double* rho;          // [R][N]
   const MRepParams* rp;
   MRepState* rs;
-  MStepAcc* acc;        // [R][2]
+  MStepAcc* acc;        // [R][3] (fused form: by step mod 3; else [R][2] by parity)
   int2* pend;           // [R][D] (site, new species) of the local accepts
   unsigned* err;
+  // fused form (no re-embedding, five-shell table): one launch per colour
+  // step.  A species byte carries the species in its low nibble and, while
+  // a flip of the previous step awaits that step's global decision, the new
+  // species + 1 in its high nibble.
+  int fused;
+  int* slot;            // [R][D] site of trial d's pending flip, or -1
+  long long* nstart;    // [R][2][MK_MAX] counts at the start of a step, by parity
+  const long long* base;  // step of launch j = 0
 };
 
 // site index of trial d of colour c (ascending site index within a colour)
@@ -150,5 +164,9 @@ void launch_multi_energy(const MultiArgs& a, int r0, int nrep, double* part, cud
 void launch_multi_delta_e(const MultiArgs& a, int r, const long long* sites, const uint8_t* to, int n,
                           double* out, cudaStream_t st);
 void launch_multi_step(const MultiArgs& a, cudaStream_t st);
+// fused form: step base + j (propose = false: only the commit and the
+// bookkeeping of the previous step), and base += n
+void launch_multi_fused(const MultiArgs& a, int j, bool propose, cudaStream_t st);
+void launch_multi_advance(long long* base, int n, cudaStream_t st);
 
 }  // namespace vcsgc

@@ -35,6 +35,8 @@ struct Multi {
   double* d_out = nullptr;
   long long buf_n = 0;
   cudaGraphExec_t graph = nullptr;
+  long long* d_base = nullptr;  // fused form: device step base
+  long long h_base = 0;         // its host mirror
 };
 
 #define MCK(call)                                                                      \
@@ -119,10 +121,13 @@ int energy_of(Multi* m, int r, double* out) {
   return VCSGC_OK;
 }
 
+int flush(Multi* m);
+
 // densities, counts and energy of replica r from host species t
 int load_replica(Multi* m, int r, const uint8_t* t, bool reset_counters) {
   for (long long i = 0; i < m->N; ++i)
     if (t[i] >= m->K) return mfail(m, VCSGC_ERR_INVALID_ARG, "species value >= K");
+  MTRY(flush(m));
   MCK(cudaMemcpyAsync(m->args.types + (long long)r * m->N, t, m->N, cudaMemcpyHostToDevice, m->st));
   launch_multi_rho(m->args, r, 1, m->st);
   MCK(cudaGetLastError());
@@ -136,12 +141,55 @@ int load_replica(Multi* m, int r, const uint8_t* t, bool reset_counters) {
   for (int al = 0; al < MK_MAX; ++al) s.cnt[al] = 0;
   for (long long i = 0; i < m->N; ++i) s.cnt[t[i]]++;
   s.energy = e;
+  if (reset_counters) s.fin_step = -1;
+  if (m->args.fused)
+    MCK(cudaMemcpyAsync(m->args.nstart + (2 * r + (int)(m->h_base & 1)) * MK_MAX, s.cnt, sizeof(long long) * MK_MAX,
+                        cudaMemcpyHostToDevice, m->st));
   MCK(cudaMemcpyAsync(m->args.rs + r, &s, sizeof(MRepState), cudaMemcpyHostToDevice, m->st));
   MCK(cudaStreamSynchronize(m->st));
   return VCSGC_OK;
 }
 
+// fused form: commit the last proposed step and fold it into the state
+int flush(Multi* m) {
+  if (!m->args.fused || m->h_base == 0) return VCSGC_OK;
+  launch_multi_fused(m->args, 0, false, m->st);
+  MCK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
+int run_steps_fused(Multi* m, long long n) {
+  const int G = 64;
+  if (n >= G && !m->graph) {
+    cudaGraph_t g;
+    MCK(cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < G; ++q) launch_multi_fused(m->args, q, true, m->st);
+    launch_multi_advance(m->d_base, G, m->st);
+    cudaError_t e1 = cudaGetLastError();
+    MCK(cudaStreamEndCapture(m->st, &g));
+    if (e1 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return mfail(m, VCSGC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e1));
+    }
+    cudaError_t e2 = cudaGraphInstantiate(&m->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return mfail(m, VCSGC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(e2));
+  }
+  for (; n >= G; n -= G) {
+    MCK(cudaGraphLaunch(m->graph, m->st));
+    m->h_base += G;
+  }
+  if (n > 0) {
+    for (long long q = 0; q < n; ++q) launch_multi_fused(m->args, (int)q, true, m->st);
+    launch_multi_advance(m->d_base, (int)n, m->st);
+    m->h_base += n;
+  }
+  MCK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
 int run_steps(Multi* m, long long n) {
+  if (m->args.fused) return run_steps_fused(m, n);
   const int G = 64;
   if (n >= G && !m->graph) {
     cudaGraph_t g;
@@ -301,6 +349,7 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
   // |phi_b - phi_a| <= 2 vmax; 58 x 24 x 2 vmax x 2^qbits < 2^62
   a.qbits = 52;
   while (a.qbits > 0 && 2.0 * vmax * 58.0 * 24.0 * std::ldexp(1.0, a.qbits) >= std::ldexp(1.0, 62)) --a.qbits;
+  a.qscale = std::ldexp(1.0, -a.qbits);
   long long* Dq = nullptr;
   MTRY(malloc_dev(m, &Dq, (size_t)a.n_sh * m->K * m->K * m->K));
   launch_multi_fixed(V, a.n_sh, m->K, a.qbits, Dq, m->st);
@@ -320,11 +369,20 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
   MTRY(malloc_dev(m, &rp, R));
   a.rp = rp;
   MTRY(malloc_dev(m, &a.rs, R));
-  MTRY(malloc_dev(m, &a.acc, 2 * R));
+  MTRY(malloc_dev(m, &a.acc, 3 * R));
   MTRY(malloc_dev(m, &a.pend, (size_t)R * a.D));
   m->n_part = multi_energy_blocks(m->N);
   MTRY(malloc_dev(m, &m->part, m->n_part));
-  MCK(cudaMemsetAsync(a.acc, 0, sizeof(MStepAcc) * 2 * R, m->st));
+  MCK(cudaMemsetAsync(a.acc, 0, sizeof(MStepAcc) * 3 * R, m->st));
+  // fused form: one launch per colour step (no re-embedding, five-shell table)
+  a.fused = (!a.reembed && a.bcc5) ? 1 : 0;
+  MTRY(malloc_dev(m, &a.slot, (size_t)R * a.D));
+  MCK(cudaMemsetAsync(a.slot, 0xFF, sizeof(int) * R * a.D, m->st));
+  MTRY(malloc_dev(m, &a.nstart, (size_t)R * 2 * MK_MAX));
+  MCK(cudaMemsetAsync(a.nstart, 0, sizeof(long long) * R * 2 * MK_MAX, m->st));
+  MTRY(malloc_dev(m, &m->d_base, 1));
+  MCK(cudaMemsetAsync(m->d_base, 0, sizeof(long long), m->st));
+  a.base = m->d_base;
   MCK(cudaMemsetAsync(a.rs, 0, sizeof(MRepState) * R, m->st));
   m->h_rp.resize(R);
   const int S = m->K - 1;
@@ -355,6 +413,16 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
   launch_multi_df(a, dF, m->st);
   MCK(cudaGetLastError());
   a.dF = dF;
+  // float constants of the local screen: dF_ab + dmu0_b - dmu0_a, beta
+  std::vector<double> hdF(MK_MAX * MK_MAX);
+  MCK(cudaMemcpyAsync(hdF.data(), dF, sizeof(double) * m->K * m->K, cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  for (int r = 0; r < R; ++r) {
+    MRepParams& p = m->h_rp[r];
+    p.beta32 = (float)p.beta;
+    for (int x = 0; x < m->K; ++x)
+      for (int y = 0; y < m->K; ++y) p.c32[x * m->K + y] = (float)(hdF[x * m->K + y] + p.dmu0[y] - p.dmu0[x]);
+  }
   MCK(cudaMemcpyAsync(rp, m->h_rp.data(), sizeof(MRepParams) * R, cudaMemcpyHostToDevice, m->st));
   MCK(cudaStreamSynchronize(m->st));
   return VCSGC_OK;
@@ -411,6 +479,7 @@ int vcsgc_multi_observables(void* h, int32_t r, vcsgc_multi_obs* o) {
   Multi* m = as_multi(h);
   if (!m || !o || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
   MCK(cudaSetDevice(m->device));
+  MTRY(flush(m));
   MRepState s;
   MCK(cudaMemcpyAsync(&s, m->args.rs + r, sizeof(MRepState), cudaMemcpyDeviceToHost, m->st));
   MCK(cudaStreamSynchronize(m->st));
@@ -447,6 +516,7 @@ int vcsgc_multi_get_types(void* h, int32_t r, uint8_t* out) {
   Multi* m = as_multi(h);
   if (!m || !out || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
   MCK(cudaSetDevice(m->device));
+  MTRY(flush(m));
   MCK(cudaMemcpyAsync(out, m->args.types + (long long)r * m->N, m->N, cudaMemcpyDeviceToHost, m->st));
   MCK(cudaStreamSynchronize(m->st));
   return VCSGC_OK;
@@ -473,6 +543,7 @@ int vcsgc_multi_delta_e(void* h, int32_t r, const int64_t* sites, const uint8_t*
     MTRY(malloc_dev(m, &m->d_out, n));
     m->buf_n = n;
   }
+  MTRY(flush(m));
   MCK(cudaMemcpyAsync(m->d_sites, sites, sizeof(long long) * n, cudaMemcpyHostToDevice, m->st));
   MCK(cudaMemcpyAsync(m->d_to, to, n, cudaMemcpyHostToDevice, m->st));
   launch_multi_delta_e(m->args, r, m->d_sites, m->d_to, (int)n, m->d_out, m->st);
@@ -486,6 +557,7 @@ int vcsgc_multi_energy(void* h, int32_t r, double* out) {
   Multi* m = as_multi(h);
   if (!m || !out || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
   MCK(cudaSetDevice(m->device));
+  MTRY(flush(m));
   return energy_of(m, r, out);
 }
 

@@ -101,3 +101,29 @@ def test_multi_replicas_independent(V):
     assert not np.array_equal(g.types(0), g.types(2))
     assert g.observables(0)["flips"] == g.observables(1)["flips"] > 0
     g.close()
+
+
+def test_multi_k2_retraces_binary_fused_step(V):
+    """K = 2 through the multicomponent kernels and the binary fused step on
+    the same 12^3 lattice, period-4 sublattice, seeds and parameters: the same
+    species after every sweep (both are the binary chain, up to near-ties)."""
+    tab = I.eam_tables(I.multi_eam_params(2))
+    lat = I.bcc_lattice(12, 12, 12)
+    t = I.random_types(lat.n, int(0.05 * lat.n), seed=77)
+    kappa, T, c0, phi = 100.0, 1200.0, 0.05, -3.0
+    m = V.Multi(lat, t, tab, [phi], kappa, T, c0=c0, seed_r=np.array([78], dtype=np.uint64))
+    b = V.Context(lat, t, tab, phi, kappa, T, seed=78, c0=c0, schedule=V.SCHED_SUBLATTICE, sched=(4, 4, 4))
+    assert m.steps_per_sweep == b.steps_per_sweep == 128
+    same = 0
+    for s in range(40):
+        m.sweep(1)
+        b.sweep(1)
+        if np.array_equal(m.types(), b.types()):
+            same += 1
+        else:
+            break
+    assert same == 40, same
+    om, ob = m.observables(), b.observables()
+    assert om["flips"] == ob["flips"] > 500 and om["n"][1] == ob["n_b"]
+    m.close()
+    b.close()
