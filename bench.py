@@ -553,6 +553,30 @@ def multi_bench(V, torch, stream, local, sweeps=10, warmup=2):
     return out
 
 
+def rank_seeds(rank: int, n: int = N_PHI) -> np.ndarray:
+    """Philox keys of one rank's replicas.  Ranks run independent replicas
+    (the method does not shard: weak scaling), so the keys must differ
+    between ranks: rank r takes 2001 + 1000 r + (0 .. n-1)."""
+    return np.arange(n, dtype=np.uint64) + np.uint64(2001 + 1000 * rank)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over the ranks (the slowest rank times the
+    job); x itself when there is one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return world * units_per_rank / seconds
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle times the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -634,7 +658,7 @@ def main():
         return 0
     lat, types, tab, phi, c0 = workload()
     stream = torch.cuda.Stream()
-    seeds = np.arange(N_PHI, dtype=np.uint64) + np.uint64(2001 + 1000 * rank)
+    seeds = rank_seeds(rank)
     ctx = V.Context(lat, np.tile(types, N_PHI), tab, 0.0, KAPPA, T_K, schedule=V.SCHED_SUBLATTICE,
                     sched=(4, 4, 4), n_replicas=N_PHI, phi_r=phi, c0_r=c0, seed_r=seeds,
                     stream=stream, device=local)
@@ -654,11 +678,8 @@ def main():
         barrier()
         ms = timed_sweeps(torch, stream, ctx, args.steps, flush)
         barrier()
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * trials_per_step * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = aggregate(world, trials_per_step * args.steps, ms_max * 1e-3)
 
     # roofline of the dominant kernel: the fused colour step (one launch per
     # colour step; state resident in L2, so ALU work and latency bound it).
@@ -695,8 +716,8 @@ def main():
         obs = ctx.observables_all()
         ctx.types_all(host)
     barrier()
-    dt_e2e = time.perf_counter() - t0
-    e2e = {"value": world * trials_per_step * args.steps / dt_e2e, "unit": "trial moves/s",
+    dt_e2e = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": aggregate(world, trials_per_step * args.steps, dt_e2e), "unit": "trial moves/s",
            "h2d_bytes_per_step": N_PHI * lat.n,
            "d2h_bytes_per_step": N_PHI * lat.n + N_PHI * ctypes.sizeof(V.Observables),
            "calls_per_step": "vcsgc_set_types_all, vcsgc_sweep(1), vcsgc_observables_all, vcsgc_get_types_all",
