@@ -28,6 +28,7 @@
 // decision of its own step.
 #include "common.cuh"
 #include "kernels.h"
+#include "multi.cuh"
 
 namespace vcsgc {
 
@@ -879,7 +880,81 @@ __global__ void __launch_bounds__(LAT_E_BLOCK)
   if (threadIdx.x < LAT_E_W) {
     long long tot = 0;
     for (int w2 = 0; w2 < LAT_E_BLOCK / 32; ++w2) tot += s_acc[w2][threadIdx.x];
-    part[(long long)LAT_E_W * blockIdx.x + threadIdx.x] = (double)tot;
+    // integer totals of the replica: one atomic per block and counter
+    if (tot) atomicAdd(reinterpret_cast<unsigned long long*>(part) + threadIdx.x, (unsigned long long)tot);
+  }
+}
+
+// The same totals bit-parallel for the five-shell table: one thread per
+// word of 32 row positions, whose B sites are summed against every
+// neighbour offset at once.  For own basis b and offset h (half-lattice
+// units) the neighbours sit in row (Y + dy, Z + dz) at row position H + hx,
+// so a 32-bit window of that row shifted by hx, ANDed with the word's B
+// sites of basis b, counts the ordered B-B pairs of shell s(h) in popc.
+// The rows' halo copies make the windows of valid positions periodic.
+__device__ __forceinline__ uint32_t spec_word(const LatArgs& a, const LatGeom& g, int Y, int Z, int q) {
+  return (q < 0 || q >= g.W) ? 0u : (uint32_t)__ldcg(a.bits + g.bits_off + ((long long)Z * g.ny + Y) * g.W + q);
+}
+
+__global__ void __launch_bounds__(LAT_E_BLOCK) k_lattice_pairs_bcc5(LatArgs a, int r0, double* part, int pstride) {
+  if (*(volatile unsigned*)a.err & ERRF_SPECIES) return;
+  const int r = r0 + blockIdx.y;
+  part += (long long)LAT_E_W * pstride * blockIdx.y;
+  const LatGeom g = a.geom[r];
+  const long long nw = (long long)g.ny * g.nz * g.W;
+  if ((long long)blockIdx.x * LAT_E_BLOCK >= nw) return;
+  const long long idx = (long long)blockIdx.x * LAT_E_BLOCK + threadIdx.x;
+  int acc[LAT_E_W];
+#pragma unroll
+  for (int s = 0; s < LAT_E_W; ++s) acc[s] = 0;
+  if (idx < nw) {
+    const long long row = idx / g.W;
+    const int q = (int)(idx - row * g.W);
+    const int Y = (int)(row % g.ny), Z = (int)(row / g.ny);
+    uint32_t w = spec_word(a, g, Y, Z, q);
+    // own positions p = 32 q + k with LAT_HALO <= p < LAT_HALO + 2 nx
+    const int lo = LAT_HALO - 32 * q, hi = LAT_HALO + 2 * g.nx - 32 * q;
+    if (lo > 0) w &= lo >= 32 ? 0u : ~((1u << lo) - 1u);
+    if (hi < 32) w &= hi <= 0 ? 0u : ((1u << hi) - 1u);
+    acc[LAT_MAX_SH] = __popc(w);
+    if (w) {
+      int yw[5], zw[5];
+#pragma unroll
+      for (int d = -2; d <= 2; ++d) {
+        yw[d + 2] = wrap_add(Y, d, g.ny);
+        zw[d + 2] = wrap_add(Z, d, g.nz);
+      }
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        // row position parity = basis (LAT_HALO is even)
+        const uint32_t wb = w & (b ? 0xAAAAAAAAu : 0x55555555u);
+        if (!wb) continue;
+#pragma unroll
+        for (int k = 0; k < MK_BCC5_N; ++k) {
+          const int code = mk_bcc5_code(k);
+          const int hx = (code & 15) - 4, hy = ((code >> 4) & 15) - 4, hz = ((code >> 8) & 15) - 4;
+          const int bb = b ^ (hx & 1);
+          const int Yn = yw[((b + hy - bb) >> 1) + 2], Zn = zw[((b + hz - bb) >> 1) + 2];
+          const uint32_t win = hx >= 0 ? __funnelshift_r(spec_word(a, g, Yn, Zn, q), spec_word(a, g, Yn, Zn, q + 1), hx)
+                                       : __funnelshift_r(spec_word(a, g, Yn, Zn, q - 1), spec_word(a, g, Yn, Zn, q),
+                                                         32 + hx);
+          acc[code >> 12] += __popc(wb & win);
+        }
+      }
+    }
+  }
+  __shared__ int s_acc[LAT_E_BLOCK / 32][LAT_E_W];
+#pragma unroll
+  for (int s = 0; s < LAT_E_W; ++s) acc[s] = __reduce_add_sync(0xffffffffu, acc[s]);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int s = 0; s < LAT_E_W; ++s) s_acc[threadIdx.x >> 5][s] = acc[s];
+  }
+  __syncthreads();
+  if (threadIdx.x < LAT_E_W) {
+    long long tot = 0;
+    for (int w2 = 0; w2 < LAT_E_BLOCK / 32; ++w2) tot += s_acc[w2][threadIdx.x];
+    if (tot) atomicAdd(reinterpret_cast<unsigned long long*>(part) + threadIdx.x, (unsigned long long)tot);
   }
 }
 
@@ -892,13 +967,8 @@ __global__ void k_lattice_energy_final(LatArgs a, int r0, const double* etab, co
   const int r = r0 + blockIdx.x;
   part += (long long)LAT_E_W * pstride * blockIdx.x;
   const LatGeom g = a.geom[r];
-  const int nblk = (int)((((long long)g.ny * g.nz * g.W) + LAT_E_BLOCK - 1) / LAT_E_BLOCK);
   __shared__ double s_tot[LAT_E_W];
-  if (threadIdx.x < LAT_E_W) {
-    double t = 0.0;  // integer-valued: exact
-    for (int q = 0; q < nblk; ++q) t += part[(long long)LAT_E_W * q + threadIdx.x];
-    s_tot[threadIdx.x] = t;
-  }
+  if (threadIdx.x < LAT_E_W) s_tot[threadIdx.x] = (double)reinterpret_cast<const unsigned long long*>(part)[threadIdx.x];
   __syncthreads();
   if (threadIdx.x == 0) {
     const int S = a.n_shells;
@@ -922,7 +992,9 @@ int lattice_energy_width() { return LAT_E_W; }
 void launch_lattice_energy(const LatArgs& a, int r0, int nrep, long long max_words, const double* etab,
                            double* part, int pstride, int parity, cudaStream_t st) {
   const dim3 grid(lattice_energy_blocks(max_words), nrep);
-  if (a.bcc5) k_lattice_energy<true><<<grid, LAT_E_BLOCK, 0, st>>>(a, r0, part, pstride);
+  // the first LAT_E_W words of each replica's region take integer totals
+  cudaMemsetAsync(part, 0, sizeof(double) * LAT_E_W * pstride * nrep, st);
+  if (a.bcc5) k_lattice_pairs_bcc5<<<grid, LAT_E_BLOCK, 0, st>>>(a, r0, part, pstride);
   else k_lattice_energy<false><<<grid, LAT_E_BLOCK, 0, st>>>(a, r0, part, pstride);
   k_lattice_energy_final<<<nrep, 32, 0, st>>>(a, r0, etab, part, pstride, parity);
 }

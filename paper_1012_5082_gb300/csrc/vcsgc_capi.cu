@@ -115,6 +115,9 @@ struct Ctx {
   std::vector<struct Ctx*> subs;   // batch of lattices of different sizes
   LatArgs lat{};
   long long h_base = 0;            // host mirror of lat.ctl->base_step
+  bool pending = false;            // steps launched since the last flush
+  void* h_pin = nullptr;           // pinned staging: RepState[R] then the error word
+  size_t h_pin_bytes = 0;
   std::vector<int3> offsets;       // half-lattice neighbour offsets (kind 0)
   std::vector<int> offset_shell;
   // delayed acceptance: the context's copy of the surrogate's fragments
@@ -175,10 +178,8 @@ int dalloc(Ctx* c, T** p, size_t count) {
     if (rc_ != VCSGC_OK) return rc_; \
   } while (0)
 
-int check_device_error(Ctx* c) {
-  unsigned e = 0;
-  CK(cudaMemcpyAsync(&e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
+// the device error bits e (already copied to the host) as a status
+int device_error_status(Ctx* c, unsigned e) {
   if (!e) return VCSGC_OK;
   CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -187,6 +188,13 @@ int check_device_error(Ctx* c) {
   if (e & ERRF_OVERFLOW) return fail(c, VCSGC_ERR_OVERFLOW, "neighbour list capacity exceeded");
   if (e & ERRF_TABLE) return fail(c, VCSGC_ERR_TABLE_RANGE, "r or rho outside the EAM table grid");
   return fail(c, VCSGC_ERR_NONFINITE, "non-finite energy difference or force");
+}
+
+int check_device_error(Ctx* c) {
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return device_error_status(c, e);
 }
 
 void fill_args(Ctx* c) {
@@ -659,15 +667,18 @@ int run_steps_fast(Ctx* c, long long n) {
     launch_lattice_advance(c->lat, (int)n, c->st);
     c->h_base += n;
   }
+  c->pending = true;
   CK(cudaGetLastError());
   return VCSGC_OK;
 }
 
-// apply the pending commit of the last proposed step (fused form)
+// apply the pending commit of the last proposed step (fused form); a no-op
+// when no step ran since the last flush
 int flush(Ctx* c) {
-  if (!c->fast) return VCSGC_OK;
+  if (!c->fast || !c->pending) return VCSGC_OK;
   launch_lattice_step(c->lat, 0, false, c->st);
   CK(cudaGetLastError());
+  c->pending = false;
   return VCSGC_OK;
 }
 
@@ -1408,6 +1419,7 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   c->h_base = 0;
+  c->pending = false;
   drop_graph(c);
   return check_device_error(c);
 }
@@ -1448,6 +1460,7 @@ static void destroy(Ctx* c) {
   c->subs.clear();
   drop_graph(c);
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
   for (void* p : c->allocs) cudaFree(p);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   delete c;
@@ -1757,9 +1770,21 @@ int vcsgc_observables_all(void* ctx, vcsgc_observables* o) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !o) return VCSGC_ERR_INVALID_ARG;
   TRY(flush(c));
-  std::vector<RepState> s(c->R);
-  CK(cudaMemcpyAsync(s.data(), c->rs, sizeof(RepState) * c->R, cudaMemcpyDeviceToHost, c->st));
-  TRY(check_device_error(c));
+  // the states and the error word through one pinned buffer, one synchronisation
+  const size_t bytes = sizeof(RepState) * c->R + sizeof(unsigned);
+  if (c->h_pin_bytes < bytes) {
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    c->h_pin = nullptr;
+    c->h_pin_bytes = 0;
+    CK(cudaMallocHost(&c->h_pin, bytes));
+    c->h_pin_bytes = bytes;
+  }
+  RepState* s = static_cast<RepState*>(c->h_pin);
+  unsigned* e = reinterpret_cast<unsigned*>(s + c->R);
+  CK(cudaMemcpyAsync(s, c->rs, sizeof(RepState) * c->R, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  TRY(device_error_status(c, *e));
   for (int r = 0; r < c->R; ++r) fill_observables(c, r, s[r], o + r);
   return VCSGC_OK;
 }
@@ -2341,6 +2366,7 @@ int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_com
   if (c->fast) {
     launch_lattice_advance(c->lat, (int)n, c->st);
     c->h_base += n;
+    c->pending = true;
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
