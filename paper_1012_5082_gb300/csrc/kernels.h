@@ -154,6 +154,7 @@ struct LatArgs {
   int da;
   MlpW mlp;
   int bcc5;                     // rows and masks equal the compile-time 5-shell BCC table
+  int unpack4;                  // every replica's nx is even and its bytes 4-aligned: unpack 4 sites per thread
 };
 
 void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);

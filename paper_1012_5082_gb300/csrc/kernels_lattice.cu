@@ -765,6 +765,23 @@ __global__ void k_lattice_unpack(LatArgs a, uint8_t* const* tptr, int r0) {
   types_r[i] = (uint8_t)own_bit(row_ptr(a, g, Y, Z), 2 * X + b, 0u);
 }
 
+// four sites per thread when nx is even: sites 4u .. 4u + 3 share a row and
+// a 4-bit window of one species word (row positions are multiples of 4 plus
+// the even halo), written as one 32-bit store of four bytes
+__global__ void k_lattice_unpack4(LatArgs a, uint8_t* const* tptr, int r0) {
+  const int r = r0 + blockIdx.y;
+  const LatGeom g = a.geom[r];
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * u >= g.n_sites) return;
+  const int i = (int)(4 * u);
+  const int row = fdiv(i >> 1, g.nx, g.rcp_nx);  // (Z ny + Y)
+  const int p = LAT_HALO + (i - 2 * g.nx * row);
+  const uint32_t w = (uint32_t)__ldcg(a.bits + g.bits_off + (long long)row * g.W + (p >> 5));
+  const uint32_t f = (w >> (p & 31)) & 15u;
+  const uint32_t v = (f & 1u) | ((f & 2u) << 7) | ((f & 4u) << 14) | ((f & 8u) << 21);
+  *reinterpret_cast<uint32_t*>(tptr[r] + i) = v;
+}
+
 template <int NS>
 __global__ void k_lattice_delta_e(LatArgs a, int r, const int* sites, int n, double* out) {
   const LatGeom g = a.geom[r];
@@ -886,8 +903,8 @@ __global__ void __launch_bounds__(LAT_E_BLOCK)
 }
 
 // The same totals bit-parallel for the five-shell table: one thread per
-// word of 32 row positions, whose B sites are summed against every
-// neighbour offset at once.  For own basis b and offset h (half-lattice
+// word of 32 row positions, whose B sites are summed against the neighbour
+// offsets of one sign at once (twice that is the ordered-pair count).  For own basis b and offset h (half-lattice
 // units) the neighbours sit in row (Y + dy, Z + dz) at row position H + hx,
 // so a 32-bit window of that row shifted by hx, ANDed with the word's B
 // sites of basis b, counts the ordered B-B pairs of shell s(h) in popc.
@@ -933,6 +950,9 @@ __global__ void __launch_bounds__(LAT_E_BLOCK) k_lattice_pairs_bcc5(LatArgs a, i
         for (int k = 0; k < MK_BCC5_N; ++k) {
           const int code = mk_bcc5_code(k);
           const int hx = (code & 15) - 4, hy = ((code >> 4) & 15) - 4, hz = ((code >> 8) & 15) - 4;
+          // the table holds h and -h: pairs along offsets of one sign, each
+          // unordered pair once (doubled below)
+          if (!(hx > 0 || (hx == 0 && (hy > 0 || (hy == 0 && hz > 0))))) continue;
           const int bb = b ^ (hx & 1);
           const int Yn = yw[((b + hy - bb) >> 1) + 2], Zn = zw[((b + hz - bb) >> 1) + 2];
           const uint32_t win = hx >= 0 ? __funnelshift_r(spec_word(a, g, Yn, Zn, q), spec_word(a, g, Yn, Zn, q + 1), hx)
@@ -941,6 +961,8 @@ __global__ void __launch_bounds__(LAT_E_BLOCK) k_lattice_pairs_bcc5(LatArgs a, i
           acc[code >> 12] += __popc(wb & win);
         }
       }
+#pragma unroll
+      for (int sh = 0; sh < 5; ++sh) acc[sh] *= 2;  // ordered pairs
     }
   }
   __shared__ int s_acc[LAT_E_BLOCK / 32][LAT_E_W];
@@ -1092,7 +1114,12 @@ void launch_lattice_pack(const LatArgs& a, uint8_t* const* tptr, int r0, int nre
 
 void launch_lattice_unpack(const LatArgs& a, uint8_t* const* tptr, int r0, int nrep, long long max_sites,
                            cudaStream_t st) {
-  k_lattice_unpack<<<dim3((unsigned)((max_sites + 255) / 256), nrep), 256, 0, st>>>(a, tptr, r0);
+  if (a.unpack4) {
+    const long long groups = (max_sites + 3) / 4;
+    k_lattice_unpack4<<<dim3((unsigned)((groups + 255) / 256), nrep), 256, 0, st>>>(a, tptr, r0);
+  } else {
+    k_lattice_unpack<<<dim3((unsigned)((max_sites + 255) / 256), nrep), 256, 0, st>>>(a, tptr, r0);
+  }
 }
 
 void launch_lattice_delta_e(const LatArgs& a, int r, const int* sites, int n, double* out, cudaStream_t st) {

@@ -13,6 +13,7 @@
 #include "../../include/vcsgc.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "trace.h"
 
 using namespace vcsgc;
 
@@ -1371,6 +1372,11 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   TRY(dalloc(c, &c->epart, (size_t)((long long)lattice_energy_width() * R * c->epstride)));
   TRY(dalloc(c, &c->d_tptr, (size_t)R));
   CK(cudaMemcpyAsync(c->d_tptr, c->rep_types.data(), sizeof(uint8_t*) * R, cudaMemcpyHostToDevice, c->st));
+  // four sites per thread in the unpack: every replica's rows of even length
+  // and species bytes starting 4-byte aligned
+  l.unpack4 = 1;
+  for (int r = 0; r < R; ++r)
+    if ((c->h_geom[r].nx & 1) || ((uintptr_t)c->rep_types[r] & 3)) l.unpack4 = 0;
   CK(cudaMemcpyAsync(dg, c->h_geom.data(), sizeof(LatGeom) * R, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(dlr, lr.data(), sizeof(LatRep) * R, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(l.bits, 0, sizeof(unsigned long long) * (words + 1), c->st));
@@ -1468,6 +1474,7 @@ static void destroy(Ctx* c) {
 
 int vcsgc_init(void** out, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_eam_tables* E,
                double phi, double kappa, double T, const vcsgc_options* opt) {
+  VCSGC_TRACE("vcsgc_init");
   if (!out) return VCSGC_ERR_INVALID_ARG;
   *out = nullptr;
   vcsgc_options def;
@@ -1608,6 +1615,7 @@ static int batch_impl(Ctx* c, int32_t n_rep, const int32_t* cells, double a, con
 int vcsgc_batch_init(void** out, int32_t n_rep, const int32_t* cells, double a, const uint8_t* types,
                      const vcsgc_eam_tables* E, const double* phi, const double* kappa, const double* T,
                      const vcsgc_options* opt) {
+  VCSGC_TRACE("vcsgc_batch_init");
   if (!out) return VCSGC_ERR_INVALID_ARG;
   *out = nullptr;
   vcsgc_options def;
@@ -1628,6 +1636,7 @@ int vcsgc_batch_init(void** out, int32_t n_rep, const int32_t* cells, double a, 
 }
 
 int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
+  VCSGC_TRACE("vcsgc_autotune");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || steps < 1 || !best_block) return VCSGC_ERR_INVALID_ARG;
   if (!c->fast) {
@@ -1677,6 +1686,7 @@ const char* vcsgc_last_error(void* ctx) {
 }
 
 int vcsgc_steps(void* ctx, int64_t n) {
+  VCSGC_TRACE("vcsgc_steps");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n < 0) return VCSGC_ERR_INVALID_ARG;
   return run_steps(c, n);
@@ -1690,12 +1700,14 @@ int vcsgc_steps_per_sweep(void* ctx, int64_t* out) {
 }
 
 int vcsgc_sweep(void* ctx, int64_t n) {
+  VCSGC_TRACE("vcsgc_sweep");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n < 0) return VCSGC_ERR_INVALID_ARG;
   return run_steps(c, n * c->steps_per_sweep);
 }
 
 int md_steps(void* ctx, int64_t n) {
+  VCSGC_TRACE("md_steps");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n < 0) return VCSGC_ERR_INVALID_ARG;
   if (!c->subs.empty()) return fail(c, VCSGC_ERR_STATE, "no MD on a batch");
@@ -1704,6 +1716,7 @@ int md_steps(void* ctx, int64_t n) {
 }
 
 int vcsgc_hybrid(void* ctx, int64_t n_cycles, int64_t n_md, int64_t n_mc) {
+  VCSGC_TRACE("vcsgc_hybrid");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n_cycles < 0 || n_md < 0 || n_mc < 0) return VCSGC_ERR_INVALID_ARG;
   for (int64_t q = 0; q < n_cycles; ++q) {
@@ -1755,6 +1768,7 @@ static void fill_observables(const Ctx* c, int r, const RepState& s, vcsgc_obser
 }
 
 int observables(void* ctx, int32_t r, vcsgc_observables* o) {
+  VCSGC_TRACE("observables");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !o || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   TRY(flush(c));
@@ -1767,6 +1781,7 @@ int observables(void* ctx, int32_t r, vcsgc_observables* o) {
 }
 
 int vcsgc_observables_all(void* ctx, vcsgc_observables* o) {
+  VCSGC_TRACE("vcsgc_observables_all");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !o) return VCSGC_ERR_INVALID_ARG;
   TRY(flush(c));
@@ -1790,6 +1805,7 @@ int vcsgc_observables_all(void* ctx, vcsgc_observables* o) {
 }
 
 int vcsgc_get_types(void* ctx, int32_t r, uint8_t* out) {
+  VCSGC_TRACE("vcsgc_get_types");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   TRY(sync_bytes(c, r));
@@ -1830,6 +1846,7 @@ static int checked_species(Ctx* c) {
 }
 
 int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
+  VCSGC_TRACE("vcsgc_set_types");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !in || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   const long long Nr = c->rep_n[r];
@@ -1881,6 +1898,7 @@ int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
 }
 
 int vcsgc_get_types_all(void* ctx, uint8_t* out) {
+  VCSGC_TRACE("vcsgc_get_types_all");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out) return VCSGC_ERR_INVALID_ARG;
   TRY(sync_bytes(c, -1));
@@ -1903,6 +1921,7 @@ int vcsgc_get_types_all(void* ctx, uint8_t* out) {
 }
 
 int vcsgc_set_types_all(void* ctx, const uint8_t* in) {
+  VCSGC_TRACE("vcsgc_set_types_all");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !in) return VCSGC_ERR_INVALID_ARG;
   if (!(c->fast && c->etab)) {
@@ -1953,6 +1972,7 @@ int vcsgc_get_rho(void* ctx, int32_t r, double* out) {
 }
 
 int vcsgc_delta_e(void* ctx, int32_t r, const int64_t* sites, int64_t n, double* out) {
+  VCSGC_TRACE("vcsgc_delta_e");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || (n > 0 && (!sites || !out)) || n < 0 || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   if (n == 0) return VCSGC_OK;
@@ -1979,6 +1999,7 @@ int vcsgc_delta_e(void* ctx, int32_t r, const int64_t* sites, int64_t n, double*
 }
 
 int vcsgc_energy(void* ctx, int32_t r, double* out) {
+  VCSGC_TRACE("vcsgc_energy");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   return energy_of(c, r, out);
@@ -2068,6 +2089,7 @@ int vcsgc_set_ensemble(void* ctx, int32_t kind, double t_damp, double p_damp, do
 }
 
 int vcsgc_md_state(void* ctx, double* out) {
+  VCSGC_TRACE("vcsgc_md_state");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out) return VCSGC_ERR_INVALID_ARG;
   if (c->kind != 1 || c->R != 1 || !c->d_vir) return fail(c, VCSGC_ERR_STATE, "needs explicit positions and one replica");
@@ -2101,6 +2123,7 @@ int vcsgc_md_state(void* ctx, double* out) {
 }
 
 int vcsgc_minimize(void* ctx, double ftol, int64_t max_iter, int64_t* iters, double* fmax_out) {
+  VCSGC_TRACE("vcsgc_minimize");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !(ftol > 0.0) || max_iter < 0) return VCSGC_ERR_INVALID_ARG;
   if (c->kind != 1 || c->R != 1) return fail(c, VCSGC_ERR_STATE, "needs explicit positions and one replica");
@@ -2242,6 +2265,7 @@ int vcsgc_minimize(void* ctx, double ftol, int64_t max_iter, int64_t* iters, dou
 static const char kCkMagic[8] = {'V', 'C', 'S', 'G', 'C', 'C', 'K', '1'};
 
 int vcsgc_save(void* ctx, const char* path) {
+  VCSGC_TRACE("vcsgc_save");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !path) return VCSGC_ERR_INVALID_ARG;
   TRY(sync_bytes(c, -1));
@@ -2282,6 +2306,7 @@ int vcsgc_save(void* ctx, const char* path) {
 }
 
 int vcsgc_load(void* ctx, const char* path) {
+  VCSGC_TRACE("vcsgc_load");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !path) return VCSGC_ERR_INVALID_ARG;
   FILE* f = std::fopen(path, "rb");
@@ -2410,6 +2435,7 @@ static bool da_neighbourhood(const Ctx* c) {
 }
 
 int vcsgc_features(void* ctx, float* d_X, float* d_Y) {
+  VCSGC_TRACE("vcsgc_features");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !d_X || !d_Y) return VCSGC_ERR_INVALID_ARG;
   if (!da_neighbourhood(c))

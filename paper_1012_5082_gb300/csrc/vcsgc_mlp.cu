@@ -10,6 +10,7 @@
 #include "../../include/vcsgc.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "trace.h"
 
 namespace {
 
@@ -147,6 +148,7 @@ int vcsgc_mlp_get_params(void* mlp, float* params) {
 }
 
 int vcsgc_mlp_forward(void* mlp, const float* d_X, int64_t n, float* d_out) {
+  VCSGC_TRACE("vcsgc_mlp_forward");
   Mlp* m = static_cast<Mlp*>(mlp);
   if (!m || n < 0 || (n > 0 && (!d_X || !d_out))) return VCSGC_ERR_INVALID_ARG;
   launch_mlp_forward(m->buf, d_X, n, d_out, m->st);
@@ -156,6 +158,7 @@ int vcsgc_mlp_forward(void* mlp, const float* d_X, int64_t n, float* d_out) {
 }
 
 int vcsgc_mlp_grad(void* mlp, const float* d_X, const float* d_Y, int64_t n, float* grad, double* loss) {
+  VCSGC_TRACE("vcsgc_mlp_grad");
   Mlp* m = static_cast<Mlp*>(mlp);
   if (!m || !d_X || !d_Y || n < 1 || !grad || !loss) return VCSGC_ERR_INVALID_ARG;
   if (m->loss_cap < 1) {
@@ -175,6 +178,7 @@ int vcsgc_mlp_grad(void* mlp, const float* d_X, const float* d_Y, int64_t n, flo
 
 int vcsgc_mlp_train(void* mlp, const float* d_X, const float* d_Y, int64_t n, int64_t batch, int64_t steps,
                     double lr, uint64_t seed, double* loss_hist) {
+  VCSGC_TRACE("vcsgc_mlp_train");
   Mlp* m = static_cast<Mlp*>(mlp);
   if (!m || !d_X || !d_Y || n < 1 || batch < 1 || steps < 0 || !(lr > 0.0) || n > (1LL << 40))
     return VCSGC_ERR_INVALID_ARG;

@@ -10,6 +10,7 @@
 
 #include "kernels.h"
 #include "multi.cuh"
+#include "trace.h"
 #include "vcsgc.h"
 
 namespace vcsgc {
@@ -440,6 +441,7 @@ extern "C" {
 int vcsgc_multi_init(void** out, const vcsgc_lattice* lattice, const uint8_t* types, const vcsgc_multi_tables* tables,
                      int32_t n_replicas, const double* phi, const double* kappa, const double* T, const double* c0,
                      const uint64_t* seed_r, const int32_t period[3], void* stream, int32_t device) {
+  VCSGC_TRACE("vcsgc_multi_init");
   if (!out) return VCSGC_ERR_INVALID_ARG;
   *out = nullptr;
   Multi* m = new (std::nothrow) Multi();
@@ -455,6 +457,7 @@ int vcsgc_multi_init(void** out, const vcsgc_lattice* lattice, const uint8_t* ty
 }
 
 int vcsgc_multi_steps(void* h, int64_t n) {
+  VCSGC_TRACE("vcsgc_multi_steps");
   Multi* m = as_multi(h);
   if (!m || n < 0) return VCSGC_ERR_INVALID_ARG;
   MCK(cudaSetDevice(m->device));
@@ -462,6 +465,7 @@ int vcsgc_multi_steps(void* h, int64_t n) {
 }
 
 int vcsgc_multi_sweep(void* h, int64_t n) {
+  VCSGC_TRACE("vcsgc_multi_sweep");
   Multi* m = as_multi(h);
   if (!m || n < 0) return VCSGC_ERR_INVALID_ARG;
   MCK(cudaSetDevice(m->device));
@@ -476,6 +480,7 @@ int vcsgc_multi_steps_per_sweep(void* h, int64_t* out) {
 }
 
 int vcsgc_multi_observables(void* h, int32_t r, vcsgc_multi_obs* o) {
+  VCSGC_TRACE("vcsgc_multi_observables");
   Multi* m = as_multi(h);
   if (!m || !o || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
   MCK(cudaSetDevice(m->device));
@@ -513,6 +518,7 @@ int vcsgc_multi_observables(void* h, int32_t r, vcsgc_multi_obs* o) {
 }
 
 int vcsgc_multi_get_types(void* h, int32_t r, uint8_t* out) {
+  VCSGC_TRACE("vcsgc_multi_get_types");
   Multi* m = as_multi(h);
   if (!m || !out || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
   MCK(cudaSetDevice(m->device));
@@ -523,6 +529,7 @@ int vcsgc_multi_get_types(void* h, int32_t r, uint8_t* out) {
 }
 
 int vcsgc_multi_set_types(void* h, int32_t r, const uint8_t* in) {
+  VCSGC_TRACE("vcsgc_multi_set_types");
   Multi* m = as_multi(h);
   if (!m || !in || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
   MCK(cudaSetDevice(m->device));

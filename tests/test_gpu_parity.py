@@ -115,6 +115,25 @@ def test_sublattice_schedule_trajectory(V):
     g.close()
 
 
+def test_odd_row_length_trajectory(V):
+    """A lattice with an odd cell count along x (15 x 16 x 16, period-(5, 4, 4)
+    sublattice, 5 a = 14.3 A > 2 r_c): rows of odd length take the
+    site-by-site paths of the bit-packed form (the four-site unpack needs
+    even rows); 30 sweeps site for site."""
+    lat = I.bcc_lattice(15, 16, 16)
+    types = I.random_types(lat.n, int(0.05 * lat.n), seed=1500)
+    tab = I.eam_tables()
+    orc, g = make_pair(lat, types, tab, -2.45, 20.0, 700.0, c0=0.05, seed=2200,
+                       schedule="sublattice", sched=(5, 4, 4))
+    spw = g.steps_per_sweep
+    assert spw == 5 * 4 * 4 * 2
+    resyncs = _lockstep(orc, g, 30, spw)
+    if resyncs == 0:
+        compare_obs(orc.obs(), g.observables())
+    assert g.observables()["flips"] > 100
+    g.close()
+
+
 def test_replicas_match_independent_oracles(V):
     """R replicas in one context equal R separate oracle chains."""
     lat, types, tab = c0_config(n_cells=8)
