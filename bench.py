@@ -664,6 +664,8 @@ def main():
                     stream=stream, device=local)
     spw = ctx.steps_per_sweep
     trials_per_step = N_PHI * lat.n
+    # launch shape (threads per block, row prefetch) by timing, as a user would
+    tuned_block = ctx.autotune(256)
 
     def barrier():
         torch.cuda.synchronize()
@@ -728,7 +730,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "trial moves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict({"parallelism": f"replicas x{world}"}),
+            "data": "synthetic",
+            "config": config_dict({"parallelism": f"replicas x{world}", "block": tuned_block}),
             "e2e": e2e, "gpu_launches": spw * args.steps + 2 * ((spw * args.steps) // 64), "roofline": roof,
             "clocks": clk.summary(),
             "acceptance": {"local": o0["acc_local"], "global": o0["acc_global"], "c": o0["c"]}}
