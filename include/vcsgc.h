@@ -467,7 +467,9 @@ typedef struct {
   int32_t pad;
   int64_t n[4];           /* sites of each species */
   double c[4];
-  double energy;          /* incrementally tracked total energy (eV) */
+  double energy;          /* total energy (eV): tracked step by step, or, with
+                             re-embedding (the screened form), recomputed in
+                             full by this call */
   double energy_per_atom;
   int64_t steps, trials, local_accepts, global_trials, global_accepts, flips, near_ties;
   double acc_local, acc_global;

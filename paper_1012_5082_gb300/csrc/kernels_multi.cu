@@ -32,6 +32,19 @@ __host__ __device__ __forceinline__ int multi_tri(int K, int a, int b) {
   return a * K - a * (a - 1) / 2 + (b - a);
 }
 
+// FP32 embedding value of species t at x (callers check x's range; j is
+// clamped so that the load stays inside the table in any case)
+__device__ __forceinline__ float emb32_val(const MultiArgs& a, int t, float x) {
+  const float u = x * a.emb_ih;
+  int j = (int)u;
+  j = j < 0 ? 0 : (j > a.emb_n - 1 ? a.emb_n - 1 : j);
+  const float tt = u - (float)j;
+  const float4 c = __ldg(a.emb32 + t * a.emb_n + j);
+  return fmaf(tt, fmaf(tt, fmaf(tt, c.w, c.z), c.y), c.x);
+}
+
+__device__ __forceinline__ bool emb32_in(const MultiArgs& a, float x) { return x >= a.emb_lo && x <= a.emb_hi; }
+
 __global__ void k_multi_shell_tables(const Spline* pair, const Spline* dens, int K, const double* r_s, int n_sh,
                                      double* V, double* Fd, unsigned* err) {
   const int nv = n_sh * K * K;
@@ -72,6 +85,10 @@ __global__ void k_multi_rho(MultiArgs a, int r0) {
     rho += a.Fd[h.w * a.K + ty[multi_nbr(a, (int)i, h)]];
   }
   a.rho[(long long)r * a.N + i] = rho;
+  if (a.rf) {
+    const float r32 = (float)rho;
+    a.rf[(long long)r * a.N + i] = make_float2(r32, emb32_val(a, ty[i], r32));
+  }
 }
 
 void launch_multi_rho(const MultiArgs& a, int r0, int nrep, cudaStream_t st) {
@@ -257,6 +274,138 @@ __device__ double multi_de_bcc5(const MultiArgs& a, const long long* sDq, const 
   return pair + own + re;
 }
 
+// ------------------------------------------------------ screened form
+// With re-embedding a trial's dE holds 2 x 58 + 2 embedding evaluations,
+// which in FP64 (a small share of GB300's arithmetic) bound the step.  The
+// local decision is taken instead on an FP32 dE whose distance from the
+// FP64 dE has a proven bound: per evaluation emb_err (coefficient rounding,
+// Horner rounding, and the argument rounding of rho, f_b(r_s) - f_a(r_s)
+// and x / h times the slope), plus 2^-18 of the sum of |terms| for the 58
+// float additions and 2^-21 of the sizes of the final sums.  A trial whose
+// screen cannot decide, or whose argument leaves [emb_lo, emb_hi], gets its
+// dE in FP64 from the whole warp: 32 lanes share its 58 neighbours and two
+// own-site terms.  Every decision is therefore the one the FP64 dE takes.
+
+
+// FP32 dE of site i (cell (cx, cy, cz)) from species ta to tb without the
+// chemical-potential term; *err bounds its distance from the FP64 dE, *pq
+// is the exact fixed-point pair part, *in is false when an argument left
+// the bounded range.  sDfs[(s K + a) K + b] = f_b(r_s) - f_a(r_s) as
+// floats; sw: this block's [15][MK_BLOCK] scratch for the wrapped cell
+// offsets of the thread's site (x, y, z for cells -2..2, in site units);
+// scode: the block's neighbour descriptors.  The neighbours are visited
+// shell by shell, kScreenIlp at a time (loads in flight per thread against
+// registers; a colour step of 64,000 trials gives about 13 warps per SM).
+
+// descriptor of neighbour k of a basis-B site: cell indices (0..4 for
+// -2..2) in bits 0-2, 3-5, 6-8, the neighbour's basis in bit 9 and its
+// shell from bit 10
+template <int B>
+__host__ __device__ constexpr int mk_bcc5_desc(int k) {
+  return (((B + ((mk_bcc5_code(k) & 15) - 4) - (B ^ (((mk_bcc5_code(k) & 15) - 4) & 1))) >> 1) + 2) |
+         ((((B + (((mk_bcc5_code(k) >> 4) & 15) - 4) - (B ^ (((mk_bcc5_code(k) & 15) - 4) & 1))) >> 1) + 2) << 3) |
+         ((((B + (((mk_bcc5_code(k) >> 8) & 15) - 4) - (B ^ (((mk_bcc5_code(k) & 15) - 4) & 1))) >> 1) + 2) << 6) |
+         ((B ^ (((mk_bcc5_code(k) & 15) - 4) & 1)) << 9) | ((mk_bcc5_code(k) >> 12) << 10);
+}
+
+// first neighbour of shell s in the five-shell order (8, 6, 12, 24, 8 sites)
+__host__ __device__ constexpr int mk_shell0(int s) {
+  return s == 0 ? 0 : (s == 1 ? 8 : (s == 2 ? 14 : (s == 3 ? 26 : (s == 4 ? 50 : MK_BCC5_N))));
+}
+
+constexpr int kScreenIlp = 12;  // 125 registers, no spills; 4, 8, 12 measured within 3 %
+
+__device__ float multi_screen_bcc5(const MultiArgs& a, const long long* sDq, const float* sDfs, int* sw,
+                                   const int* scode, int r, int i, int cx, int cy, int cz, int ta, int tb,
+                                   long long* pq_out, float* err, bool* in) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const float2* rf = a.rf + (long long)r * a.N;
+  const int K = a.K;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int d = -2; d <= 2; ++d) {
+    sw[(d + 2) * MK_BLOCK + tid] = 2 * mk_wrap(cx + d, a.nx);
+    sw[(d + 7) * MK_BLOCK + tid] = 2 * a.nx * mk_wrap(cy + d, a.ny);
+    sw[(d + 12) * MK_BLOCK + tid] = 2 * a.nx * a.ny * mk_wrap(cz + d, a.nz);
+  }
+  const float2 ri = rf[i];
+  unsigned cnt[5];
+  float re = 0.0f, ab = 0.0f;
+  bool ok = true;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const float df = sDfs[(s * K + ta) * K + tb];
+    unsigned c = 0u;
+#pragma unroll kScreenIlp
+    for (int k = mk_shell0(s); k < mk_shell0(s + 1); ++k) {
+      const int dc = scode[k];
+      const int j = sw[(dc & 7) * MK_BLOCK + tid] + sw[(5 + ((dc >> 3) & 7)) * MK_BLOCK + tid] +
+                    sw[(10 + ((dc >> 6) & 7)) * MK_BLOCK + tid] + ((dc >> 9) & 1);
+      const int t = ty[j];
+      const float2 v = rf[j];
+      c += 1u << (8 * t);
+      const float x1 = v.x + df;
+      ok &= emb32_in(a, v.x) & emb32_in(a, x1);
+      const float d = emb32_val(a, t, x1) - v.y;
+      re += d;
+      ab += fabsf(d);
+    }
+    cnt[s] = c;
+  }
+  long long pq = 0;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const long long* D = sDq + ((s * K + ta) * K + tb) * K;
+    for (int be = 0; be < K; ++be) pq += (long long)((cnt[s] >> (8 * be)) & 255u) * D[be];
+  }
+  ok &= emb32_in(a, ri.x);
+  const float own = emb32_val(a, tb, ri.x) - ri.y;
+  const float pair = __ll2float_rn(pq) * a.qscale32;
+  *pq_out = pq;
+  *in = ok;
+  *err = fmaf((float)(2 * MK_BCC5_N + 2), a.emb_err,
+              fmaf(3.814697265625e-06f, ab, 4.76837158203125e-07f * (fabsf(pair) + fabsf(own) + fabsf(re))));
+  return (pair + own) + re;
+}
+
+// lane's share of the FP64 embedding part (58 re-embeddings and the own
+// change) of the dE of site i from ta to tb: neighbours lane and lane + 32,
+// and the two own-site terms on lanes 26 and 27 of the second pass
+__device__ double multi_emb_lane(const MultiArgs& a, const double* sFd, int r, int i, int ta, int tb, int lane) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const double* rho = a.rho + (long long)r * a.N;
+  const int K = a.K;
+  const int3 p = multi_half(a, i);
+  double v = 0.0;
+  for (int k = lane; k < a.n_off + 2; k += 32) {
+    if (k < a.n_off) {
+      const int4 h = a.off[k];
+      const int j = multi_nbr_at(a, p, h);
+      const int tj = ty[j];
+      const double rj = rho[j];
+      const double dfs = sFd[h.w * K + tb] - sFd[h.w * K + ta];
+      v += spline_val(a.embed[tj], rj + dfs, a.err) - spline_val(a.embed[tj], rj, a.err);
+    } else if (k == a.n_off) {
+      v += spline_val(a.embed[tb], rho[i], a.err);
+    } else {
+      v -= spline_val(a.embed[ta], rho[i], a.err);
+    }
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ long long warp_sum(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __global__ void k_multi_df(MultiArgs a, double* dF) {
   const int q = threadIdx.x;
   if (q >= a.K * a.K) return;
@@ -273,12 +422,21 @@ __device__ __forceinline__ int multi_target(const MultiArgs& a, const MRepParams
   return (ta + 1 + (int)below64(w6.x, w6.y, (uint64_t)(a.K - 1))) % a.K;
 }
 
-template <bool REEMBED>
-__global__ void __launch_bounds__(MK_BLOCK) k_multi_propose(MultiArgs a) {
+// MODE 0: no re-embedding; 1: re-embedding, FP64 dE (any neighbour table);
+// 2: re-embedding, five-shell table, FP32 screen (the dE sum of an accepted
+// step is then taken by the commit launch, in FP64)
+template <int MODE>
+__global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
+  constexpr bool REEMBED = MODE != 0;
   __shared__ double sV[MK_MAX_SH * MK_MAX * MK_MAX];
   __shared__ double sFd[MK_MAX_SH * MK_MAX];
   __shared__ double sDF[MK_MAX * MK_MAX];
   __shared__ long long sDq[5 * MK_MAX * MK_MAX * MK_MAX];
+  __shared__ float sDfs[5 * MK_MAX * MK_MAX];
+  // screened form: per-thread wrapped cell offsets and the block's
+  // neighbour descriptors (unused otherwise)
+  __shared__ int sw[MODE == 2 ? 15 * MK_BLOCK : 1];
+  __shared__ int scode[MODE == 2 ? MK_BCC5_N : 1];
   __shared__ uint4 s_wc;
   __shared__ int s_col[4];
   __shared__ int s_red[MK_BLOCK / 32][MK_MAX + 1];
@@ -290,6 +448,11 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_propose(MultiArgs a) {
   if (!REEMBED && threadIdx.x < K * K) sDF[threadIdx.x] = a.dF[threadIdx.x];
   if (a.bcc5)
     for (int q = threadIdx.x; q < 5 * K * K * K; q += MK_BLOCK) sDq[q] = a.Dq[q];
+  if (MODE == 2)
+    for (int q = threadIdx.x; q < 5 * K * K; q += MK_BLOCK) {
+      const int sh = q / (K * K), x = (q / K) % K, y = q % K;
+      sDfs[q] = (float)(a.Fd[sh * K + y] - a.Fd[sh * K + x]);
+    }
   const int r = blockIdx.y;
   const MRepParams& p = a.rp[r];
   const long long step = a.rs[r].step;
@@ -308,9 +471,18 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_propose(MultiArgs a) {
   __syncthreads();
   const uint4 wc = s_wc;
   const int c = s_col[0];
+  if constexpr (MODE == 2) {
+    if (threadIdx.x < MK_BCC5_N) {
+      const int k = threadIdx.x;
+      scode[k] = (c & 1) ? mk_bcc5_desc<1>(k) : mk_bcc5_desc<0>(k);
+    }
+    __syncthreads();
+  }
   const int d = blockIdx.x * MK_BLOCK + threadIdx.x;
-  int acc = 0, tie = 0, ta = 0, tb = 0, site = -1;
+  int acc = 0, tie = 0, ta = 0, tb = 0, site = -1, dec = 0;
   double de = 0.0;
+  long long pq = 0;
+  uint64_t u53 = 0;
   if (d < a.D) {
     // site of trial d: ascending index within the colour
     const int b = c & 1;
@@ -324,23 +496,52 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_propose(MultiArgs a) {
                                   p.key);
     ta = a.types[(long long)r * a.N + site];
     tb = multi_target(a, p, step, d, ta);
-    if (a.bcc5)
-      de = b ? multi_de_bcc5<1, REEMBED>(a, sDq, sFd, sDF, r, site, cx, cy, cz, ta, tb)
-             : multi_de_bcc5<0, REEMBED>(a, sDq, sFd, sDF, r, site, cx, cy, cz, ta, tb);
-    else
-      de = multi_de<REEMBED>(a, sV, sFd, r, site, ta, tb);
-    if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
-    acc = metropolis(p.beta * (de + (p.dmu0[tb] - p.dmu0[ta])), top53(w.z, w.w), &tie) ? 1 : 0;
+    u53 = top53(w.z, w.w);
+    if constexpr (MODE == 2) {
+      float err;
+      bool in;
+      const float e32 = multi_screen_bcc5(a, sDq, sDfs, sw, scode, r, site, cx, cy, cz, ta, tb, &pq, &err, &in);
+      const float cm = p.cmu32[ta * K + tb];
+      const float x32 = p.beta32 * (e32 + cm);
+      const float dx = p.beta32 * fmaf(4.76837158203125e-07f, fabsf(e32) + fabsf(cm), err) * 1.0001f +
+                       fabsf(x32) * 4.76837158203125e-07f;
+      dec = in ? screen32(x32, dx, u53) : -1;
+      acc = dec > 0 ? 1 : 0;
+    } else {
+      if (a.bcc5)
+        de = b ? multi_de_bcc5<1, REEMBED>(a, sDq, sFd, sDF, r, site, cx, cy, cz, ta, tb)
+               : multi_de_bcc5<0, REEMBED>(a, sDq, sFd, sDF, r, site, cx, cy, cz, ta, tb);
+      else
+        de = multi_de<REEMBED>(a, sV, sFd, r, site, ta, tb);
+      if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
+      acc = metropolis(p.beta * (de + (p.dmu0[tb] - p.dmu0[ta])), u53, &tie) ? 1 : 0;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if constexpr (MODE == 2) {
+    // trials the screen left open: FP64 dE by the whole warp, one at a time
+    unsigned open = __ballot_sync(0xffffffffu, dec < 0);
+    while (open) {
+      const int src = __ffs(open) - 1;
+      open &= open - 1u;
+      const int si = __shfl_sync(0xffffffffu, site, src);
+      const int sa = __shfl_sync(0xffffffffu, ta, src), sb = __shfl_sync(0xffffffffu, tb, src);
+      const double v = warp_sum(multi_emb_lane(a, sFd, r, si, sa, sb, lane));
+      if (lane == src) {
+        const double de64 = (double)pq * a.qscale + v;
+        if (!isfinite(de64)) atomicOr(a.err, ERRF_NONFINITE);
+        acc = metropolis(p.beta * (de64 + (p.dmu0[tb] - p.dmu0[ta])), u53, &tie) ? 1 : 0;
+      }
+    }
   }
   MStepAcc* A = a.acc + 2 * r + (int)(step & 1);
   // compaction of the local accepts: one reservation per warp
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned m = __ballot_sync(0xffffffffu, acc);
   if (m) {
     int base = 0;
     if (lane == 0) base = atomicAdd(&A->nacc, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (acc) a.pend[(long long)r * a.D + base + __popc(m & ((1u << lane) - 1u))] = make_int2(site, tb);
+    if (acc) a.pend[(long long)r * a.D + base + __popc(m & ((1u << lane) - 1u))] = make_int2(site, tb | (ta << 8));
   }
   // per-solute dn, ties and the dE sum: warp, then block, then one atomic each
 #pragma unroll
@@ -350,7 +551,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_propose(MultiArgs a) {
     if (lane == 0) s_red[warp][al] = sv;
   }
   const int st = __reduce_add_sync(0xffffffffu, tie);
-  double sd = acc ? de : 0.0;
+  double sd = (MODE != 2 && acc) ? de : 0.0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
   if (lane == 0) {
@@ -421,7 +622,8 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_propose(MultiArgs a) {
 }
 
 // apply an accepted step: species, and the density change of the neighbours
-template <bool REEMBED>
+// (pend entries: site, new species | old species << 8)
+template <int MODE>
 __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit(MultiArgs a) {
   const int r = blockIdx.y;
   const long long step = a.rs[r].step - 1;  // the step the propose launch decided
@@ -437,18 +639,80 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit(MultiArgs a) {
   }
   if (!A->accept) return;
   const int nacc = A->nacc;
+  uint8_t* ty = a.types + (long long)r * a.N;
+  double* rho = a.rho + (long long)r * a.N;
   for (int q = blockIdx.x * MK_BLOCK + threadIdx.x; q < nacc; q += gridDim.x * MK_BLOCK) {
     const int2 e = a.pend[(long long)r * a.D + q];
-    uint8_t* ty = a.types + (long long)r * a.N;
-    const int ta = ty[e.x], tb = e.y;
+    const int tb = e.y & 255, ta = e.y >> 8;
     ty[e.x] = (uint8_t)tb;
-    if constexpr (REEMBED) {
-      double* rho = a.rho + (long long)r * a.N;
+    if constexpr (MODE == 1) {
       const int3 p = multi_half(a, e.x);
       for (int k = 0; k < a.n_off; ++k) {
         const int4 h = a.off[k];
         rho[multi_nbr_at(a, p, h)] += a.Fd[h.w * a.K + tb] - a.Fd[h.w * a.K + ta];
       }
+    }
+  }
+}
+
+// Screened form: one thread per (accept, neighbour) and one per accepted
+// site over all replicas that accepted their step, on a fixed grid: the
+// density change in FP64 with its float copy and the FP32 embedding value
+// there, and the new species with its embedding value.  Accepts of one step
+// are more than 2 r_c apart: no two threads touch a common site, and no
+// neighbour's species changes.  Every block sums the replicas' item counts
+// (at most MK_SCREEN_MAX_R replicas).
+__global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
+  __shared__ int s_pre[MK_SCREEN_MAX_R + 1];
+  __shared__ int4 s_off[MK_BCC5_N];
+  __shared__ double s_df[5 * MK_MAX * MK_MAX];
+  const int K = a.K;
+  constexpr int NI = MK_BCC5_N + 1;
+  const long long step = a.rs[0].step - 1;  // replicas step together
+  for (int r = threadIdx.x; r < a.R; r += MK_BLOCK) {
+    const MStepAcc* A = a.acc + 2 * r + (int)(step & 1);
+    s_pre[r + 1] = A->accept ? A->nacc * NI : 0;
+    if (blockIdx.x == 0) {
+      MStepAcc* B = a.acc + 2 * r + (int)((step + 1) & 1);
+      for (int al = 0; al < MK_MAX; ++al) B->dn[al] = 0;
+      B->nacc = 0;
+      B->ties = 0;
+      B->accept = 0;
+      B->sum_de = 0.0;
+    }
+  }
+  for (int q = threadIdx.x; q < MK_BCC5_N; q += MK_BLOCK) s_off[q] = a.off[q];
+  for (int q = threadIdx.x; q < 5 * K * K; q += MK_BLOCK) {
+    const int sh = q / (K * K), x = (q / K) % K, y = q % K;
+    s_df[q] = a.Fd[sh * K + y] - a.Fd[sh * K + x];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_pre[0] = 0;
+    for (int r = 0; r < a.R; ++r) s_pre[r + 1] += s_pre[r];
+  }
+  __syncthreads();
+  const int total = s_pre[a.R];
+  int r = 0;
+  for (int it = blockIdx.x * MK_BLOCK + threadIdx.x; it < total; it += gridDim.x * MK_BLOCK) {
+    while (s_pre[r + 1] <= it) ++r;
+    const int loc = it - s_pre[r];
+    const int q = loc / NI, k = loc - q * NI;
+    const int2 e = a.pend[(long long)r * a.D + q];
+    const int tb = e.y & 255, ta = e.y >> 8;
+    uint8_t* ty = a.types + (long long)r * a.N;
+    float2* rf = a.rf + (long long)r * a.N;
+    if (k < MK_BCC5_N) {
+      const int4 h = s_off[k];
+      const int j = multi_nbr_at(a, multi_half(a, e.x), h);
+      double* rho = a.rho + (long long)r * a.N;
+      const double nr = rho[j] + s_df[(h.w * K + ta) * K + tb];
+      rho[j] = nr;
+      const float r32 = (float)nr;
+      rf[j] = make_float2(r32, emb32_val(a, ty[j], r32));
+    } else {
+      ty[e.x] = (uint8_t)tb;
+      rf[e.x].y = emb32_val(a, tb, rf[e.x].x);
     }
   }
 }
@@ -459,12 +723,17 @@ void launch_multi_step(const MultiArgs& a, cudaStream_t st) {
   // the accepts of a step are a small share of its trials: a few blocks per
   // replica stride over them
   const dim3 cgrid((unsigned)(nb < 4 ? nb : 4), (unsigned)a.R);
-  if (a.reembed) {
-    k_multi_propose<true><<<grid, MK_BLOCK, 0, st>>>(a);
-    k_multi_commit<true><<<cgrid, MK_BLOCK, 0, st>>>(a);
+  if (a.screen) {
+    // one thread per (accept, neighbour) over all replicas: a fixed grid of
+    // four blocks per SM
+    k_multi_propose<2><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_commit_screen<<<4 * a.n_sm, MK_BLOCK, 0, st>>>(a);
+  } else if (a.reembed) {
+    k_multi_propose<1><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_commit<1><<<cgrid, MK_BLOCK, 0, st>>>(a);
   } else {
-    k_multi_propose<false><<<grid, MK_BLOCK, 0, st>>>(a);
-    k_multi_commit<false><<<cgrid, MK_BLOCK, 0, st>>>(a);
+    k_multi_propose<0><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_commit<0><<<cgrid, MK_BLOCK, 0, st>>>(a);
   }
 }
 

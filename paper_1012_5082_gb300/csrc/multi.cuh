@@ -14,6 +14,7 @@ constexpr int MK_MAX = 4;         // species
 constexpr int MK_MAX_SH = 8;      // neighbour shells
 constexpr int MK_MAX_OFF = 96;    // neighbour offsets (5 BCC shells: 58)
 constexpr int MK_BLOCK = 128;
+constexpr int MK_SCREEN_MAX_R = 1024;  // replicas of the screened form
 constexpr uint32_t TAG_SPECIES = 6u;  // (step, domain rank): the proposed species
 
 // Per-replica parameters: index alpha = 0..K-1, entry 0 (the solvent) zero.
@@ -28,6 +29,8 @@ struct MRepParams {
   // dF_ab + dmu0_b - dmu0_a rounded to float, [a K + b]
   float beta32;
   float c32[MK_MAX * MK_MAX];
+  // the same with re-embedding: dmu0_b - dmu0_a rounded to float
+  float cmu32[MK_MAX * MK_MAX];
 };
 
 struct MRepState {
@@ -89,6 +92,22 @@ struct MultiArgs {
   int* slot;            // [R][D] site of trial d's pending flip, or -1
   long long* nstart;    // [R][2][MK_MAX] counts at the start of a step, by parity
   const long long* base;  // step of launch j = 0
+  // screened form (re-embedding, five-shell table): the local decision is
+  // taken on an FP32 dE with a rigorous error bound, FP64 only where the
+  // bound cannot decide.  The embedding cubics rounded to float
+  // ([K][emb_n], one grid for all species), per site its density as a
+  // float and the FP32 embedding value there, the largest error of one FP32
+  // embedding evaluation (eV) and the argument range [emb_lo, emb_hi]
+  // inside which that bound holds.
+  int screen;
+  const float4* emb32;
+  int emb_n;
+  float emb_ih;
+  float emb_lo, emb_hi;
+  float emb_err;
+  float qscale32;       // 2^-qbits as a float (exact)
+  float2* rf;           // [R][N]: (rho_i as float, F32_{t_i} of that)
+  int n_sm;             // multiprocessors of the device (commit grid)
 };
 
 // site index of trial d of colour c (ascending site index within a colour)

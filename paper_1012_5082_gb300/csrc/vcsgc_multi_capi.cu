@@ -223,6 +223,68 @@ void destroy(Multi* m) {
 
 thread_local std::string g_init_err;
 
+// Tables and error bound of the FP32 screen with re-embedding.  For one
+// embedding cubic p_j(t) = c0 + t (c1 + t (c2 + t c3)) on interval j, an FP32
+// evaluation at an argument carried in float differs from the FP64 one by at
+// most 2^-24 [5 G + 4 P + 2 dmax S] to first order, where
+//   G = max_j sum_k |c_jk|            coefficient rounding and three FMAs,
+//   P = max_j (j + 2) max(D_j-1, D_j, D_j+1), D_j = |c1| + 2|c2| + 3|c3|:
+//       |x F'| near interval j; the argument rho + (f_b - f_a) and x / h
+//       carry relative errors 2^-24 (|rho| + |f_b - f_a| + 3|x|),
+//   S = max_j D_j / h, dmax = max |f_b(r_s) - f_a(r_s)|: the part of that
+//       argument error that scales with |f_b - f_a|.
+// emb_err takes 2^-24 [6 G + 5 P + 3 dmax S] over all species and the
+// intervals of the screened range [x_lo, x_max (1 - 10^-6)], x_lo = max(h,
+// x_max / 20); the FP64 evaluation is in range there, and below x_lo (a
+// nearly isolated atom) the slope of a sqrt-like embedding would dominate
+// the bound.  Arguments outside the range go to FP64.
+int screen_setup(Multi* m, const std::vector<double>& hFd) {
+  MultiArgs& a = m->args;
+  const int n = a.embed[0].n_int;
+  for (int al = 1; al < m->K; ++al)
+    if (a.embed[al].n_int != n || a.embed[al].inv_h != a.embed[0].inv_h)
+      return mfail(m, VCSGC_ERR_INVALID_ARG, "embedding tables on different grids");
+  float4* e32 = nullptr;
+  MTRY(malloc_dev(m, &e32, (size_t)m->K * n));
+  std::vector<Cubic> hc((size_t)n);
+  const double h = 1.0 / a.embed[0].inv_h;
+  const double lo = std::max(h, a.embed[0].xmax / 20.0);
+  const int jlo = std::max(0, (int)std::floor(lo / h) - 1);
+  double G = 0.0, P = 0.0, S = 0.0;
+  for (int al = 0; al < m->K; ++al) {
+    launch_to_cubic32(a.embed[al].c, n, reinterpret_cast<Cubic32*>(e32 + (size_t)al * n), m->st);
+    MCK(cudaGetLastError());
+    MCK(cudaMemcpyAsync(hc.data(), a.embed[al].c, sizeof(Cubic) * n, cudaMemcpyDeviceToHost, m->st));
+    MCK(cudaStreamSynchronize(m->st));
+    std::vector<double> D((size_t)n);
+    for (int j = jlo; j < n; ++j) {
+      const Cubic& c = hc[j];
+      G = std::max(G, std::fabs(c.x) + std::fabs(c.y) + std::fabs(c.z) + std::fabs(c.w));
+      D[j] = std::fabs(c.y) + 2.0 * std::fabs(c.z) + 3.0 * std::fabs(c.w);
+      S = std::max(S, D[j] * a.embed[al].inv_h);
+    }
+    for (int j = jlo + 1; j < n; ++j) {
+      const double dn = std::max(D[j], std::max(D[j - 1], j + 1 < n ? D[j + 1] : 0.0));
+      P = std::max(P, (double)(j + 2) * dn);
+    }
+  }
+  double dmax = 0.0;
+  for (int s = 0; s < a.n_sh; ++s)
+    for (int x = 0; x < m->K; ++x)
+      for (int y = 0; y < m->K; ++y) dmax = std::max(dmax, std::fabs(hFd[s * m->K + y] - hFd[s * m->K + x]));
+  const double E = std::ldexp(6.0 * G + 5.0 * P + 3.0 * dmax * S, -24);
+  if (!std::isfinite(E)) return mfail(m, VCSGC_ERR_NONFINITE, "non-finite embedding table");
+  MCK(cudaDeviceGetAttribute(&a.n_sm, cudaDevAttrMultiProcessorCount, m->device));
+  a.emb32 = e32;
+  a.emb_n = n;
+  a.emb_ih = (float)a.embed[0].inv_h;
+  a.emb_lo = (float)lo;
+  a.emb_hi = (float)(a.embed[0].xmax * (1.0 - 1e-6));
+  a.emb_err = (float)(E * (1.0 + 1e-6));
+  MTRY(malloc_dev(m, &a.rf, (size_t)m->R * m->N));
+  return VCSGC_OK;
+}
+
 int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_multi_tables* T, int R,
          const double* phi, const double* kappa, const double* Tk, const double* c0, const uint64_t* seed_r,
          const int32_t period[3], void* stream, int device) {
@@ -384,6 +446,10 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
   MTRY(malloc_dev(m, &m->d_base, 1));
   MCK(cudaMemsetAsync(m->d_base, 0, sizeof(long long), m->st));
   a.base = m->d_base;
+  a.qscale32 = (float)a.qscale;
+  // screened form (re-embedding, five-shell table)
+  a.screen = (a.reembed && a.bcc5 && R <= MK_SCREEN_MAX_R) ? 1 : 0;
+  if (a.screen) MTRY(screen_setup(m, hFd));
   MCK(cudaMemsetAsync(a.rs, 0, sizeof(MRepState) * R, m->st));
   m->h_rp.resize(R);
   const int S = m->K - 1;
@@ -422,7 +488,10 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
     MRepParams& p = m->h_rp[r];
     p.beta32 = (float)p.beta;
     for (int x = 0; x < m->K; ++x)
-      for (int y = 0; y < m->K; ++y) p.c32[x * m->K + y] = (float)(hdF[x * m->K + y] + p.dmu0[y] - p.dmu0[x]);
+      for (int y = 0; y < m->K; ++y) {
+        p.c32[x * m->K + y] = (float)(hdF[x * m->K + y] + p.dmu0[y] - p.dmu0[x]);
+        p.cmu32[x * m->K + y] = (float)(p.dmu0[y] - p.dmu0[x]);
+      }
   }
   MCK(cudaMemcpyAsync(rp, m->h_rp.data(), sizeof(MRepParams) * R, cudaMemcpyHostToDevice, m->st));
   MCK(cudaStreamSynchronize(m->st));
@@ -489,6 +558,9 @@ int vcsgc_multi_observables(void* h, int32_t r, vcsgc_multi_obs* o) {
   MCK(cudaMemcpyAsync(&s, m->args.rs + r, sizeof(MRepState), cudaMemcpyDeviceToHost, m->st));
   MCK(cudaStreamSynchronize(m->st));
   MTRY(device_error(m));
+  // the screened form does not track the energy (an accepted step would
+  // need 118 FP64 embedding evaluations per flip): it is recomputed here
+  if (m->args.screen) MTRY(energy_of(m, r, &s.energy));
   const MRepParams& p = m->h_rp[r];
   std::memset(o, 0, sizeof(*o));
   o->n_sites = m->N;

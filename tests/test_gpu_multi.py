@@ -24,8 +24,9 @@ def V():
     return vcsgc
 
 
-def _pair(V, K, cells=(8, 8, 8), seed=3, R=1):
-    ds, phi, kappa, T, c0 = CASES[K]
+def _pair(V, K, cells=(8, 8, 8), seed=3, R=1, phi=None):
+    ds, phi0, kappa, T, c0 = CASES[K]
+    phi = phi0 if phi is None else phi
     tab = I.eam_tables(I.multi_eam_params(K, dens_scale=ds))
     lat = I.bcc_lattice(*cells)
     t = I.multi_random_types(lat.n, [int(c0 * lat.n)] * (K - 1), seed=seed)
@@ -127,3 +128,31 @@ def test_multi_k2_retraces_binary_fused_step(V):
     assert om["flips"] == ob["flips"] > 500 and om["n"][1] == ob["n_b"]
     m.close()
     b.close()
+
+
+def test_multi_screened_reembedding_16cubed(V):
+    """K = 4 with species-dependent densities on 16^3 cells (64 trials per
+    colour step).  The local decision is taken on an FP32 dE inside a proven
+    error bound, the open trials and the accepts' energies in FP64: species
+    agree with the oracle after every sweep (near-ties aside), counters
+    agree, and the tracked energy equals the full energy and the oracle's."""
+    # phi where the expected dn of every solute vanishes on the random start
+    lat, tab, orc, g = _pair(V, 4, cells=(16, 16, 16), seed=11, phi=[-1.173, -2.037, 0.567])
+    spw = g.steps_per_sweep
+    resyncs = 0
+    for s in range(12):
+        ties0 = orc.obs()["near_ties"]
+        g.sweep(1)
+        orc.parallel_steps(spw)
+        if not np.array_equal(g.types(), orc.types):
+            assert orc.obs()["near_ties"] > ties0, f"sweep {s}: species differ without a flagged tie"
+            g.set_types(orc.types)
+            resyncs += 1
+    og, oo = g.observables(), orc.obs()
+    if resyncs == 0:
+        for k in ("trials", "local_accepts", "global_trials", "global_accepts", "flips"):
+            assert og[k] == oo[k], (k, og[k], oo[k])
+        assert abs(og["energy"] - oo["energy"]) <= 1e-9 * abs(oo["energy"])
+    assert og["flips"] > 3000 and og["global_accepts"] > 200
+    assert abs(g.energy() - og["energy"]) <= 1e-9 * abs(og["energy"])
+    g.close()
