@@ -1,0 +1,88 @@
+"""The error bound behind the FP32 screen of the multicomponent step with
+re-embedding.  For an embedding cubic p_j(t) = c0 + t (c1 + t (c2 + t c3))
+evaluated in float (coefficients rounded to float, three FMAs, the
+argument rho + f_b(r_s) - f_a(r_s) and x / h carried in float), the
+distance from the FP64 evaluation is at most 2^-24 [6 G + 5 P + 3 dmax S]
+(G = max sum |c_k|, P = max (j + 2) |dp/dt| near interval j, S = max
+|F'|, dmax = max |f_b(r_s) - f_a(r_s)|; over the screened range x >=
+max(h, x_max / 20)).  This restates the bound as the device's setup
+computes it and checks it against float evaluations emulated in numpy on
+the four-species tables of the workload."""
+import numpy as np
+
+from paper_1012_5082_gb300 import inputs as I
+
+A = 2.855
+
+
+def _coefficients(y, m, h):
+    """Power-form coefficients of the cubic Hermite interpolant on each
+    interval (values y, derivatives m, spacing h)."""
+    c0 = y[:-1]
+    c1 = h * m[:-1]
+    c2 = 3 * (y[1:] - y[:-1]) - h * (2 * m[:-1] + m[1:])
+    c3 = 2 * (y[:-1] - y[1:]) + h * (m[:-1] + m[1:])
+    return np.stack([c0, c1, c2, c3], 1)
+
+
+def _fma32(a, b, c):
+    # a*b is exact in float64 for float32 operands; one rounding of the sum
+    # to float64 then float32 (a rare double rounding is 1 ulp, far inside
+    # the margin tested)
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+
+
+def test_fp32_embedding_error_within_bound():
+    p = I.multi_eam_params(4, dens_scale=(1.0, 1.25, 0.85, 1.1))
+    T = I.eam_tables(p)
+    h, n = T.drho, T.nrho - 1
+    ih = 1.0 / h
+    lo = max(h, (n * h) / 20.0)
+    jlo = max(0, int(np.floor(lo / h)) - 1)
+    coefs = [_coefficients(np.asarray(T.embed[t]), np.asarray(T.dembed[t]), h) for t in range(4)]
+    G = P = S = 0.0
+    for C in coefs:
+        G = max(G, np.abs(C[jlo:]).sum(1).max())
+        D = np.abs(C[:, 1]) + 2 * np.abs(C[:, 2]) + 3 * np.abs(C[:, 3])
+        S = max(S, D[jlo:].max() * ih)
+        Dn = np.maximum(D, np.maximum(np.r_[0.0, D[:-1]], np.r_[D[1:], 0.0]))
+        P = max(P, ((np.arange(n) + 2) * Dn)[jlo + 1:].max())
+    rs = A * np.sqrt(np.array([3, 4, 8, 11, 12])) / 2
+    Fd = np.array([[p.dens(t, r)[0] for t in range(4)] for r in rs])
+    dmax = np.abs(Fd[:, :, None] - Fd[:, None, :]).max()
+    E = 2.0 ** -24 * (6 * G + 5 * P + 3 * dmax * S)
+
+    rho0 = (np.array([8, 6, 12, 24, 8]) * Fd[:, 0]).sum()
+    rng = np.random.default_rng(7)
+    M = 400_000
+    t = rng.integers(0, 4, M)
+    rho = rng.uniform(0.5 * rho0, 1.6 * rho0, M)
+    s, a, b = rng.integers(0, 5, M), rng.integers(0, 4, M), rng.integers(0, 4, M)
+    dfs = Fd[s, b] - Fd[s, a]
+    Call = np.stack(coefs)                     # [4, n, 4]
+
+    def ev64(x):
+        u = x * ih
+        j = np.minimum(u.astype(np.int64), n - 1)
+        tt = u - j
+        c = Call[t, j]
+        return c[:, 0] + tt * (c[:, 1] + tt * (c[:, 2] + tt * c[:, 3]))
+
+    def ev32(x32):
+        u = (x32 * np.float32(ih)).astype(np.float32)
+        j = np.minimum(u.astype(np.int64), n - 1)
+        tt = (u - j.astype(np.float32)).astype(np.float32)
+        c = Call[t, j].astype(np.float32)
+        return _fma32(tt, _fma32(tt, _fma32(tt, c[:, 3], c[:, 2]), c[:, 1]), c[:, 0])
+
+    r32 = rho.astype(np.float32)
+    x32 = (r32 + dfs.astype(np.float32)).astype(np.float32)
+    err1 = np.abs(ev32(x32).astype(np.float64) - ev64(rho + dfs))
+    err0 = np.abs(ev32(r32).astype(np.float64) - ev64(rho))
+    worst = max(err1.max(), err0.max())
+    assert worst <= E, (worst, E)
+    # the bound is not vacuous: within a factor 20 of what float evaluation reaches
+    assert worst > E / 20, (worst, E)
+    # and small enough that the screen decides nearly every trial: 118
+    # evaluations at 1200 K are below 1 % of kT
+    assert 118 * E < 0.01 * I.KB_EV * 1200.0
