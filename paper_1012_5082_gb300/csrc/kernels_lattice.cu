@@ -730,31 +730,28 @@ void launch_species_check(const uint8_t* t, long long n, unsigned* err, cudaStre
   if (threads > 0) k_species_check<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(t, n, err);
 }
 
-// one warp per 64-bit word of the rows: lane k loads the byte of row
-// position 32 q + k (coalesced) and a ballot forms the 32 species bits (halo
-// included); the pending half is zero.  Nothing is written after a failed
-// species check.  Replica r0 + blockIdx.y, species bytes at tptr[r].
+// one thread per 64-bit word of the rows: 32 species bits (halo included),
+// pending half zero; nothing is written after a failed species check.
+// Replica r0 + blockIdx.y, species bytes at tptr[r].
 __global__ void k_lattice_pack(LatArgs a, uint8_t* const* tptr, int r0) {
   if (*(volatile unsigned*)a.err & ERRF_SPECIES) return;
   const int r = r0 + blockIdx.y;
   const LatGeom g = a.geom[r];
-  const long long nw = (long long)g.ny * g.nz * g.W;
-  const int lane = threadIdx.x & 31;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)g.ny * g.nz * g.W) return;
+  const long long row = idx / g.W;
+  const int q = (int)(idx - row * g.W);
+  const uint8_t* t = tptr[r] + row * 2 * g.nx;
   const int L = 2 * g.nx;
-  for (long long idx = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < nw; idx += nwarps) {
-    const long long row = idx / g.W;
-    const int q = (int)(idx - row * g.W);
-    const int p = 32 * q + lane;
-    unsigned bit = 0u;
-    if (p < L + 2 * LAT_HALO) {
-      int H = p - LAT_HALO;
-      H = H < 0 ? H + L : (H >= L ? H - L : H);
-      bit = tptr[r][row * L + H] & 1u;
-    }
-    const unsigned bits = __ballot_sync(0xffffffffu, bit);
-    if (lane == 0) a.bits[g.bits_off + idx] = (unsigned long long)bits;
+  uint32_t bits = 0u;
+  for (int k = 0; k < 32; ++k) {
+    const int p = 32 * q + k;
+    if (p >= L + 2 * LAT_HALO) break;
+    int H = p - LAT_HALO;
+    H = H < 0 ? H + L : (H >= L ? H - L : H);
+    bits |= (uint32_t)(t[H] & 1u) << k;
   }
+  a.bits[g.bits_off + idx] = (unsigned long long)bits;
 }
 
 __global__ void k_lattice_unpack(LatArgs a, uint8_t* const* tptr, int r0) {
@@ -1112,8 +1109,7 @@ void launch_lattice_advance(const LatArgs& a, int n, cudaStream_t st) {
 
 void launch_lattice_pack(const LatArgs& a, uint8_t* const* tptr, int r0, int nrep, long long max_words,
                          cudaStream_t st) {
-  // one warp (32 threads) per word, eight words per 256-thread block
-  k_lattice_pack<<<dim3((unsigned)((max_words + 7) / 8), nrep), 256, 0, st>>>(a, tptr, r0);
+  k_lattice_pack<<<dim3((unsigned)((max_words + 255) / 256), nrep), 256, 0, st>>>(a, tptr, r0);
 }
 
 void launch_lattice_unpack(const LatArgs& a, uint8_t* const* tptr, int r0, int nrep, long long max_sites,
