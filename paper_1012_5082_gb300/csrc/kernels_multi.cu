@@ -483,20 +483,30 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
   double de = 0.0;
   long long pq = 0;
   uint64_t u53 = 0;
+  // site of trial d (ascending index within the colour) and its draw: they
+  // depend on no earlier launch
+  const int b = c & 1;
+  int cx = 0, cy = 0, cz = 0;
   if (d < a.D) {
-    // site of trial d: ascending index within the colour
-    const int b = c & 1;
     const int dq = mk_div(d, a.nxq, a.rcp_nxq);
     const int kx = d - dq * a.nxq;
     const int kz = mk_div(dq, a.nyq, a.rcp_nyq);
     const int ky = dq - kz * a.nyq;
-    const int cx = s_col[1] + a.qx * kx, cy = s_col[2] + a.qy * ky, cz = s_col[3] + a.qz * kz;
+    cx = s_col[1] + a.qx * kx;
+    cy = s_col[2] + a.qy * ky;
+    cz = s_col[3] + a.qz * kz;
     site = ((cz * a.ny + cy) * a.nx + cx) * 2 + b;
     const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL),
                                   p.key);
+    u53 = top53(w.z, w.w);
+  }
+  // screened form: launched after the previous step's commit with
+  // programmatic dependent launch; the species, densities and this step's
+  // accumulators are read after the wait (a no-op for an ordinary launch)
+  if constexpr (MODE == 2) pdl_wait();
+  if (d < a.D) {
     ta = a.types[(long long)r * a.N + site];
     tb = multi_target(a, p, step, d, ta);
-    u53 = top53(w.z, w.w);
     if constexpr (MODE == 2) {
       float err;
       bool in;
@@ -663,6 +673,9 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit(MultiArgs a) {
 // neighbour's species changes.  Every block sums the replicas' item counts
 // (at most MK_SCREEN_MAX_R replicas).
 __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
+  // the next step's propose may start its draws now; it reads what this
+  // launch writes only after griddepcontrol.wait
+  pdl_trigger();
   __shared__ int s_pre[MK_SCREEN_MAX_R + 1];
   __shared__ int4 s_off[MK_BCC5_N];
   __shared__ double s_df[5 * MK_MAX * MK_MAX];
@@ -717,7 +730,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
   }
 }
 
-void launch_multi_step(const MultiArgs& a, cudaStream_t st) {
+void launch_multi_step(const MultiArgs& a, cudaStream_t st, bool after_step) {
   const int nb = (a.D + MK_BLOCK - 1) / MK_BLOCK;
   const dim3 grid((unsigned)nb, (unsigned)a.R);
   // the accepts of a step are a small share of its trials: a few blocks per
@@ -726,7 +739,16 @@ void launch_multi_step(const MultiArgs& a, cudaStream_t st) {
   if (a.screen) {
     // one thread per (accept, neighbour) over all replicas: a fixed grid of
     // four blocks per SM
-    k_multi_propose<2><<<grid, MK_BLOCK, 0, st>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(MK_BLOCK);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_step ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_multi_propose<2>, a);
     k_multi_commit_screen<<<4 * a.n_sm, MK_BLOCK, 0, st>>>(a);
   } else if (a.reembed) {
     k_multi_propose<1><<<grid, MK_BLOCK, 0, st>>>(a);

@@ -182,7 +182,9 @@ int multi_energy_blocks(long long N);
 void launch_multi_energy(const MultiArgs& a, int r0, int nrep, double* part, cudaStream_t st);
 void launch_multi_delta_e(const MultiArgs& a, int r, const long long* sites, const uint8_t* to, int n,
                           double* out, cudaStream_t st);
-void launch_multi_step(const MultiArgs& a, cudaStream_t st);
+// one colour step (propose and commit); after_step: the previous launch on
+// the stream is this context's commit (the screened form then overlaps)
+void launch_multi_step(const MultiArgs& a, cudaStream_t st, bool after_step);
 // fused form: step base + j (propose = false: only the commit and the
 // bookkeeping of the previous step), and base += n
 void launch_multi_fused(const MultiArgs& a, int j, bool propose, cudaStream_t st);

@@ -195,7 +195,7 @@ int run_steps(Multi* m, long long n) {
   if (n >= G && !m->graph) {
     cudaGraph_t g;
     MCK(cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal));
-    for (int q = 0; q < G; ++q) launch_multi_step(m->args, m->st);
+    for (int q = 0; q < G; ++q) launch_multi_step(m->args, m->st, q > 0);
     cudaError_t e1 = cudaGetLastError();
     MCK(cudaStreamEndCapture(m->st, &g));
     if (e1 != cudaSuccess) {
@@ -207,7 +207,7 @@ int run_steps(Multi* m, long long n) {
     if (e2 != cudaSuccess) return mfail(m, VCSGC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(e2));
   }
   for (; n >= G; n -= G) MCK(cudaGraphLaunch(m->graph, m->st));
-  for (; n > 0; --n) launch_multi_step(m->args, m->st);
+  for (bool after = false; n > 0; --n, after = true) launch_multi_step(m->args, m->st, after);
   MCK(cudaGetLastError());
   return VCSGC_OK;
 }

@@ -156,3 +156,29 @@ def test_multi_screened_reembedding_16cubed(V):
     assert og["flips"] > 3000 and og["global_accepts"] > 200
     assert abs(g.energy() - og["energy"]) <= 1e-9 * abs(og["energy"])
     g.close()
+
+
+def test_multi_screen_out_of_range_goes_fp64(V):
+    """An embedding grid to rho = 400 puts every density (about 15) below
+    the screened range (rho >= x_max / 20), so every trial of the
+    re-embedding step takes the FP64 path of the whole warp: the
+    trajectory still follows the oracle's site for site."""
+    ds, phi, kappa, T, c0 = CASES[4]
+    tab = I.eam_tables(I.multi_eam_params(4, dens_scale=ds, rho_max=400.0))
+    lat = I.bcc_lattice(8, 8, 8)
+    t = I.multi_random_types(lat.n, [int(c0 * lat.n)] * 3, seed=5)
+    orc = O.MultiSystem(lat, t, tab)
+    orc.set_params(phi, [kappa] * 3, T, c0=[c0] * 3, seed=105)
+    orc.schedule_sublattice(lat.cells, (4, 4, 4))
+    g = V.Multi(lat, t, tab, phi, kappa, T, c0=c0, seed_r=np.array([105], dtype=np.uint64))
+    for s in range(10):
+        ties0 = orc.obs()["near_ties"]
+        g.sweep(1)
+        orc.parallel_steps(g.steps_per_sweep)
+        if not np.array_equal(g.types(), orc.types):
+            assert orc.obs()["near_ties"] > ties0, f"sweep {s}: species differ without a flagged tie"
+            g.set_types(orc.types)
+    og, oo = g.observables(), orc.obs()
+    assert og["flips"] > 100
+    assert abs(og["energy"] - orc.energy_full()) <= 1e-9 * abs(og["energy"])
+    g.close()
