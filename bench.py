@@ -701,7 +701,13 @@ def main():
             "frac": achieved / peak,
             "peak_source": "derived: 128 INT32/FP32 lanes x 152 SMs x 2070 MHz "
                            "(measured xor+add 37.8 / 36.1 Tops/s on two boxes)",
-            "traffic": None, "ops_per_launch": ops_per_launch, "ops_per_trial": OPS_PER_TRIAL,
+            # DRAM bytes per launch from an ncu capture of this kernel (256-thread
+            # blocks, warm L2, three launches of the timed loop): the state is
+            # L2-resident, so HBM traffic is nil
+            "traffic": 256,
+            "traffic_source": "ncu --set full --cache-control none, k_lattice_step<...,256,...> x 3: "
+                              "dram__bytes_read.sum 256 B + dram__bytes_write.sum 0 B per launch",
+            "ops_per_launch": ops_per_launch, "ops_per_trial": OPS_PER_TRIAL,
             "trials_per_launch": trials_per_launch, "avg_launch_us": avg_ms * 1e3,
             "isolated_launch_us": (ms_prop + ms_comm) / n_prof * 1e3}
 
