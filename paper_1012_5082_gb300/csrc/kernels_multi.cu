@@ -87,7 +87,10 @@ __global__ void k_multi_rho(MultiArgs a, int r0) {
   a.rho[(long long)r * a.N + i] = rho;
   if (a.rf) {
     const float r32 = (float)rho;
-    a.rf[(long long)r * a.N + i] = make_float2(r32, emb32_val(a, ty[i], r32));
+    const int3 h = multi_half(a, (int)i);
+    const int b = (int)(i & 1);
+    a.rf[(long long)r * a.rf_n + multi_rfi(a, (h.x - b) >> 1, (h.y - b) >> 1, (h.z - b) >> 1, b)] =
+        make_float2(r32, emb32_val(a, ty[i], r32));
   }
 }
 
@@ -319,16 +322,24 @@ __device__ float multi_screen_bcc5(const MultiArgs& a, const long long* sDq, con
                                    const int* scode, int r, int i, int cx, int cy, int cz, int ta, int tb,
                                    long long* pq_out, float* err, bool* in) {
   const uint8_t* ty = a.types + (long long)r * a.N;
-  const float2* rf = a.rf + (long long)r * a.N;
+  const float2* rf = a.rf + (long long)r * a.rf_n;
   const int K = a.K;
   const int tid = threadIdx.x;
+  // wrapped offsets of cells -2..2: species index (sw[0..14]) and the
+  // per-site floats' index (sw[15..29]); rplane: the basis-1 half of the latter
+  const int rrow = a.qx * a.rf_q;
+  const int rplane = a.nz * a.ny * rrow;
 #pragma unroll
   for (int d = -2; d <= 2; ++d) {
-    sw[(d + 2) * MK_BLOCK + tid] = 2 * mk_wrap(cx + d, a.nx);
+    const int X = mk_wrap(cx + d, a.nx), xq = X / a.qx;
+    sw[(d + 2) * MK_BLOCK + tid] = 2 * X;
     sw[(d + 7) * MK_BLOCK + tid] = 2 * a.nx * mk_wrap(cy + d, a.ny);
     sw[(d + 12) * MK_BLOCK + tid] = 2 * a.nx * a.ny * mk_wrap(cz + d, a.nz);
+    sw[(d + 17) * MK_BLOCK + tid] = (X - xq * a.qx) * a.rf_q + xq;
+    sw[(d + 22) * MK_BLOCK + tid] = rrow * mk_wrap(cy + d, a.ny);
+    sw[(d + 27) * MK_BLOCK + tid] = rrow * a.ny * mk_wrap(cz + d, a.nz);
   }
-  const float2 ri = rf[i];
+  const float2 ri = rf[sw[17 * MK_BLOCK + tid] + sw[22 * MK_BLOCK + tid] + sw[27 * MK_BLOCK + tid] + (i & 1) * rplane];
   unsigned cnt[5];
   float re = 0.0f, ab = 0.0f;
   bool ok = true;
@@ -339,10 +350,12 @@ __device__ float multi_screen_bcc5(const MultiArgs& a, const long long* sDq, con
 #pragma unroll kScreenIlp
     for (int k = mk_shell0(s); k < mk_shell0(s + 1); ++k) {
       const int dc = scode[k];
-      const int j = sw[(dc & 7) * MK_BLOCK + tid] + sw[(5 + ((dc >> 3) & 7)) * MK_BLOCK + tid] +
-                    sw[(10 + ((dc >> 6) & 7)) * MK_BLOCK + tid] + ((dc >> 9) & 1);
+      const int ix = dc & 7, iy = (dc >> 3) & 7, iz = (dc >> 6) & 7, bb = (dc >> 9) & 1;
+      const int j = sw[ix * MK_BLOCK + tid] + sw[(5 + iy) * MK_BLOCK + tid] + sw[(10 + iz) * MK_BLOCK + tid] + bb;
+      const int jr = sw[(15 + ix) * MK_BLOCK + tid] + sw[(20 + iy) * MK_BLOCK + tid] + sw[(25 + iz) * MK_BLOCK + tid] +
+                     (bb ? rplane : 0);
       const int t = ty[j];
-      const float2 v = rf[j];
+      const float2 v = rf[jr];
       c += 1u << (8 * t);
       const float x1 = v.x + df;
       ok &= emb32_in(a, v.x) & emb32_in(a, x1);
@@ -435,7 +448,7 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
   __shared__ float sDfs[5 * MK_MAX * MK_MAX];
   // screened form: per-thread wrapped cell offsets and the block's
   // neighbour descriptors (unused otherwise)
-  __shared__ int sw[MODE == 2 ? 15 * MK_BLOCK : 1];
+  __shared__ int sw[MODE == 2 ? 30 * MK_BLOCK : 1];
   __shared__ int scode[MODE == 2 ? MK_BCC5_N : 1];
   __shared__ uint4 s_wc;
   __shared__ int s_col[4];
@@ -714,18 +727,23 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
     const int2 e = a.pend[(long long)r * a.D + q];
     const int tb = e.y & 255, ta = e.y >> 8;
     uint8_t* ty = a.types + (long long)r * a.N;
-    float2* rf = a.rf + (long long)r * a.N;
+    float2* rf = a.rf + (long long)r * a.rf_n;
+    const int3 ph = multi_half(a, e.x);
     if (k < MK_BCC5_N) {
       const int4 h = s_off[k];
-      const int j = multi_nbr_at(a, multi_half(a, e.x), h);
+      int X, Y, Z, bb;
+      multi_nbr_cell(a, ph, h, X, Y, Z, bb);
+      const int j = ((Z * a.ny + Y) * a.nx + X) * 2 + bb;
       double* rho = a.rho + (long long)r * a.N;
       const double nr = rho[j] + s_df[(h.w * K + ta) * K + tb];
       rho[j] = nr;
       const float r32 = (float)nr;
-      rf[j] = make_float2(r32, emb32_val(a, ty[j], r32));
+      rf[multi_rfi(a, X, Y, Z, bb)] = make_float2(r32, emb32_val(a, ty[j], r32));
     } else {
       ty[e.x] = (uint8_t)tb;
-      rf[e.x].y = emb32_val(a, tb, rf[e.x].x);
+      const int b = e.x & 1;
+      const long long q = multi_rfi(a, (ph.x - b) >> 1, (ph.y - b) >> 1, (ph.z - b) >> 1, b);
+      rf[q].y = emb32_val(a, tb, rf[q].x);
     }
   }
 }

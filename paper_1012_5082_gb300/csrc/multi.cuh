@@ -106,7 +106,13 @@ struct MultiArgs {
   float emb_lo, emb_hi;
   float emb_err;
   float qscale32;       // 2^-qbits as a float (exact)
-  float2* rf;           // [R][N]: (rho_i as float, F32_{t_i} of that)
+  // (rho_i as float, F32_{t_i} of that) per site, [R][rf_n], laid out by
+  // (basis, z, y, x mod qx, x div qx): the lanes of a warp, trials qx
+  // cells apart along x, read neighbours at one offset from consecutive
+  // entries.  rf_q = ceil(nx / qx); rf_n = 2 nz ny qx rf_q
+  float2* rf;
+  int rf_q;
+  long long rf_n;
   int n_sm;             // multiprocessors of the device (commit grid)
 };
 
@@ -137,6 +143,25 @@ __device__ __forceinline__ int multi_nbr_at(const MultiArgs& a, int3 p, int4 h) 
   Y += Y < 0 ? a.ny : (Y >= a.ny ? -a.ny : 0);
   Z += Z < 0 ? a.nz : (Z >= a.nz ? -a.nz : 0);
   return ((Z * a.ny + Y) * a.nx + X) * 2 + bb;
+}
+
+// neighbour at half-lattice position p + h as cell (X, Y, Z) and basis bb
+__device__ __forceinline__ void multi_nbr_cell(const MultiArgs& a, int3 p, int4 h, int& X, int& Y, int& Z, int& bb) {
+  const int qx = p.x + h.x, qy = p.y + h.y, qz = p.z + h.z;
+  bb = qx & 1;
+  X = (qx - bb) >> 1;
+  Y = (qy - bb) >> 1;
+  Z = (qz - bb) >> 1;
+  X += X < 0 ? a.nx : (X >= a.nx ? -a.nx : 0);
+  Y += Y < 0 ? a.ny : (Y >= a.ny ? -a.ny : 0);
+  Z += Z < 0 ? a.nz : (Z >= a.nz ? -a.nz : 0);
+}
+
+// entry of cell (X, Y, Z), basis b in the screened form's per-site floats
+__device__ __forceinline__ long long multi_rfi(const MultiArgs& a, int X, int Y, int Z, int b) {
+  const int xq = X / a.qx;
+  return ((long long)(b * a.nz + Z) * a.ny + Y) * ((long long)a.qx * a.rf_q) + (long long)(X - xq * a.qx) * a.rf_q +
+         xq;
 }
 
 __device__ __forceinline__ int multi_nbr(const MultiArgs& a, int i, int4 h) {

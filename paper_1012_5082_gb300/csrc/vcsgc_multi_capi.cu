@@ -281,7 +281,9 @@ int screen_setup(Multi* m, const std::vector<double>& hFd) {
   a.emb_lo = (float)lo;
   a.emb_hi = (float)(a.embed[0].xmax * (1.0 - 1e-6));
   a.emb_err = (float)(E * (1.0 + 1e-6));
-  MTRY(malloc_dev(m, &a.rf, (size_t)m->R * m->N));
+  a.rf_q = (m->nx + a.qx - 1) / a.qx;
+  a.rf_n = 2LL * m->nz * m->ny * a.qx * a.rf_q;
+  MTRY(malloc_dev(m, &a.rf, (size_t)m->R * a.rf_n));
   return VCSGC_OK;
 }
 
