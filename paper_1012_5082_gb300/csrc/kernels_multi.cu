@@ -289,14 +289,14 @@ __device__ double multi_de_bcc5(const MultiArgs& a, const long long* sDq, const 
 // dE in FP64 from the whole warp: 32 lanes share its 58 neighbours and two
 // own-site terms.  Every decision is therefore the one the FP64 dE takes.
 
-
 // FP32 dE of site i (cell (cx, cy, cz)) from species ta to tb without the
 // chemical-potential term; *err bounds its distance from the FP64 dE, *pq
 // is the exact fixed-point pair part, *in is false when an argument left
 // the bounded range.  sDfs[(s K + a) K + b] = f_b(r_s) - f_a(r_s) as
-// floats; sw: this block's [15][MK_BLOCK] scratch for the wrapped cell
-// offsets of the thread's site (x, y, z for cells -2..2, in site units);
-// scode: the block's neighbour descriptors.  The neighbours are visited
+// floats; sw: this block's [30][MK_BLOCK] scratch for the wrapped cell
+// offsets of the thread's site (x, y, z for cells -2..2), as species
+// indices and as indices of the per-site floats; scode: the block's
+// neighbour descriptors.  The neighbours are visited
 // shell by shell, kScreenIlp at a time (loads in flight per thread against
 // registers; a colour step of 64,000 trials gives about 13 warps per SM).
 
