@@ -549,6 +549,27 @@ def multi_bench(V, torch, stream, local, sweeps=10, warmup=2):
                         "reembed": ds is not None, "acc_local": o["acc_local"], "acc_global": o["acc_global"],
                         "launches_per_step": 2 if ds is not None else 1}
         g.close()
+    # binary with species-dependent densities (f_B = 1.25 f_A), one chain two
+    # ways: the binary context's FP64 re-embedding step and the
+    # multicomponent context's FP32-screened step with K = 2
+    tab = I.eam_tables(I.multi_eam_params(2, dens_scale=(1.0, 1.25)))
+    t = np.stack([I.random_types(lat.n, int(0.05 * lat.n), seed=8200 + r) for r in range(N_PHI)])
+    seeds = np.arange(N_PHI, dtype=np.uint64) + np.uint64(8300)
+    phi_b, kappa_b, T_b, c0_b = -2.2, 100.0, 1200.0, 0.05
+    g = V.Multi(lat, t, tab, [phi_b], kappa_b, T_b, c0=c0_b, seed_r=seeds, stream=stream, device=local)
+    b = V.Context(lat, t.reshape(-1), tab, phi_b, kappa_b, T_b, schedule=V.SCHED_SUBLATTICE, sched=(4, 4, 4),
+                  n_replicas=N_PHI, phi_r=np.full(N_PHI, phi_b), c0_r=np.full(N_PHI, c0_b), seed_r=seeds,
+                  stream=stream, device=local)
+    res = {}
+    for name, obj, sw in (("screened_K2", g, sweeps), ("binary_fp64", b, max(2, sweeps // 5))):
+        obj.sweep(warmup)
+        ms = timed_sweeps(torch, stream, obj, sw)
+        res[name] = {"trial_moves_per_s": N_PHI * lat.n * sw / (ms * 1e-3),
+                     "us_per_step": ms * 1e3 / (sw * obj.steps_per_sweep)}
+    res["acc_local"] = g.observables(0)["acc_local"]
+    g.close()
+    b.close()
+    out["binary_reembedding"] = res
     out["workload"] = "80^3 x 8 replicas, period-4 sublattice (64,000 trials per colour step)"
     return out
 

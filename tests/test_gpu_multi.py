@@ -182,3 +182,27 @@ def test_multi_screen_out_of_range_goes_fp64(V):
     assert og["flips"] > 100
     assert abs(og["energy"] - orc.energy_full()) <= 1e-9 * abs(og["energy"])
     g.close()
+
+
+def test_multi_k2_reembedding_retraces_binary_general_step(V):
+    """K = 2 with species-dependent densities (f_B = 1.25 f_A): the
+    multicomponent context's FP32-screened step and the binary context's
+    FP64 re-embedding step run the same chain on a 12^3 lattice (period-4
+    sublattice, same seeds and parameters): the same species after every
+    sweep, the same counters, and energies within 1e-9 relative."""
+    tab = I.eam_tables(I.multi_eam_params(2, dens_scale=(1.0, 1.25)))
+    lat = I.bcc_lattice(12, 12, 12)
+    t = I.random_types(lat.n, int(0.05 * lat.n), seed=77)
+    kappa, T, c0, phi = 100.0, 1200.0, 0.05, -2.2
+    m = V.Multi(lat, t, tab, [phi], kappa, T, c0=c0, seed_r=np.array([78], dtype=np.uint64))
+    b = V.Context(lat, t, tab, phi, kappa, T, seed=78, c0=c0, schedule=V.SCHED_SUBLATTICE, sched=(4, 4, 4))
+    for s in range(20):
+        m.sweep(1)
+        b.sweep(1)
+        assert np.array_equal(m.types(), b.types()), f"sweep {s}"
+    om, ob = m.observables(), b.observables()
+    assert om["flips"] == ob["flips"] > 2000 and om["n"][1] == ob["n_b"]
+    assert om["global_accepts"] == ob["global_accepts"]
+    assert abs(om["energy"] - ob["energy"]) <= 1e-9 * abs(ob["energy"])
+    m.close()
+    b.close()
