@@ -290,6 +290,25 @@ struct StepAcc {
 };
 
 // Everything the colour-step kernels read, passed by value.
+// FP32 embedding value of species t at x for the screened forms (Args: the
+// binary or multicomponent launch arguments, with emb32 [K][emb_n] float
+// cubics on one grid of 1/h = emb_ih).  Callers check x's range with
+// emb32_in; j is clamped so that the load stays inside the table anyway.
+template <class Args>
+__device__ __forceinline__ float emb32_val(const Args& a, int t, float x) {
+  const float u = x * a.emb_ih;
+  int j = (int)u;
+  j = j < 0 ? 0 : (j > a.emb_n - 1 ? a.emb_n - 1 : j);
+  const float tt = u - (float)j;
+  const float4 c = __ldg(a.emb32 + t * a.emb_n + j);
+  return fmaf(tt, fmaf(tt, fmaf(tt, c.w, c.z), c.y), c.x);
+}
+
+template <class Args>
+__device__ __forceinline__ bool emb32_in(const Args& a, float x) {
+  return x >= a.emb_lo && x <= a.emb_hi;
+}
+
 struct McArgs {
   long long N;
   int R;
@@ -329,6 +348,15 @@ struct McArgs {
   StepAcc* acc;
   int* acc_list;  // [R][dmax]
   unsigned* err;
+  // screened re-embedding (rigid lattice, shell form): the local decision on
+  // an FP32 dE within a proven bound.  Per site (rho as float, F32_t(rho)),
+  // [R][N]; the embedding cubics as floats [2][emb_n]; the bound per
+  // evaluation (eV) and the argument range where it holds.
+  int screen;
+  float2* rf;
+  const float4* emb32;
+  int emb_n;
+  float emb_ih, emb_lo, emb_hi, emb_err;
 };
 
 }  // namespace vcsgc

@@ -64,6 +64,8 @@ void launch_half_list(long long N, int K, const int* nbr, const int* cnt, int* n
 // rho_i of replica r (shared array when !per_rep) and, if dF != nullptr,
 // dF_i = F_B(rho_i) - F_A(rho_i).
 void launch_rho(const McArgs& a, bool shell, int r, cudaStream_t st);
+// screened re-embedding: per-site (float rho, F32 embedding) of replica r
+void launch_fill_rf(const McArgs& a, int r, cudaStream_t st);
 // Block partial sums of the energy of replica r into part[0..nblocks).
 int energy_blocks(long long N);
 void launch_energy(const McArgs& a, bool shell, int r, double* part, cudaStream_t st);

@@ -199,6 +199,84 @@ __device__ __forceinline__ int draw_colour(const McArgs& a, uint2 key, long long
   return (int)below64(w.x, w.y, (uint64_t)a.n_colours);
 }
 
+// Screened form of the shell dE with re-embedding (a.screen).  With
+// species-dependent densities a trial's dE holds 2 x 58 + 2 embedding
+// evaluations, which in FP64 (a small share of GB300's arithmetic) bound the
+// step.  The local decision is taken instead on this FP32 dE: the pair part
+// in FP64 as in delta_e (exact in arithmetic) rounded once, the own and the
+// neighbours' embedding changes in FP32 from the per-site floats (rho, and
+// F32_t(rho) cached).  *err bounds its distance from the FP64 dE: emb_err per
+// evaluation (the bound of screen.h), 2^-18 of the sum of |terms| for the
+// float additions and 2^-21 of the sizes of the final sums.  *in is false
+// when an argument left [emb_lo, emb_hi].
+__device__ float delta_e_screen(const McArgs& a, int r, int i, int t, float* err, bool* in) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const int* row = a.nbr + (long long)i * a.K;
+  const float2* rf = a.rf + (long long)r * a.N;
+  const int S = a.n_shells;
+  double pair = a.shell_tab[0];
+  float re = 0.0f, ab = 0.0f;
+  bool ok = true;
+  int k = 0;
+  for (int s = 0; s < S; ++s) {
+    const float dfs = (float)a.shell_tab[1 + S + s];
+    const float drho = t ? -dfs : dfs;
+    const int end = a.shell_end[s];
+    int cnt = 0;
+#pragma unroll 4
+    for (; k < end; ++k) {
+      const int j = row[k];
+      const int tj = ty[j];
+      const float2 v = rf[j];
+      cnt += tj;
+      const float x1 = v.x + drho;
+      ok &= emb32_in(a, v.x) & emb32_in(a, x1);
+      const float d = emb32_val(a, tj, x1) - v.y;
+      re += d;
+      ab += fabsf(d);
+    }
+    pair = fma((double)cnt, a.shell_tab[1 + s], pair);
+  }
+  if (t) pair = -pair;
+  const float2 ri = rf[i];
+  ok &= emb32_in(a, ri.x);
+  const float own = emb32_val(a, 1 - t, ri.x) - ri.y;
+  const float p32 = (float)pair;
+  *in = ok;
+  *err = fmaf((float)(2 * k + 2), a.emb_err,
+              fmaf(3.814697265625e-06f, ab, 4.76837158203125e-07f * (fabsf(p32) + fabsf(own) + fabsf(re))));
+  return (p32 + own) + re;
+}
+
+// lane's share of the FP64 shell dE with re-embedding of site i (species t):
+// neighbours k = lane, lane + 32, ... (their B-count pair terms and
+// re-embeddings); lane 0 adds the constant and the own change.  The warp's
+// sum is delta_e<true, true> up to the order of the additions.
+__device__ double delta_e_shell_lane(const McArgs& a, int r, int i, int t, int lane, unsigned* err) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const int* row = a.nbr + (long long)i * a.K;
+  const double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
+  const int S = a.n_shells;
+  const int n = a.shell_end[S - 1];
+  const double sg = t ? -1.0 : 1.0;
+  double v = 0.0;
+  for (int k = lane; k < n; k += 32) {
+    int s = 0;
+    while (k >= a.shell_end[s]) ++s;
+    const int j = row[k];
+    const int tj = ty[j];
+    const double drho = sg * a.shell_tab[1 + S + s];
+    const double rj = rho[j];
+    v += sg * (double)tj * a.shell_tab[1 + s];
+    v += spline_val(a.tab.sp[5 + tj], rj + drho, err) - spline_val(a.tab.sp[5 + tj], rj, err);
+  }
+  if (lane == 0) {
+    const double ri = rho[i];
+    v += sg * a.shell_tab[0] + spline_val(a.tab.sp[6 - t], ri, err) - spline_val(a.tab.sp[5 + t], ri, err);
+  }
+  return v;
+}
+
 template <bool SHELL, bool REEMBED>
 __global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
   const int r = blockIdx.y;
@@ -208,7 +286,8 @@ __global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
   const int d0 = a.col_start[c];
   const int D = a.col_start[c + 1] - d0;
   const int d = blockIdx.x * MC_BLOCK + threadIdx.x;
-  int dn = 0, acc = 0, tie = 0, site = -1;
+  int dn = 0, acc = 0, tie = 0, site = -1, t = 0, dec = 0;
+  uint64_t u53 = 0;
   double sde = 0.0;
   if (d < D) {
     const int g = d0 + d;
@@ -217,23 +296,64 @@ __global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
     if (size > 0) {
       const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL), p.key);
       site = a.dom_sites[base + pick_index(a.pick, w.x, w.y, size)];
-      const uint64_t u53 = top53(w.z, w.w);
-      const int t = a.types[(long long)r * a.N + site];
+      u53 = top53(w.z, w.w);
+      t = a.types[(long long)r * a.N + site];
       const double sg = t ? -1.0 : 1.0;
-      const double de = delta_e<SHELL, REEMBED>(a, r, site, a.err);
-      if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
-      const double X = p.beta * fma(sg, p.dmu0, de);
-      if (metropolis(X, u53, &tie)) {
-        acc = 1;
-        dn = t ? -1 : 1;
-        sde = de;
+      bool screened = false;
+      if constexpr (SHELL && REEMBED) {
+        if (a.screen) {
+          screened = true;
+          float err;
+          bool in;
+          const float e32 = delta_e_screen(a, r, site, t, &err, &in);
+          const float cm = (float)(sg * p.dmu0), b32 = (float)p.beta;
+          const float x32 = b32 * (e32 + cm);
+          const float dx = b32 * fmaf(4.76837158203125e-07f, fabsf(e32) + fabsf(cm), err) * 1.0001f +
+                           fabsf(x32) * 4.76837158203125e-07f;
+          dec = in ? screen32(x32, dx, u53) : -1;
+          if (dec > 0) {
+            acc = 1;
+            dn = t ? -1 : 1;
+          }
+        }
+      }
+      if (!screened) {
+        const double de = delta_e<SHELL, REEMBED>(a, r, site, a.err);
+        if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
+        const double X = p.beta * fma(sg, p.dmu0, de);
+        if (metropolis(X, u53, &tie)) {
+          acc = 1;
+          dn = t ? -1 : 1;
+          sde = de;
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  if constexpr (SHELL && REEMBED) {
+    // trials the screen left open: FP64 dE by the whole warp, one at a time
+    // (the energy of the screened form is not tracked: no dE sum)
+    unsigned open = __ballot_sync(0xffffffffu, dec < 0);
+    while (open) {
+      const int src = __ffs(open) - 1;
+      open &= open - 1u;
+      const int si = __shfl_sync(0xffffffffu, site, src), st = __shfl_sync(0xffffffffu, t, src);
+      double v = delta_e_shell_lane(a, r, si, st, lane, a.err);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == src) {
+        if (!isfinite(v)) atomicOr(a.err, ERRF_NONFINITE);
+        const double X = p.beta * fma(t ? -1.0 : 1.0, p.dmu0, v);
+        if (metropolis(X, u53, &tie)) {
+          acc = 1;
+          dn = t ? -1 : 1;
+        }
       }
     }
   }
   // compact the accepted sites: warp ballot, one reservation per warp
   const unsigned m = __ballot_sync(0xffffffffu, acc);
   int slot_base = 0;
-  const int lane = threadIdx.x & 31;
   if (m) {
     if (lane == 0) slot_base = atomicAdd(&a.acc[r].nacc, __popc(m));
     slot_base = __shfl_sync(0xffffffffu, slot_base, 0);
@@ -302,11 +422,22 @@ __device__ void commit_site(const McArgs& a, int r, int i, unsigned* err) {
     if constexpr (SHELL) {
       const int S = a.n_shells;
       int k = 0;
+      float2* rf = a.screen ? a.rf + (long long)r * a.N : nullptr;
       for (int s = 0; s < S; ++s) {
         const double dfs = a.shell_tab[1 + S + s];
         const double drho = t ? -dfs : dfs;
-        for (; k < a.shell_end[s]; ++k) rho[row[k]] += drho;
+        for (; k < a.shell_end[s]; ++k) {
+          const int j = row[k];
+          const double nr = rho[j] + drho;
+          rho[j] = nr;
+          if (rf) {
+            // the screened form's float copy and its FP32 embedding value
+            const float r32 = (float)nr;
+            rf[j] = make_float2(r32, emb32_val(a, ty[j], r32));
+          }
+        }
       }
+      if (rf) rf[i].y = emb32_val(a, 1 - t, rf[i].x);
     } else {
       const int cnt = a.nbr_cnt[i];
       const int tp = 1 - t;
@@ -388,6 +519,18 @@ __global__ void __launch_bounds__(MC_BLOCK) k_commit(McArgs a) {
       A->done = 0u;
     }
   }
+}
+
+// the screened form's per-site floats of replica r from its densities
+__global__ void k_fill_rf(McArgs a, int r) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const float r32 = (float)a.rho[(long long)r * a.N + i];
+  a.rf[(long long)r * a.N + i] = make_float2(r32, emb32_val(a, a.types[(long long)r * a.N + i], r32));
+}
+
+void launch_fill_rf(const McArgs& a, int r, cudaStream_t st) {
+  k_fill_rf<<<(unsigned)((a.N + 255) / 256), 256, 0, st>>>(a, r);
 }
 
 // dE of a list of sites with the sweep's own device function (general

@@ -32,18 +32,6 @@ __host__ __device__ __forceinline__ int multi_tri(int K, int a, int b) {
   return a * K - a * (a - 1) / 2 + (b - a);
 }
 
-// FP32 embedding value of species t at x (callers check x's range; j is
-// clamped so that the load stays inside the table in any case)
-__device__ __forceinline__ float emb32_val(const MultiArgs& a, int t, float x) {
-  const float u = x * a.emb_ih;
-  int j = (int)u;
-  j = j < 0 ? 0 : (j > a.emb_n - 1 ? a.emb_n - 1 : j);
-  const float tt = u - (float)j;
-  const float4 c = __ldg(a.emb32 + t * a.emb_n + j);
-  return fmaf(tt, fmaf(tt, fmaf(tt, c.w, c.z), c.y), c.x);
-}
-
-__device__ __forceinline__ bool emb32_in(const MultiArgs& a, float x) { return x >= a.emb_lo && x <= a.emb_hi; }
 
 __global__ void k_multi_shell_tables(const Spline* pair, const Spline* dens, int K, const double* r_s, int n_sh,
                                      double* V, double* Fd, unsigned* err) {

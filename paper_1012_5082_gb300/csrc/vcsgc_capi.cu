@@ -13,6 +13,7 @@
 #include "../../include/vcsgc.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "screen.h"
 #include "trace.h"
 
 using namespace vcsgc;
@@ -59,6 +60,14 @@ struct Ctx {
   Cubic* coef[7] = {};
   Cubic* dcoef[7] = {};
   double* shell_tab = nullptr;
+  // screened re-embedding (rigid lattice): per-site floats, float cubics of
+  // the embedding, the bound; the energy is recomputed when read
+  bool screen = false;
+  float2* rf = nullptr;
+  float4* emb32 = nullptr;
+  int emb_n = 0;
+  float emb_ih = 0.f, emb_lo = 0.f, emb_hi = 0.f, emb_err = 0.f;
+  bool energy_stale = false;
   int* col_start = nullptr;
   int* dom_start = nullptr;
   int* dom_sites = nullptr;
@@ -221,6 +230,14 @@ void fill_args(Ctx* c) {
   for (int q = 0; q < 3; ++q) a.box[q] = c->box[q];
   a.rc = c->rc;
   a.mixed = c->mixed ? 1 : 0;
+  a.screen = c->screen ? 1 : 0;
+  a.rf = c->rf;
+  a.emb32 = c->emb32;
+  a.emb_n = c->emb_n;
+  a.emb_ih = c->emb_ih;
+  a.emb_lo = c->emb_lo;
+  a.emb_hi = c->emb_hi;
+  a.emb_err = c->emb_err;
   a.n_colours = c->n_colours;
   a.col_start = c->col_start;
   a.dom_start = c->dom_start;
@@ -620,7 +637,54 @@ int energy_of(Ctx* c, int r, double* out) {
 // recompute rho (and dF) of replica r, or of the shared array
 int refresh_rho(Ctx* c, int r) {
   launch_rho(c->mc, c->shell, r, c->st);
+  if (c->screen) launch_fill_rf(c->mc, r, c->st);
   CK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
+// screened form: the tracked energies are not kept up to date by the sweep;
+// recompute them before anything reads the replica states
+int refresh_energies(Ctx* c) {
+  if (!c->screen || !c->energy_stale) return VCSGC_OK;
+  for (int r = 0; r < c->R; ++r) {
+    double e;
+    TRY(energy_of(c, r, &e));
+    CK(cudaMemcpyAsync(&c->rs[r].energy, &e, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  }
+  c->energy_stale = false;
+  return VCSGC_OK;
+}
+
+// Tables and bound of the screened re-embedding form (rigid lattice, shell
+// form; the bound: screen.h)
+int screen_setup(Ctx* c) {
+  const int n = c->mc.tab.sp[5].n_int;
+  const double h = 1.0 / c->mc.tab.sp[5].inv_h;
+  if (c->mc.tab.sp[6].n_int != n || c->mc.tab.sp[6].inv_h != c->mc.tab.sp[5].inv_h) return VCSGC_OK;
+  TRY(dalloc(c, &c->emb32, (size_t)2 * n));
+  std::vector<std::vector<Cubic>> hc(2, std::vector<Cubic>((size_t)n));
+  for (int t = 0; t < 2; ++t) {
+    launch_to_cubic32(c->coef[5 + t], n, reinterpret_cast<Cubic32*>(c->emb32 + (size_t)t * n), c->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(hc[t].data(), c->coef[5 + t], sizeof(Cubic) * n, cudaMemcpyDeviceToHost, c->st));
+  }
+  const int S = c->mc.n_shells;
+  std::vector<double> dfs((size_t)S);
+  CK(cudaMemcpyAsync(dfs.data(), c->shell_tab + 1 + S, sizeof(double) * S, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double dmax = 0.0;
+  for (double v : dfs) dmax = std::max(dmax, std::fabs(v));
+  const ScreenBound sb = screen_bound(hc, h, dmax);
+  if (!std::isfinite(sb.err)) return fail(c, VCSGC_ERR_NONFINITE, "non-finite embedding table");
+  TRY(dalloc(c, &c->rf, (size_t)c->R * c->N));
+  c->emb_n = n;
+  c->emb_ih = (float)c->mc.tab.sp[5].inv_h;
+  c->emb_lo = (float)sb.lo;
+  c->emb_hi = (float)sb.hi;
+  c->emb_err = (float)sb.err;
+  c->screen = true;
+  fill_args(c);
   return VCSGC_OK;
 }
 
@@ -696,6 +760,7 @@ int sync_bytes(Ctx* c, int r) {
 int run_steps(Ctx* c, long long n) {
   if (n <= 0) return VCSGC_OK;
   if (c->fast) return run_steps_fast(c, n);
+  if (c->screen) c->energy_stale = true;
   const int G = 64;
   if (n >= G) {
     if (!c->graph) {
@@ -1200,6 +1265,8 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   CK(cudaMemcpyAsync(c->rp, c->h_rp.data(), sizeof(RepParams) * c->R, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->rs, hs.data(), sizeof(RepState) * c->R, cudaMemcpyHostToDevice, c->st));
 
+  // ---- screened re-embedding on the rigid lattice
+  if (c->kind == 0 && c->reembed && c->shell && c->mc.n_shells > 0) TRY(screen_setup(c));
   // ---- rho, dF and energies (A2)
   if (c->reembed) {
     for (int r = 0; r < c->R; ++r) TRY(refresh_rho(c, r));
@@ -1773,6 +1840,7 @@ int observables(void* ctx, int32_t r, vcsgc_observables* o) {
   if (!c || !o || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   TRY(flush(c));
   TRY(check_device_error(c));
+  TRY(refresh_energies(c));
   RepState s;
   CK(cudaMemcpyAsync(&s, c->rs + r, sizeof(RepState), cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -1785,6 +1853,7 @@ int vcsgc_observables_all(void* ctx, vcsgc_observables* o) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !o) return VCSGC_ERR_INVALID_ARG;
   TRY(flush(c));
+  TRY(refresh_energies(c));
   // the states and the error word through one pinned buffer, one synchronisation
   const size_t bytes = sizeof(RepState) * c->R + sizeof(unsigned);
   if (c->h_pin_bytes < bytes) {
@@ -2269,6 +2338,7 @@ int vcsgc_save(void* ctx, const char* path) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !path) return VCSGC_ERR_INVALID_ARG;
   TRY(sync_bytes(c, -1));
+  TRY(refresh_energies(c));
   long long tot = 0;
   for (int r = 0; r < c->R; ++r) tot += c->rep_n[r];
   std::vector<uint8_t> types(tot);
@@ -2365,6 +2435,7 @@ int vcsgc_load(void* ctx, const char* path) {
   // counters, step and the tracked energy exactly as saved
   CK(cudaMemcpyAsync(c->rs, rs.data(), sizeof(RepState) * c->R, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
+  c->energy_stale = false;
   c->forces_valid = false;
   fill_args(c);
   return check_device_error(c);

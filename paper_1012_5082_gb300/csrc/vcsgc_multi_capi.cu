@@ -10,6 +10,7 @@
 
 #include "kernels.h"
 #include "multi.cuh"
+#include "screen.h"
 #include "trace.h"
 #include "vcsgc.h"
 
@@ -223,21 +224,8 @@ void destroy(Multi* m) {
 
 thread_local std::string g_init_err;
 
-// Tables and error bound of the FP32 screen with re-embedding.  For one
-// embedding cubic p_j(t) = c0 + t (c1 + t (c2 + t c3)) on interval j, an FP32
-// evaluation at an argument carried in float differs from the FP64 one by at
-// most 2^-24 [5 G + 4 P + 2 dmax S] to first order, where
-//   G = max_j sum_k |c_jk|            coefficient rounding and three FMAs,
-//   P = max_j (j + 2) max(D_j-1, D_j, D_j+1), D_j = |c1| + 2|c2| + 3|c3|:
-//       |x F'| near interval j; the argument rho + (f_b - f_a) and x / h
-//       carry relative errors 2^-24 (|rho| + |f_b - f_a| + 3|x|),
-//   S = max_j D_j / h, dmax = max |f_b(r_s) - f_a(r_s)|: the part of that
-//       argument error that scales with |f_b - f_a|.
-// emb_err takes 2^-24 [6 G + 5 P + 3 dmax S] over all species and the
-// intervals of the screened range [x_lo, x_max (1 - 10^-6)], x_lo = max(h,
-// x_max / 20); the FP64 evaluation is in range there, and below x_lo (a
-// nearly isolated atom) the slope of a sqrt-like embedding would dominate
-// the bound.  Arguments outside the range go to FP64.
+// Tables and error bound of the FP32 screen with re-embedding (the bound:
+// screen.h).
 int screen_setup(Multi* m, const std::vector<double>& hFd) {
   MultiArgs& a = m->args;
   const int n = a.embed[0].n_int;
@@ -246,41 +234,26 @@ int screen_setup(Multi* m, const std::vector<double>& hFd) {
       return mfail(m, VCSGC_ERR_INVALID_ARG, "embedding tables on different grids");
   float4* e32 = nullptr;
   MTRY(malloc_dev(m, &e32, (size_t)m->K * n));
-  std::vector<Cubic> hc((size_t)n);
-  const double h = 1.0 / a.embed[0].inv_h;
-  const double lo = std::max(h, a.embed[0].xmax / 20.0);
-  const int jlo = std::max(0, (int)std::floor(lo / h) - 1);
-  double G = 0.0, P = 0.0, S = 0.0;
+  std::vector<std::vector<Cubic>> hc((size_t)m->K, std::vector<Cubic>((size_t)n));
   for (int al = 0; al < m->K; ++al) {
     launch_to_cubic32(a.embed[al].c, n, reinterpret_cast<Cubic32*>(e32 + (size_t)al * n), m->st);
     MCK(cudaGetLastError());
-    MCK(cudaMemcpyAsync(hc.data(), a.embed[al].c, sizeof(Cubic) * n, cudaMemcpyDeviceToHost, m->st));
-    MCK(cudaStreamSynchronize(m->st));
-    std::vector<double> D((size_t)n);
-    for (int j = jlo; j < n; ++j) {
-      const Cubic& c = hc[j];
-      G = std::max(G, std::fabs(c.x) + std::fabs(c.y) + std::fabs(c.z) + std::fabs(c.w));
-      D[j] = std::fabs(c.y) + 2.0 * std::fabs(c.z) + 3.0 * std::fabs(c.w);
-      S = std::max(S, D[j] * a.embed[al].inv_h);
-    }
-    for (int j = jlo + 1; j < n; ++j) {
-      const double dn = std::max(D[j], std::max(D[j - 1], j + 1 < n ? D[j + 1] : 0.0));
-      P = std::max(P, (double)(j + 2) * dn);
-    }
+    MCK(cudaMemcpyAsync(hc[al].data(), a.embed[al].c, sizeof(Cubic) * n, cudaMemcpyDeviceToHost, m->st));
   }
+  MCK(cudaStreamSynchronize(m->st));
   double dmax = 0.0;
   for (int s = 0; s < a.n_sh; ++s)
     for (int x = 0; x < m->K; ++x)
       for (int y = 0; y < m->K; ++y) dmax = std::max(dmax, std::fabs(hFd[s * m->K + y] - hFd[s * m->K + x]));
-  const double E = std::ldexp(6.0 * G + 5.0 * P + 3.0 * dmax * S, -24);
-  if (!std::isfinite(E)) return mfail(m, VCSGC_ERR_NONFINITE, "non-finite embedding table");
+  const ScreenBound sb = screen_bound(hc, 1.0 / a.embed[0].inv_h, dmax);
+  if (!std::isfinite(sb.err)) return mfail(m, VCSGC_ERR_NONFINITE, "non-finite embedding table");
   MCK(cudaDeviceGetAttribute(&a.n_sm, cudaDevAttrMultiProcessorCount, m->device));
   a.emb32 = e32;
   a.emb_n = n;
   a.emb_ih = (float)a.embed[0].inv_h;
-  a.emb_lo = (float)lo;
-  a.emb_hi = (float)(a.embed[0].xmax * (1.0 - 1e-6));
-  a.emb_err = (float)(E * (1.0 + 1e-6));
+  a.emb_lo = (float)sb.lo;
+  a.emb_hi = (float)sb.hi;
+  a.emb_err = (float)sb.err;
   a.rf_q = (m->nx + a.qx - 1) / a.qx;
   a.rf_n = 2LL * m->nz * m->ny * a.qx * a.rf_q;
   MTRY(malloc_dev(m, &a.rf, (size_t)m->R * a.rf_n));
