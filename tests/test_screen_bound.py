@@ -1,5 +1,5 @@
 """The error bound behind the FP32 screen of the multicomponent step with
-re-embedding.  For an embedding cubic p_j(t) = c0 + t (c1 + t (c2 + t c3))
+re-embedding (multicomponent and binary forms).  For an embedding cubic p_j(t) = c0 + t (c1 + t (c2 + t c3))
 evaluated in float (coefficients rounded to float, three FMAs, the
 argument rho + f_b(r_s) - f_a(r_s) and x / h carried in float), the
 distance from the FP64 evaluation is at most 2^-24 [6 G + 5 P + 3 dmax S]
@@ -7,8 +7,9 @@ distance from the FP64 evaluation is at most 2^-24 [6 G + 5 P + 3 dmax S]
 |F'|, dmax = max |f_b(r_s) - f_a(r_s)|; over the screened range x >=
 max(h, x_max / 20)).  This restates the bound as the device's setup
 computes it and checks it against float evaluations emulated in numpy on
-the four-species tables of the workload."""
+the tables of the workloads."""
 import numpy as np
+import pytest
 
 from paper_1012_5082_gb300 import inputs as I
 
@@ -32,14 +33,17 @@ def _fma32(a, b, c):
     return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
 
 
-def test_fp32_embedding_error_within_bound():
-    p = I.multi_eam_params(4, dens_scale=(1.0, 1.25, 0.85, 1.1))
+@pytest.mark.parametrize("K,ds", [(4, (1.0, 1.25, 0.85, 1.1)), (2, (1.0, 1.25))])
+def test_fp32_embedding_error_within_bound(K, ds):
+    """K = 4: the multicomponent workload's tables; K = 2: the binary
+    context's re-embedding tables (f_B = 1.25 f_A)."""
+    p = I.multi_eam_params(K, dens_scale=ds)
     T = I.eam_tables(p)
     h, n = T.drho, T.nrho - 1
     ih = 1.0 / h
     lo = max(h, (n * h) / 20.0)
     jlo = max(0, int(np.floor(lo / h)) - 1)
-    coefs = [_coefficients(np.asarray(T.embed[t]), np.asarray(T.dembed[t]), h) for t in range(4)]
+    coefs = [_coefficients(np.asarray(T.embed[t]), np.asarray(T.dembed[t]), h) for t in range(K)]
     G = P = S = 0.0
     for C in coefs:
         G = max(G, np.abs(C[jlo:]).sum(1).max())
@@ -48,18 +52,18 @@ def test_fp32_embedding_error_within_bound():
         Dn = np.maximum(D, np.maximum(np.r_[0.0, D[:-1]], np.r_[D[1:], 0.0]))
         P = max(P, ((np.arange(n) + 2) * Dn)[jlo + 1:].max())
     rs = A * np.sqrt(np.array([3, 4, 8, 11, 12])) / 2
-    Fd = np.array([[p.dens(t, r)[0] for t in range(4)] for r in rs])
+    Fd = np.array([[p.dens(t, r)[0] for t in range(K)] for r in rs])
     dmax = np.abs(Fd[:, :, None] - Fd[:, None, :]).max()
     E = 2.0 ** -24 * (6 * G + 5 * P + 3 * dmax * S)
 
     rho0 = (np.array([8, 6, 12, 24, 8]) * Fd[:, 0]).sum()
     rng = np.random.default_rng(7)
     M = 400_000
-    t = rng.integers(0, 4, M)
+    t = rng.integers(0, K, M)
     rho = rng.uniform(0.5 * rho0, 1.6 * rho0, M)
-    s, a, b = rng.integers(0, 5, M), rng.integers(0, 4, M), rng.integers(0, 4, M)
+    s, a, b = rng.integers(0, 5, M), rng.integers(0, K, M), rng.integers(0, K, M)
     dfs = Fd[s, b] - Fd[s, a]
-    Call = np.stack(coefs)                     # [4, n, 4]
+    Call = np.stack(coefs)                     # [K, n, 4]
 
     def ev64(x):
         u = x * ih
