@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
   if (m) {
     if (lane == 0) slot_base = atomicAdd(&a.acc[r].nacc, __popc(m));
     slot_base = __shfl_sync(0xffffffffu, slot_base, 0);
-    if (acc) a.acc_list[(long long)r * a.dmax + slot_base + __popc(m & ((1u << lane) - 1u))] = site;
+    if (acc) a.acc_list[(long long)r * a.dmax + slot_base + __popc(m & ((1u << lane) - 1u))] = site | (t << 30);
   }
   if (tie) atomicAdd(&a.acc[r].ties, 1);
   int dummy = 0;
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(MCW_BLOCK) k_propose_warp(McArgs a) {
   const double X = p.beta * fma(t ? -1.0 : 1.0, p.dmu0, de);
   if (metropolis(X, top53(w.z, w.w), &tie)) {
     const int slot = atomicAdd(&a.acc[r].nacc, 1);
-    a.acc_list[(long long)r * a.dmax + slot] = site;
+    a.acc_list[(long long)r * a.dmax + slot] = site | (t << 30);
     atomicAdd(&a.acc[r].dn, t ? -1 : 1);
     atomicAdd(&a.acc[r].sum_de, de);
   }
@@ -463,6 +463,38 @@ __device__ void commit_site(const McArgs& a, int r, int i, unsigned* err) {
   }
 }
 
+// item k of an accepted flip of site i (old species t) on the rigid lattice
+// with re-embedding: k < n, neighbour k's density change (and the screened
+// form's floats there); k = n, the site's species (and its FP32 embedding
+// value).  No two items touch a common site: the accepts of one colour are
+// more than 2 r_c apart.
+__device__ __forceinline__ void commit_item_shell(const McArgs& a, int r, int i, int t, int k, int n) {
+  uint8_t* ty = a.types + (long long)r * a.N;
+  float2* rf = a.screen ? a.rf + (long long)r * a.N : nullptr;
+  if (k < n) {
+    int s = 0;
+    while (k >= a.shell_end[s]) ++s;
+    const double dfs = a.shell_tab[1 + a.n_shells + s];
+    const int j = a.nbr[(long long)i * a.K + k];
+    double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
+    const double nr = rho[j] + (t ? -dfs : dfs);
+    rho[j] = nr;
+    if (rf) {
+      const float r32 = (float)nr;
+      rf[j] = make_float2(r32, emb32_val(a, ty[j], r32));
+    }
+  } else {
+    ty[i] = (uint8_t)(1 - t);
+    if (a.vel[0] && r == 0) {
+      const double f = sqrt(a.mass[t] / a.mass[1 - t]);
+      a.vel[0][i] *= f;
+      a.vel[1][i] *= f;
+      a.vel[2][i] *= f;
+    }
+    if (rf) rf[i].y = emb32_val(a, 1 - t, rf[i].x);
+  }
+}
+
 template <bool SHELL, bool REEMBED>
 __global__ void __launch_bounds__(MC_BLOCK) k_commit(McArgs a) {
   const int r = blockIdx.y;
@@ -482,8 +514,23 @@ __global__ void __launch_bounds__(MC_BLOCK) k_commit(McArgs a) {
     G = metropolis(Y, ug53, &tie);
   }
   if (G) {
-    for (int q = blockIdx.x * MC_BLOCK + threadIdx.x; q < nacc; q += gridDim.x * MC_BLOCK)
-      commit_site<SHELL, REEMBED>(a, r, a.acc_list[(long long)r * a.dmax + q], a.err);
+    if constexpr (SHELL && REEMBED) {
+      // one thread per (accept, neighbour) and one per accepted site: the
+      // density change (and the screened form's floats) of each neighbour,
+      // then the species.  The old species travels in the list entry, so
+      // no thread reads a species another thread of this launch writes.
+      const int n = a.shell_end[a.n_shells - 1];
+      const int items = nacc * (n + 1);
+      for (int it = blockIdx.x * MC_BLOCK + threadIdx.x; it < items; it += gridDim.x * MC_BLOCK) {
+        const int q = it / (n + 1), k = it - q * (n + 1);
+        const int e = a.acc_list[(long long)r * a.dmax + q];
+        const int i = e & 0x3FFFFFFF, t = e >> 30;
+        commit_item_shell(a, r, i, t, k, n);
+      }
+    } else {
+      for (int q = blockIdx.x * MC_BLOCK + threadIdx.x; q < nacc; q += gridDim.x * MC_BLOCK)
+        commit_site<SHELL, REEMBED>(a, r, a.acc_list[(long long)r * a.dmax + q] & 0x3FFFFFFF, a.err);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -562,7 +609,9 @@ static void launch_step_t(const McArgs& a, cudaStream_t st, int phase) {
       else k_propose_warp<REEMBED, false><<<dim3(wb, a.R), MCW_BLOCK, 0, st>>>(a);
     }
   }
-  if (phase != 1) k_commit<SHELL, REEMBED><<<dim3(cb < 8 ? cb : 8, a.R), MC_BLOCK, 0, st>>>(a);
+  // the rigid re-embedding commit runs one thread per (accept, neighbour):
+  // as many blocks as the propose
+  if (phase != 1) k_commit<SHELL, REEMBED><<<dim3((SHELL && REEMBED) ? cb : (cb < 8 ? cb : 8), a.R), MC_BLOCK, 0, st>>>(a);
 }
 
 void launch_colour_step(const McArgs& a, bool shell, bool reembed, cudaStream_t st, int phase) {

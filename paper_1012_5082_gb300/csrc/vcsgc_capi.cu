@@ -1019,7 +1019,8 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   } else {
     return fail(c, VCSGC_ERR_INVALID_ARG, "lattice kind must be 0 or 1");
   }
-  if (c->N > 0x7fffffffLL) return fail(c, VCSGC_ERR_INVALID_ARG, "too many sites");
+  // the accepted-site list packs a site index and its species in 32 bits
+  if (c->N >= (1LL << 30)) return fail(c, VCSGC_ERR_INVALID_ARG, "too many sites (at most 2^30 - 1)");
   if (!(T > 0) || !(kappa >= 0)) return fail(c, VCSGC_ERR_INVALID_ARG, "T must be > 0 and kappa >= 0");
   for (long long i = 0; i < (long long)c->R * c->N; ++i)
     if (types[i] > 1) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
