@@ -156,7 +156,9 @@ typedef struct {
   int64_t n_sites;
   int64_t n_b;
   double c;
-  double energy;          /* incrementally tracked total energy (eV) */
+  double energy;          /* total energy (eV): tracked step by step, or
+                             recomputed by this call (rigid lattice with
+                             species-dependent densities) */
   double energy_per_atom;
   int64_t steps;          /* colour (composite) steps */
   int64_t trials;         /* local trial moves */
@@ -187,8 +189,12 @@ int vcsgc_default_options(vcsgc_options* opt);
  * device, build the neighbour list (A1), rho and U (A2) and the colour
  * schedule (A3).  phi (eV), kappa and T (K) follow Eq. pi_vcsgc:
  * pi_V ~ exp[-beta (U + phi n + kappa_p n^2)].  opt may be NULL.
- * Errors: INVALID_ARG (bad sizes, species other than 0/1, T <= 0),
- * SCHEDULE, TABLE_RANGE, NOMEM, CUDA. */
+ * With species-dependent densities on a rigid lattice the local decision is
+ * taken on an FP32 dE within a proven error bound (FP64 where the bound
+ * cannot decide), so every decision is the FP64 one; the energy is then
+ * recomputed when observables or a checkpoint read it.
+ * Errors: INVALID_ARG (bad sizes, N >= 2^30 sites, species other than 0/1,
+ * T <= 0), SCHEDULE, TABLE_RANGE, NOMEM, CUDA. */
 int vcsgc_init(void** ctx, const vcsgc_lattice* lattice, const uint8_t* types,
                const vcsgc_eam_tables* eam, double phi, double kappa, double T,
                const vcsgc_options* opt);
