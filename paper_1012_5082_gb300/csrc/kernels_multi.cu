@@ -19,6 +19,9 @@
 // colour step: propose (local stage, compaction of the accepts, per-solute
 // dn by warp reductions; the last block of each replica takes the global
 // decision) and commit (species and density scatter of an accepted step).
+// With re-embedding on the five-shell table the propose is FP32-screened
+// (below) and the commit runs one thread per (accept, neighbour); without
+// re-embedding one fused launch per step carries both (k_multi_fused).
 #include "multi.cuh"
 
 namespace vcsgc {
