@@ -11,6 +11,9 @@
 //              and, if accepted, flips its share of the list and scatters the
 //              density change; the last block to finish advances the
 //              replica's counters.
+// On the rigid lattice with species-dependent densities the local test is
+// FP32-screened (delta_e_screen) and the commit runs one thread per
+// (accept, neighbour).
 #include "common.cuh"
 #include "kernels.h"
 
