@@ -223,14 +223,18 @@ __device__ __forceinline__ float u53_float(uint64_t u53) {
 constexpr uint64_t U53_NEAR_ONE = (uint64_t)((1.0 - 1e-9) * 9007199254740992.0);
 
 // FP32 screen of u < min{1, exp(-X)} given x32 with |x32 - X| <= dx:
-// 1 accept, 0 reject, -1 undecided (decide in FP64)
+// 1 accept, 0 reject, -1 undecided (decide in FP64).  exp(-x32) is within a
+// factor exp(+-dx) of exp(-X); the relative margin dx + dx^2 covers
+// exp(dx) - 1 for dx <= 1 (the second-order term matters once dx exceeds
+// about 1e-3, as in the re-embedding screens), 2^-20 the expf bound and the
+// float products.
 __device__ __forceinline__ int screen32(float x32, float dx, uint64_t u53) {
   if (x32 <= -2.0f * dx) return 1;
   if (u53 == 0) return -1;
   if (x32 >= 80.0f + dx) return 0;
   const float pf = expf(-x32) * 9007199254740992.0f;  // p * 2^53
   const float uf = u53_float(u53);
-  const float m = dx + 9.5367431640625e-07f;          // + 2^-20 (expf, products)
+  const float m = fmaf(dx, dx, dx) + 9.5367431640625e-07f;
   if (uf * (1.0f + 2.384185791015625e-07f) < pf * (1.0f - m)) return 1;
   if (uf * (1.0f - 2.384185791015625e-07f) > pf * (1.0f + m)) return 0;
   return -1;

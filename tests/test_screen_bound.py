@@ -90,3 +90,46 @@ def test_fp32_embedding_error_within_bound(K, ds):
     # and small enough that the screen decides nearly every trial: 118
     # evaluations at 1200 K are below 1 % of kT
     assert 118 * E < 0.01 * I.KB_EV * 1200.0
+
+
+def _screen(x32, dx, u53, second_order=True):
+    """The FP32 screen's rule restated in numpy (float32 arithmetic):
+    accept, reject or -1 (undecided) for u = u53 2^-53 against exp(-X),
+    given x32 within dx of X."""
+    f = np.float32
+    x32, dx = f(x32), f(dx)
+    if x32 <= f(-2.0) * dx:
+        return 1
+    if u53 == 0:
+        return -1
+    if x32 >= f(80.0) + dx:
+        return 0
+    pf = f(np.exp(-np.float64(x32))) * f(2.0 ** 53)
+    uf = f(u53)
+    m = dx + (dx * dx if second_order else f(0.0)) + f(2.0 ** -20)
+    if uf * f(1 + 2.0 ** -22) < pf * (f(1) - m):
+        return 1
+    if uf * f(1 - 2.0 ** -22) > pf * (f(1) + m):
+        return 0
+    return -1
+
+
+def test_screen_margin_covers_the_second_order_term():
+    """With x32 at the far end of its bound (x32 = X + dx, so exp(-x32) is
+    exp(-X) e^-dx) and u just below exp(-X), a margin of dx alone rejects
+    moves the FP64 test accepts once dx exceeds about 1e-3 (as in the
+    re-embedding screens, dx ~ 5e-3); the margin dx + dx^2 never decides
+    against the FP64 test."""
+    rng = np.random.default_rng(11)
+    wrong = {True: 0, False: 0}
+    for _ in range(20000):
+        X = rng.uniform(0.05, 10.0)
+        dx = 10 ** rng.uniform(-4, -1.3)
+        p = np.exp(-X)
+        u53 = int(p * (1 - rng.uniform(0, dx * dx / 4)) * 2 ** 53)
+        truth = 1 if u53 * 2.0 ** -53 < p else 0
+        for so in (True, False):
+            d = _screen(X + 0.999 * dx, dx, u53, so)
+            wrong[so] += d >= 0 and d != truth
+    assert wrong[True] == 0
+    assert wrong[False] > 1000
