@@ -494,6 +494,10 @@ typedef struct {
  * species), T[n_replicas], seed_r[n_replicas] (Philox keys; NULL: r + 1).
  * period[3] = (qx, qy, qz) divides the cell counts.  stream: a cudaStream_t
  * or NULL (the context makes its own); device < 0: the current device.
+ * With species-dependent densities on the five-shell neighbourhood (and at
+ * most 1024 replicas) the local decision is taken on an FP32 dE within a
+ * proven error bound, FP64 where the bound cannot decide: every decision is
+ * the FP64 one; the energy is then recomputed by vcsgc_multi_observables.
  * Errors: INVALID_ARG (sizes, species, K, period), SCHEDULE (q a <= 2 r_c),
  * NOMEM, CUDA, TABLE_RANGE (a shell outside the grids). */
 int vcsgc_multi_init(void** out, const vcsgc_lattice* lattice, const uint8_t* types, const vcsgc_multi_tables* tables,
