@@ -283,6 +283,26 @@ int vcsgc_kinetic_energy(void* ctx, double* out);
  * of the commit kernels.  Same work as vcsgc_steps(n); for profiling. */
 int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_commit);
 
+/* Launch shape of the fused colour step.  form 0: one launch per colour
+ * step for every replica, `block` threads per thread block (64, 128 or
+ * 256), with (prefetch = 1) or without (0) the trial's neighbour rows loaded
+ * ahead of the block barrier.  Any shape advances the same chain (the random
+ * numbers are keyed by step and trial, not by thread).  vcsgc_autotune picks
+ * one by timing; this call sets one explicitly (tests, profiling).
+ * Errors: INVALID_ARG (unknown form or shape), STATE (the context is not in
+ * the fused form). */
+int vcsgc_set_launch(void* ctx, int32_t form, int32_t block, int32_t prefetch);
+/* The current launch shape (HOST outputs; any may be NULL). */
+int vcsgc_get_launch(void* ctx, int32_t* form, int32_t* block, int32_t* prefetch);
+
+/* Philox4x32-10 words of the device generator every kernel draws from
+ * (Salmon, Moraes, Dror and Shaw, SC'11), for checks against the
+ * generator's published known-answer values: out[4q..4q+3] = Philox4x32-10
+ * of counter ctr[4q..4q+3] under key key[2q..2q+1], q < n.  HOST arrays;
+ * one launch on the current device, which the call waits for.
+ * Errors: INVALID_ARG (null pointer, n < 1 or n > 2^20), NOMEM, CUDA. */
+int vcsgc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
+
 /* Neighbour list of replica 0's lattice: capacity K per site and, for site
  * i, the neighbour indices in out[0..count) (count <= K).  For tests. */
 int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* count);
@@ -293,11 +313,14 @@ int vcsgc_neighbours(void* ctx, int64_t i, int32_t* out, int32_t cap, int32_t* c
  * framework's caching allocator holds nearly all device memory, or code with
  * a fixed memory budget.  It builds the same cell-binned full list as a
  * context does for explicit positions.
- *   In:  n positions as DEVICE arrays d_x, d_y, d_z (doubles, inside the
- *        periodic box box[0..2], a HOST array), list radius rl (Angstrom).
+ *   In:  n positions as DEVICE arrays d_x, d_y, d_z (doubles; a position
+ *        outside the periodic box box[0..2], a HOST array, is taken at its
+ *        periodic image inside), list radius rl (Angstrom).
  *   Out: DEVICE arrays owned by the caller: d_nbr[n][K] (int32, row i lists
- *        the atoms within rl of atom i under the minimum image, cell order,
- *        -1 padded) and d_cnt[n] (row lengths).
+ *        every atom within rl of atom i under the minimum image, and may
+ *        also list atoms up to rl + 0.01 A + 1e-6 max(box) away, the margin
+ *        of the list's FP32 distance test; cell order, -1 padded) and
+ *        d_cnt[n] (row lengths).
  * Work runs on `stream` (NULL: legacy default stream); the call waits for it.
  * Its working space is one static device array of about 6 MB that every
  * GPU loading this library holds until the process exits.  The first call on

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvcsgc.so")
 SOURCES = ["kernels_mc.cu", "kernels_lattice.cu", "kernels_nbr.cu", "kernels_md.cu", "kernels_mlp.cu",
-           "vcsgc_capi.cu", "vcsgc_mlp.cu", "vcsgc_noalloc.cu", "kernels_multi.cu", "vcsgc_multi_capi.cu"]
+           "vcsgc_capi.cu", "vcsgc_mlp.cu", "vcsgc_noalloc.cu", "kernels_multi.cu", "vcsgc_multi_capi.cu",
+           "vcsgc_util.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -67,18 +68,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
-
-
-def build_alu_peaks() -> str:
-    """Compile the standalone ALU throughput probe (csrc/alu_peaks.cu)."""
-    os.makedirs(BUILD, exist_ok=True)
-    exe = os.path.join(BUILD, "alu_peaks")
-    src = os.path.join(CSRC, "alu_peaks.cu")
-    if not os.path.exists(exe) or os.path.getmtime(exe) < os.path.getmtime(src):
-        r = subprocess.run([_nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", exe], capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on alu_peaks.cu:\n{r.stderr}")
-    return exe
 
 
 if __name__ == "__main__":

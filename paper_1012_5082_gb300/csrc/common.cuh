@@ -227,8 +227,10 @@ constexpr uint64_t U53_NEAR_ONE = (uint64_t)((1.0 - 1e-9) * 9007199254740992.0);
 // factor exp(+-dx) of exp(-X); the relative margin dx + dx^2 covers
 // exp(dx) - 1 for dx <= 1 (the second-order term matters once dx exceeds
 // about 1e-3, as in the re-embedding screens), 2^-20 the expf bound and the
-// float products.
+// float products.  Past dx = 0.5 (steep tables at low T) the screen leaves
+// every decision to FP64: dx + dx^2 stops covering exp(dx) - 1 near 1.79.
 __device__ __forceinline__ int screen32(float x32, float dx, uint64_t u53) {
+  if (!(dx <= 0.5f)) return -1;
   if (x32 <= -2.0f * dx) return 1;
   if (u53 == 0) return -1;
   if (x32 >= 80.0f + dx) return 0;

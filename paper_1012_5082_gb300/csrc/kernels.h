@@ -53,6 +53,12 @@ struct CellList {
   int* cell_cursor;// [ncell]
   int* sorted;     // [N]
 };
+// Distance margin of the list's FP32 criterion: rows hold every pair within
+// rl and may hold pairs up to rl + cell_list_margin(box).
+inline double cell_list_margin(const double box[3]) {
+  const double L = box[0] > box[1] ? (box[0] > box[2] ? box[0] : box[2]) : (box[1] > box[2] ? box[1] : box[2]);
+  return 0.01 + 1e-6 * L;
+}
 void launch_cell_neighbours(long long N, const double* x, const double* y, const double* z,
                             const double box[3], double rl, CellList cl, int K, int* nbr, int* cnt,
                             unsigned* err, cudaStream_t st);

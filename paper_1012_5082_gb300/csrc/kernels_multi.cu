@@ -675,7 +675,8 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit(MultiArgs a) {
 // there, and the new species with its embedding value.  Accepts of one step
 // are more than 2 r_c apart: no two threads touch a common site, and no
 // neighbour's species changes.  Every block sums the replicas' item counts
-// (at most MK_SCREEN_MAX_R replicas).
+// (at most MK_SCREEN_MAX_R replicas; the host selects this form only while
+// R D (MK_BCC5_N + 1) < 2^31, so the int item index cannot overflow).
 __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
   // the next step's propose may start its draws now; it reads what this
   // launch writes only after griddepcontrol.wait

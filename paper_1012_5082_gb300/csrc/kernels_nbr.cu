@@ -150,9 +150,16 @@ void launch_lattice_neighbours(int nx, int ny, int nz, const int3* hoff, int K, 
 }
 
 // ------------------------------------------------------ cell neighbours
-__device__ __forceinline__ int cell_index(double v, double L, int n) {
-  int c = (int)floor(v / L * n);
-  return c < 0 ? 0 : (c >= n ? n - 1 : c);
+// periodic image of v in [0, L): positions outside the box (a caller's, or
+// one rounding step past an edge) are binned where their image lies
+__device__ __forceinline__ double wrap_into(double v, double L) {
+  const double w = v - L * floor(v / L);
+  return w < L ? w : 0.0;  // v a hair below a multiple of L rounds up to L
+}
+
+__device__ __forceinline__ int cell_index(double w, double L, int n) {
+  const int c = (int)(w / L * n);
+  return c < n ? c : n - 1;
 }
 
 __global__ void k_cell_assign(long long N, const double* x, const double* y, const double* z,
@@ -160,12 +167,13 @@ __global__ void k_cell_assign(long long N, const double* x, const double* y, con
                               int* cell_of, int* count, float* x32, float* y32, float* z32) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int c = (cell_index(z[i], bz, nz) * ny + cell_index(y[i], by, ny)) * nx + cell_index(x[i], bx, nx);
+  const double wx = wrap_into(x[i], bx), wy = wrap_into(y[i], by), wz = wrap_into(z[i], bz);
+  const int c = (cell_index(wz, bz, nz) * ny + cell_index(wy, by, ny)) * nx + cell_index(wx, bx, nx);
   cell_of[i] = c;
   atomicAdd(&count[c], 1);
-  x32[i] = (float)x[i];
-  y32[i] = (float)y[i];
-  z32[i] = (float)z[i];
+  x32[i] = (float)wx;
+  y32[i] = (float)wy;
+  z32[i] = (float)wz;
 }
 
 // exclusive scan of count[0..n) into start[0..n], one block
@@ -228,9 +236,11 @@ __global__ void k_cell_sort(int ncell, const int* start, int* sorted) {
   }
 }
 
-// Candidates are tested in FP32 against (rl + 0.01 A)^2: positions below
-// 10^3 A carry < 1e-4 A of rounding, so every pair within rl is listed; the
-// few extra pairs beyond rl are skipped where the list is used (r >= r_c).
+// Candidates are tested in FP32 against (rl + m)^2, m = 0.01 A + 1e-6 L_max:
+// the wrapped coordinates lie in [0, L), so the FP32 minimum-image distance
+// is within about 7 L 2^-24 < 1e-6 L of the exact one, and every pair within
+// rl is listed; the few extra pairs in [rl, rl + m) are skipped where the
+// list is used (r >= r_c).
 __global__ void k_cell_nbr(long long N, const float* x, const float* y, const float* z, float bx,
                            float by, float bz, int nx, int ny, int nz, const int* cell_of,
                            const int* start, const int* sorted, float rl2, int K, int* nbr, int* cnt,
@@ -278,7 +288,7 @@ void launch_cell_neighbours(long long N, const double* x, const double* y, const
   k_scan<<<1, 1024, 0, st>>>(cl.cell_count, ncell, cl.cell_start);
   k_cell_scatter<<<g, 128, 0, st>>>(N, cl.cell_of, cl.cell_start, cl.cell_cursor, cl.sorted);
   k_cell_sort<<<(ncell + 127) / 128, 128, 0, st>>>(ncell, cl.cell_start, cl.sorted);
-  const float rlm = (float)rl + 0.01f;
+  const float rlm = (float)(rl + cell_list_margin(box));
   k_cell_nbr<<<g, 128, 0, st>>>(N, cl.x32, cl.y32, cl.z32, (float)box[0], (float)box[1], (float)box[2],
                                 cl.nc[0], cl.nc[1], cl.nc[2], cl.cell_of, cl.cell_start, cl.sorted,
                                 rlm * rlm, K, nbr, cnt, err);

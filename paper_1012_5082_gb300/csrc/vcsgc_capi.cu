@@ -1748,6 +1748,28 @@ int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
   return check_device_error(c);
 }
 
+int vcsgc_set_launch(void* ctx, int32_t form, int32_t block, int32_t prefetch) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return VCSGC_ERR_INVALID_ARG;
+  if (form != 0 || (block != 64 && block != 128 && block != 256) || (prefetch != 0 && prefetch != 1))
+    return fail(c, VCSGC_ERR_INVALID_ARG, "launch shape: form 0 with block 64, 128 or 256 and prefetch 0 or 1");
+  if (!c->fast) return fail(c, VCSGC_ERR_STATE, "launch shape: the context is not in the fused form");
+  c->lat.block = block;
+  c->lat.prefetch = prefetch;
+  select_blk(c);
+  drop_graph(c);
+  return VCSGC_OK;
+}
+
+int vcsgc_get_launch(void* ctx, int32_t* form, int32_t* block, int32_t* prefetch) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c) return VCSGC_ERR_INVALID_ARG;
+  if (form) *form = 0;
+  if (block) *block = c->fast ? c->lat.block : MC_BLOCK;
+  if (prefetch) *prefetch = c->fast ? c->lat.prefetch : 0;
+  return VCSGC_OK;
+}
+
 const char* vcsgc_last_error(void* ctx) {
   if (!ctx) return g_init_error.c_str();
   return static_cast<Ctx*>(ctx)->err.c_str();

@@ -423,7 +423,10 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
   a.base = m->d_base;
   a.qscale32 = (float)a.qscale;
   // screened form (re-embedding, five-shell table)
-  a.screen = (a.reembed && a.bcc5 && R <= MK_SCREEN_MAX_R) ? 1 : 0;
+  // its commit indexes (accept, neighbour) items of all replicas in int:
+  // every replica accepting every trial must stay below 2^31 items
+  const bool items_fit = (long long)R * a.D * (MK_BCC5_N + 1) < (1LL << 31);
+  a.screen = (a.reembed && a.bcc5 && R <= MK_SCREEN_MAX_R && items_fit) ? 1 : 0;
   if (a.screen) MTRY(screen_setup(m, hFd));
   MCK(cudaMemsetAsync(a.rs, 0, sizeof(MRepState) * R, m->st));
   m->h_rp.resize(R);

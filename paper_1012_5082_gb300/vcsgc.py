@@ -75,7 +75,8 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_multi_steps", "vcsgc_multi_steps_per_sweep", "vcsgc_multi_observables",
            "vcsgc_multi_get_types", "vcsgc_multi_set_types", "vcsgc_multi_delta_e", "vcsgc_multi_energy",
            "vcsgc_multi_last_error", "vcsgc_multi_free", "vcsgc_set_ensemble", "vcsgc_md_state",
-           "vcsgc_minimize", "vcsgc_save", "vcsgc_load"]
+           "vcsgc_minimize", "vcsgc_save", "vcsgc_load", "vcsgc_set_launch", "vcsgc_get_launch",
+           "vcsgc_philox"]
 
 
 def lib():
@@ -141,6 +142,9 @@ def lib():
             "vcsgc_multi_energy": (I32, [P, I32, P]),
             "vcsgc_multi_last_error": (C.c_char_p, [P]),
             "vcsgc_multi_free": (None, [P]),
+            "vcsgc_set_launch": (I32, [P, I32, I32, I32]),
+            "vcsgc_get_launch": (I32, [P, P, P, P]),
+            "vcsgc_philox": (I32, [P, P, P, I64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -206,6 +210,17 @@ def vcsgc_neighbour_list_noalloc(n, d_x, d_y, d_z, box, rl, K, d_nbr, d_cnt, str
                                               C.c_void_p(d_z), b, float(rl), int(K),
                                               C.c_void_p(d_nbr), C.c_void_p(d_cnt),
                                               C.c_void_p(stream) if stream else None)
+
+
+def vcsgc_philox(ctr, key):
+    """Philox4x32-10 words of the device generator: ctr [n, 4] and key [n, 2]
+    uint32 in, [n, 4] uint32 out."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    assert c.shape[0] == k.shape[0]
+    out = np.zeros_like(c)
+    _check(lib().vcsgc_philox(_ptr(c), _ptr(k), _ptr(out), c.shape[0]))
+    return out
 
 
 def vcsgc_features(ctx, d_X, d_Y):
@@ -537,6 +552,15 @@ class Context:
         a, b = C.c_double(), C.c_double()
         _check(lib().vcsgc_profile_steps(self.h, int(n), C.byref(a), C.byref(b)), self.h)
         return a.value, b.value
+
+    def set_launch(self, form=0, block=128, prefetch=1):
+        """Launch shape of the fused colour step (vcsgc_set_launch)."""
+        _check(lib().vcsgc_set_launch(self.h, int(form), int(block), int(prefetch)), self.h)
+
+    def get_launch(self):
+        f, b, p = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().vcsgc_get_launch(self.h, C.byref(f), C.byref(b), C.byref(p)), self.h)
+        return f.value, b.value, p.value
 
     def autotune(self, steps=64):
         """Pick the fused colour step's block size by timing (real steps)."""

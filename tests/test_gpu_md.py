@@ -115,17 +115,29 @@ def test_hybrid_cycles_match(V):
     g = V.Context(lat, t, tab, -3.0, 50.0, T, seed=42, c0=0.05, schedule=V.SCHED_SPATIAL,
                   sched=(2, 2, 2, 2, 2, 2), dt=2.0, gamma=0.01, T_md=T, md_seed=99)
     g.set_velocities(v)
+    ties, flips0 = 0, 0
     for _ in range(4):
+        t0 = orc.obs()["near_ties"]
         g.hybrid(1, 5, 150)
         orc.hybrid_cycles(1, 5, 150)
-        if orc.obs()["near_ties"]:
-            break
-        assert np.array_equal(g.types(), orc.types)
-    og, oo = g.observables(), orc.obs()
-    if oo["near_ties"] == 0:
-        assert og["flips"] == oo["flips"] and og["flips"] > 0
         xo, xg = orc.md_state(), g.md_state()
-        assert np.max(np.abs(xg[3] - xo[3])) < 1e-8
+        if not np.array_equal(g.types(), orc.types):
+            # only a near tie decided differently by the host's and the
+            # device's exp may split the chains: re-sync species and
+            # velocities (a flip rescales its atom's velocity) and go on
+            assert orc.obs()["near_ties"] > t0, "species differ without a flagged tie"
+            ties += 1
+            g.set_types(orc.types)
+            g.set_velocities(xo[3:6])
+            flips0 = None
+        else:
+            assert np.max(np.abs(xg[0] - xo[0])) < 1e-8
+            assert np.max(np.abs(xg[3] - xo[3])) < 1e-8
+    assert ties <= 1
+    og, oo = g.observables(), orc.obs()
+    assert oo["flips"] > 0
+    if flips0 is not None:
+        assert og["flips"] == oo["flips"]
     g.close()
 
 

@@ -18,6 +18,26 @@ SHELL_Z = np.array([8, 6, 12, 24, 8])
 
 
 # ----------------------------------------------------------------- Philox
+# Known-answer values of Philox4x32-10 published with the generator (Salmon,
+# Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11;
+# the Random123 distribution's known-answer set): (counter, key) -> output.
+PHILOX_KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,want", PHILOX_KAT)
+def test_philox_known_answers(ctr, key, want):
+    """The oracle's generator reproduces the published known-answer vectors
+    (a wrong round constant, multiplier, key schedule or word order fails)."""
+    assert tuple(int(w) for w in O.philox(ctr, key)) == want
+
+
 def test_philox_uniformity_and_independence():
     """Statistical pins of the counter-based generator: uniform u01 (chi^2 over
     64 bins), no lag-1 correlation, balanced bits, distinct outputs for

@@ -92,12 +92,14 @@ def test_fp32_embedding_error_within_bound(K, ds):
     assert 118 * E < 0.01 * I.KB_EV * 1200.0
 
 
-def _screen(x32, dx, u53, second_order=True):
+def _screen(x32, dx, u53, second_order=True, guard=True):
     """The FP32 screen's rule restated in numpy (float32 arithmetic):
     accept, reject or -1 (undecided) for u = u53 2^-53 against exp(-X),
-    given x32 within dx of X."""
+    given x32 within dx of X.  guard: no decision past dx = 0.5."""
     f = np.float32
     x32, dx = f(x32), f(dx)
+    if guard and not dx <= f(0.5):
+        return -1
     if x32 <= f(-2.0) * dx:
         return 1
     if u53 == 0:
@@ -133,3 +135,23 @@ def test_screen_margin_covers_the_second_order_term():
             wrong[so] += d >= 0 and d != truth
     assert wrong[True] == 0
     assert wrong[False] > 1000
+
+
+def test_screen_leaves_large_bounds_to_fp64():
+    """For dx beyond 1.79, 1 + dx + dx^2 < e^dx: without the dx <= 0.5 guard
+    the rule rejects moves the FP64 test accepts (x32 at X + dx, u just
+    below exp(-X)); with it, no bound from 1e-4 to 3 decides wrongly."""
+    rng = np.random.default_rng(12)
+    wrong = {True: 0, False: 0}
+    for _ in range(20000):
+        X = rng.uniform(0.05, 10.0)
+        dx = 10 ** rng.uniform(-4, np.log10(3.0))
+        p = np.exp(-X)
+        u53 = int(p * rng.uniform(0.3, 1.0) * 2 ** 53)
+        truth = 1 if u53 * 2.0 ** -53 < p else 0
+        for g in (True, False):
+            for side in (0.999, -0.999):
+                d = _screen(X + side * dx, dx, u53, True, guard=g)
+                wrong[g] += d >= 0 and d != truth
+    assert wrong[True] == 0
+    assert wrong[False] > 100
