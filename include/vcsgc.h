@@ -214,11 +214,13 @@ int vcsgc_batch_init(void** ctx, int32_t n_rep, const int32_t* cells, double a, 
                      const double* T, const vcsgc_options* opt);
 
 /* Pick the launch shape of the fused colour step by timing `steps` colour
- * steps with each candidate (these are real steps of the chain): thread-
- * block size 64, 128 or 256, each with and without loading the trial's
- * neighbour rows ahead of the block barrier (shorter dependent chain, more
- * registers).  The fastest is kept for later launches; *best_block receives
- * its block size.  A context outside the fused form reports its fixed block
+ * steps with each candidate (these are real steps of the chain): form 0
+ * with thread-block size 64, 128 or 256, each with and without loading the
+ * trial's neighbour rows ahead of the block barrier (shorter dependent
+ * chain, more registers), and form 1 with every cluster size the lattices
+ * allow at 256 and 512 threads (see vcsgc_set_launch).  The fastest is kept
+ * for later launches (vcsgc_get_launch reports it); *best_block receives its
+ * block size.  A context outside the fused form reports its fixed block
  * size. */
 int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block);
 
@@ -283,17 +285,30 @@ int vcsgc_kinetic_energy(void* ctx, double* out);
  * of the commit kernels.  Same work as vcsgc_steps(n); for profiling. */
 int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_commit);
 
-/* Launch shape of the fused colour step.  form 0: one launch per colour
- * step for every replica, `block` threads per thread block (64, 128 or
- * 256), with (prefetch = 1) or without (0) the trial's neighbour rows loaded
- * ahead of the block barrier.  Any shape advances the same chain (the random
- * numbers are keyed by step and trial, not by thread).  vcsgc_autotune picks
- * one by timing; this call sets one explicitly (tests, profiling).
- * Errors: INVALID_ARG (unknown form or shape), STATE (the context is not in
- * the fused form). */
-int vcsgc_set_launch(void* ctx, int32_t form, int32_t block, int32_t prefetch);
+/* Launch shape of the fused colour step.  Any shape advances the same chain
+ * (the random numbers are keyed by step and trial, not by thread).
+ *   form 0: one launch per colour step for every replica, `block` threads
+ *           per thread block (64, 128 or 256), variant = 1 loads the
+ *           trial's neighbour rows ahead of the block barrier, 0 does not.
+ *   form 1: cluster-resident: one launch runs many colour steps; each
+ *           replica is one thread-block cluster of `variant` CTAs (1, 2, 4,
+ *           8 or 16) of `block` threads (256 or 512) that holds the
+ *           replica's bit-packed species in shared memory, tiled in (y, z)
+ *           with a two-row halo, and separates colour steps by cluster
+ *           barriers (the paper's allgather of dc_i, Sec. III B 2, becomes a
+ *           reduction in the cluster's distributed shared memory).  Needs
+ *           the period-q sublattice schedule, the five-shell BCC table, one
+ *           density function and no surrogate; vcsgc_cluster_sizes lists
+ *           the sizes these lattices allow.
+ * vcsgc_autotune picks a shape by timing; this call sets one explicitly.
+ * Errors: INVALID_ARG (unknown form or shape), STATE (not the fused form,
+ * or a form-1 size these lattices or this GPU do not allow). */
+int vcsgc_set_launch(void* ctx, int32_t form, int32_t block, int32_t variant);
 /* The current launch shape (HOST outputs; any may be NULL). */
-int vcsgc_get_launch(void* ctx, int32_t* form, int32_t* block, int32_t* prefetch);
+int vcsgc_get_launch(void* ctx, int32_t* form, int32_t* block, int32_t* variant);
+/* Cluster sizes of launch form 1 available for this context: bit q of *mask
+ * set for size 2^q (q = 0..4). */
+int vcsgc_cluster_sizes(void* ctx, int32_t* mask);
 
 /* Philox4x32-10 words of the device generator every kernel draws from
  * (Salmon, Moraes, Dror and Shaw, SC'11), for checks against the

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvcsgc.so")
 SOURCES = ["kernels_mc.cu", "kernels_lattice.cu", "kernels_nbr.cu", "kernels_md.cu", "kernels_mlp.cu",
            "vcsgc_capi.cu", "vcsgc_mlp.cu", "vcsgc_noalloc.cu", "kernels_multi.cu", "vcsgc_multi_capi.cu",
-           "vcsgc_util.cu"]
+           "vcsgc_util.cu", "kernels_cluster.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

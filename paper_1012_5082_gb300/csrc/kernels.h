@@ -166,6 +166,34 @@ struct LatArgs {
 };
 
 void launch_lattice_step(const LatArgs& a, int j, bool propose, cudaStream_t st);
+
+// ---- cluster-resident form of the fused step (kernels_cluster.cu)
+// Tiling of one replica's rows over the CTAs of its cluster: TY x TZ tiles
+// (rank = tz TY + ty) of Ty rows by Tz planes (ny = TY Ty, nz = TZ Tz,
+// Ty, Tz >= 2); lcap: accepted-trial list capacity per step (>= the trials
+// of a CTA in a step).
+struct ClTile {
+  int TY, TZ, Ty, Tz, lcap;
+};
+constexpr int CL_TRIALS_PER_THREAD = 8;
+// dynamic shared memory of a tile: rows with halo, one pad word (a trial's
+// second window word may lie one past its row; its bits are never used),
+// the uniforms of a step's trials, two accept lists
+inline size_t cluster_smem_bytes(const ClTile& t, int W) {
+  return sizeof(unsigned long long) * ((size_t)(t.Ty + 4) * (t.Tz + 4) * W + 1 + t.lcap) +
+         sizeof(int) * 2 * (size_t)t.lcap;
+}
+// largest dynamic shared memory a tile may use
+constexpr size_t CL_SMEM_MAX = 200 * 1024;
+// n colour steps from step `base` of every replica (R clusters of `csize`
+// CTAs of `block` threads, block 256 or 512); needs the five-shell table, the
+// sublattice schedule, a uniform dF and no pending commit.  Returns the
+// launch status.
+cudaError_t launch_cluster_steps(const LatArgs& a, const ClTile* d_tiles, size_t smem, int csize, int block,
+                                 long long base, int n, cudaStream_t st);
+// clusters of csize CTAs with `smem` bytes each that can be resident at once
+// (0: the shape cannot launch)
+int cluster_capacity(int csize, int block, size_t smem);
 // true when the rows and masks of a equal the compile-time five-shell table
 bool lattice_rows_bcc5(const LatArgs& a);
 // B count and energy of replicas r0 .. r0 + nrep - 1 from their packed

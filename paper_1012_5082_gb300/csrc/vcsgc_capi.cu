@@ -3,6 +3,7 @@
 // graph-captured colour-step loop, the MD driver and the observables.
 // Every numerical step of the method runs in the kernels of kernels_*.cu.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -142,7 +143,28 @@ struct Ctx {
   // fused form: block tables for blocks of 64, 128, 256 threads
   int2* blk_tab[3] = {nullptr, nullptr, nullptr};
   int n_blk_tab[3] = {0, 0, 0};
+  // cluster-resident form (launch form 1): per cluster size 1, 2, 4, 8, 16
+  // the replicas' tilings on the device (null: that size cannot serve every
+  // replica) and the shared memory a CTA needs
+  int form = 0;
+  int cl_size = 0, cl_block = 512;
+  ClTile* cl_tiles[5] = {};
+  size_t cl_smem[5] = {};
+  int cl_lcap[5] = {};             // most trials of one CTA in one step
+  long long base_lag = 0;          // steps run in form 1 not yet added to lat.ctl->base_step
 };
+
+// index of a cluster size in Ctx::cl_tiles (-1: not a supported size)
+int cl_index(int csize) {
+  switch (csize) {
+    case 1: return 0;
+    case 2: return 1;
+    case 4: return 2;
+    case 8: return 3;
+    case 16: return 4;
+    default: return -1;
+  }
+}
 
 // point the fused step at the block table of its block size
 void select_blk(Ctx* c) {
@@ -704,7 +726,41 @@ int sync_state_from_types(Ctx* c, int r, const uint8_t* host_types) {
   return VCSGC_OK;
 }
 
+// bring the device step base (and the colour table of the per-step launch)
+// up to the host's after steps run in the cluster-resident form
+int sync_base(Ctx* c) {
+  if (c->base_lag == 0) return VCSGC_OK;
+  launch_lattice_advance(c->lat, (int)c->base_lag, c->st);
+  CK(cudaGetLastError());
+  c->base_lag = 0;
+  return VCSGC_OK;
+}
+
+bool cluster_form_usable(const Ctx* c) {
+  const int q = cl_index(c->cl_size);
+  return c->form == 1 && q >= 0 && c->cl_tiles[q] && !c->lat.da;
+}
+
+// n colour steps in the cluster-resident form: any pending commit of the
+// per-step form first, then one persistent launch per chunk of steps
+int run_steps_cluster(Ctx* c, long long n) {
+  TRY(flush(c));
+  const int q = cl_index(c->cl_size);
+  const long long chunk = 1LL << 20;
+  while (n > 0) {
+    const int m = (int)std::min(n, chunk);
+    CK(launch_cluster_steps(c->lat, c->cl_tiles[q], c->cl_smem[q], c->cl_size, c->cl_block, c->h_base, m, c->st));
+    c->h_base += m;
+    c->base_lag += m;
+    n -= m;
+  }
+  c->pending = false;
+  return VCSGC_OK;
+}
+
 int run_steps_fast(Ctx* c, long long n) {
+  if (cluster_form_usable(c)) return run_steps_cluster(c, n);
+  TRY(sync_base(c));
   const int G = 64;
   if (n >= G && !c->graph) {
     cudaGraph_t g;
@@ -987,6 +1043,7 @@ int vcsgc_default_options(vcsgc_options* o) {
 }
 
 static int setup_fast(Ctx* c, const std::vector<RepState>& hs);
+static int cluster_setup(Ctx* c);
 
 static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_eam_tables* E,
                      double phi, double kappa, double T, const vcsgc_options* o) {
@@ -1495,7 +1552,61 @@ static int lattice_state(Ctx* c, const std::vector<long long>& n0, const std::ve
   c->h_base = 0;
   c->pending = false;
   drop_graph(c);
+  TRY(cluster_setup(c));
   return check_device_error(c);
+}
+
+// Tilings of the cluster-resident form.  For each cluster size s in 1, 2,
+// 4, 8, 16 every replica needs a TY x TZ = s grid of tiles dividing its
+// ny x nz rows with Ty, Tz >= 2, whose rows with halo, (Ty + 4)(Tz + 4) W
+// words, and accept lists fit in shared memory, and whose trials per step
+// fit the threads; among such grids the one with whole sublattice periods
+// per tile (equal trials per CTA) and the squarest tile is taken.  Sizes
+// the GPU cannot co-schedule (cudaOccupancyMaxActiveClusters = 0) are
+// dropped.
+static int cluster_setup(Ctx* c) {
+  const LatArgs& l = c->lat;
+  if (!l.sublattice || !l.bcc5 || !l.df_uniform || l.n_shells != 5) return VCSGC_OK;
+  const int sizes[5] = {1, 2, 4, 8, 16};
+  for (int qi = 0; qi < 5; ++qi) {
+    const int s = sizes[qi];
+    std::vector<ClTile> tiles;
+    size_t smem = 0;
+    bool ok = true;
+    for (int r = 0; r < c->R && ok; ++r) {
+      const LatGeom& g = c->h_geom[r];
+      ClTile best{};
+      bool found = false;
+      long long best_score = 0;
+      for (int TY = 1; TY <= s; TY *= 2) {
+        const int TZ = s / TY;
+        if (g.ny % TY || g.nz % TZ) continue;
+        const int Ty = g.ny / TY, Tz = g.nz / TZ;
+        if (Ty < 2 || Tz < 2) continue;
+        ClTile t{TY, TZ, Ty, Tz, 0};
+        t.lcap = ((Ty + l.qy - 1) / l.qy) * ((Tz + l.qz - 1) / l.qz) * g.nxq;
+        if (t.lcap > 512 * CL_TRIALS_PER_THREAD) continue;
+        const size_t sm = cluster_smem_bytes(t, g.W);
+        if (sm > CL_SMEM_MAX) continue;
+        const bool whole = Ty % l.qy == 0 && Tz % l.qz == 0;
+        const long long score = (whole ? 1LL << 40 : 0) - (long long)std::abs(Ty - Tz);
+        if (!found || score > best_score) {
+          found = true;
+          best_score = score;
+          best = t;
+        }
+      }
+      if (!found) ok = false;
+      tiles.push_back(best);
+      smem = std::max(smem, cluster_smem_bytes(best, g.W));
+      c->cl_lcap[qi] = std::max(c->cl_lcap[qi], best.lcap);
+    }
+    if (!ok || cluster_capacity(s, 512, smem) < 1) continue;
+    TRY(dalloc(c, &c->cl_tiles[qi], tiles.size()));
+    CK(cudaMemcpyAsync(c->cl_tiles[qi], tiles.data(), sizeof(ClTile) * tiles.size(), cudaMemcpyHostToDevice, c->st));
+    c->cl_smem[qi] = smem;
+  }
+  return VCSGC_OK;
 }
 
 // The fused bit-packed form applies to a rigid lattice with one density
@@ -1711,19 +1822,22 @@ int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
     *best_block = MC_BLOCK;
     return VCSGC_OK;
   }
-  // candidates: block size x row prefetch (prefetching shortens the
-  // dependent chain of a step but costs registers, i.e. resident blocks)
-  const int cand[6][2] = {{64, 1}, {128, 1}, {256, 1}, {64, 0}, {128, 0}, {256, 0}};
+  // candidates (form, block, variant): one launch per colour step with block
+  // size x row prefetch (prefetching shortens the dependent chain of a step
+  // but costs registers, i.e. resident blocks), then the cluster-resident
+  // form with each cluster size that serves these lattices x block size
+  std::vector<std::array<int, 3>> cand = {{0, 64, 1}, {0, 128, 1}, {0, 256, 1}, {0, 64, 0}, {0, 128, 0}, {0, 256, 0}};
+  if (!c->lat.da)
+    for (int s : {1, 2, 4, 8, 16})
+      if (c->cl_tiles[cl_index(s)])
+        for (int b : {256, 512}) cand.push_back({1, b, s});
   float best = 0.0f;
-  int bb = 128, bp = 1;
+  std::array<int, 3> bc = {0, 128, 1};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   for (const auto& cb : cand) {
-    c->lat.block = cb[0];
-    c->lat.prefetch = cb[1];
-    select_blk(c);
-    drop_graph(c);
+    if (vcsgc_set_launch(c, cb[0], cb[1], cb[2]) != VCSGC_OK) continue;
     // one untimed step with the candidate, then the timed ones
     TRY(run_steps_fast(c, 1));
     CK(cudaEventRecord(e0, c->st));
@@ -1734,39 +1848,63 @@ int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
     CK(cudaEventElapsedTime(&ms, e0, e1));
     if (best == 0.0f || ms < best) {
       best = ms;
-      bb = cb[0];
-      bp = cb[1];
+      bc = cb;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->lat.prefetch = bp;
-  c->lat.block = bb;
-  select_blk(c);
-  drop_graph(c);
-  *best_block = bb;
+  c->err.clear();
+  TRY(vcsgc_set_launch(c, bc[0], bc[1], bc[2]));
+  *best_block = bc[1];
   return check_device_error(c);
 }
 
-int vcsgc_set_launch(void* ctx, int32_t form, int32_t block, int32_t prefetch) {
+int vcsgc_set_launch(void* ctx, int32_t form, int32_t block, int32_t variant) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return VCSGC_ERR_INVALID_ARG;
-  if (form != 0 || (block != 64 && block != 128 && block != 256) || (prefetch != 0 && prefetch != 1))
-    return fail(c, VCSGC_ERR_INVALID_ARG, "launch shape: form 0 with block 64, 128 or 256 and prefetch 0 or 1");
+  const bool f0 = form == 0 && (block == 64 || block == 128 || block == 256) && (variant == 0 || variant == 1);
+  const bool f1 = form == 1 && (block == 256 || block == 512) && cl_index(variant) >= 0;
+  if (!f0 && !f1)
+    return fail(c, VCSGC_ERR_INVALID_ARG,
+                "launch shape: form 0 with block 64, 128 or 256 and prefetch 0 or 1, or form 1 with block 256 or "
+                "512 and 1, 2, 4, 8 or 16 CTAs per cluster");
   if (!c->fast) return fail(c, VCSGC_ERR_STATE, "launch shape: the context is not in the fused form");
+  if (f1) {
+    const int q = cl_index(variant);
+    if (!c->cl_tiles[q] || c->cl_lcap[q] > block * CL_TRIALS_PER_THREAD ||
+        (block == 256 && cluster_capacity(variant, 256, c->cl_smem[q]) < 1))
+      return fail(c, VCSGC_ERR_STATE, "launch shape: no cluster-resident form of this size for these lattices");
+    if (c->lat.da) return fail(c, VCSGC_ERR_STATE, "launch shape: the cluster-resident form has no delayed acceptance");
+    c->form = 1;
+    c->cl_size = variant;
+    c->cl_block = block;
+    return VCSGC_OK;
+  }
+  c->form = 0;
   c->lat.block = block;
-  c->lat.prefetch = prefetch;
+  c->lat.prefetch = variant;
   select_blk(c);
   drop_graph(c);
   return VCSGC_OK;
 }
 
-int vcsgc_get_launch(void* ctx, int32_t* form, int32_t* block, int32_t* prefetch) {
+int vcsgc_get_launch(void* ctx, int32_t* form, int32_t* block, int32_t* variant) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return VCSGC_ERR_INVALID_ARG;
-  if (form) *form = 0;
-  if (block) *block = c->fast ? c->lat.block : MC_BLOCK;
-  if (prefetch) *prefetch = c->fast ? c->lat.prefetch : 0;
+  const bool f1 = c->fast && cluster_form_usable(c);
+  if (form) *form = f1 ? 1 : 0;
+  if (block) *block = f1 ? c->cl_block : (c->fast ? c->lat.block : MC_BLOCK);
+  if (variant) *variant = f1 ? c->cl_size : (c->fast ? c->lat.prefetch : 0);
+  return VCSGC_OK;
+}
+
+int vcsgc_cluster_sizes(void* ctx, int32_t* mask) {
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !mask) return VCSGC_ERR_INVALID_ARG;
+  int m = 0;
+  for (int q = 0; q < 5; ++q)
+    if (c->cl_tiles[q]) m |= 1 << q;
+  *mask = m;
   return VCSGC_OK;
 }
 
@@ -2433,6 +2571,7 @@ int vcsgc_load(void* ctx, const char* path) {
   CK(cudaStreamSynchronize(c->st));
   // step base (fused form) first: the species upload writes n at its parity
   c->h_base = h_base;
+  c->base_lag = 0;
   if (c->fast) {
     LatCtl ctl{h_base};
     CK(cudaMemcpyAsync(c->lat.ctl, &ctl, sizeof(LatCtl), cudaMemcpyHostToDevice, c->st));
@@ -2467,6 +2606,25 @@ int vcsgc_load(void* ctx, const char* path) {
 int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_commit) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n < 1 || !ms_propose || !ms_commit) return VCSGC_ERR_INVALID_ARG;
+  if (c->fast && cluster_form_usable(c)) {
+    // one persistent launch of n steps: its whole time is reported as propose
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    TRY(flush(c));
+    CK(cudaEventRecord(e0, c->st));
+    TRY(run_steps_cluster(c, n));
+    CK(cudaEventRecord(e1, c->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_propose = ms;
+    *ms_commit = 0.0;
+    return check_device_error(c);
+  }
+  if (c->fast) TRY(sync_base(c));
   std::vector<cudaEvent_t> ev(2 * n + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   CK(cudaEventRecord(ev[0], c->st));

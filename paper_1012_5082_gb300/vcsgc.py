@@ -76,7 +76,7 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_multi_get_types", "vcsgc_multi_set_types", "vcsgc_multi_delta_e", "vcsgc_multi_energy",
            "vcsgc_multi_last_error", "vcsgc_multi_free", "vcsgc_set_ensemble", "vcsgc_md_state",
            "vcsgc_minimize", "vcsgc_save", "vcsgc_load", "vcsgc_set_launch", "vcsgc_get_launch",
-           "vcsgc_philox"]
+           "vcsgc_philox", "vcsgc_cluster_sizes"]
 
 
 def lib():
@@ -145,6 +145,7 @@ def lib():
             "vcsgc_set_launch": (I32, [P, I32, I32, I32]),
             "vcsgc_get_launch": (I32, [P, P, P, P]),
             "vcsgc_philox": (I32, [P, P, P, I64]),
+            "vcsgc_cluster_sizes": (I32, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -553,9 +554,16 @@ class Context:
         _check(lib().vcsgc_profile_steps(self.h, int(n), C.byref(a), C.byref(b)), self.h)
         return a.value, b.value
 
-    def set_launch(self, form=0, block=128, prefetch=1):
-        """Launch shape of the fused colour step (vcsgc_set_launch)."""
-        _check(lib().vcsgc_set_launch(self.h, int(form), int(block), int(prefetch)), self.h)
+    def set_launch(self, form=0, block=128, variant=1):
+        """Launch shape of the fused colour step (vcsgc_set_launch): form 0
+        with variant = row prefetch, form 1 with variant = CTAs per cluster."""
+        _check(lib().vcsgc_set_launch(self.h, int(form), int(block), int(variant)), self.h)
+
+    def cluster_sizes(self):
+        """Cluster sizes of the cluster-resident form these lattices allow."""
+        m = C.c_int32()
+        _check(lib().vcsgc_cluster_sizes(self.h, C.byref(m)), self.h)
+        return [1 << q for q in range(5) if m.value >> q & 1]
 
     def get_launch(self):
         f, b, p = C.c_int32(), C.c_int32(), C.c_int32()

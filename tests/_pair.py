@@ -69,6 +69,7 @@ class Lockstep:
         self.on_resync = on_resync
         self.resyncs = 0
         self.compared = 0
+        self._synced = [True] * len(self.orcs)  # never re-synced: whole histories equal
         self._prev = [(o.obs(), g.observables(r)) for r, o in enumerate(self.orcs)]
         self._pool = ThreadPoolExecutor(max_workers=min(8, len(self.orcs)))
 
@@ -88,6 +89,7 @@ class Lockstep:
                 if self.on_resync:
                     self.on_resync(r, o)
                 self.resyncs += 1
+                self._synced[r] = False
                 og = self.g.observables(r)
             else:
                 assert oo["n_b"] == og["n_b"], (r, oo["n_b"], og["n_b"])
@@ -97,6 +99,11 @@ class Lockstep:
                     self.compared += 1
             assert abs(oo["energy"] - og["energy"]) <= 1e-9 * max(1.0, abs(oo["energy"])), \
                 (r, oo["energy"], og["energy"])
+            if self._synced[r] and og["steps"]:
+                # <c> over the steps (Sec. II C observables): the same sum of
+                # n / N after every step, up to the summation's rounding
+                assert abs(og["mean_c"] * og["steps"] - oo["sum_c"]) <= 1e-12 * max(1.0, oo["sum_c"]), \
+                    (r, og["mean_c"] * og["steps"], oo["sum_c"])
             self._prev[r] = (oo, og)
         assert self.ties() <= self.max_ties, f"{self.ties()} near ties (at most {self.max_ties} allowed)"
 

@@ -61,8 +61,11 @@ def test_autotune_keeps_the_chain_exact(V):
     b = V.Batch(CELLS, types, tab, PHI, 20.0, T, seed_r=np.array(SEEDS, np.uint64), c0=0.05)
     best = b.autotune(steps=16)
     assert best in (64, 128, 256)
-    # six candidates (3 block sizes x row prefetch on/off), 1 + 16 steps each
-    orcs = _oracles(tab, lats, types, 6 * (1 + 16))
+    # every candidate shape (form 0: 3 block sizes x row prefetch on/off;
+    # form 1: the cluster sizes x 2 block sizes) runs 1 + 16 steps
+    ran = b.observables(0)["steps"]
+    assert ran >= 6 * (1 + 16) and ran % (1 + 16) == 0
+    orcs = _oracles(tab, lats, types, ran)
     for q, o in enumerate(orcs):
         assert np.array_equal(b.types(q), o.types), q
     ls = Lockstep(orcs, b)

@@ -107,7 +107,9 @@ def test_autotune_keeps_the_chain_exact_80cubed(V):
     lat, g, orcs = _pair(V, 80, [1], 1001, [2002])
     steps = 16
     g.autotune(steps)
-    orcs[0].parallel_steps(len(SHAPES) * (1 + steps))
+    ran = g.observables(0)["steps"]  # 1 + 16 steps per candidate shape
+    assert ran >= len(SHAPES) * (1 + steps) and ran % (1 + steps) == 0
+    orcs[0].parallel_steps(ran)
     assert np.array_equal(g.types(0), orcs[0].types)
     ls = Lockstep(orcs, g)
     ls.advance(g.steps_per_sweep)
@@ -123,4 +125,100 @@ def test_set_launch_rejects_bad_shapes(V):
         with pytest.raises(V.VcsgcError) as e:
             g.set_launch(*bad)
         assert e.value.code == -1
+    g.close()
+
+
+# ----------------------------------------- the cluster-resident form (1)
+def _cluster_shapes(g):
+    return [(1, b, s) for s in g.cluster_sizes() for b in (512, 256)]
+
+
+def test_cluster_form_80cubed(V):
+    """The benchmark's lattice in the cluster-resident form: one sweep per
+    (cluster size, block) the lattice allows, replicas 0 and 1, against the
+    oracle after each."""
+    lat, g, orcs = _pair(V, 80, [0, 1], 1001, [2001, 2002])
+    shapes = _cluster_shapes(g)
+    assert (1, 512, 16) in shapes
+    ls = Lockstep(orcs, g)
+    for shape in shapes:
+        g.set_launch(*shape)
+        assert g.get_launch() == shape
+        ls.advance(g.steps_per_sweep)
+    o = [g.observables(r) for r in range(2)]
+    assert o[0]["global_accepts"] > 0 and o[1]["flips"] > 1000, o
+    ls.close()
+    g.close()
+
+
+def test_cluster_form_40cubed_8_replicas(V):
+    """40^3 x 8 replicas: every cluster size from 1 (the whole replica in one
+    CTA) to 16, 12 sweeps, against the oracle after each."""
+    lat, g, orcs = _pair(V, 40, list(range(8)), 1001, [3000 + r for r in range(8)])
+    shapes = _cluster_shapes(g)
+    assert {s for _, _, s in shapes} == {1, 2, 4, 8, 16}
+    ls = Lockstep(orcs, g)
+    for s in range(12):
+        g.set_launch(*shapes[s % len(shapes)])
+        ls.advance(g.steps_per_sweep)
+    assert min(g.observables(r)["flips"] for r in range(8)) > 0
+    ls.close()
+    g.close()
+
+
+def test_cluster_form_uneven_batch(V):
+    """Replicas of different sizes in one launch, tiles of 2 and 3 rows, tiles
+    that are not whole sublattice periods, and (cluster size 1 on 8^3) a tile
+    whose halo wraps onto its own rows: every size, 6 sweeps each in turn."""
+    cells = [(8, 8, 8), (12, 12, 12), (16, 8, 12)]
+    phi, T, seeds = [-2.45, -2.40, -2.50], [700.0, 650.0, 750.0], [11, 12, 13]
+    tab = I.eam_tables()
+    lats = [I.bcc_lattice(*c) for c in cells]
+    types = [I.random_types(l.n, l.n // 20, seed=100 + q) for q, l in enumerate(lats)]
+    b = V.Batch(cells, types, tab, phi, 20.0, T, seed_r=np.array(seeds, np.uint64), c0=0.05)
+    orcs = []
+    for q, l in enumerate(lats):
+        o = O.System(l, types[q], tab)
+        o.set_params(phi[q], 20.0, T[q], c0=0.05, seed=seeds[q])
+        o.schedule_sublattice(l.cells, (4, 4, 4))
+        orcs.append(o)
+    assert b.cluster_sizes() == [1, 2, 4, 8, 16]
+    ls = Lockstep(orcs, b)
+    for s in (1, 2, 4, 8, 16):
+        b.set_launch(1, 512, s)
+        ls.advance(6 * 128)
+    assert min(b.observables(q)["flips"] for q in range(3)) > 0
+    ls.close()
+    b.close()
+
+
+def test_forms_interleave_mid_sweep(V):
+    """The chain passes between the per-step and the cluster-resident forms at
+    arbitrary steps (pending commits, step base and colour table handed over):
+    13, 70, 45 and 128 steps alternating."""
+    lat, g, orcs = _pair(V, 40, [1, 2], 1001, [3001, 3002])
+    ls = Lockstep(orcs, g)
+    for shape, steps in (((0, 128, 1), 13), ((1, 512, 16), 70), ((0, 256, 0), 45), ((1, 256, 4), 128),
+                         ((0, 64, 1), 77)):
+        g.set_launch(*shape)
+        ls.advance(steps)
+    o = g.observables(0)
+    assert o["steps"] == 13 + 70 + 45 + 128 + 77
+    ls.close()
+    g.close()
+
+
+def test_cluster_form_energy_and_observables(V):
+    """After cluster-resident sweeps the tracked energy equals a fresh
+    evaluation, the B count equals the species, and <c> sums are the
+    oracle's."""
+    lat, g, orcs = _pair(V, 40, [3], 1001, [3003])
+    g.set_launch(1, 512, 16)
+    g.sweep(5)
+    orcs[0].parallel_steps(5 * 128)
+    og, oo = g.observables(0), orcs[0].obs()
+    assert np.array_equal(g.types(0), orcs[0].types)
+    assert og["n_b"] == oo["n_b"] == int(g.types(0).sum())
+    assert abs(g.energy(0) - og["energy"]) <= 1e-9 * abs(og["energy"])
+    assert abs(og["mean_c"] * og["steps"] - oo["sum_c"]) <= 1e-9 * oo["sum_c"]
     g.close()
