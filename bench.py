@@ -30,41 +30,89 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1012_5082_gb300 import inputs as I  # noqa: E402
+from paper_1012_5082_gb300 import recipe as RC  # noqa: E402
 
 CELLS = 80
 T_K = 600.0
 KAPPA = 1000.0
 N_PHI = 8
 FRAC_B = 0.02
-# eV: local driving force at which locally accepted A->B and B->A moves of
-# the random 2% start balance (expected dn = 0 per 8,000-trial colour step,
-# solved once from the distribution of dE on that start), so composite moves
-# stay small; phi_j = dmu0 - 2 kappa_p N c0_j (parameter recipe, Sec. III C)
-DMU_S = -2.02
-# Algorithmic integer/FP32 operations of one trial of the fused colour step:
-# two Philox4x32-10 blocks (10 rounds x (2 mul.hi + 2 mul.lo + 4 xor + 2 add)),
-# the site decode (~12), 13 neighbour rows x (row index and address 8,
-# effective-species window 7, 5 shells x (and, popc, add) 15), and the FP32
-# exponent and screen (~30).
-OPS_PER_TRIAL = 2 * 100 + 12 + 13 * 30 + 30
-# INT32/FP32 lanes per SM x SMs x max SM clock (GB300: 128 x 152 x 2.07 GHz)
-ALU_PEAK_OPS = 128 * 152 * 2.07e9
+# Parameter recipe (Sec. III C): dmu0 = dmu_S, the driving force at two-phase
+# coexistence from kappa = 0 SGC runs of a small lattice (both single-phase
+# branches integrated to their crossing), and phi_j = dmu0 - 2 kappa_p N c0_j.
+PRESCAN_GRID = np.round(np.arange(-1.85, -1.2499, 0.05), 4)  # eV, 13 points around the crossing
+PRESCAN_CELLS, PRESCAN_WARMUP, PRESCAN_SWEEPS = 16, 200, 400
+# Algorithmic work of one trial of the fused colour step, by pipe (from the
+# source; the compile-time five-shell table holds 33 non-empty (row, shell)
+# masks, 25 of them with more than one site):
+#   simple integer ops: Philox 60 (4 xor + 2 key adds per round), site decode
+#     15, 13 rows x (two effective-species words 3 + 3, funnel shift 1, row
+#     address 2) 117, one-bit masks 8 x 2, multi-bit masks 25 x (and, add) 50,
+#     own bit 3 -> 261
+#   popc: 25;  32-bit multiply pairs (mul.hi + mul.lo): Philox 20
+#   FP32: the local exponent, its bound and the screen 20;  MUFU: expf 1
+OPS_SIMPLE, OPS_POPC, OPS_MULPAIR, OPS_FP32, OPS_MUFU = 261, 25, 20, 20, 1
+OPS_PER_TRIAL = OPS_SIMPLE + OPS_POPC + 2 * OPS_MULPAIR + OPS_FP32 + OPS_MUFU
+# Per-SM rates measured on GB300 (per clock): INT32 xor+add 120, popc 20.7,
+# multiply pairs 31, FP32 FMA 122, expf 11.3.  Integer ops and popc share
+# the ALU pipe; multiplies, FP32 and MUFU run on other pipes in parallel, so
+# the floor of a trial is the ALU pipe's time (the larger of the two).
+SM_CYCLES_PER_TRIAL = max(OPS_SIMPLE / 120.0 + OPS_POPC / 20.7,
+                          OPS_MULPAIR / 31.0 + OPS_FP32 / 122.0 + OPS_MUFU / 11.3)
+ALU_PEAK_OPS = OPS_PER_TRIAL * 152 * 2.07e9 / SM_CYCLES_PER_TRIAL
+# Nominal HBM bytes of a trial of the gather form over an explicit int32
+# neighbour list (58 x 4 B list, own species 1 B, own rho 8 B, species write
+# 1 B): the kernels here read no list (bit-packed rows resident on chip)
+HBM_BYTES_PER_TRIAL = 242
+# a chain of dependent step-shaped launches with programmatic dependent launch
+STEP_LATENCY_FLOOR_US = 1.29
 METRIC = "VC-SGC trial moves/s"
 
 
-def workload():
+def c0_grid():
+    return 0.02 + np.arange(N_PHI) * 0.48 / 7
+
+
+def workload(dmu0):
+    """The headline lattice, its random 2 % start and the 8 replicas' phi for
+    the driving force dmu0 (eV)."""
     lat = I.bcc_lattice(CELLS, CELLS, CELLS)
     types = I.random_types(lat.n, int(round(FRAC_B * lat.n)), seed=1001)
     tab = I.eam_tables()
-    c0 = 0.02 + np.arange(N_PHI) * 0.48 / 7
-    # phi_j = dmu_S - 2 kappa kB T c0_j: dmu0 = dmu_S for every replica
-    phi = DMU_S - 2.0 * KAPPA * I.KB_EV * T_K * c0
-    return lat, types, tab, phi, c0
+    c0 = c0_grid()
+    return lat, types, tab, RC.phi_grid(dmu0, KAPPA, T_K, c0), c0
+
+
+def prescan(V, stream, local):
+    """Sec. III C (i): dmu_S from kappa = 0 SGC runs of 16^3 lattices started
+    in pure A and pure B at each driving force of PRESCAN_GRID."""
+    t0 = time.perf_counter()
+    c_a, c_b, e_a, e_b = RC.sgc_branches(V, T_K, PRESCAN_GRID, cells=PRESCAN_CELLS, warmup=PRESCAN_WARMUP,
+                                         sweeps=PRESCAN_SWEEPS, stream=stream, device=local)
+    dmu_s = RC.coexistence(PRESCAN_GRID, c_a, c_b, e_a, e_b)
+    return {"dmu_S_eV": dmu_s, "grid_eV": PRESCAN_GRID.tolist(), "c_A_branch": [float(x) for x in c_a],
+            "c_B_branch": [float(x) for x in c_b], "e_A_eV": e_a, "e_B_eV": e_b,
+            "lattice": f"{PRESCAN_CELLS}^3 BCC, kappa 0, T 600 K, {PRESCAN_WARMUP} + {PRESCAN_SWEEPS} sweeps",
+            "seconds": time.perf_counter() - t0}
+
+
+def balanced_dmu(V, stream, local):
+    """The driving force at which the first composite move of the random 2 %
+    start has no expected drift (recipe.balanced_dmu0 on the dE of every
+    site, evaluated by the library)."""
+    lat = I.bcc_lattice(CELLS, CELLS, CELLS)
+    types = I.random_types(lat.n, int(round(FRAC_B * lat.n)), seed=1001)
+    ctx = V.Context(lat, types, I.eam_tables(), -2.0, KAPPA, T_K, schedule=V.SCHED_SUBLATTICE, sched=(4, 4, 4),
+                    stream=stream, device=local)
+    de = ctx.delta_e(np.arange(lat.n))
+    ctx.close()
+    return RC.balanced_dmu0(de, types, T_K)
 
 
 def config_dict(extra=None):
     d = {"workload": f"rigid BCC {CELLS}^3 cells (1,024,000 sites), EAM 5000-pt tables, "
-                     f"2% B, T=600 K, kappa=1000, {N_PHI} phi values as replicas, "
+                     f"2% B, T=600 K, kappa=1000, {N_PHI} phi values as replicas (c0 = 0.02 .. 0.5, "
+                     "phi = dmu0 - 2 kappa kB T c0, dmu0 balanced on the random start), "
                      "period-4 sublattice schedule (8,000 trials per colour step)",
          "sites": 2 * CELLS ** 3, "replicas": N_PHI, "trials_per_step": N_PHI * 2 * CELLS ** 3,
          "l2_policy": "L2 flushed between timed sweeps (a 256 MB write on the stream, outside the timed "
@@ -204,6 +252,53 @@ def md_bench(V, torch, stream, local, steps=20, warmup=3, box=250.0, precision=0
             "generate_s": gen_s}
 
 
+def mc_explicit_bench(V, torch, stream, local, dmu0, steps=256, warmup=16, box=250.0):
+    """The MC phase of the hybrid scheme (Sec. IV A) alone: colour steps of the
+    general per-pair form on the explicit positions of the 25 nm nanocrystal
+    (1% B, T = 700 K, kappa = 1000, SPATIAL boxes of more than 2 r_c in 2 x 2
+    x 2 colours, one trial per box per step), FP64 and mixed precision, with
+    the mixed form's dE error against the FP64 form on the same state."""
+    lat = I.nanocrystal(box, 16, seed=1002)
+    types = I.random_types(lat.n, int(round(0.01 * lat.n)), seed=1003)
+    tab = I.eam_tables()
+    nb = 2 * int(box // 22.0)
+    phi = float(RC.phi_grid(dmu0, KAPPA, 700.0, 0.01))
+    out = {"workload": f"nanocrystal 25 nm ({lat.n} atoms), 1% B, 700 K, kappa 1000, {nb}^3 boxes in 8 colours"}
+    hbm, src = measured_peak_hbm()
+    ctxs = {}
+    for name, prec in (("fp64", V.PREC_FP64), ("mixed", V.PREC_MIXED)):
+        ctx = V.Context(lat, types, tab, phi, KAPPA, 700.0, c0=0.01, schedule=V.SCHED_SPATIAL,
+                        sched=(nb, nb, nb, 2, 2, 2), stream=stream, device=local, precision=prec)
+        ctx.steps(warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        o0 = ctx.observables()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.steps(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        o1 = ctx.observables()
+        trials = o1["trials"] - o0["trials"]
+        v = trials / (ms * 1e-3)
+        out[name] = {"trial_moves_per_s": v, "us_per_step": ms * 1e3 / steps, "trials_per_step": trials // steps,
+                     "acc_local": (o1["local_accepts"] - o0["local_accepts"]) / max(1, trials),
+                     "hbm_nominal": {"bytes_per_trial": HBM_BYTES_PER_TRIAL, "frac": HBM_BYTES_PER_TRIAL * v / 1e9 / hbm,
+                                     "peak_gbs": hbm, "peak_source": src}}
+        ctxs[name] = ctx
+    t = ctxs["fp64"].types()
+    ctxs["mixed"].set_types(t)
+    sites = np.random.default_rng(8).choice(lat.n, 20000, replace=False)
+    err = np.abs(ctxs["mixed"].delta_e(sites) - ctxs["fp64"].delta_e(sites))
+    out["mixed_dE_error_vs_fp64"] = {"max_eV": float(err.max()), "rms_eV": float(np.sqrt(np.mean(err ** 2))),
+                                     "sampled_sites": int(len(sites))}
+    out["speedup_mixed_vs_fp64"] = out["mixed"]["trial_moves_per_s"] / out["fp64"]["trial_moves_per_s"]
+    for ctx in ctxs.values():
+        ctx.close()
+    return out
+
+
 def ensemble_bench(V, torch, stream, local, steps=20, box=250.0, cg_iters=100):
     """The paper's MD ensemble (Sec. IV B) on the 25 nm nanocrystal: CG
     pre-relaxation (Polak-Ribiere, a fixed budget of iterations), then
@@ -250,7 +345,7 @@ def ensemble_bench(V, torch, stream, local, steps=20, box=250.0, cg_iters=100):
     return out
 
 
-def mixed_bench(V, torch, stream, local, sweeps=40, warmup=3):
+def mixed_bench(V, torch, stream, local, dmu0, sweeps=40, warmup=3):
     """The mixed-precision form on the 128^3 rigid lattice (4,194,304 sites) x
     8 phi replicas, timed beside the FP64 form on the same workload, with the
     error of the mixed form: per-trial dE (max, rms) over sampled sites on the
@@ -259,8 +354,8 @@ def mixed_bench(V, torch, stream, local, sweeps=40, warmup=3):
     lat = I.bcc_lattice(cells, cells, cells)
     types = I.random_types(lat.n, int(round(FRAC_B * lat.n)), seed=1003)
     tab = I.eam_tables()
-    c0 = 0.02 + np.arange(N_PHI) * 0.48 / 7
-    phi = DMU_S - 2.0 * KAPPA * I.KB_EV * T_K * c0
+    c0 = c0_grid()
+    phi = RC.phi_grid(dmu0, KAPPA, T_K, c0)
     seeds = np.arange(N_PHI, dtype=np.uint64) + np.uint64(4001)
     out = {"workload": f"rigid BCC {cells}^3 cells ({lat.n} sites) x {N_PHI} phi replicas, "
                        "period-4 sublattice, T=600 K, kappa=1000"}
@@ -295,7 +390,7 @@ def mixed_bench(V, torch, stream, local, sweeps=40, warmup=3):
     return out
 
 
-def c4_grid():
+def c4_grid(dmu0):
     """(phi, T, c0) of the 64 replicas: 8 temperatures in 500-900 K x 8
     concentrations c0 = 0.02 .. 0.5 with the same local driving force."""
     phi, T, c0 = [], [], []
@@ -304,18 +399,18 @@ def c4_grid():
         c0r = 0.02 + (r % 8) * 0.48 / 7
         T.append(Tr)
         c0.append(c0r)
-        phi.append(DMU_S - 2.0 * KAPPA * I.KB_EV * Tr * c0r)
+        phi.append(float(RC.phi_grid(dmu0, KAPPA, Tr, c0r)))
     return phi, T, c0
 
 
-def c4_batch(V, stream, local, tab):
+def c4_batch(V, stream, local, tab, dmu0):
     cells, types = [], []
     for r in range(64):
         L = 24 + 4 * (r % 7)
         n = 2 * L ** 3
         cells.append((L, L, L))
         types.append(I.random_types(n, int(round(FRAC_B * n)), seed=3000 + r))
-    phi, T, c0 = c4_grid()
+    phi, T, c0 = c4_grid(dmu0)
     return V.Batch(cells, types, tab, phi, KAPPA, T, c0_r=c0,
                    seed_r=np.arange(64, dtype=np.uint64) + np.uint64(3000), stream=stream, device=local)
 
@@ -349,7 +444,7 @@ def timed_sweeps(torch, stream, b, sweeps, flush=None):
     return sum(a.elapsed_time(z) for a, z in ev)
 
 
-def batch_bench(V, torch, stream, local, sweeps=30, warmup=3, surrogate=True):
+def batch_bench(V, torch, stream, local, dmu0, sweeps=30, warmup=3, surrogate=True):
     """64 replicas of rigid BCC of uneven sizes (L = 24 + 4 (r mod 7) cells,
     27,648 to 221,184 sites) at 8 temperatures in 500-900 K x 8 phi values,
     kappa = 1000, advanced together by one fused launch per colour step
@@ -357,7 +452,7 @@ def batch_bench(V, torch, stream, local, sweeps=30, warmup=3, surrogate=True):
     surrogate: the same run with delayed acceptance by a network trained on
     the sampler's own dE."""
     tab = I.eam_tables()
-    b = c4_batch(V, stream, local, tab)
+    b = c4_batch(V, stream, local, tab, dmu0)
     best = b.autotune(steps=64)
     b.sweep(warmup)
     ms = timed_sweeps(torch, stream, b, sweeps)
@@ -370,17 +465,18 @@ def batch_bench(V, torch, stream, local, sweeps=30, warmup=3, surrogate=True):
            "acc_local_sample": [obs[r]["acc_local"] for r in (0, 31, 63)],
            "workload": "64 replicas, L = 24..48 cells, T 500-900 K x 8 phi, kappa 1000, FP64"}
     if surrogate:
-        out["delayed_acceptance"] = surrogate_bench(V, torch, stream, local, tab, sweeps, warmup, out["value"], obs)
+        out["delayed_acceptance"] = surrogate_bench(V, torch, stream, local, tab, dmu0, sweeps, warmup, out["value"],
+                                                    obs)
     return out
 
 
-def surrogate_bench(V, torch, stream, local, tab, sweeps, warmup, plain_value, plain_obs,
+def surrogate_bench(V, torch, stream, local, tab, dmu0, sweeps, warmup, plain_value, plain_obs,
                     n_samples=10_000_000, train_steps=5000, batch=4096, lr=2e-3):
     """Form (4): (descriptor, dE) samples drawn by the sampler itself on 12^3
     replicas of the 10^3 parity workload's EAM at the 64 (phi, T) points,
     training by the GPU kernels, then the 64-replica batch with the network
     as stage 1 of delayed acceptance."""
-    phi, T, c0 = c4_grid()
+    phi, T, c0 = c4_grid(dmu0)
     lat = I.bcc_lattice(12, 12, 12)
     types = [I.random_types(lat.n, int(round(c * lat.n)), seed=5000 + r) for r, c in enumerate(c0)]
     gen = V.Batch([(12, 12, 12)] * 64, types, tab, phi, KAPPA, T, c0_r=c0,
@@ -410,7 +506,7 @@ def surrogate_bench(V, torch, stream, local, tab, sweeps, warmup, plain_value, p
     t_train = time.perf_counter() - t0
     g = s.forward(Xh)
     rmse = float(torch.sqrt(((g - Yh) ** 2).mean()))
-    b = c4_batch(V, stream, local, tab)
+    b = c4_batch(V, stream, local, tab, dmu0)
     b.set_surrogate(s)
     best = b.autotune(steps=64)
     b.sweep(warmup)
@@ -491,7 +587,7 @@ def ising_bench(V, torch, stream, local, sweeps=30, warmup=3):
     return out
 
 
-def overlap_bench(V, torch, stream, local, sweeps=4, warmup=1):
+def overlap_bench(V, torch, stream, local, dmu0, sweeps=4, warmup=1):
     """Overlapping, position-weighted domains (Sec. III A) against the plain
     octants on the same cells of the headline lattice (80^3 x 8 replicas,
     the same phi and c0, 2% B start): cells of 10^3 lattice cells, octants =
@@ -500,7 +596,7 @@ def overlap_bench(V, torch, stream, local, sweeps=4, warmup=1):
     Reports throughput and replica 0's energy per atom after 2, 5, 10 and 20
     sweeps from the supersaturated start (the relaxation the larger trial
     volume is meant to speed up), with the period-4 sublattice beside them."""
-    lat, types, tab, phi, c0 = workload()
+    lat, types, tab, phi, c0 = workload(dmu0)
     seeds = np.arange(N_PHI, dtype=np.uint64) + np.uint64(7001)
     out = {"workload": "80^3 x 8 replicas, headline phi/c0, cells of 10^3 lattice cells"}
     for name, kind, sched in (("octants", V.SCHED_BLOCKS, (5, 5, 5, 2, 2, 2)),
@@ -599,14 +695,17 @@ def aggregate(world: int, units_per_rank: float, seconds: float) -> float:
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle times the same workload."""
+    """--impl reference: the CPU oracle times the same workload (replica 0 of
+    the headline, with the driving force of its own pre-scan)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle as O
 
-    lat, types, tab, phi, c0 = workload()
+    lat, types, tab, _, c0 = workload(0.0)
     s = O.System(lat, types, tab)
+    dmu_bal = RC.balanced_dmu0([s.delta_e(i) for i in range(lat.n)], types, T_K)
+    phi = RC.phi_grid(dmu_bal, KAPPA, T_K, c0)
     s.set_params(float(phi[0]), KAPPA, T_K, c0=float(c0[0]), seed=2001)
     s.schedule_sublattice(lat.cells, (4, 4, 4))
     step_steps = 16  # colour steps per bench step: 128,000 trial moves
@@ -618,16 +717,15 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     trials = args.steps * step_steps * (lat.n // 128)
     v = trials / dt
+    sample = f"{step_steps} colour steps ({step_steps * (lat.n // 128)} trial moves) of replica 0 per step"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "trial moves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict({"reference_sample": f"{step_steps} colour steps of replica 0 per step"}),
-            "cpu_baseline": {"value": v, "unit": "trial moves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{step_steps} colour steps ({step_steps * (lat.n // 128)} "
-                                       "trial moves) of replica 0 per step"},
-            "e2e": {"value": v, "unit": "trial moves/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": config_dict({"parallelism": f"replicas x{args.gpus}"}),
+            "cpu_baseline": {"value": v, "unit": "trial moves/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "trial moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "recipe": {"dmu0_eV": dmu_bal, "rule": "balanced on the random start, from the oracle's dE"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -650,6 +748,9 @@ def main():
     ap.add_argument("--md-only", action="store_true", help="only the MD measurement (profiling)")
     ap.add_argument("--md-box", type=float, default=250.0, help="nanocrystal box (A) for --md-only")
     ap.add_argument("--multi-only", action="store_true", help="only the multicomponent measurement (profiling)")
+    ap.add_argument("--headline-only", action="store_true", help="only the headline and its sampling points")
+    ap.add_argument("--launch", default=None,
+                    help="FORM,BLOCK,VARIANT: a fixed launch shape of the colour step instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -677,60 +778,117 @@ def main():
         print(json.dumps(multi_bench(V, torch, torch.cuda.Stream(), local, sweeps=args.steps,
                                      warmup=args.warmup)), flush=True)
         return 0
-    lat, types, tab, phi, c0 = workload()
     stream = torch.cuda.Stream()
+    # parameter recipe (Sec. III C): dmu_S from the SGC pre-scan; the balanced
+    # driving force of the random start as a second, labelled point
+    pre = prescan(V, stream, local)
+    dmu_s = pre["dmu_S_eV"]
+    dmu_bal = balanced_dmu(V, stream, local)
+    lat, types, tab, phi, c0 = workload(dmu_bal)
     seeds = rank_seeds(rank)
-    ctx = V.Context(lat, np.tile(types, N_PHI), tab, 0.0, KAPPA, T_K, schedule=V.SCHED_SUBLATTICE,
-                    sched=(4, 4, 4), n_replicas=N_PHI, phi_r=phi, c0_r=c0, seed_r=seeds,
-                    stream=stream, device=local)
+
+    def headline_context(phis):
+        return V.Context(lat, np.tile(types, N_PHI), tab, 0.0, KAPPA, T_K, schedule=V.SCHED_SUBLATTICE,
+                         sched=(4, 4, 4), n_replicas=N_PHI, phi_r=phis, c0_r=c0, seed_r=seeds,
+                         stream=stream, device=local)
+
+    ctx = headline_context(phi)
     spw = ctx.steps_per_sweep
     trials_per_step = N_PHI * lat.n
-    # launch shape (threads per block, row prefetch) by timing, as a user would
-    tuned_block = ctx.autotune(256)
+    # launch shape by timing, as a user would (or fixed from the command line)
+    if args.launch:
+        ctx.set_launch(*[int(x) for x in args.launch.split(",")])
+    else:
+        ctx.autotune(256)
+    launch = ctx.get_launch()
 
     def barrier():
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
 
+    def sampling(o0, o1, seconds):
+        """Per replica over the timed region: local and global acceptance,
+        accepted flips per second, concentration at its end."""
+        out = []
+        for r in range(N_PHI):
+            a, b = o0[r], o1[r]
+            dt, dg = b["trials"] - a["trials"], b["global_trials"] - a["global_trials"]
+            out.append({"c0": float(c0[r]), "c": b["c"],
+                        "acc_local": (b["local_accepts"] - a["local_accepts"]) / max(1, dt),
+                        "acc_global": (b["global_accepts"] - a["global_accepts"]) / max(1, dg),
+                        "accepted_flips_per_s": (b["flips"] - a["flips"]) / seconds})
+        return out
+
     # warm-up (also builds the CUDA graph)
     ctx.sweep(args.warmup)
     flush = L2Flush(torch, local)
     barrier()
+    o_start = ctx.observables_all()
     with Clocks(local) as clk:
         barrier()
         ms = timed_sweeps(torch, stream, ctx, args.steps, flush)
         barrier()
+    o_end = ctx.observables_all()
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = aggregate(world, trials_per_step * args.steps, ms_max * 1e-3)
+    reps = sampling(o_start, o_end, ms * 1e-3)
 
-    # roofline of the dominant kernel: the fused colour step (one launch per
-    # colour step; state resident in L2, so ALU work and latency bound it).
-    # Its average duration is the timed region over its launches there (the
-    # graph's other nodes, the step-base advance and the colour table of the
-    # next 64 steps, add ~3 us per 64 launches, ~1%).
+    # roofline of the dominant kernel: the fused colour step.  Its average time
+    # per colour step is the timed region over its steps (the graph's other
+    # nodes of the per-step form, the step-base advance and the colour table
+    # of the next 64 steps, add ~3 us per 64 launches, ~1 %).
     avg_ms = ms_max / (args.steps * spw)
-    n_prof = 2 * spw
-    ms_prop, ms_comm = ctx.profile_steps(n_prof)
-    trials_per_launch = N_PHI * (lat.n // 128)
-    ops_per_launch = trials_per_launch * OPS_PER_TRIAL
-    achieved = ops_per_launch / (avg_ms * 1e-3) / 1e12
+    trials_per_colour_step = N_PHI * (lat.n // 128)
+    achieved = OPS_PER_TRIAL * trials_per_colour_step / (avg_ms * 1e-3) / 1e12
     peak = ALU_PEAK_OPS / 1e12
-    roof = {"kernel": "k_lattice_step (fused colour step: commit of step k-1, site pick, dE from "
-                      "bit-packed shell counts, local test, dn reduction)",
-            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+    hbm_peak, hbm_src = measured_peak_hbm()
+    hbm_ach = HBM_BYTES_PER_TRIAL * trials_per_colour_step / (avg_ms * 1e-3) / 1e9
+    kname = ("k_lattice_step (one launch per colour step: commit of step k-1, site pick, dE from bit-packed "
+             "shell counts, local test, dn reduction)" if launch[0] == 0 else
+             "k_cluster_steps (one thread-block cluster per replica, 128 colour steps per launch)")
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
             "frac": achieved / peak,
-            "peak_source": "derived: 128 INT32/FP32 lanes x 152 SMs x 2070 MHz "
-                           "(measured xor+add 37.8 / 36.1 Tops/s on two boxes)",
-            # DRAM bytes per launch from an ncu capture of this kernel (256-thread
-            # blocks, warm L2, three launches of the timed loop): the state is
-            # L2-resident, so HBM traffic is nil
+            "peak_source": (f"derived from measured per-SM rates (INT32 120, popc 20.7, multiply pairs 31, FP32 122, "
+                            f"expf 11.3 per clock): the ALU pipe needs {SM_CYCLES_PER_TRIAL:.2f} SM cycles per trial "
+                            f"({OPS_PER_TRIAL} algorithmic ops), x 152 SMs x 2.07 GHz"),
+            # DRAM bytes per launch from an ncu capture of the per-step kernel
+            # (256-thread blocks, warm L2, three launches of the timed loop)
             "traffic": 256,
             "traffic_source": "ncu --set full --cache-control none, k_lattice_step<...,256,...> x 3: "
                               "dram__bytes_read.sum 256 B + dram__bytes_write.sum 0 B per launch",
-            "ops_per_launch": ops_per_launch, "ops_per_trial": OPS_PER_TRIAL,
-            "trials_per_launch": trials_per_launch, "avg_launch_us": avg_ms * 1e3,
-            "isolated_launch_us": (ms_prop + ms_comm) / n_prof * 1e3}
+            "ops_per_trial": {"simple_int": OPS_SIMPLE, "popc": OPS_POPC, "mul_pairs": OPS_MULPAIR,
+                              "fp32": OPS_FP32, "mufu": OPS_MUFU},
+            "trials_per_colour_step": trials_per_colour_step, "avg_colour_step_us": avg_ms * 1e3,
+            "hbm_nominal": {"bytes_per_trial": HBM_BYTES_PER_TRIAL, "achieved_gbs": hbm_ach, "peak_gbs": hbm_peak,
+                            "frac": hbm_ach / hbm_peak, "peak_source": hbm_src,
+                            "note": "the gather form's list bytes; this kernel reads no list (measured DRAM ~0)"},
+            "step_latency_floor_us": STEP_LATENCY_FLOOR_US}
+
+    # the second point: the recipe's coexistence driving force dmu_S, which
+    # freezes this supersaturated start (every isolated B dissolves locally;
+    # the composite moves' dn lies far outside the constraint's width)
+    ctx_b = headline_context(RC.phi_grid(dmu_s, KAPPA, T_K, c0))
+    ctx_b.set_launch(*launch)
+    ctx_b.sweep(args.warmup)
+    n_b = min(args.steps, 20)
+    ob0 = ctx_b.observables_all()
+    ms_b = timed_sweeps(torch, stream, ctx_b, n_b, flush)
+    ob1 = ctx_b.observables_all()
+    ctx_b.close()
+    recipe_out = {
+        "prescan": pre,
+        "headline": {"dmu0_eV": dmu_bal,
+                     "label": "dmu0 = the driving force of the metastable start (Eq. c0's optimality condition on "
+                              "the state the run starts from): the first composite move has no expected drift",
+                     "replicas": reps, "accepted_flips_per_s": sum(x["accepted_flips_per_s"] for x in reps)},
+        "recipe_dmu_S": {"dmu0_eV": dmu_s,
+                         "label": "dmu0 = dmu_S, the two-phase coexistence value of steps (i) and (iii) of "
+                                  "Sec. III C, on the same supersaturated start", "sweeps": n_b,
+                         "trial_moves_per_s": trials_per_step * n_b / (ms_b * 1e-3),
+                         "replicas": sampling(ob0, ob1, ms_b * 1e-3)}}
+    recipe_out["recipe_dmu_S"]["accepted_flips_per_s"] = sum(
+        x["accepted_flips_per_s"] for x in recipe_out["recipe_dmu_S"]["replicas"])
 
     # end to end through the C ABI with host buffers: every replica's species
     # up from pinned memory, one sweep, observables and species down, every step
@@ -752,31 +910,34 @@ def main():
            "calls_per_step": "vcsgc_set_types_all, vcsgc_sweep(1), vcsgc_observables_all, vcsgc_get_types_all",
            "clock": "host wall clock over all steps"}
 
-    o0 = ctx.observables(0)
     ctx.close()
+    launches = (spw * args.steps + 2 * ((spw * args.steps) // 64)) if launch[0] == 0 else args.steps
     line = {"metric": METRIC, "value": value, "unit": "trial moves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": config_dict({"parallelism": f"replicas x{world}", "block": tuned_block}),
-            "e2e": e2e, "gpu_launches": spw * args.steps + 2 * ((spw * args.steps) // 64), "roofline": roof,
-            "clocks": clk.summary(),
-            "acceptance": {"local": o0["acc_local"], "global": o0["acc_global"], "c": o0["c"]}}
-    if not args.no_md:
-        line["md"] = md_bench(V, torch, stream, local)
-        line["md_mixed"] = md_bench(V, torch, stream, local, precision=V.PREC_MIXED)
-    if not args.no_mixed:
-        line["mixed_128cubed"] = mixed_bench(V, torch, stream, local)
-    if not args.no_batch:
-        line["batch_64"] = batch_bench(V, torch, stream, local, surrogate=not args.no_surrogate)
-    if not args.no_ising:
-        line["ising"] = ising_bench(V, torch, stream, local)
-    if not args.no_overlap:
-        line["overlap"] = overlap_bench(V, torch, stream, local)
-    if not args.no_multi:
-        line["multicomponent"] = multi_bench(V, torch, stream, local)
-    if not args.no_ensemble and not args.no_md:
-        line["md_ensemble"] = ensemble_bench(V, torch, stream, local)
+            "config": config_dict({"parallelism": f"replicas x{world}"}),
+            "launch": {"form": launch[0], "block": launch[1], "variant": launch[2],
+                       "chosen_by": "command line" if args.launch else "vcsgc_autotune"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "clocks": clk.summary(), "sampling": recipe_out}
+    if not args.headline_only:
+        if not args.no_md:
+            line["md"] = md_bench(V, torch, stream, local)
+            line["md_mixed"] = md_bench(V, torch, stream, local, precision=V.PREC_MIXED)
+            line["mc_explicit"] = mc_explicit_bench(V, torch, stream, local, dmu_bal)
+        if not args.no_mixed:
+            line["mixed_128cubed"] = mixed_bench(V, torch, stream, local, dmu_bal)
+        if not args.no_batch:
+            line["batch_64"] = batch_bench(V, torch, stream, local, dmu_bal, surrogate=not args.no_surrogate)
+        if not args.no_ising:
+            line["ising"] = ising_bench(V, torch, stream, local)
+        if not args.no_overlap:
+            line["overlap"] = overlap_bench(V, torch, stream, local, dmu_bal)
+        if not args.no_multi:
+            line["multicomponent"] = multi_bench(V, torch, stream, local)
+        if not args.no_ensemble and not args.no_md:
+            line["md_ensemble"] = ensemble_bench(V, torch, stream, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lat, types, tab, phi, c0)
     if rank == 0:

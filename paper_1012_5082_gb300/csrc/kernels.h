@@ -62,6 +62,13 @@ inline double cell_list_margin(const double box[3]) {
 void launch_cell_neighbours(long long N, const double* x, const double* y, const double* z,
                             const double box[3], double rl, CellList cl, int K, int* nbr, int* cnt,
                             unsigned* err, cudaStream_t st);
+// SPATIAL colour schedule on the device: dom_start[ndom + 1] and
+// dom_sites[N] (atoms by domain, ascending within one) from the positions;
+// dom_of_block[nb0 nb1 nb2] gives each box's domain rank; dom_of[N],
+// count[ndom] and cursor[ndom] are scratch
+void launch_spatial_schedule(long long N, const double* x, const double* y, const double* z, const double box[3],
+                             const int nb[3], const int* dom_of_block, int ndom, int* dom_of, int* count,
+                             int* cursor, int* dom_start, int* dom_sites, cudaStream_t st);
 // half list: the entries j > i of each full row (same stride K)
 void launch_half_list(long long N, int K, const int* nbr, const int* cnt, int* nbr_h, int* cnt_h,
                       cudaStream_t st);

@@ -294,6 +294,42 @@ void launch_cell_neighbours(long long N, const double* x, const double* y, const
                                 rlm * rlm, K, nbr, cnt, err);
 }
 
+// ------------------------------------------------- spatial colour schedule
+// Domain of every atom for the SPATIAL schedule (boxes of the periodic cell,
+// Sec. III A): box index from floor(v / L * n) clamped to the grid -- the
+// host's rule, so the tables are the same -- mapped to its domain rank
+// (colour-major, then box index) by dom_of_block.
+__device__ __forceinline__ int spatial_box(double v, double L, int n) {
+  const int q = (int)floor(v / L * n);
+  return q < 0 ? 0 : (q >= n ? n - 1 : q);
+}
+
+__global__ void k_spatial_assign(long long N, const double* x, const double* y, const double* z, double bx,
+                                 double by, double bz, int nbx, int nby, int nbz, const int* dom_of_block,
+                                 int* dom_of, int* count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int b = (spatial_box(z[i], bz, nbz) * nby + spatial_box(y[i], by, nby)) * nbx + spatial_box(x[i], bx, nbx);
+  const int d = dom_of_block[b];
+  dom_of[i] = d;
+  atomicAdd(&count[d], 1);
+}
+
+void launch_spatial_schedule(long long N, const double* x, const double* y, const double* z, const double box[3],
+                             const int nb[3], const int* dom_of_block, int ndom, int* dom_of, int* count,
+                             int* cursor, int* dom_start, int* dom_sites, cudaStream_t st) {
+  const unsigned g = (unsigned)((N + 127) / 128);
+  cudaMemsetAsync(count, 0, sizeof(int) * ndom, st);
+  cudaMemsetAsync(cursor, 0, sizeof(int) * ndom, st);
+  k_spatial_assign<<<g, 128, 0, st>>>(N, x, y, z, box[0], box[1], box[2], nb[0], nb[1], nb[2], dom_of_block, dom_of,
+                                      count);
+  // counting sort by domain, ascending atom index within a domain (the
+  // cell-list kernels with domains as bins)
+  k_scan<<<1, 1024, 0, st>>>(count, ndom, dom_start);
+  k_cell_scatter<<<g, 128, 0, st>>>(N, dom_of, dom_start, cursor, dom_sites);
+  k_cell_sort<<<(ndom + 127) / 128, 128, 0, st>>>(ndom, dom_start, dom_sites);
+}
+
 __global__ void k_half_list(long long N, int K, const int* nbr, const int* cnt, int* nbr_h, int* cnt_h) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;

@@ -152,6 +152,13 @@ struct Ctx {
   size_t cl_smem[5] = {};
   int cl_lcap[5] = {};             // most trials of one CTA in one step
   long long base_lag = 0;          // steps run in form 1 not yet added to lat.ctl->base_step
+  // SPATIAL schedule rebuilt on the device between MD phases: box -> domain
+  // rank, and scratch of the counting sort
+  int* sp_dom_of_block = nullptr;
+  int* sp_dom_of = nullptr;
+  int* sp_count = nullptr;
+  int* sp_cursor = nullptr;
+  int sp_ndom = 0;
 };
 
 // index of a cluster size in Ctx::cl_tiles (-1: not a supported size)
@@ -1943,19 +1950,44 @@ int md_steps(void* ctx, int64_t n) {
   return check_device_error(c);
 }
 
+// Rebuild the SPATIAL schedule from the current positions on the device
+// (the same tables as build_schedule: domains by colour, then box index;
+// atoms ascending within a domain).  The colour and domain counts do not
+// depend on the positions, only the domains' members do.
+static int spatial_schedule_device(Ctx* c) {
+  const int nb[3] = {c->sched[0], c->sched[1], c->sched[2]}, pp[3] = {c->sched[3], c->sched[4], c->sched[5]};
+  const int nblk = nb[0] * nb[1] * nb[2];
+  if (!c->sp_dom_of_block) {
+    std::vector<int> rank_of(nblk);
+    int d = 0;
+    const int ncol = pp[0] * pp[1] * pp[2];
+    for (int col = 0; col < ncol; ++col)
+      for (int b = 0; b < nblk; ++b) {
+        const int ibx = b % nb[0], iby = (b / nb[0]) % nb[1], ibz = b / (nb[0] * nb[1]);
+        if (((ibz % pp[2]) * pp[1] + (iby % pp[1])) * pp[0] + (ibx % pp[0]) == col) rank_of[b] = d++;
+      }
+    if (d != c->n_domains) return fail(c, VCSGC_ERR_STATE, "spatial schedule: domain count changed");
+    TRY(dalloc(c, &c->sp_dom_of_block, nblk));
+    TRY(dalloc(c, &c->sp_dom_of, c->N));
+    TRY(dalloc(c, &c->sp_count, d));
+    TRY(dalloc(c, &c->sp_cursor, d));
+    CK(cudaMemcpyAsync(c->sp_dom_of_block, rank_of.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice, c->st));
+    c->sp_ndom = d;
+  }
+  if (c->dom_sites_cap < c->N) return fail(c, VCSGC_ERR_STATE, "spatial schedule: site table too small");
+  launch_spatial_schedule(c->N, c->x, c->y, c->z, c->box, nb, c->sp_dom_of_block, c->sp_ndom, c->sp_dom_of,
+                          c->sp_count, c->sp_cursor, c->dom_start, c->dom_sites, c->st);
+  CK(cudaGetLastError());
+  return VCSGC_OK;
+}
+
 int vcsgc_hybrid(void* ctx, int64_t n_cycles, int64_t n_md, int64_t n_mc) {
   VCSGC_TRACE("vcsgc_hybrid");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n_cycles < 0 || n_md < 0 || n_mc < 0) return VCSGC_ERR_INVALID_ARG;
   for (int64_t q = 0; q < n_cycles; ++q) {
     TRY(md_run(c, n_md));
-    if (c->sched_kind == VCSGC_SCHED_SPATIAL) {
-      std::vector<double> hx, hy, hz;
-      TRY(positions_host(c, hx, hy, hz));
-      Sched S;
-      TRY(build_schedule(c, hx, hy, hz, S));
-      TRY(upload_schedule(c, S));
-    }
+    if (c->sched_kind == VCSGC_SCHED_SPATIAL) TRY(spatial_schedule_device(c));
     // positions moved: the tracked energy restarts from a full evaluation
     double e;
     TRY(energy_of(c, 0, &e));
