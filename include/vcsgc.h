@@ -192,7 +192,11 @@ int vcsgc_default_options(vcsgc_options* opt);
  * With species-dependent densities on a rigid lattice the local decision is
  * taken on an FP32 dE within a proven error bound (FP64 where the bound
  * cannot decide), so every decision is the FP64 one; the energy is then
- * recomputed when observables or a checkpoint read it.
+ * recomputed when observables or a checkpoint read it.  With the period-q
+ * sublattice schedule, the five-shell BCC neighbourhood, FP64 precision and
+ * kappa_units 0, such a context advances its replicas through the
+ * multicomponent kernels with K = 2 (the same chain step for step, see
+ * vcsgc_multi_init) and mirrors their species and counters when read.
  * Errors: INVALID_ARG (bad sizes, N >= 2^30 sites, species other than 0/1,
  * T <= 0), SCHEDULE, TABLE_RANGE, NOMEM, CUDA. */
 int vcsgc_init(void** ctx, const vcsgc_lattice* lattice, const uint8_t* types,

@@ -14,6 +14,7 @@
 #include "../../include/vcsgc.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "multi_host.h"
 #include "screen.h"
 #include "trace.h"
 
@@ -159,6 +160,12 @@ struct Ctx {
   int* sp_count = nullptr;
   int* sp_cursor = nullptr;
   int sp_ndom = 0;
+  // species-dependent densities on the period-q sublattice: the colour steps
+  // run through a two-species multicomponent object (its FP32-screened
+  // kernels with compile-time offsets); this context mirrors its species and
+  // running state on reading
+  void* multi = nullptr;
+  bool multi_dirty = false;
 };
 
 // index of a cluster size in Ctx::cl_tiles (-1: not a supported size)
@@ -191,6 +198,7 @@ void select_blk(Ctx* c) {
 
 int flush(Ctx* c);
 int sync_bytes(Ctx* c, int r);
+int sync_from_multi(Ctx* c);
 
 int fail(Ctx* c, int code, const std::string& msg) {
   c->err = msg;
@@ -812,6 +820,7 @@ int flush(Ctx* c) {
 
 // refresh the species bytes of replica r (or all when r < 0) from the bits
 int sync_bytes(Ctx* c, int r) {
+  TRY(sync_from_multi(c));
   if (!c->fast) return VCSGC_OK;
   TRY(flush(c));
   if (r < 0) launch_lattice_unpack(c->lat, c->d_tptr, 0, c->R, c->max_sites, c->st);
@@ -822,6 +831,12 @@ int sync_bytes(Ctx* c, int r) {
 
 int run_steps(Ctx* c, long long n) {
   if (n <= 0) return VCSGC_OK;
+  if (c->multi) {
+    const int rc = vcsgc_multi_steps(c->multi, n);
+    if (rc != VCSGC_OK) return fail(c, rc, vcsgc_multi_last_error(c->multi));
+    c->multi_dirty = true;
+    return VCSGC_OK;
+  }
   if (c->fast) return run_steps_fast(c, n);
   if (c->screen) c->energy_stale = true;
   const int G = 64;
@@ -849,6 +864,65 @@ int run_steps(Ctx* c, long long n) {
   for (long long q = 0; q < n; ++q) launch_colour_step(c->mc, c->shell, c->reembed, c->st);
   CK(cudaGetLastError());
   return VCSGC_OK;
+}
+
+// species, densities and running state of every replica from the
+// multicomponent object after its steps (the energy is recomputed when read)
+int sync_from_multi(Ctx* c) {
+  if (!c->multi || !c->multi_dirty) return VCSGC_OK;
+  for (int r = 0; r < c->R; ++r) {
+    MRepState ms;
+    const int rc = multi_get_state(c->multi, r, &ms);
+    if (rc != VCSGC_OK) return fail(c, rc, vcsgc_multi_last_error(c->multi));
+    const uint8_t* t = multi_types_device(c->multi, r);
+    if (!t) return fail(c, VCSGC_ERR_CUDA, vcsgc_multi_last_error(c->multi));
+    CK(cudaMemcpyAsync(c->rep_types[r], t, c->N, cudaMemcpyDeviceToDevice, c->st));
+    TRY(refresh_rho(c, r));
+    RepState s;
+    std::memset(&s, 0, sizeof(s));
+    s.n = ms.cnt[1];
+    s.step = ms.step;
+    s.fin_step = ms.fin_step;
+    s.trials = ms.trials;
+    s.local_acc = ms.local_acc;
+    s.global_trials = ms.global_trials;
+    s.global_acc = ms.global_acc;
+    s.flips = ms.flips;
+    s.near_ties = ms.near_ties;
+    s.steps = ms.steps;
+    s.sum_c = ms.sum_c[1];
+    s.sum_c2 = ms.sum_c2[1];
+    CK(cudaMemcpyAsync(c->rs + r, &s, sizeof(RepState), cudaMemcpyHostToDevice, c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  c->energy_stale = true;
+  c->multi_dirty = false;
+  return VCSGC_OK;
+}
+
+// this context's species and state of replica r into the multicomponent object
+int push_to_multi(Ctx* c, int r, const uint8_t* host_types, const RepState* s) {
+  if (!c->multi) return VCSGC_OK;
+  int rc = vcsgc_multi_set_types(c->multi, r, host_types);
+  if (rc == VCSGC_OK && s) {
+    MRepState ms;
+    rc = multi_get_state(c->multi, r, &ms);
+    ms.step = s->step;
+    ms.fin_step = s->fin_step;
+    ms.trials = s->trials;
+    ms.local_acc = s->local_acc;
+    ms.global_trials = s->global_trials;
+    ms.global_acc = s->global_acc;
+    ms.flips = s->flips;
+    ms.near_ties = s->near_ties;
+    ms.steps = s->steps;
+    ms.sum_c[1] = s->sum_c;
+    ms.sum_c2[1] = s->sum_c2;
+    ms.sum_c[0] = (double)s->steps - s->sum_c;
+    ms.sum_c2[0] = (double)s->steps - 2.0 * s->sum_c + s->sum_c2;
+    if (rc == VCSGC_OK) rc = multi_set_state(c->multi, r, &ms);
+  }
+  return rc == VCSGC_OK ? VCSGC_OK : fail(c, rc, vcsgc_multi_last_error(c->multi));
 }
 
 // ------------------------------------------------------------------- MD
@@ -1348,6 +1422,50 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   if (c->kind == 1 && c->R == 1) TRY(md_forces(c));
   TRY(check_device_error(c));
   TRY(setup_fast(c, hs));
+  // species-dependent densities on the period-q sublattice with the
+  // five-shell table: the colour steps run through a two-species
+  // multicomponent object, whose FP32-screened kernels (compile-time
+  // offsets, per-site floats ordered by x mod period) advance the same chain
+  // step for step
+  if (c->kind == 0 && c->reembed && c->sched_kind == VCSGC_SCHED_SUBLATTICE && o->kappa_units == 0 && !c->mixed &&
+      !c->no_fast && c->mc.n_shells == 5 && c->K == 58) {
+    vcsgc_multi_tables mt{};
+    mt.K = 2;
+    mt.nr = E->nr;
+    mt.dr = E->dr;
+    mt.nrho = E->nrho;
+    mt.drho = E->drho;
+    mt.rc = E->rc;
+    for (int q = 0; q < 3; ++q) {
+      mt.pair[q] = E->pair[q];  // (0,0), (0,1), (1,1)
+      mt.dpair[q] = E->dpair[q];
+    }
+    for (int q = 0; q < 2; ++q) {
+      mt.dens[q] = E->dens[q];
+      mt.ddens[q] = E->ddens[q];
+      mt.embed[q] = E->embed[q];
+      mt.dembed[q] = E->dembed[q];
+    }
+    std::vector<double> ph(c->R), ka(c->R), TT(c->R), cc(c->R);
+    std::vector<uint64_t> sd(c->R);
+    for (int r = 0; r < c->R; ++r) {
+      ph[r] = o->phi_r ? o->phi_r[r] : phi;
+      ka[r] = o->kappa_r ? o->kappa_r[r] : kappa;
+      TT[r] = o->T_r ? o->T_r[r] : T;
+      cc[r] = o->c0_r ? o->c0_r[r] : o->c0;
+      sd[r] = o->seed_r ? o->seed_r[r] : o->seed + (uint64_t)r;
+    }
+    const int32_t period[3] = {c->sched[0], c->sched[1], c->sched[2]};
+    void* m = nullptr;
+    const int rc = vcsgc_multi_init(&m, L, types, &mt, c->R, ph.data(), ka.data(), TT.data(), cc.data(), sd.data(),
+                                    period, c->st, c->device);
+    if (rc != VCSGC_OK) return fail(c, rc, std::string("multicomponent engine: ") + vcsgc_multi_last_error(nullptr));
+    if (multi_screened(m)) {
+      c->multi = m;
+    } else {
+      vcsgc_multi_free(m);
+    }
+  }
   return VCSGC_OK;
 }
 
@@ -1648,6 +1766,8 @@ static int setup_fast(Ctx* c, const std::vector<RepState>& hs) {
 
 static void destroy(Ctx* c) {
   if (!c) return;
+  if (c->multi) vcsgc_multi_free(c->multi);
+  c->multi = nullptr;
   for (Ctx* sc : c->subs) destroy(sc);
   c->subs.clear();
   drop_graph(c);
@@ -2031,6 +2151,7 @@ int observables(void* ctx, int32_t r, vcsgc_observables* o) {
   VCSGC_TRACE("observables");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !o || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  TRY(sync_from_multi(c));
   TRY(flush(c));
   TRY(check_device_error(c));
   TRY(refresh_energies(c));
@@ -2045,6 +2166,7 @@ int vcsgc_observables_all(void* ctx, vcsgc_observables* o) {
   VCSGC_TRACE("vcsgc_observables_all");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !o) return VCSGC_ERR_INVALID_ARG;
+  TRY(sync_from_multi(c));
   TRY(flush(c));
   TRY(refresh_energies(c));
   // the states and the error word through one pinned buffer, one synchronisation
@@ -2127,6 +2249,7 @@ int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
     return checked_species(c);
   }
   if (!species_ok(in, Nr)) return fail(c, VCSGC_ERR_INVALID_ARG, "species must be 0 or 1");
+  TRY(sync_from_multi(c));
   TRY(flush(c));
   CK(cudaMemcpyAsync(c->rep_types[r], in, Nr, cudaMemcpyHostToDevice, c->st));
   if (c->fast) {
@@ -2155,6 +2278,7 @@ int vcsgc_set_types(void* ctx, int32_t r, const uint8_t* in) {
     return check_device_error(c);
   }
   TRY(sync_state_from_types(c, r, in));
+  TRY(push_to_multi(c, r, in, nullptr));
   c->forces_valid = false;
   return check_device_error(c);
 }
@@ -2227,6 +2351,7 @@ int vcsgc_set_types_all(void* ctx, const uint8_t* in) {
 int vcsgc_get_rho(void* ctx, int32_t r, double* out) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  TRY(sync_from_multi(c));
   if (!c->subs.empty()) return vcsgc_get_rho(c->subs[r], 0, out);
   const double* src = c->rho + (c->reembed ? (long long)r * c->N : 0);
   CK(cudaMemcpyAsync(out, src, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->st));
@@ -2238,6 +2363,7 @@ int vcsgc_delta_e(void* ctx, int32_t r, const int64_t* sites, int64_t n, double*
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || (n > 0 && (!sites || !out)) || n < 0 || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
   if (n == 0) return VCSGC_OK;
+  TRY(sync_from_multi(c));
   std::vector<int> s32(n);
   for (int64_t q = 0; q < n; ++q) {
     if (sites[q] < 0 || sites[q] >= c->rep_n[r]) return fail(c, VCSGC_ERR_INVALID_ARG, "site index out of range");
@@ -2264,6 +2390,7 @@ int vcsgc_energy(void* ctx, int32_t r, double* out) {
   VCSGC_TRACE("vcsgc_energy");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !out || r < 0 || r >= c->R) return VCSGC_ERR_INVALID_ARG;
+  TRY(sync_from_multi(c));
   return energy_of(c, r, out);
 }
 
@@ -2530,6 +2657,7 @@ int vcsgc_save(void* ctx, const char* path) {
   VCSGC_TRACE("vcsgc_save");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !path) return VCSGC_ERR_INVALID_ARG;
+  TRY(sync_from_multi(c));
   TRY(sync_bytes(c, -1));
   TRY(refresh_energies(c));
   long long tot = 0;
@@ -2629,6 +2757,11 @@ int vcsgc_load(void* ctx, const char* path) {
   // counters, step and the tracked energy exactly as saved
   CK(cudaMemcpyAsync(c->rs, rs.data(), sizeof(RepState) * c->R, cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
+  off = 0;
+  for (int r = 0; r < c->R; ++r) {
+    TRY(push_to_multi(c, r, types.data() + off, &rs[r]));
+    off += rep_n[r];
+  }
   c->energy_stale = false;
   c->forces_valid = false;
   fill_args(c);
@@ -2638,14 +2771,14 @@ int vcsgc_load(void* ctx, const char* path) {
 int vcsgc_profile_steps(void* ctx, int64_t n, double* ms_propose, double* ms_commit) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || n < 1 || !ms_propose || !ms_commit) return VCSGC_ERR_INVALID_ARG;
-  if (c->fast && cluster_form_usable(c)) {
+  if (c->multi || (c->fast && cluster_form_usable(c))) {
     // one persistent launch of n steps: its whole time is reported as propose
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     TRY(flush(c));
     CK(cudaEventRecord(e0, c->st));
-    TRY(run_steps_cluster(c, n));
+    TRY(c->multi ? run_steps(c, n) : run_steps_cluster(c, n));
     CK(cudaEventRecord(e1, c->st));
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;

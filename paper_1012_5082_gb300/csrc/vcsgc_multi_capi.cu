@@ -626,3 +626,49 @@ const char* vcsgc_multi_last_error(void* h) {
 void vcsgc_multi_free(void* h) { destroy(as_multi(h)); }
 
 }  // extern "C"
+
+// ---- host-side access for a binary context that runs its colour steps
+//      through a two-species multicomponent object (multi_host.h)
+namespace vcsgc {
+
+int multi_get_state(void* h, int r, MRepState* out) {
+  Multi* m = as_multi(h);
+  if (!m || !out || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  MTRY(flush(m));
+  MCK(cudaMemcpyAsync(out, m->args.rs + r, sizeof(MRepState), cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  return device_error(m);
+}
+
+int multi_set_state(void* h, int r, const MRepState* in) {
+  Multi* m = as_multi(h);
+  if (!m || !in || r < 0 || r >= m->R || m->args.fused) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  MCK(cudaMemcpyAsync(m->args.rs + r, in, sizeof(MRepState), cudaMemcpyHostToDevice, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  return VCSGC_OK;
+}
+
+int multi_get_rho(void* h, int r, double* out) {
+  Multi* m = as_multi(h);
+  if (!m || !out || r < 0 || r >= m->R) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  MTRY(flush(m));
+  MCK(cudaMemcpyAsync(out, m->args.rho + (long long)r * m->N, sizeof(double) * m->N, cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  return VCSGC_OK;
+}
+
+bool multi_screened(void* h) {
+  Multi* m = as_multi(h);
+  return m && m->args.screen;
+}
+
+const uint8_t* multi_types_device(void* h, int r) {
+  Multi* m = as_multi(h);
+  if (!m || r < 0 || r >= m->R || flush(m) != VCSGC_OK) return nullptr;
+  return m->args.types + (long long)r * m->N;
+}
+
+}  // namespace vcsgc
