@@ -670,6 +670,30 @@ def multi_bench(V, torch, stream, local, sweeps=10, warmup=2):
     return out
 
 
+def schedule_bench(V, torch, stream, local, dmu0, sweeps=2):
+    """The schedule autotuner (vcsgc_autotune_schedule) on the headline
+    workload: the period-4 sublattice (8,000 trials per replica per colour
+    step), octant blocks of 4^3 and 5^3 cells (1,000 and 512 trials) and
+    overlapping domains in cells of 10^3 (512 trials), each scored by the
+    accepted flips per second it delivers from the random start."""
+    lat, types, tab, phi, c0 = workload(dmu0)
+    cand = [("sublattice 4^3", V.SCHED_SUBLATTICE, (4, 4, 4, 0, 0, 0)),
+            ("octant blocks 4^3", V.SCHED_BLOCKS, (4, 4, 4, 2, 2, 2)),
+            ("octant blocks 5^3", V.SCHED_BLOCKS, (5, 5, 5, 2, 2, 2)),
+            ("overlapping 10^3, gap 4", V.SCHED_OVERLAP, (10, 10, 10, 4, 4, 4))]
+    ctx = V.Context(lat, np.tile(types, N_PHI), tab, 0.0, KAPPA, T_K, schedule=V.SCHED_SUBLATTICE,
+                    sched=(4, 4, 4), n_replicas=N_PHI, phi_r=phi, c0_r=c0, seed_r=rank_seeds(0),
+                    stream=stream, device=local)
+    t0 = time.perf_counter()
+    best, scores = ctx.autotune_schedule([(k, s) for _, k, s in cand], sweeps=sweeps)
+    dt = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": "80^3 x 8 replicas, headline phi and c0, from the random start",
+            "score": "accepted flips/s of all replicas over the candidate's timed sweeps",
+            "scores": {name: float(v) for (name, _, _), v in zip(cand, scores)}, "chosen": cand[best][0],
+            "sweeps_per_candidate": 2 * sweeps, "seconds": dt}
+
+
 def rank_seeds(rank: int, n: int = N_PHI) -> np.ndarray:
     """Philox keys of one rank's replicas.  Ranks run independent replicas
     (the method does not shard: weak scaling), so the keys must differ
@@ -934,6 +958,7 @@ def main():
             line["ising"] = ising_bench(V, torch, stream, local)
         if not args.no_overlap:
             line["overlap"] = overlap_bench(V, torch, stream, local, dmu_bal)
+            line["schedule_autotune"] = schedule_bench(V, torch, stream, local, dmu_bal)
         if not args.no_multi:
             line["multicomponent"] = multi_bench(V, torch, stream, local)
         if not args.no_ensemble and not args.no_md:

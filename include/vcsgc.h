@@ -228,6 +228,29 @@ int vcsgc_batch_init(void** ctx, int32_t n_rep, const int32_t* cells, double a, 
  * size. */
 int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block);
 
+/* Change the colour schedule of a rigid single-lattice context between two
+ * colour steps (kind and sched[6] as in vcsgc_options; BLOCKS, SUBLATTICE or
+ * OVERLAP).  Each schedule leaves pi_V invariant (Sec. III A-B: the
+ * decomposition only chooses which independent trials a composite move
+ * holds), so the chain stays exact; the step counter and the random streams
+ * continue.  Errors: INVALID_ARG, SCHEDULE (domains closer than 2 r_c, sizes
+ * that do not divide; the old schedule is kept), STATE (explicit positions,
+ * batches, or a context run through the multicomponent kernels). */
+int vcsgc_set_schedule(void* ctx, int32_t kind, const int32_t* sched);
+
+/* Pick a colour schedule by the sampling it delivers: for each of n_cand
+ * candidates (kinds[q], scheds[6 q .. 6 q + 5]) the chain, started from its
+ * state at the call (species, counters, step counter), runs `sweeps` sweeps
+ * under the candidate to settle, then `sweeps` timed sweeps; scores[q]
+ * receives the accepted flips per second of all replicas over the timed
+ * sweeps (-1 for a schedule the lattices refuse).  These trial runs are
+ * discarded: the chain then resumes from its state at the call under the
+ * best candidate, as if they had not been run; *best receives its index.
+ * Errors: INVALID_ARG, STATE as vcsgc_set_schedule, SCHEDULE (no candidate
+ * applies). */
+int vcsgc_autotune_schedule(void* ctx, int32_t n_cand, const int32_t* kinds, const int32_t* scheds, int64_t sweeps,
+                            double* scores, int32_t* best);
+
 /* Advance every replica by n_steps colour steps (composite moves of
  * Sec. III B 2: site pick, dE gather, local Metropolis test with
  * dmu0 = phi + 2 kappa_p N c0, reduction of dn, global test with exponent

@@ -1986,6 +1986,182 @@ int vcsgc_autotune(void* ctx, int64_t steps, int32_t* best_block) {
   return check_device_error(c);
 }
 
+// A new colour schedule for a rigid-lattice context, mid-chain.  Every
+// schedule leaves pi_V invariant (its composite moves satisfy detailed
+// balance on their own), so a chain may change schedules between colour
+// steps; the step counter, and with it the random streams, runs on.  The
+// fused form's per-schedule data (domains per colour, pending slots, block
+// tables, colour table, cluster tilings) is rebuilt; species, running state
+// and step base are kept.
+static int reschedule(Ctx* c, int kind, const int32_t sched[6]) {
+  if (c->kind != 0 || !c->subs.empty() || c->multi || c->no_fast)
+    return fail(c, VCSGC_ERR_STATE, "schedule change: rigid single-lattice contexts only");
+  if (kind != VCSGC_SCHED_BLOCKS && kind != VCSGC_SCHED_SUBLATTICE && kind != VCSGC_SCHED_OVERLAP)
+    return fail(c, VCSGC_ERR_INVALID_ARG, "schedule change: BLOCKS, SUBLATTICE or OVERLAP");
+  TRY(sync_bytes(c, -1));  // the pending step committed, the species bytes current
+  const int old_kind = c->sched_kind;
+  int old_sched[6];
+  std::memcpy(old_sched, c->sched, sizeof(old_sched));
+  c->sched_kind = kind;
+  std::memcpy(c->sched, sched, sizeof(c->sched));
+  Sched S;
+  const std::vector<double> none;
+  const int rc = build_schedule(c, none, none, none, S);
+  if (rc != VCSGC_OK) {
+    c->sched_kind = old_kind;
+    std::memcpy(c->sched, old_sched, sizeof(old_sched));
+    return rc;
+  }
+  int dnew = 0;  // domains of the fullest colour: the fused form's trials per replica and step
+  for (size_t k = 0; k + 1 < S.col.size(); ++k) dnew = std::max(dnew, S.col[k + 1] - S.col[k]);
+  TRY(upload_schedule(c, S));
+  drop_graph(c);
+  if (!c->fast) return check_device_error(c);
+  c->dmax = dnew;
+  LatArgs& l = c->lat;
+  const bool sub = kind == VCSGC_SCHED_SUBLATTICE;
+  const int q[3] = {sched[0], sched[1], sched[2]};
+  if (sub) {
+    l.rcp_qx = 1.0f / (float)q[0];
+    l.rcp_qy = 1.0f / (float)q[1];
+  }
+  // geometry (domains per colour, pending slots) and block tables
+  long long slots = 0;
+  for (int r = 0; r < c->R; ++r) {
+    LatGeom g = lattice_geom(c->nx, c->ny, c->nz, sub ? q : nullptr, c->sublattice_d, c->dmax, c->h_geom[r].bits_off,
+                             (long long)r * c->dmax);
+    g.site_off = c->h_geom[r].site_off;
+    c->h_geom[r] = g;
+    slots = std::max(slots, g.pend_off + g.dmax);
+  }
+  CK(cudaMemcpyAsync(const_cast<LatGeom*>(l.geom), c->h_geom.data(), sizeof(LatGeom) * c->R, cudaMemcpyHostToDevice,
+                     c->st));
+  TRY(dalloc(c, &l.pend, (size_t)slots));
+  CK(cudaMemsetAsync(l.pend, 0xFF, sizeof(int) * slots, c->st));
+  const int bsz[3] = {64, 128, 256};
+  for (int b = 0; b < 3; ++b) {
+    std::vector<int2> tab;
+    for (int r = 0; r < c->R; ++r) {
+      const int nb = std::max(1, (c->h_geom[r].dmax + bsz[b] - 1) / bsz[b]);
+      for (int k = 0; k < nb; ++k) tab.push_back(make_int2(r, k * bsz[b]));
+    }
+    TRY(dalloc(c, &c->blk_tab[b], tab.size()));
+    CK(cudaMemcpyAsync(c->blk_tab[b], tab.data(), sizeof(int2) * tab.size(), cudaMemcpyHostToDevice, c->st));
+    c->n_blk_tab[b] = (int)tab.size();
+  }
+  l.dmax = c->dmax;
+  select_blk(c);
+  fill_args(c);
+  // the colour table of the chain's next steps under the new colour count
+  TRY(sync_base(c));
+  launch_colour_table(l, c->st);
+  CK(cudaGetLastError());
+  // cluster tilings exist for the sublattice schedule only
+  for (int k = 0; k < 5; ++k) {
+    c->cl_tiles[k] = nullptr;
+    c->cl_smem[k] = 0;
+    c->cl_lcap[k] = 0;
+  }
+  TRY(cluster_setup(c));
+  if (c->form == 1 && !cluster_form_usable(c)) c->form = 0;
+  CK(cudaStreamSynchronize(c->st));
+  return check_device_error(c);
+}
+
+int vcsgc_set_schedule(void* ctx, int32_t kind, const int32_t* sched) {
+  VCSGC_TRACE("vcsgc_set_schedule");
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || !sched) return VCSGC_ERR_INVALID_ARG;
+  return reschedule(c, kind, sched);
+}
+
+// In-memory snapshot of a rigid single-lattice chain: species, running
+// states, step base.  Restoring it makes the chain continue as if the steps
+// since the snapshot had not been taken (the schedule is not part of it).
+struct Snap {
+  std::vector<uint8_t> types;
+  std::vector<RepState> rs;
+  long long h_base = 0;
+};
+
+static int snap_take(Ctx* c, Snap& s) {
+  TRY(sync_bytes(c, -1));
+  TRY(refresh_energies(c));
+  s.types.resize((size_t)c->R * c->N);
+  s.rs.resize(c->R);
+  for (int r = 0; r < c->R; ++r)
+    CK(cudaMemcpyAsync(s.types.data() + (size_t)r * c->N, c->rep_types[r], c->N, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(s.rs.data(), c->rs, sizeof(RepState) * c->R, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  s.h_base = c->h_base;
+  return check_device_error(c);
+}
+
+static int snap_restore(Ctx* c, const Snap& s) {
+  TRY(flush(c));
+  c->h_base = s.h_base;
+  c->base_lag = 0;
+  if (c->fast) {
+    LatCtl ctl{s.h_base};
+    CK(cudaMemcpyAsync(c->lat.ctl, &ctl, sizeof(LatCtl), cudaMemcpyHostToDevice, c->st));
+    // no accumulated dn or accepts of any step: the next step starts afresh
+    CK(cudaMemsetAsync(c->lat.acc, 0, sizeof(StepAcc) * c->R * 3, c->st));
+    launch_colour_table(c->lat, c->st);
+    CK(cudaGetLastError());
+  } else {
+    CK(cudaMemsetAsync(c->acc, 0, sizeof(StepAcc) * c->R, c->st));
+  }
+  for (int r = 0; r < c->R; ++r) TRY(vcsgc_set_types(c, r, s.types.data() + (size_t)r * c->N));
+  CK(cudaMemcpyAsync(c->rs, s.rs.data(), sizeof(RepState) * c->R, cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->energy_stale = false;
+  drop_graph(c);
+  return check_device_error(c);
+}
+
+int vcsgc_autotune_schedule(void* ctx, int32_t n_cand, const int32_t* kinds, const int32_t* scheds, int64_t sweeps,
+                            double* scores, int32_t* best) {
+  VCSGC_TRACE("vcsgc_autotune_schedule");
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c || n_cand < 1 || !kinds || !scheds || sweeps < 1 || !scores || !best) return VCSGC_ERR_INVALID_ARG;
+  if (c->kind != 0 || !c->subs.empty() || c->multi || c->no_fast)
+    return fail(c, VCSGC_ERR_STATE, "schedule autotune: rigid single-lattice contexts only");
+  // every candidate starts from the same state; the chain resumes from it
+  Snap s0;
+  TRY(snap_take(c, s0));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int bi = -1;
+  std::vector<vcsgc_observables> o0(c->R), o1(c->R);
+  for (int k = 0; k < n_cand; ++k) {
+    scores[k] = -1.0;
+    if (reschedule(c, kinds[k], scheds + 6 * k) != VCSGC_OK) continue;  // a schedule these lattices refuse
+    TRY(snap_restore(c, s0));
+    TRY(run_steps(c, sweeps * c->steps_per_sweep));                        // settle under the candidate
+    TRY(vcsgc_observables_all(c, o0.data()));
+    CK(cudaEventRecord(e0, c->st));
+    TRY(run_steps(c, sweeps * c->steps_per_sweep));
+    CK(cudaEventRecord(e1, c->st));
+    CK(cudaEventSynchronize(e1));
+    TRY(vcsgc_observables_all(c, o1.data()));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    long long flips = 0;
+    for (int r = 0; r < c->R; ++r) flips += o1[r].flips - o0[r].flips;
+    scores[k] = (double)flips / (ms * 1e-3);
+    if (bi < 0 || scores[k] > scores[bi]) bi = k;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->err.clear();
+  if (bi < 0) return fail(c, VCSGC_ERR_SCHEDULE, "schedule autotune: no candidate schedule applies");
+  TRY(reschedule(c, kinds[bi], scheds + 6 * bi));
+  TRY(snap_restore(c, s0));
+  *best = bi;
+  return VCSGC_OK;
+}
+
 int vcsgc_set_launch(void* ctx, int32_t form, int32_t block, int32_t variant) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return VCSGC_ERR_INVALID_ARG;

@@ -76,7 +76,7 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_multi_get_types", "vcsgc_multi_set_types", "vcsgc_multi_delta_e", "vcsgc_multi_energy",
            "vcsgc_multi_last_error", "vcsgc_multi_free", "vcsgc_set_ensemble", "vcsgc_md_state",
            "vcsgc_minimize", "vcsgc_save", "vcsgc_load", "vcsgc_set_launch", "vcsgc_get_launch",
-           "vcsgc_philox", "vcsgc_cluster_sizes"]
+           "vcsgc_philox", "vcsgc_cluster_sizes", "vcsgc_set_schedule", "vcsgc_autotune_schedule"]
 
 
 def lib():
@@ -146,6 +146,8 @@ def lib():
             "vcsgc_get_launch": (I32, [P, P, P, P]),
             "vcsgc_philox": (I32, [P, P, P, I64]),
             "vcsgc_cluster_sizes": (I32, [P, P]),
+            "vcsgc_set_schedule": (I32, [P, I32, P]),
+            "vcsgc_autotune_schedule": (I32, [P, I32, P, P, I64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -558,6 +560,23 @@ class Context:
         """Launch shape of the fused colour step (vcsgc_set_launch): form 0
         with variant = row prefetch, form 1 with variant = CTAs per cluster."""
         _check(lib().vcsgc_set_launch(self.h, int(form), int(block), int(variant)), self.h)
+
+    def set_schedule(self, kind, sched):
+        """Switch the colour schedule between colour steps (vcsgc_set_schedule)."""
+        sc = np.ascontiguousarray(sched, dtype=np.int32)
+        assert sc.shape == (6,)
+        _check(lib().vcsgc_set_schedule(self.h, int(kind), _ptr(sc)), self.h)
+
+    def autotune_schedule(self, candidates, sweeps=2):
+        """candidates: [(kind, sched6), ...]; returns (best index, accepted
+        flips per second of each candidate)."""
+        kinds = np.ascontiguousarray([k for k, _ in candidates], dtype=np.int32)
+        sc = np.ascontiguousarray([list(s) for _, s in candidates], dtype=np.int32).reshape(-1)
+        scores = np.zeros(len(candidates))
+        best = C.c_int32()
+        _check(lib().vcsgc_autotune_schedule(self.h, len(candidates), _ptr(kinds), _ptr(sc), int(sweeps),
+                                             _ptr(scores), C.byref(best)), self.h)
+        return best.value, scores
 
     def cluster_sizes(self):
         """Cluster sizes of the cluster-resident form these lattices allow."""
