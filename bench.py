@@ -96,6 +96,15 @@ def prescan(V, stream, local):
             "seconds": time.perf_counter() - t0}
 
 
+def _recipe_point(pre, dmu_s, sweeps, trials_per_step, ms, reps):
+    return {"prescan": pre,
+            "recipe_dmu_S": {"dmu0_eV": dmu_s,
+                             "label": "dmu0 = dmu_S, the two-phase coexistence value of steps (i) and (iii) of "
+                                      "Sec. III C, on the same supersaturated start", "sweeps": sweeps,
+                             "trial_moves_per_s": trials_per_step * sweeps / (ms * 1e-3), "replicas": reps,
+                             "accepted_flips_per_s": sum(x["accepted_flips_per_s"] for x in reps)}}
+
+
 def balanced_dmu(V, stream, local):
     """The driving force at which the first composite move of the random 2 %
     start has no expected drift (recipe.balanced_dmu0 on the dE of every
@@ -773,6 +782,8 @@ def main():
     ap.add_argument("--md-box", type=float, default=250.0, help="nanocrystal box (A) for --md-only")
     ap.add_argument("--multi-only", action="store_true", help="only the multicomponent measurement (profiling)")
     ap.add_argument("--headline-only", action="store_true", help="only the headline and its sampling points")
+    ap.add_argument("--no-recipe", action="store_true",
+                    help="skip the SGC pre-scan and the dmu_S point (profiling of the headline)")
     ap.add_argument("--launch", default=None,
                     help="FORM,BLOCK,VARIANT: a fixed launch shape of the colour step instead of the autotuner's")
     args = ap.parse_args()
@@ -805,8 +816,8 @@ def main():
     stream = torch.cuda.Stream()
     # parameter recipe (Sec. III C): dmu_S from the SGC pre-scan; the balanced
     # driving force of the random start as a second, labelled point
-    pre = prescan(V, stream, local)
-    dmu_s = pre["dmu_S_eV"]
+    pre = None if args.no_recipe else prescan(V, stream, local)
+    dmu_s = None if args.no_recipe else pre["dmu_S_eV"]
     dmu_bal = balanced_dmu(V, stream, local)
     lat, types, tab, phi, c0 = workload(dmu_bal)
     seeds = rank_seeds(rank)
@@ -889,30 +900,25 @@ def main():
                             "note": "the gather form's list bytes; this kernel reads no list (measured DRAM ~0)"},
             "step_latency_floor_us": STEP_LATENCY_FLOOR_US}
 
-    # the second point: the recipe's coexistence driving force dmu_S, which
-    # freezes this supersaturated start (every isolated B dissolves locally;
-    # the composite moves' dn lies far outside the constraint's width)
-    ctx_b = headline_context(RC.phi_grid(dmu_s, KAPPA, T_K, c0))
-    ctx_b.set_launch(*launch)
-    ctx_b.sweep(args.warmup)
-    n_b = min(args.steps, 20)
-    ob0 = ctx_b.observables_all()
-    ms_b = timed_sweeps(torch, stream, ctx_b, n_b, flush)
-    ob1 = ctx_b.observables_all()
-    ctx_b.close()
     recipe_out = {
-        "prescan": pre,
         "headline": {"dmu0_eV": dmu_bal,
                      "label": "dmu0 = the driving force of the metastable start (Eq. c0's optimality condition on "
                               "the state the run starts from): the first composite move has no expected drift",
-                     "replicas": reps, "accepted_flips_per_s": sum(x["accepted_flips_per_s"] for x in reps)},
-        "recipe_dmu_S": {"dmu0_eV": dmu_s,
-                         "label": "dmu0 = dmu_S, the two-phase coexistence value of steps (i) and (iii) of "
-                                  "Sec. III C, on the same supersaturated start", "sweeps": n_b,
-                         "trial_moves_per_s": trials_per_step * n_b / (ms_b * 1e-3),
-                         "replicas": sampling(ob0, ob1, ms_b * 1e-3)}}
-    recipe_out["recipe_dmu_S"]["accepted_flips_per_s"] = sum(
-        x["accepted_flips_per_s"] for x in recipe_out["recipe_dmu_S"]["replicas"])
+                     "replicas": reps, "accepted_flips_per_s": sum(x["accepted_flips_per_s"] for x in reps)}}
+    if not args.no_recipe:
+        # the second point: the recipe's coexistence driving force dmu_S,
+        # which freezes this supersaturated start (every isolated B dissolves
+        # locally; the composite moves' dn lies far outside the constraint's
+        # width)
+        ctx_b = headline_context(RC.phi_grid(dmu_s, KAPPA, T_K, c0))
+        ctx_b.set_launch(*launch)
+        ctx_b.sweep(args.warmup)
+        n_b = min(args.steps, 20)
+        ob0 = ctx_b.observables_all()
+        ms_b = timed_sweeps(torch, stream, ctx_b, n_b, flush)
+        ob1 = ctx_b.observables_all()
+        ctx_b.close()
+        recipe_out.update(_recipe_point(pre, dmu_s, n_b, trials_per_step, ms_b, sampling(ob0, ob1, ms_b * 1e-3)))
 
     # end to end through the C ABI with host buffers: every replica's species
     # up from pinned memory, one sweep, observables and species down, every step
