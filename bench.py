@@ -679,6 +679,77 @@ def multi_bench(V, torch, stream, local, sweeps=10, warmup=2):
     return out
 
 
+def reembed_da_bench(V, torch, stream, local, sweeps=10, equil=400, train_steps=3000, batch=4096, lr=2e-3):
+    """Delayed acceptance on the re-embedding workload (80^3 x 8 replicas,
+    f_B = 1.25 f_A, phi = -2.2 eV, kappa = 100, 1200 K, c0 = 5 %, period-4
+    sublattice; the binary context runs the two-species multicomponent
+    kernels).  The plain rule takes the chains from the random start through
+    `equil` sweeps; a surrogate is trained on the descriptors and exact
+    targets of that state; then the plain rule and delayed acceptance are
+    timed from the same state.  Reports the step time of each, the trial
+    moves and accepted flips per second, the stage-1 pass and stage-2
+    acceptance fractions, and the energy per atom along the equilibration."""
+    lat = I.bcc_lattice(CELLS, CELLS, CELLS)
+    tab = I.eam_tables(I.multi_eam_params(2, dens_scale=(1.0, 1.25)))
+    t = np.stack([I.random_types(lat.n, int(0.05 * lat.n), seed=8200 + r) for r in range(N_PHI)])
+    seeds = np.arange(N_PHI, dtype=np.uint64) + np.uint64(8300)
+    g = V.Context(lat, t.reshape(-1), tab, -2.2, 100.0, 1200.0, c0=0.05, schedule=V.SCHED_SUBLATTICE,
+                  sched=(4, 4, 4), n_replicas=N_PHI, seed_r=seeds, stream=stream, device=local)
+
+    def mean_obs():
+        o = [g.observables(r) for r in range(N_PHI)]
+        return o, float(np.mean([q["energy_per_atom"] for q in o])), float(np.mean([q["c"] for q in o]))
+
+    trace, done = [], 0
+    for k in sorted({k for k in (0, 50, 100, 200, equil // 2, equil) if k <= equil}):
+        g.sweep(k - done)
+        done = k
+        _, e, c = mean_obs()
+        trace.append({"sweeps": k, "energy_per_atom": e, "c": c})
+    torch.cuda.synchronize()
+    X, Y = g.features()
+    s = V.Surrogate(I.mlp_init(7, out_bias=float(Y.mean())), stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = s.train(X, Y, batch=batch, steps=train_steps, lr=lr, seed=19)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    pred = s.forward(X[: 1 << 20])
+    rmse = float(torch.sqrt(((pred - Y[: 1 << 20]) ** 2).mean()))
+    y_std = float(Y.std())
+    del X, Y, pred
+    start = [g.types(r) for r in range(N_PHI)]
+    out = {"workload": "80^3 x 8 replicas, f_B = 1.25 f_A, phi -2.2 eV, kappa 100, 1200 K, c0 5 %, "
+                       "period-4 sublattice (64,000 trials per colour step)",
+           "equilibration": trace, "train_s": t_train, "train_steps": train_steps,
+           "loss_first_last": [float(hist[:10].mean()), float(hist[-100:].mean())],
+           "target_rmse_eV": rmse, "target_std_eV": y_std}
+    for mode in ("plain", "delayed"):
+        for r in range(N_PHI):
+            g.set_types(start[r], r)
+        g.set_surrogate(s if mode == "delayed" else None)
+        g.sweep(2)
+        o0, _, _ = mean_obs()
+        ms = timed_sweeps(torch, stream, g, sweeps)
+        o1, e, c = mean_obs()
+        trials = sum(o1[r]["trials"] - o0[r]["trials"] for r in range(N_PHI))
+        s1 = sum(o1[r]["stage1_accepts"] - o0[r]["stage1_accepts"] for r in range(N_PHI))
+        acc = sum(o1[r]["local_accepts"] - o0[r]["local_accepts"] for r in range(N_PHI))
+        flips = sum(o1[r]["flips"] - o0[r]["flips"] for r in range(N_PHI))
+        res = {"us_per_step": ms * 1e3 / (sweeps * g.steps_per_sweep),
+               "trial_moves_per_s": N_PHI * lat.n * sweeps / (ms * 1e-3),
+               "accepted_flips_per_s": flips / (ms * 1e-3),
+               "acc_local": acc / trials, "energy_per_atom": e, "c": c}
+        if mode == "delayed":
+            res["stage1_pass"] = s1 / trials
+            res["stage2_accept"] = acc / max(s1, 1)
+        out[mode] = res
+    out["speedup"] = out["plain"]["us_per_step"] / out["delayed"]["us_per_step"]
+    g.close()
+    s.close()
+    return out
+
+
 def schedule_bench(V, torch, stream, local, dmu0, sweeps=2):
     """The schedule autotuner (vcsgc_autotune_schedule) on the headline
     workload: the period-4 sublattice (8,000 trials per replica per colour
@@ -781,6 +852,9 @@ def main():
     ap.add_argument("--md-only", action="store_true", help="only the MD measurement (profiling)")
     ap.add_argument("--md-box", type=float, default=250.0, help="nanocrystal box (A) for --md-only")
     ap.add_argument("--multi-only", action="store_true", help="only the multicomponent measurement (profiling)")
+    ap.add_argument("--da-reembed-only", action="store_true",
+                    help="only delayed acceptance on the re-embedding workload (profiling)")
+    ap.add_argument("--da-equil", type=int, default=400, help="plain sweeps before the surrogate is trained")
     ap.add_argument("--headline-only", action="store_true", help="only the headline and its sampling points")
     ap.add_argument("--no-recipe", action="store_true",
                     help="skip the SGC pre-scan and the dmu_S point (profiling of the headline)")
@@ -812,6 +886,10 @@ def main():
     if args.multi_only:
         print(json.dumps(multi_bench(V, torch, torch.cuda.Stream(), local, sweeps=args.steps,
                                      warmup=args.warmup)), flush=True)
+        return 0
+    if args.da_reembed_only:
+        print(json.dumps(reembed_da_bench(V, torch, torch.cuda.Stream(), local, sweeps=args.steps,
+                                          equil=args.da_equil)), flush=True)
         return 0
     stream = torch.cuda.Stream()
     # parameter recipe (Sec. III C): dmu_S from the SGC pre-scan; the balanced

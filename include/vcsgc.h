@@ -393,7 +393,10 @@ int vcsgc_neighbour_list_noalloc(int64_t n, const double* d_x, const double* d_y
  * in shell s = 1..5; nb[s] = sum over the 8 first-shell neighbours k of i of
  * the B sites other than i in shell s of k.  Only the rigid BCC lattice with
  * r_c between sqrt(3) a and sqrt(19) a / 2 (five shells: 8, 6, 12, 24, 8
- * sites) in the fused form has it.
+ * sites) has it: in the fused form, and, with species-dependent densities,
+ * in a context that runs its steps through the two-species multicomponent
+ * kernels (vcsgc_init; the calls go to vcsgc_multi_set_surrogate and
+ * vcsgc_multi_features).
  *
  * Surrogate network (VCSGC_MLP_NPARAM FP32 parameters, in this order):
  * W1[64][10], b1[64], W2[64][64], b2[64], w3[64], b3.  x_c = count_c / max_c
@@ -401,7 +404,7 @@ int vcsgc_neighbour_list_noalloc(int64_t n, const double* d_x, const double* d_y
  * h1 = SiLU(z1); z2 = W2 h1 + b2; h2 = SiLU(z2); g = w3 . h2 + b3 (eV).
  * On the GPU x, W1, W2 and h1 enter the tensor cores as BF16 with FP32
  * accumulation, and SiLU(z) = z (1 + tanh(z / 2)) / 2 uses the hardware
- * tanh approximation. */
+ * tanh approximation on half-precision arguments. */
 #define VCSGC_MLP_IN 10
 #define VCSGC_MLP_NPARAM 4929
 
@@ -409,8 +412,8 @@ int vcsgc_neighbour_list_noalloc(int64_t n, const double* d_x, const double* d_y
  * current (committed) species.  DEVICE outputs owned by the caller:
  * d_X[rows][10] (float, raw counts own[1..5], nb[1..5]) and d_Y[rows]
  * (float, E(i = B) - E(i = A) in eV), rows = sum of the replica sizes,
- * replica after replica in site order.  Errors: STATE when the context is
- * not a fused rigid lattice with the five-shell neighbourhood; CUDA. */
+ * replica after replica in site order.  Errors: STATE when the context has
+ * neither form of the five-shell rigid lattice above; CUDA. */
 int vcsgc_features(void* ctx, float* d_X, float* d_Y);
 
 /* A surrogate network on the current device: FP32 master parameters (copied
@@ -550,6 +553,7 @@ typedef struct {
   double kappa_p[4];      /* eV */
   double dmu0[4];         /* eV */
   double sweeps;          /* trials / N */
+  int64_t stage1_accepts; /* delayed acceptance: trials that passed stage 1 */
 } vcsgc_multi_obs;
 
 /* Create a K-species context of n_replicas copies of one rigid lattice
@@ -586,6 +590,23 @@ int vcsgc_multi_set_types(void* m, int32_t r, const uint8_t* in);
 int vcsgc_multi_delta_e(void* m, int32_t r, const int64_t* sites, const uint8_t* to, int64_t n, double* out);
 /* Full energy of replica r from its species and densities (eV). */
 int vcsgc_multi_energy(void* m, int32_t r, double* out);
+/* Delayed acceptance (the two stages of vcsgc_set_surrogate) for K = 2 with
+ * species-dependent densities on the five-shell table (the screened form):
+ * stage 1 on the surrogate's g from the descriptor, stage 2 on the exact
+ * dE - s g (FP32-screened, FP64 where the bound cannot decide).  The
+ * descriptor comes from per-site B counts by shell (4 bytes per site),
+ * built from the species when delayed acceptance is turned on or the
+ * species were set, and updated by the commit of every accepted step.  The
+ * context keeps a copy of the surrogate's current weights; mlp NULL turns
+ * it off.  Errors: STATE (K != 2 or not the screened form), INVALID_ARG,
+ * NOMEM, CUDA. */
+int vcsgc_multi_set_surrogate(void* m, void* mlp);
+/* Descriptors and exact targets of every site of every replica (the rows
+ * and units of vcsgc_features: DEVICE d_X[R N][10] raw counts, d_Y[R N]
+ * E(i = B) - E(i = A) in eV, replica after replica in site order), from the
+ * per-site counts and the FP64 dE.  Synchronises.  Errors: as
+ * vcsgc_multi_set_surrogate, and the device error bits. */
+int vcsgc_multi_features(void* m, float* d_X, float* d_Y);
 const char* vcsgc_multi_last_error(void* m);
 void vcsgc_multi_free(void* m);
 

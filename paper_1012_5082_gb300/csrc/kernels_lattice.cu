@@ -208,18 +208,11 @@ __device__ __forceinline__ void lattice_nb_counts(const LatArgs& a, const LatGeo
   nb[0] -= 8 * ti;
 }
 
-// The ten scaled descriptor inputs as BF16 pairs (p[4] = inputs 8, 9)
+// The ten scaled descriptor inputs as BF16 pairs (mlp_pairs)
 template <int NS>
 __device__ __forceinline__ void descriptor_pairs(const int (&cnt)[NS], const int (&nb)[NS], uint32_t (&p)[5]) {
   static_assert(NS == 5, "the descriptor has five shells");
-  float x[10];
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    x[s] = (float)cnt[s] * mlp_in_scale(s);
-    x[5 + s] = (float)nb[s] * mlp_in_scale(5 + s);
-  }
-#pragma unroll
-  for (int c = 0; c < 5; ++c) p[c] = bf16x2(x[2 * c], x[2 * c + 1]);
+  mlp_pairs(cnt, nb, p);
 }
 
 // The same counts in two phases: the raw words of the NR rows (and of the

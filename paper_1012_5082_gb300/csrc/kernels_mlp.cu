@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(32 * TRAIN_WARPS)
     // h1 tile (the same BF16 values the forward used as the layer-2 operand)
 #pragma unroll
     for (int nn = 0; nn < 8; ++nn) {
-      Th[(g * MLP_H + 8 * nn + 2 * t) >> 1] = bf16x2(silu(z1[nn][0]), silu(z1[nn][1]));
-      Th[((g + 8) * MLP_H + 8 * nn + 2 * t) >> 1] = bf16x2(silu(z1[nn][2]), silu(z1[nn][3]));
+      Th[(g * MLP_H + 8 * nn + 2 * t) >> 1] = silu_bf16x2(z1[nn][0], z1[nn][1]);
+      Th[((g + 8) * MLP_H + 8 * nn + 2 * t) >> 1] = silu_bf16x2(z1[nn][2], z1[nn][3]);
     }
     const float e0 = v0 ? ylo - Y[r0] : 0.0f;
     const float e1 = v1 ? yhi - Y[r1] : 0.0f;
@@ -172,7 +172,9 @@ __global__ void __launch_bounds__(32 * TRAIN_WARPS)
       for (int c = 0; c < 2; ++c) {
         const int col = 8 * nn + 2 * t + c;
         const float za = z2[nn][c], zb = z2[nn][2 + c];
-        const float gw3 = sum_rows(d3a * silu(za) + d3b * silu(zb));
+        float ha, hb;
+        silu2(za, zb, ha, hb);
+        const float gw3 = sum_rows(d3a * ha + d3b * hb);
         if (g == 0) atomicAdd(&s_grad[MLP_OFF_W3 + col], gw3);
         const float wc = __ldg(w3 + col);
         d2[nn][c] = d3a * wc * dsilu(za);

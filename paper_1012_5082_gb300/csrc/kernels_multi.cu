@@ -372,6 +372,86 @@ __device__ float multi_screen_bcc5(const MultiArgs& a, const long long* sDq, con
   return (pair + own) + re;
 }
 
+// The same FP32 dE by a group of MK_GROUP lanes of one warp (delayed
+// acceptance, where only the block's stage-1 passes need it): lane gl of
+// the group takes neighbours gl, gl + MK_GROUP, ... of the five-shell table
+// and lane 0 the own-site term; the partial sums are combined by shuffles
+// inside the group, so every lane of the group returns the trial's values.
+// The partial sums change the order of the float additions only: at most 7
+// sequential and 3 pairwise steps, well inside the 2^-18 sum(|terms|) of
+// the bound.  gw: the group's [30] scratch of wrapped cell offsets (the
+// layout of multi_screen_bcc5's sw); has: the group holds a trial.  Must be
+// called by all 32 lanes.
+constexpr int MK_GROUP = 8;
+
+__device__ float multi_screen_group(const MultiArgs& a, const long long* sDq, const float* sDfs, int* gw,
+                                    const int* scode, int r, int i, int cx, int cy, int cz, int ta, int tb, int gl,
+                                    bool has, long long* pq_out, float* err, bool* in) {
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  const float2* rf = a.rf + (long long)r * a.rf_n;
+  const int K = a.K;
+  const int rrow = a.qx * a.rf_q;
+  const int rplane = a.nz * a.ny * rrow;
+  for (int q = gl; has && q < 5; q += MK_GROUP) {
+    const int dd = q - 2;
+    const int X = mk_wrap(cx + dd, a.nx), xq = X / a.qx;
+    const int Y = mk_wrap(cy + dd, a.ny), Z = mk_wrap(cz + dd, a.nz);
+    gw[q] = 2 * X;
+    gw[5 + q] = 2 * a.nx * Y;
+    gw[10 + q] = 2 * a.nx * a.ny * Z;
+    gw[15 + q] = (X - xq * a.qx) * a.rf_q + xq;
+    gw[20 + q] = rrow * Y;
+    gw[25 + q] = rrow * a.ny * Z;
+  }
+  __syncwarp();
+  long long pq = 0;
+  float re = 0.0f, ab = 0.0f, own = 0.0f;
+  bool ok = true;
+  if (has) {
+    const float* Df = sDfs + (ta * K + tb);
+    const long long* Dq = sDq + (ta * K + tb) * K;
+#pragma unroll
+    for (int m = 0; m < (MK_BCC5_N + MK_GROUP - 1) / MK_GROUP; ++m) {
+      const int k = gl + MK_GROUP * m;
+      if (k < MK_BCC5_N) {
+        const int dc = scode[k];
+        const int ix = dc & 7, iy = (dc >> 3) & 7, iz = (dc >> 6) & 7, bb = (dc >> 9) & 1, sh = dc >> 10;
+        const int j = gw[ix] + gw[5 + iy] + gw[10 + iz] + bb;
+        const int jr = gw[15 + ix] + gw[20 + iy] + gw[25 + iz] + (bb ? rplane : 0);
+        const int t = ty[j];
+        const float2 v = rf[jr];
+        pq += Dq[sh * K * K * K + t];
+        const float x1 = v.x + Df[sh * K * K];
+        ok &= emb32_in(a, v.x) & emb32_in(a, x1);
+        const float d = emb32_val(a, t, x1) - v.y;
+        re += d;
+        ab += fabsf(d);
+      }
+    }
+    if (gl == 0) {
+      const float2 ri = rf[gw[17] + gw[22] + gw[27] + (i & 1) * rplane];
+      ok &= emb32_in(a, ri.x);
+      own = emb32_val(a, tb, ri.x) - ri.y;
+    }
+  }
+#pragma unroll
+  for (int o = MK_GROUP / 2; o > 0; o >>= 1) {
+    pq += __shfl_xor_sync(0xffffffffu, pq, o);
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    ab += __shfl_xor_sync(0xffffffffu, ab, o);
+    own += __shfl_xor_sync(0xffffffffu, own, o);
+  }
+  const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+  const int lane = threadIdx.x & 31;
+  ok = ((bad >> (lane & ~(MK_GROUP - 1))) & ((1u << MK_GROUP) - 1u)) == 0u;
+  const float pair = __ll2float_rn(pq) * a.qscale32;
+  *pq_out = pq;
+  *in = ok;
+  *err = fmaf((float)(2 * MK_BCC5_N + 2), a.emb_err,
+              fmaf(3.814697265625e-06f, ab, 4.76837158203125e-07f * (fabsf(pair) + fabsf(own) + fabsf(re))));
+  return (pair + own) + re;
+}
+
 // lane's share of the FP64 embedding part (58 re-embeddings and the own
 // change) of the dE of site i from ta to tb: neighbours lane and lane + 32,
 // and the two own-site terms on lanes 26 and 27 of the second pass
@@ -426,12 +506,53 @@ __device__ __forceinline__ int multi_target(const MultiArgs& a, const MRepParams
   return (ta + 1 + (int)below64(w6.x, w6.y, (uint64_t)(a.K - 1))) % a.K;
 }
 
+// Surrogate descriptor of the site in cell (cx, cy, cz), basis b, species ti
+// from the per-site shell counts: own[s] = B sites in shell s of the site;
+// nb[s] = B sites other than the site itself in shell s of its 8 first-shell
+// neighbours k, summed (the site is in shell 1 of each k).  The neighbours of
+// a corner site (b = 0) are the body centres of the cells at offsets
+// {-1, 0}^3, those of a body centre the corners at {0, 1}^3.  Eight 6-bit
+// fields summed stay below 2^12: fields 0, 2, 4 and 1, 3 are summed in two
+// words with 12 bits between fields.
+__device__ __forceinline__ void multi_descriptor(const MultiArgs& a, int r, int cx, int cy, int cz, int b, int ti,
+                                                 int (&own)[5], int (&nb)[5]) {
+  const uint32_t* nc = a.nbc + (long long)r * a.rf_n;
+  const long long row = (long long)a.qx * a.rf_q;
+  const int lo = b ? 0 : -1;
+  int xp[2], yv[2], zv[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int X = mk_wrap(cx + lo + q, a.nx), xq = X / a.qx;
+    xp[q] = (X - xq * a.qx) * a.rf_q + xq;
+    yv[q] = mk_wrap(cy + lo + q, a.ny);
+    zv[q] = mk_wrap(cz + lo + q, a.nz);
+  }
+  const uint32_t w0 = nc[((long long)(b * a.nz + cz) * a.ny + cy) * row + (b ? xp[0] : xp[1])];
+  const int nbb = 1 - b;
+  uint32_t xs = 0u, ys = 0u;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const uint32_t w = nc[((long long)(nbb * a.nz + zv[q >> 2]) * a.ny + yv[(q >> 1) & 1]) * row + xp[q & 1]];
+    xs += w & 0x3F03F03Fu;
+    ys += (w >> 6) & 0x0003F03Fu;
+  }
+#pragma unroll
+  for (int s = 0; s < 5; ++s) own[s] = (int)((w0 >> (6 * s)) & 63u);
+  nb[0] = (int)(xs & 0xFFFu) - 8 * ti;
+  nb[1] = (int)(ys & 0xFFFu);
+  nb[2] = (int)((xs >> 12) & 0xFFFu);
+  nb[3] = (int)(ys >> 12);
+  nb[4] = (int)(xs >> 24);
+}
+
 // MODE 0: no re-embedding; 1: re-embedding, FP64 dE (any neighbour table);
 // 2: re-embedding, five-shell table, FP32 screen (the dE sum of an accepted
-// step is then taken by the commit launch, in FP64)
+// step is then taken by the commit launch, in FP64); 3: mode 2 with delayed
+// acceptance (K = 2)
 template <int MODE>
 __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
   constexpr bool REEMBED = MODE != 0;
+  constexpr bool SCREEN = MODE >= 2;
   __shared__ double sV[MK_MAX_SH * MK_MAX * MK_MAX];
   __shared__ double sFd[MK_MAX_SH * MK_MAX];
   __shared__ double sDF[MK_MAX * MK_MAX];
@@ -439,20 +560,34 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
   __shared__ float sDfs[5 * MK_MAX * MK_MAX];
   // screened form: per-thread wrapped cell offsets and the block's
   // neighbour descriptors (unused otherwise)
-  __shared__ int sw[MODE == 2 ? 30 * MK_BLOCK : 1];
-  __shared__ int scode[MODE == 2 ? MK_BCC5_N : 1];
+  __shared__ int sw[SCREEN ? 30 * MK_BLOCK : 1];
+  __shared__ int scode[SCREEN ? MK_BCC5_N : 1];
+  // delayed acceptance: the block's stage-1 passes, queued for the exact
+  // stage (site and cell; species, g, owner thread and trial), and the
+  // owners' stage-2 decisions
+  __shared__ int4 s_qa[MODE == 3 ? MK_BLOCK : 1];
+  __shared__ int4 s_qb[MODE == 3 ? MK_BLOCK : 1];
+  __shared__ int s_dec[MODE == 3 ? MK_BLOCK : 1];
+  __shared__ int s_gw[MODE == 3 ? MK_BLOCK / MK_GROUP : 1][30];
+  __shared__ uint64_t s_u2[MODE == 3 ? MK_BLOCK : 1];
+  __shared__ int s_nq;
   __shared__ uint4 s_wc;
   __shared__ int s_col[4];
   __shared__ int s_red[MK_BLOCK / 32][MK_MAX + 1];
   __shared__ double s_de[MK_BLOCK / 32];
+  __shared__ int s_s1[MK_BLOCK / 32];
   __shared__ bool s_last;
+  // the global stage's inputs that no block of this step writes: the
+  // replica's running state and beta kappa_p, n0 per solute
+  __shared__ MRepState s_rs;
+  __shared__ double s_bk[MK_MAX], s_n0[MK_MAX];
   const int K = a.K;
   for (int q = threadIdx.x; q < a.n_sh * K * K; q += MK_BLOCK) sV[q] = a.V[q];
   for (int q = threadIdx.x; q < a.n_sh * K; q += MK_BLOCK) sFd[q] = a.Fd[q];
   if (!REEMBED && threadIdx.x < K * K) sDF[threadIdx.x] = a.dF[threadIdx.x];
   if (a.bcc5)
     for (int q = threadIdx.x; q < 5 * K * K * K; q += MK_BLOCK) sDq[q] = a.Dq[q];
-  if (MODE == 2)
+  if (SCREEN)
     for (int q = threadIdx.x; q < 5 * K * K; q += MK_BLOCK) {
       const int sh = q / (K * K), x = (q / K) % K, y = q % K;
       sDfs[q] = (float)(a.Fd[sh * K + y] - a.Fd[sh * K + x]);
@@ -471,11 +606,17 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
     s_col[1] = pc % a.qx;
     s_col[2] = (pc / a.qx) % a.qy;
     s_col[3] = pc / (a.qx * a.qy);
+    s_nq = 0;
+    s_rs = a.rs[r];
+  }
+  if (threadIdx.x < MK_MAX) {
+    s_bk[threadIdx.x] = p.beta * p.kappa_p[threadIdx.x];
+    s_n0[threadIdx.x] = p.n0[threadIdx.x];
   }
   __syncthreads();
   const uint4 wc = s_wc;
   const int c = s_col[0];
-  if constexpr (MODE == 2) {
+  if constexpr (SCREEN) {
     if (threadIdx.x < MK_BCC5_N) {
       const int k = threadIdx.x;
       scode[k] = (c & 1) ? mk_bcc5_desc<1>(k) : mk_bcc5_desc<0>(k);
@@ -503,15 +644,108 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
     const uint4 w = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_TRIAL),
                                   p.key);
     u53 = top53(w.z, w.w);
+    if constexpr (MODE == 3) {
+      // delayed acceptance: the stage-2 uniform too, while the previous
+      // launch drains
+      const uint4 w2 = philox4x32_10(
+          make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_STAGE2), p.key);
+      s_u2[threadIdx.x] = top53(w2.x, w2.y);
+    }
   }
   // screened form: launched after the previous step's commit with
   // programmatic dependent launch; the species, densities and this step's
   // accumulators are read after the wait (a no-op for an ordinary launch)
-  if constexpr (MODE == 2) pdl_wait();
-  if (d < a.D) {
+  if constexpr (SCREEN) pdl_wait();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int s1 = 0;
+  if constexpr (MODE == 3) {
+    // delayed acceptance (K = 2).  Stage 1 on the surrogate: every lane
+    // takes part in the network (lanes without a trial feed zeros).
+    uint32_t P[5] = {0u, 0u, 0u, 0u, 0u};
+    if (d < a.D) {
+      ta = a.types[(long long)r * a.N + site];
+      tb = 1 - ta;
+      int own[5], nb[5];
+      multi_descriptor(a, r, cx, cy, cz, b, ta, own, nb);
+      mlp_pairs(own, nb, P);
+    }
+    const float gnn = mlp_warp_eval(a.mlp, P);
+    if (d < a.D) {
+      // u < min{1, exp[-beta (s g + s dmu0)]}
+      const double sg = ta ? -1.0 : 1.0;
+      s1 = metropolis(p.beta * fma(sg, p.dmu0[1], sg * (double)gnn), u53, &tie) ? 1 : 0;
+    }
+    // the block's stage-1 passes in one queue; warp w takes entries
+    // 32 w .. 32 w + 31 for stage 2, so only ceil(passes / 32) warps
+    // gather the exact dE's neighbourhood
+    const unsigned pm = __ballot_sync(0xffffffffu, s1);
+    if (pm) {
+      int qb = 0;
+      if (lane == 0) qb = atomicAdd(&s_nq, __popc(pm));
+      qb = __shfl_sync(0xffffffffu, qb, 0);
+      if (s1) {
+        const int e = qb + __popc(pm & ((1u << lane) - 1u));
+        s_qa[e] = make_int4(site, cx, cy, cz);
+        s_qb[e] = make_int4(ta, __float_as_int(gnn), threadIdx.x, d);
+      }
+    }
+    __syncthreads();
+    const int nq = s_nq;
+    int tie2 = 0;
+    // stage 2: u2 < min{1, exp[-beta (dE - s g)]}, FP32-screened with the
+    // bound of the plain rule's screen (FP64 by the warp where it cannot
+    // decide).  Every group of MK_GROUP lanes takes one queued trial, so
+    // the block's 128 threads screen 16 trials at a time.
+    const int gl = threadIdx.x & (MK_GROUP - 1);
+    for (int q0 = 0; q0 < nq; q0 += MK_BLOCK / MK_GROUP) {
+      const int e = q0 + threadIdx.x / MK_GROUP;
+      const bool has = e < nq;
+      int4 qa = make_int4(0, 0, 0, 0), qo = make_int4(0, 0, 0, 0);
+      if (has) {
+        qa = s_qa[e];
+        qo = s_qb[e];
+      }
+      long long qpq = 0;
+      float err;
+      bool in;
+      const float e32 = multi_screen_group(a, sDq, sDfs, s_gw[threadIdx.x / MK_GROUP], scode, r, qa.x, qa.y, qa.z,
+                                           qa.w, qo.x, 1 - qo.x, gl, has, &qpq, &err, &in);
+      const bool lead = has && gl == 0;
+      int dec2 = 0;
+      uint64_t u2 = 0;
+      if (lead) {
+        u2 = s_u2[qo.z];
+        const float g = __int_as_float(qo.y);
+        const float cm = qo.x ? g : -g;  // -s g, exact
+        const float x32 = p.beta32 * (e32 + cm);
+        const float dx = p.beta32 * fmaf(4.76837158203125e-07f, fabsf(e32) + fabsf(cm), err) * 1.0001f +
+                         fabsf(x32) * 4.76837158203125e-07f;
+        dec2 = in ? screen32(x32, dx, u2) : -1;
+      }
+      unsigned open = __ballot_sync(0xffffffffu, lead && dec2 < 0);
+      while (open) {
+        const int src = __ffs(open) - 1;
+        open &= open - 1u;
+        const int si = __shfl_sync(0xffffffffu, qa.x, src);
+        const int sa = __shfl_sync(0xffffffffu, qo.x, src);
+        const double v = warp_sum(multi_emb_lane(a, sFd, r, si, sa, 1 - sa, lane));
+        if (lane == src) {
+          const double de64 = (double)qpq * a.qscale + v;
+          if (!isfinite(de64)) atomicOr(a.err, ERRF_NONFINITE);
+          const double sg = qo.x ? -1.0 : 1.0;
+          dec2 = metropolis(p.beta * (de64 - sg * (double)__int_as_float(qo.y)), u2, &tie2) ? 1 : 0;
+        }
+      }
+      if (lead) s_dec[qo.z] = dec2;
+      __syncwarp();  // the group's scratch is rewritten by the next round
+    }
+    __syncthreads();
+    acc = s1 ? s_dec[threadIdx.x] : 0;
+    tie += tie2;
+  } else if (d < a.D) {
     ta = a.types[(long long)r * a.N + site];
     tb = multi_target(a, p, step, d, ta);
-    if constexpr (MODE == 2) {
+    if constexpr (SCREEN) {
       float err;
       bool in;
       const float e32 = multi_screen_bcc5(a, sDq, sDfs, sw, scode, r, site, cx, cy, cz, ta, tb, &pq, &err, &in);
@@ -531,7 +765,6 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
       acc = metropolis(p.beta * (de + (p.dmu0[tb] - p.dmu0[ta])), u53, &tie) ? 1 : 0;
     }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if constexpr (MODE == 2) {
     // trials the screen left open: FP64 dE by the whole warp, one at a time
     unsigned open = __ballot_sync(0xffffffffu, dec < 0);
@@ -565,21 +798,25 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
     if (lane == 0) s_red[warp][al] = sv;
   }
   const int st = __reduce_add_sync(0xffffffffu, tie);
-  double sd = (MODE != 2 && acc) ? de : 0.0;
+  const int ss1 = MODE == 3 ? __reduce_add_sync(0xffffffffu, s1) : 0;
+  double sd = (!SCREEN && acc) ? de : 0.0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
   if (lane == 0) {
     s_red[warp][0] = st;
     s_de[warp] = sd;
+    s_s1[warp] = ss1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int tsum = 0;
+    int tsum = 0, s1sum = 0;
     double dsum = 0.0;
     for (int w = 0; w < MK_BLOCK / 32; ++w) {
       tsum += s_red[w][0];
       dsum += s_de[w];
+      s1sum += s_s1[w];
     }
+    if (s1sum) atomicAdd(&A->s1, s1sum);
     for (int al = 1; al < K; ++al) {
       int v = 0;
       for (int w = 0; w < MK_BLOCK / 32; ++w) v += s_red[w][al];
@@ -592,22 +829,28 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
   }
   __syncthreads();
   if (!s_last || threadIdx.x != 0) return;
-  // global stage (last block of the replica): every block's sums are visible
+  // global stage (last block of the replica): every block's sums are
+  // visible; they are loaded in one round
   __threadfence();
   const int nacc = __ldcg(&A->nacc);
-  MRepState s = a.rs[r];
+  const int ties = __ldcg(&A->ties);
+  const int s1v = MODE == 3 ? __ldcg(&A->s1) : 0;
+  const double sde = __ldcg(&A->sum_de);
+  int dn[MK_MAX];
+#pragma unroll
+  for (int al = 1; al < MK_MAX; ++al) dn[al] = al < K ? __ldcg(&A->dn[al]) : 0;
+  MRepState s = s_rs;
   s.trials += a.D;
   s.local_acc += nacc;
-  s.near_ties += __ldcg(&A->ties);
+  s.near_ties += ties;
+  s.s1_acc += s1v;
   int accept = 0;
   if (nacc > 0) {
     s.global_trials++;
-    int dn[MK_MAX];
     double Y = 0.0;
-    for (int al = 1; al < K; ++al) {
-      dn[al] = __ldcg(&A->dn[al]);
-      Y += p.beta * p.kappa_p[al] * (double)dn[al] * ((double)dn[al] + 2.0 * ((double)s.cnt[al] - p.n0[al]));
-    }
+#pragma unroll
+    for (int al = 1; al < MK_MAX; ++al)
+      if (al < K) Y += s_bk[al] * (double)dn[al] * ((double)dn[al] + 2.0 * ((double)s.cnt[al] - s_n0[al]));
     int gtie = 0;
     accept = metropolis(Y, top53(wc.z, wc.w), &gtie) ? 1 : 0;
     s.near_ties += gtie;
@@ -615,22 +858,26 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
       s.global_acc++;
       s.flips += nacc;
       long long d0 = 0;
-      for (int al = 1; al < K; ++al) {
-        s.cnt[al] += dn[al];
-        d0 += dn[al];
-      }
+#pragma unroll
+      for (int al = 1; al < MK_MAX; ++al)
+        if (al < K) {
+          s.cnt[al] += dn[al];
+          d0 += dn[al];
+        }
       s.cnt[0] -= d0;
-      s.energy += __ldcg(&A->sum_de);
+      s.energy += sde;
     }
   }
   A->accept = accept;
   A->done = 0u;
   s.steps++;
-  for (int al = 0; al < K; ++al) {
-    const double cc = (double)s.cnt[al] / (double)a.N;
-    s.sum_c[al] += cc;
-    s.sum_c2[al] += cc * cc;
-  }
+#pragma unroll
+  for (int al = 0; al < MK_MAX; ++al)
+    if (al < K) {
+      const double cc = (double)s.cnt[al] / (double)a.N;
+      s.sum_c[al] += cc;
+      s.sum_c2[al] += cc * cc;
+    }
   s.step++;
   a.rs[r] = s;
 }
@@ -649,6 +896,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit(MultiArgs a) {
     B->nacc = 0;
     B->ties = 0;
     B->accept = 0;
+    B->s1 = 0;
     B->sum_de = 0.0;
   }
   if (!A->accept) return;
@@ -696,6 +944,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
       B->nacc = 0;
       B->ties = 0;
       B->accept = 0;
+      B->s1 = 0;
       B->sum_de = 0.0;
     }
   }
@@ -730,7 +979,10 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
       const double nr = rho[j] + s_df[(h.w * K + ta) * K + tb];
       rho[j] = nr;
       const float r32 = (float)nr;
-      rf[multi_rfi(a, X, Y, Z, bb)] = make_float2(r32, emb32_val(a, ty[j], r32));
+      const long long q = multi_rfi(a, X, Y, Z, bb);
+      rf[q] = make_float2(r32, emb32_val(a, ty[j], r32));
+      // delayed acceptance (K = 2): the flipped site is in shell h.w of j
+      if (a.da) a.nbc[(long long)r * a.rf_n + q] += (uint32_t)(tb - ta) << (6 * h.w);
     } else {
       ty[e.x] = (uint8_t)tb;
       const int b = e.x & 1;
@@ -758,7 +1010,10 @@ void launch_multi_step(const MultiArgs& a, cudaStream_t st, bool after_step) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = after_step ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k_multi_propose<2>, a);
+    if (a.da)
+      cudaLaunchKernelEx(&cfg, k_multi_propose<3>, a);
+    else
+      cudaLaunchKernelEx(&cfg, k_multi_propose<2>, a);
     k_multi_commit_screen<<<4 * a.n_sm, MK_BLOCK, 0, st>>>(a);
   } else if (a.reembed) {
     k_multi_propose<1><<<grid, MK_BLOCK, 0, st>>>(a);
@@ -1078,6 +1333,56 @@ void launch_multi_delta_e(const MultiArgs& a, int r, const long long* sites, con
                           cudaStream_t st) {
   if (n <= 0) return;
   k_multi_delta_e<<<(n + 127) / 128, 128, 0, st>>>(a, r, sites, to, n, out);
+}
+
+// Delayed acceptance (K = 2): per-site B counts in the five shells from the
+// species of every replica (shell s at bit 6 s of nbc, laid out like rf)
+__global__ void k_multi_nbc(MultiArgs a) {
+  const int r = blockIdx.y;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const uint8_t* ty = a.types + (long long)r * a.N;
+  uint32_t w = 0u;
+  for (int k = 0; k < a.n_off; ++k) {
+    const int4 h = a.off[k];
+    w += (uint32_t)(ty[multi_nbr(a, (int)i, h)] == 1) << (6 * h.w);
+  }
+  const int3 p = multi_half(a, (int)i);
+  const int b = (int)(i & 1);
+  a.nbc[(long long)r * a.rf_n + multi_rfi(a, (p.x - b) >> 1, (p.y - b) >> 1, (p.z - b) >> 1, b)] = w;
+}
+
+void launch_multi_nbc(const MultiArgs& a, cudaStream_t st) {
+  const dim3 grid((unsigned)((a.N + 255) / 256), (unsigned)a.R);
+  k_multi_nbc<<<grid, 256, 0, st>>>(a);
+}
+
+// Surrogate descriptors X[r N + i][10] (raw counts from nbc) and targets
+// Y[r N + i] = E(i = B) - E(i = A) (FP64 dE with re-embedding, rounded to
+// float) of every site of every replica
+__global__ void k_multi_features(MultiArgs a, float* X, float* Y) {
+  const int r = blockIdx.y;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const int ti = a.types[(long long)r * a.N + i];
+  const int3 p = multi_half(a, (int)i);
+  const int b = (int)(i & 1);
+  int own[5], nb[5];
+  multi_descriptor(a, r, (p.x - b) >> 1, (p.y - b) >> 1, (p.z - b) >> 1, b, ti, own, nb);
+  const long long row = (long long)r * a.N + i;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    X[row * 10 + s] = (float)own[s];
+    X[row * 10 + 5 + s] = (float)nb[s];
+  }
+  const double de = multi_de<true>(a, a.V, a.Fd, r, (int)i, ti, 1 - ti);
+  if (!isfinite(de)) atomicOr(a.err, ERRF_NONFINITE);
+  Y[row] = (float)(ti == 0 ? de : -de);
+}
+
+void launch_multi_features(const MultiArgs& a, float* X, float* Y, cudaStream_t st) {
+  const dim3 grid((unsigned)((a.N + 127) / 128), (unsigned)a.R);
+  k_multi_features<<<grid, 128, 0, st>>>(a, X, Y);
 }
 
 }  // namespace vcsgc

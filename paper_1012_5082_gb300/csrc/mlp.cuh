@@ -5,6 +5,7 @@
 // first-shell neighbours' summed B counts in shells 1-5) scaled to
 // x = c / max_c, then z1 = W1 x + b1, h1 = SiLU(z1), z2 = W2 h1 + b2,
 // h2 = SiLU(z2), g = w3 . h2 + b3 (g predicts E(site = B) - E(site = A)).
+// SiLU(z) = z (1 + tanh(z / 2)) / 2 with the hardware tanh on half pairs.
 //
 // Tensor-core form: a warp evaluates a tile of 16 samples with mma.sync
 // m16n8k16 (BF16 operands, FP32 accumulation).  The inputs are padded from
@@ -68,6 +69,19 @@ __device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+// The ten scaled descriptor inputs as BF16 pairs (p[4] = inputs 8, 9): own
+// B counts in shells 1-5, then the first-shell neighbours' summed counts
+__device__ __forceinline__ void mlp_pairs(const int (&own)[5], const int (&nb)[5], uint32_t (&p)[5]) {
+  float x[10];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    x[s] = (float)own[s] * mlp_in_scale(s);
+    x[5 + s] = (float)nb[s] * mlp_in_scale(5 + s);
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) p[c] = bf16x2(x[2 * c], x[2 * c + 1]);
+}
+
 // D += A (16x16, row) * B (16x8, col); BF16 operands, FP32 accumulators
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint2 b) {
@@ -85,7 +99,34 @@ __device__ __forceinline__ float tanh_fast(float x) {
   return y;
 }
 __device__ __forceinline__ float sigm(float z) { return fmaf(0.5f, tanh_fast(0.5f * z), 0.5f); }
-__device__ __forceinline__ float silu(float z) { return z * sigm(z); }
+// The network's activations take their tanh on pairs of half-precision
+// arguments: one MUFU instruction per two values, which halves the pipe
+// that bounds the colour step's inference.  Element by element the result
+// does not depend on the pairing; the f16 rounding of z / 2 and the
+// approximation keep the error near 2^-11 relative, as tanh.approx.f32.
+__device__ __forceinline__ void sigm2(float za, float zb, float& sa, float& sb) {
+  uint32_t h, t;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(0.5f * zb), "f"(0.5f * za));  // za in the low half
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
+  float ta, tb;
+  asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.f16 %0, lo;\n\tcvt.f32.f16 %1, hi;\n\t}"
+      : "=f"(ta), "=f"(tb)
+      : "r"(t));
+  sa = fmaf(0.5f, ta, 0.5f);
+  sb = fmaf(0.5f, tb, 0.5f);
+}
+__device__ __forceinline__ void silu2(float za, float zb, float& ya, float& yb) {
+  float sa, sb;
+  sigm2(za, zb, sa, sb);
+  ya = za * sa;
+  yb = zb * sb;
+}
+// BF16 pair (SiLU(za), SiLU(zb)), za in the low half
+__device__ __forceinline__ uint32_t silu_bf16x2(float za, float zb) {
+  float ya, yb;
+  silu2(za, zb, ya, yb);
+  return bf16x2(ya, yb);
+}
 // d SiLU / dz = sigma (1 + z (1 - sigma))
 __device__ __forceinline__ float dsilu(float z) {
   const float s = sigm(z);
@@ -112,10 +153,10 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpW& w, uint32_t x0, uin
   uint32_t h[4][4];  // layer-2 A fragments, k-tile kk
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-    h[kk][0] = bf16x2(silu(z1[2 * kk][0]), silu(z1[2 * kk][1]));
-    h[kk][1] = bf16x2(silu(z1[2 * kk][2]), silu(z1[2 * kk][3]));
-    h[kk][2] = bf16x2(silu(z1[2 * kk + 1][0]), silu(z1[2 * kk + 1][1]));
-    h[kk][3] = bf16x2(silu(z1[2 * kk + 1][2]), silu(z1[2 * kk + 1][3]));
+    h[kk][0] = silu_bf16x2(z1[2 * kk][0], z1[2 * kk][1]);
+    h[kk][1] = silu_bf16x2(z1[2 * kk][2], z1[2 * kk][3]);
+    h[kk][2] = silu_bf16x2(z1[2 * kk + 1][0], z1[2 * kk + 1][1]);
+    h[kk][3] = silu_bf16x2(z1[2 * kk + 1][2], z1[2 * kk + 1][3]);
   }
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
@@ -132,10 +173,13 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpW& w, uint32_t x0, uin
 #pragma unroll
   for (int n = 0; n < 8; ++n) {
     const float2 c = __ldg(reinterpret_cast<const float2*>(w.vec + 2 * MLP_H) + 4 * n + t);  // w3
-    lo = fmaf(silu(z2[n][0]), c.x, lo);
-    lo = fmaf(silu(z2[n][1]), c.y, lo);
-    hi = fmaf(silu(z2[n][2]), c.x, hi);
-    hi = fmaf(silu(z2[n][3]), c.y, hi);
+    float s0, s1, s2, s3;
+    silu2(z2[n][0], z2[n][1], s0, s1);
+    silu2(z2[n][2], z2[n][3], s2, s3);
+    lo = fmaf(s0, c.x, lo);
+    lo = fmaf(s1, c.y, lo);
+    hi = fmaf(s2, c.x, hi);
+    hi = fmaf(s3, c.y, hi);
   }
   lo += __shfl_xor_sync(0xffffffffu, lo, 1);
   lo += __shfl_xor_sync(0xffffffffu, lo, 2);
@@ -148,10 +192,15 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpW& w, uint32_t x0, uin
 
 // Inference with one sample per lane: p[c] = BF16 pair (x_2c, x_2c+1) of
 // this lane's scaled inputs (p[4] = x8, x9).  Returns this lane's output.
-// Must be called by all 32 lanes.
+// Must be called by all 32 lanes.  The warp's 32 samples are two 16-row
+// tiles that share every weight fragment load; layer 2 is taken one n-tile
+// at a time with its SiLU and output products right after, so h2 is never
+// held.  Every value is formed in the order mlp_tile_forward uses (bias,
+// then the k-steps of each MMA in order; the output sum over n-tiles, then
+// over the row's four lanes, then b3): the results equal its, bit for bit.
 __device__ __forceinline__ float mlp_warp_eval(const MlpW& w, const uint32_t (&p)[5]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  float out = 0.0f;
+  uint32_t x[2][4];
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt) {
     uint32_t a0 = 0, a1 = 0;
@@ -166,12 +215,81 @@ __device__ __forceinline__ float mlp_warp_eval(const MlpW& w, const uint32_t (&p
     }
     const uint32_t v0 = __shfl_sync(0xffffffffu, p[4], 16 * mt + g);
     const uint32_t v1 = __shfl_sync(0xffffffffu, p[4], 16 * mt + g + 8);
-    const uint32_t a2 = t == 0 ? v0 : 0u, a3 = t == 0 ? v1 : 0u;
-    float z1[8][4], z2[8][4], lo, hi;
-    mlp_tile_forward(w, a0, a1, a2, a3, z1, z2, lo, hi);
-    const int rr = lane & 15;
-    const float vlo = __shfl_sync(0xffffffffu, lo, 4 * (rr & 7));
-    const float vhi = __shfl_sync(0xffffffffu, hi, 4 * (rr & 7));
+    x[mt][0] = a0;
+    x[mt][1] = a1;
+    x[mt][2] = t == 0 ? v0 : 0u;
+    x[mt][3] = t == 0 ? v1 : 0u;
+  }
+  // layer 1 and SiLU, two n-tiles (one layer-2 k-tile) at a time
+  uint32_t h[2][4][4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    float z[2][2][4];
+#pragma unroll
+    for (int hn = 0; hn < 2; ++hn) {
+      const int n = 2 * kk + hn;
+      const float2 bb = __ldg(reinterpret_cast<const float2*>(w.vec) + 4 * n + t);  // b1[8n + 2t], +1
+      const uint2 b = __ldg(w.w1f + n * 32 + lane);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        z[hn][mt][0] = bb.x;
+        z[hn][mt][1] = bb.y;
+        z[hn][mt][2] = bb.x;
+        z[hn][mt][3] = bb.y;
+        mma_bf16(z[hn][mt], x[mt][0], x[mt][1], x[mt][2], x[mt][3], b);
+      }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      h[mt][kk][0] = silu_bf16x2(z[0][mt][0], z[0][mt][1]);
+      h[mt][kk][1] = silu_bf16x2(z[0][mt][2], z[0][mt][3]);
+      h[mt][kk][2] = silu_bf16x2(z[1][mt][0], z[1][mt][1]);
+      h[mt][kk][3] = silu_bf16x2(z[1][mt][2], z[1][mt][3]);
+    }
+  }
+  // layer 2, SiLU and the output products, one n-tile at a time
+  float lo[2] = {0.0f, 0.0f}, hi[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    const float2 bb = __ldg(reinterpret_cast<const float2*>(w.vec + MLP_H) + 4 * n + t);  // b2
+    float z[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      z[mt][0] = bb.x;
+      z[mt][1] = bb.y;
+      z[mt][2] = bb.x;
+      z[mt][3] = bb.y;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint2 b = __ldg(w.w2f + (n * 4 + kk) * 32 + lane);
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) mma_bf16(z[mt], h[mt][kk][0], h[mt][kk][1], h[mt][kk][2], h[mt][kk][3], b);
+    }
+    const float2 c = __ldg(reinterpret_cast<const float2*>(w.vec + 2 * MLP_H) + 4 * n + t);  // w3
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      float s0, s1, s2, s3;
+      silu2(z[mt][0], z[mt][1], s0, s1);
+      silu2(z[mt][2], z[mt][3], s2, s3);
+      lo[mt] = fmaf(s0, c.x, lo[mt]);
+      lo[mt] = fmaf(s1, c.y, lo[mt]);
+      hi[mt] = fmaf(s2, c.x, hi[mt]);
+      hi[mt] = fmaf(s3, c.y, hi[mt]);
+    }
+  }
+  const float b3 = __ldg(w.vec + 3 * MLP_H);
+  const int rr = lane & 15;
+  float out = 0.0f;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    float l = lo[mt], u = hi[mt];
+    l += __shfl_xor_sync(0xffffffffu, l, 1);
+    l += __shfl_xor_sync(0xffffffffu, l, 2);
+    u += __shfl_xor_sync(0xffffffffu, u, 1);
+    u += __shfl_xor_sync(0xffffffffu, u, 2);
+    const float vlo = __shfl_sync(0xffffffffu, l + b3, 4 * (rr & 7));
+    const float vhi = __shfl_sync(0xffffffffu, u + b3, 4 * (rr & 7));
     if ((lane >> 4) == mt) out = rr < 8 ? vlo : vhi;
   }
   return out;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "mlp.cuh"
 
 namespace vcsgc {
 
@@ -40,6 +41,7 @@ struct MRepState {
   double energy;
   long long trials, local_acc, global_trials, global_acc, flips, near_ties, steps;
   double sum_c[MK_MAX], sum_c2[MK_MAX];
+  long long s1_acc;  // delayed acceptance: trials that passed stage 1
 };
 
 // accumulator of one colour step (two per replica, by step parity)
@@ -49,6 +51,7 @@ struct MStepAcc {
   int ties;
   unsigned done;
   int accept;
+  int s1;  // delayed acceptance: stage-1 passes
   double sum_de;
 };
 
@@ -114,6 +117,15 @@ struct MultiArgs {
   int rf_q;
   long long rf_n;
   int n_sm;             // multiprocessors of the device (commit grid)
+  // delayed acceptance (K = 2, screened form): a trial first passes a
+  // stage on the surrogate's prediction g of E(i = B) - E(i = A), then a
+  // stage on the exact dE - s g.  The surrogate's descriptor comes from
+  // nbc[R][rf_n] (laid out like rf): per site the B sites in each of its
+  // five shells, 6 bits per shell (shell s at bit 6 s), kept up to date by
+  // the commit while da is set.
+  int da;
+  MlpW mlp;
+  uint32_t* nbc;
 };
 
 // site index of trial d of colour c (ascending site index within a colour)
@@ -207,6 +219,11 @@ int multi_energy_blocks(long long N);
 void launch_multi_energy(const MultiArgs& a, int r0, int nrep, double* part, cudaStream_t st);
 void launch_multi_delta_e(const MultiArgs& a, int r, const long long* sites, const uint8_t* to, int n,
                           double* out, cudaStream_t st);
+// delayed acceptance (K = 2, five-shell table): the per-site shell counts of
+// every replica from its species; descriptors and exact targets of every
+// site (rows r N + i) from those counts
+void launch_multi_nbc(const MultiArgs& a, cudaStream_t st);
+void launch_multi_features(const MultiArgs& a, float* X, float* Y, cudaStream_t st);
 // one colour step (propose and commit); after_step: the previous launch on
 // the stream is this context's commit (the screened form then overlaps)
 void launch_multi_step(const MultiArgs& a, cudaStream_t st, bool after_step);

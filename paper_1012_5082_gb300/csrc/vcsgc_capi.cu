@@ -892,6 +892,7 @@ int sync_from_multi(Ctx* c) {
     s.steps = ms.steps;
     s.sum_c = ms.sum_c[1];
     s.sum_c2 = ms.sum_c2[1];
+    s.s1_acc = ms.s1_acc;
     CK(cudaMemcpyAsync(c->rs + r, &s, sizeof(RepState), cudaMemcpyHostToDevice, c->st));
   }
   CK(cudaStreamSynchronize(c->st));
@@ -916,6 +917,7 @@ int push_to_multi(Ctx* c, int r, const uint8_t* host_types, const RepState* s) {
     ms.flips = s->flips;
     ms.near_ties = s->near_ties;
     ms.steps = s->steps;
+    ms.s1_acc = s->s1_acc;
     ms.sum_c[1] = s->sum_c;
     ms.sum_c2[1] = s->sum_c2;
     ms.sum_c[0] = (double)s->steps - s->sum_c;
@@ -3031,6 +3033,12 @@ int vcsgc_features(void* ctx, float* d_X, float* d_Y) {
   VCSGC_TRACE("vcsgc_features");
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c || !d_X || !d_Y) return VCSGC_ERR_INVALID_ARG;
+  if (c->multi) {
+    // species-dependent densities: the two-species multicomponent object
+    // holds the state (same rows: replica after replica in site order)
+    const int rc = vcsgc_multi_features(c->multi, d_X, d_Y);
+    return rc == VCSGC_OK ? VCSGC_OK : fail(c, rc, vcsgc_multi_last_error(c->multi));
+  }
   if (!da_neighbourhood(c))
     return fail(c, VCSGC_ERR_STATE, "features need the fused rigid-lattice form with the 5-shell BCC neighbourhood");
   TRY(flush(c));
@@ -3044,6 +3052,10 @@ int vcsgc_features(void* ctx, float* d_X, float* d_Y) {
 int vcsgc_set_surrogate(void* ctx, void* mlp) {
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c) return VCSGC_ERR_INVALID_ARG;
+  if (c->multi) {
+    const int rc = vcsgc_multi_set_surrogate(c->multi, mlp);
+    return rc == VCSGC_OK ? VCSGC_OK : fail(c, rc, vcsgc_multi_last_error(c->multi));
+  }
   if (!mlp) {
     TRY(flush(c));
     CK(cudaStreamSynchronize(c->st));

@@ -39,6 +39,11 @@ struct Multi {
   cudaGraphExec_t graph = nullptr;
   long long* d_base = nullptr;  // fused form: device step base
   long long h_base = 0;         // its host mirror
+  // delayed acceptance: the context's copy of the surrogate's fragments;
+  // the per-site shell counts are rebuilt from the species before the next
+  // use after any change the commit did not track
+  MlpBuf sur{};
+  bool nbc_stale = true;
 };
 
 #define MCK(call)                                                                      \
@@ -130,6 +135,7 @@ int load_replica(Multi* m, int r, const uint8_t* t, bool reset_counters) {
   for (long long i = 0; i < m->N; ++i)
     if (t[i] >= m->K) return mfail(m, VCSGC_ERR_INVALID_ARG, "species value >= K");
   MTRY(flush(m));
+  m->nbc_stale = true;
   MCK(cudaMemcpyAsync(m->args.types + (long long)r * m->N, t, m->N, cudaMemcpyHostToDevice, m->st));
   launch_multi_rho(m->args, r, 1, m->st);
   MCK(cudaGetLastError());
@@ -190,8 +196,20 @@ int run_steps_fused(Multi* m, long long n) {
   return VCSGC_OK;
 }
 
+// delayed acceptance: per-site shell counts from the species, if stale
+int nbc_fresh(Multi* m) {
+  if (!m->nbc_stale) return VCSGC_OK;
+  launch_multi_nbc(m->args, m->st);
+  MCK(cudaGetLastError());
+  m->nbc_stale = false;
+  return VCSGC_OK;
+}
+
 int run_steps(Multi* m, long long n) {
   if (m->args.fused) return run_steps_fused(m, n);
+  if (m->args.da) MTRY(nbc_fresh(m));
+  // steps without delayed acceptance do not keep the counts
+  else if (n > 0) m->nbc_stale = true;
   const int G = 64;
   if (n >= G && !m->graph) {
     cudaGraph_t g;
@@ -211,6 +229,11 @@ int run_steps(Multi* m, long long n) {
   for (bool after = false; n > 0; --n, after = true) launch_multi_step(m->args, m->st, after);
   MCK(cudaGetLastError());
   return VCSGC_OK;
+}
+
+void drop_graph(Multi* m) {
+  if (m->graph) cudaGraphExecDestroy(m->graph);
+  m->graph = nullptr;
 }
 
 void destroy(Multi* m) {
@@ -552,6 +575,7 @@ int vcsgc_multi_observables(void* h, int32_t r, vcsgc_multi_obs* o) {
   o->global_accepts = s.global_acc;
   o->flips = s.flips;
   o->near_ties = s.near_ties;
+  o->stage1_accepts = s.s1_acc;
   o->acc_local = s.trials ? (double)s.local_acc / (double)s.trials : 0.0;
   o->acc_global = s.global_trials ? (double)s.global_acc / (double)s.global_trials : 0.0;
   o->sweeps = (double)s.trials / (double)m->N;
@@ -616,6 +640,66 @@ int vcsgc_multi_energy(void* h, int32_t r, double* out) {
   MCK(cudaSetDevice(m->device));
   MTRY(flush(m));
   return energy_of(m, r, out);
+}
+
+int vcsgc_multi_set_surrogate(void* h, void* mlp) {
+  VCSGC_TRACE("vcsgc_multi_set_surrogate");
+  Multi* m = as_multi(h);
+  if (!m) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  MultiArgs& a = m->args;
+  if (!mlp) {
+    MCK(cudaStreamSynchronize(m->st));
+    a.da = 0;
+    drop_graph(m);
+    return VCSGC_OK;
+  }
+  if (m->K != 2 || !a.screen)
+    return mfail(m, VCSGC_ERR_STATE,
+                 "delayed acceptance needs K = 2 with species-dependent densities on the five-shell table");
+  MlpBuf src{};
+  if (!mlp_object_buffers(mlp, &src)) return VCSGC_ERR_INVALID_ARG;
+  if (!m->sur.w1f) {
+    MTRY(malloc_dev(m, &m->sur.w1f, MLP_W1F));
+    MTRY(malloc_dev(m, &m->sur.w2f, MLP_W2F));
+    MTRY(malloc_dev(m, &m->sur.w2tf, MLP_W2F));
+    MTRY(malloc_dev(m, &m->sur.vec, MLP_VEC));
+  }
+  if (!a.nbc) {
+    MTRY(malloc_dev(m, &a.nbc, (size_t)m->R * a.rf_n));
+    m->nbc_stale = true;
+  }
+  // the surrogate's own stream may still be writing its fragments
+  MCK(cudaStreamSynchronize(mlp_object_stream(mlp)));
+  MCK(cudaMemcpyAsync(m->sur.w1f, src.w1f, sizeof(uint2) * MLP_W1F, cudaMemcpyDeviceToDevice, m->st));
+  MCK(cudaMemcpyAsync(m->sur.w2f, src.w2f, sizeof(uint2) * MLP_W2F, cudaMemcpyDeviceToDevice, m->st));
+  MCK(cudaMemcpyAsync(m->sur.w2tf, src.w2tf, sizeof(uint2) * MLP_W2F, cudaMemcpyDeviceToDevice, m->st));
+  MCK(cudaMemcpyAsync(m->sur.vec, src.vec, sizeof(float) * MLP_VEC, cudaMemcpyDeviceToDevice, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  a.mlp = mlp_view(m->sur);
+  a.da = 1;
+  drop_graph(m);  // the captured steps hold the arguments by value
+  return VCSGC_OK;
+}
+
+int vcsgc_multi_features(void* h, float* d_X, float* d_Y) {
+  VCSGC_TRACE("vcsgc_multi_features");
+  Multi* m = as_multi(h);
+  if (!m || !d_X || !d_Y) return VCSGC_ERR_INVALID_ARG;
+  MCK(cudaSetDevice(m->device));
+  MultiArgs& a = m->args;
+  if (m->K != 2 || !a.screen)
+    return mfail(m, VCSGC_ERR_STATE,
+                 "features need K = 2 with species-dependent densities on the five-shell table");
+  if (!a.nbc) {
+    MTRY(malloc_dev(m, &a.nbc, (size_t)m->R * a.rf_n));
+    m->nbc_stale = true;
+  }
+  MTRY(nbc_fresh(m));
+  launch_multi_features(a, d_X, d_Y, m->st);
+  MCK(cudaGetLastError());
+  MCK(cudaStreamSynchronize(m->st));
+  return device_error(m);
 }
 
 const char* vcsgc_multi_last_error(void* h) {

@@ -76,7 +76,8 @@ EXPORTS = ["vcsgc_default_options", "vcsgc_init", "vcsgc_steps", "vcsgc_sweep", 
            "vcsgc_multi_get_types", "vcsgc_multi_set_types", "vcsgc_multi_delta_e", "vcsgc_multi_energy",
            "vcsgc_multi_last_error", "vcsgc_multi_free", "vcsgc_set_ensemble", "vcsgc_md_state",
            "vcsgc_minimize", "vcsgc_save", "vcsgc_load", "vcsgc_set_launch", "vcsgc_get_launch",
-           "vcsgc_philox", "vcsgc_cluster_sizes", "vcsgc_set_schedule", "vcsgc_autotune_schedule"]
+           "vcsgc_philox", "vcsgc_cluster_sizes", "vcsgc_set_schedule", "vcsgc_autotune_schedule",
+           "vcsgc_multi_set_surrogate", "vcsgc_multi_features"]
 
 
 def lib():
@@ -140,6 +141,8 @@ def lib():
             "vcsgc_multi_set_types": (I32, [P, I32, P]),
             "vcsgc_multi_delta_e": (I32, [P, I32, P, P, I64, P]),
             "vcsgc_multi_energy": (I32, [P, I32, P]),
+            "vcsgc_multi_set_surrogate": (I32, [P, P]),
+            "vcsgc_multi_features": (I32, [P, P, P]),
             "vcsgc_multi_last_error": (C.c_char_p, [P]),
             "vcsgc_multi_free": (None, [P]),
             "vcsgc_set_launch": (I32, [P, I32, I32, I32]),
@@ -683,7 +686,8 @@ class MultiObs(C.Structure):
                 ("global_trials", C.c_int64), ("global_accepts", C.c_int64), ("flips", C.c_int64),
                 ("near_ties", C.c_int64), ("acc_local", C.c_double), ("acc_global", C.c_double),
                 ("mean_c", C.c_double * 4), ("var_c", C.c_double * 4), ("dmu_est", C.c_double * 4),
-                ("kappa_p", C.c_double * 4), ("dmu0", C.c_double * 4), ("sweeps", C.c_double)]
+                ("kappa_p", C.c_double * 4), ("dmu0", C.c_double * 4), ("sweeps", C.c_double),
+                ("stage1_accepts", C.c_int64)]
 
 
 class Multi:
@@ -787,6 +791,22 @@ class Multi:
         e = C.c_double()
         self._chk(lib().vcsgc_multi_energy(self.h, int(r), C.byref(e)))
         return e.value
+
+    def set_surrogate(self, surrogate):
+        """Delayed acceptance (K = 2, species-dependent densities) with a copy
+        of surrogate's weights (None: off); vcsgc_multi_set_surrogate."""
+        self._chk(lib().vcsgc_multi_set_surrogate(self.h, None if surrogate is None else surrogate.h))
+
+    def features(self):
+        """(X [R N, 10], Y [R N]) CUDA float32 tensors of every site of every
+        replica (vcsgc_multi_features)."""
+        import torch
+        rows = self.n * self.R
+        X = torch.empty((rows, MLP_IN), dtype=torch.float32, device="cuda")
+        Y = torch.empty(rows, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        self._chk(lib().vcsgc_multi_features(self.h, X.data_ptr(), Y.data_ptr()))
+        return X, Y
 
     def close(self):
         if getattr(self, "h", None):
