@@ -874,7 +874,7 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
 #pragma unroll
   for (int al = 0; al < MK_MAX; ++al)
     if (al < K) {
-      const double cc = (double)s.cnt[al] / (double)a.N;
+      const double cc = (double)s.cnt[al] * a.inv_n;
       s.sum_c[al] += cc;
       s.sum_c2[al] += cc * cc;
     }
@@ -1208,7 +1208,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_fused(MultiArgs a, int j) {
       for (int al = 0; al < K; ++al) {
         S.cnt[al] = cnt[al];
         n1[al] = cnt[al];
-        const double cc = (double)cnt[al] / (double)a.N;
+        const double cc = (double)cnt[al] * a.inv_n;
         S.sum_c[al] += cc;
         S.sum_c2[al] += cc * cc;
       }

@@ -78,6 +78,7 @@ struct MultiArgs {
   const long long* Dq;
   int qbits;
   double qscale;        // 2^-qbits
+  double inv_n;         // 1 / N (the per-step concentrations n / N)
   float rcp_nxq, rcp_nyq;  // 1 / nxq, 1 / nyq for the trial decode
   Spline embed[MK_MAX];
   uint8_t* types;       // [R][N]

@@ -324,6 +324,7 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
   a.ny = m->ny;
   a.nz = m->nz;
   a.N = m->N;
+  a.inv_n = 1.0 / (double)m->N;
   a.qx = period[0];
   a.qy = period[1];
   a.qz = period[2];
