@@ -966,10 +966,14 @@ def main():
                             f"expf 11.3 per clock): the ALU pipe needs {SM_CYCLES_PER_TRIAL:.2f} SM cycles per trial "
                             f"({OPS_PER_TRIAL} algorithmic ops), x 152 SMs x 2.07 GHz"),
             # DRAM bytes per launch from an ncu capture of the per-step kernel
-            # (256-thread blocks, warm L2, three launches of the timed loop)
-            "traffic": 256,
-            "traffic_source": "ncu --set full --cache-control none, k_lattice_step<...,256,...> x 3: "
-                              "dram__bytes_read.sum 256 B + dram__bytes_write.sum 0 B per launch",
+            # (256-thread blocks, warm L2, three launches of the timed loop);
+            # the cluster form is another kernel, not captured
+            "traffic": 255061 if launch[0] == 0 else None,
+            "traffic_source": ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --cache-control none, "
+                               "k_lattice_step<...,256,...> x 3 (launches 600-602): read 47,360 / 256 / 256 B, "
+                               "write 252,672 / 250,368 / 214,272 B; the kernel's own reads are L2-resident, the "
+                               "writes are write-backs of lines dirtied before it (the L2 flush between sweeps)"
+                               if launch[0] == 0 else None),
             "ops_per_trial": {"simple_int": OPS_SIMPLE, "popc": OPS_POPC, "mul_pairs": OPS_MULPAIR,
                               "fp32": OPS_FP32, "mufu": OPS_MUFU},
             "trials_per_colour_step": trials_per_colour_step, "avg_colour_step_us": avg_ms * 1e3,
@@ -1045,6 +1049,8 @@ def main():
             line["schedule_autotune"] = schedule_bench(V, torch, stream, local, dmu_bal)
         if not args.no_multi:
             line["multicomponent"] = multi_bench(V, torch, stream, local)
+            if not args.no_surrogate:
+                line["delayed_acceptance_reembedding"] = reembed_da_bench(V, torch, stream, local)
         if not args.no_ensemble and not args.no_md:
             line["md_ensemble"] = ensemble_bench(V, torch, stream, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
