@@ -548,9 +548,12 @@ __device__ __forceinline__ void multi_descriptor(const MultiArgs& a, int r, int 
 // MODE 0: no re-embedding; 1: re-embedding, FP64 dE (any neighbour table);
 // 2: re-embedding, five-shell table, FP32 screen (the dE sum of an accepted
 // step is then taken by the commit launch, in FP64); 3: mode 2 with delayed
-// acceptance (K = 2)
+// acceptance (K = 2).  Modes 0 and 1 take their step from the replica's
+// state and the last block of each replica takes the global decision; the
+// screened modes take step *base + j and leave the decision to the commit
+// launch, whose every block reads the step's complete sums.
 template <int MODE>
-__global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
+__global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a, int j) {
   constexpr bool REEMBED = MODE != 0;
   constexpr bool SCREEN = MODE >= 2;
   __shared__ double sV[MK_MAX_SH * MK_MAX * MK_MAX];
@@ -594,7 +597,7 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
     }
   const int r = blockIdx.y;
   const MRepParams& p = a.rp[r];
-  const long long step = a.rs[r].step;
+  const long long step = SCREEN ? *a.base + j : a.rs[r].step;
   if (threadIdx.x == 0) {
     // the step's colour (and global uniform), once per block
     const uint4 wc = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0xFFFFFFFFu, TAG_STEP),
@@ -607,9 +610,9 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
     s_col[2] = (pc / a.qx) % a.qy;
     s_col[3] = pc / (a.qx * a.qy);
     s_nq = 0;
-    s_rs = a.rs[r];
+    if (!SCREEN) s_rs = a.rs[r];
   }
-  if (threadIdx.x < MK_MAX) {
+  if (!SCREEN && threadIdx.x < MK_MAX) {
     s_bk[threadIdx.x] = p.beta * p.kappa_p[threadIdx.x];
     s_n0[threadIdx.x] = p.n0[threadIdx.x];
   }
@@ -824,9 +827,13 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a) {
     }
     if (tsum) atomicAdd(&A->ties, tsum);
     if (dsum != 0.0) atomicAdd(&A->sum_de, dsum);
-    __threadfence();
-    s_last = atomicAdd(&A->done, 1u) == gridDim.x - 1;
+    if (!SCREEN) {
+      __threadfence();
+      s_last = atomicAdd(&A->done, 1u) == gridDim.x - 1;
+    }
   }
+  // screened forms: the commit launch takes the global decision
+  if constexpr (SCREEN) return;
   __syncthreads();
   if (!s_last || threadIdx.x != 0) return;
   // global stage (last block of the replica): every block's sums are
@@ -925,7 +932,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit(MultiArgs a) {
 // neighbour's species changes.  Every block sums the replicas' item counts
 // (at most MK_SCREEN_MAX_R replicas; the host selects this form only while
 // R D (MK_BCC5_N + 1) < 2^31, so the int item index cannot overflow).
-__global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
+__global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a, int jl) {
   // the next step's propose may start its draws now; it reads what this
   // launch writes only after griddepcontrol.wait
   pdl_trigger();
@@ -934,15 +941,74 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
   __shared__ double s_df[5 * MK_MAX * MK_MAX];
   const int K = a.K;
   constexpr int NI = MK_BCC5_N + 1;
-  const long long step = a.rs[0].step - 1;  // replicas step together
+  const long long step = *a.base + jl;  // the step the propose launch proposed
+  // the global stage of every replica (Eq. trans_vcsgc_par2 per solute),
+  // taken in every block from the step's complete sums: the same FP64
+  // arithmetic everywhere, so the same decision.  Block 0 folds the step
+  // into the replica's state and readies the next step's accumulator.
   for (int r = threadIdx.x; r < a.R; r += MK_BLOCK) {
     const MStepAcc* A = a.acc + 2 * r + (int)(step & 1);
-    s_pre[r + 1] = A->accept ? A->nacc * NI : 0;
+    const MRepParams& p = a.rp[r];
+    const int nacc = __ldcg(&A->nacc);
+    int dn[MK_MAX];
+    long long c0[MK_MAX];
+#pragma unroll
+    for (int al = 0; al < MK_MAX; ++al) {
+      dn[al] = al > 0 && al < K ? __ldcg(&A->dn[al]) : 0;
+      c0[al] = al < K ? __ldcg(&A->cnt[al]) : 0;
+    }
+    int accept = 0, gtie = 0;
+    if (nacc > 0) {
+      double Y = 0.0;
+#pragma unroll
+      for (int al = 1; al < MK_MAX; ++al)
+        if (al < K)
+          Y += p.beta * p.kappa_p[al] * (double)dn[al] * ((double)dn[al] + 2.0 * ((double)c0[al] - p.n0[al]));
+      const uint4 wc = philox4x32_10(
+          make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0xFFFFFFFFu, TAG_STEP), p.key);
+      accept = metropolis(Y, top53(wc.z, wc.w), &gtie) ? 1 : 0;
+    }
+    s_pre[r + 1] = accept ? nacc * NI : 0;
     if (blockIdx.x == 0) {
+      MRepState s = a.rs[r];
+      s.trials += a.D;
+      s.local_acc += nacc;
+      s.near_ties += __ldcg(&A->ties) + gtie;
+      s.s1_acc += __ldcg(&A->s1);
+      if (nacc > 0) {
+        s.global_trials++;
+        if (accept) {
+          s.global_acc++;
+          s.flips += nacc;
+          long long d0 = 0;
+#pragma unroll
+          for (int al = 1; al < MK_MAX; ++al)
+            if (al < K) {
+              s.cnt[al] += dn[al];
+              d0 += dn[al];
+            }
+          s.cnt[0] -= d0;
+        }
+      }
+      s.steps++;
+#pragma unroll
+      for (int al = 0; al < MK_MAX; ++al)
+        if (al < K) {
+          const double cc = (double)s.cnt[al] * a.inv_n;
+          s.sum_c[al] += cc;
+          s.sum_c2[al] += cc * cc;
+        }
+      s.step = step + 1;
+      a.rs[r] = s;
       MStepAcc* B = a.acc + 2 * r + (int)((step + 1) & 1);
-      for (int al = 0; al < MK_MAX; ++al) B->dn[al] = 0;
+#pragma unroll
+      for (int al = 0; al < MK_MAX; ++al) {
+        B->dn[al] = 0;
+        B->cnt[al] = s.cnt[al];
+      }
       B->nacc = 0;
       B->ties = 0;
+      B->done = 0u;
       B->accept = 0;
       B->s1 = 0;
       B->sum_de = 0.0;
@@ -992,7 +1058,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a) {
   }
 }
 
-void launch_multi_step(const MultiArgs& a, cudaStream_t st, bool after_step) {
+void launch_multi_step(const MultiArgs& a, int j, cudaStream_t st, bool after_step) {
   const int nb = (a.D + MK_BLOCK - 1) / MK_BLOCK;
   const dim3 grid((unsigned)nb, (unsigned)a.R);
   // the accepts of a step are a small share of its trials: a few blocks per
@@ -1011,15 +1077,15 @@ void launch_multi_step(const MultiArgs& a, cudaStream_t st, bool after_step) {
     cfg.attrs = attr;
     cfg.numAttrs = after_step ? 1 : 0;
     if (a.da)
-      cudaLaunchKernelEx(&cfg, k_multi_propose<3>, a);
+      cudaLaunchKernelEx(&cfg, k_multi_propose<3>, a, j);
     else
-      cudaLaunchKernelEx(&cfg, k_multi_propose<2>, a);
-    k_multi_commit_screen<<<4 * a.n_sm, MK_BLOCK, 0, st>>>(a);
+      cudaLaunchKernelEx(&cfg, k_multi_propose<2>, a, j);
+    k_multi_commit_screen<<<4 * a.n_sm, MK_BLOCK, 0, st>>>(a, j);
   } else if (a.reembed) {
-    k_multi_propose<1><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_propose<1><<<grid, MK_BLOCK, 0, st>>>(a, 0);
     k_multi_commit<1><<<cgrid, MK_BLOCK, 0, st>>>(a);
   } else {
-    k_multi_propose<0><<<grid, MK_BLOCK, 0, st>>>(a);
+    k_multi_propose<0><<<grid, MK_BLOCK, 0, st>>>(a, 0);
     k_multi_commit<0><<<cgrid, MK_BLOCK, 0, st>>>(a);
   }
 }

@@ -53,6 +53,10 @@ struct MStepAcc {
   int accept;
   int s1;  // delayed acceptance: stage-1 passes
   double sum_de;
+  // screened form: the species counts at the start of the step, written
+  // with the zeroed sums by the commit of the step before (or the host), so
+  // that every commit block can take the step's global decision
+  long long cnt[MK_MAX];
 };
 
 struct MultiArgs {
@@ -226,8 +230,10 @@ void launch_multi_delta_e(const MultiArgs& a, int r, const long long* sites, con
 void launch_multi_nbc(const MultiArgs& a, cudaStream_t st);
 void launch_multi_features(const MultiArgs& a, float* X, float* Y, cudaStream_t st);
 // one colour step (propose and commit); after_step: the previous launch on
-// the stream is this context's commit (the screened form then overlaps)
-void launch_multi_step(const MultiArgs& a, cudaStream_t st, bool after_step);
+// the stream is this context's commit (the screened form then overlaps).
+// The screened form takes step *base + j (launch_multi_advance moves the
+// base after a run of steps); the others keep the step in each replica's state.
+void launch_multi_step(const MultiArgs& a, int j, cudaStream_t st, bool after_step);
 // fused form: step base + j (propose = false: only the commit and the
 // bookkeeping of the previous step), and base += n
 void launch_multi_fused(const MultiArgs& a, int j, bool propose, cudaStream_t st);

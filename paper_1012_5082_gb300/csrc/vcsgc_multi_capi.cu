@@ -44,6 +44,10 @@ struct Multi {
   // use after any change the commit did not track
   MlpBuf sur{};
   bool nbc_stale = true;
+  // screened form: the accumulator of the next step (zero sums, the counts
+  // at its start) is rewritten from the replicas' states before the next
+  // run after the host changed a state or the step base
+  bool acc_stale = true;
 };
 
 #define MCK(call)                                                                      \
@@ -136,6 +140,7 @@ int load_replica(Multi* m, int r, const uint8_t* t, bool reset_counters) {
     if (t[i] >= m->K) return mfail(m, VCSGC_ERR_INVALID_ARG, "species value >= K");
   MTRY(flush(m));
   m->nbc_stale = true;
+  m->acc_stale = true;
   MCK(cudaMemcpyAsync(m->args.types + (long long)r * m->N, t, m->N, cudaMemcpyHostToDevice, m->st));
   launch_multi_rho(m->args, r, 1, m->st);
   MCK(cudaGetLastError());
@@ -205,8 +210,29 @@ int nbc_fresh(Multi* m) {
   return VCSGC_OK;
 }
 
+// screened form: every replica's accumulator of step h_base from its state
+int screen_acc_ready(Multi* m) {
+  if (!m->args.screen || !m->acc_stale) return VCSGC_OK;
+  std::vector<MRepState> s(m->R);
+  MCK(cudaMemcpyAsync(s.data(), m->args.rs, sizeof(MRepState) * m->R, cudaMemcpyDeviceToHost, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  std::vector<MStepAcc> acc(m->R);
+  for (int r = 0; r < m->R; ++r) {
+    acc[r] = MStepAcc{};
+    for (int al = 0; al < MK_MAX; ++al) acc[r].cnt[al] = s[r].cnt[al];
+  }
+  const int par = (int)(m->h_base & 1);
+  for (int r = 0; r < m->R; ++r)
+    MCK(cudaMemcpyAsync(m->args.acc + 2 * r + par, &acc[r], sizeof(MStepAcc), cudaMemcpyHostToDevice, m->st));
+  MCK(cudaMemcpyAsync(m->d_base, &m->h_base, sizeof(long long), cudaMemcpyHostToDevice, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  m->acc_stale = false;
+  return VCSGC_OK;
+}
+
 int run_steps(Multi* m, long long n) {
   if (m->args.fused) return run_steps_fused(m, n);
+  MTRY(screen_acc_ready(m));
   if (m->args.da) MTRY(nbc_fresh(m));
   // steps without delayed acceptance do not keep the counts
   else if (n > 0) m->nbc_stale = true;
@@ -214,7 +240,8 @@ int run_steps(Multi* m, long long n) {
   if (n >= G && !m->graph) {
     cudaGraph_t g;
     MCK(cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal));
-    for (int q = 0; q < G; ++q) launch_multi_step(m->args, m->st, q > 0);
+    for (int q = 0; q < G; ++q) launch_multi_step(m->args, q, m->st, q > 0);
+    if (m->args.screen) launch_multi_advance(m->d_base, G, m->st);
     cudaError_t e1 = cudaGetLastError();
     MCK(cudaStreamEndCapture(m->st, &g));
     if (e1 != cudaSuccess) {
@@ -225,8 +252,17 @@ int run_steps(Multi* m, long long n) {
     cudaGraphDestroy(g);
     if (e2 != cudaSuccess) return mfail(m, VCSGC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(e2));
   }
-  for (; n >= G; n -= G) MCK(cudaGraphLaunch(m->graph, m->st));
-  for (bool after = false; n > 0; --n, after = true) launch_multi_step(m->args, m->st, after);
+  for (; n >= G; n -= G) {
+    MCK(cudaGraphLaunch(m->graph, m->st));
+    m->h_base += G;
+  }
+  if (n > 0) {
+    for (long long q = 0; q < n; ++q) launch_multi_step(m->args, (int)q, m->st, q > 0);
+    // the base is read before the next propose's wait: it moves by an
+    // ordinary launch, and the next run starts with an ordinary launch
+    if (m->args.screen) launch_multi_advance(m->d_base, (int)n, m->st);
+    m->h_base += n;
+  }
   MCK(cudaGetLastError());
   return VCSGC_OK;
 }
@@ -732,6 +768,11 @@ int multi_set_state(void* h, int r, const MRepState* in) {
   MCK(cudaSetDevice(m->device));
   MCK(cudaMemcpyAsync(m->args.rs + r, in, sizeof(MRepState), cudaMemcpyHostToDevice, m->st));
   MCK(cudaStreamSynchronize(m->st));
+  // screened form: the replicas step together from the device base
+  if (m->args.screen) {
+    m->h_base = in->step;
+    m->acc_stale = true;
+  }
   return VCSGC_OK;
 }
 
