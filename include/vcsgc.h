@@ -404,7 +404,7 @@ int vcsgc_neighbour_list_noalloc(int64_t n, const double* d_x, const double* d_y
  * h1 = SiLU(z1); z2 = W2 h1 + b2; h2 = SiLU(z2); g = w3 . h2 + b3 (eV).
  * On the GPU x, W1, W2 and h1 enter the tensor cores as BF16 with FP32
  * accumulation, and SiLU(z) = z (1 + tanh(z / 2)) / 2 uses the hardware
- * tanh approximation on half-precision arguments. */
+ * tanh approximation. */
 #define VCSGC_MLP_IN 10
 #define VCSGC_MLP_NPARAM 4929
 

@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a, int 
       multi_descriptor(a, r, cx, cy, cz, b, ta, own, nb);
       mlp_pairs(own, nb, P);
     }
-    const float gnn = mlp_warp_eval(a.mlp, P);
+    const float gnn = mlp_warp_eval_pair(a.mlp, P);
     if (d < a.D) {
       // u < min{1, exp[-beta (s g + s dmu0)]}
       const double sg = ta ? -1.0 : 1.0;

@@ -5,7 +5,7 @@
 // first-shell neighbours' summed B counts in shells 1-5) scaled to
 // x = c / max_c, then z1 = W1 x + b1, h1 = SiLU(z1), z2 = W2 h1 + b2,
 // h2 = SiLU(z2), g = w3 . h2 + b3 (g predicts E(site = B) - E(site = A)).
-// SiLU(z) = z (1 + tanh(z / 2)) / 2 with the hardware tanh on half pairs.
+// SiLU(z) = z (1 + tanh(z / 2)) / 2 with the hardware tanh.
 //
 // Tensor-core form: a warp evaluates a tile of 16 samples with mma.sync
 // m16n8k16 (BF16 operands, FP32 accumulation).  The inputs are padded from
@@ -99,21 +99,10 @@ __device__ __forceinline__ float tanh_fast(float x) {
   return y;
 }
 __device__ __forceinline__ float sigm(float z) { return fmaf(0.5f, tanh_fast(0.5f * z), 0.5f); }
-// The network's activations take their tanh on pairs of half-precision
-// arguments: one MUFU instruction per two values, which halves the pipe
-// that bounds the colour step's inference.  Element by element the result
-// does not depend on the pairing; the f16 rounding of z / 2 and the
-// approximation keep the error near 2^-11 relative, as tanh.approx.f32.
+// sigma of two values (FP32 tanh.approx each)
 __device__ __forceinline__ void sigm2(float za, float zb, float& sa, float& sb) {
-  uint32_t h, t;
-  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(0.5f * zb), "f"(0.5f * za));  // za in the low half
-  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
-  float ta, tb;
-  asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tcvt.f32.f16 %0, lo;\n\tcvt.f32.f16 %1, hi;\n\t}"
-      : "=f"(ta), "=f"(tb)
-      : "r"(t));
-  sa = fmaf(0.5f, ta, 0.5f);
-  sb = fmaf(0.5f, tb, 0.5f);
+  sa = sigm(za);
+  sb = sigm(zb);
 }
 __device__ __forceinline__ void silu2(float za, float zb, float& ya, float& yb) {
   float sa, sb;
@@ -193,12 +182,45 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpW& w, uint32_t x0, uin
 // Inference with one sample per lane: p[c] = BF16 pair (x_2c, x_2c+1) of
 // this lane's scaled inputs (p[4] = x8, x9).  Returns this lane's output.
 // Must be called by all 32 lanes.  The warp's 32 samples are two 16-row
-// tiles that share every weight fragment load; layer 2 is taken one n-tile
-// at a time with its SiLU and output products right after, so h2 is never
-// held.  Every value is formed in the order mlp_tile_forward uses (bias,
-// then the k-steps of each MMA in order; the output sum over n-tiles, then
-// over the row's four lanes, then b3): the results equal its, bit for bit.
+// tiles, evaluated one after the other by mlp_tile_forward.
 __device__ __forceinline__ float mlp_warp_eval(const MlpW& w, const uint32_t (&p)[5]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float out = 0.0f;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    uint32_t a0 = 0, a1 = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t v0 = __shfl_sync(0xffffffffu, p[c], 16 * mt + g);
+      const uint32_t v1 = __shfl_sync(0xffffffffu, p[c], 16 * mt + g + 8);
+      if (t == c) {
+        a0 = v0;
+        a1 = v1;
+      }
+    }
+    const uint32_t v0 = __shfl_sync(0xffffffffu, p[4], 16 * mt + g);
+    const uint32_t v1 = __shfl_sync(0xffffffffu, p[4], 16 * mt + g + 8);
+    const uint32_t a2 = t == 0 ? v0 : 0u, a3 = t == 0 ? v1 : 0u;
+    float z1[8][4], z2[8][4], lo, hi;
+    mlp_tile_forward(w, a0, a1, a2, a3, z1, z2, lo, hi);
+    const int rr = lane & 15;
+    const float vlo = __shfl_sync(0xffffffffu, lo, 4 * (rr & 7));
+    const float vhi = __shfl_sync(0xffffffffu, hi, 4 * (rr & 7));
+    if ((lane >> 4) == mt) out = rr < 8 ? vlo : vhi;
+  }
+  return out;
+}
+
+// The same evaluation with the warp's two 16-row tiles side by side: they
+// share every weight fragment load, and layer 2 is taken one n-tile at a
+// time with its SiLU and output products right after, so h2 is never held.
+// Every value is formed in the order mlp_tile_forward uses (bias, then the
+// k-steps of each MMA in order; the output sum over n-tiles, then over the
+// row's four lanes, then b3): the results equal mlp_warp_eval's bit for
+// bit.  Measured: it shortens a latency-bound step (the screened
+// multicomponent propose) and slows a throughput-bound one (the fused
+// lattice step), where mlp_warp_eval stays.
+__device__ __forceinline__ float mlp_warp_eval_pair(const MlpW& w, const uint32_t (&p)[5]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   uint32_t x[2][4];
 #pragma unroll
