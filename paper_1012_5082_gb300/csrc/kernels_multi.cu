@@ -597,125 +597,6 @@ __device__ __forceinline__ void multi_descriptor(const MultiArgs& a, int r, int 
   nb[4] = (int)(xs >> 24);
 }
 
-// Stage 2 of delayed acceptance (K = 2), one launch over every trial of the
-// step that passed stage 1: u2 < min{1, exp[-beta (dE - s g)]}, the dE
-// FP32-screened by groups of MK_GROUP lanes with the bound of the plain
-// rule's screen, FP64 by the warp where the screen cannot decide.  Blocks
-// (x, r) stride over replica r's queue, so the work spreads evenly over
-// the GPU whatever the stage-1 passes of each block of the propose were.
-// The accepts are compacted into the replica's pending list, their dn and
-// the near ties summed per block with one atomic each.
-__global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_da_stage2(MultiArgs a, int j) {
-  __shared__ long long sDq[5 * MK_MAX * MK_MAX * MK_MAX];
-  __shared__ float sDfs[5 * MK_MAX * MK_MAX];
-  __shared__ double sFd[MK_MAX_SH * MK_MAX];
-  __shared__ int scode[MK_BCC5_N];
-  __shared__ int s_gw[MK_BLOCK / MK_GROUP][30];
-  __shared__ int s_red[MK_BLOCK / 32][3];
-  __shared__ int s_fw[MK_BLOCK / 32][15];
-  __shared__ int s_b;
-  const int K = a.K;
-  const int r = blockIdx.y;
-  const MRepParams& p = a.rp[r];
-  const long long step = *a.base + j;
-  for (int q = threadIdx.x; q < 5 * K * K * K; q += MK_BLOCK) sDq[q] = a.Dq[q];
-  for (int q = threadIdx.x; q < a.n_sh * K; q += MK_BLOCK) sFd[q] = a.Fd[q];
-  for (int q = threadIdx.x; q < 5 * K * K; q += MK_BLOCK) {
-    const int sh = q / (K * K), x = (q / K) % K, y = q % K;
-    sDfs[q] = (float)(a.Fd[sh * K + y] - a.Fd[sh * K + x]);
-  }
-  if (threadIdx.x == 0) {
-    // the step's colour, for the basis of its sites
-    const uint4 wc = philox4x32_10(make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0xFFFFFFFFu, TAG_STEP),
-                                   p.key);
-    s_b = (int)below64(wc.x, wc.y, (uint64_t)a.n_colours) & 1;
-  }
-  __syncthreads();
-  if (threadIdx.x < MK_BCC5_N) scode[threadIdx.x] = s_b ? mk_bcc5_desc<1>(threadIdx.x) : mk_bcc5_desc<0>(threadIdx.x);
-  __syncthreads();
-  // the queue is the propose launch's output
-  pdl_wait();
-  const int par = (int)(step & 1);
-  int4* q = a.daq + ((long long)par * a.R + r) * a.D;
-  // the count and this block's first entries in one round (the queue holds
-  // D entries, so the entries' loads need not wait for the count)
-  const int e0 = blockIdx.x * (MK_BLOCK / MK_GROUP) + threadIdx.x / MK_GROUP;
-  const int n = __ldcg(a.daq_n + par * a.R + r);
-  int4 qn = e0 < a.D ? __ldcg(q + e0) : make_int4(0, 0, 0, 0);
-  MStepAcc* A = a.acc + 2 * r + par;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gl = threadIdx.x & (MK_GROUP - 1);
-  const int nx = a.nx, nxy = a.nx * a.ny;
-  int tie = 0, dn = 0, nac = 0;
-  for (int q0 = blockIdx.x * (MK_BLOCK / MK_GROUP); q0 < n; q0 += gridDim.x * (MK_BLOCK / MK_GROUP)) {
-    const int e = q0 + threadIdx.x / MK_GROUP;
-    const bool has = e < n;
-    const int4 qe = qn;
-    const int en = e + gridDim.x * (MK_BLOCK / MK_GROUP);
-    if (en < a.D) qn = __ldcg(q + en);
-    const int site = qe.x & 0x3FFFFFFF, ta = (qe.x >> 30) & 1;
-    const int cell = site >> 1;
-    const int cz = cell / nxy, cy = (cell - cz * nxy) / nx, cx = cell - cz * nxy - cy * nx;
-    long long qpq = 0;
-    float err;
-    bool in;
-    const float e32 = multi_screen_group(a, sDq, sDfs, s_gw[threadIdx.x / MK_GROUP], scode, r, site, cx, cy, cz,
-                                         ta, 1 - ta, gl, has, &qpq, &err, &in);
-    const bool lead = has && gl == 0;
-    int dec2 = 0;
-    uint64_t u2 = 0;
-    const float g = __int_as_float(qe.y);
-    if (lead) {
-      u2 = top53((uint32_t)qe.z, (uint32_t)qe.w);
-      const float cm = ta ? g : -g;  // -s g, exact
-      const float x32 = p.beta32 * (e32 + cm);
-      const float dx = p.beta32 * fmaf(4.76837158203125e-07f, fabsf(e32) + fabsf(cm), err) * 1.0001f +
-                       fabsf(x32) * 4.76837158203125e-07f;
-      dec2 = in ? screen32(x32, dx, u2) : -1;
-    }
-    unsigned open = __ballot_sync(0xffffffffu, lead && dec2 < 0);
-    while (open) {
-      const int src = __ffs(open) - 1;
-      open &= open - 1u;
-      const int si = __shfl_sync(0xffffffffu, site, src);
-      const int sa = __shfl_sync(0xffffffffu, ta, src);
-      const double v = warp_sum(multi_emb_warp5(a, sFd, scode, s_fw[warp], r, si, sa, 1 - sa, lane));
-      if (lane == src) {
-        const double de64 = (double)qpq * a.qscale + v;
-        if (!isfinite(de64)) atomicOr(a.err, ERRF_NONFINITE);
-        const double sg = ta ? -1.0 : 1.0;
-        dec2 = metropolis(p.beta * (de64 - sg * (double)g), u2, &tie) ? 1 : 0;
-      }
-    }
-    // an accept is marked in its queue entry (bit 31); the commit walks the
-    // queue, so no slot needs reserving
-    if (lead && dec2 > 0) {
-      q[e].x = qe.x | (int)0x80000000u;
-      dn += ta ? -1 : 1;
-      ++nac;
-    }
-    __syncwarp();  // the group's scratch is rewritten by the next round
-  }
-  const int sd = __reduce_add_sync(0xffffffffu, dn), st = __reduce_add_sync(0xffffffffu, tie);
-  const int sa = __reduce_add_sync(0xffffffffu, nac);
-  if (lane == 0) {
-    s_red[warp][0] = sd;
-    s_red[warp][1] = st;
-    s_red[warp][2] = sa;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int vd = 0, vt = 0, va = 0;
-    for (int w = 0; w < MK_BLOCK / 32; ++w) {
-      vd += s_red[w][0];
-      vt += s_red[w][1];
-      va += s_red[w][2];
-    }
-    if (vd) atomicAdd(&A->dn[1], vd);
-    if (vt) atomicAdd(&A->ties, vt);
-    if (va) atomicAdd(&A->nacc, va);
-  }
-}
-
 // MODE 0: no re-embedding; 1: re-embedding, FP64 dE (any neighbour table);
 // 2: re-embedding, five-shell table, FP32 screen (the dE sum of an accepted
 // step is then taken by the commit launch, in FP64); 3: mode 2 with delayed
@@ -727,9 +608,6 @@ template <int MODE>
 __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a, int j) {
   constexpr bool REEMBED = MODE != 0;
   constexpr bool SCREEN = MODE >= 2;
-  // delayed acceptance: the stage-2 launch may be scheduled now; it reads
-  // the queue this launch fills only after griddepcontrol.wait
-  if constexpr (MODE == 3) pdl_trigger();
   __shared__ double sV[MK_MAX_SH * MK_MAX * MK_MAX];
   __shared__ double sFd[MK_MAX_SH * MK_MAX];
   __shared__ double sDF[MK_MAX * MK_MAX];
@@ -740,12 +618,20 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a, int 
   __shared__ int sw[SCREEN ? 30 * MK_BLOCK : 1];
   __shared__ int scode[SCREEN ? MK_BCC5_N : 1];
   __shared__ int s_fw[SCREEN ? MK_BLOCK / 32 : 1][15];
+  // delayed acceptance: the block's stage-1 passes, queued for the exact
+  // stage (site and cell; species, g, owner thread and trial), and the
+  // owners' stage-2 decisions
+  __shared__ int4 s_qa[MODE == 3 ? MK_BLOCK : 1];
+  __shared__ int4 s_qb[MODE == 3 ? MK_BLOCK : 1];
+  __shared__ int s_dec[MODE == 3 ? MK_BLOCK : 1];
+  __shared__ int s_gw[MODE == 3 ? MK_BLOCK / MK_GROUP : 1][30];
+  __shared__ uint64_t s_u2[MODE == 3 ? MK_BLOCK : 1];
+  __shared__ int s_nq;
   __shared__ uint4 s_wc;
   __shared__ int s_col[4];
   __shared__ int s_red[MK_BLOCK / 32][MK_MAX + 1];
   __shared__ double s_de[MK_BLOCK / 32];
   __shared__ int s_s1[MK_BLOCK / 32];
-  __shared__ uint2 s_u2[MODE == 3 ? MK_BLOCK : 1];
   __shared__ bool s_last;
   // the global stage's inputs that no block of this step writes: the
   // replica's running state and beta kappa_p, n0 per solute
@@ -776,6 +662,7 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a, int 
     s_col[1] = pc % a.qx;
     s_col[2] = (pc / a.qx) % a.qy;
     s_col[3] = pc / (a.qx * a.qy);
+    s_nq = 0;
     if (!SCREEN) s_rs = a.rs[r];
   }
   if (!SCREEN && threadIdx.x < MK_MAX) {
@@ -814,11 +701,11 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a, int 
                                   p.key);
     u53 = top53(w.z, w.w);
     if constexpr (MODE == 3) {
-      // delayed acceptance: the stage-2 uniform's words too, while the
-      // previous launch drains; they travel in the queue entry
+      // delayed acceptance: the stage-2 uniform too, while the previous
+      // launch drains
       const uint4 w2 = philox4x32_10(
           make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)d, TAG_STAGE2), p.key);
-      s_u2[threadIdx.x] = make_uint2(w2.x, w2.y);
+      s_u2[threadIdx.x] = top53(w2.x, w2.y);
     }
   }
   // screened form: launched after the previous step's commit with
@@ -844,21 +731,73 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a, int 
       const double sg = ta ? -1.0 : 1.0;
       s1 = metropolis(p.beta * fma(sg, p.dmu0[1], sg * (double)gnn), u53, &tie) ? 1 : 0;
     }
-    // the stage-1 passes join the replica's queue for the stage-2 launch,
-    // which screens every queued trial of the step at once
+    // the block's stage-1 passes in one queue; warp w takes entries
+    // 32 w .. 32 w + 31 for stage 2, so only ceil(passes / 32) warps
+    // gather the exact dE's neighbourhood
     const unsigned pm = __ballot_sync(0xffffffffu, s1);
     if (pm) {
-      const int par = (int)(step & 1);
       int qb = 0;
-      if (lane == 0) qb = atomicAdd(a.daq_n + par * a.R + r, __popc(pm));
+      if (lane == 0) qb = atomicAdd(&s_nq, __popc(pm));
       qb = __shfl_sync(0xffffffffu, qb, 0);
       if (s1) {
-        const uint2 u = s_u2[threadIdx.x];
-        a.daq[((long long)par * a.R + r) * a.D + qb + __popc(pm & ((1u << lane) - 1u))] =
-            make_int4(site | (ta << 30), __float_as_int(gnn), (int)u.x, (int)u.y);
+        const int e = qb + __popc(pm & ((1u << lane) - 1u));
+        s_qa[e] = make_int4(site, cx, cy, cz);
+        s_qb[e] = make_int4(ta, __float_as_int(gnn), threadIdx.x, d);
       }
     }
-    acc = 0;
+    __syncthreads();
+    const int nq = s_nq;
+    int tie2 = 0;
+    // stage 2: u2 < min{1, exp[-beta (dE - s g)]}, FP32-screened with the
+    // bound of the plain rule's screen (FP64 by the warp where it cannot
+    // decide).  Every group of MK_GROUP lanes takes one queued trial, so
+    // the block's 128 threads screen 16 trials at a time.
+    const int gl = threadIdx.x & (MK_GROUP - 1);
+    for (int q0 = 0; q0 < nq; q0 += MK_BLOCK / MK_GROUP) {
+      const int e = q0 + threadIdx.x / MK_GROUP;
+      const bool has = e < nq;
+      int4 qa = make_int4(0, 0, 0, 0), qo = make_int4(0, 0, 0, 0);
+      if (has) {
+        qa = s_qa[e];
+        qo = s_qb[e];
+      }
+      long long qpq = 0;
+      float err;
+      bool in;
+      const float e32 = multi_screen_group(a, sDq, sDfs, s_gw[threadIdx.x / MK_GROUP], scode, r, qa.x, qa.y, qa.z,
+                                           qa.w, qo.x, 1 - qo.x, gl, has, &qpq, &err, &in);
+      const bool lead = has && gl == 0;
+      int dec2 = 0;
+      uint64_t u2 = 0;
+      if (lead) {
+        u2 = s_u2[qo.z];
+        const float g = __int_as_float(qo.y);
+        const float cm = qo.x ? g : -g;  // -s g, exact
+        const float x32 = p.beta32 * (e32 + cm);
+        const float dx = p.beta32 * fmaf(4.76837158203125e-07f, fabsf(e32) + fabsf(cm), err) * 1.0001f +
+                         fabsf(x32) * 4.76837158203125e-07f;
+        dec2 = in ? screen32(x32, dx, u2) : -1;
+      }
+      unsigned open = __ballot_sync(0xffffffffu, lead && dec2 < 0);
+      while (open) {
+        const int src = __ffs(open) - 1;
+        open &= open - 1u;
+        const int si = __shfl_sync(0xffffffffu, qa.x, src);
+        const int sa = __shfl_sync(0xffffffffu, qo.x, src);
+        const double v = warp_sum(multi_emb_warp5(a, sFd, scode, s_fw[warp], r, si, sa, 1 - sa, lane));
+        if (lane == src) {
+          const double de64 = (double)qpq * a.qscale + v;
+          if (!isfinite(de64)) atomicOr(a.err, ERRF_NONFINITE);
+          const double sg = qo.x ? -1.0 : 1.0;
+          dec2 = metropolis(p.beta * (de64 - sg * (double)__int_as_float(qo.y)), u2, &tie2) ? 1 : 0;
+        }
+      }
+      if (lead) s_dec[qo.z] = dec2;
+      __syncwarp();  // the group's scratch is rewritten by the next round
+    }
+    __syncthreads();
+    acc = s1 ? s_dec[threadIdx.x] : 0;
+    tie += tie2;
   } else if (d < a.D) {
     ta = a.types[(long long)r * a.N + site];
     tb = multi_target(a, p, step, d, ta);
@@ -1082,10 +1021,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a, i
           make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0xFFFFFFFFu, TAG_STEP), p.key);
       accept = metropolis(Y, top53(wc.z, wc.w), &gtie) ? 1 : 0;
     }
-    // delayed acceptance: the commit walks the step's queue of stage-1
-    // passes (accepts marked by the stage-2 launch) instead of a list
-    const int nlist = a.da ? __ldcg(a.daq_n + (int)(step & 1) * a.R + r) : nacc;
-    s_pre[r + 1] = accept ? nlist * NI : 0;
+    s_pre[r + 1] = accept ? nacc * NI : 0;
     if (blockIdx.x == 0) {
       MRepState s = a.rs[r];
       s.trials += a.D;
@@ -1129,7 +1065,6 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a, i
       B->accept = 0;
       B->s1 = 0;
       B->sum_de = 0.0;
-      if (a.daq_n) a.daq_n[(int)((step + 1) & 1) * a.R + r] = 0;
     }
   }
   for (int q = threadIdx.x; q < MK_BCC5_N; q += MK_BLOCK) s_off[q] = a.off[q];
@@ -1149,16 +1084,7 @@ __global__ void __launch_bounds__(MK_BLOCK) k_multi_commit_screen(MultiArgs a, i
     while (s_pre[r + 1] <= it) ++r;
     const int loc = it - s_pre[r];
     const int q = loc / NI, k = loc - q * NI;
-    int2 e;
-    if (a.da) {
-      // queue entry: site | old species << 30 | accepted << 31
-      const int x = __ldcg(&a.daq[((long long)(step & 1) * a.R + r) * a.D + q].x);
-      if (x >= 0) continue;  // rejected by stage 2
-      const int t0 = (x >> 30) & 1;
-      e = make_int2(x & 0x3FFFFFFF, (1 - t0) | (t0 << 8));
-    } else {
-      e = a.pend[(long long)r * a.D + q];
-    }
+    const int2 e = a.pend[(long long)r * a.D + q];
     const int tb = e.y & 255, ta = e.y >> 8;
     uint8_t* ty = a.types + (long long)r * a.N;
     float2* rf = a.rf + (long long)r * a.rf_n;
@@ -1203,17 +1129,10 @@ void launch_multi_step(const MultiArgs& a, int j, cudaStream_t st, bool after_st
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = after_step ? 1 : 0;
-    if (a.da) {
+    if (a.da)
       cudaLaunchKernelEx(&cfg, k_multi_propose<3>, a, j);
-      // stage 2 over every replica's queue, scheduled while the propose runs
-      cudaLaunchConfig_t c2 = cfg;
-      const int gb = (4 * a.n_sm + a.R - 1) / a.R;
-      c2.gridDim = dim3((unsigned)(gb < 1 ? 1 : (gb > 1024 ? 1024 : gb)), (unsigned)a.R);
-      c2.numAttrs = 1;
-      cudaLaunchKernelEx(&c2, k_multi_da_stage2, a, j);
-    } else {
+    else
       cudaLaunchKernelEx(&cfg, k_multi_propose<2>, a, j);
-    }
     k_multi_commit_screen<<<4 * a.n_sm, MK_BLOCK, 0, st>>>(a, j);
   } else if (a.reembed) {
     k_multi_propose<1><<<grid, MK_BLOCK, 0, st>>>(a, 0);

@@ -131,11 +131,6 @@ struct MultiArgs {
   int da;
   MlpW mlp;
   uint32_t* nbc;
-  // the stage-1 passes of a step, queued per replica for the stage-2
-  // launch: daq[par][R][D] (site, trial, species, g as bits) and their
-  // counts daq_n[par][R], par = step & 1 (the commit zeroes the next one)
-  int4* daq;
-  int* daq_n;
 };
 
 // site index of trial d of colour c (ascending site index within a colour)

@@ -224,7 +224,6 @@ int screen_acc_ready(Multi* m) {
   const int par = (int)(m->h_base & 1);
   for (int r = 0; r < m->R; ++r)
     MCK(cudaMemcpyAsync(m->args.acc + 2 * r + par, &acc[r], sizeof(MStepAcc), cudaMemcpyHostToDevice, m->st));
-  if (m->args.daq_n) MCK(cudaMemsetAsync(m->args.daq_n, 0, sizeof(int) * 2 * m->R, m->st));
   MCK(cudaMemcpyAsync(m->d_base, &m->h_base, sizeof(long long), cudaMemcpyHostToDevice, m->st));
   MCK(cudaStreamSynchronize(m->st));
   m->acc_stale = false;
@@ -706,11 +705,6 @@ int vcsgc_multi_set_surrogate(void* h, void* mlp) {
   if (!a.nbc) {
     MTRY(malloc_dev(m, &a.nbc, (size_t)m->R * a.rf_n));
     m->nbc_stale = true;
-  }
-  if (!a.daq) {
-    MTRY(malloc_dev(m, &a.daq, (size_t)2 * m->R * a.D));
-    MTRY(malloc_dev(m, &a.daq_n, (size_t)2 * m->R));
-    MCK(cudaMemsetAsync(a.daq_n, 0, sizeof(int) * 2 * m->R, m->st));
   }
   // the surrogate's own stream may still be writing its fragments
   MCK(cudaStreamSynchronize(mlp_object_stream(mlp)));
