@@ -772,10 +772,14 @@ __global__ void __launch_bounds__(MK_BLOCK, 4) k_multi_propose(MultiArgs a, int 
       if (lead) {
         u2 = s_u2[qo.z];
         const float g = __int_as_float(qo.y);
-        const float cm = qo.x ? g : -g;  // -s g, exact
+        // -s g (exact) plus the own-site offset of the FP32 tables: two
+        // roundings, inside 2^-21 (|g| + |offset|)
+        const float off = a.emb_off[qo.x * K + 1 - qo.x];
+        const float cm = (qo.x ? g : -g) + off;
         const float x32 = p.beta32 * (e32 + cm);
-        const float dx = p.beta32 * fmaf(4.76837158203125e-07f, fabsf(e32) + fabsf(cm), err) * 1.0001f +
-                         fabsf(x32) * 4.76837158203125e-07f;
+        const float dx =
+            p.beta32 * fmaf(4.76837158203125e-07f, fabsf(e32) + fabsf(g) + fabsf(off), err) * 1.0001f +
+            fabsf(x32) * 4.76837158203125e-07f;
         dec2 = in ? screen32(x32, dx, u2) : -1;
       }
       unsigned open = __ballot_sync(0xffffffffu, lead && dec2 < 0);

@@ -106,15 +106,20 @@ struct MultiArgs {
   // ([K][emb_n], one grid for all species), per site its density as a
   // float and the FP32 embedding value there, the largest error of one FP32
   // embedding evaluation (eV) and the argument range [emb_lo, emb_hi]
-  // inside which that bound holds.
+  // (the densities the lattice can reach) inside which that bound holds.
   int screen;
   const float4* emb32;
   int emb_n;
   float emb_ih;
   float emb_lo, emb_hi;
   float emb_err;
+  // the table of species t holds F_t - F_t(rho_mid) (its coefficients'
+  // rounding then scales with the offset values); emb_off[a K + b] =
+  // F_b(rho_mid) - F_a(rho_mid) as a float, which an own-site change adds
+  float emb_off[MK_MAX * MK_MAX];
   float qscale32;       // 2^-qbits as a float (exact)
-  // (rho_i as float, F32_{t_i} of that) per site, [R][rf_n], laid out by
+  // (rho_i as float, the offset table's F32_{t_i} of that) per site,
+  // [R][rf_n], laid out by
   // (basis, z, y, x mod qx, x div qx): the lanes of a warp, trials qx
   // cells apart along x, read neighbours at one offset from consecutive
   // entries.  rf_q = ceil(nx / qx); rf_n = 2 nz ny qx rf_q

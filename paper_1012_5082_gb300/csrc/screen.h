@@ -57,4 +57,31 @@ inline ScreenBound screen_bound(const std::vector<std::vector<Cubic>>& cubics, d
   return b;
 }
 
+// The same bound for arguments confined to [lo, hi] (the intervals that
+// reach them, and their neighbours in P), for cubics offset by a constant
+// per species.  The offset changes c0 only, so it shrinks G where the
+// function is far from zero; an evaluation of the offset table differs
+// from the FP64 offset cubic by at most the bound returned.
+inline double screen_bound_in(const std::vector<std::vector<Cubic>>& cubics, double h, double dmax, double lo,
+                              double hi) {
+  const int n = (int)cubics[0].size();
+  const int j0 = std::max(0, (int)std::floor(lo / h) - 1);
+  const int j1 = std::min(n - 1, (int)std::floor(hi / h) + 1);
+  double G = 0.0, P = 0.0, S = 0.0;
+  for (const std::vector<Cubic>& hc : cubics) {
+    auto D = [&](int j) {
+      if (j < 0 || j >= n) return 0.0;
+      const Cubic& c = hc[j];
+      return std::fabs(c.y) + 2.0 * std::fabs(c.z) + 3.0 * std::fabs(c.w);
+    };
+    for (int j = j0; j <= j1; ++j) {
+      const Cubic& c = hc[j];
+      G = std::max(G, std::fabs(c.x) + std::fabs(c.y) + std::fabs(c.z) + std::fabs(c.w));
+      S = std::max(S, D(j) / h);
+      P = std::max(P, (double)(j + 2) * std::max(D(j), std::max(D(j - 1), D(j + 1))));
+    }
+  }
+  return std::ldexp(6.0 * G + 5.0 * P + 3.0 * dmax * S, -24) * (1.0 + 1e-6);
+}
+
 }  // namespace vcsgc

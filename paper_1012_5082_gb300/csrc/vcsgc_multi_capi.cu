@@ -48,6 +48,9 @@ struct Multi {
   // at its start) is rewritten from the replicas' states before the next
   // run after the host changed a state or the step base
   bool acc_stale = true;
+  // screened form: F_t at the middle of the reachable densities, the
+  // offset of species t's FP32 embedding table
+  std::vector<double> fref;
 };
 
 #define MCK(call)                                                                      \
@@ -294,25 +297,67 @@ int screen_setup(Multi* m, const std::vector<double>& hFd) {
   float4* e32 = nullptr;
   MTRY(malloc_dev(m, &e32, (size_t)m->K * n));
   std::vector<std::vector<Cubic>> hc((size_t)m->K, std::vector<Cubic>((size_t)n));
-  for (int al = 0; al < m->K; ++al) {
-    launch_to_cubic32(a.embed[al].c, n, reinterpret_cast<Cubic32*>(e32 + (size_t)al * n), m->st);
-    MCK(cudaGetLastError());
+  for (int al = 0; al < m->K; ++al)
     MCK(cudaMemcpyAsync(hc[al].data(), a.embed[al].c, sizeof(Cubic) * n, cudaMemcpyDeviceToHost, m->st));
-  }
   MCK(cudaStreamSynchronize(m->st));
+  const double h = 1.0 / a.embed[0].inv_h;
   double dmax = 0.0;
   for (int s = 0; s < a.n_sh; ++s)
     for (int x = 0; x < m->K; ++x)
       for (int y = 0; y < m->K; ++y) dmax = std::max(dmax, std::fabs(hFd[s * m->K + y] - hFd[s * m->K + x]));
-  const ScreenBound sb = screen_bound(hc, 1.0 / a.embed[0].inv_h, dmax);
-  if (!std::isfinite(sb.err)) return mfail(m, VCSGC_ERR_NONFINITE, "non-finite embedding table");
+  // Every site of the rigid five-shell lattice has the same 58 neighbours,
+  // so its density lies between the sums of each shell's smallest and
+  // largest f, and a screened argument (a density plus one shell's f_b -
+  // f_a) within dmax of that (with a margin for float rounding and the
+  // FP64 densities' accumulated updates).  Arguments outside go to FP64.
+  std::vector<int> n_s((size_t)a.n_sh, 0);
+  for (int k = 0; k < a.n_off; ++k) n_s[a.off[k].w]++;
+  double rmin = 0.0, rmax = 0.0;
+  for (int s = 0; s < a.n_sh; ++s) {
+    double fl = hFd[s * m->K], fh = hFd[s * m->K];
+    for (int x = 1; x < m->K; ++x) {
+      fl = std::min(fl, hFd[s * m->K + x]);
+      fh = std::max(fh, hFd[s * m->K + x]);
+    }
+    rmin += n_s[s] * fl;
+    rmax += n_s[s] * fh;
+  }
+  const double xmax = n * h * (1.0 - 1e-6);
+  const double lo = std::max(h, (rmin - dmax) * (1.0 - 1e-5));
+  const double hi = std::min(xmax, (rmax + dmax) * (1.0 + 1e-5));
+  if (!(lo < hi)) return mfail(m, VCSGC_ERR_TABLE_RANGE, "densities outside the embedding grid");
+  // FP32 tables of F_t - F_t(rho_mid): differences of one species' values
+  // are unchanged, the own-site change gets F_b(rho_mid) - F_a(rho_mid)
+  // back through the screen's constant, and the coefficients' rounding
+  // (the bound's largest term) scales with the smaller values
+  const double rmid = 0.5 * (rmin + rmax);
+  std::vector<std::vector<Cubic>> hs = hc;
+  std::vector<float4> h32((size_t)m->K * n);
+  m->fref.assign((size_t)m->K, 0.0);
+  for (int al = 0; al < m->K; ++al) {
+    const int jm = std::min(n - 1, (int)(rmid / h));
+    const double tt = rmid / h - jm;
+    const Cubic& cm = hc[al][jm];
+    m->fref[al] = cm.x + tt * (cm.y + tt * (cm.z + tt * cm.w));
+    for (int j = 0; j < n; ++j) {
+      hs[al][j].x -= m->fref[al];
+      const Cubic& q = hs[al][j];
+      h32[(size_t)al * n + j] = make_float4((float)q.x, (float)q.y, (float)q.z, (float)q.w);
+    }
+  }
+  MCK(cudaMemcpyAsync(e32, h32.data(), sizeof(float4) * h32.size(), cudaMemcpyHostToDevice, m->st));
+  MCK(cudaStreamSynchronize(m->st));
+  const double err = screen_bound_in(hs, h, dmax, lo, hi);
+  if (!std::isfinite(err)) return mfail(m, VCSGC_ERR_NONFINITE, "non-finite embedding table");
+  for (int x = 0; x < m->K; ++x)
+    for (int y = 0; y < m->K; ++y) a.emb_off[x * m->K + y] = (float)(m->fref[y] - m->fref[x]);
   MCK(cudaDeviceGetAttribute(&a.n_sm, cudaDevAttrMultiProcessorCount, m->device));
   a.emb32 = e32;
   a.emb_n = n;
   a.emb_ih = (float)a.embed[0].inv_h;
-  a.emb_lo = (float)sb.lo;
-  a.emb_hi = (float)sb.hi;
-  a.emb_err = (float)sb.err;
+  a.emb_lo = (float)lo;
+  a.emb_hi = (float)hi;
+  a.emb_err = (float)err;
   a.rf_q = (m->nx + a.qx - 1) / a.qx;
   a.rf_n = 2LL * m->nz * m->ny * a.qx * a.rf_q;
   MTRY(malloc_dev(m, &a.rf, (size_t)m->R * a.rf_n));
@@ -528,7 +573,9 @@ int init(Multi* m, const vcsgc_lattice* L, const uint8_t* types, const vcsgc_mul
     for (int x = 0; x < m->K; ++x)
       for (int y = 0; y < m->K; ++y) {
         p.c32[x * m->K + y] = (float)(hdF[x * m->K + y] + p.dmu0[y] - p.dmu0[x]);
-        p.cmu32[x * m->K + y] = (float)(p.dmu0[y] - p.dmu0[x]);
+        // the screened form's FP32 embedding tables are offset by fref
+        const double off = a.screen ? m->fref[y] - m->fref[x] : 0.0;
+        p.cmu32[x * m->K + y] = (float)(p.dmu0[y] - p.dmu0[x] + off);
       }
   }
   MCK(cudaMemcpyAsync(rp, m->h_rp.data(), sizeof(MRepParams) * R, cudaMemcpyHostToDevice, m->st));

@@ -92,6 +92,87 @@ def test_fp32_embedding_error_within_bound(K, ds):
     assert 118 * E < 0.01 * I.KB_EV * 1200.0
 
 
+@pytest.mark.parametrize("K,ds", [(4, (1.0, 1.25, 0.85, 1.1)), (2, (1.0, 1.25))])
+def test_offset_tables_within_the_reachable_range_bound(K, ds):
+    """The multicomponent screen's tables: each species' cubics offset by
+    its value at the middle of the densities a rigid five-shell lattice can
+    reach (the 58 neighbours' f summed shell by shell, smallest to largest
+    species), the bound taken over the intervals reaching [rho_min - dmax,
+    rho_max + dmax] only.  Float evaluations of the offset tables stay within
+    it, and it is tighter than the full-table bound."""
+    p = I.multi_eam_params(K, dens_scale=ds)
+    T = I.eam_tables(p)
+    h, n = T.drho, T.nrho - 1
+    ih = 1.0 / h
+    coefs = [_coefficients(np.asarray(T.embed[t]), np.asarray(T.dembed[t]), h) for t in range(K)]
+    rs = A * np.sqrt(np.array([3, 4, 8, 11, 12])) / 2
+    ns = np.array([8, 6, 12, 24, 8])
+    Fd = np.array([[p.dens(t, r)[0] for t in range(K)] for r in rs])
+    dmax = np.abs(Fd[:, :, None] - Fd[:, None, :]).max()
+    rmin, rmax = (ns * Fd.min(1)).sum(), (ns * Fd.max(1)).sum()
+    lo = max(h, (rmin - dmax) * (1 - 1e-5))
+    hi = min(n * h * (1 - 1e-6), (rmax + dmax) * (1 + 1e-5))
+    rmid = 0.5 * (rmin + rmax)
+    jm = min(n - 1, int(rmid / h))
+    tm = rmid / h - jm
+    fref = np.array([C[jm, 0] + tm * (C[jm, 1] + tm * (C[jm, 2] + tm * C[jm, 3])) for C in coefs])
+    shifted = [C - np.array([f, 0.0, 0.0, 0.0]) for C, f in zip(coefs, fref)]
+    j0, j1 = max(0, int(np.floor(lo / h)) - 1), min(n - 1, int(np.floor(hi / h)) + 1)
+    G = P = S = 0.0
+    for C in shifted:
+        D = np.abs(C[:, 1]) + 2 * np.abs(C[:, 2]) + 3 * np.abs(C[:, 3])
+        Dp = np.r_[0.0, D, 0.0]
+        Dn = np.maximum(D, np.maximum(Dp[:-2], Dp[2:]))
+        G = max(G, np.abs(C[j0:j1 + 1]).sum(1).max())
+        S = max(S, D[j0:j1 + 1].max() * ih)
+        P = max(P, ((np.arange(n) + 2) * Dn)[j0:j1 + 1].max())
+    E = 2.0 ** -24 * (6 * G + 5 * P + 3 * dmax * S)
+
+    rng = np.random.default_rng(17)
+    M = 400_000
+    t = rng.integers(0, K, M)
+    rho = rng.uniform(rmin, rmax, M)
+    s, a, b = rng.integers(0, 5, M), rng.integers(0, K, M), rng.integers(0, K, M)
+    dfs = Fd[s, b] - Fd[s, a]
+    Call = np.stack(coefs)
+    Cs = np.stack(shifted)
+
+    def ev64(x):
+        u = x * ih
+        j = np.minimum(u.astype(np.int64), n - 1)
+        tt = u - j
+        c = Call[t, j]
+        return c[:, 0] + tt * (c[:, 1] + tt * (c[:, 2] + tt * c[:, 3])) - fref[t]
+
+    def ev32(x32):
+        u = (x32 * np.float32(ih)).astype(np.float32)
+        j = np.minimum(u.astype(np.int64), n - 1)
+        tt = (u - j.astype(np.float32)).astype(np.float32)
+        c = Cs[t, j].astype(np.float32)
+        return _fma32(tt, _fma32(tt, _fma32(tt, c[:, 3], c[:, 2]), c[:, 1]), c[:, 0])
+
+    r32 = rho.astype(np.float32)
+    x32 = (r32 + dfs.astype(np.float32)).astype(np.float32)
+    assert np.all((x32 >= lo) & (x32 <= hi))
+    err1 = np.abs(ev32(x32).astype(np.float64) - ev64(rho + dfs))
+    err0 = np.abs(ev32(r32).astype(np.float64) - ev64(rho))
+    worst = max(err1.max(), err0.max())
+    assert worst <= E, (worst, E)
+    # tighter than the bound over the whole table without offsets
+    lo_full = max(h, (n * h) / 20.0)
+    jlo = max(0, int(np.floor(lo_full / h)) - 1)
+    Gf = Pf = Sf = 0.0
+    for C in coefs:
+        D = np.abs(C[:, 1]) + 2 * np.abs(C[:, 2]) + 3 * np.abs(C[:, 3])
+        Gf = max(Gf, np.abs(C[jlo:]).sum(1).max())
+        Sf = max(Sf, D[jlo:].max() * ih)
+        Dn = np.maximum(D, np.maximum(np.r_[0.0, D[:-1]], np.r_[D[1:], 0.0]))
+        Pf = max(Pf, ((np.arange(n) + 2) * Dn)[jlo + 1:].max())
+    E_full = 2.0 ** -24 * (6 * Gf + 5 * Pf + 3 * dmax * Sf)
+    print(f"K={K}: offset bound {E:.3g} eV, full-table bound {E_full:.3g} eV, worst {worst:.3g} eV")
+    assert E < 0.6 * E_full
+
+
 def _screen(x32, dx, u53, second_order=True, guard=True):
     """The FP32 screen's rule restated in numpy (float32 arithmetic):
     accept, reject or -1 (undecided) for u = u53 2^-53 against exp(-X),
