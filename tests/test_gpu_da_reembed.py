@@ -119,6 +119,53 @@ def test_constant_surrogate_chain_and_kept_counts(V, torch, tab):
     s.close()
 
 
+def test_multiblock_lockstep_plain_then_constant_surrogate(V, torch, tab):
+    """40^3 x 2 replicas: 1,000 trials per replica per colour step over 8
+    blocks, so the block queues of stage 2, the global decision the commit
+    takes from every block's sums and the count words kept across blocks
+    all run as at full size.  3 sweeps of the plain rule, then 3 with a
+    constant surrogate, in lockstep with the oracle's chains; the
+    descriptors of 2,000 sampled sites then equal the oracle's."""
+    lat = I.bcc_lattice(40, 40, 40)
+    t = I.random_types(lat.n, int(0.05 * lat.n), seed=97)
+    phis, seeds = [-2.2, -2.25], [98, 99]
+    orcs = []
+    for phi, seed in zip(phis, seeds):
+        o = O.System(lat, t, tab)
+        o.set_params(phi, KAPPA, T_K, c0=C0, seed=seed)
+        o.schedule_sublattice(lat.cells, (4, 4, 4))
+        o.set_shells(SHELL_R)
+        orcs.append(o)
+    b = V.Context(lat, np.tile(t, 2), tab, 0.0, KAPPA, T_K, c0=C0, schedule=V.SCHED_SUBLATTICE, sched=(4, 4, 4),
+                  n_replicas=2, phi_r=np.array(phis), seed_r=np.array(seeds, dtype=np.uint64))
+    ls = Lockstep(orcs, b)
+    for _ in range(3):
+        ls.advance(b.steps_per_sweep)
+    a_sites = np.nonzero(orcs[0].types == 0)[0][:400]
+    g0 = float(np.float32(np.mean([orcs[0].delta_e(i) for i in a_sites])))
+    p = np.zeros(M.NPARAM, np.float32)
+    p[-1] = g0
+    s = V.Surrogate(p)
+    b.set_surrogate(s)
+    for o in orcs:
+        o.set_surrogate("mlp", p.astype(np.float64))
+    for _ in range(3):
+        ls.advance(b.steps_per_sweep)
+    for r, o in enumerate(orcs):
+        og, oo = b.observables(r), o.obs()
+        assert og["flips"] > 1000, og["flips"]
+        assert 0 < og["stage1_accepts"] < og["trials"]
+        if ls.resyncs == 0:
+            assert og["stage1_accepts"] == oo["stage1_accepts"]
+    X, Y = b.features()
+    rng = np.random.default_rng(9)
+    _check_features(X.cpu().numpy(), Y.cpu().numpy().astype(np.float64), orcs, lat.n,
+                    sample=sorted(rng.choice(lat.n, 1000, replace=False)))
+    ls.close()
+    b.close()
+    s.close()
+
+
 def test_multicomponent_object_surrogate(V, torch, tab):
     """The K = 2 multicomponent object takes the surrogate directly and runs
     the same two-stage chain as the oracle; K = 3, or no re-embedding, is
