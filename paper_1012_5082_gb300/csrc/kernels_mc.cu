@@ -105,7 +105,12 @@ __device__ double delta_e(const McArgs& a, int r, int i, unsigned* err) {
 
 // The general (explicit-position) form of dE by one warp: lanes take
 // neighbours k = lane, lane + 32, ...; partial sums meet in a shuffle tree.
-// Every lane returns the total.
+// Every lane returns the total.  The neighbours come in chunks of 96, three
+// per lane, whose list entries, then positions and species, then table
+// cubics load together (each lane adds its neighbours in the order k, as a
+// one-at-a-time loop would).
+constexpr int MCW_SLOTS = 3;
+
 template <bool REEMBED, bool MIXED>
 __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned* err) {
   const uint8_t* ty = a.types + (long long)r * a.N;
@@ -117,45 +122,64 @@ __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned
   const double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
   const double rc2 = a.rc * a.rc;
   double part = 0.0;
-  for (int k = lane; k < cnt; k += 32) {
-    const int j = row[k];
-    const int tj = ty[j];
-    double vp, vm, fp = 0.0, fm = 0.0;
-    if constexpr (MIXED) {
-      // FP32 distance and table values, FP64 differences and sums
-      const float dx = mimg32(a.x[j], xi, (float)a.box[0], (float)(1.0 / a.box[0]));
-      const float dy = mimg32(a.y[j], yi, (float)a.box[1], (float)(1.0 / a.box[1]));
-      const float dz = mimg32(a.z[j], zi, (float)a.box[2], (float)(1.0 / a.box[2]));
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 >= (float)rc2) continue;
-      float tt;
-      const int jj = spline32_locate(a.tab32.sp[0], sqrtf(r2), tt, err);
-      vp = (double)spline32_val_at(a.tab32.sp[tp + tj], jj, tt);
-      vm = (double)spline32_val_at(a.tab32.sp[t + tj], jj, tt);
-      if (REEMBED) {
-        fp = (double)spline32_val_at(a.tab32.sp[3 + tp], jj, tt);
-        fm = (double)spline32_val_at(a.tab32.sp[3 + t], jj, tt);
-      }
-    } else {
-      const double dx = min_image(a.x[j] - xi, a.box[0]);
-      const double dy = min_image(a.y[j] - yi, a.box[1]);
-      const double dz = min_image(a.z[j] - zi, a.box[2]);
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 >= rc2) continue;
-      double tt;
-      const int jj = spline_locate(a.tab.sp[0], r2 * rsqrt_nr(r2), tt, err);
-      vp = spline_val_at(a.tab.sp[tp + tj], jj, tt);
-      vm = spline_val_at(a.tab.sp[t + tj], jj, tt);
-      if (REEMBED) {
-        fp = spline_val_at(a.tab.sp[3 + tp], jj, tt);
-        fm = spline_val_at(a.tab.sp[3 + t], jj, tt);
-      }
+  for (int k0 = 0; k0 < cnt; k0 += 32 * MCW_SLOTS) {
+    int jv[MCW_SLOTS];
+    bool in[MCW_SLOTS];
+#pragma unroll
+    for (int u = 0; u < MCW_SLOTS; ++u) {
+      const int k = k0 + lane + 32 * u;
+      in[u] = k < cnt;
+      jv[u] = in[u] ? row[k] : i;
     }
-    part += vp - vm;
-    if constexpr (REEMBED) {
-      const double drho = fp - fm;
-      const double rj = rho[j];
-      part += spline_val(a.tab.sp[5 + tj], rj + drho, err) - spline_val(a.tab.sp[5 + tj], rj, err);
+    int tj[MCW_SLOTS];
+    double xj[MCW_SLOTS], yj[MCW_SLOTS], zj[MCW_SLOTS], rj[MCW_SLOTS];
+#pragma unroll
+    for (int u = 0; u < MCW_SLOTS; ++u) {
+      tj[u] = ty[jv[u]];
+      xj[u] = a.x[jv[u]];
+      yj[u] = a.y[jv[u]];
+      zj[u] = a.z[jv[u]];
+      rj[u] = REEMBED ? rho[jv[u]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < MCW_SLOTS; ++u) {
+      if (!in[u]) continue;
+      double vp, vm, fp = 0.0, fm = 0.0;
+      if constexpr (MIXED) {
+        // FP32 distance and table values, FP64 differences and sums
+        const float dx = mimg32(xj[u], xi, (float)a.box[0], (float)(1.0 / a.box[0]));
+        const float dy = mimg32(yj[u], yi, (float)a.box[1], (float)(1.0 / a.box[1]));
+        const float dz = mimg32(zj[u], zi, (float)a.box[2], (float)(1.0 / a.box[2]));
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= (float)rc2) continue;
+        float tt;
+        const int jj = spline32_locate(a.tab32.sp[0], sqrtf(r2), tt, err);
+        vp = (double)spline32_val_at(a.tab32.sp[tp + tj[u]], jj, tt);
+        vm = (double)spline32_val_at(a.tab32.sp[t + tj[u]], jj, tt);
+        if (REEMBED) {
+          fp = (double)spline32_val_at(a.tab32.sp[3 + tp], jj, tt);
+          fm = (double)spline32_val_at(a.tab32.sp[3 + t], jj, tt);
+        }
+      } else {
+        const double dx = min_image(xj[u] - xi, a.box[0]);
+        const double dy = min_image(yj[u] - yi, a.box[1]);
+        const double dz = min_image(zj[u] - zi, a.box[2]);
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 >= rc2) continue;
+        double tt;
+        const int jj = spline_locate(a.tab.sp[0], r2 * rsqrt_nr(r2), tt, err);
+        vp = spline_val_at(a.tab.sp[tp + tj[u]], jj, tt);
+        vm = spline_val_at(a.tab.sp[t + tj[u]], jj, tt);
+        if (REEMBED) {
+          fp = spline_val_at(a.tab.sp[3 + tp], jj, tt);
+          fm = spline_val_at(a.tab.sp[3 + t], jj, tt);
+        }
+      }
+      part += vp - vm;
+      if constexpr (REEMBED) {
+        const double drho = fp - fm;
+        part += spline_val(a.tab.sp[5 + tj[u]], rj[u] + drho, err) - spline_val(a.tab.sp[5 + tj[u]], rj[u], err);
+      }
     }
   }
 #pragma unroll
