@@ -309,7 +309,8 @@ int screen_setup(Multi* m, const std::vector<double>& hFd) {
   // so its density lies between the sums of each shell's smallest and
   // largest f, and a screened argument (a density plus one shell's f_b -
   // f_a) within dmax of that (with a margin for float rounding and the
-  // FP64 densities' accumulated updates).  Arguments outside go to FP64.
+  // FP64 densities' accumulated updates), clipped to the grid.  Arguments
+  // outside go to FP64.
   std::vector<int> n_s((size_t)a.n_sh, 0);
   for (int k = 0; k < a.n_off; ++k) n_s[a.off[k].w]++;
   double rmin = 0.0, rmax = 0.0;
@@ -323,19 +324,24 @@ int screen_setup(Multi* m, const std::vector<double>& hFd) {
     rmax += n_s[s] * fh;
   }
   const double xmax = n * h * (1.0 - 1e-6);
-  const double lo = std::max(h, (rmin - dmax) * (1.0 - 1e-5));
-  const double hi = std::min(xmax, (rmax + dmax) * (1.0 + 1e-5));
-  if (!(lo < hi)) return mfail(m, VCSGC_ERR_TABLE_RANGE, "densities outside the embedding grid");
+  double lo = std::max(h, (rmin - dmax) * (1.0 - 1e-5));
+  double hi = std::min(xmax, (rmax + dmax) * (1.0 + 1e-5));
+  if (!(lo < hi)) {
+    // the reachable densities lie beyond the grid: the whole grid's range
+    // (every trial then takes the FP64 path, which reports the table range)
+    lo = std::max(h, n * h / 20.0);
+    hi = xmax;
+  }
   // FP32 tables of F_t - F_t(rho_mid): differences of one species' values
   // are unchanged, the own-site change gets F_b(rho_mid) - F_a(rho_mid)
   // back through the screen's constant, and the coefficients' rounding
   // (the bound's largest term) scales with the smaller values
-  const double rmid = 0.5 * (rmin + rmax);
+  const double rmid = std::min(hi, std::max(lo, 0.5 * (rmin + rmax)));
   std::vector<std::vector<Cubic>> hs = hc;
   std::vector<float4> h32((size_t)m->K * n);
   m->fref.assign((size_t)m->K, 0.0);
   for (int al = 0; al < m->K; ++al) {
-    const int jm = std::min(n - 1, (int)(rmid / h));
+    const int jm = std::max(0, std::min(n - 1, (int)(rmid / h)));
     const double tt = rmid / h - jm;
     const Cubic& cm = hc[al][jm];
     m->fref[al] = cm.x + tt * (cm.y + tt * (cm.z + tt * cm.w));

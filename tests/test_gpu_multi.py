@@ -159,13 +159,16 @@ def test_multi_screened_reembedding_16cubed(V):
     g.close()
 
 
-def test_multi_screen_out_of_range_goes_fp64(V):
-    """An embedding grid to rho = 400 puts every density (about 15) below
-    the screened range (rho >= x_max / 20), so every trial of the
-    re-embedding step takes the FP64 path of the whole warp: the
-    trajectory still follows the oracle's site for site."""
+@pytest.mark.parametrize("nrho", [5000, 8])
+def test_multi_screen_out_of_range_goes_fp64(V, nrho):
+    """Embedding grids to rho = 400.  With 5000 points the screen covers
+    the densities the five shells can reach (about 12 to 18).  With 8
+    points (h = 57) every reachable density lies in the grid's first
+    interval, below the screened range, so the context still opens and
+    every trial of the re-embedding step takes the FP64 path of the whole
+    warp.  Either way the trajectory follows the oracle's site for site."""
     ds, phi, kappa, T, c0 = CASES[4]
-    tab = I.eam_tables(I.multi_eam_params(4, dens_scale=ds, rho_max=400.0))
+    tab = I.eam_tables(I.multi_eam_params(4, dens_scale=ds, rho_max=400.0, nrho=nrho))
     lat = I.bcc_lattice(8, 8, 8)
     t = I.multi_random_types(lat.n, [int(c0 * lat.n)] * 3, seed=5)
     orc = O.MultiSystem(lat, t, tab)
