@@ -198,9 +198,15 @@ __device__ __forceinline__ float spline32_dval_at(const Spline32& ds, int j, flo
 }
 
 // minimum-image separation in FP32 of two FP64 coordinates (difference in FP64)
-__device__ __forceinline__ float mimg32(double xj, double xi, float L, float iL) {
-  float d = (float)(xj - xi);
-  return d - L * rintf(d * iL);
+// Explicit positions of the mixed form as fixed-point fractions of the box,
+// u = x / L 2^32 mod 2^32 per axis.  The difference of two words read as a
+// signed 32-bit integer is the minimum-image separation in units of L 2^-32,
+// exactly (wrap-around of the integer is the periodic image), so the FP32
+// separation carries only the int-to-float and scale roundings (3 2^-24
+// relative) and the quantisation (L 2^-33; 2.9e-8 A in a 250 A box)
+// whatever the box size, with no FP64 arithmetic per pair.  ul = L 2^-32.
+__device__ __forceinline__ float fix_diff(uint32_t uj, uint32_t ui, float ul) {
+  return (float)(int32_t)(uj - ui) * ul;
 }
 
 // ------------------------------------------------------------ Metropolis
@@ -336,6 +342,8 @@ struct McArgs {
   const double* x;
   const double* y;
   const double* z;
+  uint32_t *ux, *uy, *uz;  // fixed-point copies (mixed form; fix_diff)
+  float ul[3];             // L 2^-32 per axis
   double box[3];
   double rc;
   Tables tab;

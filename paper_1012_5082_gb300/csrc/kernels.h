@@ -278,6 +278,8 @@ struct MdArgs {
   float* dFp32;  // the same in FP32 (mixed form)
   double* dF;    // F_B(rho_i) - F_A(rho_i)
   double *x0, *y0, *z0;  // positions at the last neighbour build
+  uint32_t *ux, *uy, *uz;  // fixed-point copies of x, y, z (mixed form; fix_diff)
+  float ul[3];             // L 2^-32 per axis
   double box[3];
   double rc;
   double mass[2];
@@ -291,6 +293,10 @@ struct MdArgs {
   double* vir;   // accumulates the virial sum r_ij . F_ij (FP64 forms) when set
   double lam;    // box length over its length at the last neighbour build
 };
+// u = x / L 2^32 mod 2^32 per axis (fix_diff)
+void launch_fix_positions(long long N, const double* x, const double* y, const double* z, const double box[3],
+                          uint32_t* ux, uint32_t* uy, uint32_t* uz, cudaStream_t st);
+// the mixed form refreshes the fixed-point positions first
 void launch_md_rho(const MdArgs& m, cudaStream_t st);
 void launch_md_force(const MdArgs& m, cudaStream_t st);
 void launch_md_first_half(const MdArgs& m, long long md_step, cudaStream_t st);

@@ -118,7 +118,9 @@ __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned
   const int tp = 1 - t;
   const int* row = a.nbr + (long long)i * a.K;
   const int cnt = a.nbr_cnt[i];
-  const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
+  // FP64 positions, or the mixed form's fixed-point words (fix_diff)
+  const double xi = MIXED ? 0.0 : a.x[i], yi = MIXED ? 0.0 : a.y[i], zi = MIXED ? 0.0 : a.z[i];
+  const uint32_t uxi = MIXED ? a.ux[i] : 0u, uyi = MIXED ? a.uy[i] : 0u, uzi = MIXED ? a.uz[i] : 0u;
   const double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
   const double rc2 = a.rc * a.rc;
   double part = 0.0;
@@ -133,12 +135,19 @@ __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned
     }
     int tj[MCW_SLOTS];
     double xj[MCW_SLOTS], yj[MCW_SLOTS], zj[MCW_SLOTS], rj[MCW_SLOTS];
+    uint32_t uxj[MCW_SLOTS], uyj[MCW_SLOTS], uzj[MCW_SLOTS];
 #pragma unroll
     for (int u = 0; u < MCW_SLOTS; ++u) {
       tj[u] = ty[jv[u]];
-      xj[u] = a.x[jv[u]];
-      yj[u] = a.y[jv[u]];
-      zj[u] = a.z[jv[u]];
+      if constexpr (MIXED) {
+        uxj[u] = a.ux[jv[u]];
+        uyj[u] = a.uy[jv[u]];
+        uzj[u] = a.uz[jv[u]];
+      } else {
+        xj[u] = a.x[jv[u]];
+        yj[u] = a.y[jv[u]];
+        zj[u] = a.z[jv[u]];
+      }
       rj[u] = REEMBED ? rho[jv[u]] : 0.0;
     }
 #pragma unroll
@@ -147,9 +156,9 @@ __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned
       double vp, vm, fp = 0.0, fm = 0.0;
       if constexpr (MIXED) {
         // FP32 distance and table values, FP64 differences and sums
-        const float dx = mimg32(xj[u], xi, (float)a.box[0], (float)(1.0 / a.box[0]));
-        const float dy = mimg32(yj[u], yi, (float)a.box[1], (float)(1.0 / a.box[1]));
-        const float dz = mimg32(zj[u], zi, (float)a.box[2], (float)(1.0 / a.box[2]));
+        const float dx = fix_diff(uxj[u], uxi, a.ul[0]);
+        const float dy = fix_diff(uyj[u], uyi, a.ul[1]);
+        const float dz = fix_diff(uzj[u], uzi, a.ul[2]);
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= (float)rc2) continue;
         float tt;

@@ -18,15 +18,16 @@ __global__ void k_md_rho(MdArgs m) {
   const int* row = m.nbr + i * m.K;
   const int cnt = m.nbr_cnt[i];
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  const uint32_t uxi = MIXED ? m.ux[i] : 0u, uyi = MIXED ? m.uy[i] : 0u, uzi = MIXED ? m.uz[i] : 0u;
   const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
   const double rc2 = m.rc * m.rc;
   double rho = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
     if constexpr (MIXED) {
-      const float dx = mimg32(m.x[j], xi, (float)m.box[0], (float)ix);
-      const float dy = mimg32(m.y[j], yi, (float)m.box[1], (float)iy);
-      const float dz = mimg32(m.z[j], zi, (float)m.box[2], (float)iz);
+      const float dx = fix_diff(m.ux[j], uxi, m.ul[0]);
+      const float dy = fix_diff(m.uy[j], uyi, m.ul[1]);
+      const float dz = fix_diff(m.uz[j], uzi, m.ul[2]);
       const float r2 = dx * dx + dy * dy + dz * dz;
       if (r2 >= (float)rc2) continue;
       float t;
@@ -99,17 +100,15 @@ __global__ void k_md_rho_half32(MdArgs m) {
   if (i >= m.N) return;
   const int* row = m.nbr_h + i * m.K;
   const int cnt = m.cnt_h[i];
-  const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
-  const float bx = (float)m.box[0], by = (float)m.box[1], bz = (float)m.box[2];
-  const float ix = (float)(1.0 / m.box[0]), iy = (float)(1.0 / m.box[1]), iz = (float)(1.0 / m.box[2]);
+  const uint32_t uxi = m.ux[i], uyi = m.uy[i], uzi = m.uz[i];
   const float rc2 = (float)(m.rc * m.rc);
   const int ti = m.types[i];
   double rho = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
-    const float dx = mimg32(m.x[j], xi, bx, ix);
-    const float dy = mimg32(m.y[j], yi, by, iy);
-    const float dz = mimg32(m.z[j], zi, bz, iz);
+    const float dx = fix_diff(m.ux[j], uxi, m.ul[0]);
+    const float dy = fix_diff(m.uy[j], uyi, m.ul[1]);
+    const float dz = fix_diff(m.uz[j], uzi, m.ul[2]);
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= rc2) continue;
     const int tj = m.types[j];
@@ -128,18 +127,16 @@ __global__ void k_md_force_half32(MdArgs m) {
   if (i >= m.N) return;
   const int* row = m.nbr_h + i * m.K;
   const int cnt = m.cnt_h[i];
-  const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
+  const uint32_t uxi = m.ux[i], uyi = m.uy[i], uzi = m.uz[i];
   const int ti = m.types[i];
   const float Fi = m.dFp32[i];
-  const float bx = (float)m.box[0], by = (float)m.box[1], bz = (float)m.box[2];
-  const float ix = (float)(1.0 / m.box[0]), iy = (float)(1.0 / m.box[1]), iz = (float)(1.0 / m.box[2]);
   const float rc2 = (float)(m.rc * m.rc);
   double fx = 0.0, fy = 0.0, fz = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
-    const float dx = mimg32(m.x[j], xi, bx, ix);
-    const float dy = mimg32(m.y[j], yi, by, iy);
-    const float dz = mimg32(m.z[j], zi, bz, iz);
+    const float dx = fix_diff(m.ux[j], uxi, m.ul[0]);
+    const float dy = fix_diff(m.uy[j], uyi, m.ul[1]);
+    const float dz = fix_diff(m.uz[j], uzi, m.ul[2]);
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= rc2) continue;
     const float ir = rsqrtf(r2);
@@ -257,13 +254,14 @@ __device__ __forceinline__ void force_row(const MdArgs& m, long long i, double& 
   const double rc2 = m.rc * m.rc;
   double fx = 0.0, fy = 0.0, fz = 0.0;
   const float Fi32 = (float)Fi;
+  const uint32_t uxi = MIXED ? m.ux[i] : 0u, uyi = MIXED ? m.uy[i] : 0u, uzi = MIXED ? m.uz[i] : 0u;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
     if constexpr (MIXED) {
       // FP32 geometry and table derivatives, FP64 force sums
-      const float dx = mimg32(m.x[j], xi, (float)m.box[0], (float)ix);
-      const float dy = mimg32(m.y[j], yi, (float)m.box[1], (float)iy);
-      const float dz = mimg32(m.z[j], zi, (float)m.box[2], (float)iz);
+      const float dx = fix_diff(m.ux[j], uxi, m.ul[0]);
+      const float dy = fix_diff(m.uy[j], uyi, m.ul[1]);
+      const float dz = fix_diff(m.uz[j], uzi, m.ul[2]);
       const float r2 = dx * dx + dy * dy + dz * dz;
       if (r2 >= (float)rc2) continue;
       const float ir = rsqrtf(r2);
@@ -484,7 +482,27 @@ __global__ void __launch_bounds__(KE_BLOCK) k_kinetic(MdArgs m, double* part) {
 
 static unsigned grid_of(long long N) { return (unsigned)((N + 127) / 128); }
 
+__global__ void k_fix_positions(long long N, const double* x, const double* y, const double* z, double sx, double sy,
+                                double sz, uint32_t* ux, uint32_t* uy, uint32_t* uz) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  // x 2^32 / L rounded to an integer, reduced mod 2^32 (two's complement
+  // wrap of a negative or >= 2^32 value is the periodic reduction)
+  ux[i] = (uint32_t)(unsigned long long)llrint(x[i] * sx);
+  uy[i] = (uint32_t)(unsigned long long)llrint(y[i] * sy);
+  uz[i] = (uint32_t)(unsigned long long)llrint(z[i] * sz);
+}
+
+void launch_fix_positions(long long N, const double* x, const double* y, const double* z, const double box[3],
+                          uint32_t* ux, uint32_t* uy, uint32_t* uz, cudaStream_t st) {
+  if (N < 1 || !ux || !uy || !uz) return;
+  const double two32 = 4294967296.0;
+  k_fix_positions<<<grid_of(N), 128, 0, st>>>(N, x, y, z, two32 / box[0], two32 / box[1], two32 / box[2], ux, uy,
+                                              uz);
+}
+
 void launch_md_rho(const MdArgs& m, cudaStream_t st) {
+  if (m.mixed) launch_fix_positions(m.N, m.x, m.y, m.z, m.box, m.ux, m.uy, m.uz, st);
   if (m.nbr_h) {
     cudaMemsetAsync(m.rho, 0, sizeof(double) * m.N, st);
     if (m.mixed) k_md_rho_half32<<<grid_of(m.N), 128, 0, st>>>(m);

@@ -362,9 +362,9 @@ __device__ __forceinline__ double pair_r(const McArgs& a, bool shell, int i, int
 // FP32 distance of pair (i, j) for the mixed form (r_s on the rigid lattice)
 __device__ __forceinline__ float pair_r32(const McArgs& a, bool shell, int i, int j, int s) {
   if (shell) return (float)a.shell_tab[1 + 2 * a.n_shells + s];
-  const float dx = mimg32(a.x[j], a.x[i], (float)a.box[0], (float)(1.0 / a.box[0]));
-  const float dy = mimg32(a.y[j], a.y[i], (float)a.box[1], (float)(1.0 / a.box[1]));
-  const float dz = mimg32(a.z[j], a.z[i], (float)a.box[2], (float)(1.0 / a.box[2]));
+  const float dx = fix_diff(a.ux[j], a.ux[i], a.ul[0]);
+  const float dy = fix_diff(a.uy[j], a.uy[i], a.ul[1]);
+  const float dz = fix_diff(a.uz[j], a.uz[i], a.ul[2]);
   return sqrtf(dx * dx + dy * dy + dz * dz);
 }
 
@@ -412,6 +412,7 @@ __global__ void k_rho(McArgs a, int r, double* dF) {
 void launch_rho(const McArgs& a, bool shell, int r, cudaStream_t st) {
   const unsigned g = (unsigned)((a.N + 127) / 128);
   double* dF = const_cast<double*>(a.dF);
+  if (a.mixed && !shell) launch_fix_positions(a.N, a.x, a.y, a.z, a.box, a.ux, a.uy, a.uz, st);
   if (a.mixed) {
     if (shell) k_rho<true, true><<<g, 128, 0, st>>>(a, r, dF);
     else k_rho<false, true><<<g, 128, 0, st>>>(a, r, dF);
@@ -468,6 +469,7 @@ __global__ void __launch_bounds__(E_BLOCK) k_energy(McArgs a, int r, double* par
 
 void launch_energy(const McArgs& a, bool shell, int r, double* part, cudaStream_t st) {
   const int g = energy_blocks(a.N);
+  if (a.mixed && !shell) launch_fix_positions(a.N, a.x, a.y, a.z, a.box, a.ux, a.uy, a.uz, st);
   if (a.mixed) {
     if (shell) k_energy<true, true><<<g, E_BLOCK, 0, st>>>(a, r, part);
     else k_energy<false, true><<<g, E_BLOCK, 0, st>>>(a, r, part);

@@ -52,6 +52,7 @@ struct Ctx {
   double *vx = nullptr, *vy = nullptr, *vz = nullptr;
   double *fx = nullptr, *fy = nullptr, *fz = nullptr;
   double *x0 = nullptr, *y0 = nullptr, *z0 = nullptr;
+  uint32_t *ux = nullptr, *uy = nullptr, *uz = nullptr;  // fixed-point positions (mixed, kind 1)
   unsigned long long* max_disp2 = nullptr;
   int* nbr = nullptr;
   int* nbr_cnt = nullptr;
@@ -264,7 +265,13 @@ void fill_args(Ctx* c) {
   a.x = c->x;
   a.y = c->y;
   a.z = c->z;
-  for (int q = 0; q < 3; ++q) a.box[q] = c->box[q];
+  a.ux = c->ux;
+  a.uy = c->uy;
+  a.uz = c->uz;
+  for (int q = 0; q < 3; ++q) {
+    a.box[q] = c->box[q];
+    a.ul[q] = (float)(c->box[q] * 0x1p-32);
+  }
   a.rc = c->rc;
   a.mixed = c->mixed ? 1 : 0;
   a.screen = c->screen ? 1 : 0;
@@ -303,7 +310,11 @@ void fill_args(Ctx* c) {
   m.dFp = c->dFp;
   m.dF = c->dF;
   m.x0 = c->x0; m.y0 = c->y0; m.z0 = c->z0;
-  for (int q = 0; q < 3; ++q) m.box[q] = c->box[q];
+  m.ux = c->ux; m.uy = c->uy; m.uz = c->uz;
+  for (int q = 0; q < 3; ++q) {
+    m.box[q] = c->box[q];
+    m.ul[q] = (float)(c->box[q] * 0x1p-32);
+  }
   m.rc = c->rc;
   m.mass[0] = c->mass[0];
   m.mass[1] = c->mass[1];
@@ -1280,6 +1291,14 @@ static int init_impl(Ctx* c, const vcsgc_lattice* L, const uint8_t* types, const
   CK(cudaMemcpyAsync(c->x, hx.data(), sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->y, hy.data(), sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemcpyAsync(c->z, hz.data(), sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
+  if (c->mixed) {
+    // the mixed form's fixed-point copies, refreshed before each density
+    // pass and energy evaluation of the mixed kernels (fix_diff)
+    TRY(dalloc(c, &c->ux, c->N));
+    TRY(dalloc(c, &c->uy, c->N));
+    TRY(dalloc(c, &c->uz, c->N));
+    launch_fix_positions(c->N, c->x, c->y, c->z, c->box, c->ux, c->uy, c->uz, c->st);
+  }
 
   // ---- neighbour list (A1)
   TRY(dalloc(c, &c->nbr_cnt, c->N));
