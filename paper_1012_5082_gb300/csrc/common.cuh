@@ -198,6 +198,19 @@ __device__ __forceinline__ float spline32_dval_at(const Spline32& ds, int j, flo
 }
 
 // minimum-image separation in FP32 of two FP64 coordinates (difference in FP64)
+// Minimum image of d = x_j - x_i for positions kept in [0, L) (so |d| < L):
+// the image shift is -sign(d) L exactly when |d| > L/2, decided on the bit
+// pattern of d (a non-negative double orders like its bits; hb = the bits of
+// L/2), so a pair costs one FP64 FMA per axis instead of a multiply (or a
+// division), a rounding and an FMA.  For every pair within a cutoff below
+// L/2 it gives the double d - L rint(d / L) gives.
+__device__ __forceinline__ double mimg_w(double d, double L, long long hb) {
+  const long long b = __double_as_longlong(d);
+  const double s = (b & 0x7fffffffffffffffLL) > hb ? (b < 0 ? 1.0 : -1.0) : 0.0;
+  return fma(s, L, d);
+}
+__device__ __forceinline__ long long half_bits(double L) { return __double_as_longlong(0.5 * L); }
+
 // Explicit positions of the mixed form as fixed-point fractions of the box,
 // u = x / L 2^32 mod 2^32 per axis.  The difference of two words read as a
 // signed 32-bit integer is the minimum-image separation in units of L 2^-32,

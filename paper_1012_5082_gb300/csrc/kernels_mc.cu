@@ -19,9 +19,6 @@
 
 namespace vcsgc {
 
-__device__ __forceinline__ double min_image(double d, double L) {
-  return d - L * rint(d / L);
-}
 
 // Energy change of flipping site i of replica r, t -> t' = 1 - t:
 //   pair:     sum_k [phi_{t' t_k} - phi_{t t_k}](r_ik)
@@ -72,13 +69,14 @@ __device__ double delta_e(const McArgs& a, int r, int i, unsigned* err) {
     const int tp = 1 - t;
     const int cnt = a.nbr_cnt[i];
     const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
+    const long long hb[3] = {half_bits(a.box[0]), half_bits(a.box[1]), half_bits(a.box[2])};
     const double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
     double pair = 0.0, re = 0.0;
     for (int k = 0; k < cnt; ++k) {
       const int j = row[k];
-      const double dx = min_image(a.x[j] - xi, a.box[0]);
-      const double dy = min_image(a.y[j] - yi, a.box[1]);
-      const double dz = min_image(a.z[j] - zi, a.box[2]);
+      const double dx = mimg_w(a.x[j] - xi, a.box[0], hb[0]);
+      const double dy = mimg_w(a.y[j] - yi, a.box[1], hb[1]);
+      const double dz = mimg_w(a.z[j] - zi, a.box[2], hb[2]);
       const double rr = sqrt(dx * dx + dy * dy + dz * dz);
       if (rr >= a.rc) continue;
       const int tj = ty[j];
@@ -121,6 +119,7 @@ __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned
   // FP64 positions, or the mixed form's fixed-point words (fix_diff)
   const double xi = MIXED ? 0.0 : a.x[i], yi = MIXED ? 0.0 : a.y[i], zi = MIXED ? 0.0 : a.z[i];
   const uint32_t uxi = MIXED ? a.ux[i] : 0u, uyi = MIXED ? a.uy[i] : 0u, uzi = MIXED ? a.uz[i] : 0u;
+  const long long hb[3] = {half_bits(a.box[0]), half_bits(a.box[1]), half_bits(a.box[2])};
   const double* rho = a.rho + (a.rho_per_rep ? (long long)r * a.N : 0);
   const double rc2 = a.rc * a.rc;
   double part = 0.0;
@@ -170,9 +169,9 @@ __device__ double delta_e_warp(const McArgs& a, int r, int i, int lane, unsigned
           fm = (double)spline32_val_at(a.tab32.sp[3 + t], jj, tt);
         }
       } else {
-        const double dx = min_image(xj[u] - xi, a.box[0]);
-        const double dy = min_image(yj[u] - yi, a.box[1]);
-        const double dz = min_image(zj[u] - zi, a.box[2]);
+        const double dx = mimg_w(xj[u] - xi, a.box[0], hb[0]);
+        const double dy = mimg_w(yj[u] - yi, a.box[1], hb[1]);
+        const double dz = mimg_w(zj[u] - zi, a.box[2], hb[2]);
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= rc2) continue;
         double tt;
@@ -477,11 +476,12 @@ __device__ void commit_site(const McArgs& a, int r, int i, unsigned* err) {
     } else {
       const int cnt = a.nbr_cnt[i];
       const int tp = 1 - t;
+      const long long hb[3] = {half_bits(a.box[0]), half_bits(a.box[1]), half_bits(a.box[2])};
       for (int k = 0; k < cnt; ++k) {
         const int j = row[k];
-        const double dx = min_image(a.x[j] - a.x[i], a.box[0]);
-        const double dy = min_image(a.y[j] - a.y[i], a.box[1]);
-        const double dz = min_image(a.z[j] - a.z[i], a.box[2]);
+        const double dx = mimg_w(a.x[j] - a.x[i], a.box[0], hb[0]);
+        const double dy = mimg_w(a.y[j] - a.y[i], a.box[1], hb[1]);
+        const double dz = mimg_w(a.z[j] - a.z[i], a.box[2], hb[2]);
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 >= a.rc * a.rc) continue;
         if (a.mixed) {

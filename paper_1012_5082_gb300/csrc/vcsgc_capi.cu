@@ -2923,6 +2923,7 @@ int vcsgc_load(void* ctx, const char* path) {
        (md.empty() || std::fread(md.data(), sizeof(double), md.size(), f) == md.size()) &&
        std::fread(&nh, sizeof(Ctx::Nh), 1, f) == 1;
   std::fclose(f);
+  for (int q = 0; q < 3 && ok && pos; ++q) ok = std::isfinite(box[q]) && box[q] > 2.0 * c->rc;
   if (!ok) return fail(c, VCSGC_ERR_INVALID_ARG, "checkpoint does not match this context (sizes, schedule or form)");
   TRY(flush(c));
   CK(cudaStreamSynchronize(c->st));
@@ -2937,6 +2938,13 @@ int vcsgc_load(void* ctx, const char* path) {
   }
   if (pos) {
     for (int q = 0; q < 3; ++q) c->box[q] = box[q];
+    // positions into [0, L) as at init (the kernels' minimum image needs it)
+    for (int q = 0; q < 3; ++q)
+      for (long long i = 0; i < c->N; ++i) {
+        double& v = md[q * c->N + i];
+        v -= c->box[q] * std::floor(v / c->box[q]);
+        if (!(v < c->box[q]) || v < 0.0) v = 0.0;
+      }
     double* dst[3] = {c->x, c->y, c->z};
     for (int q = 0; q < 3; ++q)
       CK(cudaMemcpyAsync(dst[q], md.data() + q * c->N, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->st));
