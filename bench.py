@@ -851,6 +851,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--md-only", action="store_true", help="only the MD measurement (profiling)")
     ap.add_argument("--md-box", type=float, default=250.0, help="nanocrystal box (A) for --md-only")
+    ap.add_argument("--md-mixed", action="store_true", help="the mixed-precision form for --md-only")
     ap.add_argument("--multi-only", action="store_true", help="only the multicomponent measurement (profiling)")
     ap.add_argument("--da-reembed-only", action="store_true",
                     help="only delayed acceptance on the re-embedding workload (profiling)")
@@ -880,8 +881,8 @@ def main():
     from paper_1012_5082_gb300 import vcsgc as V
 
     if args.md_only:
-        print(json.dumps(md_bench(V, torch, torch.cuda.Stream(), local, steps=args.steps,
-                                  warmup=args.warmup, box=args.md_box)), flush=True)
+        print(json.dumps(md_bench(V, torch, torch.cuda.Stream(), local, steps=args.steps, warmup=args.warmup,
+                                  box=args.md_box, precision=1 if args.md_mixed else 0)), flush=True)
         return 0
     if args.multi_only:
         print(json.dumps(multi_bench(V, torch, torch.cuda.Stream(), local, sweeps=args.steps,
