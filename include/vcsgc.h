@@ -131,8 +131,9 @@ typedef struct {
   int32_t sched[6];
   int32_t precision;    /* VCSGC_PREC_FP64, or VCSGC_PREC_MIXED: pair, density and
                            embedding-table interpolation in FP32 (coefficients
-                           rounded to float, FP32 distances); rho sums, embedding
-                           differences, dE and force sums in FP64 */
+                           rounded to float, FP32 separations from fixed-point
+                           copies of the positions, exact minimum image); rho
+                           sums, embedding differences, dE and force sums in FP64 */
   int32_t n_replicas;   /* >= 1 */
   const double* phi_r;  /* per-replica phi, kappa, T, seed, c0 (n_replicas each) or NULL */
   const double* kappa_r;
