@@ -19,7 +19,7 @@ __global__ void k_md_rho(MdArgs m) {
   const int cnt = m.nbr_cnt[i];
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
   const uint32_t uxi = MIXED ? m.ux[i] : 0u, uyi = MIXED ? m.uy[i] : 0u, uzi = MIXED ? m.uz[i] : 0u;
-  const long long hbx = half_bits(m.box[0]), hby = half_bits(m.box[1]), hbz = half_bits(m.box[2]);
+  const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
   const double rc2 = m.rc * m.rc;
   double rho = 0.0;
   for (int k = 0; k < cnt; ++k) {
@@ -35,9 +35,9 @@ __global__ void k_md_rho(MdArgs m) {
       const int q = spline32_locate(sp, sqrtf(r2), t, m.err);
       rho += (double)spline32_val_at(sp, q, t);
     } else {
-      const double dx = mimg_w(m.x[j] - xi, m.box[0], hbx);
-      const double dy = mimg_w(m.y[j] - yi, m.box[1], hby);
-      const double dz = mimg_w(m.z[j] - zi, m.box[2], hbz);
+      const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+      const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+      const double dz = mimg(m.z[j] - zi, m.box[2], iz);
       const double r2 = dx * dx + dy * dy + dz * dz;
       if (r2 >= rc2) continue;
       rho += spline_val(m.tab.sp[3 + m.types[j]], r2 * rsqrt_nr(r2), m.err);
@@ -71,15 +71,15 @@ __global__ void k_md_rho_half(MdArgs m) {
   const int* row = m.nbr_h + i * m.K;
   const int cnt = m.cnt_h[i];
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
-  const long long hbx = half_bits(m.box[0]), hby = half_bits(m.box[1]), hbz = half_bits(m.box[2]);
+  const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
   const double rc2 = m.rc * m.rc;
   const int ti = m.types[i];
   double rho = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
-    const double dx = mimg_w(m.x[j] - xi, m.box[0], hbx);
-    const double dy = mimg_w(m.y[j] - yi, m.box[1], hby);
-    const double dz = mimg_w(m.z[j] - zi, m.box[2], hbz);
+    const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+    const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+    const double dz = mimg(m.z[j] - zi, m.box[2], iz);
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= rc2) continue;
     const double r = r2 * rsqrt_nr(r2);
@@ -198,14 +198,14 @@ __device__ __forceinline__ void force_half_row(const MdArgs& m, long long i, dou
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
   const int ti = m.types[i];
   const double Fi = m.dFp[i];
-  const long long hbx = half_bits(m.box[0]), hby = half_bits(m.box[1]), hbz = half_bits(m.box[2]);
+  const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
   const double rc2 = m.rc * m.rc;
   double fx = 0.0, fy = 0.0, fz = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int j = row[k];
-    const double dx = mimg_w(m.x[j] - xi, m.box[0], hbx);
-    const double dy = mimg_w(m.y[j] - yi, m.box[1], hby);
-    const double dz = mimg_w(m.z[j] - zi, m.box[2], hbz);
+    const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+    const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+    const double dz = mimg(m.z[j] - zi, m.box[2], iz);
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= rc2) continue;
     const double ir = rsqrt_nr(r2);
@@ -250,7 +250,7 @@ __device__ __forceinline__ void force_row(const MdArgs& m, long long i, double& 
   const double xi = m.x[i], yi = m.y[i], zi = m.z[i];
   const int ti = m.types[i];
   const double Fi = m.dFp[i];
-  const long long hbx = half_bits(m.box[0]), hby = half_bits(m.box[1]), hbz = half_bits(m.box[2]);
+  const double ix = 1.0 / m.box[0], iy = 1.0 / m.box[1], iz = 1.0 / m.box[2];
   const double rc2 = m.rc * m.rc;
   double fx = 0.0, fy = 0.0, fz = 0.0;
   const float Fi32 = (float)Fi;
@@ -277,9 +277,9 @@ __device__ __forceinline__ void force_row(const MdArgs& m, long long i, double& 
       fz += (double)(gr * dz);
       continue;
     }
-    const double dx = mimg_w(m.x[j] - xi, m.box[0], hbx);
-    const double dy = mimg_w(m.y[j] - yi, m.box[1], hby);
-    const double dz = mimg_w(m.z[j] - zi, m.box[2], hbz);
+    const double dx = mimg(m.x[j] - xi, m.box[0], ix);
+    const double dy = mimg(m.y[j] - yi, m.box[1], iy);
+    const double dz = mimg(m.z[j] - zi, m.box[2], iz);
     const double r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= rc2) continue;
     const double ir = rsqrt_nr(r2);
