@@ -187,17 +187,17 @@ def test_multicomponent_object_surrogate(V, torch, tab):
     # that sweep, and are then re-synced from it
     prev_o, prev_m = o.obs(), m.observables(0)
     compared = 0
-    for s in range(4):
+    for sw in range(4):
         m.sweep(1)
         o.parallel_steps(m.steps_per_sweep)
         oo, om = o.obs(), m.observables(0)
         if not np.array_equal(m.types(), o.types):
-            assert oo["near_ties"] > prev_o["near_ties"], f"sweep {s}: species differ without a flagged tie"
+            assert oo["near_ties"] > prev_o["near_ties"], f"sweep {sw}: species differ without a flagged tie"
             m.set_types(o.types)
             om = m.observables(0)
         elif oo["near_ties"] == prev_o["near_ties"]:
             for key in ("stage1_accepts", "local_accepts", "global_accepts", "flips"):
-                assert om[key] - prev_m[key] == oo[key] - prev_o[key], (s, key)
+                assert om[key] - prev_m[key] == oo[key] - prev_o[key], (sw, key)
             compared += 1
         prev_o, prev_m = oo, om
     assert oo["near_ties"] <= MAX_TIES and compared >= 1, (oo["near_ties"], compared)
