@@ -485,7 +485,9 @@ int vcsgc_minimize(void* ctx, double ftol, int64_t max_iter, int64_t* iters, dou
  * sizes, replica count, schedule, form); the Philox streams are counters, so
  * n sweeps, save, load into a new context and m sweeps give the species of
  * n + m sweeps bit for bit.  The surrogate (vcsgc_set_surrogate) is not
- * saved.  Errors: INVALID_ARG (path, mismatch), CUDA. */
+ * saved.  Positions read back are reduced into [0, L) per axis.  Errors:
+ * INVALID_ARG (path, mismatch, or a box that is not finite or not longer
+ * than 2 r_c), CUDA. */
 int vcsgc_save(void* ctx, const char* path);
 int vcsgc_load(void* ctx, const char* path);
 
