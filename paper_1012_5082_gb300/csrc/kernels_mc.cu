@@ -404,7 +404,11 @@ __global__ void __launch_bounds__(MC_BLOCK) k_propose(McArgs a) {
 }
 
 // General form: one warp per trial.  Same draws and rule as k_propose.
-constexpr int MCW_BLOCK = 128;  // 4 trials per block
+// One trial (one warp) per block: a colour step of a nanocrystal holds a
+// few hundred to a few thousand trials, and single-warp blocks spread them
+// over every SM (four-warp blocks left the 343 trials of a 17 nm cell on 86
+// SMs, and up to 12 of the 1,331 of a 25 nm cell on one SM against 9).
+constexpr int MCW_BLOCK = 32;
 
 template <bool REEMBED, bool MIXED>
 __global__ void __launch_bounds__(MCW_BLOCK) k_propose_warp(McArgs a) {
